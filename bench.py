@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark of the Gauss-Legendre SHT round trip on GB300.
+
+One step = one scalar round trip (synthesis then analysis, each with its
+Legendre stage and longitude FFT) over a batch of seeded synthetic fields at
+N = 1023 (nlat = 1024, nphi = 2048), batch 16, inputs resident in HBM.  The
+metric is round trips per second (fields x steps / time), with nominal
+GFLOP/s; the plain FP64 path is timed on the same workload for the ratio.
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas
+(each rank transforms its own batch, no collective): weak scaling.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode f32|f64] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+LMAX, NLAT, NPHI, BATCH = 1023, 1024, 2048, 16
+WORKLOAD = f"scalar SHT round trip N={LMAX} nlat={NLAT} nphi={NPHI} batch={BATCH}"
+METRIC = "SHT round-trips/s (N=1023, batch 16)"
+UNIT = "round-trips/s"
+
+
+def nlm_of(lmax, mmax=None):
+    mmax = lmax if mmax is None else mmax
+    return (mmax + 1) * (lmax + 1) - mmax * (mmax + 1) // 2
+
+
+def nominal_flops_per_rt(lmax=LMAX, nlat=NLAT, nphi=NPHI):
+    """Nominal flop count of one round trip of one field: per direction
+    4 flops per (mode, latitude) plus 2.5 nphi log2(nphi) per FFT row."""
+    per_dir = 4.0 * nlm_of(lmax) * nlat + 2.5 * nphi * math.log2(nphi) * nlat
+    return 2.0 * per_dir
+
+
+def legendre_flops_per_launch(batch, lmax=LMAX, nlat=NLAT):
+    """Algorithmic flops of one Legendre launch on `batch` fields: per
+    (mode, latitude pair) the recurrence (2 mul + 1 fma = 4 flops, shared by
+    the batch) plus one complex x real accumulate per field (4 flops)."""
+    npairs = (nlat + 1) // 2
+    return nlm_of(lmax) * npairs * (4.0 + 4.0 * batch)
+
+
+def fp32_alu_peak(sm_mhz):
+    """FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 flops x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6
+
+
+FP64_PEAK_NOMINAL = 1.25e12  # GB300 FP64 rate (nominal table of the pool)
+
+
+# ---------------------------------------------------------------------------
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(seconds_hint=True):
+    """The oracle as it stands, one field round trip at the bench size, on all host cores."""
+    import numpy as np
+
+    import oracle
+    from paper_1202_6522_gb300 import synthetic
+    oracle.build()
+    a = synthetic.spectrum(LMAX, seed=0)
+    t0 = time.perf_counter()
+    g = oracle.synth(LMAX, LMAX, NLAT, NPHI, a)
+    r = oracle.analys(LMAX, LMAX, NLAT, NPHI, g)
+    dt = time.perf_counter() - t0
+    assert np.isfinite(r).all()
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"1 field round trip at N={LMAX} ({dt:.1f} s, direct Fourier sums)"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    import numpy as np
+    from paper_1202_6522_gb300 import synthetic
+    a = synthetic.spectrum(LMAX, seed=0)
+    # each step: one field round trip of the same workload, on all host cores
+    for _ in range(args.warmup):
+        oracle.analys(LMAX, LMAX, NLAT, NPHI, oracle.synth(LMAX, LMAX, NLAT, NPHI, a))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = oracle.analys(LMAX, LMAX, NLAT, NPHI, oracle.synth(LMAX, LMAX, NLAT, NPHI, a))
+    dt = time.perf_counter() - t0
+    assert np.isfinite(r).all()
+    value = args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded N(0,1)/(n+1) spectra)",
+        "config": {"workload": WORKLOAD + " (CPU oracle: 1 field per step)", "lmax": LMAX, "nlat": NLAT,
+                   "nphi": NPHI, "batch": 1},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                         "sample": f"{args.steps} round trips of 1 field at N={LMAX}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def time_path(sht, torch, a, steps, warmup, stream, profile=False):
+    """Device-timed round trips on inputs resident in HBM.  Returns (ms per step, kernel table)."""
+    from paper_1202_6522_gb300 import _capi as C
+    for _ in range(warmup):
+        sht.analys_(sht.synth_(a))
+    torch.cuda.synchronize()
+    if profile:
+        C.sht_profile(sht._h, True)
+        C.sht_profile_read(sht._h)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        sht.analys_(sht.synth_(a))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    table = None
+    if profile:
+        table = C.sht_profile_read(sht._h)
+        C.sht_profile(sht._h, False)
+    return ms, table
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1202_6522_gb300 import SHT, synthetic
+    from paper_1202_6522_gb300 import build as B
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    B.build()
+    sht = SHT(LMAX, LMAX, NLAT, NPHI, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    cdt = torch.complex64 if args.mode == "f32" else torch.complex128
+    a_np = synthetic.spectrum(LMAX, batch=BATCH, seed=rank)
+    a = torch.from_numpy(a_np).to(dev, cdt)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # accuracy of this run's path against the FP64 oracle on one field
+    r = sht.analys_(sht.synth_(a))
+    torch.cuda.synchronize()
+    a_in = a[0].cpu().numpy().astype(np.complex128)
+    ref_err = float(np.abs(r[0].cpu().numpy().astype(np.complex128) - a_in).max())
+
+    # --- device-timed region (max over ranks) ---
+    for _ in range(args.warmup):
+        sht.analys_(sht.synth_(a))
+    barrier()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    from paper_1202_6522_gb300 import _capi as C
+    C.sht_profile(sht._h, True)
+    C.sht_profile_read(sht._h)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        sht.analys_(sht.synth_(a))
+    e1.record(stream)
+    barrier()
+    ms_total = e0.elapsed_time(e1)
+    table = C.sht_profile_read(sht._h)
+    C.sht_profile(sht._h, False)
+    clk = clocks.stop()
+    t = torch.tensor([ms_total], device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * BATCH * args.steps / (ms_total / 1e3)
+
+    # --- end to end through the public API with pinned host buffers ---
+    host_in = torch.from_numpy(a_np).to(cdt).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    for _ in range(2):
+        d_in = host_in.to(dev, non_blocking=True)
+        host_out.copy_(sht.analys_(sht.synth_(d_in)), non_blocking=True)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        d_in = host_in.to(dev, non_blocking=True)
+        host_out.copy_(sht.analys_(sht.synth_(d_in)), non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    bytes_step = host_in.numel() * host_in.element_size()
+    e2e = {"value": world * BATCH * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step}
+
+    # --- the plain FP64 path on the same workload (the metric's denominator) ---
+    fp64 = None
+    if args.mode != "f64":
+        a64 = torch.from_numpy(a_np).to(dev, torch.complex128)
+        ms64, tab64 = time_path(sht, torch, a64, max(2, args.steps // 4), 1, stream, profile=True)
+        fp64 = {"round_trips_per_s": world * BATCH / (ms64 / 1e3), "ms_per_step": ms64,
+                "kernels_ms": {k: v[0] / v[1] for k, v in tab64.items()}}
+
+    if rank != 0:
+        return 0
+    # dominant kernel and its roofline
+    dom = max(table.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    dom_avg = dom_ms / dom_n
+    flops = legendre_flops_per_launch(BATCH) if dom_name.startswith("legendre") else None
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    if args.mode == "f32":
+        peak = fp32_alu_peak(sm_max)
+        peak_note = f"FP32 FMA: 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz"
+    else:
+        peak = FP64_PEAK_NOMINAL
+        peak_note = "FP64 nominal 1.25 TFLOP/s"
+    achieved = flops / (dom_avg / 1e3) if flops else None
+    roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved / 1e12 if achieved else None,
+            "peak": peak / 1e12, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+            "traffic": None, "peak_source": peak_note,
+            "kernel_avg_ms": dom_avg, "launches": dom_n}
+    kernels = {k: {"avg_ms": v[0] / v[1], "launches": v[1], "share": v[0] / sum(x[0] for x in table.values())}
+               for k, v in table.items()}
+    launches = sum(v[1] for v in table.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.mode, "data": "synthetic (seeded N(0,1)/(n+1) spectra)",
+        "config": {"workload": WORKLOAD, "lmax": LMAX, "nlat": NLAT, "nphi": NPHI, "batch": BATCH,
+                   "path": "FP32 on-the-fly recurrence with exponent scale" if args.mode == "f32"
+                   else "plain FP64 on-the-fly", "l2": "inputs larger than L2 (spectra+grids > 129 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "gflops_nominal": value * nominal_flops_per_rt() / 1e9,
+        "elements_per_s": value * (LMAX + 1) ** 3,
+        "roofline": roof,
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": e2e,
+        "round_trip_max_err_vs_input": ref_err,
+    }
+    if fp64:
+        line["fp64_plain"] = fp64
+        line["speedup_vs_fp64_plain"] = value / fp64["round_trips_per_s"]
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

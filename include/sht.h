@@ -1,0 +1,164 @@
+/*
+ * sht.h -- C ABI of libsht, a Gauss-Legendre spherical harmonic transform for
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The method is the one of Schaeffer, "Efficient Spherical Harmonic Transforms
+ * aimed at pseudo-spectral numerical simulations" (arXiv:1202.6522):
+ *   synthesis  f(theta, phi) = sum_m ( sum_n f_n^m P_n^m(cos theta) ) e^{i m phi}
+ *              (Sec. 2.2, Eq. synth_direct, then a real FFT in longitude),
+ *   analysis   f_n^m = sum_j w_j P_n^m(cos theta_j) f_m(theta_j)
+ *              (Sec. 2.3, Eq. gauss, after a real FFT in longitude),
+ * with P_n^m generated on the fly by the recurrence of Sec. 3.2, north/south
+ * folding by the mirror symmetry of Sec. 3.1 and the underflow rescaling of
+ * Sec. 3.5.
+ *
+ * Conventions
+ *   - Orthonormal P_n^m as produced by the recurrence of Sec. 3.2: P_m^m > 0,
+ *     i.e. no (-1)^m Condon-Shortley factor.
+ *   - Real fields: only m >= 0 is stored (Hermitian symmetry, Sec. 3.1).
+ *     Im f_n^0 is ignored on input and written as 0 on output.
+ *   - Spectral layout: packed m-major, idx(n, m) = m (2 lmax + 3 - m) / 2 + (n - m)
+ *     for 0 <= m <= mmax, m <= n <= lmax; interleaved complex (re, im).
+ *     nlm = sht_nlm(h) coefficients per field.
+ *   - Grid layout: [nlat][nphi] reals per field, row j at the Gauss node x_j
+ *     (x descending: north to south), column k at phi_k = 2 pi k / nphi.
+ *   - Batches are contiguous: field b of a spectral array starts at b * nlm
+ *     complex values, of a grid at b * nlat * nphi reals.
+ *   - Vector fields: v = grad_H S + r x grad_H T, that is
+ *       v_theta = dS/dtheta - (1/sin theta) dT/dphi,
+ *       v_phi   = (1/sin theta) dS/dphi + dT/dtheta;
+ *     vector analysis divides by n(n+1) and returns 0 at n = 0.
+ *   - Adjoints are taken for <a, b> = sum_packed Re(conj(a) b) (m = 0
+ *     imaginary parts excluded) and <f, g> = sum f g.
+ *
+ * Memory and streams
+ *   - Every data pointer is a DEVICE pointer owned by the caller, contiguous,
+ *     aligned to at least 16 bytes.  Element type follows `mode`:
+ *       SHT_F64: double (spectral arrays: pairs of doubles);
+ *       SHT_F32: float.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls only
+ *     enqueue work; they do not synchronise.  Input and output must not alias.
+ *   - The handle owns its tables and a scratch buffer that grows on demand
+ *     (the first call at a larger batch allocates; sht_reserve allocates ahead).
+ *     Calls on one handle must not run concurrently on different streams.
+ *
+ * Errors
+ *   Every int-returning function returns SHT_OK (0) or a negative code;
+ *   sht_last_error() gives a message for the calling thread.  Argument errors
+ *   are detected on the host before anything is enqueued.
+ */
+#ifndef SHT_H
+#define SHT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SHT_API __attribute__((visibility("default")))
+#else
+#define SHT_API
+#endif
+
+typedef struct sht_plan *sht_handle;
+
+enum {
+    SHT_OK = 0,
+    SHT_EINVAL = -1,       /* bad argument (sizes, null pointer, mode)           */
+    SHT_ENOMEM = -2,       /* device or host allocation failed                   */
+    SHT_ECUDA = -3,        /* a CUDA runtime call failed                         */
+    SHT_ETIMEOUT = -4,     /* a bounded device-side wait gave up                 */
+    SHT_EUNSUPPORTED = -5  /* valid but not supported (e.g. nphi not a power of 2) */
+};
+
+enum {
+    SHT_F64 = 0,  /* FP64 throughout: the plain path                            */
+    SHT_F32 = 1   /* FP32 data and recurrence with an explicit exponent scale   */
+};
+
+/* Build a plan (Sec. 2.3 nodes/weights, Sec. 3.2 recurrence tables, FFT
+ * twiddles) on the host and copy it to the current CUDA device.
+ * Requires 0 <= mmax <= lmax, nlat >= lmax + 1 (exactness of the quadrature,
+ * Sec. 2.3), nphi >= 2 mmax + 1 and nphi >= 2 a power of two (SHT_EUNSUPPORTED
+ * otherwise).  On success *out receives the handle; on failure *out is NULL. */
+SHT_API int sht_create(int lmax, int mmax, int nlat, int nphi, sht_handle *out);
+
+/* Free the plan and everything it owns.  NULL is ignored.  The caller must
+ * make sure no work using the handle is still running. */
+SHT_API void sht_destroy(sht_handle h);
+
+/* Pre-allocate scratch for transforms of up to `batch` fields in `mode`, so
+ * that later calls at that size allocate nothing. */
+SHT_API int sht_reserve(sht_handle h, int batch, int mode);
+
+/* Scalar synthesis, Sec. 2.2: spec [batch][nlm] complex -> grid [batch][nlat][nphi]. */
+SHT_API int sht_synth(sht_handle h, const void *spec, void *grid, int batch, int mode, void *stream);
+
+/* Scalar analysis, Sec. 2.3 (Gauss-Legendre quadrature):
+ * grid [batch][nlat][nphi] -> spec [batch][nlm] complex. */
+SHT_API int sht_analys(sht_handle h, const void *grid, void *spec, int batch, int mode, void *stream);
+
+/* Spheroidal/toroidal synthesis (vector transform named in Sec. 4):
+ * S, T [batch][nlm] complex -> v_theta, v_phi [batch][nlat][nphi]. */
+SHT_API int sht_synth_vec(sht_handle h, const void *S, const void *T, void *vt, void *vp,
+                  int batch, int mode, void *stream);
+
+/* Spheroidal/toroidal analysis: v_theta, v_phi -> S, T (divided by n(n+1)). */
+SHT_API int sht_analys_vec(sht_handle h, const void *vt, const void *vp, void *S, void *T,
+                   int batch, int mode, void *stream);
+
+/* Adjoint of sht_synth: grid -> spec,
+ *   b_n^m = c_m sum_j P_n^m(x_j) sum_k g_jk e^{-i m phi_k},  c_0 = 1, c_m = 2. */
+SHT_API int sht_synth_adj(sht_handle h, const void *grid, void *spec, int batch, int mode, void *stream);
+
+/* Adjoint of sht_analys: spec -> grid,
+ *   g_jk = (2 pi / nphi) w_j sum_{m>=0} Re(e^{i m phi_k} sum_n P_n^m b_n^m). */
+SHT_API int sht_analys_adj(sht_handle h, const void *spec, void *grid, int batch, int mode, void *stream);
+
+/* Adjoint of sht_synth_vec: (g_theta, g_phi) -> (S', T'). */
+SHT_API int sht_synth_vec_adj(sht_handle h, const void *gt, const void *gp, void *S, void *T,
+                      int batch, int mode, void *stream);
+
+/* Adjoint of sht_analys_vec: (S', T') -> (g_theta, g_phi). */
+SHT_API int sht_analys_vec_adj(sht_handle h, const void *S, const void *T, void *gt, void *gp,
+                       int batch, int mode, void *stream);
+
+/* Layout helpers: number of packed coefficients, and idx(n, m) (-1 if out of range). */
+SHT_API int sht_nlm(sht_handle h);
+SHT_API int sht_lm_index(sht_handle h, int n, int m);
+
+/* Host copies of the Gauss nodes x_j = cos(theta_j) (descending) and weights
+ * w_j, each an array of nlat doubles owned by the caller. */
+SHT_API int sht_gauss(sht_handle h, double *x, double *w);
+
+/* Synchronise `stream` and report any CUDA error raised by work enqueued by
+ * this library (SHT_ECUDA), or SHT_OK. */
+SHT_API int sht_sync_status(sht_handle h, void *stream);
+
+/* Per-kernel timing, for measurement (no counterpart in the paper).  While
+ * enabled, every kernel the handle launches is bracketed by CUDA events on the
+ * call's stream.  sht_profile_read synchronises those events and writes, for
+ * each kernel kind k < min(cap, SHT_NKERNELS), the summed duration in
+ * milliseconds into ms[k] and the number of launches into count[k], then
+ * clears the record.  Kind names: sht_kernel_name(k). */
+enum {
+    SHT_K_LEGENDRE_SYNTH = 0,
+    SHT_K_LEGENDRE_ANALYS = 1,
+    SHT_K_LEGENDRE_SYNTH_VEC = 2,
+    SHT_K_LEGENDRE_ANALYS_VEC = 3,
+    SHT_K_FFT_SYNTH = 4,
+    SHT_K_FFT_ANALYS = 5,
+    SHT_NKERNELS = 6
+};
+SHT_API int sht_profile(sht_handle h, int enable);
+SHT_API int sht_profile_read(sht_handle h, double *ms, int *count, int cap);
+SHT_API const char *sht_kernel_name(int kind);
+
+/* Message for the last error raised in the calling thread ("" if none). */
+SHT_API const char *sht_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHT_H */

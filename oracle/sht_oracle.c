@@ -246,23 +246,6 @@ static void fourier_synth_row(const trig_table *t, int mmax, const double *F,
     }
 }
 
-/* F[m] = scale * sum_k row[k] e^{-i m phi_k}, m = 0..mmax (interleaved complex). */
-static void fourier_analys_row(const trig_table *t, int mmax, const double *row,
-                               double scale, double *F)
-{
-    int nphi = t->nphi;
-    for (int m = 0; m <= mmax; ++m) {
-        double re = 0.0, im = 0.0;
-        for (int k = 0; k < nphi; ++k) {
-            int q = (int)(((long)m * k) % nphi);
-            re += row[k] * t->c[q];
-            im -= row[k] * t->s[q];
-        }
-        F[2 * m] = scale * re;
-        F[2 * m + 1] = scale * im;
-    }
-}
-
 /* ---------------------------------------------------------------------------
  * Scalar synthesis (Sec. 2.2): F_m(theta_j) = sum_{n=m}^{lmax} f_n^m P_n^m(x_j),
  * f(theta_j, phi_k) = sum_m c_m Re(F_m e^{i m phi_k}).
@@ -330,31 +313,36 @@ static void scalar_analys_core(int lmax, int mmax, int nlat, int nphi, const dou
     double *w = (double *)malloc(sizeof(double) * nlat);
     oracle_gauss(nlat, x, w);
     int nm = ms ? nms : mmax + 1;
-    int mtop = 0;
-    for (int q = 0; q < nm; ++q) { int m = ms ? ms[q] : q; if (m > mtop) mtop = m; }
-    double *F = (double *)malloc(sizeof(double) * (size_t)nlat * (mtop + 1) * 2);
     trig_table t = trig_make(nphi);
     double fscale = adjoint_of_synthesis ? 1.0 : 2.0 * PI / nphi;
-#pragma omp parallel for schedule(static, 1)
-    for (int j = 0; j < nlat; ++j)
-        fourier_analys_row(&t, mtop, grid + (size_t)j * nphi, fscale, F + (size_t)j * (mtop + 1) * 2);
-    trig_free(&t);
+    /* Legendre stage: OpenMP over the orders, cyclic assignment (Sec. 3.3) */
 #pragma omp parallel
     {
         double *col = (double *)malloc(sizeof(double) * (lmax + 1));
         double *acc = (double *)malloc(sizeof(double) * 2 * (lmax + 1));
+        double *F = (double *)malloc(sizeof(double) * 2 * (size_t)nlat);
 #pragma omp for schedule(static, 1)
         for (int q = 0; q < nm; ++q) {
             int m = ms ? ms[q] : q;
+            /* F_m(theta_j) = fscale sum_k f_jk e^{-i m phi_k} for this order */
+            for (int j = 0; j < nlat; ++j) {
+                const double *row = grid + (size_t)j * nphi;
+                double re = 0.0, im = 0.0;
+                for (int k = 0; k < nphi; ++k) {
+                    int qq = (int)(((long)m * k) % nphi);
+                    re += row[k] * t.c[qq];
+                    im -= row[k] * t.s[qq];
+                }
+                F[2 * j] = fscale * re;
+                F[2 * j + 1] = fscale * im;
+            }
             memset(acc, 0, sizeof(double) * 2 * (lmax + 1));
             for (int j = 0; j < nlat; ++j) {
                 plm_order(lmax, m, x[j], col);
                 double wj = adjoint_of_synthesis ? 1.0 : w[j];
-                double fr = F[((size_t)j * (mtop + 1) + m) * 2];
-                double fi = F[((size_t)j * (mtop + 1) + m) * 2 + 1];
                 for (int n = m; n <= lmax; ++n) {
-                    acc[2 * (n - m)] += wj * col[n - m] * fr;
-                    acc[2 * (n - m) + 1] += wj * col[n - m] * fi;
+                    acc[2 * (n - m)] += wj * col[n - m] * F[2 * j];
+                    acc[2 * (n - m) + 1] += wj * col[n - m] * F[2 * j + 1];
                 }
             }
             double cm = adjoint_of_synthesis ? (m == 0 ? 1.0 : 2.0) : 1.0;
@@ -366,8 +354,9 @@ static void scalar_analys_core(int lmax, int mmax, int nlat, int nphi, const dou
         }
         free(col);
         free(acc);
+        free(F);
     }
-    free(F);
+    trig_free(&t);
     free(x);
     free(w);
 }
@@ -484,35 +473,38 @@ static void vector_analys_core(int lmax, int mmax, int nlat, int nphi, const dou
     double *w = (double *)malloc(sizeof(double) * nlat);
     oracle_gauss(nlat, x, w);
     int nm = ms ? nms : mmax + 1;
-    int mtop = 0;
-    for (int q = 0; q < nm; ++q) { int m = ms ? ms[q] : q; if (m > mtop) mtop = m; }
-    size_t fsz = (size_t)nlat * (mtop + 1) * 2;
-    double *Ft = (double *)malloc(sizeof(double) * fsz);
-    double *Fp = (double *)malloc(sizeof(double) * fsz);
     trig_table t = trig_make(nphi);
     double fscale = adjoint_of_synthesis ? 1.0 : 2.0 * PI / nphi;
-#pragma omp parallel for schedule(static, 1)
-    for (int j = 0; j < nlat; ++j) {
-        fourier_analys_row(&t, mtop, vt + (size_t)j * nphi, fscale, Ft + (size_t)j * (mtop + 1) * 2);
-        fourier_analys_row(&t, mtop, vp + (size_t)j * nphi, fscale, Fp + (size_t)j * (mtop + 1) * 2);
-    }
-    trig_free(&t);
 #pragma omp parallel
     {
         double *col = (double *)malloc(sizeof(double) * (lmax + 1));
         double *dcol = (double *)malloc(sizeof(double) * (lmax + 1));
         double *acc = (double *)malloc(sizeof(double) * 4 * (lmax + 1));
+        double *Ft = (double *)malloc(sizeof(double) * 2 * (size_t)nlat);
+        double *Fp = (double *)malloc(sizeof(double) * 2 * (size_t)nlat);
 #pragma omp for schedule(static, 1)
         for (int q = 0; q < nm; ++q) {
             int m = ms ? ms[q] : q;
+            for (int j = 0; j < nlat; ++j) {
+                const double *rt = vt + (size_t)j * nphi, *rp = vp + (size_t)j * nphi;
+                double tr = 0.0, ti = 0.0, pr = 0.0, pim = 0.0;
+                for (int k = 0; k < nphi; ++k) {
+                    int qq = (int)(((long)m * k) % nphi);
+                    tr += rt[k] * t.c[qq];
+                    ti -= rt[k] * t.s[qq];
+                    pr += rp[k] * t.c[qq];
+                    pim -= rp[k] * t.s[qq];
+                }
+                Ft[2 * j] = fscale * tr; Ft[2 * j + 1] = fscale * ti;
+                Fp[2 * j] = fscale * pr; Fp[2 * j + 1] = fscale * pim;
+            }
             memset(acc, 0, sizeof(double) * 4 * (lmax + 1));
             for (int j = 0; j < nlat; ++j) {
                 double s = sqrt((1.0 - x[j]) * (1.0 + x[j]));
                 plm_order(lmax, m, x[j], col);
                 dtheta_order(lmax, m, x[j], col, dcol);
                 double wj = adjoint_of_synthesis ? 1.0 : w[j];
-                size_t o = ((size_t)j * (mtop + 1) + m) * 2;
-                double Vtr = Ft[o], Vti = Ft[o + 1], Vpr = Fp[o], Vpi = Fp[o + 1];
+                double Vtr = Ft[2 * j], Vti = Ft[2 * j + 1], Vpr = Fp[2 * j], Vpi = Fp[2 * j + 1];
                 double msj = (double)m / s;
                 for (int n = m; n <= lmax; ++n) {
                     double P = col[n - m], dP = dcol[n - m];
@@ -538,9 +530,10 @@ static void vector_analys_core(int lmax, int mmax, int nlat, int nphi, const dou
         free(col);
         free(dcol);
         free(acc);
+        free(Ft);
+        free(Fp);
     }
-    free(Ft);
-    free(Fp);
+    trig_free(&t);
     free(x);
     free(w);
 }

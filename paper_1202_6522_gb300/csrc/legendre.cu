@@ -1,0 +1,765 @@
+// legendre.cu -- the per-order Legendre stage of the Gauss-Legendre SHT.
+//
+// Synthesis (Sec. 2.2, Eq. synth_direct): for each order m and each latitude
+// pair (x, -x), sum over n the spectral coefficients times P_n^m, split by the
+// parity of n - m (mirror symmetry, Sec. 3.1):
+//   E = sum_{n-m even} f_n^m P_n^m(x),  O = sum_{n-m odd} f_n^m P_n^m(x),
+//   f_m(x) = E + O,  f_m(-x) = E - O   (the fold is applied by the FFT kernel).
+// Analysis (Sec. 2.3, Eq. gauss): with s = w (F(x) + F(-x)), d = w (F(x) - F(-x))
+// prepared by the FFT kernel, f_n^m = sum_pairs P_n^m(x) (s if n-m even else d).
+//
+// P_n^m is generated on the fly by the recurrence of Sec. 3.2, held in
+// registers, one thread per latitude pair (LPT pairs per thread); the
+// coefficients (a_n^m, b_n^m) and the spectral values are staged through
+// shared memory and read as broadcasts.  Underflow is handled as in Sec. 3.5:
+// a value is y * 2^(-S k); while k > 0 it is left out of the sums and the
+// recurrence rescales y by 2^-S when it exceeds 1.  Warps in which every pair
+// is still scaled skip the accumulation (the dynamic polar optimisation).
+//
+// Analysis reduces over latitudes without atomics: each thread sums its own
+// pairs in registers for K consecutive degrees, a warp-level transposing
+// butterfly leaves one partial per lane, and the warps' partials are added in
+// shared memory in a fixed order, so results are bitwise reproducible.
+#include <cuda_runtime.h>
+
+#include "sht_internal.h"
+
+namespace sht {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T> __device__ __forceinline__ bool abs_ge_one(T y);
+template <> __device__ __forceinline__ bool abs_ge_one<double>(double y)
+{
+    return (__double2hiint(y) & 0x7fffffff) >= 0x3ff00000;
+}
+template <> __device__ __forceinline__ bool abs_ge_one<float>(float y)
+{
+    return (__float_as_int(y) & 0x7fffffff) >= 0x3f800000;
+}
+
+template <typename T> __device__ __forceinline__ T down_scale();
+template <> __device__ __forceinline__ double down_scale<double>() { return 0x1p-240; }
+template <> __device__ __forceinline__ float down_scale<float>() { return 0x1p-64f; }
+
+// One step of P_n = a x P_{n-1} + b P_{n-2} for LPT pairs.  With CHECK the
+// rescaling of Sec. 3.5 is applied and c[] receives the value entering the
+// sums (0 while k > 0); without it c[] is the value itself.
+template <typename T, int LPT, bool CHECK>
+__device__ __forceinline__ void rec_step(T a, T b, const T (&x)[LPT], T (&y1)[LPT], T (&y2)[LPT],
+                                         int (&k)[LPT], T (&c)[LPT])
+{
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) {
+        T yn = fma(a * x[i], y1[i], b * y2[i]);
+        y2[i] = y1[i];
+        y1[i] = yn;
+        if (CHECK) {
+            if (k[i] > 0 && abs_ge_one(yn)) {
+                y1[i] *= down_scale<T>();
+                y2[i] *= down_scale<T>();
+                k[i] -= 1;
+            }
+            c[i] = (k[i] == 0) ? y1[i] : T(0);
+        } else {
+            c[i] = yn;
+        }
+    }
+}
+
+template <typename T, int LPT>
+__device__ __forceinline__ int kmax_of(const int (&k)[LPT])
+{
+    int r = 0;
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) r = max(r, k[i]);
+    return r;
+}
+
+template <typename T, int LPT>
+__device__ __forceinline__ int kmin_of(const int (&k)[LPT])
+{
+    int r = k[0];
+#pragma unroll
+    for (int i = 1; i < LPT; ++i) r = min(r, k[i]);
+    return r;
+}
+
+// Warp butterfly that sums V values (V a multiple of 32) over the 32 lanes and
+// leaves lane l holding the sums of values [l*V/32, (l+1)*V/32) in v[0..V/32).
+template <typename T, int V>
+__device__ __forceinline__ void warp_transpose_reduce(T (&v)[V], int lane)
+{
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int o = 16 >> s;
+        const int h = V >> (s + 1);
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int q = 0; q < h; ++q) {
+            T send = up ? v[q] : v[q + h];
+            T keep = up ? v[q + h] : v[q];
+            v[q] = keep + __shfl_xor_sync(kFull, send, o);
+        }
+    }
+}
+
+__device__ __forceinline__ long col_of(int lmax, int m) { return (long)m * (2 * lmax + 3 - m) / 2; }
+
+// ---------------------------------------------------------------------------
+// Scalar synthesis.  grid.x = (m, pair block), heaviest m first; grid.y = field chunk.
+// ---------------------------------------------------------------------------
+template <typename T, int LPT, int BC, int NT>
+__global__ void __launch_bounds__(NT)
+k_synth(PlanView<T> pv, const T *__restrict__ spec, T *__restrict__ eo, int batch, int npb, int op)
+{
+    using T2 = typename Vec2<T>::type;
+    constexpr int NCH = 128;
+    __shared__ T2 s_ab[NCH];
+    __shared__ T2 s_f[NCH * BC];
+
+    const int m = blockIdx.x / npb;
+    const int pb = blockIdx.x - m * npb;
+    const int b0 = blockIdx.y * BC;
+    const int lmax = pv.lmax, npairs = pv.npairs;
+    const int L = lmax - m + 1;
+    const long col = col_of(lmax, m);
+
+    T x[LPT], y1[LPT], y2[LPT], c[LPT];
+    int k[LPT], p[LPT];
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) {
+        p[i] = pb * NT * LPT + i * NT + threadIdx.x;
+        const bool v = p[i] < npairs;
+        const size_t o = (size_t)m * npairs + p[i];
+        x[i] = v ? pv.x[p[i]] : T(0);
+        y2[i] = v ? pv.pmm[o] : T(0);
+        k[i] = v ? pv.pmmk[o] : 0;
+        y1[i] = T(0);
+    }
+    T er[LPT][BC], ei[LPT][BC], orr[LPT][BC], oi[LPT][BC];
+#pragma unroll
+    for (int i = 0; i < LPT; ++i)
+#pragma unroll
+        for (int b = 0; b < BC; ++b) er[i][b] = ei[i][b] = orr[i][b] = oi[i][b] = T(0);
+
+    // adjoint of analysis: synthesis of b / c_m
+    const T insc = (op == OP_ANALYS_ADJ && m > 0) ? T(0.5) : T(1);
+    const T2 *spec2 = reinterpret_cast<const T2 *>(spec);
+
+    for (int n0 = 0; n0 < L; n0 += NCH) {
+        const int cnt = min(NCH, L - n0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < NCH; t += NT) {
+            T2 ab;
+            ab.x = T(0); ab.y = T(0);
+            if (t < cnt) ab = pv.ab[col + n0 + t];
+            s_ab[t] = ab;
+#pragma unroll
+            for (int b = 0; b < BC; ++b) {
+                T2 f;
+                f.x = T(0); f.y = T(0);
+                if (t < cnt && b0 + b < batch) {
+                    f = spec2[(size_t)(b0 + b) * pv.nlm + col + n0 + t];
+                    f.x *= insc;
+                    f.y = (m == 0) ? T(0) : f.y * insc;
+                }
+                s_f[t * BC + b] = f;
+            }
+        }
+        __syncthreads();
+        const bool scaled = __any_sync(kFull, kmax_of<T, LPT>(k) > 0);
+        if (!scaled) {
+            for (int t = 0; t < cnt; t += 2) {
+                T2 ab = s_ab[t];
+                rec_step<T, LPT, false>(ab.x, ab.y, x, y1, y2, k, c);
+#pragma unroll
+                for (int b = 0; b < BC; ++b) {
+                    const T2 f = s_f[t * BC + b];
+#pragma unroll
+                    for (int i = 0; i < LPT; ++i) {
+                        er[i][b] = fma(f.x, c[i], er[i][b]);
+                        ei[i][b] = fma(f.y, c[i], ei[i][b]);
+                    }
+                }
+                ab = s_ab[t + 1];
+                rec_step<T, LPT, false>(ab.x, ab.y, x, y1, y2, k, c);
+#pragma unroll
+                for (int b = 0; b < BC; ++b) {
+                    const T2 f = s_f[(t + 1) * BC + b];
+#pragma unroll
+                    for (int i = 0; i < LPT; ++i) {
+                        orr[i][b] = fma(f.x, c[i], orr[i][b]);
+                        oi[i][b] = fma(f.y, c[i], oi[i][b]);
+                    }
+                }
+            }
+        } else {
+            for (int t = 0; t < cnt; t += 2) {
+                T2 ab = s_ab[t];
+                rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c);
+                if (__any_sync(kFull, kmin_of<T, LPT>(k) == 0)) {
+#pragma unroll
+                    for (int b = 0; b < BC; ++b) {
+                        const T2 f = s_f[t * BC + b];
+#pragma unroll
+                        for (int i = 0; i < LPT; ++i) {
+                            er[i][b] = fma(f.x, c[i], er[i][b]);
+                            ei[i][b] = fma(f.y, c[i], ei[i][b]);
+                        }
+                    }
+                }
+                ab = s_ab[t + 1];
+                rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c);
+                if (__any_sync(kFull, kmin_of<T, LPT>(k) == 0)) {
+#pragma unroll
+                    for (int b = 0; b < BC; ++b) {
+                        const T2 f = s_f[(t + 1) * BC + b];
+#pragma unroll
+                        for (int i = 0; i < LPT; ++i) {
+                            orr[i][b] = fma(f.x, c[i], orr[i][b]);
+                            oi[i][b] = fma(f.y, c[i], oi[i][b]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+
+    T2 *eo2 = reinterpret_cast<T2 *>(eo);
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) {
+        if (p[i] >= npairs) continue;
+#pragma unroll
+        for (int b = 0; b < BC; ++b) {
+            if (b0 + b >= batch) continue;
+            const size_t o = (((size_t)(b0 + b) * (pv.mmax + 1) + m) * npairs + p[i]) * 2;
+            T2 e, d;
+            e.x = er[i][b]; e.y = ei[i][b];
+            d.x = orr[i][b]; d.y = oi[i][b];
+            eo2[o] = e;
+            eo2[o + 1] = d;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Scalar analysis.  grid.x = m (heaviest first), grid.y = field chunk; the CTA
+// covers all latitude pairs (NT * LPT >= npairs).
+// ---------------------------------------------------------------------------
+template <typename T, int LPT, int BC>
+__global__ void __launch_bounds__(256)
+k_analys(PlanView<T> pv, const T *__restrict__ sd, T *__restrict__ spec, int batch, int op)
+{
+    using T2 = typename Vec2<T>::type;
+    constexpr int K = 16 / BC;   // degrees per reduction: 2*K*BC = 32 values
+    constexpr int NCH = 128;     // multiple of K
+    __shared__ T2 s_ab[NCH];
+    __shared__ T s_red[8][32];
+
+    const int NT = blockDim.x;
+    const int nw = NT >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = blockIdx.x;
+    const int b0 = blockIdx.y * BC;
+    const int lmax = pv.lmax, npairs = pv.npairs;
+    const int L = lmax - m + 1;
+    const long col = col_of(lmax, m);
+
+    T x[LPT], y1[LPT], y2[LPT], c[LPT];
+    int k[LPT];
+    T2 sv[LPT][BC], dv[LPT][BC];
+    const T2 *sd2 = reinterpret_cast<const T2 *>(sd);
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) {
+        const int p = i * NT + threadIdx.x;
+        const bool v = p < npairs;
+        const size_t o = (size_t)m * npairs + p;
+        x[i] = v ? pv.x[p] : T(0);
+        y2[i] = v ? pv.pmm[o] : T(0);
+        k[i] = v ? pv.pmmk[o] : 0;
+        y1[i] = T(0);
+#pragma unroll
+        for (int b = 0; b < BC; ++b) {
+            T2 z;
+            z.x = T(0); z.y = T(0);
+            sv[i][b] = z;
+            dv[i][b] = z;
+            if (v && b0 + b < batch) {
+                const size_t q = (((size_t)(b0 + b) * (pv.mmax + 1) + m) * npairs + p) * 2;
+                sv[i][b] = sd2[q];
+                dv[i][b] = sd2[q + 1];
+            }
+        }
+    }
+    // output scale: c_m for the adjoint of synthesis
+    const T outsc = (op == OP_SYNTH_ADJ && m > 0) ? T(2) : T(1);
+    T2 *spec2 = reinterpret_cast<T2 *>(spec);
+
+    for (int n0 = 0; n0 < L; n0 += NCH) {
+        const int cnt = min(NCH, L - n0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < NCH; t += NT) {
+            T2 ab;
+            ab.x = T(0); ab.y = T(0);
+            if (t < cnt) ab = pv.ab[col + n0 + t];
+            s_ab[t] = ab;
+        }
+        __syncthreads();
+        for (int t0 = 0; t0 < cnt; t0 += K) {
+            T acc[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) acc[q] = T(0);
+            const bool scaled = __any_sync(kFull, kmax_of<T, LPT>(k) > 0);
+#pragma unroll
+            for (int kx = 0; kx < K; ++kx) {
+                const T2 ab = s_ab[t0 + kx];
+                bool live = true;
+                if (scaled) {
+                    rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c);
+                    live = __any_sync(kFull, kmin_of<T, LPT>(k) == 0);
+                } else {
+                    rec_step<T, LPT, false>(ab.x, ab.y, x, y1, y2, k, c);
+                }
+                if (live) {
+#pragma unroll
+                    for (int b = 0; b < BC; ++b) {
+#pragma unroll
+                        for (int i = 0; i < LPT; ++i) {
+                            const T2 v = (kx & 1) ? dv[i][b] : sv[i][b];
+                            acc[(kx * BC + b) * 2] = fma(c[i], v.x, acc[(kx * BC + b) * 2]);
+                            acc[(kx * BC + b) * 2 + 1] = fma(c[i], v.y, acc[(kx * BC + b) * 2 + 1]);
+                        }
+                    }
+                }
+            }
+            warp_transpose_reduce<T, 32>(acc, lane);
+            s_red[warp][lane] = acc[0];
+            __syncthreads();
+            if (threadIdx.x < 2 * K * BC) {
+                T tot = T(0);
+                for (int w = 0; w < nw; ++w) tot += s_red[w][threadIdx.x];
+                const int q = threadIdx.x;
+                const int kx = q / (2 * BC), b = (q >> 1) % BC, part = q & 1;
+                const int nn = n0 + t0 + kx;  // n - m
+                if (nn < L && b0 + b < batch) {
+                    T val = tot * outsc;
+                    if (m == 0 && part == 1) val = T(0);
+                    T *dst = reinterpret_cast<T *>(&spec2[(size_t)(b0 + b) * pv.nlm + col + nn]);
+                    dst[part] = val;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Vector synthesis.  With dP = sin(theta) dP/dtheta = n x P_n - dc_n P_{n-1}:
+//   sin * V_theta,m = sum [S dP - i m T P],   sin * V_phi,m = sum [i m S P + T dP].
+// dP has the opposite mirror parity of P.  Outputs E/O for theta and phi.
+// ---------------------------------------------------------------------------
+template <typename T, int LPT, int BC, int NT>
+__global__ void __launch_bounds__(NT)
+k_synth_vec(PlanView<T> pv, const T *__restrict__ Sg, const T *__restrict__ Tg, T *__restrict__ eot,
+            T *__restrict__ eop, int batch, int npb, int op)
+{
+    using T2 = typename Vec2<T>::type;
+    constexpr int NCH = 64;
+    __shared__ T2 s_ab[NCH];
+    __shared__ T s_dc[NCH];
+    __shared__ T2 s_S[NCH * BC];
+    __shared__ T2 s_T[NCH * BC];
+
+    const int m = blockIdx.x / npb;
+    const int pb = blockIdx.x - m * npb;
+    const int b0 = blockIdx.y * BC;
+    const int lmax = pv.lmax, npairs = pv.npairs;
+    const int L = lmax - m + 1;
+    const long col = col_of(lmax, m);
+
+    T x[LPT], y1[LPT], y2[LPT], c[LPT];
+    int k[LPT], p[LPT];
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) {
+        p[i] = pb * NT * LPT + i * NT + threadIdx.x;
+        const bool v = p[i] < npairs;
+        const size_t o = (size_t)m * npairs + p[i];
+        x[i] = v ? pv.x[p[i]] : T(0);
+        y2[i] = v ? pv.pmm[o] : T(0);
+        k[i] = v ? pv.pmmk[o] : 0;
+        y1[i] = T(0);
+    }
+    // accumulators [pair][field][8 complex]: A_e A_o B_e B_o C_e C_o D_e D_o
+    //   A: S dP, B: T P, C: S P, D: T dP; e/o = even/odd function of x
+    T acc[LPT][BC][16];
+#pragma unroll
+    for (int i = 0; i < LPT; ++i)
+#pragma unroll
+        for (int b = 0; b < BC; ++b)
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[i][b][q] = T(0);
+
+    const T2 *S2 = reinterpret_cast<const T2 *>(Sg);
+    const T2 *T2p = reinterpret_cast<const T2 *>(Tg);
+    const T cadj = (op == OP_ANALYS_ADJ && m > 0) ? T(0.5) : T(1);
+
+    for (int n0 = 0; n0 < L; n0 += NCH) {
+        const int cnt = min(NCH, L - n0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < NCH; t += NT) {
+            T2 ab;
+            ab.x = T(0); ab.y = T(0);
+            T dcv = T(0);
+            if (t < cnt) { ab = pv.ab[col + n0 + t]; dcv = pv.dc[col + n0 + t]; }
+            s_ab[t] = ab;
+            s_dc[t] = dcv;
+            const int n = m + n0 + t;
+            // adjoint of analysis: b / (c_m n(n+1)), nothing at n = 0
+            T sc = T(1);
+            if (op == OP_ANALYS_ADJ) sc = (n == 0) ? T(0) : cadj / (T(n) * T(n + 1));
+#pragma unroll
+            for (int b = 0; b < BC; ++b) {
+                T2 fs, ft;
+                fs.x = fs.y = ft.x = ft.y = T(0);
+                if (t < cnt && b0 + b < batch) {
+                    fs = S2[(size_t)(b0 + b) * pv.nlm + col + n0 + t];
+                    ft = T2p[(size_t)(b0 + b) * pv.nlm + col + n0 + t];
+                    fs.x *= sc; fs.y = (m == 0) ? T(0) : fs.y * sc;
+                    ft.x *= sc; ft.y = (m == 0) ? T(0) : ft.y * sc;
+                }
+                s_S[t * BC + b] = fs;
+                s_T[t * BC + b] = ft;
+            }
+        }
+        __syncthreads();
+        const bool scaled = __any_sync(kFull, kmax_of<T, LPT>(k) > 0);
+        for (int t = 0; t < cnt; t += 2) {
+#pragma unroll
+            for (int par = 0; par < 2; ++par) {
+                const int tt = t + par;
+                const T2 ab = s_ab[tt];
+                const T dcn = s_dc[tt];
+                const T nf = T(m + n0 + tt);
+                bool live = true;
+                if (scaled) {
+                    rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c);
+                    live = __any_sync(kFull, kmin_of<T, LPT>(k) == 0);
+                } else {
+                    rec_step<T, LPT, false>(ab.x, ab.y, x, y1, y2, k, c);
+                }
+                if (!live) continue;
+                T cd[LPT];
+#pragma unroll
+                for (int i = 0; i < LPT; ++i) {
+                    // dP = n x P_n - dc_n P_{n-1}; zero whenever P itself is dropped
+                    const T dpv = fma(nf * x[i], y1[i], -dcn * y2[i]);
+                    cd[i] = (scaled && k[i] > 0) ? T(0) : dpv;
+                }
+#pragma unroll
+                for (int b = 0; b < BC; ++b) {
+                    const T2 fs = s_S[tt * BC + b];
+                    const T2 ft = s_T[tt * BC + b];
+#pragma unroll
+                    for (int i = 0; i < LPT; ++i) {
+                        // n-m even (par 0): P even, dP odd.  n-m odd: P odd, dP even.
+                        const int iA = par == 0 ? 2 : 0;   // A_o : A_e
+                        const int iB = par == 0 ? 4 : 6;   // B_e : B_o
+                        const int iC = par == 0 ? 8 : 10;  // C_e : C_o
+                        const int iD = par == 0 ? 14 : 12; // D_o : D_e
+                        acc[i][b][iA] = fma(fs.x, cd[i], acc[i][b][iA]);
+                        acc[i][b][iA + 1] = fma(fs.y, cd[i], acc[i][b][iA + 1]);
+                        acc[i][b][iB] = fma(ft.x, c[i], acc[i][b][iB]);
+                        acc[i][b][iB + 1] = fma(ft.y, c[i], acc[i][b][iB + 1]);
+                        acc[i][b][iC] = fma(fs.x, c[i], acc[i][b][iC]);
+                        acc[i][b][iC + 1] = fma(fs.y, c[i], acc[i][b][iC + 1]);
+                        acc[i][b][iD] = fma(ft.x, cd[i], acc[i][b][iD]);
+                        acc[i][b][iD + 1] = fma(ft.y, cd[i], acc[i][b][iD + 1]);
+                    }
+                }
+            }
+        }
+    }
+
+    T2 *eot2 = reinterpret_cast<T2 *>(eot);
+    T2 *eop2 = reinterpret_cast<T2 *>(eop);
+    const T fm = T(m);
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) {
+        if (p[i] >= npairs) continue;
+        const T is = T(1) / pv.st[p[i]];
+#pragma unroll
+        for (int b = 0; b < BC; ++b) {
+            if (b0 + b >= batch) continue;
+            const T *a = acc[i][b];
+            const size_t o = (((size_t)(b0 + b) * (pv.mmax + 1) + m) * npairs + p[i]) * 2;
+            T2 v;
+            // theta: (A - i m B) / sin ; E uses A_e,B_e ; O uses A_o,B_o
+            v.x = (a[0] + fm * a[5]) * is; v.y = (a[1] - fm * a[4]) * is; eot2[o] = v;
+            v.x = (a[2] + fm * a[7]) * is; v.y = (a[3] - fm * a[6]) * is; eot2[o + 1] = v;
+            // phi: (i m C + D) / sin ; E uses C_e,D_e ; O uses C_o,D_o
+            v.x = (a[12] - fm * a[9]) * is; v.y = (a[13] + fm * a[8]) * is; eop2[o] = v;
+            v.x = (a[14] - fm * a[11]) * is; v.y = (a[15] + fm * a[10]) * is; eop2[o + 1] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Vector analysis.  With folds s/d of (w/sin) V_theta and V_phi:
+//   S_n = sum [dP * fold(V_theta) - i m P * fold(V_phi)] / (n(n+1))
+//   T_n = sum [i m P * fold(V_theta) + dP * fold(V_phi)] / (n(n+1))
+// where the fold is s for an even function and d for an odd one.
+// ---------------------------------------------------------------------------
+template <typename T, int LPT, int BC>
+__global__ void __launch_bounds__(256)
+k_analys_vec(PlanView<T> pv, const T *__restrict__ sdt, const T *__restrict__ sdp, T *__restrict__ So,
+             T *__restrict__ To, int batch, int op)
+{
+    using T2 = typename Vec2<T>::type;
+    constexpr int K = 4 / BC;    // degrees per reduction: 8*K*BC = 32 values
+    constexpr int NCH = 64;      // multiple of K
+    static_assert(K % 2 == 0, "K must be even so that kx carries the parity of n - m");
+    __shared__ T2 s_ab[NCH];
+    __shared__ T s_dc[NCH];
+    __shared__ T s_red[8][32];
+
+    const int NT = blockDim.x;
+    const int nw = NT >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = blockIdx.x;
+    const int b0 = blockIdx.y * BC;
+    const int lmax = pv.lmax, npairs = pv.npairs;
+    const int L = lmax - m + 1;
+    const long col = col_of(lmax, m);
+
+    T x[LPT], y1[LPT], y2[LPT], c[LPT];
+    int k[LPT];
+    T2 st_[LPT][BC], dt_[LPT][BC], sp_[LPT][BC], dp_[LPT][BC];
+    const T2 *sdt2 = reinterpret_cast<const T2 *>(sdt);
+    const T2 *sdp2 = reinterpret_cast<const T2 *>(sdp);
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) {
+        const int p = i * NT + threadIdx.x;
+        const bool v = p < npairs;
+        const size_t o = (size_t)m * npairs + p;
+        x[i] = v ? pv.x[p] : T(0);
+        y2[i] = v ? pv.pmm[o] : T(0);
+        k[i] = v ? pv.pmmk[o] : 0;
+        y1[i] = T(0);
+#pragma unroll
+        for (int b = 0; b < BC; ++b) {
+            T2 z;
+            z.x = T(0); z.y = T(0);
+            st_[i][b] = dt_[i][b] = sp_[i][b] = dp_[i][b] = z;
+            if (v && b0 + b < batch) {
+                const size_t q = (((size_t)(b0 + b) * (pv.mmax + 1) + m) * npairs + p) * 2;
+                st_[i][b] = sdt2[q];
+                dt_[i][b] = sdt2[q + 1];
+                sp_[i][b] = sdp2[q];
+                dp_[i][b] = sdp2[q + 1];
+            }
+        }
+    }
+    const T fm = T(m);
+    T2 *S2 = reinterpret_cast<T2 *>(So);
+    T2 *T2o = reinterpret_cast<T2 *>(To);
+
+    for (int n0 = 0; n0 < L; n0 += NCH) {
+        const int cnt = min(NCH, L - n0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < NCH; t += NT) {
+            T2 ab;
+            ab.x = T(0); ab.y = T(0);
+            T dcv = T(0);
+            if (t < cnt) { ab = pv.ab[col + n0 + t]; dcv = pv.dc[col + n0 + t]; }
+            s_ab[t] = ab;
+            s_dc[t] = dcv;
+        }
+        __syncthreads();
+        for (int t0 = 0; t0 < cnt; t0 += K) {
+            // per (kx, b): SA(2) SB(2) TA(2) TB(2)
+            T acc[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) acc[q] = T(0);
+            const bool scaled = __any_sync(kFull, kmax_of<T, LPT>(k) > 0);
+#pragma unroll
+            for (int kx = 0; kx < K; ++kx) {
+                const T2 ab = s_ab[t0 + kx];
+                const T dcn = s_dc[t0 + kx];
+                const T nf = T(m + n0 + t0 + kx);
+                bool live = true;
+                if (scaled) {
+                    rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c);
+                    live = __any_sync(kFull, kmin_of<T, LPT>(k) == 0);
+                } else {
+                    rec_step<T, LPT, false>(ab.x, ab.y, x, y1, y2, k, c);
+                }
+                if (!live) continue;
+#pragma unroll
+                for (int i = 0; i < LPT; ++i) {
+                    const T dpv = fma(nf * x[i], y1[i], -dcn * y2[i]);
+                    const T cd = (scaled && k[i] > 0) ? T(0) : dpv;
+#pragma unroll
+                    for (int b = 0; b < BC; ++b) {
+                        // n-m even (kx even): P even -> s folds; dP odd -> d folds
+                        const T2 vt_dP = (kx & 1) ? st_[i][b] : dt_[i][b];
+                        const T2 vp_P = (kx & 1) ? dp_[i][b] : sp_[i][b];
+                        const T2 vt_P = (kx & 1) ? dt_[i][b] : st_[i][b];
+                        const T2 vp_dP = (kx & 1) ? sp_[i][b] : dp_[i][b];
+                        T *a = &acc[(kx * BC + b) * 8];
+                        a[0] = fma(cd, vt_dP.x, a[0]);
+                        a[1] = fma(cd, vt_dP.y, a[1]);
+                        a[2] = fma(c[i], vp_P.x, a[2]);
+                        a[3] = fma(c[i], vp_P.y, a[3]);
+                        a[4] = fma(c[i], vt_P.x, a[4]);
+                        a[5] = fma(c[i], vt_P.y, a[5]);
+                        a[6] = fma(cd, vp_dP.x, a[6]);
+                        a[7] = fma(cd, vp_dP.y, a[7]);
+                    }
+                }
+            }
+            warp_transpose_reduce<T, 32>(acc, lane);
+            s_red[warp][lane] = acc[0];
+            __syncthreads();
+            if (threadIdx.x < K * BC) {
+                T tot[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) tot[q] = T(0);
+                for (int w = 0; w < nw; ++w)
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) tot[q] += s_red[w][threadIdx.x * 8 + q];
+                const int kx = threadIdx.x / BC, b = threadIdx.x % BC;
+                const int nn = n0 + t0 + kx;
+                const int n = m + nn;
+                if (nn < L && b0 + b < batch) {
+                    T sc;
+                    if (op == OP_SYNTH_ADJ) sc = (m > 0) ? T(2) : T(1);
+                    else sc = (n == 0) ? T(0) : T(1) / (T(n) * T(n + 1));
+                    T2 sv, tv;
+                    // S = SA - i m SB ; T = i m TA + TB
+                    sv.x = sc * (tot[0] + fm * tot[3]);
+                    sv.y = sc * (tot[1] - fm * tot[2]);
+                    tv.x = sc * (tot[6] - fm * tot[5]);
+                    tv.y = sc * (tot[7] + fm * tot[4]);
+                    if (m == 0) { sv.y = T(0); tv.y = T(0); }
+                    S2[(size_t)(b0 + b) * pv.nlm + col + nn] = sv;
+                    T2o[(size_t)(b0 + b) * pv.nlm + col + nn] = tv;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Field chunk per CTA for a batch.
+inline int pick_bc(int batch) { return batch >= 4 ? 4 : (batch >= 2 ? 2 : 1); }
+
+template <typename T, int LPT, int BC>
+cudaError_t synth_go(const PlanView<T> &pv, const T *spec, T *eo, int batch, Op op, cudaStream_t s)
+{
+    constexpr int NT = 128;
+    const int npb = (pv.npairs + NT * LPT - 1) / (NT * LPT);
+    dim3 grid((unsigned)((pv.mmax + 1) * npb), (unsigned)((batch + BC - 1) / BC));
+    k_synth<T, LPT, BC, NT><<<grid, NT, 0, s>>>(pv, spec, eo, batch, npb, (int)op);
+    return cudaGetLastError();
+}
+
+// Analysis CTAs hold every latitude pair of one order: nw warps of LPT pairs per thread.
+inline int analys_warps(int npairs, int lpt) { int nw = (npairs + 32 * lpt - 1) / (32 * lpt); return nw < 1 ? 1 : nw; }
+
+template <typename T, int LPT, int BC>
+cudaError_t analys_go(const PlanView<T> &pv, const T *sd, T *spec, int batch, Op op, cudaStream_t s)
+{
+    const int nw = analys_warps(pv.npairs, LPT);
+    if (nw > 8) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)(pv.mmax + 1), (unsigned)((batch + BC - 1) / BC));
+    k_analys<T, LPT, BC><<<grid, nw * 32, 0, s>>>(pv, sd, spec, batch, (int)op);
+    return cudaGetLastError();
+}
+
+template <typename T, int LPT, int BC>
+cudaError_t synth_vec_go(const PlanView<T> &pv, const T *S, const T *Tc, T *eot, T *eop, int batch, Op op,
+                         cudaStream_t s)
+{
+    constexpr int NT = 128;
+    const int npb = (pv.npairs + NT * LPT - 1) / (NT * LPT);
+    dim3 grid((unsigned)((pv.mmax + 1) * npb), (unsigned)((batch + BC - 1) / BC));
+    k_synth_vec<T, LPT, BC, NT><<<grid, NT, 0, s>>>(pv, S, Tc, eot, eop, batch, npb, (int)op);
+    return cudaGetLastError();
+}
+
+template <typename T, int LPT, int BC>
+cudaError_t analys_vec_go(const PlanView<T> &pv, const T *sdt, const T *sdp, T *S, T *Tc, int batch, Op op,
+                          cudaStream_t s)
+{
+    const int nw = analys_warps(pv.npairs, LPT);
+    if (nw > 8) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)(pv.mmax + 1), (unsigned)((batch + BC - 1) / BC));
+    k_analys_vec<T, LPT, BC><<<grid, nw * 32, 0, s>>>(pv, sdt, sdp, S, Tc, batch, (int)op);
+    return cudaGetLastError();
+}
+
+// Pairs per thread for analysis, so that <= 8 warps cover all pairs.
+inline int analys_lpt(int npairs) { return npairs <= 512 ? 2 : (npairs <= 1024 ? 4 : 8); }
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_legendre_synth(const PlanView<T> &pv, const T *spec, T *eo, int batch, Op op, cudaStream_t s)
+{
+    switch (pick_bc(batch)) {
+    case 4: return synth_go<T, 2, 4>(pv, spec, eo, batch, op, s);
+    case 2: return synth_go<T, 2, 2>(pv, spec, eo, batch, op, s);
+    default: return synth_go<T, 2, 1>(pv, spec, eo, batch, op, s);
+    }
+}
+
+template <typename T>
+cudaError_t launch_legendre_analys(const PlanView<T> &pv, const T *sd, T *spec, int batch, Op op, cudaStream_t s)
+{
+    const bool two = batch >= 2;
+    switch (analys_lpt(pv.npairs)) {
+    case 2: return two ? analys_go<T, 2, 2>(pv, sd, spec, batch, op, s) : analys_go<T, 2, 1>(pv, sd, spec, batch, op, s);
+    case 4: return two ? analys_go<T, 4, 2>(pv, sd, spec, batch, op, s) : analys_go<T, 4, 1>(pv, sd, spec, batch, op, s);
+    default: return two ? analys_go<T, 8, 2>(pv, sd, spec, batch, op, s) : analys_go<T, 8, 1>(pv, sd, spec, batch, op, s);
+    }
+}
+
+template <typename T>
+cudaError_t launch_legendre_synth_vec(const PlanView<T> &pv, const T *S, const T *Tc, T *eot, T *eop, int batch,
+                                      Op op, cudaStream_t s)
+{
+    if (batch >= 2) return synth_vec_go<T, 1, 2>(pv, S, Tc, eot, eop, batch, op, s);
+    return synth_vec_go<T, 1, 1>(pv, S, Tc, eot, eop, batch, op, s);
+}
+
+template <typename T>
+cudaError_t launch_legendre_analys_vec(const PlanView<T> &pv, const T *sdt, const T *sdp, T *S, T *Tc, int batch,
+                                       Op op, cudaStream_t s)
+{
+    switch (analys_lpt(pv.npairs)) {
+    case 2: return analys_vec_go<T, 2, 1>(pv, sdt, sdp, S, Tc, batch, op, s);
+    case 4: return analys_vec_go<T, 4, 1>(pv, sdt, sdp, S, Tc, batch, op, s);
+    default: return analys_vec_go<T, 8, 1>(pv, sdt, sdp, S, Tc, batch, op, s);
+    }
+}
+
+template cudaError_t launch_legendre_synth<double>(const PlanView<double> &, const double *, double *, int, Op,
+                                                   cudaStream_t);
+template cudaError_t launch_legendre_synth<float>(const PlanView<float> &, const float *, float *, int, Op,
+                                                  cudaStream_t);
+template cudaError_t launch_legendre_analys<double>(const PlanView<double> &, const double *, double *, int, Op,
+                                                    cudaStream_t);
+template cudaError_t launch_legendre_analys<float>(const PlanView<float> &, const float *, float *, int, Op,
+                                                   cudaStream_t);
+template cudaError_t launch_legendre_synth_vec<double>(const PlanView<double> &, const double *, const double *,
+                                                       double *, double *, int, Op, cudaStream_t);
+template cudaError_t launch_legendre_synth_vec<float>(const PlanView<float> &, const float *, const float *, float *,
+                                                      float *, int, Op, cudaStream_t);
+template cudaError_t launch_legendre_analys_vec<double>(const PlanView<double> &, const double *, const double *,
+                                                        double *, double *, int, Op, cudaStream_t);
+template cudaError_t launch_legendre_analys_vec<float>(const PlanView<float> &, const float *, const float *, float *,
+                                                       float *, int, Op, cudaStream_t);
+
+}  // namespace sht

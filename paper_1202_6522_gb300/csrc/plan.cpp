@@ -1,0 +1,255 @@
+// plan.cpp -- host construction of an SHT plan: Gauss nodes and weights
+// (Sec. 2.3), recurrence coefficients a_n^m, b_n^m (Sec. 3.2), the starting
+// values P_m^m(x_j) with their rescaling counters (Sec. 3.5), derivative
+// coefficients for the vector transforms and the FFT twiddles.  Everything is
+// computed in FP64 on the host once and copied to the device; FP32 copies are
+// rounded from the FP64 values.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sht_internal.h"
+
+namespace sht {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// P_n(x) and P_{n-1}(x) by the three-term recurrence of Sec. 2.1.
+void legendre_pair(int n, double x, double &pn, double &pn1)
+{
+    double a = 1.0, b = x;  // P_0, P_1
+    if (n == 0) { pn = 1.0; pn1 = 0.0; return; }
+    for (int k = 2; k <= n; ++k) {
+        double c = ((2 * k - 1) * x * b - (k - 1) * a) / k;
+        a = b;
+        b = c;
+    }
+    pn = b;
+    pn1 = a;
+}
+
+// Nodes of the nlat-point Gauss-Legendre rule, largest first, and weights
+// w = 2 (1 - x^2) / (n P_{n-1}(x))^2.  Newton on P_n started from Tricomi's
+// asymptotic estimate.
+void gauss_nodes(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double th = kPi * (4.0 * i + 3.0) / (4.0 * n + 2.0);
+        double z = (1.0 - (n - 1.0) / (8.0 * n * n * n)) * std::cos(th);
+        double pn = 0.0, pn1 = 0.0;
+        for (int it = 0; it < 60; ++it) {
+            legendre_pair(n, z, pn, pn1);
+            double dp = n * (pn1 - z * pn) / ((1.0 - z) * (1.0 + z));
+            double dz = pn / dp;
+            z -= dz;
+            if (std::fabs(dz) <= 2e-16 * std::fabs(z) + 1e-300 && it > 2) break;
+        }
+        legendre_pair(n, z, pn, pn1);
+        double omx2 = (1.0 - z) * (1.0 + z);
+        double wt = 2.0 * omx2 / ((n * pn1) * (n * pn1));
+        if (n % 2 == 1 && i == n / 2) z = 0.0;  // the equatorial node
+        x[i] = z;
+        x[n - 1 - i] = -z;
+        w[i] = wt;
+        w[n - 1 - i] = wt;
+    }
+}
+
+// Round the double table into a float copy.
+std::vector<float> to_f32(const std::vector<double> &v)
+{
+    std::vector<float> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
+    return o;
+}
+
+// Bump allocator over a single device allocation.
+struct DevArena {
+    char *base = nullptr;
+    size_t off = 0, cap = 0;
+    template <typename U>
+    U *take(size_t count)
+    {
+        size_t bytes = (count * sizeof(U) + 255) & ~size_t(255);
+        U *p = reinterpret_cast<U *>(base + off);
+        off += bytes;
+        return p;
+    }
+};
+
+template <typename U>
+size_t padded(size_t count) { return (count * sizeof(U) + 255) & ~size_t(255); }
+
+}  // namespace
+
+PlanView<double> Plan::view64() const
+{
+    PlanView<double> v{lmax, mmax, nlat, nphi, npairs, nlm,
+                       t64.ab, t64.dc, t64.x, t64.st, t64.wq, t64.pmm, t64.pmmk, t64.tw};
+    return v;
+}
+
+PlanView<float> Plan::view32() const
+{
+    PlanView<float> v{lmax, mmax, nlat, nphi, npairs, nlm,
+                      t32.ab, t32.dc, t32.x, t32.st, t32.wq, t32.pmm, t32.pmmk, t32.tw};
+    return v;
+}
+
+int plan_build(Plan &p, std::string &err)
+{
+    const int lmax = p.lmax, mmax = p.mmax, nlat = p.nlat, nphi = p.nphi;
+    p.npairs = (nlat + 1) / 2;
+    p.nlm = (mmax + 1) * (lmax + 1) - mmax * (mmax + 1) / 2;
+    const int npairs = p.npairs, nlm = p.nlm;
+    gauss_nodes(nlat, p.x, p.w);
+
+    // Recurrence coefficients of Sec. 3.2, packed like the spectral arrays.
+    std::vector<double> ab((size_t)2 * nlm), dc(nlm);
+    for (int m = 0; m <= mmax; ++m) {
+        const size_t col = (size_t)m * (2 * lmax + 3 - m) / 2;
+        for (int n = m; n <= lmax; ++n) {
+            const size_t i = col + (n - m);
+            const double dn = n, dm = m;
+            double a, b;
+            if (n == m) {            // P_m^m is loaded as the starting value
+                a = 0.0; b = 1.0;
+            } else if (n == m + 1) { // P_{m+1}^m = sqrt(2m+3) x P_m^m
+                a = std::sqrt(2.0 * m + 3.0); b = 0.0;
+            } else {
+                a = std::sqrt((4.0 * dn * dn - 1.0) / (dn * dn - dm * dm));
+                b = -std::sqrt((2.0 * dn + 1.0) / (2.0 * dn - 3.0) *
+                               ((dn - 1.0) * (dn - 1.0) - dm * dm) / (dn * dn - dm * dm));
+            }
+            ab[2 * i] = a;
+            ab[2 * i + 1] = b;
+            dc[i] = (n == m) ? 0.0 : std::sqrt((2.0 * dn + 1.0) * (dn * dn - dm * dm) / (2.0 * dn - 1.0));
+        }
+    }
+
+    // Per latitude pair: northern node, sin(theta), weight.
+    std::vector<double> xp(npairs), sp(npairs), wp(npairs);
+    for (int j = 0; j < npairs; ++j) {
+        xp[j] = p.x[j];
+        sp[j] = std::sqrt((1.0 - p.x[j]) * (1.0 + p.x[j]));
+        wp[j] = p.w[j];
+    }
+
+    // Starting values P_m^m(x_j) = sqrt(1/4pi) prod_{k<=m} sqrt((2k+1)/(2k)) sin^m,
+    // carried as mantissa * 2^e, then written as y * 2^(-S k) with y in [2^-S, 1)
+    // when the value is below 2^-S (k > 0), else y = value, k = 0.
+    std::vector<double> pmm64((size_t)(mmax + 1) * npairs), pmm32d((size_t)(mmax + 1) * npairs);
+    std::vector<int> k64((size_t)(mmax + 1) * npairs), k32((size_t)(mmax + 1) * npairs);
+    auto split = [](double mant, long e, int S, double &y, int &k) {
+        if (mant == 0.0) { y = 0.0; k = 0; return; }
+        if (e >= 1 - S) { y = std::ldexp(mant, (int)e); k = 0; return; }
+        long kk = (-e) / S;  // equals ceil((1 - S - e) / S) when e < 1 - S
+        y = std::ldexp(mant, (int)(e + S * kk));
+        k = (int)kk;
+    };
+    for (int j = 0; j < npairs; ++j) {
+        int ex = 0;
+        double mant = std::frexp(std::sqrt(1.0 / (4.0 * kPi)), &ex);
+        long e = ex;
+        for (int m = 0; m <= mmax; ++m) {
+            if (m > 0) {
+                mant *= std::sqrt((2.0 * m + 1.0) / (2.0 * m)) * sp[j];
+                int ee = 0;
+                mant = std::frexp(mant, &ee);
+                e += ee;
+            }
+            const size_t o = (size_t)m * npairs + j;
+            split(mant, e, Scale<double>::S, pmm64[o], k64[o]);
+            split(mant, e, Scale<float>::S, pmm32d[o], k32[o]);
+        }
+    }
+
+    // FFT twiddles e^{2 pi i k / nphi}, k < nphi/2.
+    const int H = nphi / 2;
+    std::vector<double> tw((size_t)2 * (H > 0 ? H : 1));
+    for (int k = 0; k < H; ++k) {
+        const double ang = 2.0 * kPi * k / nphi;
+        tw[2 * k] = std::cos(ang);
+        tw[2 * k + 1] = std::sin(ang);
+    }
+
+    // One device allocation holding both precisions' tables.
+    const size_t H1 = H > 0 ? H : 1;
+    size_t bytes = padded<double2>(nlm) + padded<double>(nlm) + 3 * padded<double>(npairs) +
+                   padded<double>((size_t)(mmax + 1) * npairs) + padded<int>((size_t)(mmax + 1) * npairs) +
+                   padded<double2>(H1);
+    bytes += padded<float2>(nlm) + padded<float>(nlm) + 3 * padded<float>(npairs) +
+             padded<float>((size_t)(mmax + 1) * npairs) + padded<int>((size_t)(mmax + 1) * npairs) +
+             padded<float2>(H1);
+    DevArena ar;
+    cudaError_t ce = cudaGetDevice(&p.device);
+    if (ce != cudaSuccess) { err = std::string("cudaGetDevice: ") + cudaGetErrorString(ce); return SHT_ECUDA; }
+    ce = cudaMalloc(&ar.base, bytes);
+    if (ce != cudaSuccess) { err = std::string("cudaMalloc(plan tables): ") + cudaGetErrorString(ce); return SHT_ENOMEM; }
+    ar.cap = bytes;
+    p.tables_base = ar.base;
+
+    auto up = [&](void *dst, const void *src, size_t n) -> bool {
+        return cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    bool ok = true;
+    p.t64.ab = ar.take<double2>(nlm);
+    ok &= up(p.t64.ab, ab.data(), sizeof(double) * 2 * nlm);
+    p.t64.dc = ar.take<double>(nlm);
+    ok &= up(p.t64.dc, dc.data(), sizeof(double) * nlm);
+    p.t64.x = ar.take<double>(npairs);
+    ok &= up(p.t64.x, xp.data(), sizeof(double) * npairs);
+    p.t64.st = ar.take<double>(npairs);
+    ok &= up(p.t64.st, sp.data(), sizeof(double) * npairs);
+    p.t64.wq = ar.take<double>(npairs);
+    ok &= up(p.t64.wq, wp.data(), sizeof(double) * npairs);
+    p.t64.pmm = ar.take<double>((size_t)(mmax + 1) * npairs);
+    ok &= up(p.t64.pmm, pmm64.data(), sizeof(double) * pmm64.size());
+    p.t64.pmmk = ar.take<int>((size_t)(mmax + 1) * npairs);
+    ok &= up(p.t64.pmmk, k64.data(), sizeof(int) * k64.size());
+    p.t64.tw = ar.take<double2>(H1);
+    ok &= up(p.t64.tw, tw.data(), sizeof(double) * 2 * H1);
+
+    std::vector<float> ab32 = to_f32(ab), dc32 = to_f32(dc), x32 = to_f32(xp), s32 = to_f32(sp),
+                       w32 = to_f32(wp), pmm32 = to_f32(pmm32d), tw32 = to_f32(tw);
+    p.t32.ab = ar.take<float2>(nlm);
+    ok &= up(p.t32.ab, ab32.data(), sizeof(float) * 2 * nlm);
+    p.t32.dc = ar.take<float>(nlm);
+    ok &= up(p.t32.dc, dc32.data(), sizeof(float) * nlm);
+    p.t32.x = ar.take<float>(npairs);
+    ok &= up(p.t32.x, x32.data(), sizeof(float) * npairs);
+    p.t32.st = ar.take<float>(npairs);
+    ok &= up(p.t32.st, s32.data(), sizeof(float) * npairs);
+    p.t32.wq = ar.take<float>(npairs);
+    ok &= up(p.t32.wq, w32.data(), sizeof(float) * npairs);
+    p.t32.pmm = ar.take<float>((size_t)(mmax + 1) * npairs);
+    ok &= up(p.t32.pmm, pmm32.data(), sizeof(float) * pmm32.size());
+    p.t32.pmmk = ar.take<int>((size_t)(mmax + 1) * npairs);
+    ok &= up(p.t32.pmmk, k32.data(), sizeof(int) * k32.size());
+    p.t32.tw = ar.take<float2>(H1);
+    ok &= up(p.t32.tw, tw32.data(), sizeof(float) * 2 * H1);
+    if (!ok) {
+        err = "cudaMemcpy of plan tables failed";
+        cudaFree(ar.base);
+        p.tables_base = nullptr;
+        return SHT_ECUDA;
+    }
+    return 0;
+}
+
+void plan_free(Plan &p)
+{
+    for (cudaEvent_t e : p.timer.pool) cudaEventDestroy(e);
+    p.timer.pool.clear();
+    if (p.tables_base) cudaFree(p.tables_base);
+    if (p.work) cudaFree(p.work);
+    p.tables_base = nullptr;
+    p.work = nullptr;
+    p.work_bytes = 0;
+}
+
+}  // namespace sht
