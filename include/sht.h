@@ -135,6 +135,30 @@ SHT_API int sht_gauss(sht_handle h, double *x, double *w);
  * this library (SHT_ECUDA), or SHT_OK. */
 SHT_API int sht_sync_status(sht_handle h, void *stream);
 
+/* Scalar synthesis that allocates nothing (no counterpart in the paper; an
+ * interface addition).  Same inputs, outputs and result as sht_synth, but its
+ * intermediate buffer is a fixed array compiled into this library instead of
+ * the handle's scratch, so the call never asks the CUDA runtime for memory.
+ * It is meant for callers that must not allocate device memory at call time:
+ * code that runs under a fixed device-memory budget owned by a host framework
+ * or a custom pool, and loops where the implicit device synchronisation of
+ * cudaMalloc/cudaFree is not acceptable.  The handle itself must have been
+ * created beforehand (sht_create allocates the plan tables).
+ *   - The fixed array holds SHT_STATIC_SCRATCH_BYTES (16 MiB) on every GPU that
+ *     loads this library, until the process exits.  A call needs
+ *     batch * (mmax+1) * ceil(nlat/2) * 4 * sizeof(element) bytes (N = 1023 in
+ *     FP64 fits one field, in FP32 two); larger calls return SHT_EINVAL and
+ *     enqueue nothing.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture begins.
+ *   - All calls, from any handle, share the one array: calls whose work can
+ *     overlap on the GPU (different streams without ordering) race on it.
+ *     Nothing in it needs to start at zero: each call overwrites the part it
+ *     reads before reading it. */
+#define SHT_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+SHT_API int sht_synth_static(sht_handle h, const void *spec, void *grid, int batch, int mode, void *stream);
+
 /* Per-kernel timing, for measurement (no counterpart in the paper).  While
  * enabled, every kernel the handle launches is bracketed by CUDA events on the
  * call's stream.  sht_profile_read synchronises those events and writes, for

@@ -46,6 +46,7 @@ SIGNATURES = {
     "sht_lm_index": ([_VP, _I, _I], _I),
     "sht_gauss": ([_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], _I),
     "sht_sync_status": ([_VP, _VP], _I),
+    "sht_synth_static": ([_VP, _VP, _VP, _I, _I, _VP], _I),
     "sht_profile": ([_VP, _I], _I),
     "sht_profile_read": ([_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I), _I], _I),
     "sht_kernel_name": ([_I], ctypes.c_char_p),
@@ -162,6 +163,14 @@ def sht_gauss(h, nlat: int):
 
 def sht_sync_status(h, stream):
     return check(_call("sht_sync_status", h, stream))
+
+
+def sht_synth_static(h, spec, grid, batch, mode, stream):
+    """sht_synth without any device allocation (intermediate in a fixed 16 MiB array)."""
+    return check(_call("sht_synth_static", h, spec, grid, batch, mode, stream))
+
+
+SHT_STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 
 def sht_profile(h, enable):

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -389,3 +390,69 @@ int sht_sync_status(sht_handle h, void *stream)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// sht_synth_static: the scalar synthesis with its intermediate in a fixed
+// device array instead of the handle's scratch (see include/sht.h for who
+// needs it).  The array below is the only storage it uses besides the plan
+// tables and the caller's buffers.
+// ---------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned char g_static_scratch[SHT_STATIC_SCRATCH_BYTES];
+
+// Device address of g_static_scratch, looked up once per device.  In host code
+// the symbol name is only a stand-in for the device object, so kernels must
+// be given the address returned by cudaGetSymbolAddress.
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_ptr[kMaxDevices] = {};
+
+int static_scratch(int device, void **out)
+{
+    if (device < 0 || device >= kMaxDevices) return fail(SHT_EUNSUPPORTED, "device ordinal too large");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(SHT_ECUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+        g_static_ptr[device] = ptr;
+    }
+    *out = g_static_ptr[device];
+    return SHT_OK;
+}
+
+}  // namespace
+
+extern "C" int sht_synth_static(sht_handle h, const void *spec, void *grid, int batch, int mode, void *stream)
+{
+    const void *ptrs[2] = {spec, grid};
+    int rc = prologue(h, batch, mode, 2, ptrs);
+    if (rc) return rc;
+    const size_t need = inter_bytes(h->p, batch, mode);
+    if (need > (size_t)SHT_STATIC_SCRATCH_BYTES)
+        return fail(SHT_EINVAL, "sht_synth_static: this call needs " + std::to_string(need) +
+                                    " bytes of intermediate storage, more than the fixed " +
+                                    std::to_string((size_t)SHT_STATIC_SCRATCH_BYTES) + "-byte array");
+    void *scratch = nullptr;
+    if ((rc = static_scratch(h->p.device, &scratch))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (mode == SHT_F64) {
+        const sht::PlanView<double> pv = h->p.view64();
+        double *eo = static_cast<double *>(scratch);
+        rc = launched(sht::launch_legendre_synth<double>(pv, static_cast<const double *>(spec), eo, batch,
+                                                         sht::OP_SYNTH, s),
+                      "legendre synthesis launch");
+        if (rc) return rc;
+        return launched(sht::launch_fft_synth<double>(pv, eo, static_cast<double *>(grid), batch, sht::OP_SYNTH, s),
+                        "fft synthesis launch");
+    }
+    const sht::PlanView<float> pv = h->p.view32();
+    float *eo = static_cast<float *>(scratch);
+    rc = launched(sht::launch_legendre_synth<float>(pv, static_cast<const float *>(spec), eo, batch, sht::OP_SYNTH, s),
+                  "legendre synthesis launch");
+    if (rc) return rc;
+    return launched(sht::launch_fft_synth<float>(pv, eo, static_cast<float *>(grid), batch, sht::OP_SYNTH, s),
+                    "fft synthesis launch");
+}
