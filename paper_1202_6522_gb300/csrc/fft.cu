@@ -10,8 +10,12 @@
 //              s = w (X_north + X_south), d = w (X_north - X_south).
 // A real transform of length N = 2H is one complex transform of length H on
 // z_n = f_{2n} + i f_{2n+1} plus a pre/post twiddle.  The complex transform is
-// an in-place radix-2 decimation-in-frequency pass sequence, which leaves the
-// spectrum in bit-reversed order; the reads/writes around it undo that.
+// a sequence of Stockham (self-sorting) passes: each thread holds 16 values
+// in registers, runs a radix-16 (or 2/4/8 for the remainder) DFT on them and
+// writes them back permuted, so no bit reversal is needed.  The first r2c
+// pass reads the grid straight from global memory and the last c2r pass
+// writes it straight back; rows in shared memory are padded (one slot every
+// 16) to spread the strided accesses over the banks.
 #include <cuda_runtime.h>
 
 #include "sht_internal.h"
@@ -21,82 +25,198 @@ namespace {
 
 constexpr double kTwoPiD = 6.283185307179586476925286766559;
 
-template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { T2 r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
-template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { T2 r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename T2> __device__ __forceinline__ T2 mk(decltype(T2::x) a, decltype(T2::x) b) { T2 r; r.x = a; r.y = b; return r; }
+template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { return mk<T2>(a.x + b.x, a.y + b.y); }
+template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { return mk<T2>(a.x - b.x, a.y - b.y); }
 template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b)
 {
-    T2 r;
-    r.x = a.x * b.x - a.y * b.y;
-    r.y = a.x * b.y + a.y * b.x;
-    return r;
+    return mk<T2>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 template <typename T2> __device__ __forceinline__ T2 conj_(T2 a) { a.y = -a.y; return a; }
-template <typename T2> __device__ __forceinline__ T2 mul_i(T2 a) { T2 r; r.x = -a.y; r.y = a.x; return r; }
+template <typename T2> __device__ __forceinline__ T2 mul_i(T2 a) { return mk<T2>(-a.y, a.x); }
 
-__device__ __forceinline__ int bitrev(int n, int logH) { return logH == 0 ? 0 : (int)(__brev((unsigned)n) >> (32 - logH)); }
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
 
-// In-place radix-2 DIF over R rows of length H (row stride ld) in shared memory.
-// INV: twiddles e^{+2 pi i ...} (inverse), else e^{-2 pi i ...}.
-template <typename T, bool INV>
-__device__ __forceinline__ void dif_fft(typename Vec2<T>::type *buf, int R, int H, int logH, int ld,
-                                        const typename Vec2<T>::type *__restrict__ tw)
+// cos/sin(2 pi k / 16), k = 0..7 (cos(pi/8) = sqrt(2 + sqrt 2)/2, sin(pi/8) = sqrt(2 - sqrt 2)/2)
+constexpr double kC1 = 0.92387953251128675613, kS1 = 0.38268343236508977173, kR2 = 0.70710678118654752440;
+__host__ __device__ constexpr double c16(int k)
 {
-    using T2 = typename Vec2<T>::type;
-    const int half_total = H >> 1;
-    for (int lh = logH - 1; lh >= 0; --lh) {
-        const int h = 1 << lh;
-        const int tws = logH - lh;  // twiddle index stride: pos * (H / h)
-        for (int t = threadIdx.x; t < R * half_total; t += blockDim.x) {
-            const int r = t >> (logH - 1);
-            const int u = t & (half_total - 1);
-            const int pos = u & (h - 1);
-            const int i0 = ((u >> lh) << (lh + 1)) + pos;
-            T2 *row = buf + r * ld;
-            const T2 a = row[i0], b = row[i0 + h];
-            row[i0] = cadd(a, b);
-            T2 w = tw[pos << tws];
-            if (!INV) w = conj_(w);
-            row[i0 + h] = cmul(csub(a, b), w);
+    return k == 0 ? 1.0 : k == 1 ? kC1 : k == 2 ? kR2 : k == 3 ? kS1 : k == 4 ? 0.0 : k == 5 ? -kS1 : k == 6 ? -kR2 : -kC1;
+}
+__host__ __device__ constexpr double s16(int k)
+{
+    return k == 0 ? 0.0 : k == 1 ? kS1 : k == 2 ? kR2 : k == 3 ? kC1 : k == 4 ? 1.0 : k == 5 ? kC1 : k == 6 ? kR2 : kS1;
+}
+
+// In-register DFT of size RD (natural order in and out), split into even and
+// odd halves recursively.  SIGN = +1: e^{+2 pi i ...} (inverse), -1: forward.
+template <typename T2, int RD, int SIGN>
+struct RegDft {
+    using T = decltype(T2::x);
+    __device__ __forceinline__ static void run(T2 (&v)[RD])
+    {
+        T2 e[RD / 2], o[RD / 2];
+#pragma unroll
+        for (int k = 0; k < RD / 2; ++k) { e[k] = v[2 * k]; o[k] = v[2 * k + 1]; }
+        RegDft<T2, RD / 2, SIGN>::run(e);
+        RegDft<T2, RD / 2, SIGN>::run(o);
+#pragma unroll
+        for (int k = 0; k < RD / 2; ++k) {
+            const int q = k * (16 / RD);
+            const T2 w = mk<T2>(T(c16(q)), T(SIGN * s16(q)));
+            const T2 t = (k == 0) ? o[k] : cmul(w, o[k]);
+            v[k] = cadd(e[k], t);
+            v[k + RD / 2] = csub(e[k], t);
         }
-        __syncthreads();
+    }
+};
+template <typename T2, int SIGN>
+struct RegDft<T2, 1, SIGN> {
+    __device__ __forceinline__ static void run(T2 (&)[1]) {}
+};
+
+// One Stockham pass of radix RD over a row of length H held in `row` (padded
+// indices) or, for the first/last pass, in global memory.  Each thread owns
+// 16 / RD items j = t + it * TPR; item j reads x[j + r H/RD], applies the
+// twiddle W^(r (j mod Ns) H/(Ns RD)), runs the RD-point DFT and writes
+// y[(j / Ns) Ns RD + j mod Ns + r Ns].
+template <typename T2, int RD, int SIGN>
+__device__ __forceinline__ void stockham_load(const T2 *src, bool global_src, int t, int TPR, int H, int Ns,
+                                              const T2 *__restrict__ wtab, T2 (&v)[16])
+{
+    constexpr int IT = 16 / RD;
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int j = t + it * TPR;
+        if (j >= H / RD) break;  // only when H < 16
+        T2 a[RD];
+#pragma unroll
+        for (int r = 0; r < RD; ++r) {
+            const int idx = j + r * (H / RD);
+            a[r] = global_src ? src[idx] : src[padi(idx)];
+        }
+        if (Ns > 1) {
+            const int q0 = (j % Ns) * (H / (Ns * RD));
+#pragma unroll
+            for (int r = 1; r < RD; ++r) {
+                T2 w = wtab[(r * q0) & (H - 1)];
+                if (SIGN < 0) w = conj_(w);
+                a[r] = cmul(a[r], w);
+            }
+        }
+        RegDft<T2, RD, SIGN>::run(a);
+#pragma unroll
+        for (int r = 0; r < RD; ++r) v[it * RD + r] = a[r];
+    }
+}
+
+template <typename T2, int RD>
+__device__ __forceinline__ int stockham_out(int j, int r, int Ns)
+{
+    return (j / Ns) * Ns * RD + (j % Ns) + r * Ns;
+}
+
+template <typename T2, int RD>
+__device__ __forceinline__ void stockham_store_smem(T2 *row, int t, int TPR, int H, int Ns, const T2 (&v)[16])
+{
+    constexpr int IT = 16 / RD;
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int j = t + it * TPR;
+        if (j >= H / RD) break;  // only when H < 16
+#pragma unroll
+        for (int r = 0; r < RD; ++r) row[padi(stockham_out<T2, RD>(j, r, Ns))] = v[it * RD + r];
+    }
+}
+
+// Radix of the first pass: the remainder of log2(H) by 4 (or 16).
+__host__ __device__ inline int first_radix(int logH)
+{
+    const int rem = logH % 4;
+    return rem == 0 ? 16 : (1 << rem);
+}
+
+// Runs a pass of the given radix (run-time selected).
+template <typename T2, int SIGN>
+__device__ __forceinline__ void pass_load(int rd, const T2 *src, bool g, int t, int TPR, int H, int Ns,
+                                          const T2 *wtab, T2 (&v)[16])
+{
+    switch (rd) {
+    case 2: stockham_load<T2, 2, SIGN>(src, g, t, TPR, H, Ns, wtab, v); break;
+    case 4: stockham_load<T2, 4, SIGN>(src, g, t, TPR, H, Ns, wtab, v); break;
+    case 8: stockham_load<T2, 8, SIGN>(src, g, t, TPR, H, Ns, wtab, v); break;
+    default: stockham_load<T2, 16, SIGN>(src, g, t, TPR, H, Ns, wtab, v); break;
+    }
+}
+
+template <typename T2>
+__device__ __forceinline__ void pass_store(int rd, T2 *row, int t, int TPR, int H, int Ns, const T2 (&v)[16])
+{
+    switch (rd) {
+    case 2: stockham_store_smem<T2, 2>(row, t, TPR, H, Ns, v); break;
+    case 4: stockham_store_smem<T2, 4>(row, t, TPR, H, Ns, v); break;
+    case 8: stockham_store_smem<T2, 8>(row, t, TPR, H, Ns, v); break;
+    default: stockham_store_smem<T2, 16>(row, t, TPR, H, Ns, v); break;
+    }
+}
+
+// Twiddle table W_H^q = e^{2 pi i q / H}, q < H, from the plan's e^{2 pi i k / nphi}.
+template <typename T2>
+__device__ __forceinline__ void fill_wtab(T2 *wtab, const T2 *__restrict__ tw, int H)
+{
+    for (int q = threadIdx.x; q < H; q += blockDim.x) {
+        T2 w;
+        if (2 * q < H) {
+            w = tw[2 * q];
+        } else {
+            w = tw[2 * q - H];
+            w.x = -w.x;
+            w.y = -w.y;
+        }
+        wtab[q] = w;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Synthesis: EO [batch][mmax+1][npairs][2] -> grid [batch][nlat][nphi]
+// blockDim = R * TPR with TPR = max(1, H/16) threads per row, R = 2G rows.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_fft_synth(PlanView<T> pv, const T *__restrict__ eo, T *__restrict__ grid, int G, int logH, int op)
 {
     using T2 = typename Vec2<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T2 *buf = reinterpret_cast<T2 *>(smem_raw);
-    const int H = 1 << logH, ld = H + 1, R = 2 * G;
+    const int H = 1 << logH, R = 2 * G;
+    const int TPR = H >= 16 ? H / 16 : 1;
+    const int ld = padi(H) + 1;
+    T2 *wtab = reinterpret_cast<T2 *>(smem_raw);
+    T2 *buf = wtab + H;
     const int b = blockIdx.y;
     const int p0 = blockIdx.x * G;
     const int mmax = pv.mmax, npairs = pv.npairs, nlat = pv.nlat;
     const T2 *eo2 = reinterpret_cast<const T2 *>(eo);
 
+    fill_wtab(wtab, pv.tw, H);
     // 1. spectra of the 2G rows, natural order, zero padded above mmax
-    for (int q = threadIdx.x; q < R * H; q += blockDim.x) {
-        const int m = q / R, r = q - m * R;
-        const int p = p0 + (r >> 1);
-        T2 X;
-        X.x = T(0); X.y = T(0);
+    for (int q = threadIdx.x; q < G * H; q += blockDim.x) {
+        const int m = q / G, i = q - m * G;
+        const int p = p0 + i;
+        T2 XN = mk<T2>(T(0), T(0)), XS = XN;
         if (m <= mmax && p < npairs) {
             const size_t o = (((size_t)b * (mmax + 1) + m) * npairs + p) * 2;
             const T2 E = eo2[o], O = eo2[o + 1];
-            X = (r & 1) ? csub(E, O) : cadd(E, O);
-            if (m == 0) X.y = T(0);
+            XN = cadd(E, O);
+            XS = csub(E, O);
+            if (m == 0) { XN.y = T(0); XS.y = T(0); }
         }
-        buf[r * ld + m] = X;
+        buf[(2 * i) * ld + padi(m)] = XN;
+        buf[(2 * i + 1) * ld + padi(m)] = XS;
     }
     __syncthreads();
     // 2. pre-twiddle: Z_k = (X_k + conj X_{H-k}) + i W^k (X_k - conj X_{H-k}), X_H = 0
     for (int q = threadIdx.x; q < R * (H / 2 + 1); q += blockDim.x) {
         const int r = q / (H / 2 + 1), k = q - r * (H / 2 + 1);
-        if (k > H - k && k != 0) continue;
         T2 *row = buf + r * ld;
         if (k == 0) {
             const T2 X0 = row[0];
@@ -104,32 +224,55 @@ k_fft_synth(PlanView<T> pv, const T *__restrict__ eo, T *__restrict__ grid, int 
             continue;
         }
         const int k2 = H - k;
-        const T2 Xa = row[k], Xb = row[k2];
-        const T2 Za = cadd(cadd(Xa, conj_(Xb)), mul_i(cmul(pv.tw[k], csub(Xa, conj_(Xb)))));
-        row[k] = Za;
-        if (k2 != k) {
-            const T2 Zb = cadd(cadd(Xb, conj_(Xa)), mul_i(cmul(pv.tw[k2], csub(Xb, conj_(Xa)))));
-            row[k2] = Zb;
-        }
+        const T2 Xa = row[padi(k)], Xb = row[padi(k2)];
+        row[padi(k)] = cadd(cadd(Xa, conj_(Xb)), mul_i(cmul(pv.tw[k], csub(Xa, conj_(Xb)))));
+        if (k2 != k) row[padi(k2)] = cadd(cadd(Xb, conj_(Xa)), mul_i(cmul(pv.tw[k2], csub(Xb, conj_(Xa)))));
     }
     __syncthreads();
-    // 3. inverse complex FFT of length H (output bit-reversed)
-    dif_fft<T, true>(buf, R, H, logH, ld, pv.tw);
-    // 4. f_{2n} = Re z_n, f_{2n+1} = Im z_n, scaled for the adjoint of analysis
-    T2 *grid2 = reinterpret_cast<T2 *>(grid);
-    for (int q = threadIdx.x; q < R * H; q += blockDim.x) {
-        const int r = q >> logH, n = q & (H - 1);
-        const int p = p0 + (r >> 1);
-        if (p >= npairs) continue;
-        const int j = (r & 1) ? nlat - 1 - p : p;
-        if ((r & 1) && j == p) continue;  // equator row is written once
-        T2 z = buf[r * ld + bitrev(n, logH)];
-        if (op == OP_ANALYS_ADJ) {
-            const T sc = T(kTwoPiD) / T(pv.nphi) * pv.wq[p];
-            z.x *= sc;
-            z.y *= sc;
+    // 3. inverse complex FFT of length H by Stockham passes; the last one writes the grid
+    const int r = threadIdx.x / TPR, t = threadIdx.x - r * TPR;
+    const int p = p0 + (r >> 1);
+    const int j = (r & 1) ? nlat - 1 - p : p;
+    const bool live_row = r < R && p < npairs && !((r & 1) && j == p);
+    T scale = T(1);
+    if (op == OP_ANALYS_ADJ && p < npairs) scale = T(kTwoPiD) / T(pv.nphi) * pv.wq[p];
+    T2 *row = buf + (r < R ? r : 0) * ld;
+    T2 *out = reinterpret_cast<T2 *>(grid) + ((size_t)b * nlat + (live_row ? j : 0)) * H;
+    if (H == 1) {
+        if (threadIdx.x < R && live_row) {
+            T2 z = row[0];
+            z.x *= scale; z.y *= scale;
+            out[0] = z;
         }
-        grid2[((size_t)b * nlat + j) * H + n] = z;
+        return;
+    }
+    int Ns = 1;
+    int rd = first_radix(logH);
+    T2 v[16];
+    while (true) {
+        if (r < R) pass_load<T2, 1>(rd, row, false, t, TPR, H, Ns, wtab, v);
+        const bool last = Ns * rd == H;
+        __syncthreads();
+        if (last) {
+            // last pass: y[j + r' H/RD] for item j -- contiguous over threads
+            if (live_row) {
+                const int IT = 16 / rd;
+                for (int it = 0; it < IT; ++it) {
+                    const int jj = t + it * TPR;
+                    if (jj >= H / rd) break;  // only when H < 16
+                    for (int rr = 0; rr < rd; ++rr) {
+                        T2 z = v[it * rd + rr];
+                        z.x *= scale; z.y *= scale;
+                        out[jj + rr * (H / rd)] = z;
+                    }
+                }
+            }
+            break;
+        }
+        if (r < R) pass_store<T2>(rd, row, t, TPR, H, Ns, v);
+        __syncthreads();
+        Ns *= rd;
+        rd = 16;
     }
 }
 
@@ -137,84 +280,118 @@ k_fft_synth(PlanView<T> pv, const T *__restrict__ eo, T *__restrict__ grid, int 
 // Analysis: grid [batch][nlat][nphi] -> SD [batch][mmax+1][npairs][2]
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_fft_analys(PlanView<T> pv, const T *__restrict__ grid, T *__restrict__ sd, int G, int logH, int op, int vector)
 {
     using T2 = typename Vec2<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T2 *buf = reinterpret_cast<T2 *>(smem_raw);
-    const int H = 1 << logH, ld = H + 1, R = 2 * G;
+    const int H = 1 << logH, R = 2 * G;
+    const int TPR = H >= 16 ? H / 16 : 1;
+    const int ld = padi(H) + 1;
+    T2 *wtab = reinterpret_cast<T2 *>(smem_raw);
+    T2 *buf = wtab + H;
     const int b = blockIdx.y;
     const int p0 = blockIdx.x * G;
     const int mmax = pv.mmax, npairs = pv.npairs, nlat = pv.nlat;
-    const T2 *grid2 = reinterpret_cast<const T2 *>(grid);
 
-    // 1. rows as complex z_n = f_{2n} + i f_{2n+1}
-    for (int q = threadIdx.x; q < R * H; q += blockDim.x) {
-        const int r = q >> logH, n = q & (H - 1);
-        const int p = p0 + (r >> 1);
-        const int j = (r & 1) ? nlat - 1 - p : p;
-        T2 z;
-        z.x = T(0); z.y = T(0);
-        if (p < npairs && !((r & 1) && j == p)) z = grid2[((size_t)b * nlat + j) * H + n];
-        buf[r * ld + n] = z;
+    fill_wtab(wtab, pv.tw, H);
+    __syncthreads();
+    const int r = threadIdx.x / TPR, t = threadIdx.x - r * TPR;
+    const int p = p0 + (r >> 1);
+    const int j = (r & 1) ? nlat - 1 - p : p;
+    const bool live_row = r < R && p < npairs && !((r & 1) && j == p);
+    T2 *row = buf + (r < R ? r : 0) * ld;
+    const T2 *in = reinterpret_cast<const T2 *>(grid) + ((size_t)b * nlat + (live_row ? j : 0)) * H;
+
+    if (H == 1) {
+        if (threadIdx.x < R) row[0] = live_row ? in[0] : mk<T2>(T(0), T(0));
+    } else {
+        // forward complex FFT of length H; the first pass reads the grid row
+        int Ns = 1;
+        int rd = first_radix(logH);
+        T2 v[16];
+        bool first = true;
+        while (true) {
+            if (r < R) {
+                if (first) {
+                    if (live_row) {
+                        pass_load<T2, -1>(rd, in, true, t, TPR, H, Ns, wtab, v);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) v[q] = mk<T2>(T(0), T(0));
+                    }
+                } else {
+                    pass_load<T2, -1>(rd, row, false, t, TPR, H, Ns, wtab, v);
+                }
+            }
+            first = false;
+            __syncthreads();
+            if (r < R) pass_store<T2>(rd, row, t, TPR, H, Ns, v);
+            __syncthreads();
+            Ns *= rd;
+            if (Ns == H) break;
+            rd = 16;
+        }
     }
     __syncthreads();
-    // 2. forward complex FFT of length H (output bit-reversed)
-    dif_fft<T, false>(buf, R, H, logH, ld, pv.tw);
-    // 3. post-twiddle, scale, fold north/south, weight
+    // post-twiddle, scale, fold north/south, weight
     T2 *sd2 = reinterpret_cast<T2 *>(sd);
     const T fscale = (op == OP_ANALYS) ? T(kTwoPiD) / T(pv.nphi) : T(1);
     for (int q = threadIdx.x; q < G * (mmax + 1); q += blockDim.x) {
         const int m = q / G, i = q - m * G;
-        const int p = p0 + i;
-        if (p >= npairs) continue;
+        const int pp = p0 + i;
+        if (pp >= npairs) continue;
         T2 X[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const T2 *row = buf + (2 * i + h) * ld;
-            const T2 Zk = row[bitrev(m, logH)];
-            const T2 Zc = conj_(row[bitrev((H - m) & (H - 1), logH)]);
+            const T2 *rw = buf + (2 * i + h) * ld;
+            const T2 Zk = rw[padi(m)];
+            const T2 Zc = conj_(rw[padi((H - m) & (H - 1))]);
             T2 E = cadd(Zk, Zc), O = csub(Zk, Zc);
             E.x *= T(0.5); E.y *= T(0.5);
-            // O / (2i) = -i O / 2
-            T2 Od;
-            Od.x = O.y * T(0.5);
-            Od.y = -O.x * T(0.5);
+            const T2 Od = mk<T2>(O.y * T(0.5), -O.x * T(0.5));  // O / (2i)
             X[h] = cadd(E, cmul(conj_(pv.tw[m]), Od));
         }
         T wf = fscale;
-        if (op == OP_ANALYS) wf *= pv.wq[p];
-        if (vector) wf /= pv.st[p];
-        const bool equator = (nlat & 1) && p == npairs - 1;
+        if (op == OP_ANALYS) wf *= pv.wq[pp];
+        if (vector) wf /= pv.st[pp];
+        const bool equator = (nlat & 1) && pp == npairs - 1;
         T2 s, d;
         if (equator) {
-            s.x = wf * X[0].x; s.y = wf * X[0].y;
+            s = mk<T2>(wf * X[0].x, wf * X[0].y);
             d = s;
         } else {
-            s.x = wf * (X[0].x + X[1].x); s.y = wf * (X[0].y + X[1].y);
-            d.x = wf * (X[0].x - X[1].x); d.y = wf * (X[0].y - X[1].y);
+            s = mk<T2>(wf * (X[0].x + X[1].x), wf * (X[0].y + X[1].y));
+            d = mk<T2>(wf * (X[0].x - X[1].x), wf * (X[0].y - X[1].y));
         }
-        const size_t o = (((size_t)b * (mmax + 1) + m) * npairs + p) * 2;
+        const size_t o = (((size_t)b * (mmax + 1) + m) * npairs + pp) * 2;
         sd2[o] = s;
         sd2[o + 1] = d;
     }
 }
 
-template <typename T>
-int pick_group(int H)
-{
-    // rows of (H+1) complex values; keep the CTA's buffer within 64 KB
-    const size_t row = (size_t)(H + 1) * sizeof(typename Vec2<T>::type);
-    int g = (int)((64 * 1024) / (2 * row));
-    if (g > 8) g = 8;
-    if (g < 1) g = 1;
-    return g;
-}
-
 inline int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 
-template <typename T, typename K>
+// Threads per row and pairs per CTA: TPR = H/16 threads per row (>= 1) and
+// enough rows for >= 256 threads, capped so the CTA's buffer stays <= 96 KB.
+template <typename T>
+void fft_shape(int H, int npairs, int &G, int &threads, size_t &smem)
+{
+    using T2 = typename Vec2<T>::type;
+    const int TPR = H >= 16 ? H / 16 : 1;
+    int rows = 256 / TPR;
+    if (rows < 2) rows = 2;
+    const size_t row_bytes = (size_t)((H + (H >> 4)) + 1) * sizeof(T2);
+    while (rows > 2 && (size_t)rows * row_bytes > 96 * 1024) rows /= 2;
+    G = rows / 2;
+    if (G > npairs) G = npairs < 1 ? 1 : npairs;
+    threads = 2 * G * TPR;
+    if (threads < 32) threads = 32;
+    threads = (threads + 31) & ~31;
+    smem = (size_t)H * sizeof(T2) + (size_t)2 * G * row_bytes;
+}
+
+template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes)
 {
     if (bytes <= 48 * 1024) return cudaSuccess;
@@ -227,12 +404,13 @@ template <typename T>
 cudaError_t launch_fft_synth(const PlanView<T> &pv, const T *eo, T *grid, int batch, Op op, cudaStream_t s)
 {
     const int H = pv.nphi / 2, logH = ilog2(H);
-    const int G = pick_group<T>(H);
-    const size_t smem = (size_t)2 * G * (H + 1) * sizeof(typename Vec2<T>::type);
-    cudaError_t e = set_smem<T>(k_fft_synth<T>, smem);
+    int G, threads;
+    size_t smem;
+    fft_shape<T>(H, pv.npairs, G, threads, smem);
+    cudaError_t e = set_smem(k_fft_synth<T>, smem);
     if (e != cudaSuccess) return e;
     dim3 gridd((unsigned)((pv.npairs + G - 1) / G), (unsigned)batch);
-    k_fft_synth<T><<<gridd, 256, smem, s>>>(pv, eo, grid, G, logH, (int)op);
+    k_fft_synth<T><<<gridd, threads, smem, s>>>(pv, eo, grid, G, logH, (int)op);
     return cudaGetLastError();
 }
 
@@ -241,12 +419,13 @@ cudaError_t launch_fft_analys(const PlanView<T> &pv, const T *grid, T *sd, int b
                               cudaStream_t s)
 {
     const int H = pv.nphi / 2, logH = ilog2(H);
-    const int G = pick_group<T>(H);
-    const size_t smem = (size_t)2 * G * (H + 1) * sizeof(typename Vec2<T>::type);
-    cudaError_t e = set_smem<T>(k_fft_analys<T>, smem);
+    int G, threads;
+    size_t smem;
+    fft_shape<T>(H, pv.npairs, G, threads, smem);
+    cudaError_t e = set_smem(k_fft_analys<T>, smem);
     if (e != cudaSuccess) return e;
     dim3 gridd((unsigned)((pv.npairs + G - 1) / G), (unsigned)batch);
-    k_fft_analys<T><<<gridd, 256, smem, s>>>(pv, grid, sd, G, logH, (int)op, vector ? 1 : 0);
+    k_fft_analys<T><<<gridd, threads, smem, s>>>(pv, grid, sd, G, logH, (int)op, vector ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -700,8 +700,10 @@ cudaError_t analys_vec_go(const PlanView<T> &pv, const T *sdt, const T *sdp, T *
     return cudaGetLastError();
 }
 
-// Pairs per thread for analysis, so that <= 8 warps cover all pairs.
-inline int analys_lpt(int npairs) { return npairs <= 512 ? 2 : (npairs <= 1024 ? 4 : 8); }
+// Pairs per thread for analysis: the cross-lane reduction costs ~1/LPT of the
+// sums, so use 4 pairs per thread once there are enough pairs, 8 beyond 1024
+// (at most 8 warps per CTA).
+inline int analys_lpt(int npairs) { return npairs <= 64 ? 2 : (npairs <= 1024 ? 4 : 8); }
 
 }  // namespace
 
