@@ -54,6 +54,21 @@ def legendre_flops_per_launch(batch, lmax=LMAX, nlat=NLAT):
     return nlm_of(lmax) * npairs * (4.0 + 4.0 * batch)
 
 
+def tc_panel_bytes(lmax=LMAX, nlat=NLAT):
+    """Bytes of the synthesis and analysis P_n^m panel sets (bf16 hi+lo, padded
+    to 128-row x 32-column tiles), as laid out by the library."""
+    npairs = (nlat + 1) // 2
+    T = (npairs + 127) // 128
+    kch = (npairs + 31) // 32
+    bs = ba = 0
+    for m in range(lmax + 1):
+        L = lmax - m + 1
+        Le = (L + 1) // 2
+        bs += T * ((Le + 31) // 32) * 32768
+        ba += ((Le + 127) // 128) * kch * 32768
+    return bs, ba
+
+
 def fp32_alu_peak(sm_mhz):
     """FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 flops x clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6
@@ -183,6 +198,62 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+def uneven_batch(torch, dev, replays=200):
+    """96 FP32 fields with N drawn from {63, 127, 255, 511} (nlat = N+1, nphi =
+    2(N+1)): round-trip latency of one graph launch per direction vs the same
+    persistent kernels launched directly vs one launch pair per field."""
+    from paper_1202_6522_gb300 import SHT, UnevenBatch, synthetic
+    lmaxs = synthetic.uneven_truncations(96)
+    hist = {str(n): lmaxs.count(n) for n in sorted(set(lmaxs))}
+    specs = [torch.from_numpy(synthetic.spectrum(l, seed=i).astype("complex64")).to(dev) for i, l in enumerate(lmaxs)]
+    plans = {l: SHT(l, l, l + 1, 2 * (l + 1), device=dev) for l in set(lmaxs)}
+    stream = torch.cuda.current_stream(dev)
+
+    def per_field():
+        for l, sp in zip(lmaxs, specs):
+            plans[l].analys_(plans[l].synth_(sp))
+
+    def measure(fn):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        lat = []
+        t0 = time.perf_counter()
+        for _ in range(replays):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            lat.append(e0.elapsed_time(e1))
+        wall = time.perf_counter() - t0
+        lat.sort()
+        return {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[int(0.99 * (len(lat) - 1))],
+                "round_trips_per_s": len(lmaxs) * replays / wall}
+
+    out = {"fields": len(lmaxs), "truncations": hist, "replays": replays}
+    for name, graph in (("graph", True), ("persistent_no_graph", False)):
+        ub = UnevenBatch(lmaxs, device=dev, use_graph=graph)
+        grids = ub.synth_(specs)
+        back = ub.analys_(grids)
+        out[name] = measure(lambda: ub.analys_(ub.synth_(specs, out=grids), out=back))
+    out["per_field_launches"] = measure(per_field)
+    return out
+
+
+def round_trip_errors(sht, torch, dev, cdt):
+    """Sec. 3.5 error measures of one round trip of uniform [-1, 1] spectra."""
+    import numpy as np
+    from paper_1202_6522_gb300 import synthetic
+    Q = synthetic.spectrum(LMAX, seed=0, uniform=True)
+    Qd = torch.from_numpy(Q).to(dev, cdt)
+    R = sht.analys_(sht.synth_(Qd)).cpu().numpy().astype(np.complex128)
+    Qr = Qd.cpu().numpy().astype(np.complex128)
+    d = np.abs(R - Qr)
+    return {"eps_max": float(d.max()), "eps_rms": float(np.sqrt(2.0 / ((LMAX + 1) * (LMAX + 2)) * np.sum(d * d)))}
+
+
 def time_path(sht, torch, a, steps, warmup, stream, profile=False):
     """Device-timed round trips on inputs resident in HBM.  Returns (ms per step, kernel table)."""
     from paper_1202_6522_gb300 import _capi as C
@@ -222,7 +293,17 @@ def run_ours(args):
     B.build()
     sht = SHT(LMAX, LMAX, NLAT, NPHI, device=dev)
     stream = torch.cuda.current_stream(dev)
-    cdt = torch.complex64 if args.mode == "f32" else torch.complex128
+    if args.mode == "tc":
+        sht = SHT(LMAX, LMAX, NLAT, NPHI, device=dev, fp32_path="tc")
+    tune_report = None
+    if args.mode == "auto":
+        # runtime tuning before timing: kernel shapes and on-the-fly vs precomputed panels
+        from paper_1202_6522_gb300 import _capi as C
+        f32_ms, tc_ms = C.sht_tune(sht._h, BATCH, C.SHT_F32_AUTO, stream.cuda_stream)
+        sht.fp32_mode = C.SHT_F32_AUTO
+        tune_report = {"f32_round_trip_ms": f32_ms, "tc_round_trip_ms": tc_ms,
+                       "chosen": "tc" if (tc_ms > 0 and tc_ms < f32_ms) else "f32"}
+    cdt = torch.complex128 if args.mode == "f64" else torch.complex64
     a_np = synthetic.spectrum(LMAX, batch=BATCH, seed=rank)
     a = torch.from_numpy(a_np).to(dev, cdt)
 
@@ -289,11 +370,15 @@ def run_ours(args):
     e2e = {"value": world * BATCH * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step}
 
+    errors = round_trip_errors(sht, torch, dev, cdt)
+    ubatch = uneven_batch(torch, dev) if (rank == 0 and not args.no_uneven) else None
+
     # --- the plain FP64 path on the same workload (the metric's denominator) ---
     fp64 = None
     if args.mode != "f64":
         a64 = torch.from_numpy(a_np).to(dev, torch.complex128)
         ms64, tab64 = time_path(sht, torch, a64, max(2, args.steps // 4), 1, stream, profile=True)
+        del a64
         fp64 = {"round_trips_per_s": world * BATCH / (ms64 / 1e3), "ms_per_step": ms64,
                 "kernels_ms": {k: v[0] / v[1] for k, v in tab64.items()}}
 
@@ -303,29 +388,48 @@ def run_ours(args):
     dom = max(table.items(), key=lambda kv: kv[1][0])
     dom_name, (dom_ms, dom_n) = dom
     dom_avg = dom_ms / dom_n
-    flops = legendre_flops_per_launch(BATCH) if dom_name.startswith("legendre") else None
     sm_max = clk.get("sm_max_mhz") or 2070.0
-    if args.mode == "f32":
-        peak = fp32_alu_peak(sm_max)
-        peak_note = f"FP32 FMA: 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz"
+    if dom_name.startswith("tc_"):
+        # the panels stream from HBM once per launch: bytes bound the kernel
+        bs, ba = tc_panel_bytes()
+        npairs = (NLAT + 1) // 2
+        inter = BATCH * (LMAX + 1) * npairs * 16
+        spec_b = BATCH * nlm_of(LMAX) * 8
+        algo = (bs + spec_b + inter) if dom_name == "tc_synth" else (ba + inter + spec_b)
+        peaks = read_peaks()
+        peak = peaks.get("hbm_gbs", 6800.0) * 1e9
+        achieved = algo / (dom_avg / 1e3)
+        roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved / 1e9, "peak": peak / 1e9,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
+                "algorithmic_bytes": algo, "kernel_avg_ms": dom_avg, "launches": dom_n}
     else:
-        peak = FP64_PEAK_NOMINAL
-        peak_note = "FP64 nominal 1.25 TFLOP/s"
-    achieved = flops / (dom_avg / 1e3) if flops else None
-    roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved / 1e12 if achieved else None,
-            "peak": peak / 1e12, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-            "traffic": None, "peak_source": peak_note,
-            "kernel_avg_ms": dom_avg, "launches": dom_n}
+        flops = legendre_flops_per_launch(BATCH) if dom_name.startswith("legendre") else None
+        if args.mode == "f32":
+            peak = fp32_alu_peak(sm_max)
+            peak_note = f"FP32 FMA: 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz"
+        else:
+            peak = FP64_PEAK_NOMINAL
+            peak_note = "FP64 nominal 1.25 TFLOP/s"
+        achieved = flops / (dom_avg / 1e3) if flops else None
+        roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved / 1e12 if achieved else None,
+                "peak": peak / 1e12, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": None, "peak_source": peak_note,
+                "kernel_avg_ms": dom_avg, "launches": dom_n}
     kernels = {k: {"avg_ms": v[0] / v[1], "launches": v[1], "share": v[0] / sum(x[0] for x in table.values())}
                for k, v in table.items()}
     launches = sum(v[1] for v in table.values())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": args.mode, "data": "synthetic (seeded N(0,1)/(n+1) spectra)",
+        "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "tc": "bf16x3 (f32 accumulate)",
+                                       "auto": "f32 / bf16x3 (tuned)"}[args.mode],
+        "data": "synthetic (seeded N(0,1)/(n+1) spectra)",
         "config": {"workload": WORKLOAD, "lmax": LMAX, "nlat": NLAT, "nphi": NPHI, "batch": BATCH,
-                   "path": "FP32 on-the-fly recurrence with exponent scale" if args.mode == "f32"
-                   else "plain FP64 on-the-fly", "l2": "inputs larger than L2 (spectra+grids > 129 MB)",
+                   "path": {"f32": "FP32 on-the-fly recurrence with exponent scale",
+                            "f64": "plain FP64 on-the-fly",
+                            "tc": "tcgen05 split-bf16 contraction vs FP64-built P panels",
+                            "auto": "runtime-tuned: FP32 on-the-fly or tcgen05 panels"}[args.mode], "l2": "inputs larger than L2 (spectra+grids > 129 MB)",
                    "parallelism": f"replicas x{world}"},
         "gflops_nominal": value * nominal_flops_per_rt() / 1e9,
         "elements_per_s": value * (LMAX + 1) ** 3,
@@ -335,7 +439,12 @@ def run_ours(args):
         "clocks": clk,
         "e2e": e2e,
         "round_trip_max_err_vs_input": ref_err,
+        "round_trip_error_sec35": errors,
     }
+    if tune_report:
+        line["tuning"] = tune_report
+    if ubatch:
+        line["uneven_batch"] = ubatch
     if fp64:
         line["fp64_plain"] = fp64
         line["speedup_vs_fp64_plain"] = value / fp64["round_trips_per_s"]
@@ -354,8 +463,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--mode", choices=["auto", "tc", "f32", "f64"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

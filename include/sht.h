@@ -72,8 +72,19 @@ enum {
 };
 
 enum {
-    SHT_F64 = 0,  /* FP64 throughout: the plain path                            */
-    SHT_F32 = 1   /* FP32 data and recurrence with an explicit exponent scale   */
+    SHT_F64 = 0,       /* FP64 throughout: the plain path                              */
+    SHT_F32 = 1,       /* FP32 data and recurrence with an explicit exponent scale     */
+    SHT_TC_BF16X3 = 2, /* FP32 data; the per-order Legendre contraction on the tensor
+                        * cores against P_n^m panels built once by the FP64 recurrence
+                        * (the precomputed-P_n^m variant of Sec. 3.1), each operand split
+                        * into bf16 hi + lo and multiplied as hi*hi + hi*lo + lo*hi with
+                        * FP32 accumulation.  Scalar transforms and their adjoints only
+                        * (vector calls return SHT_EUNSUPPORTED).  The panels take
+                        * about 2 (lmax+1)^3 bytes (2.5 GB at lmax = 1023) and are built
+                        * by the first call in this mode or by sht_reserve. */
+    SHT_F32_AUTO = 3   /* FP32 data: whichever of SHT_F32 and SHT_TC_BF16X3 sht_tune
+                        * measured faster for this batch size (SHT_F32 if untuned);
+                        * vector transforms always take SHT_F32. */
 };
 
 /* Build a plan (Sec. 2.3 nodes/weights, Sec. 3.2 recurrence tables, FFT
@@ -132,7 +143,9 @@ SHT_API int sht_lm_index(sht_handle h, int n, int m);
 SHT_API int sht_gauss(sht_handle h, double *x, double *w);
 
 /* Synchronise `stream` and report any CUDA error raised by work enqueued by
- * this library (SHT_ECUDA), or SHT_OK. */
+ * this library (SHT_ECUDA), a tensor-core kernel whose bounded wait for its
+ * own copies or MMAs gave up (SHT_ETIMEOUT; the kernel then skipped its
+ * output and returned), or SHT_OK.  Reading the status clears it. */
 SHT_API int sht_sync_status(sht_handle h, void *stream);
 
 /* Scalar synthesis that allocates nothing (no counterpart in the paper; an
@@ -159,6 +172,37 @@ SHT_API int sht_sync_status(sht_handle h, void *stream);
 #define SHT_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
 SHT_API int sht_synth_static(sht_handle h, const void *spec, void *grid, int batch, int mode, void *stream);
 
+/* Runtime tuning, after the paper's runtime tuning (Sec. 3.2): time the
+ * candidate kernel shapes of the Legendre stage (latitude pairs per thread x
+ * fields per CTA) for `batch` fields in `mode` (SHT_F64 or SHT_F32) and keep
+ * the fastest for later calls with that batch size.  With SHT_F32_AUTO it also
+ * times a full FP32 round trip on the CUDA cores (on-the-fly recurrence)
+ * against the tensor-core path (precomputed panels) -- the paper's two
+ * variants -- and records the faster for SHT_F32_AUTO calls at that batch.
+ * report (may be NULL): report[0], report[1] = best synthesis and analysis
+ * Legendre times in ms (SHT_F64/SHT_F32), or FP32 and tensor-core round-trip
+ * times in ms (SHT_F32_AUTO).  Allocates temporary buffers, synchronises the
+ * stream, and takes from milliseconds to a few seconds. */
+SHT_API int sht_tune(sht_handle h, int batch, int mode, double *report, void *stream);
+
+/* Uneven batches: many scalar FP32 fields, each with its own truncation
+ * (mmax = lmax), transformed by one launch.  The plan groups fields of equal
+ * shape, builds one tile list per stage over all fields, sorted longest first,
+ * and runs each stage as one persistent kernel whose CTAs take tiles from an
+ * atomic counter (no CTA waits on another).  With use_graph != 0 the whole
+ * sequence (pointer-table copy, counter reset, Legendre and FFT kernels) is
+ * captured into a CUDA graph by the first call of each direction and replayed
+ * afterwards; the capture happens on a private stream.
+ * Limits: nphi a power of two in [2, 4096], nlat <= 1024.
+ * spec[f] / grid[f]: device pointers of field f ([nlm_f] complex floats and
+ * [nlat_f][nphi_f] floats).  A call waits on the host until the previous call
+ * on this batch plan has started its pointer-table copy. */
+typedef struct sht_batch_plan *sht_batch;
+SHT_API int sht_batch_create(int nfields, const int *lmax, const int *nlat, const int *nphi, sht_batch *out);
+SHT_API void sht_batch_destroy(sht_batch b);
+SHT_API int sht_batch_synth(sht_batch b, void *const *spec, void *const *grid, int use_graph, void *stream);
+SHT_API int sht_batch_analys(sht_batch b, void *const *grid, void *const *spec, int use_graph, void *stream);
+
 /* Per-kernel timing, for measurement (no counterpart in the paper).  While
  * enabled, every kernel the handle launches is bracketed by CUDA events on the
  * call's stream.  sht_profile_read synchronises those events and writes, for
@@ -172,11 +216,20 @@ enum {
     SHT_K_LEGENDRE_ANALYS_VEC = 3,
     SHT_K_FFT_SYNTH = 4,
     SHT_K_FFT_ANALYS = 5,
-    SHT_NKERNELS = 6
+    SHT_K_TC_SYNTH = 6,
+    SHT_K_TC_ANALYS = 7,
+    SHT_NKERNELS = 8
 };
 SHT_API int sht_profile(sht_handle h, int enable);
 SHT_API int sht_profile_read(sht_handle h, double *ms, int *count, int cap);
 SHT_API const char *sht_kernel_name(int kind);
+
+/* Failure-detection self-test (no counterpart in the paper): enqueue a kernel
+ * that waits, with a bound of timeout_us microseconds, on a barrier that
+ * nothing completes -- the same bounded wait the tensor-core kernels use --
+ * so that the next sht_sync_status on that stream reports SHT_ETIMEOUT.  The
+ * kernel never faults or hangs, and the handle stays usable afterwards. */
+SHT_API int sht_selftest_timeout(sht_handle h, int timeout_us, void *stream);
 
 /* Message for the last error raised in the calling thread ("" if none). */
 SHT_API const char *sht_last_error(void);

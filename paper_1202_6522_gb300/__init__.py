@@ -6,13 +6,16 @@ front end; ``_capi`` is the ctypes binding with the C names.
 """
 from __future__ import annotations
 
-__all__ = ["SHT", "build", "synthetic"]
+__all__ = ["SHT", "UnevenBatch", "build", "synthetic"]
 
 
 def __getattr__(name):
     if name == "SHT":
         from .transform import SHT
         return SHT
+    if name == "UnevenBatch":
+        from .transform import UnevenBatch
+        return UnevenBatch
     if name == "build":
         from .build import build
         return build

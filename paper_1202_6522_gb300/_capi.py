@@ -22,6 +22,8 @@ SHT_EUNSUPPORTED = -5
 
 SHT_F64 = 0
 SHT_F32 = 1
+SHT_TC_BF16X3 = 2
+SHT_F32_AUTO = 3
 
 _lib = None
 _lock = threading.Lock()
@@ -47,13 +49,19 @@ SIGNATURES = {
     "sht_gauss": ([_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], _I),
     "sht_sync_status": ([_VP, _VP], _I),
     "sht_synth_static": ([_VP, _VP, _VP, _I, _I, _VP], _I),
+    "sht_batch_create": ([_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_VP)], _I),
+    "sht_batch_destroy": ([_VP], None),
+    "sht_batch_synth": ([_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP], _I),
+    "sht_batch_analys": ([_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP], _I),
+    "sht_tune": ([_VP, _I, _I, ctypes.POINTER(ctypes.c_double), _VP], _I),
+    "sht_selftest_timeout": ([_VP, _I, _VP], _I),
     "sht_profile": ([_VP, _I], _I),
     "sht_profile_read": ([_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I), _I], _I),
     "sht_kernel_name": ([_I], ctypes.c_char_p),
     "sht_last_error": ([], ctypes.c_char_p),
 }
 
-SHT_NKERNELS = 6
+SHT_NKERNELS = 8
 
 
 def library_path() -> str:
@@ -171,6 +179,46 @@ def sht_synth_static(h, spec, grid, batch, mode, stream):
 
 
 SHT_STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
+
+
+def _ints(v):
+    arr = (ctypes.c_int * len(v))(*[int(x) for x in v])
+    return arr
+
+
+def _ptrs(v):
+    return (_VP * len(v))(*[int(x) for x in v])
+
+
+def sht_batch_create(lmax, nlat, nphi) -> int:
+    """Uneven batch plan over len(lmax) fields (mmax = lmax each)."""
+    h = _VP()
+    n = len(lmax)
+    check(_call("sht_batch_create", n, _ints(lmax), _ints(nlat), _ints(nphi), ctypes.byref(h)))
+    return h.value
+
+
+def sht_batch_destroy(b) -> None:
+    _call("sht_batch_destroy", b)
+
+
+def sht_batch_synth(b, spec_ptrs, grid_ptrs, use_graph, stream):
+    return check(_call("sht_batch_synth", b, _ptrs(spec_ptrs), _ptrs(grid_ptrs), int(bool(use_graph)), stream))
+
+
+def sht_batch_analys(b, grid_ptrs, spec_ptrs, use_graph, stream):
+    return check(_call("sht_batch_analys", b, _ptrs(grid_ptrs), _ptrs(spec_ptrs), int(bool(use_graph)), stream))
+
+
+def sht_tune(h, batch, mode, stream):
+    """Runtime tuning; returns the two timings of the report (ms)."""
+    rep = (ctypes.c_double * 2)()
+    check(_call("sht_tune", h, batch, mode, rep, stream))
+    return rep[0], rep[1]
+
+
+def sht_selftest_timeout(h, timeout_us, stream):
+    return check(_call("sht_selftest_timeout", h, timeout_us, stream))
 
 
 def sht_profile(h, enable):

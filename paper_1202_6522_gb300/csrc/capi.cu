@@ -39,16 +39,74 @@ int check_handle(sht_handle h)
 
 int check_mode(int mode)
 {
-    if (mode != SHT_F64 && mode != SHT_F32) return fail(SHT_EINVAL, "unknown mode");
+    if (mode != SHT_F64 && mode != SHT_F32 && mode != SHT_TC_BF16X3 && mode != SHT_F32_AUTO)
+        return fail(SHT_EINVAL, "unknown mode");
+    return SHT_OK;
+}
+
+// Build the tensor-core panels once (allocates about 2 (lmax+1)^3 bytes).
+int ensure_panels(sht::Plan &p)
+{
+    if (p.panel_s) return SHT_OK;
+    std::vector<unsigned long long> off_s, off_a, dchunk;
+    size_t bs = 0, ba = 0, nch = 0;
+    sht::tc_panel_layout(p.lmax, p.mmax, p.npairs, off_s, off_a, bs, ba, dchunk, nch);
+    const size_t ob = off_s.size() * sizeof(unsigned long long);
+    cudaError_t e = cudaMalloc(&p.panel_s, bs);
+    if (e == cudaSuccess) e = cudaMalloc(&p.panel_a, ba);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_off_s, ob);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_off_a, ob);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_dchunk, ob);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p.panel_s); cudaFree(p.panel_a); cudaFree(p.d_off_s); cudaFree(p.d_off_a); cudaFree(p.d_dchunk);
+        p.panel_s = p.panel_a = nullptr;
+        p.d_off_s = p.d_off_a = p.d_dchunk = nullptr;
+        return fail(SHT_ENOMEM, std::string("cudaMalloc(tensor-core panels): ") + cudaGetErrorString(e));
+    }
+    p.tc_nchunk_s = nch;
+    e = cudaMemcpy(p.d_off_s, off_s.data(), ob, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p.d_off_a, off_a.data(), ob, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p.d_dchunk, dchunk.data(), ob, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(p.panel_s, 0, bs);
+    if (e == cudaSuccess) e = cudaMemset(p.panel_a, 0, ba);
+    if (e == cudaSuccess) e = sht::launch_build_panels(p.view64(), p.d_off_s, p.d_off_a, p.panel_s, p.panel_a, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(p.panel_s); cudaFree(p.panel_a); cudaFree(p.d_off_s); cudaFree(p.d_off_a); cudaFree(p.d_dchunk);
+        p.panel_s = p.panel_a = nullptr;
+        p.d_off_s = p.d_off_a = p.d_dchunk = nullptr;
+        return fail(SHT_ECUDA, std::string("building tensor-core panels: ") + cudaGetErrorString(e));
+    }
     return SHT_OK;
 }
 
 size_t elem_size(int mode) { return mode == SHT_F64 ? sizeof(double) : sizeof(float); }
 
+// Tensor-core scalar transforms: the Legendre contraction on tcgen05, FFTs in FP32.
+int run_synth_tc(sht::Plan &p, const void *spec, void *grid, int batch, sht::Op op, cudaStream_t s);
+int run_analys_tc(sht::Plan &p, const void *grid, void *spec, int batch, sht::Op op, cudaStream_t s);
+
 // Bytes of one [batch][mmax+1][npairs][2] complex intermediate.
 size_t inter_bytes(const sht::Plan &p, int batch, int mode)
 {
+    if (mode == SHT_TC_BF16X3 && batch > sht::tc_max_batch()) batch = sht::tc_max_batch();
     return (size_t)batch * (p.mmax + 1) * p.npairs * 4 * elem_size(mode);
+}
+
+// Tensor-core mode scratch: the FP32 intermediate of up to tc_max_batch()
+// fields, then the blocked bf16 data operand.  Both the size and the offset
+// of the data operand depend only on min(batch, tc_max_batch()).
+size_t tc_data_offset(const sht::Plan &p, int batch)
+{
+    if (batch > sht::tc_max_batch()) batch = sht::tc_max_batch();
+    return (inter_bytes(p, batch, SHT_TC_BF16X3) + 255) & ~(size_t)255;
+}
+
+size_t tc_work_bytes(const sht::Plan &p, int batch)
+{
+    const int nb = batch > sht::tc_max_batch() ? sht::tc_max_batch() : batch;
+    return tc_data_offset(p, batch) + sht::tc_data_bytes(p.lmax, p.mmax, p.npairs, p.tc_nchunk_s, nb);
 }
 
 int ensure_work(sht::Plan &p, size_t bytes)
@@ -112,14 +170,35 @@ int prologue(sht_handle h, int batch, int mode, int nptr, const void *const *ptr
     return SHT_OK;
 }
 
+// Tuned kernel shape for (mode, batch), or the defaults.
+sht::TunedShape tuned_shape(const sht::Plan &p, int mode, int batch)
+{
+    const long long key = ((long long)mode << 32) | (unsigned)batch;
+    for (const auto &kv : p.tuned)
+        if (kv.first == key) return kv.second;
+    return sht::TunedShape();
+}
+
+void set_tuned(sht::Plan &p, int mode, int batch, const sht::TunedShape &t)
+{
+    const long long key = ((long long)mode << 32) | (unsigned)batch;
+    for (auto &kv : p.tuned)
+        if (kv.first == key) { kv.second = t; return; }
+    p.tuned.push_back({key, t});
+}
+
+template <typename T> constexpr int mode_of_type() { return sizeof(T) == 8 ? SHT_F64 : SHT_F32; }
+
 // The two directions of the scalar transform, parameterised by precision.
 template <typename T>
 int run_synth(sht::Plan &p, const sht::PlanView<T> &pv, const void *spec, void *grid, int batch, sht::Op op,
               cudaStream_t s)
 {
     T *eo = static_cast<T *>(p.work);
+    const sht::TunedShape ts = tuned_shape(p, mode_of_type<T>(), batch);
     int rc = timed(p, SHT_K_LEGENDRE_SYNTH, s, "legendre synthesis launch", [&] {
-        return sht::launch_legendre_synth<T>(pv, static_cast<const T *>(spec), eo, batch, op, s);
+        return sht::launch_legendre_synth_cfg<T>(pv, static_cast<const T *>(spec), eo, batch, op, ts.synth_lpt,
+                                                 ts.synth_bc, s);
     });
     if (rc) return rc;
     return timed(p, SHT_K_FFT_SYNTH, s, "fft synthesis launch", [&] {
@@ -136,8 +215,10 @@ int run_analys(sht::Plan &p, const sht::PlanView<T> &pv, const void *grid, void 
         return sht::launch_fft_analys<T>(pv, static_cast<const T *>(grid), sd, batch, op, false, s);
     });
     if (rc) return rc;
+    const sht::TunedShape ts = tuned_shape(p, mode_of_type<T>(), batch);
     return timed(p, SHT_K_LEGENDRE_ANALYS, s, "legendre analysis launch", [&] {
-        return sht::launch_legendre_analys<T>(pv, sd, static_cast<T *>(spec), batch, op, s);
+        return sht::launch_legendre_analys_cfg<T>(pv, sd, static_cast<T *>(spec), batch, op, ts.analys_lpt,
+                                                  ts.analys_bc, s);
     });
 }
 
@@ -179,14 +260,28 @@ int run_analys_vec(sht::Plan &p, const sht::PlanView<T> &pv, const void *vt, con
     });
 }
 
+// SHT_F32_AUTO resolves to the path sht_tune found faster for this batch.
+int resolve_mode(const sht::Plan &p, int mode, int batch, bool vector)
+{
+    if (mode != SHT_F32_AUTO) return mode;
+    if (vector) return SHT_F32;
+    return tuned_shape(p, SHT_F32_AUTO, batch).prefer_tc ? SHT_TC_BF16X3 : SHT_F32;
+}
+
 int scalar_s2g(sht_handle h, const void *spec, void *grid, int batch, int mode, void *stream, sht::Op op)
 {
     const void *ptrs[2] = {spec, grid};
     int rc = prologue(h, batch, mode, 2, ptrs);
     if (rc) return rc;
+    mode = resolve_mode(h->p, mode, batch, false);
     if ((rc = ensure_work(h->p, inter_bytes(h->p, batch, mode)))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (mode == SHT_F64) return run_synth<double>(h->p, h->p.view64(), spec, grid, batch, op, s);
+    if (mode == SHT_TC_BF16X3) {
+        if ((rc = ensure_panels(h->p))) return rc;
+        if ((rc = ensure_work(h->p, tc_work_bytes(h->p, batch)))) return rc;
+        return run_synth_tc(h->p, spec, grid, batch, op, s);
+    }
     return run_synth<float>(h->p, h->p.view32(), spec, grid, batch, op, s);
 }
 
@@ -195,9 +290,15 @@ int scalar_g2s(sht_handle h, const void *grid, void *spec, int batch, int mode, 
     const void *ptrs[2] = {grid, spec};
     int rc = prologue(h, batch, mode, 2, ptrs);
     if (rc) return rc;
+    mode = resolve_mode(h->p, mode, batch, false);
     if ((rc = ensure_work(h->p, inter_bytes(h->p, batch, mode)))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (mode == SHT_F64) return run_analys<double>(h->p, h->p.view64(), grid, spec, batch, op, s);
+    if (mode == SHT_TC_BF16X3) {
+        if ((rc = ensure_panels(h->p))) return rc;
+        if ((rc = ensure_work(h->p, tc_work_bytes(h->p, batch)))) return rc;
+        return run_analys_tc(h->p, grid, spec, batch, op, s);
+    }
     return run_analys<float>(h->p, h->p.view32(), grid, spec, batch, op, s);
 }
 
@@ -207,6 +308,8 @@ int vector_s2g(sht_handle h, const void *S, const void *T, void *vt, void *vp, i
     const void *ptrs[4] = {S, T, vt, vp};
     int rc = prologue(h, batch, mode, 4, ptrs);
     if (rc) return rc;
+    mode = resolve_mode(h->p, mode, batch, true);
+    if (mode == SHT_TC_BF16X3) return fail(SHT_EUNSUPPORTED, "vector transforms have no tensor-core mode");
     if ((rc = ensure_work(h->p, 2 * inter_bytes(h->p, batch, mode)))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (mode == SHT_F64) return run_synth_vec<double>(h->p, h->p.view64(), S, T, vt, vp, batch, op, s);
@@ -219,13 +322,59 @@ int vector_g2s(sht_handle h, const void *vt, const void *vp, void *S, void *T, i
     const void *ptrs[4] = {vt, vp, S, T};
     int rc = prologue(h, batch, mode, 4, ptrs);
     if (rc) return rc;
+    mode = resolve_mode(h->p, mode, batch, true);
+    if (mode == SHT_TC_BF16X3) return fail(SHT_EUNSUPPORTED, "vector transforms have no tensor-core mode");
     if ((rc = ensure_work(h->p, 2 * inter_bytes(h->p, batch, mode)))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (mode == SHT_F64) return run_analys_vec<double>(h->p, h->p.view64(), vt, vp, S, T, batch, op, s);
     return run_analys_vec<float>(h->p, h->p.view32(), vt, vp, S, T, batch, op, s);
 }
 
+int run_synth_tc(sht::Plan &p, const void *spec, void *grid, int batch, sht::Op op, cudaStream_t s)
+{
+    const int chunk = sht::tc_max_batch();
+    for (int b0 = 0; b0 < batch; b0 += chunk) {
+        const int nb = batch - b0 < chunk ? batch - b0 : chunk;
+        const float *in = static_cast<const float *>(spec) + (size_t)b0 * p.nlm * 2;
+        float *out = static_cast<float *>(grid) + (size_t)b0 * p.nlat * p.nphi;
+        float *eo = static_cast<float *>(p.work);
+        unsigned char *data = static_cast<unsigned char *>(p.work) + tc_data_offset(p, batch);
+        int rc = timed(p, SHT_K_TC_SYNTH, s, "tensor-core synthesis launch", [&] {
+            return sht::launch_tc_legendre(true, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_s, p.d_off_s, p.d_dchunk,
+                                           data, in, eo, nb, op, p.d_err, s);
+        });
+        if (rc) return rc;
+        rc = timed(p, SHT_K_FFT_SYNTH, s, "fft synthesis launch",
+                   [&] { return sht::launch_fft_synth<float>(p.view32(), eo, out, nb, op, s); });
+        if (rc) return rc;
+    }
+    return SHT_OK;
+}
+
+int run_analys_tc(sht::Plan &p, const void *grid, void *spec, int batch, sht::Op op, cudaStream_t s)
+{
+    const int chunk = sht::tc_max_batch();
+    for (int b0 = 0; b0 < batch; b0 += chunk) {
+        const int nb = batch - b0 < chunk ? batch - b0 : chunk;
+        const float *in = static_cast<const float *>(grid) + (size_t)b0 * p.nlat * p.nphi;
+        float *out = static_cast<float *>(spec) + (size_t)b0 * p.nlm * 2;
+        float *sd = static_cast<float *>(p.work);
+        unsigned char *data = static_cast<unsigned char *>(p.work) + tc_data_offset(p, batch);
+        int rc = timed(p, SHT_K_FFT_ANALYS, s, "fft analysis launch",
+                       [&] { return sht::launch_fft_analys<float>(p.view32(), in, sd, nb, op, false, s); });
+        if (rc) return rc;
+        rc = timed(p, SHT_K_TC_ANALYS, s, "tensor-core analysis launch", [&] {
+            return sht::launch_tc_legendre(false, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_a, p.d_off_a, p.d_dchunk,
+                                           data, sd, out, nb, op, p.d_err, s);
+        });
+        if (rc) return rc;
+    }
+    return SHT_OK;
+}
+
 }  // namespace
+
+int sht::set_error(int code, const std::string &msg) { return fail(code, msg); }
 
 extern "C" {
 
@@ -271,6 +420,10 @@ int sht_reserve(sht_handle h, int batch, int mode)
     if (rc) return rc;
     if ((rc = check_mode(mode))) return rc;
     if (batch < 1) return fail(SHT_EINVAL, "batch must be >= 1");
+    if (mode == SHT_TC_BF16X3) {
+        if ((rc = ensure_panels(h->p))) return rc;
+        return ensure_work(h->p, tc_work_bytes(h->p, batch));
+    }
     return ensure_work(h->p, 2 * inter_bytes(h->p, batch, mode));
 }
 
@@ -340,6 +493,16 @@ int sht_gauss(sht_handle h, double *x, double *w)
     return SHT_OK;
 }
 
+int sht_selftest_timeout(sht_handle h, int timeout_us, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (timeout_us < 1 || timeout_us > 2000000) return fail(SHT_EINVAL, "timeout_us must be in [1, 2e6]");
+    return launched(sht::launch_selftest_timeout(h->p.d_err, (unsigned long long)timeout_us * 1000ull,
+                                                 static_cast<cudaStream_t>(stream)),
+                    "self-test launch");
+}
+
 int sht_profile(sht_handle h, int enable)
 {
     if (!h) return fail(SHT_EINVAL, "null handle");
@@ -374,7 +537,8 @@ int sht_profile_read(sht_handle h, double *ms, int *count, int cap)
 const char *sht_kernel_name(int kind)
 {
     static const char *names[SHT_NKERNELS] = {"legendre_synth", "legendre_analys", "legendre_synth_vec",
-                                              "legendre_analys_vec", "fft_synth", "fft_analys"};
+                                              "legendre_analys_vec", "fft_synth",       "fft_analys",
+                                              "tc_synth",       "tc_analys"};
     if (kind < 0 || kind >= SHT_NKERNELS) return "";
     return names[kind];
 }
@@ -386,10 +550,121 @@ int sht_sync_status(sht_handle h, void *stream)
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return fail(SHT_ECUDA, std::string("CUDA error: ") + cudaGetErrorString(e));
+    int code = 0;
+    e = cudaMemcpy(&code, h->p.d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(SHT_ECUDA, std::string("reading the error word: ") + cudaGetErrorString(e));
+    if (code != 0) {
+        cudaMemset(h->p.d_err, 0, sizeof(int));
+        return fail(SHT_ETIMEOUT, "a tensor-core kernel gave up waiting for its copies or MMAs");
+    }
     return SHT_OK;
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// sht_tune: time candidate shapes / paths and keep the fastest.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename F>
+double time_ms(F &&launch, cudaStream_t s, int reps, bool &ok)
+{
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    ok = launch() == cudaSuccess;  // warm-up
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < reps && ok; ++i) ok = launch() == cudaSuccess;
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (ok) ok = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ok ? ms / reps : 1e30;
+}
+
+}  // namespace
+
+extern "C" int sht_tune(sht_handle h, int batch, int mode, double *report, void *stream)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if ((rc = check_mode(mode))) return rc;
+    if (mode == SHT_TC_BF16X3) return fail(SHT_EINVAL, "tune SHT_F64, SHT_F32 or SHT_F32_AUTO");
+    if (batch < 1) return fail(SHT_EINVAL, "batch must be >= 1");
+    sht::Plan &p = h->p;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int shape_mode = mode == SHT_F64 ? SHT_F64 : SHT_F32;
+    const size_t es = elem_size(shape_mode);
+    void *spec = nullptr, *grid = nullptr;
+    cudaError_t e = cudaMalloc(&spec, (size_t)batch * p.nlm * 2 * es);
+    if (e == cudaSuccess) e = cudaMalloc(&grid, (size_t)batch * p.nlat * p.nphi * es);
+    if (e == cudaSuccess) e = cudaMemsetAsync(spec, 0, (size_t)batch * p.nlm * 2 * es, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grid, 0, (size_t)batch * p.nlat * p.nphi * es, s);
+    if (e != cudaSuccess) {
+        cudaFree(spec);
+        cudaFree(grid);
+        return fail(SHT_ENOMEM, "sht_tune: allocating test buffers failed");
+    }
+    if ((rc = ensure_work(p, inter_bytes(p, batch, shape_mode)))) { cudaFree(spec); cudaFree(grid); return rc; }
+    sht::TunedShape best;
+    double best_syn = 1e30, best_ana = 1e30;
+    const int reps = 3;
+    const int lpts_s[3] = {1, 2, 4}, bcs_s[3] = {1, 2, 4};
+    for (int li = 0; li < 3; ++li)
+        for (int bi = 0; bi < 3; ++bi) {
+            const int lpt = lpts_s[li], bc = bcs_s[bi];
+            if (bc > batch && bc > 1) continue;
+            bool ok = false;
+            double ms;
+            if (shape_mode == SHT_F64)
+                ms = time_ms([&] { return sht::launch_legendre_synth_cfg<double>(p.view64(), (const double *)spec, (double *)p.work, batch, sht::OP_SYNTH, lpt, bc, s); }, s, reps, ok);
+            else
+                ms = time_ms([&] { return sht::launch_legendre_synth_cfg<float>(p.view32(), (const float *)spec, (float *)p.work, batch, sht::OP_SYNTH, lpt, bc, s); }, s, reps, ok);
+            if (ok && ms < best_syn) { best_syn = ms; best.synth_lpt = lpt; best.synth_bc = bc; }
+        }
+    const int lpts_a[3] = {2, 4, 8}, bcs_a[2] = {1, 2};
+    for (int li = 0; li < 3; ++li)
+        for (int bi = 0; bi < 2; ++bi) {
+            const int lpt = lpts_a[li], bc = bcs_a[bi];
+            if (bc > batch && bc > 1) continue;
+            if ((p.npairs + 32 * lpt - 1) / (32 * lpt) > 8) continue;
+            bool ok = false;
+            double ms;
+            if (shape_mode == SHT_F64)
+                ms = time_ms([&] { return sht::launch_legendre_analys_cfg<double>(p.view64(), (const double *)p.work, (double *)spec, batch, sht::OP_ANALYS, lpt, bc, s); }, s, reps, ok);
+            else
+                ms = time_ms([&] { return sht::launch_legendre_analys_cfg<float>(p.view32(), (const float *)p.work, (float *)spec, batch, sht::OP_ANALYS, lpt, bc, s); }, s, reps, ok);
+            if (ok && ms < best_ana) { best_ana = ms; best.analys_lpt = lpt; best.analys_bc = bc; }
+        }
+    cudaGetLastError();
+    set_tuned(p, shape_mode, batch, best);
+    if (report) { report[0] = best_syn; report[1] = best_ana; }
+    if (mode == SHT_F32_AUTO) {
+        // the paper's choice: on-the-fly recurrence (FP32 cores) vs precomputed P (tensor cores)
+        bool ok1 = false, ok2 = false;
+        const double ms_f32 = time_ms([&] {
+            if (scalar_s2g(h, spec, grid, batch, SHT_F32, s, sht::OP_SYNTH)) return cudaErrorUnknown;
+            return scalar_g2s(h, grid, spec, batch, SHT_F32, s, sht::OP_ANALYS) ? cudaErrorUnknown : cudaSuccess;
+        }, s, reps, ok1);
+        double ms_tc = 1e30;
+        if (ensure_panels(p) == SHT_OK) {
+            ms_tc = time_ms([&] {
+                if (scalar_s2g(h, spec, grid, batch, SHT_TC_BF16X3, s, sht::OP_SYNTH)) return cudaErrorUnknown;
+                return scalar_g2s(h, grid, spec, batch, SHT_TC_BF16X3, s, sht::OP_ANALYS) ? cudaErrorUnknown : cudaSuccess;
+            }, s, reps, ok2);
+        }
+        sht::TunedShape a = best;
+        a.prefer_tc = ok2 && ms_tc < ms_f32;
+        set_tuned(p, SHT_F32_AUTO, batch, a);
+        if (report) { report[0] = ok1 ? ms_f32 : -1.0; report[1] = ok2 ? ms_tc : -1.0; }
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(spec);
+    cudaFree(grid);
+    return SHT_OK;
+}
 
 // ---------------------------------------------------------------------------
 // sht_synth_static: the scalar synthesis with its intermediate in a fixed

@@ -181,19 +181,19 @@ __device__ __forceinline__ void fill_wtab(T2 *wtab, const T2 *__restrict__ tw, i
 // Synthesis: EO [batch][mmax+1][npairs][2] -> grid [batch][nlat][nphi]
 // blockDim = R * TPR with TPR = max(1, H/16) threads per row, R = 2G rows.
 // ---------------------------------------------------------------------------
+// One tile (field b, pairs p0 .. p0+G-1) of the synthesis FFT, run by the
+// whole CTA (blockDim.x >= 2 G max(1, H/16)); smem_raw holds the twiddle table
+// and the 2G padded rows.
 template <typename T>
-__global__ void __launch_bounds__(512)
-k_fft_synth(PlanView<T> pv, const T *__restrict__ eo, T *__restrict__ grid, int G, int logH, int op)
+__device__ __forceinline__ void fft_synth_tile(const PlanView<T> &pv, const T *__restrict__ eo, T *__restrict__ grid,
+                                               int b, int p0, int G, int logH, int op, unsigned char *smem_raw)
 {
     using T2 = typename Vec2<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int H = 1 << logH, R = 2 * G;
     const int TPR = H >= 16 ? H / 16 : 1;
     const int ld = padi(H) + 1;
     T2 *wtab = reinterpret_cast<T2 *>(smem_raw);
     T2 *buf = wtab + H;
-    const int b = blockIdx.y;
-    const int p0 = blockIdx.x * G;
     const int mmax = pv.mmax, npairs = pv.npairs, nlat = pv.nlat;
     const T2 *eo2 = reinterpret_cast<const T2 *>(eo);
 
@@ -276,22 +276,29 @@ k_fft_synth(PlanView<T> pv, const T *__restrict__ eo, T *__restrict__ grid, int 
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_fft_synth(PlanView<T> pv, const T *__restrict__ eo, T *__restrict__ grid, int G, int logH, int op)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fft_synth_tile<T>(pv, eo, grid, blockIdx.y, blockIdx.x * G, G, logH, op, smem_raw);
+}
+
 // ---------------------------------------------------------------------------
 // Analysis: grid [batch][nlat][nphi] -> SD [batch][mmax+1][npairs][2]
 // ---------------------------------------------------------------------------
+// One tile (field b, pairs p0 .. p0+G-1) of the analysis FFT (see fft_synth_tile).
 template <typename T>
-__global__ void __launch_bounds__(512)
-k_fft_analys(PlanView<T> pv, const T *__restrict__ grid, T *__restrict__ sd, int G, int logH, int op, int vector)
+__device__ __forceinline__ void fft_analys_tile(const PlanView<T> &pv, const T *__restrict__ grid, T *__restrict__ sd,
+                                                int b, int p0, int G, int logH, int op, int vector,
+                                                unsigned char *smem_raw)
 {
     using T2 = typename Vec2<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int H = 1 << logH, R = 2 * G;
     const int TPR = H >= 16 ? H / 16 : 1;
     const int ld = padi(H) + 1;
     T2 *wtab = reinterpret_cast<T2 *>(smem_raw);
     T2 *buf = wtab + H;
-    const int b = blockIdx.y;
-    const int p0 = blockIdx.x * G;
     const int mmax = pv.mmax, npairs = pv.npairs, nlat = pv.nlat;
 
     fill_wtab(wtab, pv.tw, H);
@@ -370,6 +377,14 @@ k_fft_analys(PlanView<T> pv, const T *__restrict__ grid, T *__restrict__ sd, int
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_fft_analys(PlanView<T> pv, const T *__restrict__ grid, T *__restrict__ sd, int G, int logH, int op, int vector)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fft_analys_tile<T>(pv, grid, sd, blockIdx.y, blockIdx.x * G, G, logH, op, vector, smem_raw);
+}
+
 inline int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 
 // Threads per row and pairs per CTA: TPR = H/16 threads per row (>= 1) and
@@ -426,6 +441,58 @@ cudaError_t launch_fft_analys(const PlanView<T> &pv, const T *grid, T *sd, int b
     if (e != cudaSuccess) return e;
     dim3 gridd((unsigned)((pv.npairs + G - 1) / G), (unsigned)batch);
     k_fft_analys<T><<<gridd, threads, smem, s>>>(pv, grid, sd, G, logH, (int)op, vector ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Persistent FFT kernels for uneven batches (FP32, 256 threads, one field per tile).
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void __launch_bounds__(256) k_batch_fft(int synth, const BatchField *__restrict__ fields,
+                                                   const int4 *__restrict__ tiles, int ntiles, int *counter)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_tile;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        const int4 tl = tiles[t];
+        const BatchField f = fields[tl.x];
+        if (synth) fft_synth_tile<float>(f.pv, f.inter, f.out, 0, tl.y, f.G, f.logH, OP_SYNTH, smem_raw);
+        else fft_analys_tile<float>(f.pv, f.in, f.inter, 0, tl.y, f.G, f.logH, OP_ANALYS, 0, smem_raw);
+    }
+}
+
+}  // namespace
+
+// Pairs per FFT tile for a 256-thread CTA: 2G rows of max(1, H/16) threads.
+int batch_fft_group(int logH, int npairs)
+{
+    const int H = 1 << logH;
+    const int TPR = H >= 16 ? H / 16 : 1;
+    int G = 256 / (2 * TPR);
+    if (G < 1) G = 1;
+    if (G > npairs) G = npairs < 1 ? 1 : npairs;
+    return G;
+}
+
+size_t batch_fft_smem(int logH, int G)
+{
+    const int H = 1 << logH;
+    const size_t row_bytes = (size_t)((H + (H >> 4)) + 1) * sizeof(float2);
+    return (size_t)H * sizeof(float2) + (size_t)2 * G * row_bytes;
+}
+
+cudaError_t batch_fft_prepare(size_t smem) { return set_smem(k_batch_fft, smem); }
+
+cudaError_t launch_batch_fft(bool synth, const BatchField *fields, const int4 *tiles, int ntiles, int *counter,
+                             int ctas, size_t smem, cudaStream_t s)
+{
+    k_batch_fft<<<ctas, 256, smem, s>>>(synth ? 1 : 0, fields, tiles, ntiles, counter);
     return cudaGetLastError();
 }
 

@@ -110,18 +110,18 @@ __device__ __forceinline__ long col_of(int lmax, int m) { return (long)m * (2 * 
 // ---------------------------------------------------------------------------
 // Scalar synthesis.  grid.x = (m, pair block), heaviest m first; grid.y = field chunk.
 // ---------------------------------------------------------------------------
+constexpr int kSynthNch = 128;  // degrees staged per chunk (scalar synthesis)
+
+// One (order m, pair block pb, field chunk b0) tile of the scalar synthesis,
+// run by a whole CTA of NT threads; s_ab[kSynthNch], s_f[kSynthNch * BC] are
+// the CTA's staging buffers.
 template <typename T, int LPT, int BC, int NT>
-__global__ void __launch_bounds__(NT)
-k_synth(PlanView<T> pv, const T *__restrict__ spec, T *__restrict__ eo, int batch, int npb, int op)
+__device__ __forceinline__ void synth_tile(const PlanView<T> &pv, const T *__restrict__ spec, T *__restrict__ eo,
+                                           int batch, int m, int pb, int b0, int op, typename Vec2<T>::type *s_ab,
+                                           typename Vec2<T>::type *s_f)
 {
     using T2 = typename Vec2<T>::type;
-    constexpr int NCH = 128;
-    __shared__ T2 s_ab[NCH];
-    __shared__ T2 s_f[NCH * BC];
-
-    const int m = blockIdx.x / npb;
-    const int pb = blockIdx.x - m * npb;
-    const int b0 = blockIdx.y * BC;
+    constexpr int NCH = kSynthNch;
     const int lmax = pv.lmax, npairs = pv.npairs;
     const int L = lmax - m + 1;
     const long col = col_of(lmax, m);
@@ -244,25 +244,39 @@ k_synth(PlanView<T> pv, const T *__restrict__ spec, T *__restrict__ eo, int batc
     }
 }
 
+template <typename T, int LPT, int BC, int NT>
+__global__ void __launch_bounds__(NT)
+k_synth(PlanView<T> pv, const T *__restrict__ spec, T *__restrict__ eo, int batch, int npb, int op)
+{
+    using T2 = typename Vec2<T>::type;
+    __shared__ T2 s_ab[kSynthNch];
+    __shared__ T2 s_f[kSynthNch * BC];
+    const int m = blockIdx.x / npb;
+    const int pb = blockIdx.x - m * npb;
+    synth_tile<T, LPT, BC, NT>(pv, spec, eo, batch, m, pb, blockIdx.y * BC, op, s_ab, s_f);
+}
+
 // ---------------------------------------------------------------------------
 // Scalar analysis.  grid.x = m (heaviest first), grid.y = field chunk; the CTA
 // covers all latitude pairs (NT * LPT >= npairs).
 // ---------------------------------------------------------------------------
+constexpr int kAnalysNch = 128;  // degrees staged per chunk (scalar analysis)
+
+// One (order m, field chunk b0) tile of the scalar analysis, run by the whole
+// CTA (blockDim.x * LPT >= npairs, at most 8 warps); s_ab[kAnalysNch] and
+// s_red[8 * 32] are the CTA's buffers.
 template <typename T, int LPT, int BC>
-__global__ void __launch_bounds__(256)
-k_analys(PlanView<T> pv, const T *__restrict__ sd, T *__restrict__ spec, int batch, int op)
+__device__ __forceinline__ void analys_tile(const PlanView<T> &pv, const T *__restrict__ sd, T *__restrict__ spec,
+                                            int batch, int m, int b0, int op, typename Vec2<T>::type *s_ab,
+                                            T (*s_red)[32])
 {
     using T2 = typename Vec2<T>::type;
     constexpr int K = 16 / BC;   // degrees per reduction: 2*K*BC = 32 values
-    constexpr int NCH = 128;     // multiple of K
-    __shared__ T2 s_ab[NCH];
-    __shared__ T s_red[8][32];
+    constexpr int NCH = kAnalysNch;  // multiple of K
 
     const int NT = blockDim.x;
     const int nw = NT >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m = blockIdx.x;
-    const int b0 = blockIdx.y * BC;
     const int lmax = pv.lmax, npairs = pv.npairs;
     const int L = lmax - m + 1;
     const long col = col_of(lmax, m);
@@ -353,6 +367,16 @@ k_analys(PlanView<T> pv, const T *__restrict__ sd, T *__restrict__ spec, int bat
             __syncthreads();
         }
     }
+}
+
+template <typename T, int LPT, int BC>
+__global__ void __launch_bounds__(256)
+k_analys(PlanView<T> pv, const T *__restrict__ sd, T *__restrict__ spec, int batch, int op)
+{
+    using T2 = typename Vec2<T>::type;
+    __shared__ T2 s_ab[kAnalysNch];
+    __shared__ T s_red[8][32];
+    analys_tile<T, LPT, BC>(pv, sd, spec, batch, blockIdx.x, blockIdx.y * BC, op, s_ab, s_red);
 }
 
 // ---------------------------------------------------------------------------
@@ -708,24 +732,44 @@ inline int analys_lpt(int npairs) { return npairs <= 64 ? 2 : (npairs <= 1024 ? 
 }  // namespace
 
 template <typename T>
+cudaError_t launch_legendre_synth_cfg(const PlanView<T> &pv, const T *spec, T *eo, int batch, Op op, int lpt, int bc,
+                                      cudaStream_t s)
+{
+    // default shape: 2 pairs per thread, up to 4 fields per CTA
+    if (lpt <= 0) lpt = 2;
+    if (bc <= 0) bc = pick_bc(batch);
+#define SHT_SYN(L, B) if (lpt == L && bc == B) return synth_go<T, L, B>(pv, spec, eo, batch, op, s);
+    SHT_SYN(1, 1) SHT_SYN(1, 2) SHT_SYN(1, 4)
+    SHT_SYN(2, 1) SHT_SYN(2, 2) SHT_SYN(2, 4)
+    SHT_SYN(4, 1) SHT_SYN(4, 2) SHT_SYN(4, 4)
+#undef SHT_SYN
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
 cudaError_t launch_legendre_synth(const PlanView<T> &pv, const T *spec, T *eo, int batch, Op op, cudaStream_t s)
 {
-    switch (pick_bc(batch)) {
-    case 4: return synth_go<T, 2, 4>(pv, spec, eo, batch, op, s);
-    case 2: return synth_go<T, 2, 2>(pv, spec, eo, batch, op, s);
-    default: return synth_go<T, 2, 1>(pv, spec, eo, batch, op, s);
-    }
+    return launch_legendre_synth_cfg<T>(pv, spec, eo, batch, op, 0, 0, s);
+}
+
+template <typename T>
+cudaError_t launch_legendre_analys_cfg(const PlanView<T> &pv, const T *sd, T *spec, int batch, Op op, int lpt, int bc,
+                                       cudaStream_t s)
+{
+    // default shape: LPT from the pair count (<= 8 warps), 2 fields per CTA when batched
+    if (lpt <= 0) lpt = analys_lpt(pv.npairs);
+    if (bc <= 0) bc = batch >= 2 ? 2 : 1;
+    if (analys_warps(pv.npairs, lpt) > 8) return cudaErrorInvalidValue;
+#define SHT_ANA(L, B) if (lpt == L && bc == B) return analys_go<T, L, B>(pv, sd, spec, batch, op, s);
+    SHT_ANA(2, 1) SHT_ANA(2, 2) SHT_ANA(4, 1) SHT_ANA(4, 2) SHT_ANA(8, 1) SHT_ANA(8, 2)
+#undef SHT_ANA
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>
 cudaError_t launch_legendre_analys(const PlanView<T> &pv, const T *sd, T *spec, int batch, Op op, cudaStream_t s)
 {
-    const bool two = batch >= 2;
-    switch (analys_lpt(pv.npairs)) {
-    case 2: return two ? analys_go<T, 2, 2>(pv, sd, spec, batch, op, s) : analys_go<T, 2, 1>(pv, sd, spec, batch, op, s);
-    case 4: return two ? analys_go<T, 4, 2>(pv, sd, spec, batch, op, s) : analys_go<T, 4, 1>(pv, sd, spec, batch, op, s);
-    default: return two ? analys_go<T, 8, 2>(pv, sd, spec, batch, op, s) : analys_go<T, 8, 1>(pv, sd, spec, batch, op, s);
-    }
+    return launch_legendre_analys_cfg<T>(pv, sd, spec, batch, op, 0, 0, s);
 }
 
 template <typename T>
@@ -747,6 +791,65 @@ cudaError_t launch_legendre_analys_vec(const PlanView<T> &pv, const T *sdt, cons
     }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent kernels for uneven batches (FP32, one field per tile).
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void __launch_bounds__(128) k_batch_synth(const BatchField *__restrict__ fields,
+                                                     const int4 *__restrict__ tiles, int ntiles, int *counter)
+{
+    __shared__ float2 s_ab[kSynthNch];
+    __shared__ float2 s_f[kSynthNch];
+    __shared__ int s_tile;
+    for (;;) {
+        __syncthreads();  // the previous tile is done with the shared buffers
+        if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        const int4 tl = tiles[t];
+        const BatchField f = fields[tl.x];
+        synth_tile<float, 2, 1, 128>(f.pv, f.in, f.inter, 1, tl.y, tl.z, 0, OP_SYNTH, s_ab, s_f);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_batch_analys(const BatchField *__restrict__ fields,
+                                                      const int4 *__restrict__ tiles, int ntiles, int *counter)
+{
+    __shared__ float2 s_ab[kAnalysNch];
+    __shared__ float s_red[8][32];
+    __shared__ int s_tile;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        const int4 tl = tiles[t];
+        const BatchField f = fields[tl.x];
+        analys_tile<float, 2, 1>(f.pv, f.inter, f.out, 1, tl.y, 0, OP_ANALYS, s_ab, s_red);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_batch_legendre(bool synth, const BatchField *fields, const int4 *tiles, int ntiles, int *counter,
+                                  int ctas, cudaStream_t s)
+{
+    if (synth) k_batch_synth<<<ctas, 128, 0, s>>>(fields, tiles, ntiles, counter);
+    else k_batch_analys<<<ctas, 256, 0, s>>>(fields, tiles, ntiles, counter);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_legendre_synth_cfg<double>(const PlanView<double> &, const double *, double *, int, Op,
+                                                       int, int, cudaStream_t);
+template cudaError_t launch_legendre_synth_cfg<float>(const PlanView<float> &, const float *, float *, int, Op, int,
+                                                      int, cudaStream_t);
+template cudaError_t launch_legendre_analys_cfg<double>(const PlanView<double> &, const double *, double *, int, Op,
+                                                        int, int, cudaStream_t);
+template cudaError_t launch_legendre_analys_cfg<float>(const PlanView<float> &, const float *, float *, int, Op, int,
+                                                       int, cudaStream_t);
 template cudaError_t launch_legendre_synth<double>(const PlanView<double> &, const double *, double *, int, Op,
                                                    cudaStream_t);
 template cudaError_t launch_legendre_synth<float>(const PlanView<float> &, const float *, float *, int, Op,

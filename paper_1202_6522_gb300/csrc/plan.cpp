@@ -185,6 +185,7 @@ int plan_build(Plan &p, std::string &err)
     bytes += padded<float2>(nlm) + padded<float>(nlm) + 3 * padded<float>(npairs) +
              padded<float>((size_t)(mmax + 1) * npairs) + padded<int>((size_t)(mmax + 1) * npairs) +
              padded<float2>(H1);
+    bytes += padded<int>(1);
     DevArena ar;
     cudaError_t ce = cudaGetDevice(&p.device);
     if (ce != cudaSuccess) { err = std::string("cudaGetDevice: ") + cudaGetErrorString(ce); return SHT_ECUDA; }
@@ -232,6 +233,8 @@ int plan_build(Plan &p, std::string &err)
     ok &= up(p.t32.pmmk, k32.data(), sizeof(int) * k32.size());
     p.t32.tw = ar.take<float2>(H1);
     ok &= up(p.t32.tw, tw32.data(), sizeof(float) * 2 * H1);
+    p.d_err = ar.take<int>(1);
+    ok &= cudaMemset(p.d_err, 0, sizeof(int)) == cudaSuccess;
     if (!ok) {
         err = "cudaMemcpy of plan tables failed";
         cudaFree(ar.base);
@@ -247,6 +250,13 @@ void plan_free(Plan &p)
     p.timer.pool.clear();
     if (p.tables_base) cudaFree(p.tables_base);
     if (p.work) cudaFree(p.work);
+    if (p.panel_s) cudaFree(p.panel_s);
+    if (p.panel_a) cudaFree(p.panel_a);
+    if (p.d_off_s) cudaFree(p.d_off_s);
+    if (p.d_off_a) cudaFree(p.d_off_a);
+    if (p.d_dchunk) cudaFree(p.d_dchunk);
+    p.panel_s = p.panel_a = nullptr;
+    p.d_off_s = p.d_off_a = p.d_dchunk = nullptr;
     p.tables_base = nullptr;
     p.work = nullptr;
     p.work_bytes = 0;

@@ -61,6 +61,12 @@ enum Op {
     OP_ANALYS_ADJ = 3   // adjoint of analysis (a weighted synthesis of b / c_m)
 };
 
+// Kernel shapes chosen by sht_tune for one (precision, batch).
+struct TunedShape {
+    int synth_lpt = 0, synth_bc = 0, analys_lpt = 0, analys_bc = 0;
+    bool prefer_tc = false;      // SHT_F32_AUTO: the tensor-core path was faster
+};
+
 // Event pairs recorded around kernel launches while profiling is enabled.
 struct KernelTimer {
     bool enabled = false;
@@ -75,10 +81,15 @@ struct Plan {
     Tables<double> t64;
     Tables<float> t32;
     void *tables_base = nullptr;     // single device allocation holding t64 and t32
+    int *d_err = nullptr;            // device error word written by bounded waits
+    unsigned char *panel_s = nullptr, *panel_a = nullptr;   // tensor-core P panels
+    unsigned long long *d_off_s = nullptr, *d_off_a = nullptr, *d_dchunk = nullptr;
+    size_t tc_nchunk_s = 0;          // synthesis data chunks over all orders
     void *work = nullptr;            // scratch (grown on demand)
     size_t work_bytes = 0;
     int device = 0;
     KernelTimer timer;
+    std::vector<std::pair<long long, TunedShape>> tuned;   // key: mode * 2^32 + batch
 
     PlanView<double> view64() const;
     PlanView<float> view32() const;
@@ -96,6 +107,15 @@ cudaError_t launch_legendre_synth(const PlanView<T> &pv, const T *spec, T *eo, i
 template <typename T>
 cudaError_t launch_legendre_analys(const PlanView<T> &pv, const T *sd, T *spec, int batch, Op op,
                                    cudaStream_t s);
+// Explicit kernel shapes (lpt pairs per thread, bc fields per CTA; 0 = default).
+// Synthesis: lpt in {1,2,4}, bc in {1,2,4}; analysis: lpt in {2,4,8}, bc in {1,2}.
+template <typename T>
+cudaError_t launch_legendre_synth_cfg(const PlanView<T> &pv, const T *spec, T *eo, int batch, Op op, int lpt,
+                                      int bc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_legendre_analys_cfg(const PlanView<T> &pv, const T *sd, T *spec, int batch, Op op, int lpt,
+                                       int bc, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_legendre_synth_vec(const PlanView<T> &pv, const T *S, const T *Tc, T *eot,
                                       T *eop, int batch, Op op, cudaStream_t s);
@@ -108,5 +128,46 @@ cudaError_t launch_fft_synth(const PlanView<T> &pv, const T *eo, T *grid, int ba
 template <typename T>
 cudaError_t launch_fft_analys(const PlanView<T> &pv, const T *grid, T *sd, int batch, Op op,
                               bool vector, cudaStream_t s);
+
+// Uneven batches (batch.cu): one field of an uneven batch, as the persistent
+// kernels see it.  FP32 data.
+struct BatchField {
+    PlanView<float> pv;
+    const float *in;   // spectra (synthesis) or grid (analysis)
+    float *out;        // grid (synthesis) or spectra (analysis)
+    float *inter;      // E/O (synthesis) or s/d folds (analysis) of this field
+    int logH, G;       // FFT length log2(nphi/2) and pairs per FFT tile
+};
+
+// Persistent kernels over a tile list: each CTA takes the next tile from
+// *counter (atomicAdd) until the list is exhausted; tiles are int4
+// (field, m or p0, pair block, 0) sorted longest first.
+cudaError_t launch_batch_legendre(bool synth, const BatchField *fields, const int4 *tiles, int ntiles, int *counter,
+                                  int ctas, cudaStream_t s);
+cudaError_t launch_batch_fft(bool synth, const BatchField *fields, const int4 *tiles, int ntiles, int *counter,
+                             int ctas, size_t smem, cudaStream_t s);
+size_t batch_fft_smem(int logH, int G);
+cudaError_t batch_fft_prepare(size_t smem);   // once, outside any stream capture
+
+// Records an error message for sht_last_error and returns `code`.
+int set_error(int code, const std::string &msg);
+int batch_fft_group(int logH, int npairs);
+constexpr int kBatchSynthPairs = 256;   // pairs per synthesis tile (128 threads x 2)
+constexpr int kBatchMaxPairs = 512;     // analysis CTA (256 threads x 2 pairs) limit
+
+// Tensor-core path (tc.cu).
+void tc_panel_layout(int lmax, int mmax, int npairs, std::vector<unsigned long long> &off_s,
+                     std::vector<unsigned long long> &off_a, size_t &bytes_s, size_t &bytes_a,
+                     std::vector<unsigned long long> &dchunk, size_t &nchunk_s);
+size_t tc_data_bytes(int lmax, int mmax, int npairs, size_t nchunk_s, int batch);
+cudaError_t launch_build_panels(const PlanView<double> &pv, const unsigned long long *off_s,
+                                const unsigned long long *off_a, unsigned char *ps, unsigned char *pa,
+                                cudaStream_t st);
+cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
+                               const unsigned long long *off, const unsigned long long *dchunk,
+                               unsigned char *data, const float *in, float *out, int batch, Op op, int *err,
+                               cudaStream_t st);
+int tc_max_batch();
+cudaError_t launch_selftest_timeout(int *err, unsigned long long max_ns, cudaStream_t st);
 
 }  // namespace sht

@@ -27,12 +27,18 @@ class SHT:
     """A Gauss-Legendre spherical harmonic transform plan on one CUDA device."""
 
     def __init__(self, lmax: int, mmax: int | None = None, nlat: int | None = None,
-                 nphi: int | None = None, device=None):
+                 nphi: int | None = None, device=None, fp32_path: str = "f32"):
+        """fp32_path selects how complex64/float32 tensors are transformed:
+        "f32" (FP32 recurrence on the CUDA cores) or "tc" (tensor cores against
+        FP64-built P_n^m panels, split-bf16 products, scalar transforms only)."""
         self.lmax = int(lmax)
         self.mmax = self.lmax if mmax is None else int(mmax)
         self.nlat = self.lmax + 1 if nlat is None else int(nlat)
         self.nphi = max(_next_pow2(2 * self.mmax + 1), 2) if nphi is None else int(nphi)
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        if fp32_path not in ("f32", "tc"):
+            raise ValueError("fp32_path must be 'f32' or 'tc'")
+        self.fp32_mode = C.SHT_TC_BF16X3 if fp32_path == "tc" else C.SHT_F32
         if self.device.type != "cuda":
             raise ValueError("SHT runs on CUDA devices only")
         with torch.cuda.device(self.device):
@@ -59,12 +65,11 @@ class SHT:
     def _stream(self):
         return torch.cuda.current_stream(self.device).cuda_stream
 
-    @staticmethod
-    def _mode_of(t: torch.Tensor) -> int:
+    def _mode_of(self, t: torch.Tensor) -> int:
         if t.dtype in (torch.complex128, torch.float64):
             return C.SHT_F64
         if t.dtype in (torch.complex64, torch.float32):
-            return C.SHT_F32
+            return self.fp32_mode
         raise TypeError(f"unsupported dtype {t.dtype}")
 
     def _check(self, t: torch.Tensor, kind: str) -> torch.Tensor:
@@ -230,3 +235,51 @@ class _AnalysVec(torch.autograd.Function):
             gT = torch.zeros_like(gS)
         gt, gp = sht.analys_vec_adj_(gS, gT)
         return None, gt, gp
+
+
+class UnevenBatch:
+    """Many FP32 scalar fields of different truncations transformed by one
+    graph launch (persistent kernels over a longest-first tile list)."""
+
+    def __init__(self, lmax, nlat=None, nphi=None, device=None, use_graph=True):
+        self.lmax = [int(v) for v in lmax]
+        self.nlat = [l + 1 for l in self.lmax] if nlat is None else [int(v) for v in nlat]
+        self.nphi = ([max(_next_pow2(2 * l + 1), 2) for l in self.lmax] if nphi is None
+                     else [int(v) for v in nphi])
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.use_graph = use_graph
+        with torch.cuda.device(self.device):
+            self._h = C.sht_batch_create(self.lmax, self.nlat, self.nphi)
+        self.nlm = [(l + 1) * (l + 2) // 2 for l in self.lmax]
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            C.sht_batch_destroy(h)
+            self._h = None
+
+    def _stream(self):
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def synth_(self, specs, out=None):
+        """specs: list of complex64 [nlm_f] tensors -> list of float32 [nlat_f, nphi_f]."""
+        specs = [s.contiguous() for s in specs]
+        for s, n in zip(specs, self.nlm):
+            if s.dtype != torch.complex64 or s.numel() != n or s.device != self.device:
+                raise ValueError("each spectrum must be complex64 [nlm_f] on the batch's device")
+        if out is None:
+            out = [torch.empty(la, ph, dtype=torch.float32, device=self.device) for la, ph in zip(self.nlat, self.nphi)]
+        C.sht_batch_synth(self._h, [s.data_ptr() for s in specs], [g.data_ptr() for g in out],
+                          self.use_graph, self._stream())
+        return out
+
+    def analys_(self, grids, out=None):
+        grids = [g.contiguous() for g in grids]
+        for g, la, ph in zip(grids, self.nlat, self.nphi):
+            if g.dtype != torch.float32 or tuple(g.shape) != (la, ph) or g.device != self.device:
+                raise ValueError("each grid must be float32 [nlat_f, nphi_f] on the batch's device")
+        if out is None:
+            out = [torch.empty(n, dtype=torch.complex64, device=self.device) for n in self.nlm]
+        C.sht_batch_analys(self._h, [g.data_ptr() for g in grids], [s.data_ptr() for s in out],
+                           self.use_graph, self._stream())
+        return out

@@ -30,3 +30,13 @@ def fp64_bound(lmax):
     """Normwise tolerance of the FP64 path: 1e-11, the accuracy the method
     reaches for N < 2048 (Sec. 3.5)."""
     return 1e-11
+
+
+def tc_bound(lmax):
+    """Normwise tolerance of the tensor-core path (bf16 hi+lo split of both
+    operands, hi*hi + hi*lo + lo*hi products, FP32 accumulation).  Each product
+    carries a relative error <= 2^-15 (the dropped lo*lo term, 2^-16, plus the
+    two split remainders, 2^-17 each); allowing a factor 4 for cancellation in
+    the Legendre sums gives 2^-13.  The panels come from the FP64 recurrence,
+    so, unlike the FP32 path, this bound does not grow with N."""
+    return 2.0 ** -13

@@ -1,0 +1,119 @@
+"""Parity of the tensor-core mode (SHT_TC_BF16X3) with the FP64 oracle.
+
+The per-order Legendre contraction runs on tcgen05 against P_n^m panels
+built once by the FP64 recurrence; data are FP32.  Cases cover several
+128-row tiles and ragged tails, mmax < lmax, odd nlat, and sampled rows/
+orders of the full N = 1023, batch 16 workload."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1202_6522_gb300 import synthetic
+
+from _util import normwise, tc_bound
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+CASES = [
+    (7, 7, 8, 16, 2),
+    (31, 20, 40, 64, 2),
+    (40, 40, 41, 128, 3),
+    (300, 300, 301, 1024, 1),
+    (255, 255, 256, 512, 16),
+    (100, 100, 101, 256, 40),   # 80 data columns: three 32-column slices
+]
+IDS = [f"N{c[0]}m{c[1]}lat{c[2]}phi{c[3]}b{c[4]}" for c in CASES]
+
+
+@pytest.fixture(scope="module")
+def SHT():
+    from paper_1202_6522_gb300 import build
+    build.build()
+    from paper_1202_6522_gb300 import SHT as cls
+    return cls
+
+
+def _spec(lmax, mmax, batch, seed):
+    return synthetic.spectrum(lmax, mmax, batch=batch, seed=seed).astype(np.complex64).astype(np.complex128)
+
+
+def _grid(nlat, nphi, batch, seed):
+    return synthetic.grid(nlat, nphi, batch=batch, seed=seed).astype(np.float32).astype(np.float64)
+
+
+def _dev(a):
+    return torch.from_numpy(a.astype(np.complex64 if np.iscomplexobj(a) else np.float32)).to(DEV)
+
+
+def _np(t):
+    return t.detach().cpu().numpy().astype(np.complex128 if t.is_complex() else np.float64)
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_tc_synthesis_and_analysis(SHT, case):
+    lmax, mmax, nlat, nphi, batch = case
+    sht = SHT(lmax, mmax, nlat, nphi, fp32_path="tc")
+    a = _spec(lmax, mmax, batch, 0)
+    got = _np(sht.synth_(_dev(a)))
+    assert normwise(got, oracle.synth(lmax, mmax, nlat, nphi, a)) < tc_bound(lmax)
+    g = _grid(nlat, nphi, batch, 1)
+    got = _np(sht.analys_(_dev(g)))
+    assert normwise(got, oracle.analys(lmax, mmax, nlat, nphi, g)) < tc_bound(lmax)
+    assert sht.sync_status() == 0
+
+
+@pytest.mark.parametrize("case", CASES[:4], ids=IDS[:4])
+def test_tc_adjoints(SHT, case):
+    lmax, mmax, nlat, nphi, batch = case
+    sht = SHT(lmax, mmax, nlat, nphi, fp32_path="tc")
+    g = _grid(nlat, nphi, batch, 2)
+    a = _spec(lmax, mmax, batch, 3)
+    assert normwise(_np(sht.synth_adj_(_dev(g))), oracle.synth_adj(lmax, mmax, nlat, nphi, g)) < tc_bound(lmax)
+    assert normwise(_np(sht.analys_adj_(_dev(a))), oracle.analys_adj(lmax, mmax, nlat, nphi, a)) < tc_bound(lmax)
+
+
+def test_tc_full_size_n1023_b16_sampled(SHT):
+    lmax, nlat, nphi, batch = 1023, 1024, 2048, 16
+    sht = SHT(lmax, lmax, nlat, nphi, fp32_path="tc")
+    a = _spec(lmax, lmax, batch, 0)
+    grid = _np(sht.synth_(_dev(a)))
+    rows = [0, 1, 127, 128, 511, 512, 900, 1023]
+    for b in (0, 9, 15):
+        ref = oracle.synth(lmax, lmax, nlat, nphi, a[b], rows=rows)
+        assert normwise(grid[b][rows], ref[rows]) < tc_bound(lmax), b
+    g = _grid(nlat, nphi, batch, 1)
+    spec = _np(sht.analys_(_dev(g)))
+    ms = [0, 1, 127, 300, 1000, 1023]
+    idx = np.concatenate([[oracle.lm_index(lmax, n, m) for n in range(m, lmax + 1)] for m in ms])
+    for b in (0, 15):
+        ref = oracle.analys(lmax, lmax, nlat, nphi, g[b], ms=ms)
+        assert normwise(spec[b][idx], ref[idx]) < tc_bound(lmax), b
+    assert sht.sync_status() == 0
+
+
+def test_tc_round_trip_error_n1023(SHT):
+    """Sec. 3.5 error measures for the tensor-core round trip (stated, bounded)."""
+    lmax = 1023
+    sht = SHT(lmax, lmax, 1024, 2048, fp32_path="tc")
+    Q = synthetic.spectrum(lmax, seed=0, uniform=True).astype(np.complex64)
+    R = _np(sht.analys_(sht.synth_(torch.from_numpy(Q).to(DEV))))
+    emax, erms = oracle.eps_max_rms(R, Q.astype(np.complex128), lmax)
+    assert emax < 4 * tc_bound(lmax) and erms < tc_bound(lmax)
+
+
+def test_tc_deterministic(SHT):
+    sht = SHT(255, 255, 256, 512, fp32_path="tc")
+    a = _dev(_spec(255, 255, 4, 5))
+    g1 = sht.synth_(a)
+    g2 = sht.synth_(a)
+    assert torch.equal(g1, g2)
+
+
+def test_tc_vector_is_unsupported(SHT):
+    from paper_1202_6522_gb300._capi import SHTError
+    sht = SHT(15, 15, 16, 32, fp32_path="tc")
+    S = _dev(_spec(15, 15, 1, 0))
+    with pytest.raises(SHTError):
+        sht.synth_vec_(S, S)
