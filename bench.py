@@ -10,7 +10,7 @@ GFLOP/s; the plain FP64 path is timed on the same workload for the ratio.
 Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas
 (each rank transforms its own batch, no collective): weak scaling.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode f32|f64] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode auto|tc|f32|f64] [--impl ours|reference]
 """
 from __future__ import annotations
 
@@ -54,19 +54,16 @@ def legendre_flops_per_launch(batch, lmax=LMAX, nlat=NLAT):
     return nlm_of(lmax) * npairs * (4.0 + 4.0 * batch)
 
 
-def tc_panel_bytes(lmax=LMAX, nlat=NLAT):
-    """Bytes of the synthesis and analysis P_n^m panel sets (bf16 hi+lo, padded
-    to 128-row x 32-column tiles), as laid out by the library."""
+def tc_algorithmic_bytes(batch, lmax=LMAX, nlat=NLAT):
+    """Bytes one tensor-core Legendre launch must move: every P_n^m(x_j) of one
+    hemisphere as a bf16 hi+lo pair (4 B; the library's tile padding is not
+    counted), the FP32 spectra of the batch and the FP32 E/O (or s/d)
+    intermediate of the batch."""
     npairs = (nlat + 1) // 2
-    T = (npairs + 127) // 128
-    kch = (npairs + 31) // 32
-    bs = ba = 0
-    for m in range(lmax + 1):
-        L = lmax - m + 1
-        Le = (L + 1) // 2
-        bs += T * ((Le + 31) // 32) * 32768
-        ba += ((Le + 127) // 128) * kch * 32768
-    return bs, ba
+    panel = nlm_of(lmax) * npairs * 4
+    spec = batch * nlm_of(lmax) * 8
+    inter = batch * (lmax + 1) * npairs * 16
+    return panel + spec + inter
 
 
 def fp32_alu_peak(sm_mhz):
@@ -242,6 +239,62 @@ def uneven_batch(torch, dev, replays=200):
     return out
 
 
+def vector_config(torch, dev, steps=5):
+    """Spheroidal/toroidal round trip, N = 511 (nlat 512, nphi 1024), 64 shells,
+    FP32 data: round trips (shells) per second on the CUDA-core path ("f32")
+    and on the tensor-core path ("tc")."""
+    from paper_1202_6522_gb300 import SHT, synthetic
+    n, shells = 511, 64
+    S = torch.from_numpy(synthetic.spectrum(n, batch=shells, seed=4, power=1.5).astype("complex64")).to(dev)
+    T = torch.from_numpy(synthetic.spectrum(n, batch=shells, seed=5, power=1.5).astype("complex64")).to(dev)
+    out = {"workload": "vector round trip N=511 nlat=512 nphi=1024, 64 shells, FP32 data"}
+    for path in ("f32", "tc"):
+        sht = SHT(n, n, 512, 1024, device=dev, fp32_path=path)
+        for _ in range(2):
+            sht.analys_vec_(*sht.synth_vec_(S, T))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            sht.analys_vec_(*sht.synth_vec_(S, T))
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[path] = {"ms_per_step": ms, "round_trips_per_s": shells / (ms / 1e3)}
+        del sht
+    return out
+
+
+def differentiable_config(sht, torch, dev, cdt, steps=10):
+    """loss = ||synth(a) - target||^2 and its gradient (through the adjoint
+    kernel) at the bench size: forward + backward steps per second x batch."""
+    from paper_1202_6522_gb300 import synthetic
+    a = torch.from_numpy(synthetic.spectrum(LMAX, batch=BATCH, seed=2)).to(dev, cdt).requires_grad_(True)
+    rdt = torch.float64 if cdt == torch.complex128 else torch.float32
+    tgt = torch.from_numpy(synthetic.grid(NLAT, NPHI, batch=BATCH, seed=2)).to(dev, rdt)
+
+    def step():
+        a.grad = None
+        loss = ((sht.synth(a) - tgt) ** 2).sum()
+        loss.backward()
+        return loss
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": f"loss=||synth(a)-target||^2 + gradient, N={LMAX}, batch {BATCH}",
+            "ms_per_step": ms, "fields_per_s": BATCH / (ms / 1e3)}
+
+
 def round_trip_errors(sht, torch, dev, cdt):
     """Sec. 3.5 error measures of one round trip of uniform [-1, 1] spectra."""
     import numpy as np
@@ -354,24 +407,56 @@ def run_ours(args):
     value = world * BATCH * args.steps / (ms_total / 1e3)
 
     # --- end to end through the public API with pinned host buffers ---
-    host_in = torch.from_numpy(a_np).to(cdt).pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
-    for _ in range(2):
-        d_in = host_in.to(dev, non_blocking=True)
-        host_out.copy_(sht.analys_(sht.synth_(d_in)), non_blocking=True)
+    # Every step uploads its own input from pinned host memory and downloads
+    # its result; uploads, transforms and downloads run on three streams with
+    # double-buffered device tensors, so step k+1's upload and step k-1's
+    # download overlap step k's transforms (as a streaming user would).
+    nbuf = 2
+    host_in = [torch.from_numpy(a_np).to(cdt).pin_memory() for _ in range(nbuf)]
+    host_out = [torch.empty_like(host_in[0]).pin_memory() for _ in range(nbuf)]
+    d_in = [torch.empty_like(host_in[0], device=dev) for _ in range(nbuf)]
+    s_up, s_down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    up_done = [torch.cuda.Event() for _ in range(nbuf)]
+    comp_done = [torch.cuda.Event() for _ in range(nbuf)]
+    down_done = [torch.cuda.Event() for _ in range(nbuf)]
+    d_out = [None] * nbuf
+
+    def e2e_steps(n):
+        for k in range(n):
+            i = k % nbuf
+            with torch.cuda.stream(s_up):
+                s_up.wait_event(comp_done[i])          # buffer i no longer read by step k - nbuf
+                d_in[i].copy_(host_in[i], non_blocking=True)
+                up_done[i].record(s_up)
+            d_in[i].record_stream(stream)
+            stream.wait_event(up_done[i])
+            stream.wait_event(down_done[i])            # d_out[i] of step k - nbuf downloaded
+            r = sht.analys_(sht.synth_(d_in[i]))
+            d_out[i] = r
+            comp_done[i].record(stream)
+            with torch.cuda.stream(s_down):
+                s_down.wait_event(comp_done[i])
+                host_out[i].copy_(r, non_blocking=True)
+                r.record_stream(s_down)                # keep r's memory until the download ran
+                down_done[i].record(s_down)
+
+    e2e_steps(2)
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        d_in = host_in.to(dev, non_blocking=True)
-        host_out.copy_(sht.analys_(sht.synth_(d_in)), non_blocking=True)
+    e2e_steps(args.steps)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    bytes_step = host_in.numel() * host_in.element_size()
+    bytes_step = host_in[0].numel() * host_in[0].element_size()
     e2e = {"value": world * BATCH * args.steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step}
+           "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step,
+           "note": "pinned host buffers, upload/transform/download overlapped across steps on 3 streams"}
 
     errors = round_trip_errors(sht, torch, dev, cdt)
     ubatch = uneven_batch(torch, dev) if (rank == 0 and not args.no_uneven) else None
+    extra = {}
+    if rank == 0 and not args.no_uneven:
+        extra["vector"] = vector_config(torch, dev)
+        extra["differentiable"] = differentiable_config(sht, torch, dev, cdt)
 
     # --- the plain FP64 path on the same workload (the metric's denominator) ---
     fp64 = None
@@ -391,11 +476,7 @@ def run_ours(args):
     sm_max = clk.get("sm_max_mhz") or 2070.0
     if dom_name.startswith("tc_"):
         # the panels stream from HBM once per launch: bytes bound the kernel
-        bs, ba = tc_panel_bytes()
-        npairs = (NLAT + 1) // 2
-        inter = BATCH * (LMAX + 1) * npairs * 16
-        spec_b = BATCH * nlm_of(LMAX) * 8
-        algo = (bs + spec_b + inter) if dom_name == "tc_synth" else (ba + inter + spec_b)
+        algo = tc_algorithmic_bytes(BATCH)
         peaks = read_peaks()
         peak = peaks.get("hbm_gbs", 6800.0) * 1e9
         achieved = algo / (dom_avg / 1e3)
@@ -445,6 +526,7 @@ def run_ours(args):
         line["tuning"] = tune_report
     if ubatch:
         line["uneven_batch"] = ubatch
+    line.update(extra)
     if fp64:
         line["fp64_plain"] = fp64
         line["speedup_vs_fp64_plain"] = value / fp64["round_trips_per_s"]

@@ -78,13 +78,14 @@ enum {
                         * cores against P_n^m panels built once by the FP64 recurrence
                         * (the precomputed-P_n^m variant of Sec. 3.1), each operand split
                         * into bf16 hi + lo and multiplied as hi*hi + hi*lo + lo*hi with
-                        * FP32 accumulation.  Scalar transforms and their adjoints only
-                        * (vector calls return SHT_EUNSUPPORTED).  The panels take
-                        * about 2 (lmax+1)^3 bytes (2.5 GB at lmax = 1023) and are built
-                        * by the first call in this mode or by sht_reserve. */
+                        * FP32 accumulation.  Scalar and vector transforms and their
+                        * adjoints; vector calls add panels of sin(theta) dP/dtheta.
+                        * The panels take about 2 (lmax+1)^3 bytes (2.2 GB at
+                        * lmax = 1023; twice that once a vector call was made) and
+                        * are built by the first call in this mode or by sht_reserve. */
     SHT_F32_AUTO = 3   /* FP32 data: whichever of SHT_F32 and SHT_TC_BF16X3 sht_tune
                         * measured faster for this batch size (SHT_F32 if untuned);
-                        * vector transforms always take SHT_F32. */
+                        * vector transforms take SHT_F32. */
 };
 
 /* Build a plan (Sec. 2.3 nodes/weights, Sec. 3.2 recurrence tables, FFT
@@ -99,7 +100,8 @@ SHT_API int sht_create(int lmax, int mmax, int nlat, int nphi, sht_handle *out);
 SHT_API void sht_destroy(sht_handle h);
 
 /* Pre-allocate scratch for transforms of up to `batch` fields in `mode`, so
- * that later calls at that size allocate nothing. */
+ * that later calls at that size allocate nothing (SHT_TC_BF16X3: scalar and
+ * vector transforms, including the vector panels). */
 SHT_API int sht_reserve(sht_handle h, int batch, int mode);
 
 /* Scalar synthesis, Sec. 2.2: spec [batch][nlm] complex -> grid [batch][nlat][nphi]. */
@@ -157,6 +159,8 @@ SHT_API int sht_sync_status(sht_handle h, void *stream);
  * or a custom pool, and loops where the implicit device synchronisation of
  * cudaMalloc/cudaFree is not acceptable.  The handle itself must have been
  * created beforehand (sht_create allocates the plan tables).
+ *   - Modes SHT_F64 and SHT_F32 (SHT_F32_AUTO runs SHT_F32 here);
+ *     SHT_TC_BF16X3 returns SHT_EUNSUPPORTED, its panels being allocated.
  *   - The fixed array holds SHT_STATIC_SCRATCH_BYTES (16 MiB) on every GPU that
  *     loads this library, until the process exits.  A call needs
  *     batch * (mmax+1) * ceil(nlat/2) * 4 * sizeof(element) bytes (N = 1023 in
@@ -216,13 +220,21 @@ enum {
     SHT_K_LEGENDRE_ANALYS_VEC = 3,
     SHT_K_FFT_SYNTH = 4,
     SHT_K_FFT_ANALYS = 5,
-    SHT_K_TC_SYNTH = 6,
+    SHT_K_TC_SYNTH = 6,      /* data prep + tensor-core contraction */
     SHT_K_TC_ANALYS = 7,
-    SHT_NKERNELS = 8
+    SHT_K_TC_SYNTH_VEC = 8,
+    SHT_K_TC_ANALYS_VEC = 9,
+    SHT_NKERNELS = 10
 };
 SHT_API int sht_profile(sht_handle h, int enable);
 SHT_API int sht_profile_read(sht_handle h, double *ms, int *count, int cap);
 SHT_API const char *sht_kernel_name(int kind);
+
+/* Static polar optimisation of the tensor-core mode (Sec. 3.1): panel chunks
+ * whose values are all below 2^-40 (near the poles at high order) are neither
+ * loaded nor multiplied.  Fractions of the synthesis and analysis panel chunks
+ * skipped, or -1 if the panels are not built yet. */
+SHT_API int sht_tc_polar_skip(sht_handle h, double *synth_frac, double *analys_frac);
 
 /* Failure-detection self-test (no counterpart in the paper): enqueue a kernel
  * that waits, with a bound of timeout_us microseconds, on a barrier that

@@ -55,13 +55,14 @@ SIGNATURES = {
     "sht_batch_analys": ([_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP], _I),
     "sht_tune": ([_VP, _I, _I, ctypes.POINTER(ctypes.c_double), _VP], _I),
     "sht_selftest_timeout": ([_VP, _I, _VP], _I),
+    "sht_tc_polar_skip": ([_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], _I),
     "sht_profile": ([_VP, _I], _I),
     "sht_profile_read": ([_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I), _I], _I),
     "sht_kernel_name": ([_I], ctypes.c_char_p),
     "sht_last_error": ([], ctypes.c_char_p),
 }
 
-SHT_NKERNELS = 8
+SHT_NKERNELS = 10
 
 
 def library_path() -> str:
@@ -215,6 +216,12 @@ def sht_tune(h, batch, mode, stream):
     rep = (ctypes.c_double * 2)()
     check(_call("sht_tune", h, batch, mode, rep, stream))
     return rep[0], rep[1]
+
+
+def sht_tc_polar_skip(h):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    check(_call("sht_tc_polar_skip", h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def sht_selftest_timeout(h, timeout_us, stream):

@@ -77,7 +77,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + [
-            "-cudart", "shared", "-Xlinker", "-rpath," + _cuda_libdir(nvcc)]
+            "-cudart", "shared", "-Xlinker", "-rpath," + _cuda_libdir(nvcc), "-Xlinker", "--no-undefined"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

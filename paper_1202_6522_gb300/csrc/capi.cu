@@ -44,7 +44,19 @@ int check_mode(int mode)
     return SHT_OK;
 }
 
-// Build the tensor-core panels once (allocates about 2 (lmax+1)^3 bytes).
+// Frees whatever ensure_panels / ensure_vec_panels allocated.
+void free_panels(sht::Plan &p)
+{
+    cudaFree(p.panel_s); cudaFree(p.panel_a); cudaFree(p.d_off_s); cudaFree(p.d_off_a); cudaFree(p.d_dchunk);
+    cudaFree(p.d_c0_s); cudaFree(p.d_c0_a);
+    p.panel_s = p.panel_a = nullptr;
+    p.d_off_s = p.d_off_a = p.d_dchunk = nullptr;
+    p.d_c0_s = p.d_c0_a = nullptr;
+}
+
+// Build the tensor-core panels once (allocates about (lmax+1)^3 bytes): the
+// P_n^m panels in both operand layouts, per-order offsets, and the first
+// chunk above the polar threshold of every (m, tile).
 int ensure_panels(sht::Plan &p)
 {
     if (p.panel_s) return SHT_OK;
@@ -52,16 +64,18 @@ int ensure_panels(sht::Plan &p)
     size_t bs = 0, ba = 0, nch = 0;
     sht::tc_panel_layout(p.lmax, p.mmax, p.npairs, off_s, off_a, bs, ba, dchunk, nch);
     const size_t ob = off_s.size() * sizeof(unsigned long long);
+    int T_s = 0, T_a = 0;
+    sht::tc_tile_counts(p.lmax, p.npairs, T_s, T_a);
     cudaError_t e = cudaMalloc(&p.panel_s, bs);
     if (e == cudaSuccess) e = cudaMalloc(&p.panel_a, ba);
     if (e == cudaSuccess) e = cudaMalloc(&p.d_off_s, ob);
     if (e == cudaSuccess) e = cudaMalloc(&p.d_off_a, ob);
     if (e == cudaSuccess) e = cudaMalloc(&p.d_dchunk, ob);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_c0_s, sizeof(int) * (size_t)(p.mmax + 1) * T_s);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_c0_a, sizeof(int) * (size_t)(p.mmax + 1) * T_a);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(p.panel_s); cudaFree(p.panel_a); cudaFree(p.d_off_s); cudaFree(p.d_off_a); cudaFree(p.d_dchunk);
-        p.panel_s = p.panel_a = nullptr;
-        p.d_off_s = p.d_off_a = p.d_dchunk = nullptr;
+        free_panels(p);
         return fail(SHT_ENOMEM, std::string("cudaMalloc(tensor-core panels): ") + cudaGetErrorString(e));
     }
     p.tc_nchunk_s = nch;
@@ -70,13 +84,76 @@ int ensure_panels(sht::Plan &p)
     if (e == cudaSuccess) e = cudaMemcpy(p.d_dchunk, dchunk.data(), ob, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p.panel_s, 0, bs);
     if (e == cudaSuccess) e = cudaMemset(p.panel_a, 0, ba);
-    if (e == cudaSuccess) e = sht::launch_build_panels(p.view64(), p.d_off_s, p.d_off_a, p.panel_s, p.panel_a, 0);
+    if (e == cudaSuccess)
+        e = sht::launch_build_panels(p.view64(), p.d_off_s, p.d_off_a, p.panel_s, p.panel_a, false, 0);
+    // static polar optimisation: first chunk above the threshold per (m, tile)
+    int ts = 0, ta = 0;
+    if (e == cudaSuccess)
+        e = sht::launch_panel_first_live(true, p.lmax, p.mmax, p.npairs, p.d_off_s, p.panel_s, sht::kPolarThreshold,
+                                         p.d_c0_s, ts, 0);
+    if (e == cudaSuccess)
+        e = sht::launch_panel_first_live(false, p.lmax, p.mmax, p.npairs, p.d_off_a, p.panel_a, sht::kPolarThreshold,
+                                         p.d_c0_a, ta, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = sht::tc_polar_stats(p.lmax, p.mmax, p.npairs, p.d_c0_s, p.d_c0_a, p.polar_skip_s, p.polar_skip_a);
     if (e != cudaSuccess) {
-        cudaFree(p.panel_s); cudaFree(p.panel_a); cudaFree(p.d_off_s); cudaFree(p.d_off_a); cudaFree(p.d_dchunk);
-        p.panel_s = p.panel_a = nullptr;
-        p.d_off_s = p.d_off_a = p.d_dchunk = nullptr;
+        free_panels(p);
         return fail(SHT_ECUDA, std::string("building tensor-core panels: ") + cudaGetErrorString(e));
+    }
+    return SHT_OK;
+}
+
+void free_vec_panels(sht::Plan &p)
+{
+    cudaFree(p.dpanel_s); cudaFree(p.dpanel_a); cudaFree(p.d_c0v_s); cudaFree(p.d_c0v_a);
+    p.dpanel_s = p.dpanel_a = nullptr;
+    p.d_c0v_s = p.d_c0v_a = nullptr;
+}
+
+// The sin(theta) dP/dtheta panels of the vector transforms (same layouts and
+// offsets as the P panels) and the first chunk live in either matrix.
+int ensure_vec_panels(sht::Plan &p)
+{
+    int rc = ensure_panels(p);
+    if (rc) return rc;
+    if (p.dpanel_s) return SHT_OK;
+    std::vector<unsigned long long> off_s, off_a, dchunk;
+    size_t bs = 0, ba = 0, nch = 0;
+    sht::tc_panel_layout(p.lmax, p.mmax, p.npairs, off_s, off_a, bs, ba, dchunk, nch);
+    int T_s = 0, T_a = 0;
+    sht::tc_tile_counts(p.lmax, p.npairs, T_s, T_a);
+    const size_t ns = (size_t)(p.mmax + 1) * T_s, na = (size_t)(p.mmax + 1) * T_a;
+    int *tmp = nullptr;
+    cudaError_t e = cudaMalloc(&p.dpanel_s, bs);
+    if (e == cudaSuccess) e = cudaMalloc(&p.dpanel_a, ba);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_c0v_s, sizeof(int) * ns);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_c0v_a, sizeof(int) * na);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, sizeof(int) * (ns > na ? ns : na));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(tmp);
+        free_vec_panels(p);
+        return fail(SHT_ENOMEM, std::string("cudaMalloc(vector tensor-core panels): ") + cudaGetErrorString(e));
+    }
+    e = cudaMemset(p.dpanel_s, 0, bs);
+    if (e == cudaSuccess) e = cudaMemset(p.dpanel_a, 0, ba);
+    if (e == cudaSuccess)
+        e = sht::launch_build_panels(p.view64(), p.d_off_s, p.d_off_a, p.dpanel_s, p.dpanel_a, true, 0);
+    int nt = 0;
+    if (e == cudaSuccess)
+        e = sht::launch_panel_first_live(true, p.lmax, p.mmax, p.npairs, p.d_off_s, p.dpanel_s, sht::kPolarThreshold,
+                                         tmp, nt, 0);
+    if (e == cudaSuccess) e = sht::launch_min_int(p.d_c0_s, tmp, p.d_c0v_s, (int)ns, 0);
+    if (e == cudaSuccess)
+        e = sht::launch_panel_first_live(false, p.lmax, p.mmax, p.npairs, p.d_off_a, p.dpanel_a, sht::kPolarThreshold,
+                                         tmp, nt, 0);
+    if (e == cudaSuccess) e = sht::launch_min_int(p.d_c0_a, tmp, p.d_c0v_a, (int)na, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(tmp);
+    if (e != cudaSuccess) {
+        free_vec_panels(p);
+        return fail(SHT_ECUDA, std::string("building vector tensor-core panels: ") + cudaGetErrorString(e));
     }
     return SHT_OK;
 }
@@ -86,6 +163,10 @@ size_t elem_size(int mode) { return mode == SHT_F64 ? sizeof(double) : sizeof(fl
 // Tensor-core scalar transforms: the Legendre contraction on tcgen05, FFTs in FP32.
 int run_synth_tc(sht::Plan &p, const void *spec, void *grid, int batch, sht::Op op, cudaStream_t s);
 int run_analys_tc(sht::Plan &p, const void *grid, void *spec, int batch, sht::Op op, cudaStream_t s);
+int run_synth_vec_tc(sht::Plan &p, const void *S, const void *T, void *vt, void *vp, int batch, sht::Op op,
+                     cudaStream_t s);
+int run_analys_vec_tc(sht::Plan &p, const void *vt, const void *vp, void *S, void *T, int batch, sht::Op op,
+                      cudaStream_t s);
 
 // Bytes of one [batch][mmax+1][npairs][2] complex intermediate.
 size_t inter_bytes(const sht::Plan &p, int batch, int mode)
@@ -94,19 +175,22 @@ size_t inter_bytes(const sht::Plan &p, int batch, int mode)
     return (size_t)batch * (p.mmax + 1) * p.npairs * 4 * elem_size(mode);
 }
 
-// Tensor-core mode scratch: the FP32 intermediate of up to tc_max_batch()
-// fields, then the blocked bf16 data operand.  Both the size and the offset
-// of the data operand depend only on min(batch, tc_max_batch()).
-size_t tc_data_offset(const sht::Plan &p, int batch)
+// Tensor-core mode scratch: the FP32 intermediate(s) of up to the tensor-core
+// batch limit of fields, then the blocked bf16 data operand.  Size and offset
+// depend only on min(batch, limit) and on whether the transform is a vector one.
+int tc_chunk(bool vec) { return vec ? sht::tc_vec_max_batch() : sht::tc_max_batch(); }
+
+size_t tc_data_offset(const sht::Plan &p, int batch, bool vec)
 {
-    if (batch > sht::tc_max_batch()) batch = sht::tc_max_batch();
-    return (inter_bytes(p, batch, SHT_TC_BF16X3) + 255) & ~(size_t)255;
+    const int nb = batch > tc_chunk(vec) ? tc_chunk(vec) : batch;
+    const size_t inter = (size_t)nb * (p.mmax + 1) * p.npairs * 4 * sizeof(float);
+    return ((vec ? 2 : 1) * inter + 255) & ~(size_t)255;
 }
 
-size_t tc_work_bytes(const sht::Plan &p, int batch)
+size_t tc_work_bytes(const sht::Plan &p, int batch, bool vec)
 {
-    const int nb = batch > sht::tc_max_batch() ? sht::tc_max_batch() : batch;
-    return tc_data_offset(p, batch) + sht::tc_data_bytes(p.lmax, p.mmax, p.npairs, p.tc_nchunk_s, nb);
+    const int nb = batch > tc_chunk(vec) ? tc_chunk(vec) : batch;
+    return tc_data_offset(p, batch, vec) + sht::tc_data_bytes(p.mmax, p.npairs, p.tc_nchunk_s, nb, vec);
 }
 
 int ensure_work(sht::Plan &p, size_t bytes)
@@ -274,14 +358,14 @@ int scalar_s2g(sht_handle h, const void *spec, void *grid, int batch, int mode, 
     int rc = prologue(h, batch, mode, 2, ptrs);
     if (rc) return rc;
     mode = resolve_mode(h->p, mode, batch, false);
-    if ((rc = ensure_work(h->p, inter_bytes(h->p, batch, mode)))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (mode == SHT_F64) return run_synth<double>(h->p, h->p.view64(), spec, grid, batch, op, s);
     if (mode == SHT_TC_BF16X3) {
         if ((rc = ensure_panels(h->p))) return rc;
-        if ((rc = ensure_work(h->p, tc_work_bytes(h->p, batch)))) return rc;
+        if ((rc = ensure_work(h->p, tc_work_bytes(h->p, batch, false)))) return rc;
         return run_synth_tc(h->p, spec, grid, batch, op, s);
     }
+    if ((rc = ensure_work(h->p, inter_bytes(h->p, batch, mode)))) return rc;
+    if (mode == SHT_F64) return run_synth<double>(h->p, h->p.view64(), spec, grid, batch, op, s);
     return run_synth<float>(h->p, h->p.view32(), spec, grid, batch, op, s);
 }
 
@@ -291,14 +375,14 @@ int scalar_g2s(sht_handle h, const void *grid, void *spec, int batch, int mode, 
     int rc = prologue(h, batch, mode, 2, ptrs);
     if (rc) return rc;
     mode = resolve_mode(h->p, mode, batch, false);
-    if ((rc = ensure_work(h->p, inter_bytes(h->p, batch, mode)))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (mode == SHT_F64) return run_analys<double>(h->p, h->p.view64(), grid, spec, batch, op, s);
     if (mode == SHT_TC_BF16X3) {
         if ((rc = ensure_panels(h->p))) return rc;
-        if ((rc = ensure_work(h->p, tc_work_bytes(h->p, batch)))) return rc;
+        if ((rc = ensure_work(h->p, tc_work_bytes(h->p, batch, false)))) return rc;
         return run_analys_tc(h->p, grid, spec, batch, op, s);
     }
+    if ((rc = ensure_work(h->p, inter_bytes(h->p, batch, mode)))) return rc;
+    if (mode == SHT_F64) return run_analys<double>(h->p, h->p.view64(), grid, spec, batch, op, s);
     return run_analys<float>(h->p, h->p.view32(), grid, spec, batch, op, s);
 }
 
@@ -309,9 +393,13 @@ int vector_s2g(sht_handle h, const void *S, const void *T, void *vt, void *vp, i
     int rc = prologue(h, batch, mode, 4, ptrs);
     if (rc) return rc;
     mode = resolve_mode(h->p, mode, batch, true);
-    if (mode == SHT_TC_BF16X3) return fail(SHT_EUNSUPPORTED, "vector transforms have no tensor-core mode");
-    if ((rc = ensure_work(h->p, 2 * inter_bytes(h->p, batch, mode)))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (mode == SHT_TC_BF16X3) {
+        if ((rc = ensure_vec_panels(h->p))) return rc;
+        if ((rc = ensure_work(h->p, tc_work_bytes(h->p, batch, true)))) return rc;
+        return run_synth_vec_tc(h->p, S, T, vt, vp, batch, op, s);
+    }
+    if ((rc = ensure_work(h->p, 2 * inter_bytes(h->p, batch, mode)))) return rc;
     if (mode == SHT_F64) return run_synth_vec<double>(h->p, h->p.view64(), S, T, vt, vp, batch, op, s);
     return run_synth_vec<float>(h->p, h->p.view32(), S, T, vt, vp, batch, op, s);
 }
@@ -323,25 +411,31 @@ int vector_g2s(sht_handle h, const void *vt, const void *vp, void *S, void *T, i
     int rc = prologue(h, batch, mode, 4, ptrs);
     if (rc) return rc;
     mode = resolve_mode(h->p, mode, batch, true);
-    if (mode == SHT_TC_BF16X3) return fail(SHT_EUNSUPPORTED, "vector transforms have no tensor-core mode");
-    if ((rc = ensure_work(h->p, 2 * inter_bytes(h->p, batch, mode)))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (mode == SHT_TC_BF16X3) {
+        if ((rc = ensure_vec_panels(h->p))) return rc;
+        if ((rc = ensure_work(h->p, tc_work_bytes(h->p, batch, true)))) return rc;
+        return run_analys_vec_tc(h->p, vt, vp, S, T, batch, op, s);
+    }
+    if ((rc = ensure_work(h->p, 2 * inter_bytes(h->p, batch, mode)))) return rc;
     if (mode == SHT_F64) return run_analys_vec<double>(h->p, h->p.view64(), vt, vp, S, T, batch, op, s);
     return run_analys_vec<float>(h->p, h->p.view32(), vt, vp, S, T, batch, op, s);
 }
 
+// Tensor-core transforms run in chunks of at most tc_chunk() fields: the
+// contraction (prep + tcgen05 kernel) and the FP32 FFTs of each chunk.
 int run_synth_tc(sht::Plan &p, const void *spec, void *grid, int batch, sht::Op op, cudaStream_t s)
 {
-    const int chunk = sht::tc_max_batch();
+    const int chunk = tc_chunk(false);
+    float *eo = static_cast<float *>(p.work);
+    unsigned char *data = static_cast<unsigned char *>(p.work) + tc_data_offset(p, batch, false);
     for (int b0 = 0; b0 < batch; b0 += chunk) {
         const int nb = batch - b0 < chunk ? batch - b0 : chunk;
         const float *in = static_cast<const float *>(spec) + (size_t)b0 * p.nlm * 2;
         float *out = static_cast<float *>(grid) + (size_t)b0 * p.nlat * p.nphi;
-        float *eo = static_cast<float *>(p.work);
-        unsigned char *data = static_cast<unsigned char *>(p.work) + tc_data_offset(p, batch);
         int rc = timed(p, SHT_K_TC_SYNTH, s, "tensor-core synthesis launch", [&] {
-            return sht::launch_tc_legendre(true, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_s, p.d_off_s, p.d_dchunk,
-                                           data, in, eo, nb, op, p.d_err, s);
+            return sht::launch_tc_legendre(true, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_s, p.d_off_s, p.d_c0_s,
+                                           p.d_dchunk, data, in, eo, nb, op, p.d_err, s);
         });
         if (rc) return rc;
         rc = timed(p, SHT_K_FFT_SYNTH, s, "fft synthesis launch",
@@ -353,19 +447,77 @@ int run_synth_tc(sht::Plan &p, const void *spec, void *grid, int batch, sht::Op 
 
 int run_analys_tc(sht::Plan &p, const void *grid, void *spec, int batch, sht::Op op, cudaStream_t s)
 {
-    const int chunk = sht::tc_max_batch();
+    const int chunk = tc_chunk(false);
+    float *sd = static_cast<float *>(p.work);
+    unsigned char *data = static_cast<unsigned char *>(p.work) + tc_data_offset(p, batch, false);
     for (int b0 = 0; b0 < batch; b0 += chunk) {
         const int nb = batch - b0 < chunk ? batch - b0 : chunk;
         const float *in = static_cast<const float *>(grid) + (size_t)b0 * p.nlat * p.nphi;
         float *out = static_cast<float *>(spec) + (size_t)b0 * p.nlm * 2;
-        float *sd = static_cast<float *>(p.work);
-        unsigned char *data = static_cast<unsigned char *>(p.work) + tc_data_offset(p, batch);
         int rc = timed(p, SHT_K_FFT_ANALYS, s, "fft analysis launch",
                        [&] { return sht::launch_fft_analys<float>(p.view32(), in, sd, nb, op, false, s); });
         if (rc) return rc;
         rc = timed(p, SHT_K_TC_ANALYS, s, "tensor-core analysis launch", [&] {
-            return sht::launch_tc_legendre(false, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_a, p.d_off_a, p.d_dchunk,
-                                           data, sd, out, nb, op, p.d_err, s);
+            return sht::launch_tc_legendre(false, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_a, p.d_off_a, p.d_c0_a,
+                                           p.d_dchunk, data, sd, out, nb, op, p.d_err, s);
+        });
+        if (rc) return rc;
+    }
+    return SHT_OK;
+}
+
+int run_synth_vec_tc(sht::Plan &p, const void *S, const void *T, void *vt, void *vp, int batch, sht::Op op,
+                     cudaStream_t s)
+{
+    const int chunk = tc_chunk(true);
+    const size_t inter = (size_t)(batch < chunk ? batch : chunk) * (p.mmax + 1) * p.npairs * 4;
+    float *eot = static_cast<float *>(p.work);
+    float *eop = eot + inter;
+    unsigned char *data = static_cast<unsigned char *>(p.work) + tc_data_offset(p, batch, true);
+    for (int b0 = 0; b0 < batch; b0 += chunk) {
+        const int nb = batch - b0 < chunk ? batch - b0 : chunk;
+        const size_t so = (size_t)b0 * p.nlm * 2, go = (size_t)b0 * p.nlat * p.nphi;
+        int rc = timed(p, SHT_K_TC_SYNTH_VEC, s, "tensor-core vector synthesis launch", [&] {
+            return sht::launch_tc_vec(true, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_s, p.dpanel_s, p.d_off_s,
+                                      p.d_c0v_s, p.d_dchunk, data, static_cast<const float *>(S) + so,
+                                      static_cast<const float *>(T) + so, eot, eop, p.t32.st, nb, op, p.d_err, s);
+        });
+        if (rc) return rc;
+        rc = timed(p, SHT_K_FFT_SYNTH, s, "fft synthesis launch", [&] {
+            return sht::launch_fft_synth<float>(p.view32(), eot, static_cast<float *>(vt) + go, nb, op, s);
+        });
+        if (rc) return rc;
+        rc = timed(p, SHT_K_FFT_SYNTH, s, "fft synthesis launch", [&] {
+            return sht::launch_fft_synth<float>(p.view32(), eop, static_cast<float *>(vp) + go, nb, op, s);
+        });
+        if (rc) return rc;
+    }
+    return SHT_OK;
+}
+
+int run_analys_vec_tc(sht::Plan &p, const void *vt, const void *vp, void *S, void *T, int batch, sht::Op op,
+                      cudaStream_t s)
+{
+    const int chunk = tc_chunk(true);
+    const size_t inter = (size_t)(batch < chunk ? batch : chunk) * (p.mmax + 1) * p.npairs * 4;
+    float *sdt = static_cast<float *>(p.work);
+    float *sdp = sdt + inter;
+    unsigned char *data = static_cast<unsigned char *>(p.work) + tc_data_offset(p, batch, true);
+    for (int b0 = 0; b0 < batch; b0 += chunk) {
+        const int nb = batch - b0 < chunk ? batch - b0 : chunk;
+        const size_t so = (size_t)b0 * p.nlm * 2, go = (size_t)b0 * p.nlat * p.nphi;
+        int rc = timed(p, SHT_K_FFT_ANALYS, s, "fft analysis launch", [&] {
+            return sht::launch_fft_analys<float>(p.view32(), static_cast<const float *>(vt) + go, sdt, nb, op, true, s);
+        });
+        if (rc) return rc;
+        rc = timed(p, SHT_K_FFT_ANALYS, s, "fft analysis launch", [&] {
+            return sht::launch_fft_analys<float>(p.view32(), static_cast<const float *>(vp) + go, sdp, nb, op, true, s);
+        });
+        if (rc) return rc;
+        rc = timed(p, SHT_K_TC_ANALYS_VEC, s, "tensor-core vector analysis launch", [&] {
+            return sht::launch_tc_vec(false, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_a, p.dpanel_a, p.d_off_a,
+                                      p.d_c0v_a, p.d_dchunk, data, sdt, sdp, static_cast<float *>(S) + so,
+                                      static_cast<float *>(T) + so, p.t32.st, nb, op, p.d_err, s);
         });
         if (rc) return rc;
     }
@@ -421,8 +573,9 @@ int sht_reserve(sht_handle h, int batch, int mode)
     if ((rc = check_mode(mode))) return rc;
     if (batch < 1) return fail(SHT_EINVAL, "batch must be >= 1");
     if (mode == SHT_TC_BF16X3) {
-        if ((rc = ensure_panels(h->p))) return rc;
-        return ensure_work(h->p, tc_work_bytes(h->p, batch));
+        if ((rc = ensure_vec_panels(h->p))) return rc;
+        const size_t a = tc_work_bytes(h->p, batch, false), b = tc_work_bytes(h->p, batch, true);
+        return ensure_work(h->p, a > b ? a : b);
     }
     return ensure_work(h->p, 2 * inter_bytes(h->p, batch, mode));
 }
@@ -493,6 +646,15 @@ int sht_gauss(sht_handle h, double *x, double *w)
     return SHT_OK;
 }
 
+int sht_tc_polar_skip(sht_handle h, double *synth_frac, double *analys_frac)
+{
+    if (!h) return fail(SHT_EINVAL, "null handle");
+    if (!synth_frac || !analys_frac) return fail(SHT_EINVAL, "null output pointer");
+    *synth_frac = h->p.panel_s ? h->p.polar_skip_s : -1.0;
+    *analys_frac = h->p.panel_s ? h->p.polar_skip_a : -1.0;
+    return SHT_OK;
+}
+
 int sht_selftest_timeout(sht_handle h, int timeout_us, void *stream)
 {
     int rc = check_handle(h);
@@ -538,7 +700,8 @@ const char *sht_kernel_name(int kind)
 {
     static const char *names[SHT_NKERNELS] = {"legendre_synth", "legendre_analys", "legendre_synth_vec",
                                               "legendre_analys_vec", "fft_synth",       "fft_analys",
-                                              "tc_synth",       "tc_analys"};
+                                              "tc_synth",       "tc_analys",          "tc_synth_vec",
+                                              "tc_analys_vec"};
     if (kind < 0 || kind >= SHT_NKERNELS) return "";
     return names[kind];
 }
@@ -705,6 +868,8 @@ extern "C" int sht_synth_static(sht_handle h, const void *spec, void *grid, int 
     const void *ptrs[2] = {spec, grid};
     int rc = prologue(h, batch, mode, 2, ptrs);
     if (rc) return rc;
+    if (mode == SHT_TC_BF16X3)
+        return fail(SHT_EUNSUPPORTED, "sht_synth_static: the tensor-core mode needs panels allocated by the handle");
     const size_t need = inter_bytes(h->p, batch, mode);
     if (need > (size_t)SHT_STATIC_SCRATCH_BYTES)
         return fail(SHT_EINVAL, "sht_synth_static: this call needs " + std::to_string(need) +

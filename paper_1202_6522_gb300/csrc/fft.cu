@@ -388,7 +388,9 @@ k_fft_analys(PlanView<T> pv, const T *__restrict__ grid, T *__restrict__ sd, int
 inline int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 
 // Threads per row and pairs per CTA: TPR = H/16 threads per row (>= 1) and
-// enough rows for >= 256 threads, capped so the CTA's buffer stays <= 96 KB.
+// enough rows for 256 threads, capped so the CTA's buffer stays <= 96 KB.
+// (512-thread CTAs read the intermediate in longer runs but fit one CTA per
+// SM and measured slower: the kernel is latency-bound, not DRAM-bound.)
 template <typename T>
 void fft_shape(int H, int npairs, int &G, int &threads, size_t &smem)
 {

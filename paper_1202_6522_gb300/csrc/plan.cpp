@@ -31,8 +31,11 @@ void legendre_pair(int n, double x, double &pn, double &pn1)
 }
 
 // Nodes of the nlat-point Gauss-Legendre rule, largest first, and weights
-// w = 2 (1 - x^2) / (n P_{n-1}(x))^2.  Newton on P_n started from Tricomi's
-// asymptotic estimate.
+// w = 2 / ((1 - x^2) P_n'(x)^2) with (1 - x^2) P_n' = n (P_{n-1} - x P_n).
+// Keeping the -x P_n term (zero at the exact root) cancels the first-order
+// effect of rounding the node to a double, which near the poles would
+// otherwise be amplified by ~ 2(n+1)/(1 - x^2).  Newton on P_n started from
+// Tricomi's asymptotic estimate.
 void gauss_nodes(int n, std::vector<double> &x, std::vector<double> &w)
 {
     x.assign(n, 0.0);
@@ -49,8 +52,9 @@ void gauss_nodes(int n, std::vector<double> &x, std::vector<double> &w)
             if (std::fabs(dz) <= 2e-16 * std::fabs(z) + 1e-300 && it > 2) break;
         }
         legendre_pair(n, z, pn, pn1);
-        double omx2 = (1.0 - z) * (1.0 + z);
-        double wt = 2.0 * omx2 / ((n * pn1) * (n * pn1));
+        const double omx2 = (1.0 - z) * (1.0 + z);
+        const double q = n * (pn1 - z * pn);   // (1 - x^2) P_n'(x)
+        const double wt = 2.0 * omx2 / (q * q);
         if (n % 2 == 1 && i == n / 2) z = 0.0;  // the equatorial node
         x[i] = z;
         x[n - 1 - i] = -z;
@@ -255,8 +259,15 @@ void plan_free(Plan &p)
     if (p.d_off_s) cudaFree(p.d_off_s);
     if (p.d_off_a) cudaFree(p.d_off_a);
     if (p.d_dchunk) cudaFree(p.d_dchunk);
-    p.panel_s = p.panel_a = nullptr;
+    if (p.d_c0_s) cudaFree(p.d_c0_s);
+    if (p.d_c0_a) cudaFree(p.d_c0_a);
+    if (p.dpanel_s) cudaFree(p.dpanel_s);
+    if (p.dpanel_a) cudaFree(p.dpanel_a);
+    if (p.d_c0v_s) cudaFree(p.d_c0v_s);
+    if (p.d_c0v_a) cudaFree(p.d_c0v_a);
+    p.panel_s = p.panel_a = p.dpanel_s = p.dpanel_a = nullptr;
     p.d_off_s = p.d_off_a = p.d_dchunk = nullptr;
+    p.d_c0_s = p.d_c0_a = p.d_c0v_s = p.d_c0v_a = nullptr;
     p.tables_base = nullptr;
     p.work = nullptr;
     p.work_bytes = 0;

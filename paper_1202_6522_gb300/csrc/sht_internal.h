@@ -84,7 +84,11 @@ struct Plan {
     int *d_err = nullptr;            // device error word written by bounded waits
     unsigned char *panel_s = nullptr, *panel_a = nullptr;   // tensor-core P panels
     unsigned long long *d_off_s = nullptr, *d_off_a = nullptr, *d_dchunk = nullptr;
-    size_t tc_nchunk_s = 0;          // synthesis data chunks over all orders
+    size_t tc_nchunk_s = 0;                     // synthesis data chunks over all orders
+    int *d_c0_s = nullptr, *d_c0_a = nullptr;   // first live chunk per (m, tile)
+    double polar_skip_s = 0, polar_skip_a = 0;  // fraction of panel chunks skipped
+    unsigned char *dpanel_s = nullptr, *dpanel_a = nullptr; // sin(theta) dP/dtheta panels (vector)
+    int *d_c0v_s = nullptr, *d_c0v_a = nullptr; // first chunk live in P or dP
     void *work = nullptr;            // scratch (grown on demand)
     size_t work_bytes = 0;
     int device = 0;
@@ -156,17 +160,39 @@ constexpr int kBatchSynthPairs = 256;   // pairs per synthesis tile (128 threads
 constexpr int kBatchMaxPairs = 512;     // analysis CTA (256 threads x 2 pairs) limit
 
 // Tensor-core path (tc.cu).
+// Panel byte offsets per order (synthesis and analysis layouts), their total
+// sizes, and the first synthesis data chunk of each order.
 void tc_panel_layout(int lmax, int mmax, int npairs, std::vector<unsigned long long> &off_s,
                      std::vector<unsigned long long> &off_a, size_t &bytes_s, size_t &bytes_a,
                      std::vector<unsigned long long> &dchunk, size_t &nchunk_s);
-size_t tc_data_bytes(int lmax, int mmax, int npairs, size_t nchunk_s, int batch);
+// Bytes of the blocked data operand (either layout) for `batch` fields.
+size_t tc_data_bytes(int mmax, int npairs, size_t nchunk_s, int batch, bool vec);
+// deriv: build sin(theta) dP/dtheta instead of P.
 cudaError_t launch_build_panels(const PlanView<double> &pv, const unsigned long long *off_s,
-                                const unsigned long long *off_a, unsigned char *ps, unsigned char *pa,
+                                const unsigned long long *off_a, unsigned char *ps, unsigned char *pa, bool deriv,
                                 cudaStream_t st);
+// Scalar contraction of <= tc_max_batch() fields: prep kernel (FP32 -> blocked
+// bf16 hi/lo in `data`) then the tcgen05 kernel.  Synthesis: spectra -> E/O;
+// analysis: s/d folds -> spectra.
 cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
-                               const unsigned long long *off, const unsigned long long *dchunk,
+                               const unsigned long long *off, const int *c0, const unsigned long long *dchunk,
                                unsigned char *data, const float *in, float *out, int batch, Op op, int *err,
                                cudaStream_t st);
+// Vector contraction of <= tc_vec_max_batch() fields.  Synthesis: (S, T) ->
+// (theta E/O, phi E/O); analysis: (theta, phi) folds -> (S, T).
+cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
+                          const unsigned char *dpanel, const unsigned long long *off, const int *c0,
+                          const unsigned long long *dchunk, unsigned char *data, const float *in0, const float *in1,
+                          float *out0, float *out1, const float *st_pairs, int batch, Op op, int *err, cudaStream_t st);
+cudaError_t launch_min_int(const int *a, const int *b, int *out, int n, cudaStream_t st);
+int tc_vec_max_batch();
+// Static polar optimisation: per (m, tile) first chunk with a panel value >= thr.
+cudaError_t launch_panel_first_live(bool synth, int lmax, int mmax, int npairs, const unsigned long long *off,
+                                    const unsigned char *panel, float thr, int *c0, int &ntiles, cudaStream_t st);
+constexpr float kPolarThreshold = 0x1p-40f;   // |P_n^m| below this is left out of the panel sums
+void tc_tile_counts(int lmax, int npairs, int &ntiles_s, int &ntiles_a);
+cudaError_t tc_polar_stats(int lmax, int mmax, int npairs, const int *d_c0_s, const int *d_c0_a, double &frac_s,
+                           double &frac_a);
 int tc_max_batch();
 cudaError_t launch_selftest_timeout(int *err, unsigned long long max_ns, cudaStream_t st);
 

@@ -6,22 +6,29 @@
 //   synthesis  E/O[pair, col] = sum_k P[pair, k] * A[k, col]       (Eq. synth_direct)
 //   analysis   f[k, col]      = sum_pair P[pair, k] * S[pair, col] (Eq. gauss)
 // with k the index of n among degrees of that parity, col = (field, re/im),
-// and S the weighted north/south folds (s for even, d for odd n - m).
+// and S the weighted north/south folds (s for even, d for odd n - m).  The
+// vector transforms run the same GEMMs with dP = sin(theta) dP/dtheta as a
+// second matrix (k_tc_vec).
 //
-// The matrices P_n^m(x_j) are built once per plan by the FP64 recurrence of
-// Sec. 3.2 with the rescaling of Sec. 3.5 (the precomputed variant of
-// Sec. 3.1), split into bf16 hi + lo parts and stored in
-// HBM already in the tensor core's shared-memory operand layout (K-major,
-// no swizzle: 8-row x 16-byte core matrices), so each chunk is one bulk copy.
-// The data operand is split the same way by the CTA's threads, and each
-// product is hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory.
+// The matrices P_n^m(x_j) (and dP) are built once per plan by the FP64
+// recurrence of Sec. 3.2 with the rescaling of Sec. 3.5 (the precomputed
+// variant of Sec. 3.1), split into bf16 hi + lo parts and stored in HBM
+// already in the tensor core's shared-memory operand layout (K-major, no
+// swizzle: 8-row x 16-byte core matrices), so each chunk is one bulk copy.
+// A prep kernel converts the FP32 data into the same blocked hi/lo layout,
+// and each product is hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor
+// memory.
 //
-// CTA: 128 threads, one (order m, 128-row tile).  Thread 0 issues the bulk
-// copies and the MMAs; all threads stage the data operand and run the
-// epilogue (tcgen05.ld of the accumulators).  Every wait is bounded; on a
-// timeout the kernel records an error code and returns.
+// CTA: 128 threads, one (order m, 128-row tile).  Thread 0 streams panel and
+// data chunks with cp.async.bulk into a ring of stages and issues the MMAs;
+// the four warps run the epilogue (tcgen05.ld of the accumulators).  Every
+// wait is bounded; on a timeout the kernel records an error code and returns.
+// Leading panel chunks whose values are all below 2^-40 (high order, near
+// the poles) are skipped: the static polar optimisation of Sec. 3.1.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <vector>
 
 #include "sht_internal.h"
 #include "tc_ptx.cuh"
@@ -30,14 +37,14 @@ namespace sht {
 namespace {
 
 constexpr int kRows = 128;            // MMA M
-constexpr int kKc = 32;               // K per chunk (per parity)
-constexpr int kBlk = kRows * kKc * 2; // bytes of one bf16 [128 x 32] operand block
-constexpr int kChunkPanel = 4 * kBlk; // [parity][hi/lo] blocks per chunk = 32 KB
-constexpr uint32_t kSbo = (kKc / 8) * 128;  // 8-row group stride in a [rows x 32] block
+constexpr int kKc = 16;               // K per chunk (per parity): one MMA K step
+constexpr int kBlk = kRows * kKc * 2; // bytes of one bf16 [128 x kKc] panel block
+constexpr int kChunkPanel = 4 * kBlk; // [parity][hi/lo] blocks per chunk = 16 KB
+constexpr uint32_t kSbo = (kKc / 8) * 128;  // 8-row group stride in a [rows x kKc] block
 constexpr uint32_t kLbo = 128;              // K-adjacent core matrices
 constexpr uint64_t kWaitNs = 2000000000ull; // 2 s
 
-// byte offset of element (row, k) in a K-major [rows x 32] bf16 block
+// byte offset of element (row, k) in a K-major [rows x kKc] bf16 block
 __host__ __device__ __forceinline__ uint32_t blk_off(int row, int k)
 {
     return (uint32_t)((row >> 3) * kSbo + (k >> 3) * kLbo + (row & 7) * 16 + (k & 7) * 2);
@@ -55,7 +62,15 @@ __device__ __forceinline__ void split_bf16_d(double v, __nv_bfloat16 &hi, __nv_b
     lo = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hi)));
 }
 
-__device__ __forceinline__ long col_of(int lmax, int m) { return (long)m * (2 * lmax + 3 - m) / 2; }
+__device__ __forceinline__ void put_split(unsigned char *bh, unsigned char *bl, int row, int k, float v)
+{
+    __nv_bfloat16 h, l;
+    split_bf16(v, h, l);
+    *reinterpret_cast<__nv_bfloat16 *>(bh + blk_off(row, k)) = h;
+    *reinterpret_cast<__nv_bfloat16 *>(bl + blk_off(row, k)) = l;
+}
+
+__host__ __device__ __forceinline__ long col_of(int lmax, int m) { return (long)m * (2 * lmax + 3 - m) / 2; }
 
 __device__ __forceinline__ void raise_err(int *err, int code)
 {
@@ -64,12 +79,14 @@ __device__ __forceinline__ void raise_err(int *err, int code)
 
 // ---------------------------------------------------------------------------
 // Panel builder: one thread per (m, pair), FP64 recurrence with rescaling.
-// Both panel sets must be zeroed beforehand; only non-zero entries are written.
+// deriv = 0: P_n^m; deriv = 1: dP = sin(theta) dP_n^m/dtheta = n x P_n - dc_n P_{n-1}
+// (both factors carry the same scale, so the identity holds in scaled form).
+// The panels must be zeroed beforehand; only non-zero entries are written.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128)
 k_build_panels(PlanView<double> pv, const unsigned long long *__restrict__ off_s,
                const unsigned long long *__restrict__ off_a, unsigned char *__restrict__ ps,
-               unsigned char *__restrict__ pa)
+               unsigned char *__restrict__ pa, int deriv)
 {
     const int m = blockIdx.y;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -97,12 +114,13 @@ k_build_panels(PlanView<double> pv, const unsigned long long *__restrict__ off_s
             y2 *= 0x1p-240;
             k -= 1;
         }
-        const double P = (k == 0) ? y1 : 0.0;
+        if (k != 0) continue;
+        const double P = deriv ? fma((double)(m + nn) * x, y1, -pv.dc[col + nn] * y2) : y1;
         if (P == 0.0) continue;
         __nv_bfloat16 hi, lo;
         split_bf16_d(P, hi, lo);
         const int par = nn & 1, kk = nn >> 1;
-        // synthesis panel: block (t, chunk kk/32, parity, hi|lo), element (row, kk%32)
+        // synthesis panel: block (t, chunk kk/kKc, parity, hi|lo), element (row, kk%kKc)
         {
             unsigned char *b = sbase + (size_t)(kk / kKc) * kChunkPanel + (size_t)(par * 2) * kBlk;
             const uint32_t o = blk_off(row, kk % kKc);
@@ -120,108 +138,199 @@ k_build_panels(PlanView<double> pv, const unsigned long long *__restrict__ off_s
     }
 }
 
-struct TcArgs {
-    int lmax, mmax, npairs, nlm, batch, nc, ntiles, stages, op;
-    const unsigned char *panel;
-    const unsigned long long *off;     // per-order panel byte offsets
-    const unsigned char *data;         // data operand, blocked bf16 hi/lo
-    const unsigned long long *dchunk;  // synthesis: first data chunk of each order
-    float *out;                        // synthesis: E/O; analysis: spectra
-    int *err;
-};
-
-// Bytes of one chunk of the data operand: [parity][hi|lo] blocks of nc rows x 32.
-__host__ __device__ inline size_t tc_data_chunk(int nc) { return 4 * (size_t)nc * kKc * 2; }
-
-// Shared memory: [stages] x { panel chunk (32 KB) | data chunk } then 2*stages+1
-// mbarriers and the TMEM address slot.
-__host__ __device__ inline size_t tc_stage_bytes(int nc) { return (size_t)kChunkPanel + tc_data_chunk(nc); }
-
-__host__ __device__ inline size_t tc_smem_bytes(int nc, int stages)
-{
-    return 1024 + (size_t)stages * tc_stage_bytes(nc) + 8 * (2 * stages + 2);
-}
-
 // ---------------------------------------------------------------------------
-// Data operand preparation: FP32 -> bf16 hi/lo, blocked like the panels.
-// Synthesis: chunk (m, c) holds degrees n - m in [64c, 64c + 64), row 2b + part.
-// Analysis:  chunk (m, kc) holds pairs [32kc, 32kc + 32), folds s (even) / d (odd).
-// grid = (chunk, m) with chunk < max chunks; one CTA of 128 threads per chunk.
+// Data operand: one chunk is [class][hi|lo] blocks of `rows` x kKc (rows a
+// multiple of 32).  Synthesis chunk (m, c) holds degrees n - m in
+// [2 kKc c, 2 kKc (c + 1)), class = parity of n - m; analysis chunk (m, kc)
+// holds pairs [kKc kc, kKc (kc + 1)), class = fold (0: s, 1: d).
+// Scalar rows: 2b + (re|im).  Vector rows: first quantity (S or theta)
+// 2b + (re|im), second (T or phi) NH + 2b + (re|im), NH = rows / 2.
+// Synthesis chunks are numbered from dchunk[m] per order; analysis chunks
+// are m * kch + kc.
 // ---------------------------------------------------------------------------
+__host__ __device__ inline size_t data_chunk_bytes(int rows) { return 4 * (size_t)rows * kKc * 2; }
+
 __global__ void __launch_bounds__(128)
-k_tc_prep(int synth, int lmax, int mmax, int npairs, int nlm, int batch, int nc, int op, const float *__restrict__ in,
-          const unsigned long long *__restrict__ dchunk, unsigned char *__restrict__ data)
+k_tc_prep(int synth, int vec, int lmax, int mmax, int npairs, int nlm, int batch, int rows, int op,
+          const float *__restrict__ in0, const float *__restrict__ in1, const unsigned long long *__restrict__ dchunk,
+          unsigned char *__restrict__ data)
 {
     const int m = blockIdx.y, c = blockIdx.x;
     const int L = lmax - m + 1, Le = (L + 1) / 2;
     const int nch = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
     if (c >= nch) return;
-    const size_t db = tc_data_chunk(nc);
+    const size_t db = data_chunk_bytes(rows);
     unsigned char *dat = data + (synth ? (dchunk[m] + c) : ((size_t)m * nch + c)) * db;
-    const size_t blk = (size_t)nc * kKc * 2;
-    // zero the chunk first: rows >= 2*batch are the MMA's pad columns
+    const size_t blk = (size_t)rows * kKc * 2;
+    const int NH = rows / 2;
+    // zero the chunk first: unused rows are the MMA's pad columns
     for (int i = threadIdx.x; i < (int)(db / 16); i += blockDim.x)
         *reinterpret_cast<uint4 *>(dat + (size_t)i * 16) = make_uint4(0, 0, 0, 0);
     __syncthreads();
     if (synth) {
         const long col = col_of(lmax, m);
-        const float cm_in = (op == OP_ANALYS_ADJ && m > 0) ? 0.5f : 1.0f;
-        const float2 *spec = reinterpret_cast<const float2 *>(in);
+        // adjoint of analysis: b / c_m (scalar) or b / (c_m n (n + 1)) (vector)
+        const float cadj = (op == OP_ANALYS_ADJ && m > 0) ? 0.5f : 1.0f;
+        const float2 *A = reinterpret_cast<const float2 *>(in0);
+        const float2 *B = reinterpret_cast<const float2 *>(in1);
         for (int i = threadIdx.x; i < batch * 2 * kKc; i += blockDim.x) {
             const int b = i / (2 * kKc), j = i - b * (2 * kKc);
             const int nn = 2 * kKc * c + j;
-            float2 v = make_float2(0.f, 0.f);
-            if (nn < L) v = spec[(size_t)b * nlm + col + nn];
-            v.x *= cm_in;
-            v.y = (m == 0) ? 0.f : v.y * cm_in;
-            const int par = j & 1, kk = j >> 1;
-            __nv_bfloat16 hr, lr, hi_, li;
-            split_bf16(v.x, hr, lr);
-            split_bf16(v.y, hi_, li);
-            unsigned char *bh = dat + (size_t)(par * 2) * blk;
+            const int n = m + nn;
+            const int cls = j & 1, kk = j >> 1;
+            unsigned char *bh = dat + (size_t)(cls * 2) * blk;
             unsigned char *bl = bh + blk;
-            *reinterpret_cast<__nv_bfloat16 *>(bh + blk_off(2 * b, kk)) = hr;
-            *reinterpret_cast<__nv_bfloat16 *>(bl + blk_off(2 * b, kk)) = lr;
-            *reinterpret_cast<__nv_bfloat16 *>(bh + blk_off(2 * b + 1, kk)) = hi_;
-            *reinterpret_cast<__nv_bfloat16 *>(bl + blk_off(2 * b + 1, kk)) = li;
+            float sc = cadj;
+            if (vec && op == OP_ANALYS_ADJ) sc = (n == 0) ? 0.f : cadj / ((float)n * (float)(n + 1));
+            float2 v = make_float2(0.f, 0.f);
+            if (nn < L) v = A[(size_t)b * nlm + col + nn];
+            put_split(bh, bl, 2 * b, kk, v.x * sc);
+            put_split(bh, bl, 2 * b + 1, kk, m == 0 ? 0.f : v.y * sc);
+            if (vec) {
+                float2 w = make_float2(0.f, 0.f);
+                if (nn < L) w = B[(size_t)b * nlm + col + nn];
+                put_split(bh, bl, NH + 2 * b, kk, w.x * sc);
+                put_split(bh, bl, NH + 2 * b + 1, kk, m == 0 ? 0.f : w.y * sc);
+            }
         }
     } else {
-        const float4 *sd = reinterpret_cast<const float4 *>(in);
+        const float4 *A = reinterpret_cast<const float4 *>(in0);
+        const float4 *B = reinterpret_cast<const float4 *>(in1);
         for (int i = threadIdx.x; i < batch * kKc; i += blockDim.x) {
             const int b = i / kKc, j = i - b * kKc;
             const int p = kKc * c + j;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (p < npairs) v = sd[((size_t)b * (mmax + 1) + m) * npairs + p];
-            const float vals[4] = {v.x, v.y, v.z, v.w};  // s.re s.im d.re d.im
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f), w = v;
+            if (p < npairs) {
+                v = A[((size_t)b * (mmax + 1) + m) * npairs + p];
+                if (vec) w = B[((size_t)b * (mmax + 1) + m) * npairs + p];
+            }
+            const float va[4] = {v.x, v.y, v.z, v.w};  // s.re s.im d.re d.im
+            const float wa[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int par = q >> 1, part = q & 1;
-                __nv_bfloat16 h, l;
-                split_bf16(vals[q], h, l);
-                unsigned char *bh = dat + (size_t)(par * 2) * blk;
+            for (int t = 0; t < 4; ++t) {
+                const int cls = t >> 1, part = t & 1;
+                unsigned char *bh = dat + (size_t)(cls * 2) * blk;
                 unsigned char *bl = bh + blk;
-                *reinterpret_cast<__nv_bfloat16 *>(bh + blk_off(2 * b + part, j)) = h;
-                *reinterpret_cast<__nv_bfloat16 *>(bl + blk_off(2 * b + part, j)) = l;
+                put_split(bh, bl, 2 * b + part, j, va[t]);
+                if (vec) put_split(bh, bl, NH + 2 * b + part, j, wa[t]);
             }
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// The contraction.  Thread 0 is the producer and MMA issuer: for each chunk it
-// waits until the stage is free (the MMAs that read it completed), issues the
-// two bulk copies (panel chunk and data chunk) D = S - 1 chunks ahead, waits
-// for the current chunk and issues its 12 MMAs.  The other threads only run
-// the epilogue once every MMA has completed.
+// Shared memory of the contraction kernels: a ring of S stages, each
+// { NP panel chunks | data chunk }, then 2 S + 1 mbarriers and the TMEM slot.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline size_t stage_bytes_of(int npanels, int rows)
+{
+    return (size_t)npanels * kChunkPanel + data_chunk_bytes(rows);
+}
+
+__host__ __device__ inline size_t smem_bytes_of(int npanels, int rows, int stages)
+{
+    return 1024 + (size_t)stages * stage_bytes_of(npanels, rows) + 8 * (2 * stages + 2);
+}
+
+struct TcArgs {
+    int lmax, mmax, npairs, nlm, batch, rows, ntiles, stages, op;
+    const unsigned char *panel, *dpanel;   // dpanel: vector transforms only
+    const unsigned long long *off;         // per-order panel byte offsets
+    const int *c0;                         // per (m, tile): first chunk above the polar threshold
+    const unsigned char *data;             // data operand, blocked bf16 hi/lo
+    const unsigned long long *dchunk;      // synthesis: first data chunk of each order
+    float *out0, *out1;                    // outputs (vector: second quantity in out1)
+    const float *st;                       // sin(theta) per pair (vector synthesis)
+    int *err;
+};
+
+// Thread 0's part of a contraction: streams chunks cstart .. cstart + nlive - 1
+// (S - 1 ahead) into the stage ring, calls mma(stage, data, first) for each,
+// and commits the MMAs to bar_done.  Returns false after a timed-out wait.
+template <int NP, typename MmaFn>
+__device__ __forceinline__ bool produce(const TcArgs &a, unsigned char *smem, size_t stage_bytes, uint64_t *bar_load,
+                                        uint64_t *bar_mma, uint64_t *bar_done, const unsigned char *panel0,
+                                        const unsigned char *panel1, const unsigned char *data, int cstart, int nlive,
+                                        MmaFn &&mma)
+{
+    const int S = a.stages;
+    const uint32_t dbytes = (uint32_t)data_chunk_bytes(a.rows);
+    const uint32_t tx = (uint32_t)NP * kChunkPanel + dbytes;
+    bool ok = true;
+    int issued[4] = {0, 0, 0, 0}, waited[4] = {0, 0, 0, 0};
+    auto issue = [&](int un) {
+        const int sn = un % S;
+        unsigned char *st = smem + (size_t)sn * stage_bytes;
+        const size_t c = (size_t)(cstart + un);
+        tc::mbar_arrive_expect_tx(&bar_load[sn], tx);
+        tc::bulk_g2s(st, panel0 + c * kChunkPanel, kChunkPanel, &bar_load[sn]);
+        if (NP == 2) tc::bulk_g2s(st + kChunkPanel, panel1 + c * kChunkPanel, kChunkPanel, &bar_load[sn]);
+        tc::bulk_g2s(st + (size_t)NP * kChunkPanel, data + c * dbytes, dbytes, &bar_load[sn]);
+        issued[sn] += 1;
+    };
+    const int D = S - 1;
+    for (int u = 0; u < D && u < nlive; ++u) issue(u);
+    for (int u = 0; u < nlive; ++u) {
+        const int q = u % S;
+        const int un = u + D;
+        if (un < nlive) {
+            if (un >= S) {
+                // chunk un goes to the stage of chunk un - S == u - 1: wait for its MMAs
+                const int up = un - S;
+                if (!tc::mbar_wait_bounded(&bar_mma[up % S], (uint32_t)((up / S) & 1), kWaitNs)) { ok = false; break; }
+            }
+            issue(un);
+        }
+        if (!tc::mbar_wait_bounded(&bar_load[q], (uint32_t)((u / S) & 1), kWaitNs)) { ok = false; break; }
+        waited[q] += 1;
+        tc::tc_fence_after();
+        unsigned char *st = smem + (size_t)q * stage_bytes;
+        mma(st, st + (size_t)NP * kChunkPanel, u == 0);
+        tc::mma_commit(&bar_mma[q]);
+    }
+    if (!ok) {
+        raise_err(a.err, SHT_ETIMEOUT);
+        // wait (bounded) for this CTA's own copies in flight before it exits
+        for (int q = 0; q < S; ++q)
+            if (issued[q] > waited[q])
+                (void)tc::mbar_wait_bounded(&bar_load[q], (uint32_t)((issued[q] - 1) & 1), 100000000ull);
+    }
+    tc::mma_commit(bar_done);  // arrives once every MMA issued above has completed
+    return ok;
+}
+
+// Common prologue: barriers, TMEM allocation.  Returns the TMEM base.
+__device__ __forceinline__ uint32_t setup_ctas(int S, uint64_t *bar_load, uint64_t *bar_mma, uint64_t *bar_done,
+                                               uint32_t *tslot, uint32_t ncols, int *s_ok)
+{
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) {
+            tc::mbar_init(&bar_load[q], 1);
+            tc::mbar_init(&bar_mma[q], 1);
+        }
+        tc::mbar_init(bar_done, 1);
+        tc::mbar_fence_init();
+        *s_ok = 1;
+    }
+    if ((tid >> 5) == 0) tc::tmem_alloc(tslot, ncols);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    return *tslot;
+}
+
+// ---------------------------------------------------------------------------
+// Scalar contraction.  Accumulators: [parity][rows columns].
 // ---------------------------------------------------------------------------
 template <bool SYNTH>
-__global__ void __launch_bounds__(128, 1) k_tc_legendre(TcArgs a)
+__global__ void __launch_bounds__(128, 2) k_tc_legendre(TcArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int S = a.stages, NC = a.nc;
-    const size_t stage_bytes = tc_stage_bytes(NC);
-    const uint32_t dbytes = (uint32_t)tc_data_chunk(NC);
+    const int S = a.stages, NC = a.rows;
+    const size_t stage_bytes = stage_bytes_of(1, NC);
+    const size_t blk = (size_t)NC * kKc * 2;
     uint64_t *bar_load = reinterpret_cast<uint64_t *>(smem + (size_t)S * stage_bytes);
     uint64_t *bar_mma = bar_load + S;
     uint64_t *bar_done = bar_mma + S;
@@ -237,97 +346,34 @@ __global__ void __launch_bounds__(128, 1) k_tc_legendre(TcArgs a)
     const long col = col_of(lmax, m);
     // analysis tiles run over degrees of this order: tiles past them have no panel
     if (!SYNTH && tile * kRows >= Le) return;
-    // chunks: synthesis over degrees (per parity), analysis over latitude pairs
     const int nchunks = SYNTH ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
     const unsigned char *panel = a.panel + a.off[m] + (size_t)tile * nchunks * kChunkPanel;
-    const unsigned char *data = a.data + (SYNTH ? a.dchunk[m] : (unsigned long long)m * nchunks) * dbytes;
+    const unsigned char *data =
+        a.data + (SYNTH ? a.dchunk[m] : (unsigned long long)m * nchunks) * data_chunk_bytes(NC);
     const uint32_t ncols = NC * 2 <= 64 ? 64 : (NC * 2 <= 128 ? 128 : 256);
+    const int cstart = a.c0 ? a.c0[m * a.ntiles + tile] : 0;
+    const int nlive = nchunks - cstart;
+
+    const uint32_t tmem = setup_ctas(S, bar_load, bar_mma, bar_done, tslot, ncols, &s_ok);
 
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) {
-            tc::mbar_init(&bar_load[s], 1);
-            tc::mbar_init(&bar_mma[s], 1);
-        }
-        tc::mbar_init(bar_done, 1);
-        tc::mbar_fence_init();
-        s_ok = 1;
-    }
-    if (warp == 0) tc::tmem_alloc(tslot, ncols);
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::tc_fence_after();
-    const uint32_t tmem = *tslot;
-
-    if (tid == 0) {
-        bool ok = true;
-        int issued[4] = {0, 0, 0, 0}, waited[4] = {0, 0, 0, 0};
         const uint32_t idesc = tc::idesc_bf16_f32(kRows, NC);
-        const int D = S - 1;
-        auto issue = [&](int cn) {
-            const int sn = cn % S;
-            unsigned char *st = smem + (size_t)sn * stage_bytes;
-            tc::mbar_arrive_expect_tx(&bar_load[sn], (uint32_t)kChunkPanel + dbytes);
-            tc::bulk_g2s(st, panel + (size_t)cn * kChunkPanel, kChunkPanel, &bar_load[sn]);
-            tc::bulk_g2s(st + kChunkPanel, data + (size_t)cn * dbytes, dbytes, &bar_load[sn]);
-            issued[sn] += 1;
-        };
-        for (int c = 0; c < D && c < nchunks; ++c) issue(c);
-        for (int c = 0; c < nchunks; ++c) {
-            const int s = c % S;
-            // refill the stage of chunk c - 1 with chunk c + D once its MMAs are done
-            const int cn = c + D;
-            if (cn < nchunks) {
-                if (cn >= S) {
-                    const int cp = cn - S;  // == c - 1
-                    if (!tc::mbar_wait_bounded(&bar_mma[cp % S], (uint32_t)((cp / S) & 1), kWaitNs)) {
-                        ok = false;
-                        break;
-                    }
-                }
-                issue(cn);
-            }
-            if (!tc::mbar_wait_bounded(&bar_load[s], (uint32_t)((c / S) & 1), kWaitNs)) {
-                ok = false;
-                break;
-            }
-            waited[s] += 1;
-            tc::tc_fence_after();
-            unsigned char *st = smem + (size_t)s * stage_bytes;
-            unsigned char *dat = st + kChunkPanel;
+        const bool ok = produce<1>(a, smem, stage_bytes, bar_load, bar_mma, bar_done, panel, nullptr, data, cstart,
+                                   nlive, [&](unsigned char *st, unsigned char *dat, bool first) {
 #pragma unroll
             for (int par = 0; par < 2; ++par) {
-                const unsigned char *ah = st + (size_t)(par * 2) * kBlk;
-                const unsigned char *al = ah + kBlk;
-                const unsigned char *bh = dat + (size_t)(par * 2) * NC * kKc * 2;
-                const unsigned char *bl = bh + (size_t)NC * kKc * 2;
+                const unsigned char *ah = st + (size_t)(par * 2) * kBlk, *al = ah + kBlk;
+                const unsigned char *bh = dat + (size_t)(par * 2) * blk, *bl = bh + blk;
                 const uint32_t d = tmem + (uint32_t)(par * NC);
-#pragma unroll
-                for (int ks = 0; ks < kKc / 16; ++ks) {
-                    const uint32_t ko = (uint32_t)ks * 2 * kLbo;  // 16 K = 2 core matrices
-                    const uint64_t dah = tc::smem_desc(ah + ko, kLbo, kSbo);
-                    const uint64_t dal = tc::smem_desc(al + ko, kLbo, kSbo);
-                    const uint64_t dbh = tc::smem_desc(bh + ko, kLbo, kSbo);
-                    const uint64_t dbl = tc::smem_desc(bl + ko, kLbo, kSbo);
-                    tc::mma_bf16(d, dah, dbh, idesc, !(c == 0 && ks == 0));
-                    tc::mma_bf16(d, dah, dbl, idesc, true);
-                    tc::mma_bf16(d, dal, dbh, idesc, true);
-                }
+                const uint64_t dah = tc::smem_desc(ah, kLbo, kSbo), dal = tc::smem_desc(al, kLbo, kSbo);
+                const uint64_t dbh = tc::smem_desc(bh, kLbo, kSbo), dbl = tc::smem_desc(bl, kLbo, kSbo);
+                tc::mma_bf16(d, dah, dbh, idesc, !first);
+                tc::mma_bf16(d, dah, dbl, idesc, true);
+                tc::mma_bf16(d, dal, dbh, idesc, true);
             }
-            tc::mma_commit(&bar_mma[s]);
-        }
-        if (ok) {
-            tc::mma_commit(bar_done);
-        } else {
-            raise_err(a.err, SHT_ETIMEOUT);
-            s_ok = 0;
-            // wait (bounded) for this CTA's own copies and MMAs before TMEM is freed
-            for (int s = 0; s < S; ++s)
-                if (issued[s] > waited[s])
-                    (void)tc::mbar_wait_bounded(&bar_load[s], (uint32_t)((issued[s] - 1) & 1), 100000000ull);
-            tc::mma_commit(bar_done);
-        }
+        });
+        if (!ok) s_ok = 0;
     }
-    // everyone waits for the last MMAs (bounded), then reads the accumulators
     bool ok = tc::mbar_wait_bounded(bar_done, 0, 2 * kWaitNs);
     if (!ok) raise_err(a.err, SHT_ETIMEOUT);
     ok = __syncthreads_and(ok && s_ok);
@@ -335,22 +381,27 @@ __global__ void __launch_bounds__(128, 1) k_tc_legendre(TcArgs a)
         tc::tc_fence_after();
         const int row = tile * kRows + warp * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c0 = 0; c0 < NC; c0 += 32) {
+        for (int cb = 0; cb < NC; cb += 32) {
             float de[32], dd[32];
-            tc::tmem_ld32(lane_base + (uint32_t)c0, de);
-            tc::tmem_ld32(lane_base + (uint32_t)(NC + c0), dd);
+            if (nlive > 0) {
+                tc::tmem_ld32(lane_base + (uint32_t)cb, de);
+                tc::tmem_ld32(lane_base + (uint32_t)(NC + cb), dd);
+            } else {  // every chunk below the polar threshold: the sums are zero
+#pragma unroll
+                for (int i = 0; i < 32; ++i) de[i] = dd[i] = 0.f;
+            }
             for (int q = 0; q < 32; q += 2) {
-                const int b = (c0 + q) >> 1;
+                const int b = (cb + q) >> 1;
                 if (b >= a.batch) break;
                 if (SYNTH) {
                     if (row < npairs) {
-                        float4 *eo = reinterpret_cast<float4 *>(a.out);
+                        float4 *eo = reinterpret_cast<float4 *>(a.out0);
                         eo[((size_t)b * (a.mmax + 1) + m) * npairs + row] = make_float4(de[q], de[q + 1], dd[q], dd[q + 1]);
                     }
                 } else {
                     const int ne = 2 * row, no = 2 * row + 1;   // n - m of the two rows
                     const float sc = (a.op == OP_SYNTH_ADJ && m > 0) ? 2.f : 1.f;
-                    float2 *spec = reinterpret_cast<float2 *>(a.out);
+                    float2 *spec = reinterpret_cast<float2 *>(a.out0);
                     if (ne < L) spec[(size_t)b * a.nlm + col + ne] = make_float2(sc * de[q], m == 0 ? 0.f : sc * de[q + 1]);
                     if (no < L) spec[(size_t)b * a.nlm + col + no] = make_float2(sc * dd[q], m == 0 ? 0.f : sc * dd[q + 1]);
                 }
@@ -362,9 +413,185 @@ __global__ void __launch_bounds__(128, 1) k_tc_legendre(TcArgs a)
     if (warp == 0) tc::tmem_dealloc(tmem, ncols);
 }
 
+// ---------------------------------------------------------------------------
+// Vector (spheroidal/toroidal) contraction.  dP = sin(theta) dP/dtheta has the
+// mirror parity opposite to P.  Per order m and output class cls (0: E rows /
+// even n - m, 1: O rows / odd n - m), with oth = 1 - cls:
+//   synthesis  acc1 = P_cls [S|T]_cls,  acc2 = dP_oth [S|T]_oth
+//     sin V_theta = acc2[S] - i m acc1[T],  sin V_phi = i m acc1[S] + acc2[T];
+//   analysis   acc1 = P_cls^T [th|ph]_cls,  acc2 = dP_cls^T [th|ph]_oth
+//     (data class 0: s folds, 1: d folds; the folds already carry 1/sin)
+//     S_n = scale (acc2[th] - i m acc1[ph]),  T_n = scale (i m acc1[th] + acc2[ph]).
+// Accumulators: [cls][acc][N columns], N = 2 NH (first | second quantity).
+// ---------------------------------------------------------------------------
+template <bool SYNTH>
+__global__ void __launch_bounds__(128, 1) k_tc_vec(TcArgs a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int S = a.stages, NV = a.rows, NH = a.rows / 2;
+    const size_t stage_bytes = stage_bytes_of(2, NV);
+    const size_t blk = (size_t)NV * kKc * 2;
+    uint64_t *bar_load = reinterpret_cast<uint64_t *>(smem + (size_t)S * stage_bytes);
+    uint64_t *bar_mma = bar_load + S;
+    uint64_t *bar_done = bar_mma + S;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_done + 1);
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    const int m = blockIdx.x / a.ntiles;
+    const int tile = blockIdx.x - m * a.ntiles;
+    const int lmax = a.lmax, npairs = a.npairs;
+    const int L = lmax - m + 1;
+    const int Le = (L + 1) / 2;
+    const long col = col_of(lmax, m);
+    if (!SYNTH && tile * kRows >= Le) return;
+    const int nchunks = SYNTH ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
+    const size_t poff = a.off[m] + (size_t)tile * nchunks * kChunkPanel;
+    const unsigned char *data =
+        a.data + (SYNTH ? a.dchunk[m] : (unsigned long long)m * nchunks) * data_chunk_bytes(NV);
+    const uint32_t ncols = 4 * NV <= 256 ? 256 : 512;
+    const int cstart = a.c0 ? a.c0[m * a.ntiles + tile] : 0;
+    const int nlive = nchunks - cstart;
+
+    const uint32_t tmem = setup_ctas(S, bar_load, bar_mma, bar_done, tslot, ncols, &s_ok);
+
+    if (tid == 0) {
+        const uint32_t idesc = tc::idesc_bf16_f32(kRows, NV);
+        const bool ok = produce<2>(a, smem, stage_bytes, bar_load, bar_mma, bar_done, a.panel + poff, a.dpanel + poff,
+                                   data, cstart, nlive, [&](unsigned char *st, unsigned char *dat, bool first) {
+#pragma unroll
+            for (int cls = 0; cls < 2; ++cls) {
+                const int dp = SYNTH ? 1 - cls : cls;   // parity of n - m of the dP block
+                const unsigned char *aph = st + (size_t)(cls * 2) * kBlk, *apl = aph + kBlk;
+                const unsigned char *adh = st + kChunkPanel + (size_t)(dp * 2) * kBlk, *adl = adh + kBlk;
+                const unsigned char *b1h = dat + (size_t)(cls * 2) * blk, *b1l = b1h + blk;
+                const unsigned char *b2h = dat + (size_t)((1 - cls) * 2) * blk, *b2l = b2h + blk;
+                const uint32_t d1 = tmem + (uint32_t)((cls * 2 + 0) * NV);
+                const uint32_t d2 = tmem + (uint32_t)((cls * 2 + 1) * NV);
+                const uint64_t Aph = tc::smem_desc(aph, kLbo, kSbo), Apl = tc::smem_desc(apl, kLbo, kSbo);
+                const uint64_t Adh = tc::smem_desc(adh, kLbo, kSbo), Adl = tc::smem_desc(adl, kLbo, kSbo);
+                const uint64_t B1h = tc::smem_desc(b1h, kLbo, kSbo), B1l = tc::smem_desc(b1l, kLbo, kSbo);
+                const uint64_t B2h = tc::smem_desc(b2h, kLbo, kSbo), B2l = tc::smem_desc(b2l, kLbo, kSbo);
+                tc::mma_bf16(d1, Aph, B1h, idesc, !first);
+                tc::mma_bf16(d1, Aph, B1l, idesc, true);
+                tc::mma_bf16(d1, Apl, B1h, idesc, true);
+                tc::mma_bf16(d2, Adh, B2h, idesc, !first);
+                tc::mma_bf16(d2, Adh, B2l, idesc, true);
+                tc::mma_bf16(d2, Adl, B2h, idesc, true);
+            }
+        });
+        if (!ok) s_ok = 0;
+    }
+    bool ok = tc::mbar_wait_bounded(bar_done, 0, 2 * kWaitNs);
+    if (!ok) raise_err(a.err, SHT_ETIMEOUT);
+    ok = __syncthreads_and(ok && s_ok);
+    if (ok) {
+        tc::tc_fence_after();
+        const int row = tile * kRows + warp * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        const float fm = (float)m;
+        float isn = 1.f;
+        if (SYNTH && row < npairs) isn = 1.f / a.st[row];
+        for (int cls = 0; cls < 2; ++cls) {
+            for (int cb = 0; cb < NH; cb += 32) {
+                float v[2][2][32];  // [acc][first|second quantity][col]
+#pragma unroll
+                for (int ac = 0; ac < 2; ++ac)
+#pragma unroll
+                    for (int hf = 0; hf < 2; ++hf) {
+                        if (nlive > 0) {
+                            tc::tmem_ld32(lane_base + (uint32_t)((cls * 2 + ac) * NV + hf * NH + cb), v[ac][hf]);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) v[ac][hf][i] = 0.f;
+                        }
+                    }
+                for (int q = 0; q < 32; q += 2) {
+                    const int b = (cb + q) >> 1;
+                    if (b >= a.batch) break;
+                    if (SYNTH) {
+                        if (row >= npairs) continue;
+                        const float psr = v[0][0][q], psi = v[0][0][q + 1];   // sum P S
+                        const float ptr = v[0][1][q], pti = v[0][1][q + 1];   // sum P T
+                        const float dsr = v[1][0][q], dsi = v[1][0][q + 1];   // sum dP S
+                        const float dtr = v[1][1][q], dti = v[1][1][q + 1];   // sum dP T
+                        const size_t oi = (((size_t)b * (a.mmax + 1) + m) * npairs + row) * 2 + cls;
+                        reinterpret_cast<float2 *>(a.out0)[oi] =
+                            make_float2((dsr + fm * pti) * isn, (dsi - fm * ptr) * isn);
+                        reinterpret_cast<float2 *>(a.out1)[oi] =
+                            make_float2((dtr - fm * psi) * isn, (dti + fm * psr) * isn);
+                    } else {
+                        const int nn = 2 * row + cls;
+                        if (nn >= L) continue;
+                        const int n = m + nn;
+                        float sc;
+                        if (a.op == OP_SYNTH_ADJ) sc = (m > 0) ? 2.f : 1.f;
+                        else sc = (n == 0) ? 0.f : 1.f / ((float)n * (float)(n + 1));
+                        const float pthr = v[0][0][q], pthi = v[0][0][q + 1];   // P^T theta folds
+                        const float pphr = v[0][1][q], pphi = v[0][1][q + 1];   // P^T phi folds
+                        const float dthr = v[1][0][q], dthi = v[1][0][q + 1];   // dP^T theta folds
+                        const float dphr = v[1][1][q], dphi = v[1][1][q + 1];   // dP^T phi folds
+                        float2 sv = make_float2(sc * (dthr + fm * pphi), sc * (dthi - fm * pphr));
+                        float2 tv = make_float2(sc * (dphr - fm * pthi), sc * (dphi + fm * pthr));
+                        if (m == 0) { sv.y = 0.f; tv.y = 0.f; }
+                        reinterpret_cast<float2 *>(a.out0)[(size_t)b * a.nlm + col + nn] = sv;
+                        reinterpret_cast<float2 *>(a.out1)[(size_t)b * a.nlm + col + nn] = tv;
+                    }
+                }
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+// ---------------------------------------------------------------------------
+// Static polar optimisation (Sec. 3.1): for each (m, tile), the first chunk
+// whose panel blocks hold a value >= thr.  One CTA per (m, tile).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+k_panel_first_live(int synth, int lmax, int npairs, int ntiles, const unsigned long long *__restrict__ off,
+                   const unsigned char *__restrict__ panel, float thr, int *__restrict__ c0)
+{
+    const int m = blockIdx.y, tile = blockIdx.x;
+    const int L = lmax - m + 1, Le = (L + 1) / 2;
+    const int nchunks = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
+    const bool valid = synth || tile * kRows < Le;
+    __shared__ int s_live;
+    int first = nchunks;
+    if (valid) {
+        const unsigned char *base = panel + off[m] + (size_t)tile * nchunks * kChunkPanel;
+        for (int c = 0; c < nchunks; ++c) {
+            if (threadIdx.x == 0) s_live = 0;
+            __syncthreads();
+            // hi blocks of both parities (the lo parts are ~2^-8 smaller)
+            const __nv_bfloat16 *blkp = reinterpret_cast<const __nv_bfloat16 *>(base + (size_t)c * kChunkPanel);
+            bool live = false;
+            for (int par = 0; par < 2; ++par) {
+                const __nv_bfloat16 *h = blkp + (size_t)(par * 2) * (kBlk / 2);
+                for (int i = threadIdx.x; i < kBlk / 2; i += blockDim.x) live |= fabsf(__bfloat162float(h[i])) >= thr;
+            }
+            if (live) s_live = 1;
+            __syncthreads();
+            const int any = s_live;
+            __syncthreads();
+            if (any) { first = c; break; }
+        }
+    }
+    if (threadIdx.x == 0) c0[m * ntiles + tile] = first;
+}
+
+__global__ void k_min_int(const int *__restrict__ a, const int *__restrict__ b, int *__restrict__ out, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = min(a[i], b[i]);
+}
+
 // Self-test of the timeout path: one thread waits on an mbarrier that nothing
 // will ever arrive on, with a bound of `max_ns`, exactly like the waits of the
-// tensor-core kernel, then records the timeout in the error word and returns.
+// tensor-core kernels, then records the timeout in the error word and returns.
 __global__ void k_selftest_timeout(int *err, unsigned long long max_ns)
 {
     __shared__ uint64_t bar;
@@ -374,15 +601,49 @@ __global__ void k_selftest_timeout(int *err, unsigned long long max_ns)
     if (!tc::mbar_wait_bounded(&bar, 0, max_ns)) raise_err(err, SHT_ETIMEOUT);
 }
 
-}  // namespace
+int cols_of(int batch) { return ((2 * batch + 31) / 32) * 32; }
 
-cudaError_t launch_selftest_timeout(int *err, unsigned long long max_ns, cudaStream_t st)
+template <typename K>
+cudaError_t launch_contraction(K kernel, bool synth, int lmax, int mmax, int npairs, int npanels, TcArgs &a,
+                               cudaStream_t st)
 {
-    k_selftest_timeout<<<1, 32, 0, st>>>(err, max_ns);
+    int stages = 4;
+    // scalar kernel: <= 110 KB so that two CTAs share an SM
+    const size_t cap = npanels == 1 ? 110 * 1024 : 200 * 1024;
+    while (stages > 2 && smem_bytes_of(npanels, a.rows, stages) > cap) --stages;
+    a.stages = stages;
+    const size_t smem = smem_bytes_of(npanels, a.rows, stages);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    int ts, ta;
+    tc_tile_counts(lmax, npairs, ts, ta);
+    a.ntiles = synth ? ts : ta;
+    const unsigned blocks = (unsigned)((mmax + 1) * a.ntiles);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<blocks, 128, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-// Sizes of the two panel sets and per-order byte offsets.
+cudaError_t launch_prep(bool synth, bool vec, int lmax, int mmax, int npairs, int nlm, int batch, int rows, Op op,
+                        const float *in0, const float *in1, const unsigned long long *dchunk, unsigned char *data,
+                        cudaStream_t st)
+{
+    const int Le0 = (lmax + 2) / 2;
+    const int maxch = synth ? (Le0 + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
+    dim3 g((unsigned)maxch, (unsigned)(mmax + 1));
+    k_tc_prep<<<g, 128, 0, st>>>(synth ? 1 : 0, vec ? 1 : 0, lmax, mmax, npairs, nlm, batch, rows, (int)op, in0, in1,
+                                 dchunk, data);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+int tc_max_batch() { return 64; }
+int tc_vec_max_batch() { return 32; }
+
 void tc_panel_layout(int lmax, int mmax, int npairs, std::vector<unsigned long long> &off_s,
                      std::vector<unsigned long long> &off_a, size_t &bytes_s, size_t &bytes_a,
                      std::vector<unsigned long long> &dchunk, size_t &nchunk_s)
@@ -390,10 +651,9 @@ void tc_panel_layout(int lmax, int mmax, int npairs, std::vector<unsigned long l
     off_s.assign(mmax + 1, 0);
     off_a.assign(mmax + 1, 0);
     dchunk.assign(mmax + 1, 0);
-    unsigned long long ch = 0;
     const int T = (npairs + kRows - 1) / kRows;
     const int kch = (npairs + kKc - 1) / kKc;
-    unsigned long long s = 0, q = 0;
+    unsigned long long s = 0, q = 0, ch = 0;
     for (int m = 0; m <= mmax; ++m) {
         const int L = lmax - m + 1, Le = (L + 1) / 2;
         const int nch = (Le + kKc - 1) / kKc;
@@ -401,93 +661,140 @@ void tc_panel_layout(int lmax, int mmax, int npairs, std::vector<unsigned long l
         off_s[m] = s;
         off_a[m] = q;
         dchunk[m] = ch;
-        ch += (unsigned long long)nch;
         s += (unsigned long long)T * nch * kChunkPanel;
         q += (unsigned long long)Mt * kch * kChunkPanel;
+        ch += (unsigned long long)nch;
     }
     bytes_s = s;
     bytes_a = q;
     nchunk_s = (size_t)ch;
 }
 
-// Bytes of the data-operand buffer for a batch: synthesis and analysis layouts.
-size_t tc_data_bytes(int lmax, int mmax, int npairs, size_t nchunk_s, int batch)
+size_t tc_data_bytes(int mmax, int npairs, size_t nchunk_s, int batch, bool vec)
 {
-    const int nc = ((2 * batch + 31) / 32) * 32;
+    const int rows = vec ? 2 * cols_of(batch) : cols_of(batch);
     const size_t kch = (size_t)(npairs + kKc - 1) / kKc;
-    const size_t a = (size_t)(mmax + 1) * kch;
-    return (nchunk_s > a ? nchunk_s : a) * tc_data_chunk(nc);
+    const size_t an = (size_t)(mmax + 1) * kch;
+    return (nchunk_s > an ? nchunk_s : an) * data_chunk_bytes(rows);
 }
 
 cudaError_t launch_build_panels(const PlanView<double> &pv, const unsigned long long *off_s,
-                                const unsigned long long *off_a, unsigned char *ps, unsigned char *pa,
+                                const unsigned long long *off_a, unsigned char *ps, unsigned char *pa, bool deriv,
                                 cudaStream_t st)
 {
     dim3 grid((unsigned)((pv.npairs + 127) / 128), (unsigned)(pv.mmax + 1));
-    k_build_panels<<<grid, 128, 0, st>>>(pv, off_s, off_a, ps, pa);
+    k_build_panels<<<grid, 128, 0, st>>>(pv, off_s, off_a, ps, pa, deriv ? 1 : 0);
     return cudaGetLastError();
 }
 
-// Columns of the data operand: 2 per field, rounded up to 32 (N of the MMA).
-static int tc_cols(int batch) { return ((2 * batch + 31) / 32) * 32; }
+cudaError_t launch_min_int(const int *a, const int *b, int *out, int n, cudaStream_t st)
+{
+    k_min_int<<<(n + 255) / 256, 256, 0, st>>>(a, b, out, n);
+    return cudaGetLastError();
+}
 
-int tc_max_batch() { return 64; }
+cudaError_t launch_selftest_timeout(int *err, unsigned long long max_ns, cudaStream_t st)
+{
+    k_selftest_timeout<<<1, 32, 0, st>>>(err, max_ns);
+    return cudaGetLastError();
+}
+
+void tc_tile_counts(int lmax, int npairs, int &ntiles_s, int &ntiles_a)
+{
+    ntiles_s = (npairs + kRows - 1) / kRows;
+    ntiles_a = (((lmax + 2) / 2) + kRows - 1) / kRows;
+}
+
+cudaError_t tc_polar_stats(int lmax, int mmax, int npairs, const int *d_c0_s, const int *d_c0_a, double &frac_s,
+                           double &frac_a)
+{
+    int T_s, T_a;
+    tc_tile_counts(lmax, npairs, T_s, T_a);
+    std::vector<int> c0s((size_t)(mmax + 1) * T_s), c0a((size_t)(mmax + 1) * T_a);
+    cudaError_t e = cudaMemcpy(c0s.data(), d_c0_s, sizeof(int) * c0s.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(c0a.data(), d_c0_a, sizeof(int) * c0a.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    double sk_s = 0, tot_s = 0, sk_a = 0, tot_a = 0;
+    const int kch = (npairs + kKc - 1) / kKc;
+    for (int m = 0; m <= mmax; ++m) {
+        const int Le = (lmax - m + 2) / 2, nch = (Le + kKc - 1) / kKc;
+        for (int t = 0; t < T_s; ++t) { sk_s += c0s[(size_t)m * T_s + t]; tot_s += nch; }
+        for (int t = 0; t < T_a; ++t)
+            if (t * kRows < Le) { sk_a += c0a[(size_t)m * T_a + t]; tot_a += kch; }
+    }
+    frac_s = tot_s > 0 ? sk_s / tot_s : 0.0;
+    frac_a = tot_a > 0 ? sk_a / tot_a : 0.0;
+    return cudaSuccess;
+}
+
+cudaError_t launch_panel_first_live(bool synth, int lmax, int mmax, int npairs, const unsigned long long *off,
+                                    const unsigned char *panel, float thr, int *c0, int &ntiles, cudaStream_t st)
+{
+    int ts, ta;
+    tc_tile_counts(lmax, npairs, ts, ta);
+    ntiles = synth ? ts : ta;
+    dim3 g((unsigned)ntiles, (unsigned)(mmax + 1));
+    k_panel_first_live<<<g, 128, 0, st>>>(synth ? 1 : 0, lmax, npairs, ntiles, off, panel, thr, c0);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
-                               const unsigned long long *off, const unsigned long long *dchunk,
+                               const unsigned long long *off, const int *c0, const unsigned long long *dchunk,
                                unsigned char *data, const float *in, float *out, int batch, Op op, int *err,
                                cudaStream_t st)
 {
-    // data operand in the blocked bf16 layout
-    {
-        const int Le0 = (lmax + 2) / 2;
-        const int maxch = synth ? (Le0 + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
-        dim3 g((unsigned)maxch, (unsigned)(mmax + 1));
-        k_tc_prep<<<g, 128, 0, st>>>(synth ? 1 : 0, lmax, mmax, npairs, nlm, batch, ((2 * batch + 31) / 32) * 32,
-                                    (int)op, in, dchunk, data);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    TcArgs a;
+    if (batch < 1 || batch > tc_max_batch()) return cudaErrorInvalidValue;
+    const int rows = cols_of(batch);
+    cudaError_t e = launch_prep(synth, false, lmax, mmax, npairs, nlm, batch, rows, op, in, nullptr, dchunk, data, st);
+    if (e != cudaSuccess) return e;
+    TcArgs a{};
     a.lmax = lmax;
     a.mmax = mmax;
     a.npairs = npairs;
     a.nlm = nlm;
     a.batch = batch;
-    a.nc = tc_cols(batch);
+    a.rows = rows;
     a.op = (int)op;
     a.panel = panel;
     a.off = off;
+    a.c0 = c0;
     a.data = data;
     a.dchunk = dchunk;
-    a.out = out;
+    a.out0 = out;
     a.err = err;
-    if (a.nc > 256) return cudaErrorInvalidValue;
-    int stages = 4;
-    while (stages > 2 && tc_smem_bytes(a.nc, stages) > 200 * 1024) --stages;
-    a.stages = stages;
-    const size_t smem = tc_smem_bytes(a.nc, stages);
-    unsigned blocks;
-    if (synth) {
-        a.ntiles = (npairs + kRows - 1) / kRows;
-        blocks = (unsigned)((mmax + 1) * a.ntiles);
-    } else {
-        // analysis tiles run over degrees; the largest order count (m = 0) sets the tile count
-        const int Le0 = (lmax + 2) / 2;
-        a.ntiles = (Le0 + kRows - 1) / kRows;
-        blocks = (unsigned)((mmax + 1) * a.ntiles);
-    }
-    cudaError_t e;
-    if (synth) {
-        e = cudaFuncSetAttribute(k_tc_legendre<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_tc_legendre<true><<<blocks, 128, smem, st>>>(a);
-    } else {
-        e = cudaFuncSetAttribute(k_tc_legendre<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_tc_legendre<false><<<blocks, 128, smem, st>>>(a);
-    }
-    return cudaGetLastError();
+    return synth ? launch_contraction(k_tc_legendre<true>, true, lmax, mmax, npairs, 1, a, st)
+                 : launch_contraction(k_tc_legendre<false>, false, lmax, mmax, npairs, 1, a, st);
+}
+
+cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
+                          const unsigned char *dpanel, const unsigned long long *off, const int *c0,
+                          const unsigned long long *dchunk, unsigned char *data, const float *in0, const float *in1,
+                          float *out0, float *out1, const float *st_pairs, int batch, Op op, int *err, cudaStream_t st)
+{
+    if (batch < 1 || batch > tc_vec_max_batch()) return cudaErrorInvalidValue;
+    const int rows = 2 * cols_of(batch);   // 4 accumulators x rows columns <= 512
+    cudaError_t e = launch_prep(synth, true, lmax, mmax, npairs, nlm, batch, rows, op, in0, in1, dchunk, data, st);
+    if (e != cudaSuccess) return e;
+    TcArgs a{};
+    a.lmax = lmax;
+    a.mmax = mmax;
+    a.npairs = npairs;
+    a.nlm = nlm;
+    a.batch = batch;
+    a.rows = rows;
+    a.op = (int)op;
+    a.panel = panel;
+    a.dpanel = dpanel;
+    a.off = off;
+    a.c0 = c0;
+    a.data = data;
+    a.dchunk = dchunk;
+    a.out0 = out0;
+    a.out1 = out1;
+    a.st = st_pairs;
+    a.err = err;
+    return synth ? launch_contraction(k_tc_vec<true>, true, lmax, mmax, npairs, 2, a, st)
+                 : launch_contraction(k_tc_vec<false>, false, lmax, mmax, npairs, 2, a, st);
 }
 
 }  // namespace sht

@@ -30,7 +30,7 @@ class SHT:
                  nphi: int | None = None, device=None, fp32_path: str = "f32"):
         """fp32_path selects how complex64/float32 tensors are transformed:
         "f32" (FP32 recurrence on the CUDA cores) or "tc" (tensor cores against
-        FP64-built P_n^m panels, split-bf16 products, scalar transforms only)."""
+        FP64-built P_n^m panels, split-bf16 products)."""
         self.lmax = int(lmax)
         self.mmax = self.lmax if mmax is None else int(mmax)
         self.nlat = self.lmax + 1 if nlat is None else int(nlat)

@@ -2,8 +2,9 @@
 
 The per-order Legendre contraction runs on tcgen05 against P_n^m panels
 built once by the FP64 recurrence; data are FP32.  Cases cover several
-128-row tiles and ragged tails, mmax < lmax, odd nlat, and sampled rows/
-orders of the full N = 1023, batch 16 workload."""
+128-row tiles and ragged tails, mmax < lmax, odd nlat, batches split into
+several chunks, the vector transforms, and sampled rows/orders of the full
+N = 1023, batch 16 scalar and N = 511, batch 64 vector workloads."""
 import numpy as np
 import pytest
 
@@ -111,9 +112,87 @@ def test_tc_deterministic(SHT):
     assert torch.equal(g1, g2)
 
 
-def test_tc_vector_is_unsupported(SHT):
-    from paper_1202_6522_gb300._capi import SHTError
-    sht = SHT(15, 15, 16, 32, fp32_path="tc")
-    S = _dev(_spec(15, 15, 1, 0))
-    with pytest.raises(SHTError):
-        sht.synth_vec_(S, S)
+VEC_CASES = [
+    (7, 7, 8, 16, 2),
+    (31, 20, 40, 64, 2),
+    (40, 40, 41, 128, 3),
+    (255, 255, 256, 512, 16),
+    (100, 100, 101, 256, 40),   # two chunks of at most 32 fields; 64 + 64 data columns
+]
+VEC_IDS = [f"N{c[0]}m{c[1]}lat{c[2]}phi{c[3]}b{c[4]}" for c in VEC_CASES]
+
+
+@pytest.mark.parametrize("case", VEC_CASES, ids=VEC_IDS)
+def test_tc_vector_synthesis_and_analysis(SHT, case):
+    """Spheroidal/toroidal transforms with P and sin(theta) dP/dtheta panels."""
+    lmax, mmax, nlat, nphi, batch = case
+    sht = SHT(lmax, mmax, nlat, nphi, fp32_path="tc")
+    S = synthetic.spectrum(lmax, mmax, batch=batch, seed=4, power=1.5).astype(np.complex64).astype(np.complex128)
+    T = synthetic.spectrum(lmax, mmax, batch=batch, seed=5, power=1.5).astype(np.complex64).astype(np.complex128)
+    vt, vp = sht.synth_vec_(_dev(S), _dev(T))
+    rt, rp = oracle.synth_vec(lmax, mmax, nlat, nphi, S, T)
+    assert normwise(_np(vt), rt) < tc_bound(lmax)
+    assert normwise(_np(vp), rp) < tc_bound(lmax)
+    gt = _grid(nlat, nphi, batch, 6)
+    gp = _grid(nlat, nphi, batch, 7)
+    S2, T2 = sht.analys_vec_(_dev(gt), _dev(gp))
+    rS, rT = oracle.analys_vec(lmax, mmax, nlat, nphi, gt, gp)
+    assert normwise(_np(S2), rS) < tc_bound(lmax)
+    assert normwise(_np(T2), rT) < tc_bound(lmax)
+    assert sht.sync_status() == 0
+
+
+@pytest.mark.parametrize("case", VEC_CASES[:3], ids=VEC_IDS[:3])
+def test_tc_vector_adjoints(SHT, case):
+    lmax, mmax, nlat, nphi, batch = case
+    sht = SHT(lmax, mmax, nlat, nphi, fp32_path="tc")
+    gt = _grid(nlat, nphi, batch, 8)
+    gp = _grid(nlat, nphi, batch, 9)
+    S, T = sht.synth_vec_adj_(_dev(gt), _dev(gp))
+    rS, rT = oracle.synth_vec_adj(lmax, mmax, nlat, nphi, gt, gp)
+    assert normwise(_np(S), rS) < tc_bound(lmax)
+    assert normwise(_np(T), rT) < tc_bound(lmax)
+    A = _spec(lmax, mmax, batch, 10)
+    B = _spec(lmax, mmax, batch, 11)
+    ht, hp = sht.analys_vec_adj_(_dev(A), _dev(B))
+    rt, rp = oracle.analys_vec_adj(lmax, mmax, nlat, nphi, A, B)
+    assert normwise(_np(ht), rt) < tc_bound(lmax)
+    assert normwise(_np(hp), rp) < tc_bound(lmax)
+
+
+def test_tc_vector_full_size_n511_b64_sampled(SHT):
+    """The vector workload (N = 511, 512 x 1024 grid, 64 fields) on sampled
+    rows and orders of the oracle."""
+    lmax, nlat, nphi, batch = 511, 512, 1024, 64
+    sht = SHT(lmax, lmax, nlat, nphi, fp32_path="tc")
+    S = synthetic.spectrum(lmax, batch=batch, seed=4, power=1.5).astype(np.complex64).astype(np.complex128)
+    T = synthetic.spectrum(lmax, batch=batch, seed=5, power=1.5).astype(np.complex64).astype(np.complex128)
+    vt, vp = sht.synth_vec_(_dev(S), _dev(T))
+    vt, vp = _np(vt), _np(vp)
+    rows = [0, 1, 127, 255, 256, 400, 511]
+    for b in (0, 33, 63):
+        rt, rp = oracle.synth_vec(lmax, lmax, nlat, nphi, S[b], T[b], rows=rows)
+        assert normwise(vt[b][rows], rt[rows]) < tc_bound(lmax), b
+        assert normwise(vp[b][rows], rp[rows]) < tc_bound(lmax), b
+    gt = _grid(nlat, nphi, batch, 6)
+    gp = _grid(nlat, nphi, batch, 7)
+    S2, T2 = sht.analys_vec_(_dev(gt), _dev(gp))
+    S2, T2 = _np(S2), _np(T2)
+    ms = [0, 1, 200, 510, 511]
+    idx = np.concatenate([[oracle.lm_index(lmax, n, m) for n in range(m, lmax + 1)] for m in ms])
+    for b in (0, 40):
+        rS, rT = oracle.analys_vec(lmax, lmax, nlat, nphi, gt[b], gp[b], ms=ms)
+        assert normwise(S2[b][idx], rS[idx]) < tc_bound(lmax), b
+        assert normwise(T2[b][idx], rT[idx]) < tc_bound(lmax), b
+    assert sht.sync_status() == 0
+
+
+def test_tc_static_polar_skip_fraction(SHT):
+    """Sec. 3.1 polar optimisation: at N = 1023 a share of the panel chunks holds
+    only values below 2^-40 and is skipped; results above stay within the bound."""
+    from paper_1202_6522_gb300 import _capi as C
+    sht = SHT(1023, 1023, 1024, 2048, fp32_path="tc")
+    assert C.sht_tc_polar_skip(sht._h) == (-1.0, -1.0)
+    sht.synth_(_dev(_spec(1023, 1023, 1, 0)))
+    fs, fa = C.sht_tc_polar_skip(sht._h)
+    assert 0.02 < fs < 0.5 and 0.02 < fa < 0.5, (fs, fa)
