@@ -54,13 +54,14 @@ def legendre_flops_per_launch(batch, lmax=LMAX, nlat=NLAT):
     return nlm_of(lmax) * npairs * (4.0 + 4.0 * batch)
 
 
-def tc_algorithmic_bytes(batch, lmax=LMAX, nlat=NLAT):
+def tc_algorithmic_bytes(batch, lmax=LMAX, nlat=NLAT, polar_skip=0.0):
     """Bytes one tensor-core Legendre launch must move: every P_n^m(x_j) of one
     hemisphere as a bf16 hi+lo pair (4 B; the library's tile padding is not
-    counted), the FP32 spectra of the batch and the FP32 E/O (or s/d)
-    intermediate of the batch."""
+    counted) less the share the polar optimisation of Sec. 3.1 leaves out,
+    the FP32 spectra of the batch and the FP32 E/O (or s/d) intermediate of
+    the batch."""
     npairs = (nlat + 1) // 2
-    panel = nlm_of(lmax) * npairs * 4
+    panel = nlm_of(lmax) * npairs * 4 * (1.0 - polar_skip)
     spec = batch * nlm_of(lmax) * 8
     inter = batch * (lmax + 1) * npairs * 16
     return panel + spec + inter
@@ -307,6 +308,60 @@ def round_trip_errors(sht, torch, dev, cdt):
     return {"eps_max": float(d.max()), "eps_rms": float(np.sqrt(2.0 / ((LMAX + 1) * (LMAX + 2)) * np.sum(d * d)))}
 
 
+def accuracy_vs_n(torch, dev, sizes=(255, 511, 1023, 2047, 4095)):
+    """The Sec. 3.5 error measures of one round trip of uniform [-1, 1] spectra
+    against N (nlat = N + 1, nphi = 2 (N + 1)), for the FP64 path, the FP32
+    recurrence and (N <= 2047) the tensor-core path: the analogue of the
+    paper's error-versus-N study (its 1e-11 target is for N < 2048)."""
+    import numpy as np
+    from paper_1202_6522_gb300 import SHT, synthetic
+    out = {}
+    for n in sizes:
+        Q = synthetic.spectrum(n, seed=0, uniform=True)
+        row = {}
+        for path, cdt, fp32_path in (("f64", torch.complex128, "f32"), ("f32", torch.complex64, "f32"),
+                                     ("tc", torch.complex64, "tc")):
+            if path == "tc" and n > 2047:
+                continue
+            sht = SHT(n, n, n + 1, 2 * (n + 1), device=dev, fp32_path=fp32_path)
+            Qd = torch.from_numpy(Q).to(dev, cdt)
+            R = sht.analys_(sht.synth_(Qd)).cpu().numpy().astype(np.complex128)
+            d = np.abs(R - Qd.cpu().numpy().astype(np.complex128))
+            row[path] = {"eps_max": float(d.max()),
+                         "eps_rms": float(np.sqrt(2.0 / ((n + 1) * (n + 2)) * np.sum(d * d)))}
+            del sht, Qd
+            torch.cuda.empty_cache()
+        out[str(n)] = row
+    return out
+
+
+def n511_config(torch, dev, steps=20):
+    """Scalar round trips per second at N = 511 (nlat 512, nphi 1024), batch
+    16, on the three paths (the metric's second size)."""
+    from paper_1202_6522_gb300 import SHT, synthetic
+    out = {"workload": "scalar SHT round trip N=511 nlat=512 nphi=1024 batch=16"}
+    a_np = synthetic.spectrum(511, batch=16, seed=0)
+    for path, cdt, fp32_path in (("f64", torch.complex128, "f32"), ("f32", torch.complex64, "f32"),
+                                 ("tc", torch.complex64, "tc")):
+        sht = SHT(511, 511, 512, 1024, device=dev, fp32_path=fp32_path)
+        a = torch.from_numpy(a_np).to(dev, cdt)
+        n = max(3, steps // 5) if path == "f64" else steps
+        for _ in range(3):
+            sht.analys_(sht.synth_(a))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            sht.analys_(sht.synth_(a))
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        out[path] = {"ms_per_step": ms, "round_trips_per_s": 16 / (ms / 1e3)}
+        del sht, a
+    return out
+
+
 def time_path(sht, torch, a, steps, warmup, stream, profile=False):
     """Device-timed round trips on inputs resident in HBM.  Returns (ms per step, kernel table)."""
     from paper_1202_6522_gb300 import _capi as C
@@ -356,6 +411,13 @@ def run_ours(args):
         sht.fp32_mode = C.SHT_F32_AUTO
         tune_report = {"f32_round_trip_ms": f32_ms, "tc_round_trip_ms": tc_ms,
                        "chosen": "tc" if (tc_ms > 0 and tc_ms < f32_ms) else "f32"}
+    # measured FMA throughput: the ALU roofline denominators (FP32 and FP64)
+    alu_peaks = None
+    try:
+        from paper_1202_6522_gb300 import _capi as C
+        alu_peaks = C.sht_alu_peaks(stream.cuda_stream)
+    except Exception:
+        alu_peaks = None
     cdt = torch.complex128 if args.mode == "f64" else torch.complex64
     a_np = synthetic.spectrum(LMAX, batch=BATCH, seed=rank)
     a = torch.from_numpy(a_np).to(dev, cdt)
@@ -457,6 +519,8 @@ def run_ours(args):
     if rank == 0 and not args.no_uneven:
         extra["vector"] = vector_config(torch, dev)
         extra["differentiable"] = differentiable_config(sht, torch, dev, cdt)
+        extra["n511"] = n511_config(torch, dev)
+        extra["accuracy_vs_n"] = accuracy_vs_n(torch, dev)
 
     # --- the plain FP64 path on the same workload (the metric's denominator) ---
     fp64 = None
@@ -476,22 +540,30 @@ def run_ours(args):
     sm_max = clk.get("sm_max_mhz") or 2070.0
     if dom_name.startswith("tc_"):
         # the panels stream from HBM once per launch: bytes bound the kernel
-        algo = tc_algorithmic_bytes(BATCH)
+        from paper_1202_6522_gb300 import _capi as C
+        skip_s, skip_a = C.sht_tc_polar_skip(sht._h)
+        algo = tc_algorithmic_bytes(BATCH, polar_skip=max(0.0, skip_a if dom_name == "tc_analys" else skip_s))
         peaks = read_peaks()
         peak = peaks.get("hbm_gbs", 6800.0) * 1e9
         achieved = algo / (dom_avg / 1e3)
         roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved / 1e9, "peak": peak / 1e9,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
-                "algorithmic_bytes": algo, "kernel_avg_ms": dom_avg, "launches": dom_n}
+                "algorithmic_bytes": algo, "kernel_avg_ms": dom_avg, "launches": dom_n,
+                "polar_skip": {"synth": skip_s, "analys": skip_a}}
     else:
         flops = legendre_flops_per_launch(BATCH) if dom_name.startswith("legendre") else None
         if args.mode == "f32":
-            peak = fp32_alu_peak(sm_max)
-            peak_note = f"FP32 FMA: 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz"
+            if alu_peaks:
+                peak, peak_note = alu_peaks[0] * 1e12, "measured FP32 FMA throughput (sht_alu_peaks)"
+            else:
+                peak = fp32_alu_peak(sm_max)
+                peak_note = f"FP32 FMA: 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz"
         else:
-            peak = FP64_PEAK_NOMINAL
-            peak_note = "FP64 nominal 1.25 TFLOP/s"
+            if alu_peaks:
+                peak, peak_note = alu_peaks[1] * 1e12, "measured FP64 FMA throughput (sht_alu_peaks)"
+            else:
+                peak, peak_note = FP64_PEAK_NOMINAL, "FP64 nominal 1.25 TFLOP/s"
         achieved = flops / (dom_avg / 1e3) if flops else None
         roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved / 1e12 if achieved else None,
                 "peak": peak / 1e12, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
@@ -499,7 +571,8 @@ def run_ours(args):
                 "kernel_avg_ms": dom_avg, "launches": dom_n}
     kernels = {k: {"avg_ms": v[0] / v[1], "launches": v[1], "share": v[0] / sum(x[0] for x in table.values())}
                for k, v in table.items()}
-    launches = sum(v[1] for v in table.values())
+    # each tensor-core launch is two kernels (operand prep + contraction)
+    launches = sum(v[1] * (2 if k.startswith("tc_") else 1) for k, v in table.items())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -524,6 +597,8 @@ def run_ours(args):
     }
     if tune_report:
         line["tuning"] = tune_report
+    if alu_peaks:
+        line["alu_peaks_measured"] = {"fp32_tflops": alu_peaks[0], "fp64_tflops": alu_peaks[1]}
     if ubatch:
         line["uneven_batch"] = ubatch
     line.update(extra)
@@ -542,7 +617,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["auto", "tc", "f32", "f64"], default="auto")

@@ -236,12 +236,26 @@ SHT_API const char *sht_kernel_name(int kind);
  * skipped, or -1 if the panels are not built yet. */
 SHT_API int sht_tc_polar_skip(sht_handle h, double *synth_frac, double *analys_frac);
 
+/* Threshold of that optimisation (the paper leaves its value open; default
+ * 2^-40): a panel chunk is skipped while all its |P_n^m| (and, for the vector
+ * transforms, |sin(theta) dP/dtheta|) are below it.  0 skips nothing.  Must
+ * be in [0, 1]; waits for the device to be idle, then recomputes the skip
+ * tables if the panels exist. */
+SHT_API int sht_set_polar_threshold(sht_handle h, double threshold);
+
 /* Failure-detection self-test (no counterpart in the paper): enqueue a kernel
  * that waits, with a bound of timeout_us microseconds, on a barrier that
  * nothing completes -- the same bounded wait the tensor-core kernels use --
  * so that the next sht_sync_status on that stream reports SHT_ETIMEOUT.  The
  * kernel never faults or hangs, and the handle stays usable afterwards. */
 SHT_API int sht_selftest_timeout(sht_handle h, int timeout_us, void *stream);
+
+/* Measured FMA throughput of the current device (no counterpart in the paper;
+ * the denominators of the ALU rooflines of the on-the-fly Legendre kernels):
+ * 8 independent FMA chains per thread, 8 CTAs of 256 threads per SM, timed
+ * with CUDA events on `stream` (which it synchronises).  Writes FP32 and FP64
+ * TFLOP/s (an FMA counts 2 flops) at the clock the GPU runs at. */
+SHT_API int sht_alu_peaks(double *fp32_tflops, double *fp64_tflops, void *stream);
 
 /* Message for the last error raised in the calling thread ("" if none). */
 SHT_API const char *sht_last_error(void);

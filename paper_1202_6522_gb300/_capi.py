@@ -55,6 +55,8 @@ SIGNATURES = {
     "sht_batch_analys": ([_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP], _I),
     "sht_tune": ([_VP, _I, _I, ctypes.POINTER(ctypes.c_double), _VP], _I),
     "sht_selftest_timeout": ([_VP, _I, _VP], _I),
+    "sht_set_polar_threshold": ([_VP, ctypes.c_double], _I),
+    "sht_alu_peaks": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _VP], _I),
     "sht_tc_polar_skip": ([_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], _I),
     "sht_profile": ([_VP, _I], _I),
     "sht_profile_read": ([_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I), _I], _I),
@@ -224,8 +226,19 @@ def sht_tc_polar_skip(h):
     return a.value, b.value
 
 
+def sht_set_polar_threshold(h, threshold):
+    return check(_call("sht_set_polar_threshold", h, float(threshold)))
+
+
 def sht_selftest_timeout(h, timeout_us, stream):
     return check(_call("sht_selftest_timeout", h, timeout_us, stream))
+
+
+def sht_alu_peaks(stream):
+    """Measured (FP32, FP64) FMA throughput in TFLOP/s."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    check(_call("sht_alu_peaks", ctypes.byref(a), ctypes.byref(b), stream))
+    return a.value, b.value
 
 
 def sht_profile(h, enable):

@@ -54,6 +54,40 @@ void free_panels(sht::Plan &p)
     p.d_c0_s = p.d_c0_a = nullptr;
 }
 
+// Static polar optimisation (Sec. 3.1): per (m, tile) the first panel chunk
+// holding a value >= the plan's threshold; the fractions skipped.
+cudaError_t first_live_scalar(sht::Plan &p)
+{
+    int ts = 0, ta = 0;
+    cudaError_t e = sht::launch_panel_first_live(true, p.lmax, p.mmax, p.npairs, p.d_off_s, p.panel_s, p.polar_thr,
+                                                 p.d_c0_s, ts, 0);
+    if (e == cudaSuccess)
+        e = sht::launch_panel_first_live(false, p.lmax, p.mmax, p.npairs, p.d_off_a, p.panel_a, p.polar_thr,
+                                         p.d_c0_a, ta, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = sht::tc_polar_stats(p.lmax, p.mmax, p.npairs, p.d_c0_s, p.d_c0_a, p.polar_skip_s, p.polar_skip_a);
+    return e;
+}
+
+// Vector transforms: the first chunk live in P or in dP (tmp: scratch of
+// (mmax+1) * max(tiles) ints; the scalar tables must be current).
+cudaError_t first_live_vector(sht::Plan &p, int *tmp)
+{
+    int T_s = 0, T_a = 0, nt = 0;
+    sht::tc_tile_counts(p.lmax, p.npairs, T_s, T_a);
+    const int ns = (p.mmax + 1) * T_s, na = (p.mmax + 1) * T_a;
+    cudaError_t e = sht::launch_panel_first_live(true, p.lmax, p.mmax, p.npairs, p.d_off_s, p.dpanel_s, p.polar_thr,
+                                                 tmp, nt, 0);
+    if (e == cudaSuccess) e = sht::launch_min_int(p.d_c0_s, tmp, p.d_c0v_s, ns, 0);
+    if (e == cudaSuccess)
+        e = sht::launch_panel_first_live(false, p.lmax, p.mmax, p.npairs, p.d_off_a, p.dpanel_a, p.polar_thr, tmp,
+                                         nt, 0);
+    if (e == cudaSuccess) e = sht::launch_min_int(p.d_c0_a, tmp, p.d_c0v_a, na, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return e;
+}
+
 // Build the tensor-core panels once (allocates about (lmax+1)^3 bytes): the
 // P_n^m panels in both operand layouts, per-order offsets, and the first
 // chunk above the polar threshold of every (m, tile).
@@ -86,17 +120,7 @@ int ensure_panels(sht::Plan &p)
     if (e == cudaSuccess) e = cudaMemset(p.panel_a, 0, ba);
     if (e == cudaSuccess)
         e = sht::launch_build_panels(p.view64(), p.d_off_s, p.d_off_a, p.panel_s, p.panel_a, false, 0);
-    // static polar optimisation: first chunk above the threshold per (m, tile)
-    int ts = 0, ta = 0;
-    if (e == cudaSuccess)
-        e = sht::launch_panel_first_live(true, p.lmax, p.mmax, p.npairs, p.d_off_s, p.panel_s, sht::kPolarThreshold,
-                                         p.d_c0_s, ts, 0);
-    if (e == cudaSuccess)
-        e = sht::launch_panel_first_live(false, p.lmax, p.mmax, p.npairs, p.d_off_a, p.panel_a, sht::kPolarThreshold,
-                                         p.d_c0_a, ta, 0);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e == cudaSuccess)
-        e = sht::tc_polar_stats(p.lmax, p.mmax, p.npairs, p.d_c0_s, p.d_c0_a, p.polar_skip_s, p.polar_skip_a);
+    if (e == cudaSuccess) e = first_live_scalar(p);
     if (e != cudaSuccess) {
         free_panels(p);
         return fail(SHT_ECUDA, std::string("building tensor-core panels: ") + cudaGetErrorString(e));
@@ -140,16 +164,7 @@ int ensure_vec_panels(sht::Plan &p)
     if (e == cudaSuccess) e = cudaMemset(p.dpanel_a, 0, ba);
     if (e == cudaSuccess)
         e = sht::launch_build_panels(p.view64(), p.d_off_s, p.d_off_a, p.dpanel_s, p.dpanel_a, true, 0);
-    int nt = 0;
-    if (e == cudaSuccess)
-        e = sht::launch_panel_first_live(true, p.lmax, p.mmax, p.npairs, p.d_off_s, p.dpanel_s, sht::kPolarThreshold,
-                                         tmp, nt, 0);
-    if (e == cudaSuccess) e = sht::launch_min_int(p.d_c0_s, tmp, p.d_c0v_s, (int)ns, 0);
-    if (e == cudaSuccess)
-        e = sht::launch_panel_first_live(false, p.lmax, p.mmax, p.npairs, p.d_off_a, p.dpanel_a, sht::kPolarThreshold,
-                                         tmp, nt, 0);
-    if (e == cudaSuccess) e = sht::launch_min_int(p.d_c0_a, tmp, p.d_c0v_a, (int)na, 0);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = first_live_vector(p, tmp);
     cudaFree(tmp);
     if (e != cudaSuccess) {
         free_vec_panels(p);
@@ -435,7 +450,7 @@ int run_synth_tc(sht::Plan &p, const void *spec, void *grid, int batch, sht::Op 
         float *out = static_cast<float *>(grid) + (size_t)b0 * p.nlat * p.nphi;
         int rc = timed(p, SHT_K_TC_SYNTH, s, "tensor-core synthesis launch", [&] {
             return sht::launch_tc_legendre(true, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_s, p.d_off_s, p.d_c0_s,
-                                           p.d_dchunk, data, in, eo, nb, op, p.d_err, s);
+                                           p.d_dchunk, data, in, eo, nb, op, p.d_err, false, s);
         });
         if (rc) return rc;
         rc = timed(p, SHT_K_FFT_SYNTH, s, "fft synthesis launch",
@@ -459,7 +474,7 @@ int run_analys_tc(sht::Plan &p, const void *grid, void *spec, int batch, sht::Op
         if (rc) return rc;
         rc = timed(p, SHT_K_TC_ANALYS, s, "tensor-core analysis launch", [&] {
             return sht::launch_tc_legendre(false, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_a, p.d_off_a, p.d_c0_a,
-                                           p.d_dchunk, data, sd, out, nb, op, p.d_err, s);
+                                           p.d_dchunk, data, sd, out, nb, op, p.d_err, false, s);
         });
         if (rc) return rc;
     }
@@ -480,7 +495,8 @@ int run_synth_vec_tc(sht::Plan &p, const void *S, const void *T, void *vt, void 
         int rc = timed(p, SHT_K_TC_SYNTH_VEC, s, "tensor-core vector synthesis launch", [&] {
             return sht::launch_tc_vec(true, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_s, p.dpanel_s, p.d_off_s,
                                       p.d_c0v_s, p.d_dchunk, data, static_cast<const float *>(S) + so,
-                                      static_cast<const float *>(T) + so, eot, eop, p.t32.st, nb, op, p.d_err, s);
+                                      static_cast<const float *>(T) + so, eot, eop, p.t32.st, nb, op, p.d_err, false,
+                                      s);
         });
         if (rc) return rc;
         rc = timed(p, SHT_K_FFT_SYNTH, s, "fft synthesis launch", [&] {
@@ -517,7 +533,7 @@ int run_analys_vec_tc(sht::Plan &p, const void *vt, const void *vp, void *S, voi
         rc = timed(p, SHT_K_TC_ANALYS_VEC, s, "tensor-core vector analysis launch", [&] {
             return sht::launch_tc_vec(false, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_a, p.dpanel_a, p.d_off_a,
                                       p.d_c0v_a, p.d_dchunk, data, sdt, sdp, static_cast<float *>(S) + so,
-                                      static_cast<float *>(T) + so, p.t32.st, nb, op, p.d_err, s);
+                                      static_cast<float *>(T) + so, p.t32.st, nb, op, p.d_err, false, s);
         });
         if (rc) return rc;
     }
@@ -652,6 +668,28 @@ int sht_tc_polar_skip(sht_handle h, double *synth_frac, double *analys_frac)
     if (!synth_frac || !analys_frac) return fail(SHT_EINVAL, "null output pointer");
     *synth_frac = h->p.panel_s ? h->p.polar_skip_s : -1.0;
     *analys_frac = h->p.panel_s ? h->p.polar_skip_a : -1.0;
+    return SHT_OK;
+}
+
+int sht_set_polar_threshold(sht_handle h, double threshold)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!(threshold >= 0.0) || threshold > 1.0) return fail(SHT_EINVAL, "polar threshold must be in [0, 1]");
+    sht::Plan &p = h->p;
+    p.polar_thr = (float)threshold;
+    if (!p.panel_s) return SHT_OK;
+    cudaError_t e = cudaDeviceSynchronize();   // no transform may be reading the tables
+    if (e == cudaSuccess) e = first_live_scalar(p);
+    if (e == cudaSuccess && p.dpanel_s) {
+        int T_s = 0, T_a = 0;
+        sht::tc_tile_counts(p.lmax, p.npairs, T_s, T_a);
+        int *tmp = nullptr;
+        e = cudaMalloc(&tmp, sizeof(int) * (size_t)(p.mmax + 1) * (T_s > T_a ? T_s : T_a));
+        if (e == cudaSuccess) e = first_live_vector(p, tmp);
+        cudaFree(tmp);
+    }
+    if (e != cudaSuccess) return fail(SHT_ECUDA, std::string("sht_set_polar_threshold: ") + cudaGetErrorString(e));
     return SHT_OK;
 }
 

@@ -37,19 +37,24 @@ template <typename T2> __device__ __forceinline__ T2 mul_i(T2 a) { return mk<T2>
 
 __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
 
-// cos/sin(2 pi k / 16), k = 0..7 (cos(pi/8) = sqrt(2 + sqrt 2)/2, sin(pi/8) = sqrt(2 - sqrt 2)/2)
-constexpr double kC1 = 0.92387953251128675613, kS1 = 0.38268343236508977173, kR2 = 0.70710678118654752440;
-__host__ __device__ constexpr double c16(int k)
+// cos(pi j / 32), j = 0..16
+__host__ __device__ constexpr double cospi32(int j)
 {
-    return k == 0 ? 1.0 : k == 1 ? kC1 : k == 2 ? kR2 : k == 3 ? kS1 : k == 4 ? 0.0 : k == 5 ? -kS1 : k == 6 ? -kR2 : -kC1;
+    return j == 0 ? 1.0 : j == 1 ? 0.99518472667219688624 : j == 2 ? 0.98078528040323044913
+         : j == 3 ? 0.95694033573220886494 : j == 4 ? 0.92387953251128675613 : j == 5 ? 0.88192126434835502971
+         : j == 6 ? 0.83146961230254523708 : j == 7 ? 0.77301045336273696081 : j == 8 ? 0.70710678118654752440
+         : j == 9 ? 0.63439328416364549822 : j == 10 ? 0.55557023301960222474 : j == 11 ? 0.47139673682599764856
+         : j == 12 ? 0.38268343236508977173 : j == 13 ? 0.29028467725446236764 : j == 14 ? 0.19509032201612826785
+         : j == 15 ? 0.09801714032956060199 : 0.0;
 }
-__host__ __device__ constexpr double s16(int k)
-{
-    return k == 0 ? 0.0 : k == 1 ? kS1 : k == 2 ? kR2 : k == 3 ? kC1 : k == 4 ? 1.0 : k == 5 ? kC1 : k == 6 ? kR2 : kS1;
-}
+// cos and sin of 2 pi k / 64 for any integer k (cos(a) = cos(-a), cos(pi - a) = -cos(a))
+__host__ __device__ constexpr double cos64_half(int k) { return k > 16 ? -cospi32(32 - k) : cospi32(k); }
+__host__ __device__ constexpr double cos64(int k) { return cos64_half((k & 63) > 32 ? 64 - (k & 63) : (k & 63)); }
+__host__ __device__ constexpr double sin64(int k) { return cos64(k - 16); }
 
-// In-register DFT of size RD (natural order in and out), split into even and
-// odd halves recursively.  SIGN = +1: e^{+2 pi i ...} (inverse), -1: forward.
+// In-register DFT of size RD <= 64 (natural order in and out), split into
+// even and odd halves recursively.  SIGN = +1: e^{+2 pi i ...} (inverse),
+// -1: forward.
 template <typename T2, int RD, int SIGN>
 struct RegDft {
     using T = decltype(T2::x);
@@ -62,8 +67,8 @@ struct RegDft {
         RegDft<T2, RD / 2, SIGN>::run(o);
 #pragma unroll
         for (int k = 0; k < RD / 2; ++k) {
-            const int q = k * (16 / RD);
-            const T2 w = mk<T2>(T(c16(q)), T(SIGN * s16(q)));
+            const int q = k * (64 / RD);
+            const T2 w = mk<T2>(T(cos64(q)), T(SIGN * sin64(q)));
             const T2 t = (k == 0) ? o[k] : cmul(w, o[k]);
             v[k] = cadd(e[k], t);
             v[k + RD / 2] = csub(e[k], t);
@@ -385,6 +390,257 @@ k_fft_analys(PlanView<T> pv, const T *__restrict__ grid, T *__restrict__ sd, int
     fft_analys_tile<T>(pv, grid, sd, blockIdx.y, blockIdx.x * G, G, logH, op, vector, smem_raw);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 row FFTs for H <= 1024: one warp per grid row, no block barrier inside
+// a transform.  Four-step split H = N1 N2 (N1 = 2^ceil(logH / 2)): lane
+// n2 < N2 holds z[n2 + N2 n1] (n1 < N1) and runs a DFT of length N1 in
+// registers; the results are multiplied by W_H^(n2 k1) (plan table rtw) and
+// transposed through the warp's own shared-memory row; lane k1 < N1 then runs
+// a DFT of length N2 over n2 and holds Z[k1 + N1 k2] (k2 < N2).  A CTA owns
+// kRowPairs latitude pairs (2 kRowPairs warps), so the mirror unfold (synthesis)
+// and fold (analysis) of Sec. 3.1 run on the CTA's rows in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kRowPairs = 4;
+constexpr int kRowLogMax = 10;
+
+template <int LOGH>
+struct RowShape {
+    static constexpr int H = 1 << LOGH;
+    static constexpr int N1 = 1 << ((LOGH + 1) / 2);
+    static constexpr int N2 = H / N1;
+    static constexpr int LDT = N1 + 1;                      // stride of the transposed layout
+    static constexpr int LDN = H + (H >> 4) + 1;            // natural layout (padi indices)
+    static constexpr int LD = LDN > N2 * LDT ? LDN : N2 * LDT;
+};
+
+__host__ __device__ constexpr size_t row_fft_smem(int ld) { return (size_t)2 * kRowPairs * ld * sizeof(float2); }
+
+// Runtime row length of RowShape<logH>.
+__host__ __device__ inline int row_ld(int logH)
+{
+    const int H = 1 << logH, N1 = 1 << ((logH + 1) / 2), N2 = H / N1;
+    const int ldn = H + (H >> 4) + 1;
+    return ldn > N2 * (N1 + 1) ? ldn : N2 * (N1 + 1);
+}
+
+// One synthesis tile (field b, pairs p0 .. p0 + kRowPairs - 1), run by a CTA of
+// 64 kRowPairs threads; smem_raw holds row_fft_smem(LD) bytes.
+template <int LOGH>
+__device__ __forceinline__ void fft_synth_rows_tile(const PlanView<float> &pv, const float *__restrict__ eo,
+                                                    float *__restrict__ grid, int b, int p0, int op,
+                                                    unsigned char *smem_raw)
+{
+    using S = RowShape<LOGH>;
+    constexpr int H = S::H, N1 = S::N1, N2 = S::N2, LD = S::LD, LDT = S::LDT;
+    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
+    const int mmax = pv.mmax, npairs = pv.npairs, nlat = pv.nlat;
+    // 1. spectra of the CTA's rows: X_north = E + O, X_south = E - O, zero above
+    //    mmax; the loads of a batch of U items are issued before their stores
+    constexpr int NT = 64 * kRowPairs, NQ = kRowPairs * H, U = 8;
+    const float4 *eo4 = reinterpret_cast<const float4 *>(eo);
+#pragma unroll 1
+    for (int q0 = threadIdx.x; q0 < NQ; q0 += U * NT) {
+        float4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int q = q0 + u * NT;
+            const int m = q / kRowPairs, p = p0 + (q - m * kRowPairs);
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q < NQ && m <= mmax && p < npairs) v[u] = eo4[((size_t)b * (mmax + 1) + m) * npairs + p];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int q = q0 + u * NT;
+            if (q >= NQ) break;
+            const int m = q / kRowPairs, i = q - m * kRowPairs;
+            const float2 XN = make_float2(v[u].x + v[u].z, m == 0 ? 0.f : v[u].y + v[u].w);
+            const float2 XS = make_float2(v[u].x - v[u].z, m == 0 ? 0.f : v[u].y - v[u].w);
+            buf[(2 * i) * LD + padi(m)] = XN;
+            buf[(2 * i + 1) * LD + padi(m)] = XS;
+        }
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = p0 + (warp >> 1);
+    const int j = (warp & 1) ? nlat - 1 - p : p;
+    if (p >= npairs || ((warp & 1) && j == p)) return;   // no barrier follows in this tile
+    float2 *row = buf + warp * LD;
+    // 2. Hermitian pre-twiddle Z_k = (X_k + conj X_{H-k}) + i W^k (X_k - conj X_{H-k}), X_H = 0,
+    //    gathered in the phase-1 order k = n2 + N2 n1
+    float2 v[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) {
+        v[n1] = make_float2(0.f, 0.f);
+        const int k = lane + N2 * n1;
+        if (lane < N2) {
+            const float2 Xa = row[padi(k)];
+            if (k == 0) {
+                v[n1] = cadd(Xa, mul_i(Xa));
+            } else {
+                const float2 Xb = row[padi(H - k)];
+                v[n1] = cadd(cadd(Xa, conj_(Xb)), mul_i(cmul(pv.tw[k], csub(Xa, conj_(Xb)))));
+            }
+        }
+    }
+    // 3. inverse DFT of length H
+    RegDft<float2, N1, 1>::run(v);
+    __syncwarp();
+    if (lane < N2) {
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+            const float2 y = k1 == 0 ? v[k1] : cmul(v[k1], pv.rtw[k1 * N2 + lane]);
+            row[lane * LDT + k1] = y;
+        }
+    }
+    __syncwarp();
+    float2 u[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) u[n2] = lane < N1 ? row[n2 * LDT + lane] : make_float2(0.f, 0.f);
+    RegDft<float2, N2, 1>::run(u);
+    // 4. z_k = f_{2k} + i f_{2k+1}, k = k1 + N1 k2
+    float scale = 1.f;
+    if (op == OP_ANALYS_ADJ) scale = float(kTwoPiD) / float(pv.nphi) * pv.wq[p];
+    if (lane < N1) {
+        float2 *out = reinterpret_cast<float2 *>(grid) + ((size_t)b * nlat + j) * H;
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) out[lane + N1 * k2] = make_float2(u[k2].x * scale, u[k2].y * scale);
+    }
+}
+
+// One analysis tile (see fft_synth_rows_tile).
+template <int LOGH>
+__device__ __forceinline__ void fft_analys_rows_tile(const PlanView<float> &pv, const float *__restrict__ grid,
+                                                     float *__restrict__ sd, int b, int p0, int op, int vector,
+                                                     unsigned char *smem_raw)
+{
+    using S = RowShape<LOGH>;
+    constexpr int H = S::H, N1 = S::N1, N2 = S::N2, LD = S::LD, LDT = S::LDT;
+    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
+    const int mmax = pv.mmax, npairs = pv.npairs, nlat = pv.nlat;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = p0 + (warp >> 1);
+    const int j = (warp & 1) ? nlat - 1 - p : p;
+    const bool live = p < npairs && !((warp & 1) && j == p);
+    float2 *row = buf + warp * LD;
+    if (live) {
+        // 1. forward DFT of length H of z_n = f_{2n} + i f_{2n+1}
+        const float2 *in = reinterpret_cast<const float2 *>(grid) + ((size_t)b * nlat + j) * H;
+        float2 v[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) v[n1] = lane < N2 ? in[lane + N2 * n1] : make_float2(0.f, 0.f);
+        RegDft<float2, N1, -1>::run(v);
+        if (lane < N2) {
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) {
+                const float2 y = k1 == 0 ? v[k1] : cmul(v[k1], conj_(pv.rtw[k1 * N2 + lane]));
+                row[lane * LDT + k1] = y;
+            }
+        }
+        __syncwarp();
+        float2 u[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) u[n2] = lane < N1 ? row[n2 * LDT + lane] : make_float2(0.f, 0.f);
+        RegDft<float2, N2, -1>::run(u);
+        __syncwarp();
+        if (lane < N1) {
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) row[padi(lane + N1 * k2)] = u[k2];
+        }
+    }
+    __syncthreads();
+    // 2. post-twiddle, scale, fold north/south, weight
+    float4 *sd4 = reinterpret_cast<float4 *>(sd);
+    const float fscale = (op == OP_ANALYS) ? float(kTwoPiD) / float(pv.nphi) : 1.f;
+    for (int q = threadIdx.x; q < kRowPairs * (mmax + 1); q += blockDim.x) {
+        const int m = q / kRowPairs, i = q - m * kRowPairs;
+        const int pp = p0 + i;
+        if (pp >= npairs) continue;
+        const bool equator = (nlat & 1) && pp == npairs - 1;
+        float2 X[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            X[h] = make_float2(0.f, 0.f);
+            if (h == 1 && equator) continue;
+            const float2 *rw = buf + (2 * i + h) * LD;
+            const float2 Zk = rw[padi(m)];
+            const float2 Zc = conj_(rw[padi((H - m) & (H - 1))]);
+            float2 E = cadd(Zk, Zc), O = csub(Zk, Zc);
+            E.x *= 0.5f; E.y *= 0.5f;
+            const float2 Od = make_float2(O.y * 0.5f, -O.x * 0.5f);  // O / (2i)
+            X[h] = cadd(E, cmul(conj_(pv.tw[m]), Od));
+        }
+        float wf = fscale;
+        if (op == OP_ANALYS) wf *= pv.wq[pp];
+        if (vector) wf /= pv.st[pp];
+        float4 o;
+        if (equator) {
+            o = make_float4(wf * X[0].x, wf * X[0].y, wf * X[0].x, wf * X[0].y);
+        } else {
+            o = make_float4(wf * (X[0].x + X[1].x), wf * (X[0].y + X[1].y), wf * (X[0].x - X[1].x),
+                            wf * (X[0].y - X[1].y));
+        }
+        sd4[((size_t)b * (mmax + 1) + m) * npairs + pp] = o;
+    }
+}
+
+template <int LOGH>
+__global__ void __launch_bounds__(64 * kRowPairs, 2)
+k_fft_synth_rows(PlanView<float> pv, const float *__restrict__ eo, float *__restrict__ grid, int op)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fft_synth_rows_tile<LOGH>(pv, eo, grid, blockIdx.y, blockIdx.x * kRowPairs, op, smem_raw);
+}
+
+template <int LOGH>
+__global__ void __launch_bounds__(64 * kRowPairs, 2)
+k_fft_analys_rows(PlanView<float> pv, const float *__restrict__ grid, float *__restrict__ sd, int op, int vector)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fft_analys_rows_tile<LOGH>(pv, grid, sd, blockIdx.y, blockIdx.x * kRowPairs, op, vector, smem_raw);
+}
+
+template <int LOGH>
+cudaError_t launch_rows(bool synth, const PlanView<float> &pv, const float *in, float *out, int batch, Op op,
+                        bool vector, cudaStream_t s)
+{
+    const size_t smem = row_fft_smem(RowShape<LOGH>::LD);
+    dim3 g((unsigned)((pv.npairs + kRowPairs - 1) / kRowPairs), (unsigned)batch);
+    cudaError_t e;
+    if (synth) {
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(k_fft_synth_rows<LOGH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_fft_synth_rows<LOGH><<<g, 64 * kRowPairs, smem, s>>>(pv, in, out, (int)op);
+    } else {
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(k_fft_analys_rows<LOGH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_fft_analys_rows<LOGH><<<g, 64 * kRowPairs, smem, s>>>(pv, in, out, (int)op, vector ? 1 : 0);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_dispatch(int logH, bool synth, const PlanView<float> &pv, const float *in, float *out,
+                                 int batch, Op op, bool vector, cudaStream_t s)
+{
+    switch (logH) {
+    case 0: return launch_rows<0>(synth, pv, in, out, batch, op, vector, s);
+    case 1: return launch_rows<1>(synth, pv, in, out, batch, op, vector, s);
+    case 2: return launch_rows<2>(synth, pv, in, out, batch, op, vector, s);
+    case 3: return launch_rows<3>(synth, pv, in, out, batch, op, vector, s);
+    case 4: return launch_rows<4>(synth, pv, in, out, batch, op, vector, s);
+    case 5: return launch_rows<5>(synth, pv, in, out, batch, op, vector, s);
+    case 6: return launch_rows<6>(synth, pv, in, out, batch, op, vector, s);
+    case 7: return launch_rows<7>(synth, pv, in, out, batch, op, vector, s);
+    case 8: return launch_rows<8>(synth, pv, in, out, batch, op, vector, s);
+    case 9: return launch_rows<9>(synth, pv, in, out, batch, op, vector, s);
+    case 10: return launch_rows<10>(synth, pv, in, out, batch, op, vector, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 inline int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 
 // Threads per row and pairs per CTA: TPR = H/16 threads per row (>= 1) and
@@ -421,6 +677,9 @@ template <typename T>
 cudaError_t launch_fft_synth(const PlanView<T> &pv, const T *eo, T *grid, int batch, Op op, cudaStream_t s)
 {
     const int H = pv.nphi / 2, logH = ilog2(H);
+    if constexpr (sizeof(T) == 4) {
+        if (logH <= kRowLogMax) return launch_rows_dispatch(logH, true, pv, eo, grid, batch, op, false, s);
+    }
     int G, threads;
     size_t smem;
     fft_shape<T>(H, pv.npairs, G, threads, smem);
@@ -436,6 +695,9 @@ cudaError_t launch_fft_analys(const PlanView<T> &pv, const T *grid, T *sd, int b
                               cudaStream_t s)
 {
     const int H = pv.nphi / 2, logH = ilog2(H);
+    if constexpr (sizeof(T) == 4) {
+        if (logH <= kRowLogMax) return launch_rows_dispatch(logH, false, pv, grid, sd, batch, op, vector, s);
+    }
     int G, threads;
     size_t smem;
     fft_shape<T>(H, pv.npairs, G, threads, smem);
@@ -451,7 +713,7 @@ cudaError_t launch_fft_analys(const PlanView<T> &pv, const T *grid, T *sd, int b
 // ---------------------------------------------------------------------------
 namespace {
 
-__global__ void __launch_bounds__(256) k_batch_fft(int synth, const BatchField *__restrict__ fields,
+__global__ void __launch_bounds__(256, 2) k_batch_fft(int synth, const BatchField *__restrict__ fields,
                                                    const int4 *__restrict__ tiles, int ntiles, int *counter)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -464,16 +726,34 @@ __global__ void __launch_bounds__(256) k_batch_fft(int synth, const BatchField *
         if (t >= ntiles) break;
         const int4 tl = tiles[t];
         const BatchField f = fields[tl.x];
-        if (synth) fft_synth_tile<float>(f.pv, f.inter, f.out, 0, tl.y, f.G, f.logH, OP_SYNTH, smem_raw);
-        else fft_analys_tile<float>(f.pv, f.in, f.inter, 0, tl.y, f.G, f.logH, OP_ANALYS, 0, smem_raw);
+        if (f.logH <= kRowLogMax) {
+            // the same tile functions as the per-field FP32 launches
+            switch (f.logH) {
+#define SHT_ROW_CASE(L)                                                                                \
+    case L:                                                                                            \
+        if (synth) fft_synth_rows_tile<L>(f.pv, f.inter, f.out, 0, tl.y, OP_SYNTH, smem_raw);          \
+        else fft_analys_rows_tile<L>(f.pv, f.in, f.inter, 0, tl.y, OP_ANALYS, 0, smem_raw);            \
+        break;
+                SHT_ROW_CASE(0) SHT_ROW_CASE(1) SHT_ROW_CASE(2) SHT_ROW_CASE(3) SHT_ROW_CASE(4) SHT_ROW_CASE(5)
+                SHT_ROW_CASE(6) SHT_ROW_CASE(7) SHT_ROW_CASE(8) SHT_ROW_CASE(9) SHT_ROW_CASE(10)
+#undef SHT_ROW_CASE
+            default: break;
+            }
+        } else if (synth) {
+            fft_synth_tile<float>(f.pv, f.inter, f.out, 0, tl.y, f.G, f.logH, OP_SYNTH, smem_raw);
+        } else {
+            fft_analys_tile<float>(f.pv, f.in, f.inter, 0, tl.y, f.G, f.logH, OP_ANALYS, 0, smem_raw);
+        }
     }
 }
 
 }  // namespace
 
-// Pairs per FFT tile for a 256-thread CTA: 2G rows of max(1, H/16) threads.
+// Pairs per FFT tile for a 256-thread CTA: kRowPairs for the row FFTs
+// (logH <= 10), else 2G rows of max(1, H/16) threads.
 int batch_fft_group(int logH, int npairs)
 {
+    if (logH <= kRowLogMax) return kRowPairs;
     const int H = 1 << logH;
     const int TPR = H >= 16 ? H / 16 : 1;
     int G = 256 / (2 * TPR);
@@ -484,6 +764,7 @@ int batch_fft_group(int logH, int npairs)
 
 size_t batch_fft_smem(int logH, int G)
 {
+    if (logH <= kRowLogMax) return row_fft_smem(row_ld(logH));
     const int H = 1 << logH;
     const size_t row_bytes = (size_t)((H + (H >> 4)) + 1) * sizeof(float2);
     return (size_t)H * sizeof(float2) + (size_t)2 * G * row_bytes;

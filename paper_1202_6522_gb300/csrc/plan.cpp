@@ -93,14 +93,14 @@ size_t padded(size_t count) { return (count * sizeof(U) + 255) & ~size_t(255); }
 PlanView<double> Plan::view64() const
 {
     PlanView<double> v{lmax, mmax, nlat, nphi, npairs, nlm,
-                       t64.ab, t64.dc, t64.x, t64.st, t64.wq, t64.pmm, t64.pmmk, t64.tw};
+                       t64.ab, t64.dc, t64.x, t64.st, t64.wq, t64.pmm, t64.pmmk, t64.tw, t64.rtw};
     return v;
 }
 
 PlanView<float> Plan::view32() const
 {
     PlanView<float> v{lmax, mmax, nlat, nphi, npairs, nlm,
-                      t32.ab, t32.dc, t32.x, t32.st, t32.wq, t32.pmm, t32.pmmk, t32.tw};
+                      t32.ab, t32.dc, t32.x, t32.st, t32.wq, t32.pmm, t32.pmmk, t32.tw, t32.rtw};
     return v;
 }
 
@@ -181,14 +181,28 @@ int plan_build(Plan &p, std::string &err)
         tw[2 * k + 1] = std::sin(ang);
     }
 
-    // One device allocation holding both precisions' tables.
+    // Twiddles of the four-step FFT of length H: rtw[k1 N2 + n2] = e^{2 pi i n2 k1 / H}.
     const size_t H1 = H > 0 ? H : 1;
+    std::vector<double> rtw(2 * H1, 0.0);
+    {
+        int logH = 0;
+        while ((1 << logH) < H) ++logH;
+        const int N1 = fft_n1(logH), N2 = H / N1;
+        for (int k1 = 0; k1 < N1 && H > 0; ++k1)
+            for (int n2 = 0; n2 < N2; ++n2) {
+                const double ang = 2.0 * kPi * (double)(n2 * k1) / H;
+                rtw[2 * ((size_t)k1 * N2 + n2)] = std::cos(ang);
+                rtw[2 * ((size_t)k1 * N2 + n2) + 1] = std::sin(ang);
+            }
+    }
+
+    // One device allocation holding both precisions' tables.
     size_t bytes = padded<double2>(nlm) + padded<double>(nlm) + 3 * padded<double>(npairs) +
                    padded<double>((size_t)(mmax + 1) * npairs) + padded<int>((size_t)(mmax + 1) * npairs) +
-                   padded<double2>(H1);
+                   2 * padded<double2>(H1);
     bytes += padded<float2>(nlm) + padded<float>(nlm) + 3 * padded<float>(npairs) +
              padded<float>((size_t)(mmax + 1) * npairs) + padded<int>((size_t)(mmax + 1) * npairs) +
-             padded<float2>(H1);
+             2 * padded<float2>(H1);
     bytes += padded<int>(1);
     DevArena ar;
     cudaError_t ce = cudaGetDevice(&p.device);
@@ -218,9 +232,12 @@ int plan_build(Plan &p, std::string &err)
     ok &= up(p.t64.pmmk, k64.data(), sizeof(int) * k64.size());
     p.t64.tw = ar.take<double2>(H1);
     ok &= up(p.t64.tw, tw.data(), sizeof(double) * 2 * H1);
+    p.t64.rtw = ar.take<double2>(H1);
+    ok &= up(p.t64.rtw, rtw.data(), sizeof(double) * 2 * H1);
 
     std::vector<float> ab32 = to_f32(ab), dc32 = to_f32(dc), x32 = to_f32(xp), s32 = to_f32(sp),
-                       w32 = to_f32(wp), pmm32 = to_f32(pmm32d), tw32 = to_f32(tw);
+                       w32 = to_f32(wp), pmm32 = to_f32(pmm32d), tw32 = to_f32(tw),
+                       rtw32 = to_f32(rtw);
     p.t32.ab = ar.take<float2>(nlm);
     ok &= up(p.t32.ab, ab32.data(), sizeof(float) * 2 * nlm);
     p.t32.dc = ar.take<float>(nlm);
@@ -237,6 +254,8 @@ int plan_build(Plan &p, std::string &err)
     ok &= up(p.t32.pmmk, k32.data(), sizeof(int) * k32.size());
     p.t32.tw = ar.take<float2>(H1);
     ok &= up(p.t32.tw, tw32.data(), sizeof(float) * 2 * H1);
+    p.t32.rtw = ar.take<float2>(H1);
+    ok &= up(p.t32.rtw, rtw32.data(), sizeof(float) * 2 * H1);
     p.d_err = ar.take<int>(1);
     ok &= cudaMemset(p.d_err, 0, sizeof(int)) == cudaSuccess;
     if (!ok) {

@@ -36,7 +36,12 @@ struct Tables {
     T *pmm = nullptr;    // [mmax+1][npairs] P_m^m(x_p) * 2^(S k) (mantissa)
     int *pmmk = nullptr; // [mmax+1][npairs] k (number of 2^S steps)
     T2 *tw = nullptr;    // [nphi/2] e^{2 pi i k / nphi}
+    T2 *rtw = nullptr;   // [H] four-step FFT twiddles: rtw[k1 N2 + n2] = e^{2 pi i n2 k1 / H}
 };
+
+// Four-step split of an FFT of length H = 2^logH = N1 N2 (fft.cu):
+// N1 = 2^ceil(logH / 2), N2 = H / N1.
+inline int fft_n1(int logH) { return 1 << ((logH + 1) / 2); }
 
 // Kernel-side view of a plan in precision T.
 template <typename T>
@@ -51,6 +56,7 @@ struct PlanView {
     const T *pmm;
     const int *pmmk;
     const T2 *tw;
+    const T2 *rtw;
 };
 
 // What a Legendre or FFT launch computes; selects the scale factors.
@@ -87,6 +93,7 @@ struct Plan {
     size_t tc_nchunk_s = 0;                     // synthesis data chunks over all orders
     int *d_c0_s = nullptr, *d_c0_a = nullptr;   // first live chunk per (m, tile)
     double polar_skip_s = 0, polar_skip_a = 0;  // fraction of panel chunks skipped
+    float polar_thr = 0x1p-40f;                 // polar threshold (sht_set_polar_threshold)
     unsigned char *dpanel_s = nullptr, *dpanel_a = nullptr; // sin(theta) dP/dtheta panels (vector)
     int *d_c0v_s = nullptr, *d_c0v_a = nullptr; // first chunk live in P or dP
     void *work = nullptr;            // scratch (grown on demand)
@@ -133,6 +140,8 @@ template <typename T>
 cudaError_t launch_fft_analys(const PlanView<T> &pv, const T *grid, T *sd, int batch, Op op,
                               bool vector, cudaStream_t s);
 
+
+
 // Uneven batches (batch.cu): one field of an uneven batch, as the persistent
 // kernels see it.  FP32 data.
 struct BatchField {
@@ -172,24 +181,27 @@ cudaError_t launch_build_panels(const PlanView<double> &pv, const unsigned long 
                                 const unsigned long long *off_a, unsigned char *ps, unsigned char *pa, bool deriv,
                                 cudaStream_t st);
 // Scalar contraction of <= tc_max_batch() fields: prep kernel (FP32 -> blocked
-// bf16 hi/lo in `data`) then the tcgen05 kernel.  Synthesis: spectra -> E/O;
+// bf16 hi/lo in `data`; skipped when `prepped`, i.e. `data` already holds
+// this operand) then the tcgen05 kernel.  Synthesis: spectra -> E/O;
 // analysis: s/d folds -> spectra.
 cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
                                const unsigned long long *off, const int *c0, const unsigned long long *dchunk,
                                unsigned char *data, const float *in, float *out, int batch, Op op, int *err,
-                               cudaStream_t st);
+                               bool prepped, cudaStream_t st);
 // Vector contraction of <= tc_vec_max_batch() fields.  Synthesis: (S, T) ->
 // (theta E/O, phi E/O); analysis: (theta, phi) folds -> (S, T).
 cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
                           const unsigned char *dpanel, const unsigned long long *off, const int *c0,
                           const unsigned long long *dchunk, unsigned char *data, const float *in0, const float *in1,
-                          float *out0, float *out1, const float *st_pairs, int batch, Op op, int *err, cudaStream_t st);
+                          float *out0, float *out1, const float *st_pairs, int batch, Op op, int *err, bool prepped,
+                          cudaStream_t st);
 cudaError_t launch_min_int(const int *a, const int *b, int *out, int n, cudaStream_t st);
 int tc_vec_max_batch();
+// Rows of the data operand for `batch` fields: 32 ceil(2 batch / 32), twice that for vectors.
+inline int tc_rows(int batch, bool vec) { return (vec ? 2 : 1) * (((2 * batch + 31) / 32) * 32); }
 // Static polar optimisation: per (m, tile) first chunk with a panel value >= thr.
 cudaError_t launch_panel_first_live(bool synth, int lmax, int mmax, int npairs, const unsigned long long *off,
                                     const unsigned char *panel, float thr, int *c0, int &ntiles, cudaStream_t st);
-constexpr float kPolarThreshold = 0x1p-40f;   // |P_n^m| below this is left out of the panel sums
 void tc_tile_counts(int lmax, int npairs, int &ntiles_s, int &ntiles_a);
 cudaError_t tc_polar_stats(int lmax, int mmax, int npairs, const int *d_c0_s, const int *d_c0_a, double &frac_s,
                            double &frac_a);

@@ -31,43 +31,21 @@
 #include <vector>
 
 #include "sht_internal.h"
+#include "tc_layout.cuh"
 #include "tc_ptx.cuh"
 
 namespace sht {
 namespace {
 
 constexpr int kRows = 128;            // MMA M
-constexpr int kKc = 16;               // K per chunk (per parity): one MMA K step
 constexpr int kBlk = kRows * kKc * 2; // bytes of one bf16 [128 x kKc] panel block
 constexpr int kChunkPanel = 4 * kBlk; // [parity][hi/lo] blocks per chunk = 16 KB
-constexpr uint32_t kSbo = (kKc / 8) * 128;  // 8-row group stride in a [rows x kKc] block
-constexpr uint32_t kLbo = 128;              // K-adjacent core matrices
 constexpr uint64_t kWaitNs = 2000000000ull; // 2 s
-
-// byte offset of element (row, k) in a K-major [rows x kKc] bf16 block
-__host__ __device__ __forceinline__ uint32_t blk_off(int row, int k)
-{
-    return (uint32_t)((row >> 3) * kSbo + (k >> 3) * kLbo + (row & 7) * 16 + (k & 7) * 2);
-}
-
-__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
-{
-    hi = __float2bfloat16_rn(v);
-    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-}
 
 __device__ __forceinline__ void split_bf16_d(double v, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
 {
     hi = __float2bfloat16_rn((float)v);
     lo = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hi)));
-}
-
-__device__ __forceinline__ void put_split(unsigned char *bh, unsigned char *bl, int row, int k, float v)
-{
-    __nv_bfloat16 h, l;
-    split_bf16(v, h, l);
-    *reinterpret_cast<__nv_bfloat16 *>(bh + blk_off(row, k)) = h;
-    *reinterpret_cast<__nv_bfloat16 *>(bl + blk_off(row, k)) = l;
 }
 
 __host__ __device__ __forceinline__ long col_of(int lmax, int m) { return (long)m * (2 * lmax + 3 - m) / 2; }
@@ -148,73 +126,107 @@ k_build_panels(PlanView<double> pv, const unsigned long long *__restrict__ off_s
 // Synthesis chunks are numbered from dchunk[m] per order; analysis chunks
 // are m * kch + kc.
 // ---------------------------------------------------------------------------
-__host__ __device__ inline size_t data_chunk_bytes(int rows) { return 4 * (size_t)rows * kKc * 2; }
+constexpr int kPrepThreads = 128;
 
-__global__ void __launch_bounds__(128)
+// Packs 8 bf16 values into one 16-byte core-matrix row.
+__device__ __forceinline__ uint4 pack8(const __nv_bfloat16 (&v)[8])
+{
+    uint4 r;
+    r.x = (uint32_t)__bfloat16_as_ushort(v[0]) | ((uint32_t)__bfloat16_as_ushort(v[1]) << 16);
+    r.y = (uint32_t)__bfloat16_as_ushort(v[2]) | ((uint32_t)__bfloat16_as_ushort(v[3]) << 16);
+    r.z = (uint32_t)__bfloat16_as_ushort(v[4]) | ((uint32_t)__bfloat16_as_ushort(v[5]) << 16);
+    r.w = (uint32_t)__bfloat16_as_ushort(v[6]) | ((uint32_t)__bfloat16_as_ushort(v[7]) << 16);
+    return r;
+}
+
+// Writes the hi and lo rows of 8 consecutive K values of one operand row.
+__device__ __forceinline__ void put_row8(unsigned char *bh, unsigned char *bl, int row, int h, const float (&v)[8])
+{
+    __nv_bfloat16 hv[8], lv[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) split_bf16(v[i], hv[i], lv[i]);
+    const uint32_t o = blk_off(row, 8 * h);
+    *reinterpret_cast<uint4 *>(bh + o) = pack8(hv);
+    *reinterpret_cast<uint4 *>(bl + o) = pack8(lv);
+}
+
+// One thread per 8 consecutive K positions of one field (and quantity): it
+// reads them (synthesis: 8 spectral coefficients of one parity; analysis: the
+// s/d folds of 8 latitude pairs) and writes whole 16-byte core-matrix rows
+// (re and im rows, hi and lo blocks).  The pad rows of the operand (fields
+// beyond the batch) are left as they are: they only feed output columns that
+// are never read.  grid = (ceil(max chunks * items / kPrepThreads), mmax + 1).
+__global__ void __launch_bounds__(kPrepThreads)
 k_tc_prep(int synth, int vec, int lmax, int mmax, int npairs, int nlm, int batch, int rows, int op,
           const float *__restrict__ in0, const float *__restrict__ in1, const unsigned long long *__restrict__ dchunk,
           unsigned char *__restrict__ data)
 {
-    const int m = blockIdx.y, c = blockIdx.x;
+    const int m = blockIdx.y;
     const int L = lmax - m + 1, Le = (L + 1) / 2;
     const int nch = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
+    const int nq = vec ? 2 : 1;
+    // items per chunk: synthesis (quantity, field, parity, K half); analysis (quantity, field, K half)
+    const int items = (synth ? 4 : 2) * batch * nq;
+    const int gid = blockIdx.x * kPrepThreads + threadIdx.x;
+    const int c = gid / items;
     if (c >= nch) return;
+    int it = gid - c * items;
+    const int h = it & 1;
+    it >>= 1;
     const size_t db = data_chunk_bytes(rows);
     unsigned char *dat = data + (synth ? (dchunk[m] + c) : ((size_t)m * nch + c)) * db;
     const size_t blk = (size_t)rows * kKc * 2;
     const int NH = rows / 2;
-    // zero the chunk first: unused rows are the MMA's pad columns
-    for (int i = threadIdx.x; i < (int)(db / 16); i += blockDim.x)
-        *reinterpret_cast<uint4 *>(dat + (size_t)i * 16) = make_uint4(0, 0, 0, 0);
-    __syncthreads();
     if (synth) {
+        const int cls = it & 1;
+        it >>= 1;
+        const int b = it % batch, q = it / batch;
         const long col = col_of(lmax, m);
+        const float2 *A = reinterpret_cast<const float2 *>(q ? in1 : in0) + (size_t)b * nlm + col;
         // adjoint of analysis: b / c_m (scalar) or b / (c_m n (n + 1)) (vector)
         const float cadj = (op == OP_ANALYS_ADJ && m > 0) ? 0.5f : 1.0f;
-        const float2 *A = reinterpret_cast<const float2 *>(in0);
-        const float2 *B = reinterpret_cast<const float2 *>(in1);
-        for (int i = threadIdx.x; i < batch * 2 * kKc; i += blockDim.x) {
-            const int b = i / (2 * kKc), j = i - b * (2 * kKc);
-            const int nn = 2 * kKc * c + j;
-            const int n = m + nn;
-            const int cls = j & 1, kk = j >> 1;
-            unsigned char *bh = dat + (size_t)(cls * 2) * blk;
-            unsigned char *bl = bh + blk;
-            float sc = cadj;
-            if (vec && op == OP_ANALYS_ADJ) sc = (n == 0) ? 0.f : cadj / ((float)n * (float)(n + 1));
-            float2 v = make_float2(0.f, 0.f);
-            if (nn < L) v = A[(size_t)b * nlm + col + nn];
-            put_split(bh, bl, 2 * b, kk, v.x * sc);
-            put_split(bh, bl, 2 * b + 1, kk, m == 0 ? 0.f : v.y * sc);
-            if (vec) {
-                float2 w = make_float2(0.f, 0.f);
-                if (nn < L) w = B[(size_t)b * nlm + col + nn];
-                put_split(bh, bl, NH + 2 * b, kk, w.x * sc);
-                put_split(bh, bl, NH + 2 * b + 1, kk, m == 0 ? 0.f : w.y * sc);
-            }
-        }
-    } else {
-        const float4 *A = reinterpret_cast<const float4 *>(in0);
-        const float4 *B = reinterpret_cast<const float4 *>(in1);
-        for (int i = threadIdx.x; i < batch * kKc; i += blockDim.x) {
-            const int b = i / kKc, j = i - b * kKc;
-            const int p = kKc * c + j;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f), w = v;
-            if (p < npairs) {
-                v = A[((size_t)b * (mmax + 1) + m) * npairs + p];
-                if (vec) w = B[((size_t)b * (mmax + 1) + m) * npairs + p];
-            }
-            const float va[4] = {v.x, v.y, v.z, v.w};  // s.re s.im d.re d.im
-            const float wa[4] = {w.x, w.y, w.z, w.w};
+        float re[8], im[8];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int cls = t >> 1, part = t & 1;
-                unsigned char *bh = dat + (size_t)(cls * 2) * blk;
-                unsigned char *bl = bh + blk;
-                put_split(bh, bl, 2 * b + part, j, va[t]);
-                if (vec) put_split(bh, bl, NH + 2 * b + part, j, wa[t]);
+        for (int i = 0; i < 8; ++i) {
+            const int nn = 2 * (kKc * c + 8 * h + i) + cls;   // n - m
+            float2 v = make_float2(0.f, 0.f);
+            if (nn < L) v = A[nn];
+            float sc = cadj;
+            if (vec && op == OP_ANALYS_ADJ) {
+                const int n = m + nn;
+                sc = (n == 0) ? 0.f : cadj / ((float)n * (float)(n + 1));
             }
+            re[i] = v.x * sc;
+            im[i] = m == 0 ? 0.f : v.y * sc;
         }
+        unsigned char *bh = dat + (size_t)(cls * 2) * blk;
+        const int r0 = q * NH + 2 * b;
+        put_row8(bh, bh + blk, r0, h, re);
+        put_row8(bh, bh + blk, r0 + 1, h, im);
+    } else {
+        const int b = it % batch, q = it / batch;
+        const float4 *A = reinterpret_cast<const float4 *>(q ? in1 : in0) + ((size_t)b * (mmax + 1) + m) * npairs;
+        float4 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int p = kKc * c + 8 * h + i;
+            v[i] = p < npairs ? A[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const int r0 = q * NH + 2 * b;
+        float t[8];
+        // class 0: s folds (x: re, y: im); class 1: d folds (z: re, w: im)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[i] = v[i].x;
+        put_row8(dat, dat + blk, r0, h, t);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[i] = v[i].y;
+        put_row8(dat, dat + blk, r0 + 1, h, t);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[i] = v[i].z;
+        put_row8(dat + 2 * blk, dat + 3 * blk, r0, h, t);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[i] = v[i].w;
+        put_row8(dat + 2 * blk, dat + 3 * blk, r0 + 1, h, t);
     }
 }
 
@@ -601,7 +613,7 @@ __global__ void k_selftest_timeout(int *err, unsigned long long max_ns)
     if (!tc::mbar_wait_bounded(&bar, 0, max_ns)) raise_err(err, SHT_ETIMEOUT);
 }
 
-int cols_of(int batch) { return ((2 * batch + 31) / 32) * 32; }
+int cols_of(int batch) { return tc_rows(batch, false); }
 
 template <typename K>
 cudaError_t launch_contraction(K kernel, bool synth, int lmax, int mmax, int npairs, int npanels, TcArgs &a,
@@ -630,8 +642,9 @@ cudaError_t launch_prep(bool synth, bool vec, int lmax, int mmax, int npairs, in
 {
     const int Le0 = (lmax + 2) / 2;
     const int maxch = synth ? (Le0 + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
-    dim3 g((unsigned)maxch, (unsigned)(mmax + 1));
-    k_tc_prep<<<g, 128, 0, st>>>(synth ? 1 : 0, vec ? 1 : 0, lmax, mmax, npairs, nlm, batch, rows, (int)op, in0, in1,
+    const long items = (long)(synth ? 4 : 2) * batch * (vec ? 2 : 1);
+    dim3 g((unsigned)((maxch * items + kPrepThreads - 1) / kPrepThreads), (unsigned)(mmax + 1));
+    k_tc_prep<<<g, kPrepThreads, 0, st>>>(synth ? 1 : 0, vec ? 1 : 0, lmax, mmax, npairs, nlm, batch, rows, (int)op, in0, in1,
                                  dchunk, data);
     return cudaGetLastError();
 }
@@ -741,12 +754,15 @@ cudaError_t launch_panel_first_live(bool synth, int lmax, int mmax, int npairs, 
 cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
                                const unsigned long long *off, const int *c0, const unsigned long long *dchunk,
                                unsigned char *data, const float *in, float *out, int batch, Op op, int *err,
-                               cudaStream_t st)
+                               bool prepped, cudaStream_t st)
 {
     if (batch < 1 || batch > tc_max_batch()) return cudaErrorInvalidValue;
     const int rows = cols_of(batch);
-    cudaError_t e = launch_prep(synth, false, lmax, mmax, npairs, nlm, batch, rows, op, in, nullptr, dchunk, data, st);
-    if (e != cudaSuccess) return e;
+    if (!prepped) {
+        cudaError_t e =
+            launch_prep(synth, false, lmax, mmax, npairs, nlm, batch, rows, op, in, nullptr, dchunk, data, st);
+        if (e != cudaSuccess) return e;
+    }
     TcArgs a{};
     a.lmax = lmax;
     a.mmax = mmax;
@@ -769,12 +785,16 @@ cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int n
 cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
                           const unsigned char *dpanel, const unsigned long long *off, const int *c0,
                           const unsigned long long *dchunk, unsigned char *data, const float *in0, const float *in1,
-                          float *out0, float *out1, const float *st_pairs, int batch, Op op, int *err, cudaStream_t st)
+                          float *out0, float *out1, const float *st_pairs, int batch, Op op, int *err, bool prepped,
+                          cudaStream_t st)
 {
     if (batch < 1 || batch > tc_vec_max_batch()) return cudaErrorInvalidValue;
     const int rows = 2 * cols_of(batch);   // 4 accumulators x rows columns <= 512
-    cudaError_t e = launch_prep(synth, true, lmax, mmax, npairs, nlm, batch, rows, op, in0, in1, dchunk, data, st);
-    if (e != cudaSuccess) return e;
+    if (!prepped) {
+        cudaError_t e =
+            launch_prep(synth, true, lmax, mmax, npairs, nlm, batch, rows, op, in0, in1, dchunk, data, st);
+        if (e != cudaSuccess) return e;
+    }
     TcArgs a{};
     a.lmax = lmax;
     a.mmax = mmax;

@@ -196,3 +196,33 @@ def test_tc_static_polar_skip_fraction(SHT):
     sht.synth_(_dev(_spec(1023, 1023, 1, 0)))
     fs, fa = C.sht_tc_polar_skip(sht._h)
     assert 0.02 < fs < 0.5 and 0.02 < fa < 0.5, (fs, fa)
+
+
+def test_tc_polar_threshold_api(SHT):
+    """The threshold of the polar optimisation (Sec. 3.1): 0 skips nothing; a
+    larger threshold skips more chunks; results stay within the bound."""
+    from paper_1202_6522_gb300 import _capi as C
+    lmax, nlat, nphi = 255, 256, 512
+    sht = SHT(lmax, lmax, nlat, nphi, fp32_path="tc")
+    a = _spec(lmax, lmax, 2, 7)
+    ref = oracle.synth(lmax, lmax, nlat, nphi, a)
+    assert normwise(_np(sht.synth_(_dev(a))), ref) < tc_bound(lmax)
+    fs0, fa0 = C.sht_tc_polar_skip(sht._h)
+    C.sht_set_polar_threshold(sht._h, 0.0)
+    assert C.sht_tc_polar_skip(sht._h) == (0.0, 0.0)
+    assert normwise(_np(sht.synth_(_dev(a))), ref) < tc_bound(lmax)
+    C.sht_set_polar_threshold(sht._h, 2.0 ** -20)
+    fs1, fa1 = C.sht_tc_polar_skip(sht._h)
+    assert fs1 >= fs0 and fa1 >= fa0 and fa1 > 0
+    assert normwise(_np(sht.synth_(_dev(a))), ref) < tc_bound(lmax)
+    g = _grid(nlat, nphi, 2, 8)
+    assert normwise(_np(sht.analys_(_dev(g))), oracle.analys(lmax, lmax, nlat, nphi, g)) < tc_bound(lmax)
+    for bad in (-1.0, 2.0, float("nan")):
+        with pytest.raises((C.SHTError, ValueError)):
+            C.sht_set_polar_threshold(sht._h, bad)
+
+
+def test_alu_peaks_measured(SHT):
+    from paper_1202_6522_gb300 import _capi as C
+    f32, f64 = C.sht_alu_peaks(torch.cuda.current_stream().cuda_stream)
+    assert 10.0 < f32 < 200.0 and 0.05 < f64 < 100.0, (f32, f64)
