@@ -401,16 +401,17 @@ def run_ours(args):
     B.build()
     sht = SHT(LMAX, LMAX, NLAT, NPHI, device=dev)
     stream = torch.cuda.current_stream(dev)
-    if args.mode == "tc":
-        sht = SHT(LMAX, LMAX, NLAT, NPHI, device=dev, fp32_path="tc")
+    if args.mode in ("tc", "otf"):
+        sht = SHT(LMAX, LMAX, NLAT, NPHI, device=dev, fp32_path=args.mode)
     tune_report = None
     if args.mode == "auto":
         # runtime tuning before timing: kernel shapes and on-the-fly vs precomputed panels
         from paper_1202_6522_gb300 import _capi as C
-        f32_ms, tc_ms = C.sht_tune(sht._h, BATCH, C.SHT_F32_AUTO, stream.cuda_stream)
+        f32_ms, tc_ms, otf_ms = C.sht_tune(sht._h, BATCH, C.SHT_F32_AUTO, stream.cuda_stream)
         sht.fp32_mode = C.SHT_F32_AUTO
-        tune_report = {"f32_round_trip_ms": f32_ms, "tc_round_trip_ms": tc_ms,
-                       "chosen": "tc" if (tc_ms > 0 and tc_ms < f32_ms) else "f32"}
+        cands = {"f32": f32_ms, "tc": tc_ms, "tc_otf": otf_ms}
+        tune_report = {"f32_round_trip_ms": f32_ms, "tc_round_trip_ms": tc_ms, "tc_otf_round_trip_ms": otf_ms,
+                       "chosen": min((v, k) for k, v in cands.items() if v > 0)[1]}
     # measured FMA throughput: the ALU roofline denominators (FP32 and FP64)
     alu_peaks = None
     try:
@@ -538,7 +539,22 @@ def run_ours(args):
     dom_name, (dom_ms, dom_n) = dom
     dom_avg = dom_ms / dom_n
     sm_max = clk.get("sm_max_mhz") or 2070.0
-    if dom_name.startswith("tc_"):
+    path_used = {"auto": (tune_report or {}).get("chosen", "f32"), "otf": "tc_otf"}.get(args.mode, args.mode)
+    if dom_name.startswith("tc_") and path_used == "tc_otf":
+        # P generated in FP32 on the CUDA cores: 5 flops per (n, m, latitude pair)
+        # (a x, b P_{n-2}, one fma, the seed scale), the tensor-core work aside
+        from paper_1202_6522_gb300 import _capi as C
+        skip_s, skip_a = C.sht_tc_polar_skip(sht._h)
+        skip = max(0.0, skip_a if dom_name == "tc_analys" else skip_s)
+        flops = nlm_of(LMAX) * ((NLAT + 1) // 2) * 5.0 * (1.0 - skip)
+        peak = (alu_peaks[0] * 1e12) if alu_peaks else fp32_alu_peak(sm_max)
+        achieved = flops / (dom_avg / 1e3)
+        roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured FP32 FMA throughput (sht_alu_peaks)" if alu_peaks else "FP32 nominal",
+                "algorithmic_flops": flops, "kernel_avg_ms": dom_avg, "launches": dom_n,
+                "polar_skip": {"synth": skip_s, "analys": skip_a}}
+    elif dom_name.startswith("tc_"):
         # the panels stream from HBM once per launch: bytes bound the kernel
         from paper_1202_6522_gb300 import _capi as C
         skip_s, skip_a = C.sht_tc_polar_skip(sht._h)
@@ -577,13 +593,16 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "tc": "bf16x3 (f32 accumulate)",
+                                       "otf": "bf16x3 (f32 accumulate)",
                                        "auto": "f32 / bf16x3 (tuned)"}[args.mode],
         "data": "synthetic (seeded N(0,1)/(n+1) spectra)",
         "config": {"workload": WORKLOAD, "lmax": LMAX, "nlat": NLAT, "nphi": NPHI, "batch": BATCH,
                    "path": {"f32": "FP32 on-the-fly recurrence with exponent scale",
                             "f64": "plain FP64 on-the-fly",
                             "tc": "tcgen05 split-bf16 contraction vs FP64-built P panels",
-                            "auto": "runtime-tuned: FP32 on-the-fly or tcgen05 panels"}[args.mode], "l2": "inputs larger than L2 (spectra+grids > 129 MB)",
+                            "otf": "tcgen05 split-bf16 contraction, P generated on the fly (FP32, reseeded)",
+                            "auto": "runtime-tuned: FP32 on-the-fly, tcgen05 panels or tcgen05 on-the-fly P"}[args.mode],
+                   "path_used": path_used, "l2": "inputs larger than L2 (spectra+grids > 129 MB)",
                    "parallelism": f"replicas x{world}"},
         "gflops_nominal": value * nominal_flops_per_rt() / 1e9,
         "elements_per_s": value * (LMAX + 1) ** 3,
@@ -620,7 +639,7 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["auto", "tc", "f32", "f64"], default="auto")
+    ap.add_argument("--mode", choices=["auto", "tc", "otf", "f32", "f64"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch measurement")
     args = ap.parse_args()

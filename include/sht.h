@@ -83,9 +83,20 @@ enum {
                         * The panels take about 2 (lmax+1)^3 bytes (2.2 GB at
                         * lmax = 1023; twice that once a vector call was made) and
                         * are built by the first call in this mode or by sht_reserve. */
-    SHT_F32_AUTO = 3   /* FP32 data: whichever of SHT_F32 and SHT_TC_BF16X3 sht_tune
-                        * measured faster for this batch size (SHT_F32 if untuned);
-                        * vector transforms take SHT_F32. */
+    SHT_F32_AUTO = 3,  /* FP32 data: whichever of SHT_F32, SHT_TC_BF16X3 and SHT_TC_OTF
+                        * sht_tune measured fastest for this batch size (SHT_F32 if
+                        * untuned); vector transforms take SHT_F32. */
+    SHT_TC_OTF = 4     /* FP32 data; the same tensor-core contraction, but P_n^m is
+                        * generated on the fly (the variant of Sec. 3.1 the paper
+                        * favours) by CUDA-core warps inside the contraction kernel:
+                        * the FP32 recurrence of Sec. 3.2, restarted every 32 degrees
+                        * from seeds computed once by the FP64 recurrence with the
+                        * rescaling of Sec. 3.5, so rounding errors grow over at most
+                        * 32 steps.  Seeds take 16 (lmax+1)^2 ceil(nlat/2) / 64 bytes
+                        * (138 MB at lmax = 1023) instead of the panels' ~(lmax+1)^3.
+                        * Scalar transforms and adjoints; vector calls run
+                        * SHT_TC_BF16X3.  SHT_EUNSUPPORTED if a segment of the
+                        * recurrence would leave the FP32 range (large lmax). */
 };
 
 /* Build a plan (Sec. 2.3 nodes/weights, Sec. 3.2 recurrence tables, FFT
@@ -180,12 +191,14 @@ SHT_API int sht_synth_static(sht_handle h, const void *spec, void *grid, int bat
  * candidate kernel shapes of the Legendre stage (latitude pairs per thread x
  * fields per CTA) for `batch` fields in `mode` (SHT_F64 or SHT_F32) and keep
  * the fastest for later calls with that batch size.  With SHT_F32_AUTO it also
- * times a full FP32 round trip on the CUDA cores (on-the-fly recurrence)
- * against the tensor-core path (precomputed panels) -- the paper's two
- * variants -- and records the faster for SHT_F32_AUTO calls at that batch.
- * report (may be NULL): report[0], report[1] = best synthesis and analysis
- * Legendre times in ms (SHT_F64/SHT_F32), or FP32 and tensor-core round-trip
- * times in ms (SHT_F32_AUTO).  Allocates temporary buffers, synchronises the
+ * times full round trips of the FP32 CUDA-core path, the tensor-core path with
+ * precomputed panels and the tensor-core path with on-the-fly P_n^m (the
+ * paper's precomputed and on-the-fly variants) and records the fastest for
+ * SHT_F32_AUTO calls at that batch.
+ * report (may be NULL, else 3 doubles): report[0], report[1] = best synthesis
+ * and analysis Legendre times in ms (SHT_F64/SHT_F32; report[2] = -1), or the
+ * round-trip times in ms of SHT_F32, SHT_TC_BF16X3 and SHT_TC_OTF (SHT_F32_AUTO;
+ * -1 for a path that could not run).  Allocates temporary buffers, synchronises the
  * stream, and takes from milliseconds to a few seconds. */
 SHT_API int sht_tune(sht_handle h, int batch, int mode, double *report, void *stream);
 
@@ -232,15 +245,16 @@ SHT_API const char *sht_kernel_name(int kind);
 
 /* Static polar optimisation of the tensor-core mode (Sec. 3.1): panel chunks
  * whose values are all below 2^-40 (near the poles at high order) are neither
- * loaded nor multiplied.  Fractions of the synthesis and analysis panel chunks
- * skipped, or -1 if the panels are not built yet. */
+ * loaded nor multiplied (SHT_TC_OTF: neither generated nor multiplied).
+ * Fractions of the synthesis and analysis chunks skipped -- of the panels if
+ * built, else of the on-the-fly mode's tables -- or -1 if neither is built. */
 SHT_API int sht_tc_polar_skip(sht_handle h, double *synth_frac, double *analys_frac);
 
 /* Threshold of that optimisation (the paper leaves its value open; default
  * 2^-40): a panel chunk is skipped while all its |P_n^m| (and, for the vector
  * transforms, |sin(theta) dP/dtheta|) are below it.  0 skips nothing.  Must
  * be in [0, 1]; waits for the device to be idle, then recomputes the skip
- * tables if the panels exist. */
+ * tables that exist. */
 SHT_API int sht_set_polar_threshold(sht_handle h, double threshold);
 
 /* Failure-detection self-test (no counterpart in the paper): enqueue a kernel

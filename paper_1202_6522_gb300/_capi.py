@@ -24,6 +24,7 @@ SHT_F64 = 0
 SHT_F32 = 1
 SHT_TC_BF16X3 = 2
 SHT_F32_AUTO = 3
+SHT_TC_OTF = 4
 
 _lib = None
 _lock = threading.Lock()
@@ -214,10 +215,10 @@ def sht_batch_analys(b, grid_ptrs, spec_ptrs, use_graph, stream):
 
 
 def sht_tune(h, batch, mode, stream):
-    """Runtime tuning; returns the two timings of the report (ms)."""
-    rep = (ctypes.c_double * 2)()
+    """Runtime tuning; returns the three timings of the report (ms)."""
+    rep = (ctypes.c_double * 3)()
     check(_call("sht_tune", h, batch, mode, rep, stream))
-    return rep[0], rep[1]
+    return rep[0], rep[1], rep[2]
 
 
 def sht_tc_polar_skip(h):

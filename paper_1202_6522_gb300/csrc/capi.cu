@@ -39,7 +39,7 @@ int check_handle(sht_handle h)
 
 int check_mode(int mode)
 {
-    if (mode != SHT_F64 && mode != SHT_F32 && mode != SHT_TC_BF16X3 && mode != SHT_F32_AUTO)
+    if (mode != SHT_F64 && mode != SHT_F32 && mode != SHT_TC_BF16X3 && mode != SHT_F32_AUTO && mode != SHT_TC_OTF)
         return fail(SHT_EINVAL, "unknown mode");
     return SHT_OK;
 }
@@ -173,11 +173,78 @@ int ensure_vec_panels(sht::Plan &p)
     return SHT_OK;
 }
 
+void free_otf(sht::Plan &p)
+{
+    cudaFree(p.otf_seeds); cudaFree(p.d_segoff); cudaFree(p.d_c0o_s); cudaFree(p.d_c0o_a);
+    p.otf_seeds = nullptr;
+    p.d_segoff = nullptr;
+    p.d_c0o_s = p.d_c0o_a = nullptr;
+}
+
+// Seeds of the on-the-fly mode (float4 per pair and 32-degree segment, about
+// 16 (lmax+1)^2 npairs / 64 bytes: 138 MB at lmax = 1023) and its polar-skip
+// tables, built once by the FP64 recurrence.
+cudaError_t otf_build(sht::Plan &p, int *flag_dev)
+{
+    cudaError_t e = cudaMemset(flag_dev, 0, sizeof(int));
+    if (e == cudaSuccess)
+        e = sht::launch_build_seeds(p.view64(), p.d_segoff, p.otf_seeds, p.polar_thr, p.d_c0o_s, p.d_c0o_a, flag_dev,
+                                    0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = sht::tc_polar_stats(p.lmax, p.mmax, p.npairs, p.d_c0o_s, p.d_c0o_a, p.otf_skip_s, p.otf_skip_a);
+    return e;
+}
+
+int ensure_otf(sht::Plan &p)
+{
+    if (p.otf_state > 0) return SHT_OK;
+    if (p.otf_state < 0)
+        return fail(SHT_EUNSUPPORTED, "on-the-fly mode: the FP32 recurrence would leave the FP32 range for this plan");
+    std::vector<unsigned long long> segoff;
+    const size_t nseg = sht::otf_segment_offsets(p.lmax, p.mmax, segoff);
+    std::vector<unsigned long long> off_s, off_a, dchunk;
+    size_t bs = 0, ba = 0, nch = 0;
+    sht::tc_panel_layout(p.lmax, p.mmax, p.npairs, off_s, off_a, bs, ba, dchunk, nch);
+    int T_s = 0, T_a = 0;
+    sht::tc_tile_counts(p.lmax, p.npairs, T_s, T_a);
+    int *flag = nullptr;
+    cudaError_t e = cudaMalloc(&p.otf_seeds, sizeof(float4) * nseg * (size_t)p.npairs);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_segoff, sizeof(unsigned long long) * segoff.size());
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_c0o_s, sizeof(int) * (size_t)(p.mmax + 1) * T_s);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_c0o_a, sizeof(int) * (size_t)(p.mmax + 1) * T_a);
+    if (e == cudaSuccess) e = cudaMalloc(&flag, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(flag);
+        free_otf(p);
+        return fail(SHT_ENOMEM, std::string("cudaMalloc(on-the-fly seeds): ") + cudaGetErrorString(e));
+    }
+    p.tc_nchunk_s = nch;
+    e = cudaMemcpy(p.d_segoff, segoff.data(), sizeof(unsigned long long) * segoff.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = otf_build(p, flag);
+    int hflag = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(flag);
+    if (e != cudaSuccess) {
+        free_otf(p);
+        return fail(SHT_ECUDA, std::string("building on-the-fly seeds: ") + cudaGetErrorString(e));
+    }
+    if (hflag) {
+        free_otf(p);
+        p.otf_state = -1;
+        return fail(SHT_EUNSUPPORTED, "on-the-fly mode: the FP32 recurrence would leave the FP32 range for this plan");
+    }
+    p.otf_state = 1;
+    return SHT_OK;
+}
+
 size_t elem_size(int mode) { return mode == SHT_F64 ? sizeof(double) : sizeof(float); }
 
 // Tensor-core scalar transforms: the Legendre contraction on tcgen05, FFTs in FP32.
 int run_synth_tc(sht::Plan &p, const void *spec, void *grid, int batch, sht::Op op, cudaStream_t s);
 int run_analys_tc(sht::Plan &p, const void *grid, void *spec, int batch, sht::Op op, cudaStream_t s);
+int run_otf(sht::Plan &p, bool synth, const void *in_, void *out_, int batch, sht::Op op, cudaStream_t s);
 int run_synth_vec_tc(sht::Plan &p, const void *S, const void *T, void *vt, void *vp, int batch, sht::Op op,
                      cudaStream_t s);
 int run_analys_vec_tc(sht::Plan &p, const void *vt, const void *vp, void *S, void *T, int batch, sht::Op op,
@@ -362,9 +429,13 @@ int run_analys_vec(sht::Plan &p, const sht::PlanView<T> &pv, const void *vt, con
 // SHT_F32_AUTO resolves to the path sht_tune found faster for this batch.
 int resolve_mode(const sht::Plan &p, int mode, int batch, bool vector)
 {
+    if (vector) {
+        if (mode == SHT_F32_AUTO) return SHT_F32;
+        if (mode == SHT_TC_OTF) return SHT_TC_BF16X3;   // vector transforms use the panels
+        return mode;
+    }
     if (mode != SHT_F32_AUTO) return mode;
-    if (vector) return SHT_F32;
-    return tuned_shape(p, SHT_F32_AUTO, batch).prefer_tc ? SHT_TC_BF16X3 : SHT_F32;
+    return tuned_shape(p, SHT_F32_AUTO, batch).auto_mode;
 }
 
 int scalar_s2g(sht_handle h, const void *spec, void *grid, int batch, int mode, void *stream, sht::Op op)
@@ -378,6 +449,11 @@ int scalar_s2g(sht_handle h, const void *spec, void *grid, int batch, int mode, 
         if ((rc = ensure_panels(h->p))) return rc;
         if ((rc = ensure_work(h->p, tc_work_bytes(h->p, batch, false)))) return rc;
         return run_synth_tc(h->p, spec, grid, batch, op, s);
+    }
+    if (mode == SHT_TC_OTF) {
+        if ((rc = ensure_otf(h->p))) return rc;
+        if ((rc = ensure_work(h->p, tc_work_bytes(h->p, batch, false)))) return rc;
+        return run_otf(h->p, true, spec, grid, batch, op, s);
     }
     if ((rc = ensure_work(h->p, inter_bytes(h->p, batch, mode)))) return rc;
     if (mode == SHT_F64) return run_synth<double>(h->p, h->p.view64(), spec, grid, batch, op, s);
@@ -395,6 +471,11 @@ int scalar_g2s(sht_handle h, const void *grid, void *spec, int batch, int mode, 
         if ((rc = ensure_panels(h->p))) return rc;
         if ((rc = ensure_work(h->p, tc_work_bytes(h->p, batch, false)))) return rc;
         return run_analys_tc(h->p, grid, spec, batch, op, s);
+    }
+    if (mode == SHT_TC_OTF) {
+        if ((rc = ensure_otf(h->p))) return rc;
+        if ((rc = ensure_work(h->p, tc_work_bytes(h->p, batch, false)))) return rc;
+        return run_otf(h->p, false, grid, spec, batch, op, s);
     }
     if ((rc = ensure_work(h->p, inter_bytes(h->p, batch, mode)))) return rc;
     if (mode == SHT_F64) return run_analys<double>(h->p, h->p.view64(), grid, spec, batch, op, s);
@@ -476,6 +557,43 @@ int run_analys_tc(sht::Plan &p, const void *grid, void *spec, int batch, sht::Op
             return sht::launch_tc_legendre(false, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_a, p.d_off_a, p.d_c0_a,
                                            p.d_dchunk, data, sd, out, nb, op, p.d_err, false, s);
         });
+        if (rc) return rc;
+    }
+    return SHT_OK;
+}
+
+// On-the-fly mode: synthesis = contraction then FFT; analysis = FFT then contraction.
+int run_otf(sht::Plan &p, bool synth, const void *in_, void *out_, int batch, sht::Op op, cudaStream_t s)
+{
+    const int chunk = tc_chunk(false);
+    float *inter = static_cast<float *>(p.work);
+    unsigned char *data = static_cast<unsigned char *>(p.work) + tc_data_offset(p, batch, false);
+    const sht::PlanView<float> pv = p.view32();
+    for (int b0 = 0; b0 < batch; b0 += chunk) {
+        const int nb = batch - b0 < chunk ? batch - b0 : chunk;
+        const size_t so = (size_t)b0 * p.nlm * 2, go = (size_t)b0 * p.nlat * p.nphi;
+        int rc;
+        if (synth) {
+            const float *in = static_cast<const float *>(in_) + so;
+            float *out = static_cast<float *>(out_) + go;
+            rc = timed(p, SHT_K_TC_SYNTH, s, "on-the-fly tensor-core synthesis launch", [&] {
+                return sht::launch_tc_otf(true, p.lmax, p.mmax, p.npairs, p.nlm, p.otf_seeds, p.d_segoff, p.d_c0o_s,
+                                          pv.ab, pv.x, data, in, inter, nb, op, p.d_err, s);
+            });
+            if (rc) return rc;
+            rc = timed(p, SHT_K_FFT_SYNTH, s, "fft synthesis launch",
+                       [&] { return sht::launch_fft_synth<float>(pv, inter, out, nb, op, s); });
+        } else {
+            const float *in = static_cast<const float *>(in_) + go;
+            float *out = static_cast<float *>(out_) + so;
+            rc = timed(p, SHT_K_FFT_ANALYS, s, "fft analysis launch",
+                       [&] { return sht::launch_fft_analys<float>(pv, in, inter, nb, op, false, s); });
+            if (rc) return rc;
+            rc = timed(p, SHT_K_TC_ANALYS, s, "on-the-fly tensor-core analysis launch", [&] {
+                return sht::launch_tc_otf(false, p.lmax, p.mmax, p.npairs, p.nlm, p.otf_seeds, p.d_segoff, p.d_c0o_a,
+                                          pv.ab, pv.x, data, inter, out, nb, op, p.d_err, s);
+            });
+        }
         if (rc) return rc;
     }
     return SHT_OK;
@@ -593,6 +711,10 @@ int sht_reserve(sht_handle h, int batch, int mode)
         const size_t a = tc_work_bytes(h->p, batch, false), b = tc_work_bytes(h->p, batch, true);
         return ensure_work(h->p, a > b ? a : b);
     }
+    if (mode == SHT_TC_OTF) {
+        if ((rc = ensure_otf(h->p))) return rc;
+        return ensure_work(h->p, tc_work_bytes(h->p, batch, false));
+    }
     return ensure_work(h->p, 2 * inter_bytes(h->p, batch, mode));
 }
 
@@ -666,8 +788,10 @@ int sht_tc_polar_skip(sht_handle h, double *synth_frac, double *analys_frac)
 {
     if (!h) return fail(SHT_EINVAL, "null handle");
     if (!synth_frac || !analys_frac) return fail(SHT_EINVAL, "null output pointer");
-    *synth_frac = h->p.panel_s ? h->p.polar_skip_s : -1.0;
-    *analys_frac = h->p.panel_s ? h->p.polar_skip_a : -1.0;
+    // the panels' tables if built, else those of the on-the-fly mode
+    const sht::Plan &p = h->p;
+    *synth_frac = p.panel_s ? p.polar_skip_s : (p.otf_state > 0 ? p.otf_skip_s : -1.0);
+    *analys_frac = p.panel_s ? p.polar_skip_a : (p.otf_state > 0 ? p.otf_skip_a : -1.0);
     return SHT_OK;
 }
 
@@ -678,9 +802,8 @@ int sht_set_polar_threshold(sht_handle h, double threshold)
     if (!(threshold >= 0.0) || threshold > 1.0) return fail(SHT_EINVAL, "polar threshold must be in [0, 1]");
     sht::Plan &p = h->p;
     p.polar_thr = (float)threshold;
-    if (!p.panel_s) return SHT_OK;
     cudaError_t e = cudaDeviceSynchronize();   // no transform may be reading the tables
-    if (e == cudaSuccess) e = first_live_scalar(p);
+    if (e == cudaSuccess && p.panel_s) e = first_live_scalar(p);
     if (e == cudaSuccess && p.dpanel_s) {
         int T_s = 0, T_a = 0;
         sht::tc_tile_counts(p.lmax, p.npairs, T_s, T_a);
@@ -688,6 +811,12 @@ int sht_set_polar_threshold(sht_handle h, double threshold)
         e = cudaMalloc(&tmp, sizeof(int) * (size_t)(p.mmax + 1) * (T_s > T_a ? T_s : T_a));
         if (e == cudaSuccess) e = first_live_vector(p, tmp);
         cudaFree(tmp);
+    }
+    if (e == cudaSuccess && p.otf_state > 0) {
+        int *flag = nullptr;
+        e = cudaMalloc(&flag, sizeof(int));
+        if (e == cudaSuccess) e = otf_build(p, flag);
+        cudaFree(flag);
     }
     if (e != cudaSuccess) return fail(SHT_ECUDA, std::string("sht_set_polar_threshold: ") + cudaGetErrorString(e));
     return SHT_OK;
@@ -841,7 +970,7 @@ extern "C" int sht_tune(sht_handle h, int batch, int mode, double *report, void 
         }
     cudaGetLastError();
     set_tuned(p, shape_mode, batch, best);
-    if (report) { report[0] = best_syn; report[1] = best_ana; }
+    if (report) { report[0] = best_syn; report[1] = best_ana; report[2] = -1.0; }
     if (mode == SHT_F32_AUTO) {
         // the paper's choice: on-the-fly recurrence (FP32 cores) vs precomputed P (tensor cores)
         bool ok1 = false, ok2 = false;
@@ -849,17 +978,32 @@ extern "C" int sht_tune(sht_handle h, int batch, int mode, double *report, void 
             if (scalar_s2g(h, spec, grid, batch, SHT_F32, s, sht::OP_SYNTH)) return cudaErrorUnknown;
             return scalar_g2s(h, grid, spec, batch, SHT_F32, s, sht::OP_ANALYS) ? cudaErrorUnknown : cudaSuccess;
         }, s, reps, ok1);
-        double ms_tc = 1e30;
+        double ms_tc = 1e30, ms_otf = 1e30;
+        bool ok3 = false;
         if (ensure_panels(p) == SHT_OK) {
             ms_tc = time_ms([&] {
                 if (scalar_s2g(h, spec, grid, batch, SHT_TC_BF16X3, s, sht::OP_SYNTH)) return cudaErrorUnknown;
                 return scalar_g2s(h, grid, spec, batch, SHT_TC_BF16X3, s, sht::OP_ANALYS) ? cudaErrorUnknown : cudaSuccess;
             }, s, reps, ok2);
         }
+        if (ensure_otf(p) == SHT_OK) {
+            ms_otf = time_ms([&] {
+                if (scalar_s2g(h, spec, grid, batch, SHT_TC_OTF, s, sht::OP_SYNTH)) return cudaErrorUnknown;
+                return scalar_g2s(h, grid, spec, batch, SHT_TC_OTF, s, sht::OP_ANALYS) ? cudaErrorUnknown : cudaSuccess;
+            }, s, reps, ok3);
+        }
+        cudaGetLastError();
         sht::TunedShape a = best;
-        a.prefer_tc = ok2 && ms_tc < ms_f32;
+        a.auto_mode = SHT_F32;
+        double best_ms = ok1 ? ms_f32 : 1e30;
+        if (ok2 && ms_tc < best_ms) { best_ms = ms_tc; a.auto_mode = SHT_TC_BF16X3; }
+        if (ok3 && ms_otf < best_ms) { best_ms = ms_otf; a.auto_mode = SHT_TC_OTF; }
         set_tuned(p, SHT_F32_AUTO, batch, a);
-        if (report) { report[0] = ok1 ? ms_f32 : -1.0; report[1] = ok2 ? ms_tc : -1.0; }
+        if (report) {
+            report[0] = ok1 ? ms_f32 : -1.0;
+            report[1] = ok2 ? ms_tc : -1.0;
+            report[2] = ok3 ? ms_otf : -1.0;
+        }
     }
     cudaStreamSynchronize(s);
     cudaFree(spec);

@@ -284,6 +284,13 @@ void plan_free(Plan &p)
     if (p.dpanel_a) cudaFree(p.dpanel_a);
     if (p.d_c0v_s) cudaFree(p.d_c0v_s);
     if (p.d_c0v_a) cudaFree(p.d_c0v_a);
+    if (p.otf_seeds) cudaFree(p.otf_seeds);
+    if (p.d_segoff) cudaFree(p.d_segoff);
+    if (p.d_c0o_s) cudaFree(p.d_c0o_s);
+    if (p.d_c0o_a) cudaFree(p.d_c0o_a);
+    p.otf_seeds = nullptr;
+    p.d_segoff = nullptr;
+    p.d_c0o_s = p.d_c0o_a = nullptr;
     p.panel_s = p.panel_a = p.dpanel_s = p.dpanel_a = nullptr;
     p.d_off_s = p.d_off_a = p.d_dchunk = nullptr;
     p.d_c0_s = p.d_c0_a = p.d_c0v_s = p.d_c0v_a = nullptr;

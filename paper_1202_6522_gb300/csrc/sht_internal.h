@@ -70,7 +70,7 @@ enum Op {
 // Kernel shapes chosen by sht_tune for one (precision, batch).
 struct TunedShape {
     int synth_lpt = 0, synth_bc = 0, analys_lpt = 0, analys_bc = 0;
-    bool prefer_tc = false;      // SHT_F32_AUTO: the tensor-core path was faster
+    int auto_mode = 1;           // SHT_F32_AUTO: the fastest of SHT_F32, SHT_TC_BF16X3, SHT_TC_OTF
 };
 
 // Event pairs recorded around kernel launches while profiling is enabled.
@@ -96,6 +96,11 @@ struct Plan {
     float polar_thr = 0x1p-40f;                 // polar threshold (sht_set_polar_threshold)
     unsigned char *dpanel_s = nullptr, *dpanel_a = nullptr; // sin(theta) dP/dtheta panels (vector)
     int *d_c0v_s = nullptr, *d_c0v_a = nullptr; // first chunk live in P or dP
+    float4 *otf_seeds = nullptr;                // on-the-fly mode: recurrence seeds
+    unsigned long long *d_segoff = nullptr;     // first segment of each order
+    int *d_c0o_s = nullptr, *d_c0o_a = nullptr; // on-the-fly mode: first live chunk per (m, tile)
+    int otf_state = 0;                          // 0 not built, 1 built, -1 not supported for this plan
+    double otf_skip_s = 0, otf_skip_a = 0;      // on-the-fly mode: fraction of chunks skipped
     void *work = nullptr;            // scratch (grown on demand)
     size_t work_bytes = 0;
     int device = 0;
@@ -207,5 +212,20 @@ cudaError_t tc_polar_stats(int lmax, int mmax, int npairs, const int *d_c0_s, co
                            double &frac_a);
 int tc_max_batch();
 cudaError_t launch_selftest_timeout(int *err, unsigned long long max_ns, cudaStream_t st);
+
+// On-the-fly mode (tc.cu): FP32 recurrence reseeded every 32 degrees.
+// Segment offsets per order (= synthesis data chunk numbering); returns the
+// total number of segments.
+size_t otf_segment_offsets(int lmax, int mmax, std::vector<unsigned long long> &segoff);
+// Seeds [segments][npairs] float4 and the polar-skip tables (first live chunk
+// per (m, synthesis tile) and per (m, analysis tile)); *flag set if some
+// segment would exceed the FP32 range.
+cudaError_t launch_build_seeds(const PlanView<double> &pv, const unsigned long long *segoff, float4 *seeds,
+                               float thr, int *c0s, int *c0a, int *flag, cudaStream_t st);
+// Scalar contraction (prep + on-the-fly kernel) of <= tc_max_batch() fields.
+cudaError_t launch_tc_otf(bool synth, int lmax, int mmax, int npairs, int nlm, const float4 *seeds,
+                          const unsigned long long *segoff, const int *c0, const float2 *ab32, const float *x32,
+                          unsigned char *data, const float *in, float *out, int batch, Op op, int *err,
+                          cudaStream_t st);
 
 }  // namespace sht

@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <vector>
 
 #include "sht_internal.h"
@@ -560,6 +561,459 @@ __global__ void __launch_bounds__(128, 1) k_tc_vec(TcArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// On-the-fly P_n^m for the contraction (mode SHT_TC_OTF): instead of streaming
+// precomputed panels from HBM, four warps run the recurrence of Sec. 3.2 in
+// FP32 and write the bf16 hi/lo operand straight into shared memory -- the
+// on-the-fly variant of Sec. 3.1 feeding the tensor cores.  The FP32
+// recurrence restarts every kSeg degrees from a seed computed once per plan
+// by the FP64 recurrence with the rescaling of Sec. 3.5, so its rounding
+// errors grow over at most kSeg steps instead of N.
+//
+// Seed (m, segment s, pair p), s covering n - m in [kSeg s, kSeg s + kSeg):
+// the recurrence state entering the segment, (P_{n0-1}, P_{n0-2}) at
+// n0 = m + kSeg s ((0, P_m^m) for s = 0), as FP32 (y1, y2) times a power of
+// two 2^E held as the FP32 value `scale` (0 when 2^E is below the FP32
+// range), E the exponent of the largest |P_n^m| of the segment, and the
+// pair's FP32 cos(theta): float4 (y1, y2, scale, x).
+// ---------------------------------------------------------------------------
+constexpr int kSeg = 2 * kKc;                // degrees per segment = one synthesis chunk
+constexpr int kSegPerTile = 2 * kRows / kSeg; // segments per analysis tile (128 rows per parity)
+constexpr int kOtfGrowthLog2 = 120;           // largest growth within a segment (FP32 range of the seed)
+
+// One thread per (m, pair).  Also records, for the polar optimisation, the
+// first live synthesis chunk of each (m, pair tile) and the first live pair
+// chunk of each (m, degree tile) (atomicMin into tables initialised to the
+// chunk counts), and sets *flag when a seed would fall below the FP32 range
+// (a segment growing by more than 2^120).
+__global__ void __launch_bounds__(128)
+k_build_seeds(PlanView<double> pv, const unsigned long long *__restrict__ segoff, float4 *__restrict__ seeds,
+              float thr, int *__restrict__ c0s, int *__restrict__ c0a, int ntiles_s, int ntiles_a,
+              int *__restrict__ flag)
+{
+    const int m = blockIdx.y;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int npairs = pv.npairs, lmax = pv.lmax;
+    if (p >= npairs) return;
+    const int L = lmax - m + 1;
+    const int nseg = (L + kSeg - 1) / kSeg;
+    const long col = col_of(lmax, m);
+    const double x = pv.x[p];
+    double y2 = pv.pmm[(size_t)m * npairs + p], y1 = 0.0;
+    int k = pv.pmmk[(size_t)m * npairs + p];
+    int first_s = nseg;
+    bool tile_live = false;
+    bool underflow = false;
+    for (int s = 0; s < nseg; ++s) {
+        // state entering the segment
+        const double s1 = y1, s2 = y2;
+        const int sk = k;
+        // run the segment: largest exponent of its values, liveness
+        int emax = INT_MIN;
+        bool live = false;
+        for (int i = 0; i < kSeg; ++i) {
+            const int nn = kSeg * s + i;
+            if (nn >= L) break;
+            const double2 ab = pv.ab[col + nn];
+            const double yn = fma(ab.x * x, y1, ab.y * y2);
+            y2 = y1;
+            y1 = yn;
+            if (k > 0 && fabs(yn) >= 1.0) {
+                y1 *= 0x1p-240;
+                y2 *= 0x1p-240;
+                k -= 1;
+            }
+            if (y1 != 0.0) emax = max(emax, ilogb(y1) - Scale<double>::S * k);
+            if ((k == 0 && fabs(y1) >= (double)thr) || thr == 0.f) live = true;
+        }
+        // seed normalised so that the largest value of the segment is in [1, 2):
+        // the FP32 chain then stays below 2 and the seed, at most ~2^116 smaller
+        // at lmax = 1023, stays a normal FP32 number
+        float4 sd = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (emax != INT_MIN) {
+            const int sh = -Scale<double>::S * sk - emax;   // true value * 2^-emax = y * 2^sh
+            const double t1 = scalbn(s1, sh), t2 = scalbn(s2, sh);
+            sd.x = (float)t1;
+            sd.y = (float)t2;
+            sd.z = emax >= -149 ? scalbnf(1.0f, emax) : 0.0f;
+            const double tmax = fmax(fabs(t1), fabs(t2));
+            if (tmax > 0.0 && ilogb(tmax) < -kOtfGrowthLog2) underflow = true;
+        }
+        sd.w = (float)x;
+        seeds[(segoff[m] + s) * npairs + p] = sd;
+        if (live && first_s == nseg) first_s = s;
+        tile_live |= live;
+        // end of a degree tile of the analysis: record this pair's chunk if live
+        if ((s + 1) % kSegPerTile == 0 || s + 1 == nseg) {
+            if (tile_live) atomicMin(&c0a[m * ntiles_a + s / kSegPerTile], p / kKc);
+            tile_live = false;
+        }
+    }
+    atomicMin(&c0s[m * ntiles_s + p / kRows], first_s);
+    if (underflow) atomicOr(flag, 1);
+}
+
+// c0 tables before k_build_seeds: the chunk counts (nothing live).
+__global__ void k_init_c0(int lmax, int mmax, int npairs, int ntiles_s, int ntiles_a, int *c0s, int *c0a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = i / (ntiles_s + ntiles_a);
+    if (m > mmax) return;
+    const int t = i - m * (ntiles_s + ntiles_a);
+    const int Le = (lmax - m + 2) / 2;
+    if (t < ntiles_s) c0s[m * ntiles_s + t] = (Le + kKc - 1) / kKc;
+    else c0a[m * ntiles_a + (t - ntiles_s)] = (npairs + kKc - 1) / kKc;
+}
+
+struct OtfArgs {
+    int lmax, mmax, npairs, nlm, batch, rows, ntiles, stages, op, nab;
+    const float4 *seeds;
+    const unsigned long long *segoff;   // first segment (= synthesis data chunk) of each order
+    const int *c0;                      // per (m, tile): first live chunk
+    const float2 *ab;                   // FP32 recurrence coefficients (a, b) per packed index
+    const float *x;                     // FP32 cos(theta) per pair
+    const unsigned char *data;          // data operand, blocked bf16 hi/lo
+    float *out;
+    int *err;
+};
+
+// Shared memory of the on-the-fly kernels: SA operand stages of kChunkPanel
+// bytes, SD data stages (data chunk + one seed per generator thread), the
+// (a, b) table, 2 SA + 2 SD + 1 mbarriers and the TMEM slot.
+constexpr size_t kOtfSeedBytes = kRows * sizeof(float4);
+__host__ __device__ inline size_t otf_dstage_bytes(int rows) { return data_chunk_bytes(rows) + kOtfSeedBytes; }
+__host__ __device__ inline size_t otf_smem_bytes(int rows, int sa, int sd, int nab)
+{
+    return 1024 + (size_t)sa * kChunkPanel + (size_t)sd * otf_dstage_bytes(rows) + (size_t)nab * sizeof(float2) +
+           8 * (2 * sa + 2 * sd + 2);
+}
+
+// Threads of the on-the-fly kernel: two groups of 4 generator warps (group g
+// generates the chunks u with u % 2 == g) and one producer / MMA warp.
+constexpr int kOtfGroups = 2;
+constexpr int kOtfThreads = 32 * (4 * kOtfGroups + 2);   // + MMA warp + producer warp
+
+// Bounded wait that also gives up when another thread of the CTA gave up.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort)
+{
+    const uint64_t t0 = tc::globaltimer();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        if (tc::mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 255u) {
+            if (*abort) return false;
+            if (tc::globaltimer() - t0 > kWaitNs) {
+                *abort = 1;
+                return false;
+            }
+        }
+    }
+    *abort = 1;
+    return false;
+}
+
+// v0, v1 -> bf16x2 hi and lo words with v = hi + lo per element.
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_t &lo)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+// kSeg steps of the FP32 recurrence from a seed (y1, y2, scale, x); P = y *
+// scale split into bf16 hi/lo and packed per parity: w[par][j] holds the
+// values of parity par at K positions 2j and 2j + 1 (j < kKc / 2).
+__device__ __forceinline__ void otf_segment(const float2 *__restrict__ ab, float4 sd, uint32_t (&hw)[2][kKc / 2],
+                                            uint32_t (&lw)[2][kKc / 2])
+{
+    float y1 = sd.x, y2 = sd.y;
+    const float sc = sd.z, x = sd.w;
+#pragma unroll
+    for (int j = 0; j < kKc / 2; ++j) {
+        float P[4];   // degrees 4j .. 4j + 3: (par 0, k 2j), (par 1, k 2j), (par 0, k 2j+1), (par 1, k 2j+1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 c = ab[4 * j + i];
+            const float yn = fmaf(c.x * x, y1, c.y * y2);
+            y2 = y1;
+            y1 = yn;
+            P[i] = yn * sc;
+        }
+        split2(P[0], P[2], hw[0][j], lw[0][j]);
+        split2(P[1], P[3], hw[1][j], lw[1][j]);
+    }
+}
+
+// Writes one generator thread's packed words into an operand stage.
+template <bool SYNTH>
+__device__ __forceinline__ void otf_store(unsigned char *st, int tid, const uint32_t (&hw)[2][kKc / 2],
+                                          const uint32_t (&lw)[2][kKc / 2])
+{
+#pragma unroll
+    for (int par = 0; par < 2; ++par) {
+        unsigned char *bh = st + (size_t)(par * 2) * kBlk, *bl = bh + kBlk;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t off;
+            if (SYNTH) {
+                off = blk_off(tid, 8 * h);   // row = pair, K = degrees of this parity
+            } else {
+                // MN-major: 8 degrees contiguous per pair; core matrices 128 B
+                // apart along the degrees, 2 KB apart along the pairs
+                const int kr = 2 * (tid / kKc) + h;
+                const int j = tid % kKc;
+                off = (uint32_t)(kr * 128 + (j >> 3) * 2048 + (j & 7) * 16);
+            }
+            *reinterpret_cast<uint4 *>(bh + off) =
+                make_uint4(hw[par][4 * h], hw[par][4 * h + 1], hw[par][4 * h + 2], hw[par][4 * h + 3]);
+            *reinterpret_cast<uint4 *>(bl + off) =
+                make_uint4(lw[par][4 * h], lw[par][4 * h + 1], lw[par][4 * h + 2], lw[par][4 * h + 3]);
+        }
+    }
+}
+
+// The contraction with on-the-fly P.  Warps 0-7 generate the operand (two
+// groups of four, alternate chunks; group 0 also runs the epilogue); warp 8
+// lane 0 issues the MMAs; warp 9 lane 0 streams the data chunks and their
+// seeds, up to SD chunks ahead of the MMAs.  Synthesis: CTA
+// (m, 128-pair tile), chunk = 32 degrees, generator thread = pair row, operand
+// K-major.  Analysis: CTA (m, 128-row degree tile per parity), chunk = 16
+// pairs, generator thread = (degree segment of the tile, pair), operand
+// MN-major (degrees contiguous).
+// Barriers: bar_load[SD] (data + seeds arrived), bar_dfree[SD] (MMAs that read
+// the data stage done), bar_gen[SA] (operand written, 4 warp arrivals),
+// bar_mma[SA] (MMAs that read the operand stage done), bar_done.
+template <bool SYNTH>
+__global__ void __launch_bounds__(kOtfThreads, 2) k_tc_otf(OtfArgs a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int SA = a.stages & 0xff, SD = a.stages >> 8, NC = a.rows;
+    const size_t dbytes = data_chunk_bytes(NC);
+    const size_t dstage = otf_dstage_bytes(NC);
+    const size_t blk = (size_t)NC * kKc * 2;
+    unsigned char *opnd = smem;                                  // SA x kChunkPanel
+    unsigned char *dst = opnd + (size_t)SA * kChunkPanel;        // SD x (data | seeds)
+    float2 *ab_s = reinterpret_cast<float2 *>(dst + (size_t)SD * dstage);
+    uint64_t *bar_load = reinterpret_cast<uint64_t *>(ab_s + a.nab);
+    uint64_t *bar_dfree = bar_load + SD;
+    uint64_t *bar_gen = bar_dfree + SD;
+    uint64_t *bar_mma = bar_gen + SA;
+    uint64_t *bar_done = bar_mma + SA;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_done + 1);
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    const int m = blockIdx.x / a.ntiles;
+    const int tile = blockIdx.x - m * a.ntiles;
+    const int lmax = a.lmax, npairs = a.npairs;
+    const int L = lmax - m + 1;
+    const int Le = (L + 1) / 2;
+    const long col = col_of(lmax, m);
+    if (!SYNTH && tile * kRows >= Le) return;
+    const int nseg = (L + kSeg - 1) / kSeg;
+    const int kch = (npairs + kKc - 1) / kKc;
+    const int nchunks = SYNTH ? nseg : kch;
+    const int cstart = a.c0[m * a.ntiles + tile];
+    const int nlive = nchunks - cstart;
+    const uint32_t ncols = NC * 2 <= 64 ? 64 : (NC * 2 <= 128 ? 128 : 256);
+    // degrees held in the (a, b) table: the whole order (synthesis) or the tile (analysis)
+    const int nn_base = SYNTH ? 0 : 2 * kRows * tile;
+
+    const unsigned char *data = a.data + (SYNTH ? a.segoff[m] : (unsigned long long)m * kch) * dbytes;
+    // data chunk + seeds of chunk un into data stage un % SD (producer thread only)
+    auto issue = [&](int un) {
+        const int sn = un % SD;
+        const int c = cstart + un;
+        unsigned char *ds = dst + (size_t)sn * dstage;
+        float4 *sd = reinterpret_cast<float4 *>(ds + dbytes);
+        // seed runs: synthesis one run of the tile's pairs; analysis one run
+        // of the chunk's pairs per segment of the tile
+        int np, ns;
+        if (SYNTH) {
+            np = min(kRows, npairs - tile * kRows);
+            ns = 1;
+        } else {
+            np = min(kKc, npairs - kKc * c);
+            ns = min(kSegPerTile, nseg - kSegPerTile * tile);
+        }
+        const uint32_t sbytes = (uint32_t)(np * ns) * (uint32_t)sizeof(float4);
+        tc::mbar_arrive_expect_tx(&bar_load[sn], (uint32_t)dbytes + sbytes);
+        tc::bulk_g2s(ds, data + (size_t)c * dbytes, (uint32_t)dbytes, &bar_load[sn]);
+        if (SYNTH) {
+            tc::bulk_g2s(sd, a.seeds + (a.segoff[m] + c) * npairs + tile * kRows, sbytes, &bar_load[sn]);
+        } else {
+            for (int sg = 0; sg < ns; ++sg)
+                tc::bulk_g2s(sd + sg * kKc, a.seeds + (a.segoff[m] + kSegPerTile * tile + sg) * npairs + kKc * c,
+                             (uint32_t)np * (uint32_t)sizeof(float4), &bar_load[sn]);
+        }
+    };
+    // the producer fills all SD data stages ahead; a stage is refilled once the
+    // MMAs of the chunk that last used it are done
+    const int DD = SD;
+    if (tid == 32 * (4 * kOtfGroups + 1)) {   // the producer thread
+        for (int q = 0; q < SD; ++q) {
+            tc::mbar_init(&bar_load[q], 1);
+            tc::mbar_init(&bar_dfree[q], 1);
+        }
+        for (int q = 0; q < SA; ++q) {
+            tc::mbar_init(&bar_gen[q], 4);
+            tc::mbar_init(&bar_mma[q], 1);
+        }
+        tc::mbar_init(bar_done, 1);
+        tc::mbar_fence_init();
+        s_abort = 0;
+        for (int u = 0; u < DD && u < nlive; ++u) issue(u);   // overlaps the table load below
+    }
+    {
+        // (a, b) of the degrees this CTA needs: loads first, then stores
+        constexpr int kAbIter = 4;   // nab <= kAbIter * kOtfThreads
+        float2 v[kAbIter];
+#pragma unroll
+        for (int k = 0; k < kAbIter; ++k) {
+            const int i = tid + k * kOtfThreads, nn = nn_base + i;
+            v[k] = (i < a.nab && nn < L) ? a.ab[col + nn] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < kAbIter; ++k) {
+            const int i = tid + k * kOtfThreads;
+            if (i < a.nab) ab_s[i] = v[k];
+        }
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, ncols);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp < 4 * kOtfGroups) {
+        // ---------------- operand generators ----------------
+        // group g generates chunks u = g, g + 2, ...; thread r = row within the
+        // group; seed slot: synthesis = pair row, analysis = segment * kKc + pair
+        const int g = warp / 4, r = tid - 128 * g;
+        for (int u = g; u < nlive; u += kOtfGroups) {
+            const int qa = u % SA, qd = u % SD;
+            const int c = cstart + u;
+            if (u >= SA && !wait_or_abort(&bar_mma[qa], (uint32_t)((u / SA - 1) & 1), &s_abort)) break;
+            if (!wait_or_abort(&bar_load[qd], (uint32_t)((u / SD) & 1), &s_abort)) break;
+            int pp, ss;
+            if (SYNTH) {
+                pp = tile * kRows + r;
+                ss = c;
+            } else {
+                pp = kKc * c + r % kKc;
+                ss = kSegPerTile * tile + r / kKc;
+            }
+            float4 sd = reinterpret_cast<const float4 *>(dst + (size_t)qd * dstage + dbytes)[r];
+            if (pp >= npairs || ss >= nseg) sd = make_float4(0.f, 0.f, 0.f, 0.f);
+            uint32_t hw[2][kKc / 2], lw[2][kKc / 2];
+            otf_segment(ab_s + (SYNTH ? kSeg * c : kSeg * (r / kKc)), sd, hw, lw);
+            otf_store<SYNTH>(opnd + (size_t)qa * kChunkPanel, r, hw, lw);
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&bar_gen[qa]);
+        }
+    } else if (warp == 4 * kOtfGroups && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        // descriptors of stage 0; a stage adds its byte offset / 16 to the
+        // start-address field (stage offsets stay far below the 256 KB field)
+        const uint32_t idesc = tc::idesc_bf16_f32(kRows, NC, !SYNTH);
+        uint64_t da0[2][2], db0[2][2];
+#pragma unroll
+        for (int par = 0; par < 2; ++par)
+#pragma unroll
+            for (int hl = 0; hl < 2; ++hl) {
+                const unsigned char *ap = opnd + (size_t)(par * 2 + hl) * kBlk;
+                da0[par][hl] = SYNTH ? tc::smem_desc(ap, kLbo, kSbo) : tc::smem_desc(ap, 2048, 128);
+                db0[par][hl] = tc::smem_desc(dst + (size_t)(par * 2 + hl) * blk, kLbo, kSbo);
+            }
+        const uint64_t astep = kChunkPanel >> 4, dstep = dstage >> 4;
+        bool ok = true;
+        for (int u = 0; u < nlive; ++u) {
+            const int qa = u % SA, qd = u % SD;
+            if (!wait_or_abort(&bar_load[qd], (uint32_t)((u / SD) & 1), &s_abort)) { ok = false; break; }
+            if (!wait_or_abort(&bar_gen[qa], (uint32_t)((u / SA) & 1), &s_abort)) { ok = false; break; }
+            tc::tc_fence_after();
+            const uint64_t ao = astep * (uint64_t)qa, bo = dstep * (uint64_t)qd;
+#pragma unroll
+            for (int par = 0; par < 2; ++par) {
+                const uint32_t d = tmem + (uint32_t)(par * NC);
+                tc::mma_bf16(d, da0[par][0] + ao, db0[par][0] + bo, idesc, u != 0);
+                tc::mma_bf16(d, da0[par][0] + ao, db0[par][1] + bo, idesc, true);
+                tc::mma_bf16(d, da0[par][1] + ao, db0[par][0] + bo, idesc, true);
+            }
+            tc::mma_commit(&bar_mma[qa]);
+            tc::mma_commit(&bar_dfree[qd]);
+        }
+        if (!ok) raise_err(a.err, SHT_ETIMEOUT);
+        tc::mma_commit(bar_done);
+    } else if (warp == 4 * kOtfGroups + 1 && lane == 0) {
+        // ---------------- data producer ----------------
+        // refills data stage un % SD once the MMAs of chunk un - SD are done
+        int issued_upto = min(DD, nlive);   // chunks 0 .. issued_upto - 1 already issued
+        bool ok = true;
+        for (int un = issued_upto; un < nlive; ++un) {
+            if (un >= SD) {
+                const int up = un - SD;
+                if (!wait_or_abort(&bar_dfree[up % SD], (uint32_t)((up / SD) & 1), &s_abort)) { ok = false; break; }
+            }
+            issue(un);
+            issued_upto = un + 1;
+        }
+        if (!ok) {
+            raise_err(a.err, SHT_ETIMEOUT);
+            // wait (bounded) for this CTA's own copies in flight: the last
+            // chunk issued to each data stage
+            for (int v = max(0, issued_upto - SD); v < issued_upto; ++v)
+                (void)tc::mbar_wait_bounded(&bar_load[v % SD], (uint32_t)((v / SD) & 1), 100000000ull);
+        }
+    }
+    bool ok = true;
+    if (warp < 4 * kOtfGroups) {
+        ok = wait_or_abort(bar_done, 0, &s_abort);
+        if (!ok) {
+            (void)tc::mbar_wait_bounded(bar_done, 0, 100000000ull);   // MMAs in flight
+            raise_err(a.err, SHT_ETIMEOUT);
+        }
+    }
+    ok = __syncthreads_and(ok && !*(volatile int *)&s_abort);
+    if (ok && warp < 4) {   // epilogue: generator group 0 (warp w reads TMEM lanes 32 w ..)
+        tc::tc_fence_after();
+        const int row = tile * kRows + warp * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int cb = 0; cb < NC; cb += 32) {
+            float de[32], dd[32];
+            if (nlive > 0) {
+                tc::tmem_ld32(lane_base + (uint32_t)cb, de);
+                tc::tmem_ld32(lane_base + (uint32_t)(NC + cb), dd);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) de[i] = dd[i] = 0.f;
+            }
+            for (int q = 0; q < 32; q += 2) {
+                const int b = (cb + q) >> 1;
+                if (b >= a.batch) break;
+                if (SYNTH) {
+                    if (row < npairs) {
+                        float4 *eo = reinterpret_cast<float4 *>(a.out);
+                        eo[((size_t)b * (a.mmax + 1) + m) * npairs + row] = make_float4(de[q], de[q + 1], dd[q], dd[q + 1]);
+                    }
+                } else {
+                    const int ne = 2 * row, no = 2 * row + 1;
+                    const float sc = (a.op == OP_SYNTH_ADJ && m > 0) ? 2.f : 1.f;
+                    float2 *spec = reinterpret_cast<float2 *>(a.out);
+                    if (ne < L) spec[(size_t)b * a.nlm + col + ne] = make_float2(sc * de[q], m == 0 ? 0.f : sc * de[q + 1]);
+                    if (no < L) spec[(size_t)b * a.nlm + col + no] = make_float2(sc * dd[q], m == 0 ? 0.f : sc * dd[q + 1]);
+                }
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+// ---------------------------------------------------------------------------
 // Static polar optimisation (Sec. 3.1): for each (m, tile), the first chunk
 // whose panel blocks hold a value >= thr.  One CTA per (m, tile).
 // ---------------------------------------------------------------------------
@@ -815,6 +1269,85 @@ cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int npairs, int nlm, c
     a.err = err;
     return synth ? launch_contraction(k_tc_vec<true>, true, lmax, mmax, npairs, 2, a, st)
                  : launch_contraction(k_tc_vec<false>, false, lmax, mmax, npairs, 2, a, st);
+}
+
+// ---------------------------------------------------------------------------
+// On-the-fly mode (host side)
+// ---------------------------------------------------------------------------
+size_t otf_segment_offsets(int lmax, int mmax, std::vector<unsigned long long> &segoff)
+{
+    segoff.assign(mmax + 1, 0);
+    unsigned long long s = 0;
+    for (int m = 0; m <= mmax; ++m) {
+        segoff[m] = s;
+        s += (unsigned long long)((lmax - m + 1 + kSeg - 1) / kSeg);
+    }
+    return (size_t)s;
+}
+
+cudaError_t launch_build_seeds(const PlanView<double> &pv, const unsigned long long *segoff, float4 *seeds,
+                               float thr, int *c0s, int *c0a, int *flag, cudaStream_t st)
+{
+    int ts, ta;
+    tc_tile_counts(pv.lmax, pv.npairs, ts, ta);
+    const int n = (pv.mmax + 1) * (ts + ta);
+    k_init_c0<<<(n + 255) / 256, 256, 0, st>>>(pv.lmax, pv.mmax, pv.npairs, ts, ta, c0s, c0a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 g((unsigned)((pv.npairs + 127) / 128), (unsigned)(pv.mmax + 1));
+    k_build_seeds<<<g, 128, 0, st>>>(pv, segoff, seeds, thr, c0s, c0a, ts, ta, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_otf(bool synth, int lmax, int mmax, int npairs, int nlm, const float4 *seeds,
+                          const unsigned long long *segoff, const int *c0, const float2 *ab32, const float *x32,
+                          unsigned char *data, const float *in, float *out, int batch, Op op, int *err,
+                          cudaStream_t st)
+{
+    if (batch < 1 || batch > tc_max_batch()) return cudaErrorInvalidValue;
+    const int rows = cols_of(batch);
+    // synthesis data chunks are numbered like the segments (one chunk = one segment)
+    cudaError_t e = launch_prep(synth, false, lmax, mmax, npairs, nlm, batch, rows, op, in, nullptr, segoff, data, st);
+    if (e != cudaSuccess) return e;
+    OtfArgs a{};
+    a.lmax = lmax;
+    a.mmax = mmax;
+    a.npairs = npairs;
+    a.nlm = nlm;
+    a.batch = batch;
+    a.rows = rows;
+    a.op = (int)op;
+    a.nab = synth ? kSeg * ((lmax + 1 + kSeg - 1) / kSeg) : 2 * kRows;
+    a.seeds = seeds;
+    a.segoff = segoff;
+    a.c0 = c0;
+    a.ab = ab32;
+    a.x = x32;
+    a.data = data;
+    a.out = out;
+    a.err = err;
+    // operand stages SA (4: generators fill two per round) and data stages SD
+    // (up to 8), within 110 KB so that two CTAs share an SM
+    int sa = 4, sd = 8;
+    while (sd > 3 && otf_smem_bytes(rows, sa, sd, a.nab) > 110 * 1024) --sd;
+    while (sa > 2 && otf_smem_bytes(rows, sa, sd, a.nab) > 110 * 1024) --sa;
+    a.stages = sa | (sd << 8);
+    const size_t smem = otf_smem_bytes(rows, sa, sd, a.nab);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    int ts, ta;
+    tc_tile_counts(lmax, npairs, ts, ta);
+    a.ntiles = synth ? ts : ta;
+    const unsigned blocks = (unsigned)((mmax + 1) * a.ntiles);
+    if (synth) {
+        e = cudaFuncSetAttribute(k_tc_otf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_tc_otf<true><<<blocks, kOtfThreads, smem, st>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(k_tc_otf<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_tc_otf<false><<<blocks, kOtfThreads, smem, st>>>(a);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace sht

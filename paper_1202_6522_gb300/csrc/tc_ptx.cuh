@@ -27,6 +27,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
+// Plain arrive (release semantics at CTA scope), no transaction count.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t done;
@@ -88,9 +94,10 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of
-// 8 rows x 16 bytes; `lbo` = byte distance between core matrices adjacent
-// along K, `sbo` = byte distance between 8-row groups along M/N.
+// Shared-memory matrix descriptor, no swizzle: core matrices of 8 x 16 bytes
+// (K-major: 8 M/N rows of 8 K values; MN-major: 8 K rows of 8 M/N values);
+// `lbo` = byte distance between core matrices adjacent along K, `sbo` = byte
+// distance between core matrices adjacent along M/N.
 __device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t lbo, uint32_t sbo)
 {
     const uint64_t addr = (uint64_t)((smem_u32(p) >> 4) & 0x3FFFu);
@@ -102,12 +109,14 @@ __device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t lbo, uint3
     return d;
 }
 
-// Instruction descriptor, kind::f16: BF16 A and B, FP32 accumulator, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
+// Instruction descriptor, kind::f16: BF16 A and B, FP32 accumulator; B
+// K-major; A K-major, or MN-major with a_mn (the "transpose A" bit 15).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N, bool a_mn = false)
 {
     return (1u << 4)                       // D format: F32
            | (1u << 7)                     // A format: BF16
            | (1u << 10)                    // B format: BF16
+           | ((a_mn ? 1u : 0u) << 15)      // A major-ness: 0 K-major, 1 MN-major
            | ((uint32_t)(N >> 3) << 17)    // N / 8
            | ((uint32_t)(M >> 4) << 24);   // M / 16
 }

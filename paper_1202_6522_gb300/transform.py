@@ -29,16 +29,18 @@ class SHT:
     def __init__(self, lmax: int, mmax: int | None = None, nlat: int | None = None,
                  nphi: int | None = None, device=None, fp32_path: str = "f32"):
         """fp32_path selects how complex64/float32 tensors are transformed:
-        "f32" (FP32 recurrence on the CUDA cores) or "tc" (tensor cores against
-        FP64-built P_n^m panels, split-bf16 products)."""
+        "f32" (FP32 recurrence on the CUDA cores), "tc" (tensor cores against
+        FP64-built P_n^m panels, split-bf16 products) or "otf" (the same
+        contraction with P_n^m generated on the fly, reseeded every 32 degrees
+        from FP64 values; scalar transforms, vector ones run "tc")."""
         self.lmax = int(lmax)
         self.mmax = self.lmax if mmax is None else int(mmax)
         self.nlat = self.lmax + 1 if nlat is None else int(nlat)
         self.nphi = max(_next_pow2(2 * self.mmax + 1), 2) if nphi is None else int(nphi)
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-        if fp32_path not in ("f32", "tc"):
-            raise ValueError("fp32_path must be 'f32' or 'tc'")
-        self.fp32_mode = C.SHT_TC_BF16X3 if fp32_path == "tc" else C.SHT_F32
+        if fp32_path not in ("f32", "tc", "otf"):
+            raise ValueError("fp32_path must be 'f32', 'tc' or 'otf'")
+        self.fp32_mode = {"f32": C.SHT_F32, "tc": C.SHT_TC_BF16X3, "otf": C.SHT_TC_OTF}[fp32_path]
         if self.device.type != "cuda":
             raise ValueError("SHT runs on CUDA devices only")
         with torch.cuda.device(self.device):

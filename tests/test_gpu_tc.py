@@ -52,10 +52,12 @@ def _np(t):
     return t.detach().cpu().numpy().astype(np.complex128 if t.is_complex() else np.float64)
 
 
+@pytest.mark.parametrize("path", ["tc", "otf"])
 @pytest.mark.parametrize("case", CASES, ids=IDS)
-def test_tc_synthesis_and_analysis(SHT, case):
+def test_tc_synthesis_and_analysis(SHT, case, path):
+    """Panels ("tc") and on-the-fly P ("otf") against the oracle."""
     lmax, mmax, nlat, nphi, batch = case
-    sht = SHT(lmax, mmax, nlat, nphi, fp32_path="tc")
+    sht = SHT(lmax, mmax, nlat, nphi, fp32_path=path)
     a = _spec(lmax, mmax, batch, 0)
     got = _np(sht.synth_(_dev(a)))
     assert normwise(got, oracle.synth(lmax, mmax, nlat, nphi, a)) < tc_bound(lmax)
@@ -65,19 +67,21 @@ def test_tc_synthesis_and_analysis(SHT, case):
     assert sht.sync_status() == 0
 
 
+@pytest.mark.parametrize("path", ["tc", "otf"])
 @pytest.mark.parametrize("case", CASES[:4], ids=IDS[:4])
-def test_tc_adjoints(SHT, case):
+def test_tc_adjoints(SHT, case, path):
     lmax, mmax, nlat, nphi, batch = case
-    sht = SHT(lmax, mmax, nlat, nphi, fp32_path="tc")
+    sht = SHT(lmax, mmax, nlat, nphi, fp32_path=path)
     g = _grid(nlat, nphi, batch, 2)
     a = _spec(lmax, mmax, batch, 3)
     assert normwise(_np(sht.synth_adj_(_dev(g))), oracle.synth_adj(lmax, mmax, nlat, nphi, g)) < tc_bound(lmax)
     assert normwise(_np(sht.analys_adj_(_dev(a))), oracle.analys_adj(lmax, mmax, nlat, nphi, a)) < tc_bound(lmax)
 
 
-def test_tc_full_size_n1023_b16_sampled(SHT):
+@pytest.mark.parametrize("path", ["tc", "otf"])
+def test_tc_full_size_n1023_b16_sampled(SHT, path):
     lmax, nlat, nphi, batch = 1023, 1024, 2048, 16
-    sht = SHT(lmax, lmax, nlat, nphi, fp32_path="tc")
+    sht = SHT(lmax, lmax, nlat, nphi, fp32_path=path)
     a = _spec(lmax, lmax, batch, 0)
     grid = _np(sht.synth_(_dev(a)))
     rows = [0, 1, 127, 128, 511, 512, 900, 1023]
@@ -94,18 +98,20 @@ def test_tc_full_size_n1023_b16_sampled(SHT):
     assert sht.sync_status() == 0
 
 
-def test_tc_round_trip_error_n1023(SHT):
+@pytest.mark.parametrize("path", ["tc", "otf"])
+def test_tc_round_trip_error_n1023(SHT, path):
     """Sec. 3.5 error measures for the tensor-core round trip (stated, bounded)."""
     lmax = 1023
-    sht = SHT(lmax, lmax, 1024, 2048, fp32_path="tc")
+    sht = SHT(lmax, lmax, 1024, 2048, fp32_path=path)
     Q = synthetic.spectrum(lmax, seed=0, uniform=True).astype(np.complex64)
     R = _np(sht.analys_(sht.synth_(torch.from_numpy(Q).to(DEV))))
     emax, erms = oracle.eps_max_rms(R, Q.astype(np.complex128), lmax)
     assert emax < 4 * tc_bound(lmax) and erms < tc_bound(lmax)
 
 
-def test_tc_deterministic(SHT):
-    sht = SHT(255, 255, 256, 512, fp32_path="tc")
+@pytest.mark.parametrize("path", ["tc", "otf"])
+def test_tc_deterministic(SHT, path):
+    sht = SHT(255, 255, 256, 512, fp32_path=path)
     a = _dev(_spec(255, 255, 4, 5))
     g1 = sht.synth_(a)
     g2 = sht.synth_(a)
@@ -226,3 +232,31 @@ def test_alu_peaks_measured(SHT):
     from paper_1202_6522_gb300 import _capi as C
     f32, f64 = C.sht_alu_peaks(torch.cuda.current_stream().cuda_stream)
     assert 10.0 < f32 < 200.0 and 0.05 < f64 < 100.0, (f32, f64)
+
+
+def test_otf_polar_threshold_and_skip(SHT):
+    """The on-the-fly mode keeps its own polar-skip tables (first live chunk per
+    tile, from the FP64 seeds); a threshold change rebuilds them."""
+    from paper_1202_6522_gb300 import _capi as C
+    lmax, nlat, nphi = 511, 512, 1024
+    sht = SHT(lmax, lmax, nlat, nphi, fp32_path="otf")
+    a = _spec(lmax, lmax, 2, 9)
+    ref = oracle.synth(lmax, lmax, nlat, nphi, a)
+    assert normwise(_np(sht.synth_(_dev(a))), ref) < tc_bound(lmax)
+    fs, fa = C.sht_tc_polar_skip(sht._h)
+    assert 0.0 < fs < 0.5 and 0.0 < fa < 0.5, (fs, fa)
+    C.sht_set_polar_threshold(sht._h, 0.0)
+    assert C.sht_tc_polar_skip(sht._h) == (0.0, 0.0)
+    assert normwise(_np(sht.synth_(_dev(a))), ref) < tc_bound(lmax)
+    g = _grid(nlat, nphi, 2, 10)
+    assert normwise(_np(sht.analys_(_dev(g))), oracle.analys(lmax, lmax, nlat, nphi, g)) < tc_bound(lmax)
+
+
+def test_otf_vector_runs_panels(SHT):
+    """Vector transforms in the on-the-fly mode run on the panels."""
+    lmax, nlat, nphi = 31, 40, 64
+    sht = SHT(lmax, 20, nlat, nphi, fp32_path="otf")
+    S = synthetic.spectrum(lmax, 20, batch=2, seed=4, power=1.5).astype(np.complex64).astype(np.complex128)
+    vt, vp = sht.synth_vec_(_dev(S), _dev(S))
+    rt, rp = oracle.synth_vec(lmax, 20, nlat, nphi, S, S)
+    assert normwise(_np(vt), rt) < tc_bound(lmax) and normwise(_np(vp), rp) < tc_bound(lmax)

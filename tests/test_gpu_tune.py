@@ -29,8 +29,8 @@ def test_tuned_shapes_keep_results(lib, prec):
     lmax, nlat, nphi, batch = 95, 96, 256, 5
     sht = P.SHT(lmax, lmax, nlat, nphi)
     mode = C.SHT_F64 if prec == "f64" else C.SHT_F32
-    syn_ms, ana_ms = C.sht_tune(sht._h, batch, mode, torch.cuda.current_stream().cuda_stream)
-    assert syn_ms > 0 and ana_ms > 0
+    syn_ms, ana_ms, none = C.sht_tune(sht._h, batch, mode, torch.cuda.current_stream().cuda_stream)
+    assert syn_ms > 0 and ana_ms > 0 and none == -1.0
     cdt = torch.complex128 if prec == "f64" else torch.complex64
     a = synthetic.spectrum(lmax, batch=batch, seed=3)
     if prec == "f32":
@@ -48,8 +48,8 @@ def test_auto_mode_chooses_a_path(lib):
     P, C = lib
     lmax, nlat, nphi, batch = 127, 128, 256, 8
     sht = P.SHT(lmax, lmax, nlat, nphi)
-    f32_ms, tc_ms = C.sht_tune(sht._h, batch, C.SHT_F32_AUTO, torch.cuda.current_stream().cuda_stream)
-    assert f32_ms > 0 and tc_ms > 0
+    f32_ms, tc_ms, otf_ms = C.sht_tune(sht._h, batch, C.SHT_F32_AUTO, torch.cuda.current_stream().cuda_stream)
+    assert f32_ms > 0 and tc_ms > 0 and otf_ms > 0
     sht.fp32_mode = C.SHT_F32_AUTO
     a = synthetic.spectrum(lmax, batch=batch, seed=4).astype(np.complex64)
     g = sht.synth_(torch.from_numpy(a).to(DEV))
