@@ -362,6 +362,39 @@ def n511_config(torch, dev, steps=20):
     return out
 
 
+def polar_sweep(torch, dev, thresholds=(0.0, 2.0 ** -40, 2.0 ** -32, 2.0 ** -26, 2.0 ** -20), steps=20):
+    """The static polar optimisation of Sec. 3.1 (threshold left open by the
+    paper): tensor-core round-trip time, fraction of panel chunks skipped and
+    round-trip error (Sec. 3.5 measures, uniform spectra) per threshold, at
+    the bench size."""
+    import numpy as np
+    from paper_1202_6522_gb300 import SHT, synthetic, _capi as C
+    sht = SHT(LMAX, LMAX, NLAT, NPHI, device=dev, fp32_path="tc")
+    a = torch.from_numpy(synthetic.spectrum(LMAX, batch=BATCH, seed=0).astype(np.complex64)).to(dev)
+    Q = synthetic.spectrum(LMAX, seed=0, uniform=True).astype(np.complex64)
+    Qd = torch.from_numpy(Q).to(dev)
+    out = []
+    for thr in thresholds:
+        C.sht_set_polar_threshold(sht._h, thr)
+        for _ in range(3):
+            sht.analys_(sht.synth_(a))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            sht.analys_(sht.synth_(a))
+        e1.record()
+        e1.synchronize()
+        R = sht.analys_(sht.synth_(Qd)).cpu().numpy().astype(np.complex128)
+        d = np.abs(R - Q.astype(np.complex128))
+        fs, fa = C.sht_tc_polar_skip(sht._h)
+        out.append({"threshold": thr, "ms_per_step": e0.elapsed_time(e1) / steps,
+                    "skip_synth": fs, "skip_analys": fa, "eps_max": float(d.max()),
+                    "eps_rms": float(np.sqrt(2.0 / ((LMAX + 1) * (LMAX + 2)) * np.sum(d * d)))})
+    return out
+
+
 def time_path(sht, torch, a, steps, warmup, stream, profile=False):
     """Device-timed round trips on inputs resident in HBM.  Returns (ms per step, kernel table)."""
     from paper_1202_6522_gb300 import _capi as C
@@ -521,6 +554,7 @@ def run_ours(args):
         extra["vector"] = vector_config(torch, dev)
         extra["differentiable"] = differentiable_config(sht, torch, dev, cdt)
         extra["n511"] = n511_config(torch, dev)
+        extra["polar_threshold_sweep"] = polar_sweep(torch, dev)
         extra["accuracy_vs_n"] = accuracy_vs_n(torch, dev)
 
     # --- the plain FP64 path on the same workload (the metric's denominator) ---

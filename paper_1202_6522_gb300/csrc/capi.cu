@@ -565,7 +565,7 @@ int run_analys_tc(sht::Plan &p, const void *grid, void *spec, int batch, sht::Op
 // On-the-fly mode: synthesis = contraction then FFT; analysis = FFT then contraction.
 int run_otf(sht::Plan &p, bool synth, const void *in_, void *out_, int batch, sht::Op op, cudaStream_t s)
 {
-    const int chunk = tc_chunk(false);
+    const int chunk = sht::tc_otf_max_batch();
     float *inter = static_cast<float *>(p.work);
     unsigned char *data = static_cast<unsigned char *>(p.work) + tc_data_offset(p, batch, false);
     const sht::PlanView<float> pv = p.view32();

@@ -202,6 +202,7 @@ cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int npairs, int nlm, c
                           cudaStream_t st);
 cudaError_t launch_min_int(const int *a, const int *b, int *out, int n, cudaStream_t st);
 int tc_vec_max_batch();
+int tc_otf_max_batch();
 // Rows of the data operand for `batch` fields: 32 ceil(2 batch / 32), twice that for vectors.
 inline int tc_rows(int batch, bool vec) { return (vec ? 2 : 1) * (((2 * batch + 31) / 32) * 32); }
 // Static polar optimisation: per (m, tile) first chunk with a panel value >= thr.

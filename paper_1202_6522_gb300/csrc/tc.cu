@@ -19,10 +19,11 @@
 // and each product is hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor
 // memory.
 //
-// CTA: 128 threads, one (order m, 128-row tile).  Thread 0 streams panel and
-// data chunks with cp.async.bulk into a ring of stages and issues the MMAs;
-// the four warps run the epilogue (tcgen05.ld of the accumulators).  Every
-// wait is bounded; on a timeout the kernel records an error code and returns.
+// CTA: one (order m, 128-row tile).  A producer warp streams panel and data
+// chunks with cp.async.bulk into a ring of stages, one thread issues the MMAs,
+// four warps convert the analysis operand and run the epilogue (tcgen05.ld of
+// the accumulators).  Every wait is bounded; on a timeout the kernel records
+// an error code and returns.
 // Leading panel chunks whose values are all below 2^-40 (high order, near
 // the poles) are skipped: the static polar optimisation of Sec. 3.1.
 #include <cuda_bf16.h>
@@ -55,6 +56,25 @@ __device__ __forceinline__ void raise_err(int *err, int code)
 {
     if (err) atomicCAS(err, 0, code);
 }
+
+// Bounded wait that also gives up when another thread of the CTA gave up.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort)
+{
+    const uint64_t t0 = tc::globaltimer();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        if (tc::mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 255u) {
+            if (*abort) return false;
+            if (tc::globaltimer() - t0 > kWaitNs) {
+                *abort = 1;
+                return false;
+            }
+        }
+    }
+    *abort = 1;
+    return false;
+}
+
 
 // ---------------------------------------------------------------------------
 // Panel builder: one thread per (m, pair), FP64 recurrence with rescaling.
@@ -247,6 +267,7 @@ __host__ __device__ inline size_t smem_bytes_of(int npanels, int rows, int stage
 
 struct TcArgs {
     int lmax, mmax, npairs, nlm, batch, rows, ntiles, stages, op;
+    const float *in;                       // raw FP32 s/d folds (warp-specialised analysis)
     const unsigned char *panel, *dpanel;   // dpanel: vector transforms only
     const unsigned long long *off;         // per-order panel byte offsets
     const int *c0;                         // per (m, tile): first chunk above the polar threshold
@@ -334,21 +355,39 @@ __device__ __forceinline__ uint32_t setup_ctas(int S, uint64_t *bar_load, uint64
 }
 
 // ---------------------------------------------------------------------------
-// Scalar contraction.  Accumulators: [parity][rows columns].
+// Warp-specialised panel contraction (the one the scalar transforms use).
+// Warps 0-3 convert (analysis: the raw FP32 s/d folds of the chunk, brought in
+// by bulk copy, into the blocked bf16 hi/lo operand) and run the epilogue;
+// warp 4 lane 0 issues the MMAs; warp 5 streams the panel chunks and the data
+// (synthesis: the prepped blocked chunk; analysis: one raw row per field).
+// Stage: [panel chunk | blocked data | raw folds (analysis)].
 // ---------------------------------------------------------------------------
+constexpr int kWsThreads = 192;
+__host__ __device__ inline size_t ws_raw_bytes(int batch) { return (size_t)batch * kKc * sizeof(float4); }
+__host__ __device__ inline size_t ws_stage_bytes(int rows, int batch, bool synth)
+{
+    return kChunkPanel + data_chunk_bytes(rows) + (synth ? 0 : ws_raw_bytes(batch));
+}
+__host__ __device__ inline size_t ws_smem_bytes(int rows, int batch, int stages, bool synth)
+{
+    return 1024 + (size_t)stages * ws_stage_bytes(rows, batch, synth) + 8 * (3 * stages + 2);
+}
+
 template <bool SYNTH>
-__global__ void __launch_bounds__(128, 2) k_tc_legendre(TcArgs a)
+__global__ void __launch_bounds__(kWsThreads, 2) k_tc_ws(TcArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int S = a.stages, NC = a.rows;
-    const size_t stage_bytes = stage_bytes_of(1, NC);
+    const size_t dbytes = data_chunk_bytes(NC);
+    const size_t stage = ws_stage_bytes(NC, a.batch, SYNTH);
     const size_t blk = (size_t)NC * kKc * 2;
-    uint64_t *bar_load = reinterpret_cast<uint64_t *>(smem + (size_t)S * stage_bytes);
-    uint64_t *bar_mma = bar_load + S;
+    uint64_t *bar_load = reinterpret_cast<uint64_t *>(smem + (size_t)S * stage);
+    uint64_t *bar_conv = bar_load + S;
+    uint64_t *bar_mma = bar_conv + S;
     uint64_t *bar_done = bar_mma + S;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_done + 1);
-    __shared__ int s_ok;
+    __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     const int m = blockIdx.x / a.ntiles;
@@ -357,40 +396,141 @@ __global__ void __launch_bounds__(128, 2) k_tc_legendre(TcArgs a)
     const int L = lmax - m + 1;
     const int Le = (L + 1) / 2;
     const long col = col_of(lmax, m);
-    // analysis tiles run over degrees of this order: tiles past them have no panel
     if (!SYNTH && tile * kRows >= Le) return;
     const int nchunks = SYNTH ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
     const unsigned char *panel = a.panel + a.off[m] + (size_t)tile * nchunks * kChunkPanel;
-    const unsigned char *data =
-        a.data + (SYNTH ? a.dchunk[m] : (unsigned long long)m * nchunks) * data_chunk_bytes(NC);
-    const uint32_t ncols = NC * 2 <= 64 ? 64 : (NC * 2 <= 128 ? 128 : 256);
     const int cstart = a.c0 ? a.c0[m * a.ntiles + tile] : 0;
     const int nlive = nchunks - cstart;
-
-    const uint32_t tmem = setup_ctas(S, bar_load, bar_mma, bar_done, tslot, ncols, &s_ok);
+    const uint32_t ncols = NC * 2 <= 64 ? 64 : (NC * 2 <= 128 ? 128 : 256);
 
     if (tid == 0) {
-        const uint32_t idesc = tc::idesc_bf16_f32(kRows, NC);
-        const bool ok = produce<1>(a, smem, stage_bytes, bar_load, bar_mma, bar_done, panel, nullptr, data, cstart,
-                                   nlive, [&](unsigned char *st, unsigned char *dat, bool first) {
-#pragma unroll
-            for (int par = 0; par < 2; ++par) {
-                const unsigned char *ah = st + (size_t)(par * 2) * kBlk, *al = ah + kBlk;
-                const unsigned char *bh = dat + (size_t)(par * 2) * blk, *bl = bh + blk;
-                const uint32_t d = tmem + (uint32_t)(par * NC);
-                const uint64_t dah = tc::smem_desc(ah, kLbo, kSbo), dal = tc::smem_desc(al, kLbo, kSbo);
-                const uint64_t dbh = tc::smem_desc(bh, kLbo, kSbo), dbl = tc::smem_desc(bl, kLbo, kSbo);
-                tc::mma_bf16(d, dah, dbh, idesc, !first);
-                tc::mma_bf16(d, dah, dbl, idesc, true);
-                tc::mma_bf16(d, dal, dbh, idesc, true);
-            }
-        });
-        if (!ok) s_ok = 0;
+        for (int q = 0; q < S; ++q) {
+            tc::mbar_init(&bar_load[q], 1);
+            tc::mbar_init(&bar_conv[q], 4);
+            tc::mbar_init(&bar_mma[q], 1);
+        }
+        tc::mbar_init(bar_done, 1);
+        tc::mbar_fence_init();
+        s_abort = 0;
     }
-    bool ok = tc::mbar_wait_bounded(bar_done, 0, 2 * kWaitNs);
-    if (!ok) raise_err(a.err, SHT_ETIMEOUT);
-    ok = __syncthreads_and(ok && s_ok);
-    if (ok) {
+    if (warp == 0) tc::tmem_alloc(tslot, ncols);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp < 4) {
+        // ---------------- converters (analysis) ----------------
+        if (!SYNTH) {
+            for (int u = 0; u < nlive; ++u) {
+                const int q = u % S;
+                const int c = cstart + u;
+                if (!wait_or_abort(&bar_load[q], (uint32_t)((u / S) & 1), &s_abort)) break;
+                unsigned char *st = smem + (size_t)q * stage;
+                unsigned char *dat = st + kChunkPanel;
+                const float4 *raw = reinterpret_cast<const float4 *>(dat + dbytes);
+                const int np = min(kKc, npairs - kKc * c);
+                for (int i = tid; i < a.batch * kKc; i += 128) {
+                    const int b = i / kKc, j = i - b * kKc;
+                    const float4 v = j < np ? raw[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float va[4] = {v.x, v.y, v.z, v.w};   // s.re s.im d.re d.im
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        __nv_bfloat16 h, l;
+                        split_bf16(va[t], h, l);
+                        const uint32_t o = blk_off(2 * b + (t & 1), j);
+                        unsigned char *bh = dat + (size_t)((t >> 1) * 2) * blk;
+                        *reinterpret_cast<__nv_bfloat16 *>(bh + o) = h;
+                        *reinterpret_cast<__nv_bfloat16 *>(bh + blk + o) = l;
+                    }
+                }
+                tc::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&bar_conv[q]);
+            }
+        }
+    } else if (warp == 4) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            const uint32_t idesc = tc::idesc_bf16_f32(kRows, NC);
+            uint64_t da0[2][2], db0[2][2];
+#pragma unroll
+            for (int par = 0; par < 2; ++par)
+#pragma unroll
+                for (int hl = 0; hl < 2; ++hl) {
+                    da0[par][hl] = tc::smem_desc(smem + (size_t)(par * 2 + hl) * kBlk, kLbo, kSbo);
+                    db0[par][hl] = tc::smem_desc(smem + kChunkPanel + (size_t)(par * 2 + hl) * blk, kLbo, kSbo);
+                }
+            const uint64_t sstep = stage >> 4;
+            bool ok = true;
+            for (int u = 0; u < nlive; ++u) {
+                const int q = u % S;
+                if (!wait_or_abort(&bar_load[q], (uint32_t)((u / S) & 1), &s_abort)) { ok = false; break; }
+                if (!SYNTH && !wait_or_abort(&bar_conv[q], (uint32_t)((u / S) & 1), &s_abort)) { ok = false; break; }
+                tc::tc_fence_after();
+                const uint64_t so = sstep * (uint64_t)q;
+#pragma unroll
+                for (int par = 0; par < 2; ++par) {
+                    const uint32_t d = tmem + (uint32_t)(par * NC);
+                    tc::mma_bf16(d, da0[par][0] + so, db0[par][0] + so, idesc, u != 0);
+                    tc::mma_bf16(d, da0[par][0] + so, db0[par][1] + so, idesc, true);
+                    tc::mma_bf16(d, da0[par][1] + so, db0[par][0] + so, idesc, true);
+                }
+                tc::mma_commit(&bar_mma[q]);
+            }
+            if (!ok) raise_err(a.err, SHT_ETIMEOUT);
+            tc::mma_commit(bar_done);
+        }
+    } else {
+        // ---------------- producer ----------------
+        const unsigned char *data = a.data + (SYNTH ? a.dchunk[m] * dbytes : 0);
+        int issued = 0;
+        bool ok = true;
+        for (int u = 0; u < nlive; ++u) {
+            const int q = u % S;
+            const int c = cstart + u;
+            if (lane == 0 && u >= S)
+                ok = wait_or_abort(&bar_mma[q], (uint32_t)((u / S - 1) & 1), &s_abort);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) break;
+            unsigned char *st = smem + (size_t)q * stage;
+            const int np = min(kKc, npairs - kKc * c);
+            if (lane == 0) {
+                const uint32_t tx = (uint32_t)kChunkPanel +
+                                    (SYNTH ? (uint32_t)dbytes : (uint32_t)(a.batch * np) * (uint32_t)sizeof(float4));
+                tc::mbar_arrive_expect_tx(&bar_load[q], tx);
+                tc::bulk_g2s(st, panel + (size_t)c * kChunkPanel, kChunkPanel, &bar_load[q]);
+                if (SYNTH) tc::bulk_g2s(st + kChunkPanel, data + (size_t)c * dbytes, (uint32_t)dbytes, &bar_load[q]);
+            }
+            __syncwarp();   // the transaction count is set before the other lanes' copies
+            if (!SYNTH) {
+                for (int b = lane; b < a.batch; b += 32) {
+                    // raw folds of field b: pairs [kKc c, kKc c + np) of order m
+                    const float4 *src = reinterpret_cast<const float4 *>(a.in) +
+                                        ((size_t)b * (a.mmax + 1) + m) * npairs + (size_t)kKc * c;
+                    tc::bulk_g2s(st + kChunkPanel + dbytes + (size_t)b * kKc * sizeof(float4), src,
+                                 (uint32_t)np * (uint32_t)sizeof(float4), &bar_load[q]);
+                }
+            }
+            __syncwarp();
+            issued = u + 1;
+        }
+        if (!ok && lane == 0) {
+            raise_err(a.err, SHT_ETIMEOUT);
+            for (int v = max(0, issued - S); v < issued; ++v)
+                (void)tc::mbar_wait_bounded(&bar_load[v % S], (uint32_t)((v / S) & 1), 100000000ull);
+        }
+    }
+    bool ok = true;
+    if (warp < 4) {
+        ok = wait_or_abort(bar_done, 0, &s_abort);
+        if (!ok) {
+            (void)tc::mbar_wait_bounded(bar_done, 0, 100000000ull);
+            raise_err(a.err, SHT_ETIMEOUT);
+        }
+    }
+    ok = __syncthreads_and(ok && !*(volatile int *)&s_abort);
+    if (ok && warp < 4) {
         tc::tc_fence_after();
         const int row = tile * kRows + warp * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
@@ -399,7 +539,7 @@ __global__ void __launch_bounds__(128, 2) k_tc_legendre(TcArgs a)
             if (nlive > 0) {
                 tc::tmem_ld32(lane_base + (uint32_t)cb, de);
                 tc::tmem_ld32(lane_base + (uint32_t)(NC + cb), dd);
-            } else {  // every chunk below the polar threshold: the sums are zero
+            } else {
 #pragma unroll
                 for (int i = 0; i < 32; ++i) de[i] = dd[i] = 0.f;
             }
@@ -412,7 +552,7 @@ __global__ void __launch_bounds__(128, 2) k_tc_legendre(TcArgs a)
                         eo[((size_t)b * (a.mmax + 1) + m) * npairs + row] = make_float4(de[q], de[q + 1], dd[q], dd[q + 1]);
                     }
                 } else {
-                    const int ne = 2 * row, no = 2 * row + 1;   // n - m of the two rows
+                    const int ne = 2 * row, no = 2 * row + 1;
                     const float sc = (a.op == OP_SYNTH_ADJ && m > 0) ? 2.f : 1.f;
                     float2 *spec = reinterpret_cast<float2 *>(a.out0);
                     if (ne < L) spec[(size_t)b * a.nlm + col + ne] = make_float2(sc * de[q], m == 0 ? 0.f : sc * de[q + 1]);
@@ -681,34 +821,27 @@ struct OtfArgs {
 // (a, b) table, 2 SA + 2 SD + 1 mbarriers and the TMEM slot.
 constexpr size_t kOtfSeedBytes = kRows * sizeof(float4);
 __host__ __device__ inline size_t otf_dstage_bytes(int rows) { return data_chunk_bytes(rows) + kOtfSeedBytes; }
-__host__ __device__ inline size_t otf_smem_bytes(int rows, int sa, int sd, int nab)
+// Synthesis keeps its operand stages in tensor memory (A from TMEM), analysis
+// in shared memory.
+__host__ __device__ inline size_t otf_smem_bytes(int rows, int sa, int sd, int nab, bool synth)
 {
-    return 1024 + (size_t)sa * kChunkPanel + (size_t)sd * otf_dstage_bytes(rows) + (size_t)nab * sizeof(float2) +
-           8 * (2 * sa + 2 * sd + 2);
+    return 1024 + (synth ? 0 : (size_t)sa * kChunkPanel) + (size_t)sd * otf_dstage_bytes(rows) +
+           (size_t)nab * sizeof(float2) + 8 * (2 * sa + 2 * sd + 2);
+}
+
+// TMEM columns: accumulators [0, 4 rows) (per parity: hi (x) [data hi | data
+// lo] in 2 rows columns), then (synthesis) SA operand stages of 4 blocks x
+// kKc / 2 columns (M = 128 rows in the lanes, two bf16 per column).
+__host__ __device__ inline uint32_t otf_tmem_cols(int rows, int sa, bool synth)
+{
+    const int need = 4 * rows + (synth ? sa * 4 * (kKc / 2) : 0);
+    return need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
 }
 
 // Threads of the on-the-fly kernel: two groups of 4 generator warps (group g
 // generates the chunks u with u % 2 == g) and one producer / MMA warp.
 constexpr int kOtfGroups = 2;
 constexpr int kOtfThreads = 32 * (4 * kOtfGroups + 2);   // + MMA warp + producer warp
-
-// Bounded wait that also gives up when another thread of the CTA gave up.
-__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort)
-{
-    const uint64_t t0 = tc::globaltimer();
-    for (uint32_t it = 0; it < (1u << 26); ++it) {
-        if (tc::mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 255u) {
-            if (*abort) return false;
-            if (tc::globaltimer() - t0 > kWaitNs) {
-                *abort = 1;
-                return false;
-            }
-        }
-    }
-    *abort = 1;
-    return false;
-}
 
 // v0, v1 -> bf16x2 hi and lo words with v = hi + lo per element.
 __device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_t &lo)
@@ -775,7 +908,9 @@ __device__ __forceinline__ void otf_store(unsigned char *st, int tid, const uint
 // The contraction with on-the-fly P.  Warps 0-7 generate the operand (two
 // groups of four, alternate chunks; group 0 also runs the epilogue); warp 8
 // lane 0 issues the MMAs; warp 9 lane 0 streams the data chunks and their
-// seeds, up to SD chunks ahead of the MMAs.  Synthesis: CTA
+// seeds, up to SD chunks ahead of the MMAs.  Synthesis writes its operand
+// into tensor memory (tcgen05.st; the MMA reads A from TMEM), analysis into
+// shared memory.  Synthesis: CTA
 // (m, 128-pair tile), chunk = 32 degrees, generator thread = pair row, operand
 // K-major.  Analysis: CTA (m, 128-row degree tile per parity), chunk = 16
 // pairs, generator thread = (degree segment of the tile, pair), operand
@@ -792,8 +927,8 @@ __global__ void __launch_bounds__(kOtfThreads, 2) k_tc_otf(OtfArgs a)
     const size_t dbytes = data_chunk_bytes(NC);
     const size_t dstage = otf_dstage_bytes(NC);
     const size_t blk = (size_t)NC * kKc * 2;
-    unsigned char *opnd = smem;                                  // SA x kChunkPanel
-    unsigned char *dst = opnd + (size_t)SA * kChunkPanel;        // SD x (data | seeds)
+    unsigned char *opnd = smem;                                  // analysis: SA x kChunkPanel
+    unsigned char *dst = opnd + (SYNTH ? 0 : (size_t)SA * kChunkPanel);   // SD x (data | seeds)
     float2 *ab_s = reinterpret_cast<float2 *>(dst + (size_t)SD * dstage);
     uint64_t *bar_load = reinterpret_cast<uint64_t *>(ab_s + a.nab);
     uint64_t *bar_dfree = bar_load + SD;
@@ -816,7 +951,7 @@ __global__ void __launch_bounds__(kOtfThreads, 2) k_tc_otf(OtfArgs a)
     const int nchunks = SYNTH ? nseg : kch;
     const int cstart = a.c0[m * a.ntiles + tile];
     const int nlive = nchunks - cstart;
-    const uint32_t ncols = NC * 2 <= 64 ? 64 : (NC * 2 <= 128 ? 128 : 256);
+    const uint32_t ncols = otf_tmem_cols(NC, SA, SYNTH);
     // degrees held in the (a, b) table: the whole order (synthesis) or the tile (analysis)
     const int nn_base = SYNTH ? 0 : 2 * kRows * tile;
 
@@ -908,8 +1043,20 @@ __global__ void __launch_bounds__(kOtfThreads, 2) k_tc_otf(OtfArgs a)
             if (pp >= npairs || ss >= nseg) sd = make_float4(0.f, 0.f, 0.f, 0.f);
             uint32_t hw[2][kKc / 2], lw[2][kKc / 2];
             otf_segment(ab_s + (SYNTH ? kSeg * c : kSeg * (r / kKc)), sd, hw, lw);
-            otf_store<SYNTH>(opnd + (size_t)qa * kChunkPanel, r, hw, lw);
-            tc::fence_proxy_async_smem();
+            if (SYNTH) {
+                // row r of the operand = TMEM lane r: block (par, hi|lo) of stage qa
+                tc::tc_fence_after();   // after the wait on the MMAs that read this stage
+                const uint32_t ta = tmem + ((uint32_t)(32 * (warp % 4)) << 16) + (uint32_t)(4 * NC + 32 * qa);
+                tc::tmem_st8(ta, hw[0]);
+                tc::tmem_st8(ta + 8, lw[0]);
+                tc::tmem_st8(ta + 16, hw[1]);
+                tc::tmem_st8(ta + 24, lw[1]);
+                tc::tmem_wait_st();
+                tc::tc_fence_before();
+            } else {
+                otf_store<SYNTH>(opnd + (size_t)qa * kChunkPanel, r, hw, lw);
+                tc::fence_proxy_async_smem();
+            }
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&bar_gen[qa]);
         }
@@ -917,7 +1064,11 @@ __global__ void __launch_bounds__(kOtfThreads, 2) k_tc_otf(OtfArgs a)
         // ---------------- MMA issuer ----------------
         // descriptors of stage 0; a stage adds its byte offset / 16 to the
         // start-address field (stage offsets stay far below the 256 KB field)
-        const uint32_t idesc = tc::idesc_bf16_f32(kRows, NC, !SYNTH);
+        // per parity two MMAs: P_hi x [data_hi ; data_lo] (N = 2 NC: the hi and lo
+        // blocks are adjacent, one 2 NC-row operand) and P_lo x data_hi (N = NC),
+        // both into the parity's accumulator; the epilogue adds its two halves
+        const uint32_t idesc2 = tc::idesc_bf16_f32(kRows, 2 * NC, !SYNTH);
+        const uint32_t idesc1 = tc::idesc_bf16_f32(kRows, NC, !SYNTH);
         uint64_t da0[2][2], db0[2][2];
 #pragma unroll
         for (int par = 0; par < 2; ++par)
@@ -937,10 +1088,15 @@ __global__ void __launch_bounds__(kOtfThreads, 2) k_tc_otf(OtfArgs a)
             const uint64_t ao = astep * (uint64_t)qa, bo = dstep * (uint64_t)qd;
 #pragma unroll
             for (int par = 0; par < 2; ++par) {
-                const uint32_t d = tmem + (uint32_t)(par * NC);
-                tc::mma_bf16(d, da0[par][0] + ao, db0[par][0] + bo, idesc, u != 0);
-                tc::mma_bf16(d, da0[par][0] + ao, db0[par][1] + bo, idesc, true);
-                tc::mma_bf16(d, da0[par][1] + ao, db0[par][0] + bo, idesc, true);
+                const uint32_t d = tmem + (uint32_t)(par * 2 * NC);
+                if (SYNTH) {
+                    const uint32_t ah = tmem + (uint32_t)(4 * NC + 32 * qa + 16 * par), al = ah + 8;
+                    tc::mma_bf16_ts(d, ah, db0[par][0] + bo, idesc2, u != 0);
+                    tc::mma_bf16_ts(d, al, db0[par][0] + bo, idesc1, true);
+                } else {
+                    tc::mma_bf16(d, da0[par][0] + ao, db0[par][0] + bo, idesc2, u != 0);
+                    tc::mma_bf16(d, da0[par][1] + ao, db0[par][0] + bo, idesc1, true);
+                }
             }
             tc::mma_commit(&bar_mma[qa]);
             tc::mma_commit(&bar_dfree[qd]);
@@ -984,8 +1140,16 @@ __global__ void __launch_bounds__(kOtfThreads, 2) k_tc_otf(OtfArgs a)
         for (int cb = 0; cb < NC; cb += 32) {
             float de[32], dd[32];
             if (nlive > 0) {
+                float t[32];
+                // parity accumulators: columns [par 2 NC, par 2 NC + 2 NC); sum of the two halves
                 tc::tmem_ld32(lane_base + (uint32_t)cb, de);
-                tc::tmem_ld32(lane_base + (uint32_t)(NC + cb), dd);
+                tc::tmem_ld32(lane_base + (uint32_t)(NC + cb), t);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) de[i] += t[i];
+                tc::tmem_ld32(lane_base + (uint32_t)(2 * NC + cb), dd);
+                tc::tmem_ld32(lane_base + (uint32_t)(3 * NC + cb), t);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) dd[i] += t[i];
             } else {
 #pragma unroll
                 for (int i = 0; i < 32; ++i) de[i] = dd[i] = 0.f;
@@ -1109,6 +1273,9 @@ cudaError_t launch_prep(bool synth, bool vec, int lmax, int mmax, int npairs, in
 // Host side
 // ---------------------------------------------------------------------------
 int tc_max_batch() { return 64; }
+// the on-the-fly kernel keeps 4 x 2 batch accumulator columns (+ the synthesis
+// operand) in tensor memory: at most 32 fields per launch
+int tc_otf_max_batch() { return 32; }
 int tc_vec_max_batch() { return 32; }
 
 void tc_panel_layout(int lmax, int mmax, int npairs, std::vector<unsigned long long> &off_s,
@@ -1212,7 +1379,9 @@ cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int n
 {
     if (batch < 1 || batch > tc_max_batch()) return cudaErrorInvalidValue;
     const int rows = cols_of(batch);
-    if (!prepped) {
+    // synthesis: prep the spectra into the blocked layout; analysis: the
+    // contraction converts the raw folds itself
+    if (synth && !prepped) {
         cudaError_t e =
             launch_prep(synth, false, lmax, mmax, npairs, nlm, batch, rows, op, in, nullptr, dchunk, data, st);
         if (e != cudaSuccess) return e;
@@ -1232,8 +1401,26 @@ cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int n
     a.dchunk = dchunk;
     a.out0 = out;
     a.err = err;
-    return synth ? launch_contraction(k_tc_legendre<true>, true, lmax, mmax, npairs, 1, a, st)
-                 : launch_contraction(k_tc_legendre<false>, false, lmax, mmax, npairs, 1, a, st);
+    a.in = in;
+    int stages = 4;
+    while (stages > 2 && ws_smem_bytes(rows, batch, stages, synth) > 110 * 1024) --stages;
+    a.stages = stages;
+    const size_t smem = ws_smem_bytes(rows, batch, stages, synth);
+    int ts, ta;
+    tc_tile_counts(lmax, npairs, ts, ta);
+    a.ntiles = synth ? ts : ta;
+    const unsigned blocks = (unsigned)((mmax + 1) * a.ntiles);
+    cudaError_t e2;
+    if (synth) {
+        e2 = cudaFuncSetAttribute(k_tc_ws<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e2 != cudaSuccess) return e2;
+        k_tc_ws<true><<<blocks, kWsThreads, smem, st>>>(a);
+    } else {
+        e2 = cudaFuncSetAttribute(k_tc_ws<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e2 != cudaSuccess) return e2;
+        k_tc_ws<false><<<blocks, kWsThreads, smem, st>>>(a);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
@@ -1304,7 +1491,7 @@ cudaError_t launch_tc_otf(bool synth, int lmax, int mmax, int npairs, int nlm, c
                           unsigned char *data, const float *in, float *out, int batch, Op op, int *err,
                           cudaStream_t st)
 {
-    if (batch < 1 || batch > tc_max_batch()) return cudaErrorInvalidValue;
+    if (batch < 1 || batch > tc_otf_max_batch()) return cudaErrorInvalidValue;
     const int rows = cols_of(batch);
     // synthesis data chunks are numbered like the segments (one chunk = one segment)
     cudaError_t e = launch_prep(synth, false, lmax, mmax, npairs, nlm, batch, rows, op, in, nullptr, segoff, data, st);
@@ -1329,10 +1516,10 @@ cudaError_t launch_tc_otf(bool synth, int lmax, int mmax, int npairs, int nlm, c
     // operand stages SA (4: generators fill two per round) and data stages SD
     // (up to 8), within 110 KB so that two CTAs share an SM
     int sa = 4, sd = 8;
-    while (sd > 3 && otf_smem_bytes(rows, sa, sd, a.nab) > 110 * 1024) --sd;
-    while (sa > 2 && otf_smem_bytes(rows, sa, sd, a.nab) > 110 * 1024) --sa;
+    while (sd > 3 && otf_smem_bytes(rows, sa, sd, a.nab, synth) > 110 * 1024) --sd;
+    while (sa > 2 && otf_smem_bytes(rows, sa, sd, a.nab, synth) > 110 * 1024) --sa;
     a.stages = sa | (sd << 8);
-    const size_t smem = otf_smem_bytes(rows, sa, sd, a.nab);
+    const size_t smem = otf_smem_bytes(rows, sa, sd, a.nab, synth);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     int ts, ta;
     tc_tile_counts(lmax, npairs, ts, ta);
