@@ -26,8 +26,11 @@
 // an error code and returns.
 // Leading panel chunks whose values are all below 2^-40 (high order, near
 // the poles) are skipped: the static polar optimisation of Sec. 3.1.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <cstring>
 
 #include <climits>
 #include <vector>
@@ -268,6 +271,7 @@ __host__ __device__ inline size_t smem_bytes_of(int npanels, int rows, int stage
 struct TcArgs {
     int lmax, mmax, npairs, nlm, batch, rows, ntiles, stages, op;
     const float *in;                       // raw FP32 s/d folds (warp-specialised analysis)
+    int fused;                             // synthesis: spectra converted in the kernel (tensor map)
     const unsigned char *panel, *dpanel;   // dpanel: vector transforms only
     const unsigned long long *off;         // per-order panel byte offsets
     const int *c0;                         // per (m, tile): first chunk above the polar threshold
@@ -359,14 +363,24 @@ __device__ __forceinline__ uint32_t setup_ctas(int S, uint64_t *bar_load, uint64
 // Warps 0-3 convert (analysis: the raw FP32 s/d folds of the chunk, brought in
 // by bulk copy, into the blocked bf16 hi/lo operand) and run the epilogue;
 // warp 4 lane 0 issues the MMAs; warp 5 streams the panel chunks and the data
-// (synthesis: the prepped blocked chunk; analysis: one raw row per field).
+// (synthesis: the prepped blocked chunk; analysis: the raw folds of all fields
+// by one TMA tensor copy, fold_map).
 // Stage: [panel chunk | blocked data | raw folds (analysis)].
 // ---------------------------------------------------------------------------
 constexpr int kWsThreads = 192;
-__host__ __device__ inline size_t ws_raw_bytes(int batch) { return (size_t)batch * kKc * sizeof(float4); }
+// Raw operand box per chunk: analysis kKc pairs (float4) per field; synthesis
+// 2 kKc spectral coefficients (float2) per field plus one more, so that the
+// box can start on a 16-byte boundary when the order's offset is odd.
+constexpr int kSynthBoxFloats = 4 * kKc + 4;
+__host__ __device__ inline size_t ws_raw_bytes(int batch, bool synth)
+{
+    return (size_t)batch * (synth ? kSynthBoxFloats * sizeof(float) : kKc * sizeof(float4));
+}
+// Stages are rounded up to 1 KB: the TMA tensor copy into a stage's raw box
+// needs a 128-byte aligned shared-memory destination.
 __host__ __device__ inline size_t ws_stage_bytes(int rows, int batch, bool synth)
 {
-    return kChunkPanel + data_chunk_bytes(rows) + (synth ? 0 : ws_raw_bytes(batch));
+    return (kChunkPanel + data_chunk_bytes(rows) + ws_raw_bytes(batch, synth) + 1023) & ~(size_t)1023;
 }
 __host__ __device__ inline size_t ws_smem_bytes(int rows, int batch, int stages, bool synth)
 {
@@ -374,7 +388,7 @@ __host__ __device__ inline size_t ws_smem_bytes(int rows, int batch, int stages,
 }
 
 template <bool SYNTH>
-__global__ void __launch_bounds__(kWsThreads, 2) k_tc_ws(TcArgs a)
+__global__ void __launch_bounds__(kWsThreads, 2) k_tc_ws(TcArgs a, const __grid_constant__ CUtensorMap fold_map)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -420,7 +434,43 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_tc_ws(TcArgs a)
     const uint32_t tmem = *tslot;
 
     if (warp < 4) {
-        // ---------------- converters (analysis) ----------------
+        // ---------------- converters ----------------
+        if (SYNTH && a.fused) {
+            // raw spectra of the chunk's 2 kKc degrees for every field -> blocked
+            // hi/lo rows 2b (re), 2b + 1 (im), class = parity of n - m
+            const int odd = (int)(col & 1);
+            const float cadj = (a.op == OP_ANALYS_ADJ && m > 0) ? 0.5f : 1.0f;
+            for (int u = 0; u < nlive; ++u) {
+                const int q = u % S;
+                const int c = cstart + u;
+                if (!wait_or_abort(&bar_load[q], (uint32_t)((u / S) & 1), &s_abort)) break;
+                unsigned char *st = smem + (size_t)q * stage;
+                unsigned char *dat = st + kChunkPanel;
+                const float *raw = reinterpret_cast<const float *>(dat + dbytes);
+                for (int i = tid; i < a.batch * 2 * kKc; i += 128) {
+                    const int b = i / (2 * kKc), j = i - b * (2 * kKc);
+                    const int nn = 2 * kKc * c + j;
+                    float re = 0.f, im = 0.f;
+                    if (nn < L) {
+                        const float *v = raw + (size_t)b * kSynthBoxFloats + 2 * (j + odd);
+                        re = v[0] * cadj;
+                        im = m == 0 ? 0.f : v[1] * cadj;
+                    }
+                    const int cls = j & 1, kk = j >> 1;
+                    unsigned char *bh = dat + (size_t)(cls * 2) * blk;
+                    __nv_bfloat16 h, l;
+                    split_bf16(re, h, l);
+                    *reinterpret_cast<__nv_bfloat16 *>(bh + blk_off(2 * b, kk)) = h;
+                    *reinterpret_cast<__nv_bfloat16 *>(bh + blk + blk_off(2 * b, kk)) = l;
+                    split_bf16(im, h, l);
+                    *reinterpret_cast<__nv_bfloat16 *>(bh + blk_off(2 * b + 1, kk)) = h;
+                    *reinterpret_cast<__nv_bfloat16 *>(bh + blk + blk_off(2 * b + 1, kk)) = l;
+                }
+                tc::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&bar_conv[q]);
+            }
+        }
         if (!SYNTH) {
             for (int u = 0; u < nlive; ++u) {
                 const int q = u % S;
@@ -466,7 +516,10 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_tc_ws(TcArgs a)
             for (int u = 0; u < nlive; ++u) {
                 const int q = u % S;
                 if (!wait_or_abort(&bar_load[q], (uint32_t)((u / S) & 1), &s_abort)) { ok = false; break; }
-                if (!SYNTH && !wait_or_abort(&bar_conv[q], (uint32_t)((u / S) & 1), &s_abort)) { ok = false; break; }
+                if ((!SYNTH || a.fused) && !wait_or_abort(&bar_conv[q], (uint32_t)((u / S) & 1), &s_abort)) {
+                    ok = false;
+                    break;
+                }
                 tc::tc_fence_after();
                 const uint64_t so = sstep * (uint64_t)q;
 #pragma unroll
@@ -497,19 +550,22 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_tc_ws(TcArgs a)
             const int np = min(kKc, npairs - kKc * c);
             if (lane == 0) {
                 const uint32_t tx = (uint32_t)kChunkPanel +
-                                    (SYNTH ? (uint32_t)dbytes : (uint32_t)(a.batch * np) * (uint32_t)sizeof(float4));
+                                    (uint32_t)(SYNTH && !a.fused ? dbytes : ws_raw_bytes(a.batch, SYNTH));
                 tc::mbar_arrive_expect_tx(&bar_load[q], tx);
                 tc::bulk_g2s(st, panel + (size_t)c * kChunkPanel, kChunkPanel, &bar_load[q]);
-                if (SYNTH) tc::bulk_g2s(st + kChunkPanel, data + (size_t)c * dbytes, (uint32_t)dbytes, &bar_load[q]);
-            }
-            __syncwarp();   // the transaction count is set before the other lanes' copies
-            if (!SYNTH) {
-                for (int b = lane; b < a.batch; b += 32) {
-                    // raw folds of field b: pairs [kKc c, kKc c + np) of order m
-                    const float4 *src = reinterpret_cast<const float4 *>(a.in) +
-                                        ((size_t)b * (a.mmax + 1) + m) * npairs + (size_t)kKc * c;
-                    tc::bulk_g2s(st + kChunkPanel + dbytes + (size_t)b * kKc * sizeof(float4), src,
-                                 (uint32_t)np * (uint32_t)sizeof(float4), &bar_load[q]);
+                if (SYNTH && a.fused) {
+                    // spectra of every field, degrees [2 kKc c, 2 kKc c + 2 kKc) of order
+                    // m, from the 16-byte boundary at or below (one coefficient earlier
+                    // when the order's offset is odd); degrees past the field arrive as zeros
+                    const int x = 2 * (int)(col - (col & 1)) + 4 * kKc * c;
+                    tc::tma_load_2d(st + kChunkPanel + dbytes, &fold_map, x, 0, &bar_load[q]);
+                } else if (SYNTH) {
+                    tc::bulk_g2s(st + kChunkPanel, data + (size_t)c * dbytes, (uint32_t)dbytes, &bar_load[q]);
+                } else {
+                    // raw folds of every field, pairs [kKc c, kKc c + kKc) of order m:
+                    // one tensor copy of the box {4 kKc floats, 1 order, batch fields};
+                    // pairs past npairs arrive as zeros
+                    tc::tma_load_3d(st + kChunkPanel + dbytes, &fold_map, 4 * kKc * c, m, 0, &bar_load[q]);
                 }
             }
             __syncwarp();
@@ -1267,6 +1323,57 @@ cudaError_t launch_prep(bool synth, bool vec, int lmax, int mmax, int npairs, in
     return cudaGetLastError();
 }
 
+// Tensor map over the s/d folds [batch][mmax+1][npairs] float4 seen as FP32
+// [batch][mmax+1][4 npairs], box {4 kKc, 1, batch}: one chunk of kKc pairs of
+// one order for every field.  cuTensorMapEncodeTiled is reached through the
+// runtime's driver entry point (no link against the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return nullptr;
+        encode = reinterpret_cast<EncodeTiledFn>(fn);
+    }
+    return encode;
+}
+
+cudaError_t make_fold_map(CUtensorMap *map, const float *sd, int npairs, int norders, int batch)
+{
+    EncodeTiledFn encode = encode_tiled();
+    if (!encode) return cudaErrorNotSupported;
+    const cuuint64_t dims[3] = {(cuuint64_t)4 * npairs, (cuuint64_t)norders, (cuuint64_t)batch};
+    const cuuint64_t strides[2] = {(cuuint64_t)npairs * sizeof(float4), (cuuint64_t)norders * npairs * sizeof(float4)};
+    const cuuint32_t box[3] = {(cuuint32_t)(4 * kKc), 1u, (cuuint32_t)batch};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(sd), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Tensor map over the spectra [batch][nlm] complex seen as FP32 [batch][2 nlm]
+// (nlm even), box {kSynthBoxFloats, batch}.
+cudaError_t make_spec_map(CUtensorMap *map, const float *spec, int nlm, int batch)
+{
+    EncodeTiledFn encode = encode_tiled();
+    if (!encode) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)2 * nlm, (cuuint64_t)batch};
+    const cuuint64_t strides[1] = {(cuuint64_t)nlm * 2 * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kSynthBoxFloats, (cuuint32_t)batch};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(spec), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1381,7 +1488,9 @@ cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int n
     const int rows = cols_of(batch);
     // synthesis: prep the spectra into the blocked layout; analysis: the
     // contraction converts the raw folds itself
-    if (synth && !prepped) {
+    // the spectra's tensor map needs a 16-byte row pitch: nlm even
+    const bool fuse_synth = synth && (nlm % 2 == 0);
+    if (synth && !fuse_synth && !prepped) {
         cudaError_t e =
             launch_prep(synth, false, lmax, mmax, npairs, nlm, batch, rows, op, in, nullptr, dchunk, data, st);
         if (e != cudaSuccess) return e;
@@ -1402,6 +1511,16 @@ cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int n
     a.out0 = out;
     a.err = err;
     a.in = in;
+    CUtensorMap fold_map;
+    memset(&fold_map, 0, sizeof(fold_map));
+    a.fused = fuse_synth ? 1 : 0;
+    if (!synth) {
+        cudaError_t em = make_fold_map(&fold_map, in, npairs, mmax + 1, batch);
+        if (em != cudaSuccess) return em;
+    } else if (fuse_synth) {
+        cudaError_t em = make_spec_map(&fold_map, in, nlm, batch);
+        if (em != cudaSuccess) return em;
+    }
     int stages = 4;
     while (stages > 2 && ws_smem_bytes(rows, batch, stages, synth) > 110 * 1024) --stages;
     a.stages = stages;
@@ -1414,11 +1533,11 @@ cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int n
     if (synth) {
         e2 = cudaFuncSetAttribute(k_tc_ws<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e2 != cudaSuccess) return e2;
-        k_tc_ws<true><<<blocks, kWsThreads, smem, st>>>(a);
+        k_tc_ws<true><<<blocks, kWsThreads, smem, st>>>(a, fold_map);
     } else {
         e2 = cudaFuncSetAttribute(k_tc_ws<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e2 != cudaSuccess) return e2;
-        k_tc_ws<false><<<blocks, kWsThreads, smem, st>>>(a);
+        k_tc_ws<false><<<blocks, kWsThreads, smem, st>>>(a, fold_map);
     }
     return cudaGetLastError();
 }
