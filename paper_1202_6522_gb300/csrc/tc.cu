@@ -537,6 +537,8 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_tc_ws(TcArgs a, const __grid_
     } else {
         // ---------------- producer ----------------
         const unsigned char *data = a.data + (SYNTH ? a.dchunk[m] * dbytes : 0);
+        const int rows_valid = SYNTH ? kRows : min(kRows, Le - kRows * tile);
+        const uint32_t pgb = (uint32_t)((rows_valid + 7) / 8) * kSbo;   // bytes of the used 8-row groups of a block
         int issued = 0;
         bool ok = true;
         for (int u = 0; u < nlive; ++u) {
@@ -549,10 +551,19 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_tc_ws(TcArgs a, const __grid_
             unsigned char *st = smem + (size_t)q * stage;
             const int np = min(kKc, npairs - kKc * c);
             if (lane == 0) {
-                const uint32_t tx = (uint32_t)kChunkPanel +
+                // analysis: the last degree tile of an order holds fewer than 128
+                // rows; only the 8-row groups holding degrees are copied (the MMA
+                // rows above them read stale data and are never written out)
+                const uint32_t tx = (pgb == (uint32_t)kBlk ? (uint32_t)kChunkPanel : 4u * pgb) +
                                     (uint32_t)(SYNTH && !a.fused ? dbytes : ws_raw_bytes(a.batch, SYNTH));
                 tc::mbar_arrive_expect_tx(&bar_load[q], tx);
-                tc::bulk_g2s(st, panel + (size_t)c * kChunkPanel, kChunkPanel, &bar_load[q]);
+                if (pgb == (uint32_t)kBlk) {
+                    tc::bulk_g2s(st, panel + (size_t)c * kChunkPanel, kChunkPanel, &bar_load[q]);
+                } else {
+                    for (int k = 0; k < 4; ++k)
+                        tc::bulk_g2s(st + (size_t)k * kBlk, panel + (size_t)c * kChunkPanel + (size_t)k * kBlk, pgb,
+                                     &bar_load[q]);
+                }
                 if (SYNTH && a.fused) {
                     // spectra of every field, degrees [2 kKc c, 2 kKc c + 2 kKc) of order
                     // m, from the 16-byte boundary at or below (one coefficient earlier
