@@ -447,24 +447,31 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_tc_ws(TcArgs a, const __grid_
                 unsigned char *st = smem + (size_t)q * stage;
                 unsigned char *dat = st + kChunkPanel;
                 const float *raw = reinterpret_cast<const float *>(dat + dbytes);
-                for (int i = tid; i < a.batch * 2 * kKc; i += 128) {
-                    const int b = i / (2 * kKc), j = i - b * (2 * kKc);
-                    const int nn = 2 * kKc * c + j;
-                    float re = 0.f, im = 0.f;
-                    if (nn < L) {
-                        const float *v = raw + (size_t)b * kSynthBoxFloats + 2 * (j + odd);
-                        re = v[0] * cadj;
-                        im = m == 0 ? 0.f : v[1] * cadj;
+                // item = (field, parity class, pair of K positions 2 kp, 2 kp + 1):
+                // two coefficients of the same parity, packed into 32-bit words
+                for (int i = tid; i < a.batch * kKc; i += 128) {
+                    const int b = i / kKc, r = i - b * kKc;
+                    const int cls = r / (kKc / 2), kp = r - cls * (kKc / 2);
+                    float re[2], im[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int j = 2 * (2 * kp + e) + cls;   // degree offset within the chunk
+                        const int nn = 2 * kKc * c + j;
+                        re[e] = im[e] = 0.f;
+                        if (nn < L) {
+                            const float *v = raw + (size_t)b * kSynthBoxFloats + 2 * (j + odd);
+                            re[e] = v[0] * cadj;
+                            im[e] = m == 0 ? 0.f : v[1] * cadj;
+                        }
                     }
-                    const int cls = j & 1, kk = j >> 1;
+                    uint32_t rh, rl, ih, il;
+                    split2(re[0], re[1], rh, rl);
+                    split2(im[0], im[1], ih, il);
                     unsigned char *bh = dat + (size_t)(cls * 2) * blk;
-                    __nv_bfloat16 h, l;
-                    split_bf16(re, h, l);
-                    *reinterpret_cast<__nv_bfloat16 *>(bh + blk_off(2 * b, kk)) = h;
-                    *reinterpret_cast<__nv_bfloat16 *>(bh + blk + blk_off(2 * b, kk)) = l;
-                    split_bf16(im, h, l);
-                    *reinterpret_cast<__nv_bfloat16 *>(bh + blk_off(2 * b + 1, kk)) = h;
-                    *reinterpret_cast<__nv_bfloat16 *>(bh + blk + blk_off(2 * b + 1, kk)) = l;
+                    *reinterpret_cast<uint32_t *>(bh + blk_off(2 * b, 2 * kp)) = rh;
+                    *reinterpret_cast<uint32_t *>(bh + blk + blk_off(2 * b, 2 * kp)) = rl;
+                    *reinterpret_cast<uint32_t *>(bh + blk_off(2 * b + 1, 2 * kp)) = ih;
+                    *reinterpret_cast<uint32_t *>(bh + blk + blk_off(2 * b + 1, 2 * kp)) = il;
                 }
                 tc::fence_proxy_async_smem();
                 __syncwarp();
@@ -480,18 +487,23 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_tc_ws(TcArgs a, const __grid_
                 unsigned char *dat = st + kChunkPanel;
                 const float4 *raw = reinterpret_cast<const float4 *>(dat + dbytes);
                 const int np = min(kKc, npairs - kKc * c);
-                for (int i = tid; i < a.batch * kKc; i += 128) {
-                    const int b = i / kKc, j = i - b * kKc;
-                    const float4 v = j < np ? raw[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const float va[4] = {v.x, v.y, v.z, v.w};   // s.re s.im d.re d.im
+                // item = (field, pair of K positions 2 jp, 2 jp + 1): two pairs' folds
+                // packed into 32-bit words per (fold, re|im, hi|lo)
+                for (int i = tid; i < a.batch * (kKc / 2); i += 128) {
+                    const int b = i / (kKc / 2), jp = i - b * (kKc / 2);
+                    const int j0 = 2 * jp;
+                    const float4 v0 = j0 < np ? raw[b * kKc + j0] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 v1 = j0 + 1 < np ? raw[b * kKc + j0 + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float a0[4] = {v0.x, v0.y, v0.z, v0.w};   // s.re s.im d.re d.im
+                    const float a1[4] = {v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        __nv_bfloat16 h, l;
-                        split_bf16(va[t], h, l);
-                        const uint32_t o = blk_off(2 * b + (t & 1), j);
+                        uint32_t h, l;
+                        split2(a0[t], a1[t], h, l);
+                        const uint32_t o = blk_off(2 * b + (t & 1), j0);
                         unsigned char *bh = dat + (size_t)((t >> 1) * 2) * blk;
-                        *reinterpret_cast<__nv_bfloat16 *>(bh + o) = h;
-                        *reinterpret_cast<__nv_bfloat16 *>(bh + blk + o) = l;
+                        *reinterpret_cast<uint32_t *>(bh + o) = h;
+                        *reinterpret_cast<uint32_t *>(bh + blk + o) = l;
                     }
                 }
                 tc::fence_proxy_async_smem();
@@ -909,16 +921,6 @@ __host__ __device__ inline uint32_t otf_tmem_cols(int rows, int sa, bool synth)
 // generates the chunks u with u % 2 == g) and one producer / MMA warp.
 constexpr int kOtfGroups = 2;
 constexpr int kOtfThreads = 32 * (4 * kOtfGroups + 2);   // + MMA warp + producer warp
-
-// v0, v1 -> bf16x2 hi and lo words with v = hi + lo per element.
-__device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_t &lo)
-{
-    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-    const float2 hf = __bfloat1622float2(h);
-    const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-    hi = *reinterpret_cast<const uint32_t *>(&h);
-    lo = *reinterpret_cast<const uint32_t *>(&l);
-}
 
 // kSeg steps of the FP32 recurrence from a seed (y1, y2, scale, x); P = y *
 // scale split into bf16 hi/lo and packed per parity: w[par][j] holds the
