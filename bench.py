@@ -655,8 +655,16 @@ def run_ours(args):
                 "kernel_avg_ms": dom_avg, "launches": dom_n}
     kernels = {k: {"avg_ms": v[0] / v[1], "launches": v[1], "share": v[0] / sum(x[0] for x in table.values())}
                for k, v in table.items()}
-    # each tensor-core launch is two kernels (operand prep + contraction)
-    launches = sum(v[1] * (2 if k.startswith("tc_") else 1) for k, v in table.items())
+    # kernels per profiled launch: the panel contraction converts its operands
+    # in-kernel (a separate operand-prep kernel runs first only for a synthesis
+    # with an odd coefficient count); the on-the-fly contraction always has one
+    def kernels_per(k):
+        if not k.startswith("tc_"):
+            return 1
+        if path_used == "tc_otf":
+            return 2
+        return 2 if (k == "tc_synth" and nlm_of(LMAX) % 2) else 1
+    launches = sum(v[1] * kernels_per(k) for k, v in table.items())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
