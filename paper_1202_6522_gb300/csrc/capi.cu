@@ -48,25 +48,28 @@ int check_mode(int mode)
 void free_panels(sht::Plan &p)
 {
     cudaFree(p.panel_s); cudaFree(p.panel_a); cudaFree(p.d_off_s); cudaFree(p.d_off_a); cudaFree(p.d_dchunk);
-    cudaFree(p.d_c0_s); cudaFree(p.d_c0_a);
+    cudaFree(p.d_c0_s); cudaFree(p.d_c0_a); cudaFree(p.d_gf_s); cudaFree(p.d_gf_a);
     p.panel_s = p.panel_a = nullptr;
     p.d_off_s = p.d_off_a = p.d_dchunk = nullptr;
     p.d_c0_s = p.d_c0_a = nullptr;
+    p.d_gf_s = p.d_gf_a = nullptr;
 }
 
-// Static polar optimisation (Sec. 3.1): per (m, tile) the first panel chunk
-// holding a value >= the plan's threshold; the fractions skipped.
+// Static polar optimisation (Sec. 3.1): per (m, tile) and per 8-row group of
+// the tile, the first panel chunk holding a value >= the plan's threshold;
+// the fractions of panel bytes skipped.
 cudaError_t first_live_scalar(sht::Plan &p)
 {
     int ts = 0, ta = 0;
     cudaError_t e = sht::launch_panel_first_live(true, p.lmax, p.mmax, p.npairs, p.d_off_s, p.panel_s, p.polar_thr,
-                                                 p.d_c0_s, ts, 0);
+                                                 p.d_c0_s, ts, 0, p.d_gf_s);
     if (e == cudaSuccess)
         e = sht::launch_panel_first_live(false, p.lmax, p.mmax, p.npairs, p.d_off_a, p.panel_a, p.polar_thr,
-                                         p.d_c0_a, ta, 0);
+                                         p.d_c0_a, ta, 0, p.d_gf_a);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess)
-        e = sht::tc_polar_stats(p.lmax, p.mmax, p.npairs, p.d_c0_s, p.d_c0_a, p.polar_skip_s, p.polar_skip_a);
+        e = sht::tc_polar_stats(p.lmax, p.mmax, p.npairs, p.d_c0_s, p.d_c0_a, p.polar_skip_s, p.polar_skip_a,
+                                p.d_gf_s, p.d_gf_a);
     return e;
 }
 
@@ -107,6 +110,8 @@ int ensure_panels(sht::Plan &p)
     if (e == cudaSuccess) e = cudaMalloc(&p.d_dchunk, ob);
     if (e == cudaSuccess) e = cudaMalloc(&p.d_c0_s, sizeof(int) * (size_t)(p.mmax + 1) * T_s);
     if (e == cudaSuccess) e = cudaMalloc(&p.d_c0_a, sizeof(int) * (size_t)(p.mmax + 1) * T_a);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_gf_s, sizeof(unsigned short) * 16 * (size_t)(p.mmax + 1) * T_s);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_gf_a, sizeof(unsigned short) * 16 * (size_t)(p.mmax + 1) * T_a);
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_panels(p);
@@ -531,7 +536,7 @@ int run_synth_tc(sht::Plan &p, const void *spec, void *grid, int batch, sht::Op 
         float *out = static_cast<float *>(grid) + (size_t)b0 * p.nlat * p.nphi;
         int rc = timed(p, SHT_K_TC_SYNTH, s, "tensor-core synthesis launch", [&] {
             return sht::launch_tc_legendre(true, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_s, p.d_off_s, p.d_c0_s,
-                                           p.d_dchunk, data, in, eo, nb, op, p.d_err, false, s);
+                                           p.d_gf_s, p.d_dchunk, data, in, eo, nb, op, p.d_err, false, s);
         });
         if (rc) return rc;
         rc = timed(p, SHT_K_FFT_SYNTH, s, "fft synthesis launch",
@@ -555,7 +560,7 @@ int run_analys_tc(sht::Plan &p, const void *grid, void *spec, int batch, sht::Op
         if (rc) return rc;
         rc = timed(p, SHT_K_TC_ANALYS, s, "tensor-core analysis launch", [&] {
             return sht::launch_tc_legendre(false, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_a, p.d_off_a, p.d_c0_a,
-                                           p.d_dchunk, data, sd, out, nb, op, p.d_err, false, s);
+                                           p.d_gf_a, p.d_dchunk, data, sd, out, nb, op, p.d_err, false, s);
         });
         if (rc) return rc;
     }

@@ -280,6 +280,9 @@ void plan_free(Plan &p)
     if (p.d_dchunk) cudaFree(p.d_dchunk);
     if (p.d_c0_s) cudaFree(p.d_c0_s);
     if (p.d_c0_a) cudaFree(p.d_c0_a);
+    if (p.d_gf_s) cudaFree(p.d_gf_s);
+    if (p.d_gf_a) cudaFree(p.d_gf_a);
+    p.d_gf_s = p.d_gf_a = nullptr;
     if (p.dpanel_s) cudaFree(p.dpanel_s);
     if (p.dpanel_a) cudaFree(p.dpanel_a);
     if (p.d_c0v_s) cudaFree(p.d_c0v_s);

@@ -92,7 +92,8 @@ struct Plan {
     unsigned long long *d_off_s = nullptr, *d_off_a = nullptr, *d_dchunk = nullptr;
     size_t tc_nchunk_s = 0;                     // synthesis data chunks over all orders
     int *d_c0_s = nullptr, *d_c0_a = nullptr;   // first live chunk per (m, tile)
-    double polar_skip_s = 0, polar_skip_a = 0;  // fraction of panel chunks skipped
+    unsigned short *d_gf_s = nullptr, *d_gf_a = nullptr;  // ... per 8-row group of (m, tile)
+    double polar_skip_s = 0, polar_skip_a = 0;  // fraction of panel bytes skipped
     float polar_thr = 0x1p-40f;                 // polar threshold (sht_set_polar_threshold)
     unsigned char *dpanel_s = nullptr, *dpanel_a = nullptr; // sin(theta) dP/dtheta panels (vector)
     int *d_c0v_s = nullptr, *d_c0v_a = nullptr; // first chunk live in P or dP
@@ -190,7 +191,8 @@ cudaError_t launch_build_panels(const PlanView<double> &pv, const unsigned long 
 // this operand) then the tcgen05 kernel.  Synthesis: spectra -> E/O;
 // analysis: s/d folds -> spectra.
 cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
-                               const unsigned long long *off, const int *c0, const unsigned long long *dchunk,
+                               const unsigned long long *off, const int *c0, const unsigned short *gfirst,
+                               const unsigned long long *dchunk,
                                unsigned char *data, const float *in, float *out, int batch, Op op, int *err,
                                bool prepped, cudaStream_t st);
 // Vector contraction of <= tc_vec_max_batch() fields.  Synthesis: (S, T) ->
@@ -205,12 +207,17 @@ int tc_vec_max_batch();
 int tc_otf_max_batch();
 // Rows of the data operand for `batch` fields: 32 ceil(2 batch / 32), twice that for vectors.
 inline int tc_rows(int batch, bool vec) { return (vec ? 2 : 1) * (((2 * batch + 31) / 32) * 32); }
-// Static polar optimisation: per (m, tile) first chunk with a panel value >= thr.
+// Static polar optimisation: per (m, tile) first chunk with a panel value >=
+// thr; with `gfirst`, also per 8-row group of the tile ([m][tile][16]).
 cudaError_t launch_panel_first_live(bool synth, int lmax, int mmax, int npairs, const unsigned long long *off,
-                                    const unsigned char *panel, float thr, int *c0, int &ntiles, cudaStream_t st);
+                                    const unsigned char *panel, float thr, int *c0, int &ntiles, cudaStream_t st,
+                                    unsigned short *gfirst = nullptr);
 void tc_tile_counts(int lmax, int npairs, int &ntiles_s, int &ntiles_a);
+// Fractions of panel bytes skipped: per 8-row group when the group tables are
+// given, else per whole chunk.
 cudaError_t tc_polar_stats(int lmax, int mmax, int npairs, const int *d_c0_s, const int *d_c0_a, double &frac_s,
-                           double &frac_a);
+                           double &frac_a, const unsigned short *d_gf_s = nullptr,
+                           const unsigned short *d_gf_a = nullptr);
 int tc_max_batch();
 cudaError_t launch_selftest_timeout(int *err, unsigned long long max_ns, cudaStream_t st);
 

@@ -32,6 +32,7 @@
 
 #include <cstring>
 
+#include <algorithm>
 #include <climits>
 #include <vector>
 
@@ -45,6 +46,15 @@ namespace {
 constexpr int kRows = 128;            // MMA M
 constexpr int kBlk = kRows * kKc * 2; // bytes of one bf16 [128 x kKc] panel block
 constexpr int kChunkPanel = 4 * kBlk; // [parity][hi/lo] blocks per chunk = 16 KB
+// A panel chunk interleaves its four blocks (parity x hi/lo) per 8-row group:
+// group g of block kb at g * kPSbo + kb * kSbo, so that the rows from any group
+// on are one contiguous byte range of the chunk.  kPSbo is the MMA's 8-row
+// group stride for a panel block.
+constexpr uint32_t kPSbo = 4 * kSbo;
+__host__ __device__ __forceinline__ uint32_t pan_off(int kb, int row, int k)
+{
+    return (uint32_t)((row >> 3) * kPSbo + kb * kSbo + (k >> 3) * kLbo + (row & 7) * 16 + (k & 7) * 2);
+}
 constexpr uint64_t kWaitNs = 2000000000ull; // 2 s
 
 __device__ __forceinline__ void split_bf16_d(double v, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
@@ -124,18 +134,16 @@ k_build_panels(PlanView<double> pv, const unsigned long long *__restrict__ off_s
         const int par = nn & 1, kk = nn >> 1;
         // synthesis panel: block (t, chunk kk/kKc, parity, hi|lo), element (row, kk%kKc)
         {
-            unsigned char *b = sbase + (size_t)(kk / kKc) * kChunkPanel + (size_t)(par * 2) * kBlk;
-            const uint32_t o = blk_off(row, kk % kKc);
-            *reinterpret_cast<__nv_bfloat16 *>(b + o) = hi;
-            *reinterpret_cast<__nv_bfloat16 *>(b + kBlk + o) = lo;
+            unsigned char *b = sbase + (size_t)(kk / kKc) * kChunkPanel;
+            *reinterpret_cast<__nv_bfloat16 *>(b + pan_off(par * 2, row, kk % kKc)) = hi;
+            *reinterpret_cast<__nv_bfloat16 *>(b + pan_off(par * 2 + 1, row, kk % kKc)) = lo;
         }
         // analysis panel: block (M tile kk/128, pair chunk kc, parity, hi|lo), element (kk%128, pc)
         {
             const int mt = kk / kRows, r = kk % kRows;
-            unsigned char *b = abase + ((size_t)mt * kch + kc) * kChunkPanel + (size_t)(par * 2) * kBlk;
-            const uint32_t o = blk_off(r, pc);
-            *reinterpret_cast<__nv_bfloat16 *>(b + o) = hi;
-            *reinterpret_cast<__nv_bfloat16 *>(b + kBlk + o) = lo;
+            unsigned char *b = abase + ((size_t)mt * kch + kc) * kChunkPanel;
+            *reinterpret_cast<__nv_bfloat16 *>(b + pan_off(par * 2, r, pc)) = hi;
+            *reinterpret_cast<__nv_bfloat16 *>(b + pan_off(par * 2 + 1, r, pc)) = lo;
         }
     }
 }
@@ -275,6 +283,7 @@ struct TcArgs {
     const unsigned char *panel, *dpanel;   // dpanel: vector transforms only
     const unsigned long long *off;         // per-order panel byte offsets
     const int *c0;                         // per (m, tile): first chunk above the polar threshold
+    const unsigned short *gf;              // per (m, tile, 8-row group): first chunk above it (or null)
     const unsigned char *data;             // data operand, blocked bf16 hi/lo
     const unsigned long long *dchunk;      // synthesis: first data chunk of each order
     float *out0, *out1;                    // outputs (vector: second quantity in out1)
@@ -368,6 +377,7 @@ __device__ __forceinline__ uint32_t setup_ctas(int S, uint64_t *bar_load, uint64
 // Stage: [panel chunk | blocked data | raw folds (analysis)].
 // ---------------------------------------------------------------------------
 constexpr int kWsThreads = 192;
+constexpr int kWsCtasPerSm = 3;   // resident CTAs per SM: 3 x 3 stages beat 2 x 4
 // Raw operand box per chunk: analysis kKc pairs (float4) per field; synthesis
 // 2 kKc spectral coefficients (float2) per field plus one more, so that the
 // box can start on a 16-byte boundary when the order's offset is odd.
@@ -376,22 +386,22 @@ __host__ __device__ inline size_t ws_raw_bytes(int batch, bool synth)
 {
     return (size_t)batch * (synth ? kSynthBoxFloats * sizeof(float) : kKc * sizeof(float4));
 }
-// Stages are rounded up to 1 KB: the TMA tensor copy into a stage's raw box
-// needs a 128-byte aligned shared-memory destination.
+// Stages are rounded up to 128 bytes: the TMA tensor copy into a stage's raw
+// box needs a 128-byte aligned shared-memory destination.
 __host__ __device__ inline size_t ws_stage_bytes(int rows, int batch, bool synth)
 {
-    return (kChunkPanel + data_chunk_bytes(rows) + ws_raw_bytes(batch, synth) + 1023) & ~(size_t)1023;
+    return (kChunkPanel + data_chunk_bytes(rows) + ws_raw_bytes(batch, synth) + 127) & ~(size_t)127;
 }
 __host__ __device__ inline size_t ws_smem_bytes(int rows, int batch, int stages, bool synth)
 {
-    return 1024 + (size_t)stages * ws_stage_bytes(rows, batch, synth) + 8 * (3 * stages + 2);
+    return 128 + (size_t)stages * ws_stage_bytes(rows, batch, synth) + 8 * (3 * stages + 2);
 }
 
 template <bool SYNTH>
-__global__ void __launch_bounds__(kWsThreads, 2) k_tc_ws(TcArgs a, const __grid_constant__ CUtensorMap fold_map)
+__global__ void __launch_bounds__(kWsThreads, kWsCtasPerSm) k_tc_ws(TcArgs a, const __grid_constant__ CUtensorMap fold_map)
 {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     const int S = a.stages, NC = a.rows;
     const size_t dbytes = data_chunk_bytes(NC);
     const size_t stage = ws_stage_bytes(NC, a.batch, SYNTH);
@@ -428,6 +438,23 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_tc_ws(TcArgs a, const __grid_
         s_abort = 0;
     }
     if (warp == 0) tc::tmem_alloc(tslot, ncols);
+    // Polar optimisation per 8-row group: a chunk's panel is copied from its
+    // first group above the threshold, g0(c) = min{g : gf[g] <= c}, which never
+    // grows with c.  Stage q first holds chunk cstart + q; its groups below that
+    // chunk's g0 are zeroed once, and the later chunks of the stage write only
+    // groups at or above their own (smaller or equal) g0, so the groups below it
+    // stay zero and add nothing to the MMAs.
+    const unsigned short *gf = a.gf ? a.gf + ((size_t)m * a.ntiles + tile) * (kRows / 8) : nullptr;
+    if (gf) {
+        for (int q = 0; q < min(S, nlive); ++q) {
+            int g0 = 0;
+            while (g0 < kRows / 8 && gf[g0] > cstart + q) ++g0;
+            if (g0 == kRows / 8) g0 = 0;
+            for (int w = tid; w < g0 * (int)(kPSbo / 16); w += kWsThreads)
+                *reinterpret_cast<uint4 *>(smem + (size_t)q * stage + (size_t)w * 16) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        tc::fence_proxy_async_smem();
+    }
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -520,7 +547,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_tc_ws(TcArgs a, const __grid_
             for (int par = 0; par < 2; ++par)
 #pragma unroll
                 for (int hl = 0; hl < 2; ++hl) {
-                    da0[par][hl] = tc::smem_desc(smem + (size_t)(par * 2 + hl) * kBlk, kLbo, kSbo);
+                    da0[par][hl] = tc::smem_desc(smem + (size_t)(par * 2 + hl) * kSbo, kLbo, kPSbo);
                     db0[par][hl] = tc::smem_desc(smem + kChunkPanel + (size_t)(par * 2 + hl) * blk, kLbo, kSbo);
                 }
             const uint64_t sstep = stage >> 4;
@@ -550,7 +577,9 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_tc_ws(TcArgs a, const __grid_
         // ---------------- producer ----------------
         const unsigned char *data = a.data + (SYNTH ? a.dchunk[m] * dbytes : 0);
         const int rows_valid = SYNTH ? kRows : min(kRows, Le - kRows * tile);
-        const uint32_t pgb = (uint32_t)((rows_valid + 7) / 8) * kSbo;   // bytes of the used 8-row groups of a block
+        const uint32_t pgb = (uint32_t)((rows_valid + 7) / 8) * kPSbo;  // panel bytes up to the last used 8-row group
+        // lane g < 16: first live chunk of 8-row group g
+        const int gfl = (gf && lane < kRows / 8) ? (int)gf[lane] : 0;
         int issued = 0;
         bool ok = true;
         for (int u = 0; u < nlive; ++u) {
@@ -561,21 +590,16 @@ __global__ void __launch_bounds__(kWsThreads, 2) k_tc_ws(TcArgs a, const __grid_
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             unsigned char *st = smem + (size_t)q * stage;
-            const int np = min(kKc, npairs - kKc * c);
+            const unsigned live = __ballot_sync(0xffffffffu, lane < kRows / 8 && gfl <= c);
+            const uint32_t lo = min(live ? (uint32_t)(__ffs(live) - 1) * kPSbo : 0u, pgb);
             if (lane == 0) {
-                // analysis: the last degree tile of an order holds fewer than 128
-                // rows; only the 8-row groups holding degrees are copied (the MMA
-                // rows above them read stale data and are never written out)
-                const uint32_t tx = (pgb == (uint32_t)kBlk ? (uint32_t)kChunkPanel : 4u * pgb) +
-                                    (uint32_t)(SYNTH && !a.fused ? dbytes : ws_raw_bytes(a.batch, SYNTH));
+                // copied: the 8-row groups from g0(c) up to the last one holding
+                // rows (analysis: the last degree tile of an order holds fewer
+                // than 128 rows; the MMA rows above them read stale data and are
+                // never written out)
+                const uint32_t tx = (pgb - lo) + (uint32_t)(SYNTH && !a.fused ? dbytes : ws_raw_bytes(a.batch, SYNTH));
                 tc::mbar_arrive_expect_tx(&bar_load[q], tx);
-                if (pgb == (uint32_t)kBlk) {
-                    tc::bulk_g2s(st, panel + (size_t)c * kChunkPanel, kChunkPanel, &bar_load[q]);
-                } else {
-                    for (int k = 0; k < 4; ++k)
-                        tc::bulk_g2s(st + (size_t)k * kBlk, panel + (size_t)c * kChunkPanel + (size_t)k * kBlk, pgb,
-                                     &bar_load[q]);
-                }
+                if (pgb > lo) tc::bulk_g2s(st + lo, panel + (size_t)c * kChunkPanel + lo, pgb - lo, &bar_load[q]);
                 if (SYNTH && a.fused) {
                     // spectra of every field, degrees [2 kKc c, 2 kKc c + 2 kKc) of order
                     // m, from the 16-byte boundary at or below (one coefficient earlier
@@ -695,14 +719,14 @@ __global__ void __launch_bounds__(128, 1) k_tc_vec(TcArgs a)
 #pragma unroll
             for (int cls = 0; cls < 2; ++cls) {
                 const int dp = SYNTH ? 1 - cls : cls;   // parity of n - m of the dP block
-                const unsigned char *aph = st + (size_t)(cls * 2) * kBlk, *apl = aph + kBlk;
-                const unsigned char *adh = st + kChunkPanel + (size_t)(dp * 2) * kBlk, *adl = adh + kBlk;
+                const unsigned char *aph = st + (size_t)(cls * 2) * kSbo, *apl = aph + kSbo;
+                const unsigned char *adh = st + kChunkPanel + (size_t)(dp * 2) * kSbo, *adl = adh + kSbo;
                 const unsigned char *b1h = dat + (size_t)(cls * 2) * blk, *b1l = b1h + blk;
                 const unsigned char *b2h = dat + (size_t)((1 - cls) * 2) * blk, *b2l = b2h + blk;
                 const uint32_t d1 = tmem + (uint32_t)((cls * 2 + 0) * NV);
                 const uint32_t d2 = tmem + (uint32_t)((cls * 2 + 1) * NV);
-                const uint64_t Aph = tc::smem_desc(aph, kLbo, kSbo), Apl = tc::smem_desc(apl, kLbo, kSbo);
-                const uint64_t Adh = tc::smem_desc(adh, kLbo, kSbo), Adl = tc::smem_desc(adl, kLbo, kSbo);
+                const uint64_t Aph = tc::smem_desc(aph, kLbo, kPSbo), Apl = tc::smem_desc(apl, kLbo, kPSbo);
+                const uint64_t Adh = tc::smem_desc(adh, kLbo, kPSbo), Adl = tc::smem_desc(adl, kLbo, kPSbo);
                 const uint64_t B1h = tc::smem_desc(b1h, kLbo, kSbo), B1l = tc::smem_desc(b1l, kLbo, kSbo);
                 const uint64_t B2h = tc::smem_desc(b2h, kLbo, kSbo), B2l = tc::smem_desc(b2l, kLbo, kSbo);
                 tc::mma_bf16(d1, Aph, B1h, idesc, !first);
@@ -1252,34 +1276,54 @@ __global__ void __launch_bounds__(kOtfThreads, 2) k_tc_otf(OtfArgs a)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128)
 k_panel_first_live(int synth, int lmax, int npairs, int ntiles, const unsigned long long *__restrict__ off,
-                   const unsigned char *__restrict__ panel, float thr, int *__restrict__ c0)
+                   const unsigned char *__restrict__ panel, float thr, int *__restrict__ c0,
+                   unsigned short *__restrict__ gfirst)
 {
     const int m = blockIdx.y, tile = blockIdx.x;
     const int L = lmax - m + 1, Le = (L + 1) / 2;
     const int nchunks = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
     const bool valid = synth || tile * kRows < Le;
-    __shared__ int s_live;
-    int first = nchunks;
+    constexpr int NG = kRows / 8;
+    __shared__ int s_live[NG], s_first[NG], s_open;
+    if (threadIdx.x < NG) s_first[threadIdx.x] = nchunks;
+    __syncthreads();
     if (valid) {
+        // rows of the tile that hold a latitude pair (synthesis) or a degree (analysis)
+        const int rows_valid = synth ? min(kRows, npairs - kRows * tile) : min(kRows, Le - kRows * tile);
+        const int ng = (rows_valid + 7) / 8;
         const unsigned char *base = panel + off[m] + (size_t)tile * nchunks * kChunkPanel;
         for (int c = 0; c < nchunks; ++c) {
-            if (threadIdx.x == 0) s_live = 0;
+            if (threadIdx.x < NG) s_live[threadIdx.x] = 0;
+            if (threadIdx.x == 0) s_open = 0;
             __syncthreads();
-            // hi blocks of both parities (the lo parts are ~2^-8 smaller)
-            const __nv_bfloat16 *blkp = reinterpret_cast<const __nv_bfloat16 *>(base + (size_t)c * kChunkPanel);
-            bool live = false;
+            // hi blocks of both parities (the lo parts are ~2^-8 smaller): the
+            // 8 kKc values of 8-row group g of block kb start at g kPSbo + kb kSbo
+            const unsigned char *cp = base + (size_t)c * kChunkPanel;
             for (int par = 0; par < 2; ++par) {
-                const __nv_bfloat16 *h = blkp + (size_t)(par * 2) * (kBlk / 2);
-                for (int i = threadIdx.x; i < kBlk / 2; i += blockDim.x) live |= fabsf(__bfloat162float(h[i])) >= thr;
+                for (int i = threadIdx.x; i < kBlk / 2; i += blockDim.x) {
+                    const int g = i / (8 * kKc), e = i - g * (8 * kKc);
+                    const __nv_bfloat16 v =
+                        *reinterpret_cast<const __nv_bfloat16 *>(cp + (size_t)g * kPSbo + (size_t)(par * 2) * kSbo + 2 * e);
+                    if (fabsf(__bfloat162float(v)) >= thr) s_live[g] = 1;
+                }
             }
-            if (live) s_live = 1;
             __syncthreads();
-            const int any = s_live;
+            if (threadIdx.x < ng) {
+                if (s_live[threadIdx.x] && s_first[threadIdx.x] == nchunks) s_first[threadIdx.x] = c;
+                if (s_first[threadIdx.x] == nchunks) s_open = 1;
+            }
             __syncthreads();
-            if (any) { first = c; break; }
+            const int open = s_open;
+            __syncthreads();
+            if (!open) break;   // every group of the tile has its first live chunk
         }
     }
-    if (threadIdx.x == 0) c0[m * ntiles + tile] = first;
+    if (threadIdx.x == 0) {
+        int first = nchunks;
+        for (int g = 0; g < NG; ++g) first = min(first, s_first[g]);
+        c0[m * ntiles + tile] = first;
+    }
+    if (gfirst && threadIdx.x < NG) gfirst[((size_t)m * ntiles + tile) * NG + threadIdx.x] = (unsigned short)s_first[threadIdx.x];
 }
 
 __global__ void k_min_int(const int *__restrict__ a, const int *__restrict__ b, int *__restrict__ out, int n)
@@ -1460,21 +1504,49 @@ void tc_tile_counts(int lmax, int npairs, int &ntiles_s, int &ntiles_a)
 }
 
 cudaError_t tc_polar_stats(int lmax, int mmax, int npairs, const int *d_c0_s, const int *d_c0_a, double &frac_s,
-                           double &frac_a)
+                           double &frac_a, const unsigned short *d_gf_s, const unsigned short *d_gf_a)
 {
     int T_s, T_a;
     tc_tile_counts(lmax, npairs, T_s, T_a);
-    std::vector<int> c0s((size_t)(mmax + 1) * T_s), c0a((size_t)(mmax + 1) * T_a);
-    cudaError_t e = cudaMemcpy(c0s.data(), d_c0_s, sizeof(int) * c0s.size(), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(c0a.data(), d_c0_a, sizeof(int) * c0a.size(), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return e;
-    double sk_s = 0, tot_s = 0, sk_a = 0, tot_a = 0;
+    constexpr int NG = kRows / 8;
     const int kch = (npairs + kKc - 1) / kKc;
-    for (int m = 0; m <= mmax; ++m) {
-        const int Le = (lmax - m + 2) / 2, nch = (Le + kKc - 1) / kKc;
-        for (int t = 0; t < T_s; ++t) { sk_s += c0s[(size_t)m * T_s + t]; tot_s += nch; }
-        for (int t = 0; t < T_a; ++t)
-            if (t * kRows < Le) { sk_a += c0a[(size_t)m * T_a + t]; tot_a += kch; }
+    double sk_s = 0, tot_s = 0, sk_a = 0, tot_a = 0;
+    if (d_gf_s && d_gf_a) {
+        // panel bytes skipped: 8-row groups of a chunk before the group's first live chunk
+        std::vector<unsigned short> gs((size_t)(mmax + 1) * T_s * NG), ga((size_t)(mmax + 1) * T_a * NG);
+        cudaError_t e = cudaMemcpy(gs.data(), d_gf_s, sizeof(unsigned short) * gs.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(ga.data(), d_gf_a, sizeof(unsigned short) * ga.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return e;
+        for (int m = 0; m <= mmax; ++m) {
+            const int Le = (lmax - m + 2) / 2, nch = (Le + kKc - 1) / kKc;
+            for (int t = 0; t < T_s; ++t) {
+                const int ng = (std::min(kRows, npairs - kRows * t) + 7) / 8;
+                for (int g = 0; g < ng; ++g) {
+                    sk_s += std::min<int>(gs[((size_t)m * T_s + t) * NG + g], nch);
+                    tot_s += nch;
+                }
+            }
+            for (int t = 0; t < T_a; ++t) {
+                if (t * kRows >= Le) continue;
+                const int ng = (std::min(kRows, Le - kRows * t) + 7) / 8;
+                for (int g = 0; g < ng; ++g) {
+                    sk_a += std::min<int>(ga[((size_t)m * T_a + t) * NG + g], kch);
+                    tot_a += kch;
+                }
+            }
+        }
+    } else {
+        // whole chunks skipped
+        std::vector<int> c0s((size_t)(mmax + 1) * T_s), c0a((size_t)(mmax + 1) * T_a);
+        cudaError_t e = cudaMemcpy(c0s.data(), d_c0_s, sizeof(int) * c0s.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(c0a.data(), d_c0_a, sizeof(int) * c0a.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return e;
+        for (int m = 0; m <= mmax; ++m) {
+            const int Le = (lmax - m + 2) / 2, nch = (Le + kKc - 1) / kKc;
+            for (int t = 0; t < T_s; ++t) { sk_s += c0s[(size_t)m * T_s + t]; tot_s += nch; }
+            for (int t = 0; t < T_a; ++t)
+                if (t * kRows < Le) { sk_a += c0a[(size_t)m * T_a + t]; tot_a += kch; }
+        }
     }
     frac_s = tot_s > 0 ? sk_s / tot_s : 0.0;
     frac_a = tot_a > 0 ? sk_a / tot_a : 0.0;
@@ -1482,18 +1554,20 @@ cudaError_t tc_polar_stats(int lmax, int mmax, int npairs, const int *d_c0_s, co
 }
 
 cudaError_t launch_panel_first_live(bool synth, int lmax, int mmax, int npairs, const unsigned long long *off,
-                                    const unsigned char *panel, float thr, int *c0, int &ntiles, cudaStream_t st)
+                                    const unsigned char *panel, float thr, int *c0, int &ntiles, cudaStream_t st,
+                                    unsigned short *gfirst)
 {
     int ts, ta;
     tc_tile_counts(lmax, npairs, ts, ta);
     ntiles = synth ? ts : ta;
     dim3 g((unsigned)ntiles, (unsigned)(mmax + 1));
-    k_panel_first_live<<<g, 128, 0, st>>>(synth ? 1 : 0, lmax, npairs, ntiles, off, panel, thr, c0);
+    k_panel_first_live<<<g, 128, 0, st>>>(synth ? 1 : 0, lmax, npairs, ntiles, off, panel, thr, c0, gfirst);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
-                               const unsigned long long *off, const int *c0, const unsigned long long *dchunk,
+                               const unsigned long long *off, const int *c0, const unsigned short *gfirst,
+                               const unsigned long long *dchunk,
                                unsigned char *data, const float *in, float *out, int batch, Op op, int *err,
                                bool prepped, cudaStream_t st)
 {
@@ -1519,6 +1593,7 @@ cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int n
     a.panel = panel;
     a.off = off;
     a.c0 = c0;
+    a.gf = c0 ? gfirst : nullptr;
     a.data = data;
     a.dchunk = dchunk;
     a.out0 = out;
@@ -1534,8 +1609,15 @@ cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int n
         cudaError_t em = make_spec_map(&fold_map, in, nlm, batch);
         if (em != cudaSuccess) return em;
     }
-    int stages = 4;
-    while (stages > 2 && ws_smem_bytes(rows, batch, stages, synth) > 110 * 1024) --stages;
+    // kWsCtasPerSm CTAs of up to 3 stages per SM (228 KB, 1 KB reserved per
+    // CTA, a little static shared memory); wider batches fall back to fewer CTAs
+    const size_t cap = (size_t)228 * 1024 / kWsCtasPerSm - 1024 - 256;
+    int stages = 3;
+    while (stages > 2 && ws_smem_bytes(rows, batch, stages, synth) > cap) --stages;
+    if (ws_smem_bytes(rows, batch, stages, synth) > cap) {
+        stages = 4;
+        while (stages > 2 && ws_smem_bytes(rows, batch, stages, synth) > 110 * 1024) --stages;
+    }
     a.stages = stages;
     const size_t smem = ws_smem_bytes(rows, batch, stages, synth);
     int ts, ta;
