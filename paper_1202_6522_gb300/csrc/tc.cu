@@ -425,7 +425,12 @@ __global__ void __launch_bounds__(kWsThreads, kWsCtasPerSm) k_tc_ws(TcArgs a, co
     const unsigned char *panel = a.panel + a.off[m] + (size_t)tile * nchunks * kChunkPanel;
     const int cstart = a.c0 ? a.c0[m * a.ntiles + tile] : 0;
     const int nlive = nchunks - cstart;
-    const uint32_t ncols = NC * 2 <= 64 ? 64 : (NC * 2 <= 128 ? 128 : 256);
+    // wide: per parity, A_hi x [B_hi ; B_lo] as one MMA of N = 2 NC (columns
+    // [hi.hi + lo.hi | hi.lo], summed by the epilogue) plus A_lo x B_hi, 4
+    // MMAs per chunk; else 3 MMAs of N = NC per parity into NC columns
+    const bool wide = 4 * NC <= 256;
+    const int pcols = wide ? 2 * NC : NC;   // accumulator columns per parity
+    const uint32_t ncols = 2 * pcols <= 64 ? 64 : (2 * pcols <= 128 ? 128 : (2 * pcols <= 256 ? 256 : 512));
 
     if (tid == 0) {
         for (int q = 0; q < S; ++q) {
@@ -542,6 +547,7 @@ __global__ void __launch_bounds__(kWsThreads, kWsCtasPerSm) k_tc_ws(TcArgs a, co
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
             const uint32_t idesc = tc::idesc_bf16_f32(kRows, NC);
+            const uint32_t idesc2 = tc::idesc_bf16_f32(kRows, 2 * NC);
             uint64_t da0[2][2], db0[2][2];
 #pragma unroll
             for (int par = 0; par < 2; ++par)
@@ -561,12 +567,22 @@ __global__ void __launch_bounds__(kWsThreads, kWsCtasPerSm) k_tc_ws(TcArgs a, co
                 }
                 tc::tc_fence_after();
                 const uint64_t so = sstep * (uint64_t)q;
+                if (wide) {
+                    // the blocked data holds B_lo right after B_hi: rows NC .. 2 NC - 1
 #pragma unroll
-                for (int par = 0; par < 2; ++par) {
-                    const uint32_t d = tmem + (uint32_t)(par * NC);
-                    tc::mma_bf16(d, da0[par][0] + so, db0[par][0] + so, idesc, u != 0);
-                    tc::mma_bf16(d, da0[par][0] + so, db0[par][1] + so, idesc, true);
-                    tc::mma_bf16(d, da0[par][1] + so, db0[par][0] + so, idesc, true);
+                    for (int par = 0; par < 2; ++par) {
+                        const uint32_t d = tmem + (uint32_t)(par * pcols);
+                        tc::mma_bf16(d, da0[par][0] + so, db0[par][0] + so, idesc2, u != 0);
+                        tc::mma_bf16(d, da0[par][1] + so, db0[par][0] + so, idesc, true);
+                    }
+                } else {
+#pragma unroll
+                    for (int par = 0; par < 2; ++par) {
+                        const uint32_t d = tmem + (uint32_t)(par * pcols);
+                        tc::mma_bf16(d, da0[par][0] + so, db0[par][0] + so, idesc, u != 0);
+                        tc::mma_bf16(d, da0[par][0] + so, db0[par][1] + so, idesc, true);
+                        tc::mma_bf16(d, da0[par][1] + so, db0[par][0] + so, idesc, true);
+                    }
                 }
                 tc::mma_commit(&bar_mma[q]);
             }
@@ -637,16 +653,25 @@ __global__ void __launch_bounds__(kWsThreads, kWsCtasPerSm) k_tc_ws(TcArgs a, co
         tc::tc_fence_after();
         const int row = tile * kRows + warp * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int cb = 0; cb < NC; cb += 32) {
-            float de[32], dd[32];
+        for (int cb = 0; cb < NC; cb += 16) {
+            float de[16], dd[16];
             if (nlive > 0) {
-                tc::tmem_ld32(lane_base + (uint32_t)cb, de);
-                tc::tmem_ld32(lane_base + (uint32_t)(NC + cb), dd);
+                tc::tmem_ld16(lane_base + (uint32_t)cb, de);
+                tc::tmem_ld16(lane_base + (uint32_t)(pcols + cb), dd);
+                if (wide) {
+                    float t[16];
+                    tc::tmem_ld16(lane_base + (uint32_t)(NC + cb), t);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) de[i] += t[i];
+                    tc::tmem_ld16(lane_base + (uint32_t)(pcols + NC + cb), t);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) dd[i] += t[i];
+                }
             } else {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) de[i] = dd[i] = 0.f;
+                for (int i = 0; i < 16; ++i) de[i] = dd[i] = 0.f;
             }
-            for (int q = 0; q < 32; q += 2) {
+            for (int q = 0; q < 16; q += 2) {
                 const int b = (cb + q) >> 1;
                 if (b >= a.batch) break;
                 if (SYNTH) {
