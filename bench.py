@@ -345,8 +345,9 @@ def round_trip_errors(sht, torch, dev, cdt):
 def accuracy_vs_n(torch, dev, sizes=(255, 511, 1023, 2047, 4095)):
     """The Sec. 3.5 error measures of one round trip of uniform [-1, 1] spectra
     against N (nlat = N + 1, nphi = 2 (N + 1)), for the FP64 path, the FP32
-    recurrence and (N <= 2047) the tensor-core path: the analogue of the
-    paper's error-versus-N study (its 1e-11 target is for N < 2048)."""
+    recurrence, (N <= 2047) the tensor-core path and (N <= 1023) the
+    FP64-accurate tensor-core path: the analogue of the paper's
+    error-versus-N study (its 1e-11 target is for N < 2048)."""
     import numpy as np
     from paper_1202_6522_gb300 import SHT, synthetic
     out = {}
@@ -354,10 +355,13 @@ def accuracy_vs_n(torch, dev, sizes=(255, 511, 1023, 2047, 4095)):
         Q = synthetic.spectrum(n, seed=0, uniform=True)
         row = {}
         for path, cdt, fp32_path in (("f64", torch.complex128, "f32"), ("f32", torch.complex64, "f32"),
-                                     ("tc", torch.complex64, "tc")):
+                                     ("tc", torch.complex64, "tc"), ("tc_f64", torch.complex128, "f32")):
             if path == "tc" and n > 2047:
                 continue
-            sht = SHT(n, n, n + 1, 2 * (n + 1), device=dev, fp32_path=fp32_path)
+            if path == "tc_f64" and n > 1023:
+                continue
+            sht = SHT(n, n, n + 1, 2 * (n + 1), device=dev, fp32_path=fp32_path,
+                      fp64_path="tc" if path == "tc_f64" else "f64")
             Qd = torch.from_numpy(Q).to(dev, cdt)
             R = sht.analys_(sht.synth_(Qd)).cpu().numpy().astype(np.complex128)
             d = np.abs(R - Qd.cpu().numpy().astype(np.complex128))
@@ -600,6 +604,21 @@ def run_ours(args):
         fp64 = {"round_trips_per_s": world * BATCH / (ms64 / 1e3), "ms_per_step": ms64,
                 "kernels_ms": {k: v[0] / v[1] for k, v in tab64.items()}}
 
+    # --- FP64-accurate tensor-core path (digit slices) on the same workload ---
+    fp64tc = None
+    if args.mode != "f64" and not args.no_uneven:
+        from paper_1202_6522_gb300 import SHT as _SHT
+        sht64 = _SHT(LMAX, LMAX, NLAT, NPHI, fp64_path="tc")
+        a64 = torch.from_numpy(a_np).to(dev, torch.complex128)
+        ms_t, tab_t = time_path(sht64, torch, a64, max(3, args.steps // 10), 2, stream, profile=True)
+        del a64
+        fp64tc = {"workload": WORKLOAD + ", FP64 data", "round_trips_per_s": world * BATCH / (ms_t / 1e3),
+                  "ms_per_step": ms_t, "kernels_ms": {k: v[0] / v[1] for k, v in tab_t.items()},
+                  "round_trip_error_sec35": round_trip_errors(sht64, torch, dev, torch.complex128)}
+        if fp64:
+            fp64tc["speedup_vs_fp64_plain"] = fp64tc["round_trips_per_s"] / fp64["round_trips_per_s"]
+        del sht64
+
     if rank != 0:
         return 0
     # dominant kernel and its roofline
@@ -700,6 +719,8 @@ def run_ours(args):
     if fp64:
         line["fp64_plain"] = fp64
         line["speedup_vs_fp64_plain"] = value / fp64["round_trips_per_s"]
+    if fp64tc:
+        line["fp64_tensor_core"] = fp64tc
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

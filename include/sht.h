@@ -86,7 +86,7 @@ enum {
     SHT_F32_AUTO = 3,  /* FP32 data: whichever of SHT_F32, SHT_TC_BF16X3 and SHT_TC_OTF
                         * sht_tune measured fastest for this batch size (SHT_F32 if
                         * untuned); vector transforms take SHT_F32. */
-    SHT_TC_OTF = 4     /* FP32 data; the same tensor-core contraction, but P_n^m is
+    SHT_TC_OTF = 4,    /* FP32 data; the same tensor-core contraction, but P_n^m is
                         * generated on the fly (the variant of Sec. 3.1 the paper
                         * favours) by CUDA-core warps inside the contraction kernel:
                         * the FP32 recurrence of Sec. 3.2, restarted every 32 degrees
@@ -97,6 +97,19 @@ enum {
                         * Scalar transforms and adjoints; vector calls run
                         * SHT_TC_BF16X3.  SHT_EUNSUPPORTED if a segment of the
                         * recurrence would leave the FP32 range (large lmax). */
+    SHT_TC_F64 = 5     /* FP64 data; the per-order Legendre contraction on the bf16
+                        * tensor cores to FP64 accuracy: P_n^m (per row) and the data
+                        * (per field) are scaled by powers of two and split into six
+                        * signed 7-bit digit slices; the tensor core sums the integer
+                        * products of each level exactly in FP32, and the epilogue
+                        * combines the levels in 64-bit integers (relative truncation
+                        * about 2^-42 of the row and field maxima).  FFTs in FP64.
+                        * Scalar transforms and adjoints, up to 16 fields per launch
+                        * (larger batches run in groups of 16).  Requires
+                        * lmax <= 1023 and nlat <= 1024 (so that every level's sum
+                        * stays below 2^24), else SHT_EUNSUPPORTED.  The digit panels
+                        * take about 6 (lmax+1)^3 bytes (6.4 GB at lmax = 1023) and
+                        * are built by the first call in this mode or by sht_reserve. */
 };
 
 /* Build a plan (Sec. 2.3 nodes/weights, Sec. 3.2 recurrence tables, FFT
@@ -171,7 +184,8 @@ SHT_API int sht_sync_status(sht_handle h, void *stream);
  * cudaMalloc/cudaFree is not acceptable.  The handle itself must have been
  * created beforehand (sht_create allocates the plan tables).
  *   - Modes SHT_F64 and SHT_F32 (SHT_F32_AUTO runs SHT_F32 here);
- *     SHT_TC_BF16X3 returns SHT_EUNSUPPORTED, its panels being allocated.
+ *     SHT_TC_BF16X3, SHT_TC_OTF and SHT_TC_F64 return SHT_EUNSUPPORTED, their
+ *     panels or seeds being allocated.
  *   - The fixed array holds SHT_STATIC_SCRATCH_BYTES (16 MiB) on every GPU that
  *     loads this library, until the process exits.  A call needs
  *     batch * (mmax+1) * ceil(nlat/2) * 4 * sizeof(element) bytes (N = 1023 in

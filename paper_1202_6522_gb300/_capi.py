@@ -25,6 +25,7 @@ SHT_F32 = 1
 SHT_TC_BF16X3 = 2
 SHT_F32_AUTO = 3
 SHT_TC_OTF = 4
+SHT_TC_F64 = 5
 
 _lib = None
 _lock = threading.Lock()

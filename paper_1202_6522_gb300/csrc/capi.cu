@@ -39,7 +39,8 @@ int check_handle(sht_handle h)
 
 int check_mode(int mode)
 {
-    if (mode != SHT_F64 && mode != SHT_F32 && mode != SHT_TC_BF16X3 && mode != SHT_F32_AUTO && mode != SHT_TC_OTF)
+    if (mode != SHT_F64 && mode != SHT_F32 && mode != SHT_TC_BF16X3 && mode != SHT_F32_AUTO && mode != SHT_TC_OTF &&
+        mode != SHT_TC_F64)
         return fail(SHT_EINVAL, "unknown mode");
     return SHT_OK;
 }
@@ -244,7 +245,66 @@ int ensure_otf(sht::Plan &p)
     return SHT_OK;
 }
 
-size_t elem_size(int mode) { return mode == SHT_F64 ? sizeof(double) : sizeof(float); }
+size_t elem_size(int mode) { return (mode == SHT_F64 || mode == SHT_TC_F64) ? sizeof(double) : sizeof(float); }
+
+// FP64-accurate tensor-core mode: digit-slice panels (about 6 (lmax+1)^3
+// bytes), row exponents and first nonzero chunks, built once per plan.
+int ensure_panels64(sht::Plan &p)
+{
+    if (p.p64_s) return SHT_OK;
+    if (p.lmax > 1023 || p.npairs > 512)
+        return fail(SHT_EUNSUPPORTED, "SHT_TC_F64 needs lmax <= 1023 and nlat <= 1024");
+    std::vector<unsigned long long> off_s, off_a, dchunk;
+    size_t bs = 0, ba = 0, nch = 0;
+    sht::tc64_panel_layout(p.lmax, p.mmax, p.npairs, off_s, off_a, bs, ba, dchunk, nch);
+    const size_t ob = off_s.size() * sizeof(unsigned long long);
+    int T_s = 0, T_a = 0;
+    sht::tc_tile_counts(p.lmax, p.npairs, T_s, T_a);
+    cudaError_t e = cudaMalloc(&p.p64_s, bs);
+    if (e == cudaSuccess) e = cudaMalloc(&p.p64_a, ba);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_off64_s, ob);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_off64_a, ob);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_dchunk64, ob);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_e64_s, sizeof(int) * (size_t)(p.mmax + 1) * p.npairs);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_e64_a, sizeof(int) * (size_t)p.nlm);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_c064_s, sizeof(int) * (size_t)(p.mmax + 1) * T_s);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_c064_a, sizeof(int) * (size_t)(p.mmax + 1) * T_a);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_fcol, sizeof(int) * (size_t)sht::tc64_max_batch());
+    if (e == cudaSuccess) e = cudaMemcpy(p.d_off64_s, off_s.data(), ob, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p.d_off64_a, off_a.data(), ob, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p.d_dchunk64, dchunk.data(), ob, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(p.p64_s, 0, bs);
+    if (e == cudaSuccess) e = cudaMemset(p.p64_a, 0, ba);
+    if (e == cudaSuccess)
+        e = sht::tc64_build(p.view64(), p.d_off64_s, p.d_off64_a, p.p64_s, p.p64_a, p.d_e64_s, p.d_e64_a, p.d_c064_s,
+                            p.d_c064_a, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p.p64_s); cudaFree(p.p64_a); cudaFree(p.d_off64_s); cudaFree(p.d_off64_a); cudaFree(p.d_dchunk64);
+        cudaFree(p.d_e64_s); cudaFree(p.d_e64_a); cudaFree(p.d_c064_s); cudaFree(p.d_c064_a); cudaFree(p.d_fcol);
+        p.p64_s = p.p64_a = nullptr;
+        p.d_off64_s = p.d_off64_a = p.d_dchunk64 = nullptr;
+        p.d_e64_s = p.d_e64_a = p.d_c064_s = p.d_c064_a = p.d_fcol = nullptr;
+        return fail(SHT_ENOMEM, std::string("building the digit-slice panels: ") + cudaGetErrorString(e));
+    }
+    p.nchunk64_s = nch;
+    return SHT_OK;
+}
+
+// Scratch of SHT_TC_F64: the FP64 intermediate of up to 16 fields, then the
+// blocked digit data.
+size_t tc64_data_offset(const sht::Plan &p, int batch)
+{
+    const int nb = batch > sht::tc64_max_batch() ? sht::tc64_max_batch() : batch;
+    return ((size_t)nb * (p.mmax + 1) * p.npairs * 4 * sizeof(double) + 255) & ~(size_t)255;
+}
+size_t tc64_work_bytes(const sht::Plan &p, int batch)
+{
+    return tc64_data_offset(p, batch) + sht::tc64_data_bytes(p.mmax, p.npairs, p.nchunk64_s);
+}
+
+int run_tc64(sht::Plan &p, bool synth, const void *in_, void *out_, int batch, sht::Op op, cudaStream_t s);
 
 // Tensor-core scalar transforms: the Legendre contraction on tcgen05, FFTs in FP32.
 int run_synth_tc(sht::Plan &p, const void *spec, void *grid, int batch, sht::Op op, cudaStream_t s);
@@ -437,6 +497,7 @@ int resolve_mode(const sht::Plan &p, int mode, int batch, bool vector)
     if (vector) {
         if (mode == SHT_F32_AUTO) return SHT_F32;
         if (mode == SHT_TC_OTF) return SHT_TC_BF16X3;   // vector transforms use the panels
+        if (mode == SHT_TC_F64) return SHT_F64;         // ... and the FP64 recurrence
         return mode;
     }
     if (mode != SHT_F32_AUTO) return mode;
@@ -460,6 +521,11 @@ int scalar_s2g(sht_handle h, const void *spec, void *grid, int batch, int mode, 
         if ((rc = ensure_work(h->p, tc_work_bytes(h->p, batch, false)))) return rc;
         return run_otf(h->p, true, spec, grid, batch, op, s);
     }
+    if (mode == SHT_TC_F64) {
+        if ((rc = ensure_panels64(h->p))) return rc;
+        if ((rc = ensure_work(h->p, tc64_work_bytes(h->p, batch)))) return rc;
+        return run_tc64(h->p, true, spec, grid, batch, op, s);
+    }
     if ((rc = ensure_work(h->p, inter_bytes(h->p, batch, mode)))) return rc;
     if (mode == SHT_F64) return run_synth<double>(h->p, h->p.view64(), spec, grid, batch, op, s);
     return run_synth<float>(h->p, h->p.view32(), spec, grid, batch, op, s);
@@ -481,6 +547,11 @@ int scalar_g2s(sht_handle h, const void *grid, void *spec, int batch, int mode, 
         if ((rc = ensure_otf(h->p))) return rc;
         if ((rc = ensure_work(h->p, tc_work_bytes(h->p, batch, false)))) return rc;
         return run_otf(h->p, false, grid, spec, batch, op, s);
+    }
+    if (mode == SHT_TC_F64) {
+        if ((rc = ensure_panels64(h->p))) return rc;
+        if ((rc = ensure_work(h->p, tc64_work_bytes(h->p, batch)))) return rc;
+        return run_tc64(h->p, false, grid, spec, batch, op, s);
     }
     if ((rc = ensure_work(h->p, inter_bytes(h->p, batch, mode)))) return rc;
     if (mode == SHT_F64) return run_analys<double>(h->p, h->p.view64(), grid, spec, batch, op, s);
@@ -562,6 +633,44 @@ int run_analys_tc(sht::Plan &p, const void *grid, void *spec, int batch, sht::Op
             return sht::launch_tc_legendre(false, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_a, p.d_off_a, p.d_c0_a,
                                            p.d_gf_a, p.d_dchunk, data, sd, out, nb, op, p.d_err, false, s);
         });
+        if (rc) return rc;
+    }
+    return SHT_OK;
+}
+
+// FP64-accurate tensor-core mode: synthesis = contraction then FP64 FFT;
+// analysis = FP64 FFT then contraction; groups of up to 16 fields.
+int run_tc64(sht::Plan &p, bool synth, const void *in_, void *out_, int batch, sht::Op op, cudaStream_t s)
+{
+    const int chunk = sht::tc64_max_batch();
+    double *inter = static_cast<double *>(p.work);
+    unsigned char *data = static_cast<unsigned char *>(p.work) + tc64_data_offset(p, batch);
+    const size_t spec_n = (size_t)p.nlm * 2, grid_n = (size_t)p.nlat * p.nphi;
+    for (int b0 = 0; b0 < batch; b0 += chunk) {
+        const int nb = batch - b0 < chunk ? batch - b0 : chunk;
+        int rc;
+        if (synth) {
+            const double *in = static_cast<const double *>(in_) + (size_t)b0 * spec_n;
+            double *out = static_cast<double *>(out_) + (size_t)b0 * grid_n;
+            rc = timed(p, SHT_K_TC_SYNTH, s, "FP64 tensor-core synthesis launch", [&] {
+                return sht::launch_tc64(true, p.lmax, p.mmax, p.npairs, p.nlm, p.p64_s, p.d_off64_s, p.d_c064_s,
+                                        p.d_e64_s, p.d_dchunk64, p.d_fcol, data, in, inter, nb, op, p.d_err, s);
+            });
+            if (rc) return rc;
+            rc = timed(p, SHT_K_FFT_SYNTH, s, "fft synthesis launch",
+                       [&] { return sht::launch_fft_synth<double>(p.view64(), inter, out, nb, op, s); });
+        } else {
+            const double *in = static_cast<const double *>(in_) + (size_t)b0 * grid_n;
+            double *out = static_cast<double *>(out_) + (size_t)b0 * spec_n;
+            rc = timed(p, SHT_K_FFT_ANALYS, s, "fft analysis launch",
+                       [&] { return sht::launch_fft_analys<double>(p.view64(), in, inter, nb, op, false, s); });
+            if (rc) return rc;
+            rc = timed(p, SHT_K_TC_ANALYS, s, "FP64 tensor-core analysis launch", [&] {
+                return sht::launch_tc64(false, p.lmax, p.mmax, p.npairs, p.nlm, p.p64_a, p.d_off64_a, p.d_c064_a,
+                                        p.d_e64_a, p.d_dchunk64, p.d_fcol, data, inter, out, nb, op,
+                                        p.d_err, s);
+            });
+        }
         if (rc) return rc;
     }
     return SHT_OK;
@@ -719,6 +828,10 @@ int sht_reserve(sht_handle h, int batch, int mode)
     if (mode == SHT_TC_OTF) {
         if ((rc = ensure_otf(h->p))) return rc;
         return ensure_work(h->p, tc_work_bytes(h->p, batch, false));
+    }
+    if (mode == SHT_TC_F64) {
+        if ((rc = ensure_panels64(h->p))) return rc;
+        return ensure_work(h->p, tc64_work_bytes(h->p, batch));
     }
     return ensure_work(h->p, 2 * inter_bytes(h->p, batch, mode));
 }
@@ -1055,8 +1168,9 @@ extern "C" int sht_synth_static(sht_handle h, const void *spec, void *grid, int 
     const void *ptrs[2] = {spec, grid};
     int rc = prologue(h, batch, mode, 2, ptrs);
     if (rc) return rc;
-    if (mode == SHT_TC_BF16X3)
-        return fail(SHT_EUNSUPPORTED, "sht_synth_static: the tensor-core mode needs panels allocated by the handle");
+    if (mode == SHT_TC_BF16X3 || mode == SHT_TC_OTF || mode == SHT_TC_F64)
+        return fail(SHT_EUNSUPPORTED, "sht_synth_static: the tensor-core modes need tables allocated by the handle");
+    if (mode == SHT_F32_AUTO) mode = SHT_F32;
     const size_t need = inter_bytes(h->p, batch, mode);
     if (need > (size_t)SHT_STATIC_SCRATCH_BYTES)
         return fail(SHT_EINVAL, "sht_synth_static: this call needs " + std::to_string(need) +

@@ -280,6 +280,12 @@ void plan_free(Plan &p)
     if (p.d_dchunk) cudaFree(p.d_dchunk);
     if (p.d_c0_s) cudaFree(p.d_c0_s);
     if (p.d_c0_a) cudaFree(p.d_c0_a);
+    cudaFree(p.p64_s); cudaFree(p.p64_a); cudaFree(p.d_off64_s); cudaFree(p.d_off64_a); cudaFree(p.d_dchunk64);
+    p.d_dchunk64 = nullptr;
+    cudaFree(p.d_e64_s); cudaFree(p.d_e64_a); cudaFree(p.d_c064_s); cudaFree(p.d_c064_a); cudaFree(p.d_fcol);
+    p.p64_s = p.p64_a = nullptr;
+    p.d_off64_s = p.d_off64_a = nullptr;
+    p.d_e64_s = p.d_e64_a = p.d_c064_s = p.d_c064_a = p.d_fcol = nullptr;
     if (p.d_gf_s) cudaFree(p.d_gf_s);
     if (p.d_gf_a) cudaFree(p.d_gf_a);
     p.d_gf_s = p.d_gf_a = nullptr;

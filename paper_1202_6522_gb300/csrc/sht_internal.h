@@ -97,6 +97,12 @@ struct Plan {
     float polar_thr = 0x1p-40f;                 // polar threshold (sht_set_polar_threshold)
     unsigned char *dpanel_s = nullptr, *dpanel_a = nullptr; // sin(theta) dP/dtheta panels (vector)
     int *d_c0v_s = nullptr, *d_c0v_a = nullptr; // first chunk live in P or dP
+    unsigned char *p64_s = nullptr, *p64_a = nullptr;     // SHT_TC_F64: digit-slice panels
+    unsigned long long *d_off64_s = nullptr, *d_off64_a = nullptr, *d_dchunk64 = nullptr;
+    size_t nchunk64_s = 0;                                // ... synthesis data chunks over all orders
+    int *d_e64_s = nullptr, *d_e64_a = nullptr;           // ... row exponents
+    int *d_c064_s = nullptr, *d_c064_a = nullptr;         // ... first nonzero chunk per (m, tile)
+    int *d_fcol = nullptr;                                // ... field exponents of a launch
     float4 *otf_seeds = nullptr;                // on-the-fly mode: recurrence seeds
     unsigned long long *d_segoff = nullptr;     // first segment of each order
     int *d_c0o_s = nullptr, *d_c0o_a = nullptr; // on-the-fly mode: first live chunk per (m, tile)
@@ -219,6 +225,23 @@ cudaError_t tc_polar_stats(int lmax, int mmax, int npairs, const int *d_c0_s, co
                            double &frac_a, const unsigned short *d_gf_s = nullptr,
                            const unsigned short *d_gf_a = nullptr);
 int tc_max_batch();
+// FP64-accurate contraction (tc64.cu): digit-slice panels and row exponents,
+// built once; per launch the field exponents, the data digits and the
+// contraction.  Synthesis: FP64 spectra -> E/O (double4 [b][m][pair]);
+// analysis: FP64 s/d folds -> spectra.
+int tc64_max_batch();
+// Byte offsets of each order's digit-slice panel chunks (synthesis, analysis),
+// total bytes, and the first synthesis data chunk of each order.
+void tc64_panel_layout(int lmax, int mmax, int npairs, std::vector<unsigned long long> &off_s,
+                       std::vector<unsigned long long> &off_a, size_t &bytes_s, size_t &bytes_a,
+                       std::vector<unsigned long long> &dchunk, size_t &nchunk_s);
+size_t tc64_data_bytes(int mmax, int npairs, size_t nchunk_s);
+cudaError_t tc64_build(const PlanView<double> &pv, const unsigned long long *off_s, const unsigned long long *off_a,
+                       unsigned char *ps, unsigned char *pa, int *es, int *ea, int *c0_s, int *c0_a, cudaStream_t st);
+cudaError_t launch_tc64(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
+                        const unsigned long long *off, const int *c0, const int *erow,
+                        const unsigned long long *dchunk, int *fcol, unsigned char *data, const double *in,
+                        double *out, int batch, Op op, int *err, cudaStream_t st);
 cudaError_t launch_selftest_timeout(int *err, unsigned long long max_ns, cudaStream_t st);
 
 // On-the-fly mode (tc.cu): FP32 recurrence reseeded every 32 degrees.

@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "sht_internal.h"
+#include "tc_common.cuh"
 #include "tc_layout.cuh"
 #include "tc_ptx.cuh"
 
@@ -55,39 +56,16 @@ __host__ __device__ __forceinline__ uint32_t pan_off(int kb, int row, int k)
 {
     return (uint32_t)((row >> 3) * kPSbo + kb * kSbo + (k >> 3) * kLbo + (row & 7) * 16 + (k & 7) * 2);
 }
-constexpr uint64_t kWaitNs = 2000000000ull; // 2 s
+using tcc::kWaitNs;
+using tcc::col_of;
+using tcc::raise_err;
+using tcc::wait_or_abort;
 
 __device__ __forceinline__ void split_bf16_d(double v, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
 {
     hi = __float2bfloat16_rn((float)v);
     lo = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hi)));
 }
-
-__host__ __device__ __forceinline__ long col_of(int lmax, int m) { return (long)m * (2 * lmax + 3 - m) / 2; }
-
-__device__ __forceinline__ void raise_err(int *err, int code)
-{
-    if (err) atomicCAS(err, 0, code);
-}
-
-// Bounded wait that also gives up when another thread of the CTA gave up.
-__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort)
-{
-    const uint64_t t0 = tc::globaltimer();
-    for (uint32_t it = 0; it < (1u << 26); ++it) {
-        if (tc::mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 255u) {
-            if (*abort) return false;
-            if (tc::globaltimer() - t0 > kWaitNs) {
-                *abort = 1;
-                return false;
-            }
-        }
-    }
-    *abort = 1;
-    return false;
-}
-
 
 // ---------------------------------------------------------------------------
 // Panel builder: one thread per (m, pair), FP64 recurrence with rescaling.

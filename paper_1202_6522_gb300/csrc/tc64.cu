@@ -1,0 +1,613 @@
+// tc64.cu -- the per-order Legendre contraction to FP64 accuracy on the bf16
+// tensor cores (mode SHT_TC_F64): the same GEMMs as tc.cu (Sec. 3.1, Eq.
+// synth_direct and Eq. gauss per order m and parity of n - m), with both
+// operands split into fixed-point digit slices whose products the tensor
+// core adds exactly.
+//
+// Splitting (an Ozaki-style scheme).  A row of P (a latitude pair for
+// synthesis, a degree for analysis) is scaled by 2^-e with 2^e above its
+// largest |P|, and a data column (one field) by 2^-f likewise; then
+//     P 2^(6 - e) = sum_i d_i 2^(-7 i),   a 2^(6 - f) = sum_j c_j 2^(-7 j),
+// i < kSA = 7 panel digits, j < kSB = 8 data digits, all signed with
+// |d_i|, |c_j| <= 64 (exact in bf16): 49 bits of P relative to its row
+// maximum and 56 of the data relative to the field maximum, so that the
+// small coefficients of a decaying spectrum keep FP64-level absolute error.
+// The digits of level t = i + j all carry the scale 2^(e + f - 12 - 7 t), so
+//     sum_n P a = 2^(e + f - 12) sum_t 2^(-7 t) L_t,  L_t = sum_{i+j=t} sum_n d_i c_j,
+// and the tensor core forms each L_t as a sum of integer products: at most
+// kSA x 512 products of magnitude <= 2^12, below 2^24, so the FP32
+// accumulation in tensor memory is exact.  Levels t < kL = 8 are kept (the
+// dropped ones are below 2^-56 of the leading level); the epilogue combines
+// them in 64-bit integers and scales in FP64.
+//
+// For A slice i, one MMA multiplies it by the data slices j = 0 .. kL-1-i,
+// stacked along N, whose products land on levels i .. kL-1: the accumulator
+// columns of the levels are contiguous, so the MMA's D starts at level i.
+// That is kSA MMAs per parity and chunk (N = 32 (kL - i)), 14 per chunk.
+// The accumulators are zeroed once and every MMA accumulates.
+//
+// CTA: one (order m, 128-row tile), 192 threads: warps 0-3 run the epilogue,
+// warp 4 lane 0 issues the MMAs, warp 5 lane 0 streams 56 KB panel chunks and
+// 16 KB data chunks by bulk copy into 3 stages.  Tensor memory: 2 parities x
+// kL levels x 32 columns (16 fields x re/im) = all 512 columns of the SM, so
+// one CTA per SM.  Every wait is bounded.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <vector>
+
+#include "sht_internal.h"
+#include "tc_common.cuh"
+#include "tc_layout.cuh"
+#include "tc_ptx.cuh"
+
+namespace sht {
+namespace {
+
+using tcc::col_of;
+using tcc::raise_err;
+using tcc::wait_or_abort;
+
+constexpr int kR = 128;                        // MMA M
+constexpr int kSA = 7;                         // digit slices of P
+constexpr int kSB = 8;                         // digit slices of the data
+constexpr int kNC = 32;                        // data rows per slice: 16 fields x (re, im)
+constexpr int kBatch64 = kNC / 2;              // fields per launch
+constexpr int kPBlk = kR * kKc * 2;            // one slice of one parity: [128 x 16] bf16 = 4 KB
+constexpr int kPChunk = 2 * kSA * kPBlk;       // panel chunk: [slice][parity] blocks = 56 KB
+constexpr int kDRows = kSB * kNC;              // data rows per class: slices stacked along N
+constexpr int kDBlk = kDRows * kKc * 2;        // 6 KB
+constexpr int kDChunk = 2 * kDBlk;             // data chunk: [class] blocks = 12 KB
+constexpr int kStage = kPChunk + kDChunk;      // 60 KB
+constexpr int kStages = 3;
+constexpr int kThreads = 192;
+constexpr int kL = kSB;                        // accumulated levels t = i + j < kL
+constexpr int kLevelCols = kNC;                // accumulator columns per level
+constexpr int kParCols = kL * kLevelCols;      // per parity: 224
+constexpr uint32_t kTmemCols = 512;
+constexpr int kExpNone = INT_MIN / 2;          // exponent of an all-zero row or column
+
+// Panel slice block of (slice i, parity par) in a chunk.
+__host__ __device__ __forceinline__ uint32_t pblk(int i, int par) { return (uint32_t)((2 * i + par) * kPBlk); }
+
+// Exponent e with |v| < 2^e for every |v| <= max (frexp convention).
+__device__ __forceinline__ int exp_above(double max_abs)
+{
+    int e;
+    (void)frexp(max_abs, &e);
+    return e;
+}
+
+// Digits of a panel value (FP64 arithmetic; the panels are built once):
+// v 2^(6 - e) = sum_i d[i] 2^(-7 i), rounding each digit to nearest.
+__device__ __forceinline__ void digits_fp64(double v, int e, int (&d)[kSA])
+{
+    double X = ldexp(v, 6 - e);
+#pragma unroll
+    for (int i = 0; i < kSA; ++i) {
+        const double r = rint(X);
+        d[i] = (int)r;
+        X = (X - r) * 128.0;
+    }
+}
+
+// Digits of a data value with integer operations only (no FP64 pipe):
+// Y = round(v 2^(55 - e)) from the bit pattern (|Y| < 2^55), then signed
+// base-2^7 digits from the top, Y = sum_i d[i] 2^(7 (kSB - 1 - i)).
+// Requires |v| < 2^e.
+__device__ __forceinline__ void digits_int(double v, int e, int (&d)[kSB])
+{
+    const long long bits = __double_as_longlong(v);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    long long Y = 0;
+    if (ex != 0 && e != kExpNone) {
+        const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+        const int sh = ex - 1075 + 7 * (kSB - 1) + 6 - e;   // |v| 2^(55 - e) = mant 2^sh, sh <= 2
+        if (sh >= 0) Y = mant << sh;
+        else if (sh > -63) Y = (mant + (1LL << (-sh - 1))) >> (-sh);
+        if (bits < 0) Y = -Y;
+    }
+#pragma unroll
+    for (int i = 0; i < kSB - 1; ++i) {
+        const int s = 7 * (kSB - 1 - i);
+        const long long q = (Y + (1LL << (s - 1))) >> s;
+        d[i] = (int)q;
+        Y -= q << s;
+    }
+    d[kSB - 1] = (int)Y;
+}
+
+// The Sec. 3.2 recurrence for (m, pair p) as in the panel builder of tc.cu,
+// calling f(nn, P) for every degree n = m + nn with P != 0 (k = 0 region).
+template <typename F>
+__device__ __forceinline__ void recur_pair(const PlanView<double> &pv, int m, int p, F &&f)
+{
+    const int npairs = pv.npairs, lmax = pv.lmax;
+    const int L = lmax - m + 1;
+    const long col = col_of(lmax, m);
+    const double x = pv.x[p];
+    double y2 = pv.pmm[(size_t)m * npairs + p], y1 = 0.0;
+    int k = pv.pmmk[(size_t)m * npairs + p];
+    for (int nn = 0; nn < L; ++nn) {
+        const double2 ab = pv.ab[col + nn];
+        const double yn = fma(ab.x * x, y1, ab.y * y2);
+        y2 = y1;
+        y1 = yn;
+        if (k > 0 && fabs(yn) >= 1.0) {
+            y1 *= 0x1p-240;
+            y2 *= 0x1p-240;
+            k -= 1;
+        }
+        if (k != 0 || y1 == 0.0) continue;
+        f(nn, y1);
+    }
+}
+
+// Row exponents: es[m][p] over the degrees of (m, p) (synthesis rows), and
+// ea[col(m) + nn] over the pairs (analysis rows; initialised to kExpNone).
+__global__ void k_p64_scales(PlanView<double> pv, int *__restrict__ es, int *__restrict__ ea)
+{
+    const int m = blockIdx.y, p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= pv.npairs) return;
+    const long col = col_of(pv.lmax, m);
+    double mx = 0.0;
+    recur_pair(pv, m, p, [&](int nn, double P) {
+        mx = fmax(mx, fabs(P));
+        atomicMax(&ea[col + nn], exp_above(fabs(P)));
+    });
+    es[(size_t)m * pv.npairs + p] = mx > 0.0 ? exp_above(mx) : kExpNone;
+}
+
+// Digit-slice panels, in the operand layout of the contraction.  Synthesis
+// chunk (m, tile t, c): rows = pairs of the tile, K = the kKc degree indices
+// kk = (n - m) / 2 of chunk c, one block per (slice, parity of n - m).
+// Analysis chunk (m, degree tile mt, pair chunk kc): rows = kk, K = pairs.
+__global__ void k_p64_build(PlanView<double> pv, const int *__restrict__ es, const int *__restrict__ ea,
+                            const unsigned long long *__restrict__ off_s, const unsigned long long *__restrict__ off_a,
+                            unsigned char *__restrict__ ps, unsigned char *__restrict__ pa)
+{
+    const int m = blockIdx.y, p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int npairs = pv.npairs;
+    if (p >= npairs) return;
+    const int L = pv.lmax - m + 1, Le = (L + 1) / 2;
+    const int nch = (Le + kKc - 1) / kKc, kch = (npairs + kKc - 1) / kKc;
+    const long col = col_of(pv.lmax, m);
+    const int t = p / kR, row = p % kR, kc = p / kKc, pc = p % kKc;
+    const int e_row = es[(size_t)m * npairs + p];
+    unsigned char *sbase = ps + off_s[m] + (size_t)t * nch * kPChunk;
+    unsigned char *abase = pa + off_a[m];
+    recur_pair(pv, m, p, [&](int nn, double P) {
+        const int par = nn & 1, kk = nn >> 1;
+        int d[kSA];
+        digits_fp64(P, e_row, d);
+        unsigned char *b = sbase + (size_t)(kk / kKc) * kPChunk;
+        const uint32_t o = blk_off(row, kk % kKc);
+#pragma unroll
+        for (int i = 0; i < kSA; ++i)
+            *reinterpret_cast<__nv_bfloat16 *>(b + pblk(i, par) + o) = __int2bfloat16_rn(d[i]);
+        digits_fp64(P, ea[col + nn], d);
+        const int mt = kk / kR, r = kk % kR;
+        unsigned char *ba = abase + ((size_t)mt * kch + kc) * kPChunk;
+        const uint32_t oa = blk_off(r, pc);
+#pragma unroll
+        for (int i = 0; i < kSA; ++i)
+            *reinterpret_cast<__nv_bfloat16 *>(ba + pblk(i, par) + oa) = __int2bfloat16_rn(d[i]);
+    });
+}
+
+// First chunk of each (m, tile) holding a nonzero digit (all-zero chunks,
+// high orders near the poles, add nothing: the polar optimisation of
+// Sec. 3.1 without a threshold).
+__global__ void k_p64_first_live(int synth, int lmax, int npairs, int ntiles, const unsigned long long *__restrict__ off,
+                                 const unsigned char *__restrict__ panel, int *__restrict__ c0)
+{
+    const int m = blockIdx.y, tile = blockIdx.x;
+    const int L = lmax - m + 1, Le = (L + 1) / 2;
+    const int nchunks = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
+    const bool valid = synth || tile * kR < Le;
+    __shared__ int s_live;
+    int first = nchunks;
+    if (valid) {
+        const uint4 *base =
+            reinterpret_cast<const uint4 *>(panel + off[m] + (size_t)tile * nchunks * kPChunk);
+        for (int c = 0; c < nchunks; ++c) {
+            if (threadIdx.x == 0) s_live = 0;
+            __syncthreads();
+            bool live = false;
+            for (int i = threadIdx.x; i < kPChunk / 16; i += blockDim.x) {
+                const uint4 v = base[(size_t)c * (kPChunk / 16) + i];
+                live |= (v.x | v.y | v.z | v.w) != 0u;
+            }
+            if (live) s_live = 1;
+            __syncthreads();
+            const int any = s_live;
+            __syncthreads();
+            if (any) { first = c; break; }
+        }
+    }
+    if (threadIdx.x == 0) c0[m * ntiles + tile] = first;
+}
+
+// Column exponents: f[b] with |x| < 2^f[b] for every value of field b
+// (initialised to kExpNone by the caller).
+__global__ void k_colscale(const double *__restrict__ x, size_t per_field, int *__restrict__ f)
+{
+    const int b = blockIdx.y;
+    const double *xb = x + (size_t)b * per_field;
+    double mx = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_field; i += (size_t)gridDim.x * blockDim.x)
+        mx = fmax(mx, fabs(xb[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(&f[b], exp_above(mx));
+}
+
+__global__ void k_fill_int(int *__restrict__ a, int v, size_t n)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+
+// Data digits in the blocked operand layout: chunk [class][kDRows x kKc],
+// row = 32 slice + 2 field + (re|im).  Synthesis chunk (m, c) = degrees
+// n - m in [2 kKc c, 2 kKc (c + 1)), class = parity of n - m, numbered from
+// dchunk[m]; analysis chunk (m, kc) = pairs [kKc kc, kKc (kc + 1)), class
+// 0 = s fold, 1 = d fold, numbered m kch + kc.  One thread per (field,
+// degree or pair) of a chunk.
+__global__ void k_prep64(int synth, int lmax, int mmax, int npairs, int nlm, int batch, int op,
+                         const double *__restrict__ in, const int *__restrict__ f,
+                         const unsigned long long *__restrict__ dchunk, unsigned char *__restrict__ data)
+{
+    const int m = blockIdx.y;
+    const int L = lmax - m + 1, Le = (L + 1) / 2;
+    const int per = synth ? 2 * kKc : kKc;                    // degrees or pairs per chunk
+    const int nchunks = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
+    const long item = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= (long)nchunks * batch * per) return;
+    const int c = (int)(item / (batch * per));
+    const int r = (int)(item - (long)c * batch * per);
+    const int b = r / per, j = r - b * per;
+    const int e = f[b];
+    int dv[2][kSB];
+    unsigned char *chunk;
+    if (synth) {
+        const long col = col_of(lmax, m);
+        const int nn = 2 * kKc * c + j;
+        double re = 0.0, im = 0.0;
+        if (nn < L) {
+            const double2 v = reinterpret_cast<const double2 *>(in)[(size_t)b * nlm + col + nn];
+            const double cadj = (op == OP_ANALYS_ADJ && m > 0) ? 0.5 : 1.0;
+            re = v.x * cadj;
+            im = m == 0 ? 0.0 : v.y * cadj;
+        }
+        digits_int(re, e, dv[0]);
+        digits_int(im, e, dv[1]);
+        chunk = data + (size_t)(dchunk[m] + c) * kDChunk + (size_t)(j & 1) * kDBlk;
+        const int k = j >> 1;
+#pragma unroll
+        for (int s = 0; s < kSB; ++s)
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                *reinterpret_cast<__nv_bfloat16 *>(chunk + blk_off(kNC * s + 2 * b + q, k)) = __int2bfloat16_rn(dv[q][s]);
+    } else {
+        const int p = kKc * c + j;
+        double4 v = make_double4(0.0, 0.0, 0.0, 0.0);
+        if (p < npairs) v = reinterpret_cast<const double4 *>(in)[((size_t)b * (mmax + 1) + m) * npairs + p];
+        const double vv[4] = {v.x, v.y, v.z, v.w};   // s.re s.im d.re d.im
+        unsigned char *base = data + ((size_t)m * nchunks + c) * kDChunk;
+#pragma unroll
+        for (int cls = 0; cls < 2; ++cls) {
+            digits_int(vv[2 * cls], e, dv[0]);
+            digits_int(vv[2 * cls + 1], e, dv[1]);
+            chunk = base + (size_t)cls * kDBlk;
+#pragma unroll
+            for (int s = 0; s < kSB; ++s)
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                    *reinterpret_cast<__nv_bfloat16 *>(chunk + blk_off(kNC * s + 2 * b + q, j)) =
+                        __int2bfloat16_rn(dv[q][s]);
+        }
+    }
+}
+
+struct Tc64Args {
+    int lmax, mmax, npairs, nlm, batch, ntiles, op;
+    const unsigned char *panel;
+    const unsigned long long *off;         // per-order panel byte offsets
+    const int *c0;                         // per (m, tile): first chunk with a nonzero digit
+    const int *erow;                       // row exponents (synthesis [m][pair], analysis packed [nlm])
+    const int *fcol;                       // field exponents
+    const unsigned char *data;             // blocked data digits
+    const unsigned long long *dchunk;      // synthesis: first data chunk of each order
+    double *out;                           // synthesis: E/O [b][m][pair] (double4); analysis: spectra
+    int *err;
+};
+
+template <bool SYNTH>
+__global__ void __launch_bounds__(kThreads, 1) k_tc64(Tc64Args a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    uint64_t *bar_load = reinterpret_cast<uint64_t *>(smem + (size_t)kStages * kStage);
+    uint64_t *bar_mma = bar_load + kStages;
+    uint64_t *bar_done = bar_mma + kStages;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_done + 1);
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    const int m = blockIdx.x / a.ntiles;
+    const int tile = blockIdx.x - m * a.ntiles;
+    const int lmax = a.lmax, npairs = a.npairs;
+    const int L = lmax - m + 1, Le = (L + 1) / 2;
+    const long col = col_of(lmax, m);
+    if (!SYNTH && tile * kR >= Le) return;
+    const int nchunks = SYNTH ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
+    const unsigned char *panel = a.panel + a.off[m] + (size_t)tile * nchunks * kPChunk;
+    const unsigned char *data =
+        a.data + (SYNTH ? a.dchunk[m] : (unsigned long long)m * nchunks) * (unsigned long long)kDChunk;
+    const int cstart = a.c0[m * a.ntiles + tile];
+    const int nlive = nchunks - cstart;
+
+    if (tid == 0) {
+        for (int q = 0; q < kStages; ++q) {
+            tc::mbar_init(&bar_load[q], 1);
+            tc::mbar_init(&bar_mma[q], 1);
+        }
+        tc::mbar_init(bar_done, 1);
+        tc::mbar_fence_init();
+        s_abort = 0;
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+    if (warp < 4) {
+        // zero this warp's lanes of every accumulator column; the MMAs all accumulate
+        const uint32_t zero8[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        for (int c = 0; c < 2 * kParCols; c += 8)
+            tc::tmem_st8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, zero8);
+        tc::tmem_wait_st();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            uint64_t da[kSA][2], db[2];
+            uint32_t idesc[kSA];
+#pragma unroll
+            for (int i = 0; i < kSA; ++i) {
+                idesc[i] = tc::idesc_bf16_f32(kR, (kL - i) * kNC);
+#pragma unroll
+                for (int par = 0; par < 2; ++par) da[i][par] = tc::smem_desc(smem + pblk(i, par), kLbo, kSbo);
+            }
+#pragma unroll
+            for (int par = 0; par < 2; ++par) db[par] = tc::smem_desc(smem + kPChunk + (size_t)par * kDBlk, kLbo, kSbo);
+            const uint64_t sstep = (uint64_t)kStage >> 4;
+            bool ok = true;
+            for (int u = 0; u < nlive; ++u) {
+                const int q = u % kStages;
+                if (!wait_or_abort(&bar_load[q], (uint32_t)((u / kStages) & 1), &s_abort)) { ok = false; break; }
+                tc::tc_fence_after();
+                const uint64_t so = sstep * (uint64_t)q;
+#pragma unroll
+                for (int par = 0; par < 2; ++par)
+#pragma unroll
+                    for (int i = 0; i < kSA; ++i)
+                        tc::mma_bf16(tmem + (uint32_t)(par * kParCols + i * kLevelCols), da[i][par] + so, db[par] + so,
+                                     idesc[i], true);
+                tc::mma_commit(&bar_mma[q]);
+            }
+            if (!ok) raise_err(a.err, SHT_ETIMEOUT);
+            tc::mma_commit(bar_done);
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // ---------------- producer ----------------
+            bool ok = true;
+            int issued = 0;
+            for (int u = 0; u < nlive; ++u) {
+                const int q = u % kStages;
+                const int c = cstart + u;
+                if (u >= kStages && !wait_or_abort(&bar_mma[q], (uint32_t)((u / kStages - 1) & 1), &s_abort)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char *st = smem + (size_t)q * kStage;
+                tc::mbar_arrive_expect_tx(&bar_load[q], (uint32_t)kStage);
+                tc::bulk_g2s(st, panel + (size_t)c * kPChunk, (uint32_t)kPChunk, &bar_load[q]);
+                tc::bulk_g2s(st + kPChunk, data + (size_t)c * kDChunk, (uint32_t)kDChunk, &bar_load[q]);
+                issued = u + 1;
+            }
+            if (!ok) {
+                raise_err(a.err, SHT_ETIMEOUT);
+                for (int v = issued > kStages ? issued - kStages : 0; v < issued; ++v)
+                    (void)tc::mbar_wait_bounded(&bar_load[v % kStages], (uint32_t)((v / kStages) & 1), 100000000ull);
+            }
+        }
+    }
+    bool ok = true;
+    if (warp < 4) {
+        ok = wait_or_abort(bar_done, 0, &s_abort);
+        if (!ok) {
+            (void)tc::mbar_wait_bounded(bar_done, 0, 100000000ull);
+            raise_err(a.err, SHT_ETIMEOUT);
+        }
+    }
+    ok = __syncthreads_and(ok && !*(volatile int *)&s_abort);
+    if (ok && warp < 4) {
+        // ---------------- epilogue ----------------
+        tc::tc_fence_after();
+        const int row = tile * kR + warp * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        const double sc = (!SYNTH && a.op == OP_SYNTH_ADJ && m > 0) ? 2.0 : 1.0;
+#pragma unroll 1
+        for (int par = 0; par < 2; ++par) {
+            // row exponent: synthesis per (m, pair), analysis per (m, n)
+            const int nn = 2 * row + par;
+            int e_row = kExpNone;
+            if (SYNTH) {
+                if (row < npairs) e_row = a.erow[(size_t)m * npairs + row];
+            } else {
+                if (nn < L) e_row = a.erow[col + nn];
+            }
+#pragma unroll 1
+            for (int h = 0; h < kNC / 16; ++h) {
+                // Z = sum_t L_t 2^(7 (kL - 1 - t)) = Zh 2^28 + Zl, levels split so that
+                // both parts stay exact in 64-bit integers and in doubles (< 2^48)
+                long long Zh[16], Zl[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) Zh[k] = Zl[k] = 0;
+                if (nlive > 0) {
+#pragma unroll
+                    for (int t = 0; t < kL; ++t) {
+                        float v[16];
+                        tc::tmem_ld16(lane_base + (uint32_t)(par * kParCols + t * kLevelCols + 16 * h), v);
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) {
+                            const long long L = __float2ll_rn(v[k]);
+                            if (t < kL / 2) Zh[k] += L << (7 * (kL / 2 - 1 - t));
+                            else Zl[k] += L << (7 * (kL - 1 - t));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 16; k += 2) {
+                    const int b = (16 * h + k) >> 1;
+                    if (b >= a.batch) break;
+                    // sum = 2^(e + f - 12 - 7 (kL - 1)) Z; zero for a row whose P are all
+                    // zero (or outside the order) and for an all-zero field
+                    const bool zero = e_row == kExpNone || a.fcol[b] == kExpNone;
+                    const int sh = zero ? 0 : e_row + a.fcol[b] - 12 - 7 * (kL - 1);
+                    const double re =
+                        zero ? 0.0 : sc * (ldexp((double)Zh[k], sh + 7 * (kL / 2)) + ldexp((double)Zl[k], sh));
+                    double im =
+                        zero ? 0.0 : sc * (ldexp((double)Zh[k + 1], sh + 7 * (kL / 2)) + ldexp((double)Zl[k + 1], sh));
+                    if (SYNTH) {
+                        if (row < npairs) {
+                            double2 *eo = reinterpret_cast<double2 *>(a.out);
+                            eo[(((size_t)b * (a.mmax + 1) + m) * npairs + row) * 2 + par] = make_double2(re, im);
+                        }
+                    } else {
+                        if (m == 0) im = 0.0;
+                        if (nn < L) reinterpret_cast<double2 *>(a.out)[(size_t)b * a.nlm + col + nn] = make_double2(re, im);
+                    }
+                }
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+}  // namespace
+
+int tc64_max_batch() { return kBatch64; }
+
+void tc64_panel_layout(int lmax, int mmax, int npairs, std::vector<unsigned long long> &off_s,
+                       std::vector<unsigned long long> &off_a, size_t &bytes_s, size_t &bytes_a,
+                       std::vector<unsigned long long> &dchunk, size_t &nchunk_s)
+{
+    off_s.assign(mmax + 1, 0);
+    off_a.assign(mmax + 1, 0);
+    dchunk.assign(mmax + 1, 0);
+    const int T = (npairs + kR - 1) / kR;
+    const int kch = (npairs + kKc - 1) / kKc;
+    unsigned long long s = 0, q = 0, ch = 0;
+    for (int m = 0; m <= mmax; ++m) {
+        const int L = lmax - m + 1, Le = (L + 1) / 2;
+        const int nch = (Le + kKc - 1) / kKc;
+        const int Mt = (Le + kR - 1) / kR;
+        off_s[m] = s;
+        off_a[m] = q;
+        dchunk[m] = ch;
+        s += (unsigned long long)T * nch * kPChunk;
+        q += (unsigned long long)Mt * kch * kPChunk;
+        ch += (unsigned long long)nch;
+    }
+    bytes_s = s;
+    bytes_a = q;
+    nchunk_s = (size_t)ch;
+}
+
+size_t tc64_data_bytes(int mmax, int npairs, size_t nchunk_s)
+{
+    const size_t kch = (size_t)(npairs + kKc - 1) / kKc;
+    const size_t an = (size_t)(mmax + 1) * kch;
+    return (nchunk_s > an ? nchunk_s : an) * kDChunk;
+}
+
+cudaError_t tc64_build(const PlanView<double> &pv, const unsigned long long *off_s, const unsigned long long *off_a,
+                       unsigned char *ps, unsigned char *pa, int *es, int *ea, int *c0_s, int *c0_a, cudaStream_t st)
+{
+    const int nlm = pv.nlm;
+    k_fill_int<<<(unsigned)((nlm + 255) / 256), 256, 0, st>>>(ea, kExpNone, (size_t)nlm);
+    dim3 g((unsigned)((pv.npairs + 127) / 128), (unsigned)(pv.mmax + 1));
+    k_p64_scales<<<g, 128, 0, st>>>(pv, es, ea);
+    k_p64_build<<<g, 128, 0, st>>>(pv, es, ea, off_s, off_a, ps, pa);
+    int ts, ta;
+    tc_tile_counts(pv.lmax, pv.npairs, ts, ta);
+    k_p64_first_live<<<dim3((unsigned)ts, (unsigned)(pv.mmax + 1)), 256, 0, st>>>(1, pv.lmax, pv.npairs, ts, off_s,
+                                                                                 ps, c0_s);
+    k_p64_first_live<<<dim3((unsigned)ta, (unsigned)(pv.mmax + 1)), 256, 0, st>>>(0, pv.lmax, pv.npairs, ta, off_a,
+                                                                                 pa, c0_a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc64(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
+                        const unsigned long long *off, const int *c0, const int *erow,
+                        const unsigned long long *dchunk, int *fcol, unsigned char *data, const double *in,
+                        double *out, int batch, Op op, int *err, cudaStream_t st)
+{
+    if (batch < 1 || batch > kBatch64) return cudaErrorInvalidValue;
+    // field exponents of the data
+    k_fill_int<<<1, 32, 0, st>>>(fcol, kExpNone, (size_t)batch);
+    const size_t per_field = synth ? (size_t)2 * nlm : (size_t)(mmax + 1) * npairs * 4;
+    k_colscale<<<dim3(64, (unsigned)batch), 256, 0, st>>>(in, per_field, fcol);
+    // data digits
+    const int Le0 = (lmax + 2) / 2;
+    const int maxch = synth ? (Le0 + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
+    const long items = (long)maxch * batch * (synth ? 2 * kKc : kKc);
+    k_prep64<<<dim3((unsigned)((items + 127) / 128), (unsigned)(mmax + 1)), 128, 0, st>>>(
+        synth ? 1 : 0, lmax, mmax, npairs, nlm, batch, (int)op, in, fcol, dchunk, data);
+    Tc64Args a{};
+    a.lmax = lmax;
+    a.mmax = mmax;
+    a.npairs = npairs;
+    a.nlm = nlm;
+    a.batch = batch;
+    a.op = (int)op;
+    a.panel = panel;
+    a.off = off;
+    a.c0 = c0;
+    a.erow = erow;
+    a.fcol = fcol;
+    a.data = data;
+    a.dchunk = dchunk;
+    a.out = out;
+    a.err = err;
+    int ts, ta;
+    tc_tile_counts(lmax, npairs, ts, ta);
+    a.ntiles = synth ? ts : ta;
+    const size_t smem = 128 + (size_t)kStages * kStage + 8 * (2 * kStages + 1) + 16;
+    const unsigned blocks = (unsigned)((mmax + 1) * a.ntiles);
+    cudaError_t e;
+    if (synth) {
+        e = cudaFuncSetAttribute(k_tc64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_tc64<true><<<blocks, kThreads, smem, st>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(k_tc64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_tc64<false><<<blocks, kThreads, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sht

@@ -27,12 +27,16 @@ class SHT:
     """A Gauss-Legendre spherical harmonic transform plan on one CUDA device."""
 
     def __init__(self, lmax: int, mmax: int | None = None, nlat: int | None = None,
-                 nphi: int | None = None, device=None, fp32_path: str = "f32"):
+                 nphi: int | None = None, device=None, fp32_path: str = "f32", fp64_path: str = "f64"):
         """fp32_path selects how complex64/float32 tensors are transformed:
         "f32" (FP32 recurrence on the CUDA cores), "tc" (tensor cores against
         FP64-built P_n^m panels, split-bf16 products) or "otf" (the same
         contraction with P_n^m generated on the fly, reseeded every 32 degrees
-        from FP64 values; scalar transforms, vector ones run "tc")."""
+        from FP64 values; scalar transforms, vector ones run "tc").
+        fp64_path selects it for complex128/float64 tensors: "f64" (FP64
+        recurrence on the CUDA cores) or "tc" (tensor cores on 7-bit digit
+        slices of both operands, FP64 accuracy; scalar transforms, lmax <= 1023,
+        vector ones run "f64")."""
         self.lmax = int(lmax)
         self.mmax = self.lmax if mmax is None else int(mmax)
         self.nlat = self.lmax + 1 if nlat is None else int(nlat)
@@ -41,6 +45,9 @@ class SHT:
         if fp32_path not in ("f32", "tc", "otf"):
             raise ValueError("fp32_path must be 'f32', 'tc' or 'otf'")
         self.fp32_mode = {"f32": C.SHT_F32, "tc": C.SHT_TC_BF16X3, "otf": C.SHT_TC_OTF}[fp32_path]
+        if fp64_path not in ("f64", "tc"):
+            raise ValueError("fp64_path must be 'f64' or 'tc'")
+        self.fp64_mode = {"f64": C.SHT_F64, "tc": C.SHT_TC_F64}[fp64_path]
         if self.device.type != "cuda":
             raise ValueError("SHT runs on CUDA devices only")
         with torch.cuda.device(self.device):
@@ -69,7 +76,7 @@ class SHT:
 
     def _mode_of(self, t: torch.Tensor) -> int:
         if t.dtype in (torch.complex128, torch.float64):
-            return C.SHT_F64
+            return self.fp64_mode
         if t.dtype in (torch.complex64, torch.float32):
             return self.fp32_mode
         raise TypeError(f"unsupported dtype {t.dtype}")
