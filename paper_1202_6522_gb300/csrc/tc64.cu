@@ -26,11 +26,11 @@
 // That is kSA MMAs per parity and chunk (N = 32 (kL - i)), 14 per chunk.
 // The accumulators are zeroed once and every MMA accumulates.
 //
-// CTA: one (order m, 128-row tile), 192 threads: warps 0-3 run the epilogue,
-// warp 4 lane 0 issues the MMAs, warp 5 lane 0 streams 56 KB panel chunks and
-// 16 KB data chunks by bulk copy into 3 stages.  Tensor memory: 2 parities x
-// kL levels x 32 columns (16 fields x re/im) = all 512 columns of the SM, so
-// one CTA per SM.  Every wait is bounded.
+// CTA: one (order m, 128-row tile, parity of n - m), 192 threads: warps 0-3
+// run the epilogue, warp 4 lane 0 issues the MMAs, warp 5 lane 0 streams the
+// parity's 28 KB of each panel chunk and its 8 KB of data by bulk copy into 3
+// stages.  Tensor memory: kL levels x 32 columns (16 fields x re/im) = 256, so
+// two CTAs share an SM.  Every wait is bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -56,21 +56,30 @@ constexpr int kSB = 8;                         // digit slices of the data
 constexpr int kNC = 32;                        // data rows per slice: 16 fields x (re, im)
 constexpr int kBatch64 = kNC / 2;              // fields per launch
 constexpr int kPBlk = kR * kKc * 2;            // one slice of one parity: [128 x 16] bf16 = 4 KB
-constexpr int kPChunk = 2 * kSA * kPBlk;       // panel chunk: [slice][parity] blocks = 56 KB
+constexpr int kPPar = kSA * kPBlk;             // one parity's slices: 28 KB
+constexpr int kPChunk = 2 * kPPar;             // panel chunk: [parity][slice] blocks = 56 KB
 constexpr int kDRows = kSB * kNC;              // data rows per class: slices stacked along N
 constexpr int kDBlk = kDRows * kKc * 2;        // 6 KB
 constexpr int kDChunk = 2 * kDBlk;             // data chunk: [class] blocks = 12 KB
-constexpr int kStage = kPChunk + kDChunk;      // 60 KB
+constexpr int kStage = kPPar + kDBlk;          // one parity: 36 KB
 constexpr int kStages = 3;
 constexpr int kThreads = 192;
 constexpr int kL = kSB;                        // accumulated levels t = i + j < kL
 constexpr int kLevelCols = kNC;                // accumulator columns per level
-constexpr int kParCols = kL * kLevelCols;      // per parity: 224
-constexpr uint32_t kTmemCols = 512;
+constexpr int kParCols = kL * kLevelCols;      // accumulator columns of a CTA: 256
+constexpr uint32_t kTmemCols = kParCols;
 constexpr int kExpNone = INT_MIN / 2;          // exponent of an all-zero row or column
 
 // Panel slice block of (slice i, parity par) in a chunk.
-__host__ __device__ __forceinline__ uint32_t pblk(int i, int par) { return (uint32_t)((2 * i + par) * kPBlk); }
+__host__ __device__ __forceinline__ uint32_t pblk(int i, int par) { return (uint32_t)(par * kPPar + i * kPBlk); }
+
+// 2^k as a double for the epilogue's scaling; 0 below the normal range (a
+// term below 2^-1022 of the unit is far under the FP64 rounding of any
+// result of this size).
+__device__ __forceinline__ double pow2_or_zero(int k)
+{
+    return k < -1022 ? 0.0 : __longlong_as_double((long long)(k + 1023) << 52);
+}
 
 // Exponent e with |v| < 2^e for every |v| <= max (frexp convention).
 __device__ __forceinline__ int exp_above(double max_abs)
@@ -326,7 +335,7 @@ struct Tc64Args {
 };
 
 template <bool SYNTH>
-__global__ void __launch_bounds__(kThreads, 1) k_tc64(Tc64Args a)
+__global__ void __launch_bounds__(kThreads, 2) k_tc64(Tc64Args a)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -337,8 +346,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc64(Tc64Args a)
     __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    const int m = blockIdx.x / a.ntiles;
-    const int tile = blockIdx.x - m * a.ntiles;
+    const int par = blockIdx.x & 1;
+    const int m = (blockIdx.x >> 1) / a.ntiles;
+    const int tile = (blockIdx.x >> 1) - m * a.ntiles;
     const int lmax = a.lmax, npairs = a.npairs;
     const int L = lmax - m + 1, Le = (L + 1) / 2;
     const long col = col_of(lmax, m);
@@ -367,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc64(Tc64Args a)
     if (warp < 4) {
         // zero this warp's lanes of every accumulator column; the MMAs all accumulate
         const uint32_t zero8[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-        for (int c = 0; c < 2 * kParCols; c += 8)
+        for (int c = 0; c < kParCols; c += 8)
             tc::tmem_st8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, zero8);
         tc::tmem_wait_st();
     }
@@ -378,16 +388,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc64(Tc64Args a)
     if (warp == 4) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            uint64_t da[kSA][2], db[2];
+            uint64_t da[kSA], db;
             uint32_t idesc[kSA];
 #pragma unroll
             for (int i = 0; i < kSA; ++i) {
                 idesc[i] = tc::idesc_bf16_f32(kR, (kL - i) * kNC);
-#pragma unroll
-                for (int par = 0; par < 2; ++par) da[i][par] = tc::smem_desc(smem + pblk(i, par), kLbo, kSbo);
+                da[i] = tc::smem_desc(smem + pblk(i, 0), kLbo, kSbo);
             }
-#pragma unroll
-            for (int par = 0; par < 2; ++par) db[par] = tc::smem_desc(smem + kPChunk + (size_t)par * kDBlk, kLbo, kSbo);
+            db = tc::smem_desc(smem + kPPar, kLbo, kSbo);
             const uint64_t sstep = (uint64_t)kStage >> 4;
             bool ok = true;
             for (int u = 0; u < nlive; ++u) {
@@ -396,11 +404,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc64(Tc64Args a)
                 tc::tc_fence_after();
                 const uint64_t so = sstep * (uint64_t)q;
 #pragma unroll
-                for (int par = 0; par < 2; ++par)
-#pragma unroll
-                    for (int i = 0; i < kSA; ++i)
-                        tc::mma_bf16(tmem + (uint32_t)(par * kParCols + i * kLevelCols), da[i][par] + so, db[par] + so,
-                                     idesc[i], true);
+                for (int i = 0; i < kSA; ++i)
+                    tc::mma_bf16(tmem + (uint32_t)(i * kLevelCols), da[i] + so, db + so, idesc[i], true);
                 tc::mma_commit(&bar_mma[q]);
             }
             if (!ok) raise_err(a.err, SHT_ETIMEOUT);
@@ -420,8 +425,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc64(Tc64Args a)
                 }
                 unsigned char *st = smem + (size_t)q * kStage;
                 tc::mbar_arrive_expect_tx(&bar_load[q], (uint32_t)kStage);
-                tc::bulk_g2s(st, panel + (size_t)c * kPChunk, (uint32_t)kPChunk, &bar_load[q]);
-                tc::bulk_g2s(st + kPChunk, data + (size_t)c * kDChunk, (uint32_t)kDChunk, &bar_load[q]);
+                tc::bulk_g2s(st, panel + (size_t)c * kPChunk + (size_t)par * kPPar, (uint32_t)kPPar, &bar_load[q]);
+                tc::bulk_g2s(st + kPPar, data + (size_t)c * kDChunk + (size_t)par * kDBlk, (uint32_t)kDBlk,
+                             &bar_load[q]);
                 issued = u + 1;
             }
             if (!ok) {
@@ -446,8 +452,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc64(Tc64Args a)
         const int row = tile * kR + warp * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
         const double sc = (!SYNTH && a.op == OP_SYNTH_ADJ && m > 0) ? 2.0 : 1.0;
-#pragma unroll 1
-        for (int par = 0; par < 2; ++par) {
+        {
             // row exponent: synthesis per (m, pair), analysis per (m, n)
             const int nn = 2 * row + par;
             int e_row = kExpNone;
@@ -467,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc64(Tc64Args a)
 #pragma unroll
                     for (int t = 0; t < kL; ++t) {
                         float v[16];
-                        tc::tmem_ld16(lane_base + (uint32_t)(par * kParCols + t * kLevelCols + 16 * h), v);
+                        tc::tmem_ld16(lane_base + (uint32_t)(t * kLevelCols + 16 * h), v);
 #pragma unroll
                         for (int k = 0; k < 16; ++k) {
                             const long long L = __float2ll_rn(v[k]);
@@ -484,10 +489,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc64(Tc64Args a)
                     // zero (or outside the order) and for an all-zero field
                     const bool zero = e_row == kExpNone || a.fcol[b] == kExpNone;
                     const int sh = zero ? 0 : e_row + a.fcol[b] - 12 - 7 * (kL - 1);
-                    const double re =
-                        zero ? 0.0 : sc * (ldexp((double)Zh[k], sh + 7 * (kL / 2)) + ldexp((double)Zl[k], sh));
-                    double im =
-                        zero ? 0.0 : sc * (ldexp((double)Zh[k + 1], sh + 7 * (kL / 2)) + ldexp((double)Zl[k + 1], sh));
+                    const double s_hi = zero ? 0.0 : sc * pow2_or_zero(sh + 7 * (kL / 2));
+                    const double s_lo = zero ? 0.0 : sc * pow2_or_zero(sh);
+                    const double re = fma((double)Zh[k], s_hi, (double)Zl[k] * s_lo);
+                    double im = fma((double)Zh[k + 1], s_hi, (double)Zl[k + 1] * s_lo);
                     if (SYNTH) {
                         if (row < npairs) {
                             double2 *eo = reinterpret_cast<double2 *>(a.out);
@@ -596,7 +601,7 @@ cudaError_t launch_tc64(bool synth, int lmax, int mmax, int npairs, int nlm, con
     tc_tile_counts(lmax, npairs, ts, ta);
     a.ntiles = synth ? ts : ta;
     const size_t smem = 128 + (size_t)kStages * kStage + 8 * (2 * kStages + 1) + 16;
-    const unsigned blocks = (unsigned)((mmax + 1) * a.ntiles);
+    const unsigned blocks = (unsigned)(2 * (mmax + 1) * a.ntiles);   // x parity
     cudaError_t e;
     if (synth) {
         e = cudaFuncSetAttribute(k_tc64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
