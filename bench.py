@@ -474,6 +474,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     if args.mode in ("tc", "otf"):
         sht = SHT(LMAX, LMAX, NLAT, NPHI, device=dev, fp32_path=args.mode)
+    if args.mode == "tc_f64":
+        sht = SHT(LMAX, LMAX, NLAT, NPHI, device=dev, fp64_path="tc")
     tune_report = None
     if args.mode == "auto":
         # runtime tuning before timing: kernel shapes and on-the-fly vs precomputed panels
@@ -490,7 +492,7 @@ def run_ours(args):
         alu_peaks = C.sht_alu_peaks(stream.cuda_stream)
     except Exception:
         alu_peaks = None
-    cdt = torch.complex128 if args.mode == "f64" else torch.complex64
+    cdt = torch.complex128 if args.mode in ("f64", "tc_f64") else torch.complex64
     a_np = synthetic.spectrum(LMAX, batch=BATCH, seed=rank)
     a = torch.from_numpy(a_np).to(dev, cdt)
 
@@ -599,14 +601,15 @@ def run_ours(args):
     fp64 = None
     if args.mode != "f64":
         a64 = torch.from_numpy(a_np).to(dev, torch.complex128)
-        ms64, tab64 = time_path(sht, torch, a64, max(2, args.steps // 4), 1, stream, profile=True)
+        sht_plain = SHT(LMAX, LMAX, NLAT, NPHI, device=dev) if args.mode == "tc_f64" else sht
+        ms64, tab64 = time_path(sht_plain, torch, a64, max(2, args.steps // 4), 1, stream, profile=True)
         del a64
         fp64 = {"round_trips_per_s": world * BATCH / (ms64 / 1e3), "ms_per_step": ms64,
                 "kernels_ms": {k: v[0] / v[1] for k, v in tab64.items()}}
 
     # --- FP64-accurate tensor-core path (digit slices) on the same workload ---
     fp64tc = None
-    if args.mode != "f64" and not args.no_uneven:
+    if args.mode not in ("f64", "tc_f64") and not args.no_uneven:
         from paper_1202_6522_gb300 import SHT as _SHT
         sht64 = _SHT(LMAX, LMAX, NLAT, NPHI, fp64_path="tc")
         a64 = torch.from_numpy(a_np).to(dev, torch.complex128)
@@ -627,6 +630,7 @@ def run_ours(args):
     dom_avg = dom_ms / dom_n
     sm_max = clk.get("sm_max_mhz") or 2070.0
     path_used = {"auto": (tune_report or {}).get("chosen", "f32"), "otf": "tc_otf"}.get(args.mode, args.mode)
+    fft_flops = BATCH * NLAT * 2.5 * NPHI * math.log2(NPHI)   # one FFT launch, nominal
     if dom_name.startswith("tc_") and path_used == "tc_otf":
         # P generated in FP32 on the CUDA cores: 5 flops per (n, m, latitude pair)
         # (a x, b P_{n-2}, one fma, the seed scale), the tensor-core work aside
@@ -656,6 +660,8 @@ def run_ours(args):
                 "polar_skip": {"synth": skip_s, "analys": skip_a}}
     else:
         flops = legendre_flops_per_launch(BATCH) if dom_name.startswith("legendre") else None
+        if dom_name.startswith("fft"):
+            flops = fft_flops
         if args.mode == "f32":
             if alu_peaks:
                 peak, peak_note = alu_peaks[0] * 1e12, "measured FP32 FMA throughput (sht_alu_peaks)"
@@ -682,6 +688,8 @@ def run_ours(args):
             return 1
         if path_used == "tc_otf":
             return 2
+        if path_used == "tc_f64":
+            return 4   # field exponents (fill + reduction), data digits, contraction
         return 2 if (k == "tc_synth" and nlm_of(LMAX) % 2) else 1
     launches = sum(v[1] * kernels_per(k) for k, v in table.items())
     line = {
@@ -689,6 +697,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "tc": "bf16x3 (f32 accumulate)",
                                        "otf": "bf16x3 (f32 accumulate)",
+                                       "tc_f64": "f64 (bf16 digit slices, exact f32 level sums)",
                                        "auto": "f32 / bf16x3 (tuned)"}[args.mode],
         "data": "synthetic (seeded N(0,1)/(n+1) spectra)",
         "config": {"workload": WORKLOAD, "lmax": LMAX, "nlat": NLAT, "nphi": NPHI, "batch": BATCH,
@@ -696,6 +705,7 @@ def run_ours(args):
                             "f64": "plain FP64 on-the-fly",
                             "tc": "tcgen05 split-bf16 contraction vs FP64-built P panels",
                             "otf": "tcgen05 split-bf16 contraction, P generated on the fly (FP32, reseeded)",
+                            "tc_f64": "tcgen05 contraction on 7-bit digit slices (FP64 accuracy), FP64 FFTs",
                             "auto": "runtime-tuned: FP32 on-the-fly, tcgen05 panels or tcgen05 on-the-fly P"}[args.mode],
                    "path_used": path_used, "l2": "inputs larger than L2 (spectra+grids > 129 MB)",
                    "parallelism": f"replicas x{world}"},
@@ -736,7 +746,7 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["auto", "tc", "otf", "f32", "f64"], default="auto")
+    ap.add_argument("--mode", choices=["auto", "tc", "otf", "f32", "f64", "tc_f64"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch measurement")
     args = ap.parse_args()

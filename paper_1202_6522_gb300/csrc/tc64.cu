@@ -73,12 +73,34 @@ constexpr int kExpNone = INT_MIN / 2;          // exponent of an all-zero row or
 // Panel slice block of (slice i, parity par) in a chunk.
 __host__ __device__ __forceinline__ uint32_t pblk(int i, int par) { return (uint32_t)(par * kPPar + i * kPBlk); }
 
-// 2^k as a double for the epilogue's scaling; 0 below the normal range (a
-// term below 2^-1022 of the unit is far under the FP64 rounding of any
-// result of this size).
-__device__ __forceinline__ double pow2_or_zero(int k)
+// Z 2^k as a double, for a 128-bit integer Z, with integer operations only
+// (the FP64 pipe is the scarce one): normalise, round the 53-bit mantissa to
+// nearest (ties away from zero), and assemble the exponent.  Results below
+// the normal range are flushed to zero: they are under 2^-1022, far below the
+// FP64 rounding of the sums this kernel forms.
+__device__ __forceinline__ double i128_ldexp(__int128 Z, int k)
 {
-    return k < -1022 ? 0.0 : __longlong_as_double((long long)(k + 1023) << 52);
+    if (Z == 0) return 0.0;
+    const bool neg = Z < 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)(-Z) : (unsigned __int128)Z;
+    const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+    int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    unsigned long long mant;
+    if (msb > 52) {
+        mant = (unsigned long long)(u >> (msb - 53));   // 54 bits: one rounding bit
+        mant = (mant + 1) >> 1;
+        if (mant >> 53) {
+            mant >>= 1;
+            msb += 1;
+        }
+    } else {
+        mant = lo << (52 - msb);
+    }
+    const int e = msb + k + 1023;
+    if (e <= 0) return 0.0;
+    const unsigned long long bits =
+        ((unsigned long long)e << 52) | (mant & 0xFFFFFFFFFFFFFull) | (neg ? 0x8000000000000000ull : 0ull);
+    return __longlong_as_double((long long)bits);
 }
 
 // Exponent e with |v| < 2^e for every |v| <= max (frexp convention).
@@ -244,13 +266,15 @@ __global__ void k_p64_first_live(int synth, int lmax, int npairs, int ntiles, co
 __global__ void k_colscale(const double *__restrict__ x, size_t per_field, int *__restrict__ f)
 {
     const int b = blockIdx.y;
-    const double *xb = x + (size_t)b * per_field;
-    double mx = 0.0;
+    // the bit patterns of non-negative doubles order like the values: the
+    // maximum |x| is an integer maximum, off the FP64 pipe
+    const unsigned long long *xb = reinterpret_cast<const unsigned long long *>(x) + (size_t)b * per_field;
+    unsigned long long mx = 0;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_field; i += (size_t)gridDim.x * blockDim.x)
-        mx = fmax(mx, fabs(xb[i]));
+        mx = max(mx, xb[i] & 0x7FFFFFFFFFFFFFFFull);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(&f[b], exp_above(mx));
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx != 0) atomicMax(&f[b], exp_above(__longlong_as_double((long long)mx)));
 }
 
 __global__ void k_fill_int(int *__restrict__ a, int v, size_t n)
@@ -287,9 +311,12 @@ __global__ void k_prep64(int synth, int lmax, int mmax, int npairs, int nlm, int
         double re = 0.0, im = 0.0;
         if (nn < L) {
             const double2 v = reinterpret_cast<const double2 *>(in)[(size_t)b * nlm + col + nn];
-            const double cadj = (op == OP_ANALYS_ADJ && m > 0) ? 0.5 : 1.0;
-            re = v.x * cadj;
-            im = m == 0 ? 0.0 : v.y * cadj;
+            re = v.x;
+            im = m == 0 ? 0.0 : v.y;
+            if (op == OP_ANALYS_ADJ && m > 0) {   // adjoint factor 1/2
+                re *= 0.5;
+                im *= 0.5;
+            }
         }
         digits_int(re, e, dv[0]);
         digits_int(im, e, dv[1]);
@@ -451,7 +478,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc64(Tc64Args a)
         tc::tc_fence_after();
         const int row = tile * kR + warp * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-        const double sc = (!SYNTH && a.op == OP_SYNTH_ADJ && m > 0) ? 2.0 : 1.0;
+        const int sc_log2 = (!SYNTH && a.op == OP_SYNTH_ADJ && m > 0) ? 1 : 0;   // adjoint factor 2
         {
             // row exponent: synthesis per (m, pair), analysis per (m, n)
             const int nn = 2 * row + par;
@@ -488,11 +515,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc64(Tc64Args a)
                     // sum = 2^(e + f - 12 - 7 (kL - 1)) Z; zero for a row whose P are all
                     // zero (or outside the order) and for an all-zero field
                     const bool zero = e_row == kExpNone || a.fcol[b] == kExpNone;
-                    const int sh = zero ? 0 : e_row + a.fcol[b] - 12 - 7 * (kL - 1);
-                    const double s_hi = zero ? 0.0 : sc * pow2_or_zero(sh + 7 * (kL / 2));
-                    const double s_lo = zero ? 0.0 : sc * pow2_or_zero(sh);
-                    const double re = fma((double)Zh[k], s_hi, (double)Zl[k] * s_lo);
-                    double im = fma((double)Zh[k + 1], s_hi, (double)Zl[k + 1] * s_lo);
+                    const int sh = zero ? 0 : e_row + a.fcol[b] - 12 - 7 * (kL - 1) + sc_log2;
+                    const __int128 zr = ((__int128)Zh[k] << (7 * (kL / 2))) + Zl[k];
+                    const __int128 zi = ((__int128)Zh[k + 1] << (7 * (kL / 2))) + Zl[k + 1];
+                    const double re = zero ? 0.0 : i128_ldexp(zr, sh);
+                    double im = zero ? 0.0 : i128_ldexp(zi, sh);
                     if (SYNTH) {
                         if (row < npairs) {
                             double2 *eo = reinterpret_cast<double2 *>(a.out);

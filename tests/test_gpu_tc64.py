@@ -1,8 +1,8 @@
 """Parity of the FP64-accurate tensor-core mode (SHT_TC_F64) with the FP64 oracle.
 
-Both operands of each per-order contraction are split into six signed 7-bit
-digit slices (P per row, the data per field) whose integer products the tensor
-core sums exactly; the bound is the FP64 path's, 1e-11 normwise.  Cases cover
+Both operands of each per-order contraction are split into signed 7-bit digit
+slices (7 for P per row, 8 for the data per field) whose integer products the
+tensor core sums exactly; the bound is the FP64 path's, 1e-11 normwise.  Cases cover
 several 128-row tiles and ragged tails, mmax < lmax, odd nlat, batches of more
 than 16 fields (several launches), the adjoints, sampled rows/orders of the
 full N = 1023, batch 16 workload, and the size limit."""
@@ -82,6 +82,24 @@ def test_tc64_full_size_n1023_b16_sampled(SHT):
     for b in (0, 15):
         ref = oracle.analys(lmax, lmax, nlat, nphi, g[b], ms=ms)
         assert normwise(spec[b][idx], ref[idx]) < fp64_bound(lmax), b
+    assert sht.sync_status() == 0
+
+
+def test_tc64_n511_b16_sampled(SHT):
+    """N = 511, batch 16 (panels larger than L2): sampled rows and orders."""
+    lmax, nlat, nphi, batch = 511, 512, 1024, 16
+    sht = SHT(lmax, lmax, nlat, nphi, fp64_path="tc")
+    a = synthetic.spectrum(lmax, batch=batch, seed=4)
+    grid = _np(sht.synth_(torch.from_numpy(a).to(DEV)))
+    rows = [0, 5, 255, 256, 400, 511]
+    ref = oracle.synth(lmax, lmax, nlat, nphi, a[7], rows=rows)
+    assert normwise(grid[7][rows], ref[rows]) < fp64_bound(lmax)
+    g = synthetic.grid(nlat, nphi, batch=batch, seed=5)
+    spec = _np(sht.analys_(torch.from_numpy(g).to(DEV)))
+    ms = [0, 3, 200, 511]
+    idx = np.concatenate([[oracle.lm_index(lmax, n, m) for n in range(m, lmax + 1)] for m in ms])
+    ref = oracle.analys(lmax, lmax, nlat, nphi, g[11], ms=ms)
+    assert normwise(spec[11][idx], ref[idx]) < fp64_bound(lmax)
     assert sht.sync_status() == 0
 
 
