@@ -67,6 +67,25 @@ def tc_algorithmic_bytes(batch, lmax=LMAX, nlat=NLAT, polar_skip=0.0):
     return panel + spec + inter
 
 
+# DRAM bytes (read + write) per launch of the panel contraction at this
+# workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum);
+# valid only while the kernel source is the one that was profiled (its SHA-256
+# below), else null.
+TC_TRAFFIC_SRC_SHA256 = "b3e2a85a7897880a7e4474fd3d596379cd50b5a826d7791eb6d2bb9ef9e4dede"
+TC_TRAFFIC_BYTES = {"tc_synth": 869.112320e6 + 94.180096e6, "tc_analys": 883.195648e6 + 55.916544e6}
+
+
+def tc_traffic(kernel):
+    import hashlib
+    src = os.path.join(ROOT, "paper_1202_6522_gb300", "csrc", "tc.cu")
+    try:
+        with open(src, "rb") as fh:
+            same = hashlib.sha256(fh.read()).hexdigest() == TC_TRAFFIC_SRC_SHA256
+    except OSError:
+        same = False
+    return TC_TRAFFIC_BYTES.get(kernel) if same else None
+
+
 def fp32_alu_peak(sm_mhz):
     """FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 flops x clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6
@@ -654,7 +673,8 @@ def run_ours(args):
         peak = peaks.get("hbm_gbs", 6800.0) * 1e9
         achieved = algo / (dom_avg / 1e3)
         roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved / 1e9, "peak": peak / 1e9,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "unit": "GB/s", "frac": achieved / peak,
+                "traffic": tc_traffic(dom_name) if path_used == "tc" else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
                 "algorithmic_bytes": algo, "kernel_avg_ms": dom_avg, "launches": dom_n,
                 "polar_skip": {"synth": skip_s, "analys": skip_a}}
