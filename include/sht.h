@@ -115,8 +115,11 @@ enum {
 /* Build a plan (Sec. 2.3 nodes/weights, Sec. 3.2 recurrence tables, FFT
  * twiddles) on the host and copy it to the current CUDA device.
  * Requires 0 <= mmax <= lmax, nlat >= lmax + 1 (exactness of the quadrature,
- * Sec. 2.3), nphi >= 2 mmax + 1 and nphi >= 2 a power of two (SHT_EUNSUPPORTED
- * otherwise).  On success *out receives the handle; on failure *out is NULL. */
+ * Sec. 2.3), nphi >= 2 mmax + 1 and nphi = 2 x 2^a 3^b 5^c <= 8192
+ * (SHT_EUNSUPPORTED otherwise; the longitude FFT of length nphi / 2 runs in
+ * radix-16/8/4/2, 3 and 5 passes, and power-of-two lengths up to 1024 in FP32
+ * take the faster one-warp-per-row kernel).  On success *out receives the
+ * handle; on failure *out is NULL. */
 SHT_API int sht_create(int lmax, int mmax, int nlat, int nphi, sht_handle *out);
 
 /* Free the plan and everything it owns.  NULL is ignored.  The caller must
@@ -224,7 +227,7 @@ SHT_API int sht_tune(sht_handle h, int batch, int mode, double *report, void *st
  * sequence (pointer-table copy, counter reset, Legendre and FFT kernels) is
  * captured into a CUDA graph by the first call of each direction and replayed
  * afterwards; the capture happens on a private stream.
- * Limits: nphi a power of two in [2, 4096], nlat <= 1024.
+ * Limits: nphi = 2 x 2^a 3^b 5^c in [2, 4096], nlat <= 1024.
  * spec[f] / grid[f]: device pointers of field f ([nlm_f] complex floats and
  * [nlat_f][nphi_f] floats).  A call waits on the host until the previous call
  * on this batch plan has started its pointer-table copy. */

@@ -73,10 +73,12 @@ void fill_fields(sht_batch_plan *b, void *const *in, void *const *out)
         bf.in = static_cast<const float *>(in[f]);
         bf.out = static_cast<float *>(out[f]);
         bf.inter = b->d_inter + b->inter_off[f];
+        // row FFT tiles for power-of-two lengths <= 2^10, else the mixed-radix kernel
+        const int H = p.nphi / 2;
         int logH = 0;
-        while ((1 << logH) < p.nphi / 2) ++logH;
-        bf.logH = logH;
-        bf.G = sht::batch_fft_group(logH, p.npairs);
+        while ((1 << logH) < H) ++logH;
+        bf.logH = (1 << logH) == H ? logH : 31;
+        bf.G = sht::batch_fft_group(H, p.npairs);
     }
 }
 
@@ -158,8 +160,8 @@ int sht_batch_create(int nfields, const int *lmax, const int *nlat, const int *n
     for (int f = 0; f < nfields; ++f) {
         if (lmax[f] < 0 || nlat[f] < lmax[f] + 1 || nphi[f] < 2 * lmax[f] + 1)
             return bfail(SHT_EINVAL, "field " + std::to_string(f) + ": need nlat >= lmax+1 and nphi >= 2 lmax + 1");
-        if (nphi[f] < 2 || nphi[f] > 4096 || (nphi[f] & (nphi[f] - 1)))
-            return bfail(SHT_EUNSUPPORTED, "field " + std::to_string(f) + ": nphi must be a power of two in [2, 4096]");
+        if (nphi[f] < 2 || nphi[f] > 4096 || nphi[f] % 2 != 0 || sht::fft_plan_of(nphi[f] / 2) == sht::kFftPlanBad)
+            return bfail(SHT_EUNSUPPORTED, "field " + std::to_string(f) + ": nphi must be 2 x 2^a 3^b 5^c in [2, 4096]");
         if ((nlat[f] + 1) / 2 > sht::kBatchMaxPairs)
             return bfail(SHT_EUNSUPPORTED, "field " + std::to_string(f) + ": nlat > 1024 is not supported in a batch");
     }
@@ -210,8 +212,8 @@ int sht_batch_create(int nfields, const int *lmax, const int *nlat, const int *n
         }
         int logH = 0;
         while ((1 << logH) < p.nphi / 2) ++logH;
-        const int G = sht::batch_fft_group(logH, p.npairs);
-        smem = std::max(smem, sht::batch_fft_smem(logH, G));
+        const int G = sht::batch_fft_group(p.nphi / 2, p.npairs);
+        smem = std::max(smem, sht::batch_fft_smem(p.nphi / 2, G));
         for (int p0 = 0; p0 < p.npairs; p0 += G)
             ffts.push_back({(double)G * p.nphi * (logH + 2) + p.mmax, make_int4(f, p0, 0, 0)});
     }

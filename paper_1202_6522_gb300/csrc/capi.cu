@@ -24,7 +24,6 @@ int fail(int code, const std::string &msg)
     return code;
 }
 
-bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 int check_handle(sht_handle h)
 {
@@ -788,8 +787,8 @@ int sht_create(int lmax, int mmax, int nlat, int nphi, sht_handle *out)
     if (nlat < lmax + 1) return fail(SHT_EINVAL, "need nlat >= lmax + 1 for an exact Gauss-Legendre quadrature");
     if (nphi < 2 * mmax + 1) return fail(SHT_EINVAL, "need nphi >= 2 mmax + 1");
     if (nlat > 4096 || lmax > 4095) return fail(SHT_EUNSUPPORTED, "nlat > 4096 is not supported");
-    if (!is_pow2(nphi) || nphi < 2 || nphi > 8192)
-        return fail(SHT_EUNSUPPORTED, "nphi must be a power of two in [2, 8192]");
+    if (nphi < 2 || nphi > 8192 || nphi % 2 != 0 || sht::fft_plan_of(nphi / 2) == sht::kFftPlanBad)
+        return fail(SHT_EUNSUPPORTED, "nphi must be 2 x 2^a 3^b 5^c in [2, 8192]");
     sht_plan *h = new (std::nothrow) sht_plan;
     if (!h) return fail(SHT_ENOMEM, "host allocation failed");
     h->p.lmax = lmax;

@@ -79,21 +79,68 @@ template <typename T2, int SIGN>
 struct RegDft<T2, 1, SIGN> {
     __device__ __forceinline__ static void run(T2 (&)[1]) {}
 };
+// Length 3 from the definition y_k = sum_r a_r w^(r k), w = e^(SIGN 2 pi i / 3):
+// y_1,2 = a_0 - (a_1 + a_2) / 2 +- i SIGN (sqrt(3) / 2) (a_1 - a_2).
+template <typename T2, int SIGN>
+struct RegDft<T2, 3, SIGN> {
+    using T = decltype(T2::x);
+    __device__ __forceinline__ static void run(T2 (&a)[3])
+    {
+        const T s3 = T(SIGN * 0.86602540378443864676);
+        const T2 t = cadd(a[1], a[2]), d = csub(a[1], a[2]);
+        const T2 c = mk<T2>(a[0].x - T(0.5) * t.x, a[0].y - T(0.5) * t.y);
+        const T2 id = mk<T2>(-s3 * d.y, s3 * d.x);   // i SIGN sqrt(3)/2 (a_1 - a_2)
+        a[0] = cadd(a[0], t);
+        a[1] = cadd(c, id);
+        a[2] = csub(c, id);
+    }
+};
+// Length 5 from the definition, with b_1 = a_1 + a_4, b_2 = a_2 + a_3,
+// d_1 = a_1 - a_4, d_2 = a_2 - a_3, c_k = cos(2 pi k / 5), s_k = SIGN sin(2 pi k / 5):
+// y_1,4 = a_0 + c_1 b_1 + c_2 b_2 +- i (s_1 d_1 + s_2 d_2),
+// y_2,3 = a_0 + c_2 b_1 + c_1 b_2 +- i (s_2 d_1 - s_1 d_2).
+template <typename T2, int SIGN>
+struct RegDft<T2, 5, SIGN> {
+    using T = decltype(T2::x);
+    __device__ __forceinline__ static void run(T2 (&a)[5])
+    {
+        const T c1 = T(0.30901699437494742410), c2 = T(-0.80901699437494742410);
+        const T s1 = T(SIGN * 0.95105651629515357212), s2 = T(SIGN * 0.58778525229247312917);
+        const T2 b1 = cadd(a[1], a[4]), b2 = cadd(a[2], a[3]);
+        const T2 d1 = csub(a[1], a[4]), d2 = csub(a[2], a[3]);
+        const T2 r1 = mk<T2>(a[0].x + c1 * b1.x + c2 * b2.x, a[0].y + c1 * b1.y + c2 * b2.y);
+        const T2 r2 = mk<T2>(a[0].x + c2 * b1.x + c1 * b2.x, a[0].y + c2 * b1.y + c1 * b2.y);
+        const T2 q1 = mk<T2>(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
+        const T2 q2 = mk<T2>(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
+        a[0] = cadd(a[0], cadd(b1, b2));
+        a[1] = cadd(r1, mul_i(q1));
+        a[4] = csub(r1, mul_i(q1));
+        a[2] = cadd(r2, mul_i(q2));
+        a[3] = csub(r2, mul_i(q2));
+    }
+};
+
+// Registers per thread of a Stockham pass: ceil(16 / RD) items of RD values
+// with TPR = ceil(H / 16) threads per row: 16 for power-of-two radices, 20
+// once radix 3 or 5 passes occur (MIXED; compiled separately so that the
+// power-of-two kernels keep their smaller register footprint).
+template <bool MIXED> struct PassRegs { static constexpr int n = MIXED ? 20 : 16; };
+__host__ __device__ inline int row_tpr(int H) { return (H + 15) / 16; }
 
 // One Stockham pass of radix RD over a row of length H held in `row` (padded
 // indices) or, for the first/last pass, in global memory.  Each thread owns
-// 16 / RD items j = t + it * TPR; item j reads x[j + r H/RD], applies the
-// twiddle W^(r (j mod Ns) H/(Ns RD)), runs the RD-point DFT and writes
-// y[(j / Ns) Ns RD + j mod Ns + r Ns].
-template <typename T2, int RD, int SIGN>
+// up to ceil(16 / RD) items j = t + it * TPR; item j reads x[j + r H/RD],
+// applies the twiddle W^(r (j mod Ns) H/(Ns RD)), runs the RD-point DFT and
+// writes y[(j / Ns) Ns RD + j mod Ns + r Ns].
+template <typename T2, int RD, int SIGN, int NR>
 __device__ __forceinline__ void stockham_load(const T2 *src, bool global_src, int t, int TPR, int H, int Ns,
-                                              const T2 *__restrict__ wtab, T2 (&v)[16])
+                                              const T2 *__restrict__ wtab, T2 (&v)[NR])
 {
-    constexpr int IT = 16 / RD;
+    constexpr int IT = (16 + RD - 1) / RD;
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
         const int j = t + it * TPR;
-        if (j >= H / RD) break;  // only when H < 16
+        if (j >= H / RD) break;
         T2 a[RD];
 #pragma unroll
         for (int r = 0; r < RD; ++r) {
@@ -104,7 +151,7 @@ __device__ __forceinline__ void stockham_load(const T2 *src, bool global_src, in
             const int q0 = (j % Ns) * (H / (Ns * RD));
 #pragma unroll
             for (int r = 1; r < RD; ++r) {
-                T2 w = wtab[(r * q0) & (H - 1)];
+                T2 w = wtab[(r * q0) % H];
                 if (SIGN < 0) w = conj_(w);
                 a[r] = cmul(a[r], w);
             }
@@ -121,47 +168,47 @@ __device__ __forceinline__ int stockham_out(int j, int r, int Ns)
     return (j / Ns) * Ns * RD + (j % Ns) + r * Ns;
 }
 
-template <typename T2, int RD>
-__device__ __forceinline__ void stockham_store_smem(T2 *row, int t, int TPR, int H, int Ns, const T2 (&v)[16])
+template <typename T2, int RD, int NR>
+__device__ __forceinline__ void stockham_store_smem(T2 *row, int t, int TPR, int H, int Ns, const T2 (&v)[NR])
 {
-    constexpr int IT = 16 / RD;
+    constexpr int IT = (16 + RD - 1) / RD;
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
         const int j = t + it * TPR;
-        if (j >= H / RD) break;  // only when H < 16
+        if (j >= H / RD) break;
 #pragma unroll
         for (int r = 0; r < RD; ++r) row[padi(stockham_out<T2, RD>(j, r, Ns))] = v[it * RD + r];
     }
 }
 
-// Radix of the first pass: the remainder of log2(H) by 4 (or 16).
-__host__ __device__ inline int first_radix(int logH)
-{
-    const int rem = logH % 4;
-    return rem == 0 ? 16 : (1 << rem);
-}
-
 // Runs a pass of the given radix (run-time selected).
-template <typename T2, int SIGN>
+template <typename T2, int SIGN, bool MIXED>
 __device__ __forceinline__ void pass_load(int rd, const T2 *src, bool g, int t, int TPR, int H, int Ns,
-                                          const T2 *wtab, T2 (&v)[16])
+                                          const T2 *wtab, T2 (&v)[PassRegs<MIXED>::n])
 {
+    constexpr int NR = PassRegs<MIXED>::n;
+    if (MIXED && rd == 3) { stockham_load<T2, 3, SIGN, NR>(src, g, t, TPR, H, Ns, wtab, v); return; }
+    if (MIXED && rd == 5) { stockham_load<T2, 5, SIGN, NR>(src, g, t, TPR, H, Ns, wtab, v); return; }
     switch (rd) {
-    case 2: stockham_load<T2, 2, SIGN>(src, g, t, TPR, H, Ns, wtab, v); break;
-    case 4: stockham_load<T2, 4, SIGN>(src, g, t, TPR, H, Ns, wtab, v); break;
-    case 8: stockham_load<T2, 8, SIGN>(src, g, t, TPR, H, Ns, wtab, v); break;
-    default: stockham_load<T2, 16, SIGN>(src, g, t, TPR, H, Ns, wtab, v); break;
+    case 2: stockham_load<T2, 2, SIGN, NR>(src, g, t, TPR, H, Ns, wtab, v); break;
+    case 4: stockham_load<T2, 4, SIGN, NR>(src, g, t, TPR, H, Ns, wtab, v); break;
+    case 8: stockham_load<T2, 8, SIGN, NR>(src, g, t, TPR, H, Ns, wtab, v); break;
+    default: stockham_load<T2, 16, SIGN, NR>(src, g, t, TPR, H, Ns, wtab, v); break;
     }
 }
 
-template <typename T2>
-__device__ __forceinline__ void pass_store(int rd, T2 *row, int t, int TPR, int H, int Ns, const T2 (&v)[16])
+template <typename T2, bool MIXED>
+__device__ __forceinline__ void pass_store(int rd, T2 *row, int t, int TPR, int H, int Ns,
+                                           const T2 (&v)[PassRegs<MIXED>::n])
 {
+    constexpr int NR = PassRegs<MIXED>::n;
+    if (MIXED && rd == 3) { stockham_store_smem<T2, 3, NR>(row, t, TPR, H, Ns, v); return; }
+    if (MIXED && rd == 5) { stockham_store_smem<T2, 5, NR>(row, t, TPR, H, Ns, v); return; }
     switch (rd) {
-    case 2: stockham_store_smem<T2, 2>(row, t, TPR, H, Ns, v); break;
-    case 4: stockham_store_smem<T2, 4>(row, t, TPR, H, Ns, v); break;
-    case 8: stockham_store_smem<T2, 8>(row, t, TPR, H, Ns, v); break;
-    default: stockham_store_smem<T2, 16>(row, t, TPR, H, Ns, v); break;
+    case 2: stockham_store_smem<T2, 2, NR>(row, t, TPR, H, Ns, v); break;
+    case 4: stockham_store_smem<T2, 4, NR>(row, t, TPR, H, Ns, v); break;
+    case 8: stockham_store_smem<T2, 8, NR>(row, t, TPR, H, Ns, v); break;
+    default: stockham_store_smem<T2, 16, NR>(row, t, TPR, H, Ns, v); break;
     }
 }
 
@@ -189,13 +236,13 @@ __device__ __forceinline__ void fill_wtab(T2 *wtab, const T2 *__restrict__ tw, i
 // One tile (field b, pairs p0 .. p0+G-1) of the synthesis FFT, run by the
 // whole CTA (blockDim.x >= 2 G max(1, H/16)); smem_raw holds the twiddle table
 // and the 2G padded rows.
-template <typename T>
+template <typename T, bool MIXED>
 __device__ __forceinline__ void fft_synth_tile(const PlanView<T> &pv, const T *__restrict__ eo, T *__restrict__ grid,
-                                               int b, int p0, int G, int logH, int op, unsigned char *smem_raw)
+                                               int b, int p0, int G, int op, unsigned char *smem_raw)
 {
     using T2 = typename Vec2<T>::type;
-    const int H = 1 << logH, R = 2 * G;
-    const int TPR = H >= 16 ? H / 16 : 1;
+    const int H = pv.nphi / 2, R = 2 * G;
+    const int TPR = row_tpr(H);
     const int ld = padi(H) + 1;
     T2 *wtab = reinterpret_cast<T2 *>(smem_raw);
     T2 *buf = wtab + H;
@@ -252,19 +299,19 @@ __device__ __forceinline__ void fft_synth_tile(const PlanView<T> &pv, const T *_
         return;
     }
     int Ns = 1;
-    int rd = first_radix(logH);
-    T2 v[16];
-    while (true) {
-        if (r < R) pass_load<T2, 1>(rd, row, false, t, TPR, H, Ns, wtab, v);
+    T2 v[PassRegs<MIXED>::n];
+    for (int ps = 0;; ++ps) {
+        const int rd = fft_plan_radix(pv.fftplan, ps);
+        if (r < R) pass_load<T2, 1, MIXED>(rd, row, false, t, TPR, H, Ns, wtab, v);
         const bool last = Ns * rd == H;
         __syncthreads();
         if (last) {
             // last pass: y[j + r' H/RD] for item j -- contiguous over threads
             if (live_row) {
-                const int IT = 16 / rd;
+                const int IT = (16 + rd - 1) / rd;
                 for (int it = 0; it < IT; ++it) {
                     const int jj = t + it * TPR;
-                    if (jj >= H / rd) break;  // only when H < 16
+                    if (jj >= H / rd) break;
                     for (int rr = 0; rr < rd; ++rr) {
                         T2 z = v[it * rd + rr];
                         z.x *= scale; z.y *= scale;
@@ -274,33 +321,31 @@ __device__ __forceinline__ void fft_synth_tile(const PlanView<T> &pv, const T *_
             }
             break;
         }
-        if (r < R) pass_store<T2>(rd, row, t, TPR, H, Ns, v);
+        if (r < R) pass_store<T2, MIXED>(rd, row, t, TPR, H, Ns, v);
         __syncthreads();
         Ns *= rd;
-        rd = 16;
     }
 }
 
-template <typename T>
+template <typename T, bool MIXED>
 __global__ void __launch_bounds__(512)
-k_fft_synth(PlanView<T> pv, const T *__restrict__ eo, T *__restrict__ grid, int G, int logH, int op)
+k_fft_synth(PlanView<T> pv, const T *__restrict__ eo, T *__restrict__ grid, int G, int op)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fft_synth_tile<T>(pv, eo, grid, blockIdx.y, blockIdx.x * G, G, logH, op, smem_raw);
+    fft_synth_tile<T, MIXED>(pv, eo, grid, blockIdx.y, blockIdx.x * G, G, op, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
 // Analysis: grid [batch][nlat][nphi] -> SD [batch][mmax+1][npairs][2]
 // ---------------------------------------------------------------------------
 // One tile (field b, pairs p0 .. p0+G-1) of the analysis FFT (see fft_synth_tile).
-template <typename T>
+template <typename T, bool MIXED>
 __device__ __forceinline__ void fft_analys_tile(const PlanView<T> &pv, const T *__restrict__ grid, T *__restrict__ sd,
-                                                int b, int p0, int G, int logH, int op, int vector,
-                                                unsigned char *smem_raw)
+                                                int b, int p0, int G, int op, int vector, unsigned char *smem_raw)
 {
     using T2 = typename Vec2<T>::type;
-    const int H = 1 << logH, R = 2 * G;
-    const int TPR = H >= 16 ? H / 16 : 1;
+    const int H = pv.nphi / 2, R = 2 * G;
+    const int TPR = row_tpr(H);
     const int ld = padi(H) + 1;
     T2 *wtab = reinterpret_cast<T2 *>(smem_raw);
     T2 *buf = wtab + H;
@@ -320,29 +365,26 @@ __device__ __forceinline__ void fft_analys_tile(const PlanView<T> &pv, const T *
     } else {
         // forward complex FFT of length H; the first pass reads the grid row
         int Ns = 1;
-        int rd = first_radix(logH);
-        T2 v[16];
-        bool first = true;
-        while (true) {
+        T2 v[PassRegs<MIXED>::n];
+        const int npass = fft_plan_npass(pv.fftplan);
+        for (int ps = 0; ps < npass; ++ps) {
+            const int rd = fft_plan_radix(pv.fftplan, ps);
             if (r < R) {
-                if (first) {
+                if (ps == 0) {
                     if (live_row) {
-                        pass_load<T2, -1>(rd, in, true, t, TPR, H, Ns, wtab, v);
+                        pass_load<T2, -1, MIXED>(rd, in, true, t, TPR, H, Ns, wtab, v);
                     } else {
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) v[q] = mk<T2>(T(0), T(0));
+                        for (int q = 0; q < PassRegs<MIXED>::n; ++q) v[q] = mk<T2>(T(0), T(0));
                     }
                 } else {
-                    pass_load<T2, -1>(rd, row, false, t, TPR, H, Ns, wtab, v);
+                    pass_load<T2, -1, MIXED>(rd, row, false, t, TPR, H, Ns, wtab, v);
                 }
             }
-            first = false;
             __syncthreads();
-            if (r < R) pass_store<T2>(rd, row, t, TPR, H, Ns, v);
+            if (r < R) pass_store<T2, MIXED>(rd, row, t, TPR, H, Ns, v);
             __syncthreads();
             Ns *= rd;
-            if (Ns == H) break;
-            rd = 16;
         }
     }
     __syncthreads();
@@ -358,7 +400,7 @@ __device__ __forceinline__ void fft_analys_tile(const PlanView<T> &pv, const T *
         for (int h = 0; h < 2; ++h) {
             const T2 *rw = buf + (2 * i + h) * ld;
             const T2 Zk = rw[padi(m)];
-            const T2 Zc = conj_(rw[padi((H - m) & (H - 1))]);
+            const T2 Zc = conj_(rw[padi((H - m) % H)]);
             T2 E = cadd(Zk, Zc), O = csub(Zk, Zc);
             E.x *= T(0.5); E.y *= T(0.5);
             const T2 Od = mk<T2>(O.y * T(0.5), -O.x * T(0.5));  // O / (2i)
@@ -382,12 +424,12 @@ __device__ __forceinline__ void fft_analys_tile(const PlanView<T> &pv, const T *
     }
 }
 
-template <typename T>
+template <typename T, bool MIXED>
 __global__ void __launch_bounds__(512)
-k_fft_analys(PlanView<T> pv, const T *__restrict__ grid, T *__restrict__ sd, int G, int logH, int op, int vector)
+k_fft_analys(PlanView<T> pv, const T *__restrict__ grid, T *__restrict__ sd, int G, int op, int vector)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fft_analys_tile<T>(pv, grid, sd, blockIdx.y, blockIdx.x * G, G, logH, op, vector, smem_raw);
+    fft_analys_tile<T, MIXED>(pv, grid, sd, blockIdx.y, blockIdx.x * G, G, op, vector, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -642,8 +684,9 @@ cudaError_t launch_rows_dispatch(int logH, bool synth, const PlanView<float> &pv
 }
 
 inline int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
+inline bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
-// Threads per row and pairs per CTA: TPR = H/16 threads per row (>= 1) and
+// Threads per row and pairs per CTA: TPR = ceil(H/16) threads per row and
 // enough rows for 256 threads, capped so the CTA's buffer stays <= 96 KB.
 // (512-thread CTAs read the intermediate in longer runs but fit one CTA per
 // SM and measured slower: the kernel is latency-bound, not DRAM-bound.)
@@ -651,7 +694,7 @@ template <typename T>
 void fft_shape(int H, int npairs, int &G, int &threads, size_t &smem)
 {
     using T2 = typename Vec2<T>::type;
-    const int TPR = H >= 16 ? H / 16 : 1;
+    const int TPR = row_tpr(H);
     int rows = 256 / TPR;
     if (rows < 2) rows = 2;
     const size_t row_bytes = (size_t)((H + (H >> 4)) + 1) * sizeof(T2);
@@ -678,15 +721,19 @@ cudaError_t launch_fft_synth(const PlanView<T> &pv, const T *eo, T *grid, int ba
 {
     const int H = pv.nphi / 2, logH = ilog2(H);
     if constexpr (sizeof(T) == 4) {
-        if (logH <= kRowLogMax) return launch_rows_dispatch(logH, true, pv, eo, grid, batch, op, false, s);
+        if (pow2(H) && logH <= kRowLogMax) return launch_rows_dispatch(logH, true, pv, eo, grid, batch, op, false, s);
     }
     int G, threads;
     size_t smem;
     fft_shape<T>(H, pv.npairs, G, threads, smem);
-    cudaError_t e = set_smem(k_fft_synth<T>, smem);
+    const bool mixed = !pow2(H);
+    cudaError_t e = mixed ? set_smem(k_fft_synth<T, true>, smem) : set_smem(k_fft_synth<T, false>, smem);
     if (e != cudaSuccess) return e;
     dim3 gridd((unsigned)((pv.npairs + G - 1) / G), (unsigned)batch);
-    k_fft_synth<T><<<gridd, threads, smem, s>>>(pv, eo, grid, G, logH, (int)op);
+    if (mixed)
+        k_fft_synth<T, true><<<gridd, threads, smem, s>>>(pv, eo, grid, G, (int)op);
+    else
+        k_fft_synth<T, false><<<gridd, threads, smem, s>>>(pv, eo, grid, G, (int)op);
     return cudaGetLastError();
 }
 
@@ -696,15 +743,20 @@ cudaError_t launch_fft_analys(const PlanView<T> &pv, const T *grid, T *sd, int b
 {
     const int H = pv.nphi / 2, logH = ilog2(H);
     if constexpr (sizeof(T) == 4) {
-        if (logH <= kRowLogMax) return launch_rows_dispatch(logH, false, pv, grid, sd, batch, op, vector, s);
+        if (pow2(H) && logH <= kRowLogMax)
+            return launch_rows_dispatch(logH, false, pv, grid, sd, batch, op, vector, s);
     }
     int G, threads;
     size_t smem;
     fft_shape<T>(H, pv.npairs, G, threads, smem);
-    cudaError_t e = set_smem(k_fft_analys<T>, smem);
+    const bool mixed = !pow2(H);
+    cudaError_t e = mixed ? set_smem(k_fft_analys<T, true>, smem) : set_smem(k_fft_analys<T, false>, smem);
     if (e != cudaSuccess) return e;
     dim3 gridd((unsigned)((pv.npairs + G - 1) / G), (unsigned)batch);
-    k_fft_analys<T><<<gridd, threads, smem, s>>>(pv, grid, sd, G, logH, (int)op, vector ? 1 : 0);
+    if (mixed)
+        k_fft_analys<T, true><<<gridd, threads, smem, s>>>(pv, grid, sd, G, (int)op, vector ? 1 : 0);
+    else
+        k_fft_analys<T, false><<<gridd, threads, smem, s>>>(pv, grid, sd, G, (int)op, vector ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -740,9 +792,9 @@ __global__ void __launch_bounds__(256, 2) k_batch_fft(int synth, const BatchFiel
             default: break;
             }
         } else if (synth) {
-            fft_synth_tile<float>(f.pv, f.inter, f.out, 0, tl.y, f.G, f.logH, OP_SYNTH, smem_raw);
+            fft_synth_tile<float, true>(f.pv, f.inter, f.out, 0, tl.y, f.G, OP_SYNTH, smem_raw);
         } else {
-            fft_analys_tile<float>(f.pv, f.in, f.inter, 0, tl.y, f.G, f.logH, OP_ANALYS, 0, smem_raw);
+            fft_analys_tile<float, true>(f.pv, f.in, f.inter, 0, tl.y, f.G, OP_ANALYS, 0, smem_raw);
         }
     }
 }
@@ -751,21 +803,19 @@ __global__ void __launch_bounds__(256, 2) k_batch_fft(int synth, const BatchFiel
 
 // Pairs per FFT tile for a 256-thread CTA: kRowPairs for the row FFTs
 // (logH <= 10), else 2G rows of max(1, H/16) threads.
-int batch_fft_group(int logH, int npairs)
+int batch_fft_group(int H, int npairs)
 {
-    if (logH <= kRowLogMax) return kRowPairs;
-    const int H = 1 << logH;
-    const int TPR = H >= 16 ? H / 16 : 1;
+    if (pow2(H) && ilog2(H) <= kRowLogMax) return kRowPairs;
+    const int TPR = row_tpr(H);
     int G = 256 / (2 * TPR);
     if (G < 1) G = 1;
     if (G > npairs) G = npairs < 1 ? 1 : npairs;
     return G;
 }
 
-size_t batch_fft_smem(int logH, int G)
+size_t batch_fft_smem(int H, int G)
 {
-    if (logH <= kRowLogMax) return row_fft_smem(row_ld(logH));
-    const int H = 1 << logH;
+    if (pow2(H) && ilog2(H) <= kRowLogMax) return row_fft_smem(row_ld(ilog2(H)));
     const size_t row_bytes = (size_t)((H + (H >> 4)) + 1) * sizeof(float2);
     return (size_t)H * sizeof(float2) + (size_t)2 * G * row_bytes;
 }

@@ -93,14 +93,14 @@ size_t padded(size_t count) { return (count * sizeof(U) + 255) & ~size_t(255); }
 PlanView<double> Plan::view64() const
 {
     PlanView<double> v{lmax, mmax, nlat, nphi, npairs, nlm,
-                       t64.ab, t64.dc, t64.x, t64.st, t64.wq, t64.pmm, t64.pmmk, t64.tw, t64.rtw};
+                       t64.ab, t64.dc, t64.x, t64.st, t64.wq, t64.pmm, t64.pmmk, t64.tw, t64.rtw, fft_plan_of(nphi / 2)};
     return v;
 }
 
 PlanView<float> Plan::view32() const
 {
     PlanView<float> v{lmax, mmax, nlat, nphi, npairs, nlm,
-                      t32.ab, t32.dc, t32.x, t32.st, t32.wq, t32.pmm, t32.pmmk, t32.tw, t32.rtw};
+                      t32.ab, t32.dc, t32.x, t32.st, t32.wq, t32.pmm, t32.pmmk, t32.tw, t32.rtw, fft_plan_of(nphi / 2)};
     return v;
 }
 

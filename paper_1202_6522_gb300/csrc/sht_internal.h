@@ -57,7 +57,34 @@ struct PlanView {
     const int *pmmk;
     const T2 *tw;
     const T2 *rtw;
+    unsigned long long fftplan;   // radices of the FFT of length nphi/2 (fft_plan_of)
 };
+
+// Pass plan of a mixed-radix FFT of length H = 2^a 3^b 5^c: bits 0-3 the
+// number of passes (none for H = 1), then 5 bits per pass radix (2, 4, 8, 16,
+// 3 or 5), the power-of-two part first.  kFftPlanBad if H has another prime
+// factor or needs more than 12 passes.
+constexpr unsigned long long kFftPlanBad = ~0ull;
+inline unsigned long long fft_plan_of(int H)
+{
+    if (H < 1) return kFftPlanBad;
+    int a = 0, b = 0, c = 0, h = H;
+    while (h % 2 == 0) { h /= 2; ++a; }
+    while (h % 3 == 0) { h /= 3; ++b; }
+    while (h % 5 == 0) { h /= 5; ++c; }
+    if (h != 1) return kFftPlanBad;
+    int rad[16], n = 0;
+    if (a % 4) rad[n++] = 1 << (a % 4);
+    for (int i = 0; i < a / 4; ++i) rad[n++] = 16;
+    for (int i = 0; i < b; ++i) rad[n++] = 3;
+    for (int i = 0; i < c; ++i) rad[n++] = 5;
+    if (n > 12) return kFftPlanBad;
+    unsigned long long p = (unsigned long long)n;
+    for (int i = 0; i < n; ++i) p |= (unsigned long long)rad[i] << (4 + 5 * i);
+    return p;
+}
+__host__ __device__ inline int fft_plan_npass(unsigned long long p) { return (int)(p & 15u); }
+__host__ __device__ inline int fft_plan_radix(unsigned long long p, int i) { return (int)((p >> (4 + 5 * i)) & 31u); }
 
 // What a Legendre or FFT launch computes; selects the scale factors.
 enum Op {
@@ -161,7 +188,7 @@ struct BatchField {
     const float *in;   // spectra (synthesis) or grid (analysis)
     float *out;        // grid (synthesis) or spectra (analysis)
     float *inter;      // E/O (synthesis) or s/d folds (analysis) of this field
-    int logH, G;       // FFT length log2(nphi/2) and pairs per FFT tile
+    int logH, G;       // log2(nphi/2) (kRowLogMax + 1 or more when not a power of two) and pairs per FFT tile
 };
 
 // Persistent kernels over a tile list: each CTA takes the next tile from
@@ -171,12 +198,12 @@ cudaError_t launch_batch_legendre(bool synth, const BatchField *fields, const in
                                   int ctas, cudaStream_t s);
 cudaError_t launch_batch_fft(bool synth, const BatchField *fields, const int4 *tiles, int ntiles, int *counter,
                              int ctas, size_t smem, cudaStream_t s);
-size_t batch_fft_smem(int logH, int G);
+size_t batch_fft_smem(int H, int G);
 cudaError_t batch_fft_prepare(size_t smem);   // once, outside any stream capture
 
 // Records an error message for sht_last_error and returns `code`.
 int set_error(int code, const std::string &msg);
-int batch_fft_group(int logH, int npairs);
+int batch_fft_group(int H, int npairs);
 constexpr int kBatchSynthPairs = 256;   // pairs per synthesis tile (128 threads x 2)
 constexpr int kBatchMaxPairs = 512;     // analysis CTA (256 threads x 2 pairs) limit
 

@@ -52,7 +52,8 @@ def test_binding_covers_every_symbol(lib):
     ((10, 11, 16, 32), -1),  # mmax > lmax
     ((10, 10, 10, 32), -1),  # nlat < lmax + 1 (quadrature not exact)
     ((10, 10, 11, 20), -1),  # nphi < 2 mmax + 1
-    ((10, 10, 11, 24), -5),  # nphi not a power of two
+    ((10, 10, 11, 28), -5),  # nphi / 2 = 14 has the factor 7 (FFT lengths are 2^a 3^b 5^c)
+    ((10, 10, 11, 25), -5),  # nphi odd
 ])
 def test_create_rejects_bad_sizes_on_host(lib, args, code):
     h = ctypes.c_void_p()
