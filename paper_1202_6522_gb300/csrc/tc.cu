@@ -269,61 +269,6 @@ struct TcArgs {
     int *err;
 };
 
-// Thread 0's part of a contraction: streams chunks cstart .. cstart + nlive - 1
-// (S - 1 ahead) into the stage ring, calls mma(stage, data, first) for each,
-// and commits the MMAs to bar_done.  Returns false after a timed-out wait.
-template <int NP, typename MmaFn>
-__device__ __forceinline__ bool produce(const TcArgs &a, unsigned char *smem, size_t stage_bytes, uint64_t *bar_load,
-                                        uint64_t *bar_mma, uint64_t *bar_done, const unsigned char *panel0,
-                                        const unsigned char *panel1, const unsigned char *data, int cstart, int nlive,
-                                        MmaFn &&mma)
-{
-    const int S = a.stages;
-    const uint32_t dbytes = (uint32_t)data_chunk_bytes(a.rows);
-    const uint32_t tx = (uint32_t)NP * kChunkPanel + dbytes;
-    bool ok = true;
-    int issued[4] = {0, 0, 0, 0}, waited[4] = {0, 0, 0, 0};
-    auto issue = [&](int un) {
-        const int sn = un % S;
-        unsigned char *st = smem + (size_t)sn * stage_bytes;
-        const size_t c = (size_t)(cstart + un);
-        tc::mbar_arrive_expect_tx(&bar_load[sn], tx);
-        tc::bulk_g2s(st, panel0 + c * kChunkPanel, kChunkPanel, &bar_load[sn]);
-        if (NP == 2) tc::bulk_g2s(st + kChunkPanel, panel1 + c * kChunkPanel, kChunkPanel, &bar_load[sn]);
-        tc::bulk_g2s(st + (size_t)NP * kChunkPanel, data + c * dbytes, dbytes, &bar_load[sn]);
-        issued[sn] += 1;
-    };
-    const int D = S - 1;
-    for (int u = 0; u < D && u < nlive; ++u) issue(u);
-    for (int u = 0; u < nlive; ++u) {
-        const int q = u % S;
-        const int un = u + D;
-        if (un < nlive) {
-            if (un >= S) {
-                // chunk un goes to the stage of chunk un - S == u - 1: wait for its MMAs
-                const int up = un - S;
-                if (!tc::mbar_wait_bounded(&bar_mma[up % S], (uint32_t)((up / S) & 1), kWaitNs)) { ok = false; break; }
-            }
-            issue(un);
-        }
-        if (!tc::mbar_wait_bounded(&bar_load[q], (uint32_t)((u / S) & 1), kWaitNs)) { ok = false; break; }
-        waited[q] += 1;
-        tc::tc_fence_after();
-        unsigned char *st = smem + (size_t)q * stage_bytes;
-        mma(st, st + (size_t)NP * kChunkPanel, u == 0);
-        tc::mma_commit(&bar_mma[q]);
-    }
-    if (!ok) {
-        raise_err(a.err, SHT_ETIMEOUT);
-        // wait (bounded) for this CTA's own copies in flight before it exits
-        for (int q = 0; q < S; ++q)
-            if (issued[q] > waited[q])
-                (void)tc::mbar_wait_bounded(&bar_load[q], (uint32_t)((issued[q] - 1) & 1), 100000000ull);
-    }
-    tc::mma_commit(bar_done);  // arrives once every MMA issued above has completed
-    return ok;
-}
-
 // Common prologue: barriers, TMEM allocation.  Returns the TMEM base.
 __device__ __forceinline__ uint32_t setup_ctas(int S, uint64_t *bar_load, uint64_t *bar_mma, uint64_t *bar_done,
                                                uint32_t *tslot, uint32_t ncols, int *s_ok)
@@ -714,11 +659,44 @@ __global__ void __launch_bounds__(128, 1) k_tc_vec(TcArgs a)
     const int nlive = nchunks - cstart;
 
     const uint32_t tmem = setup_ctas(S, bar_load, bar_mma, bar_done, tslot, ncols, &s_ok);
+    __shared__ int s_abort;
+    if (tid == 0) s_abort = 0;
+    __syncthreads();
 
-    if (tid == 0) {
+    if (tid == 32) {
+        // ---------------- producer (warp 1 lane 0): P, dP and data chunks, S - 1 ahead ----------------
+        const unsigned char *p0 = a.panel + poff, *p1 = a.dpanel + poff;
+        const uint32_t dbytes = (uint32_t)data_chunk_bytes(NV);
+        bool okp = true;
+        int issued = 0;
+        for (int u = 0; u < nlive; ++u) {
+            const int q = u % S;
+            const size_t c = (size_t)(cstart + u);
+            if (u >= S && !wait_or_abort(&bar_mma[q], (uint32_t)((u / S - 1) & 1), &s_abort)) { okp = false; break; }
+            unsigned char *st = smem + (size_t)q * stage_bytes;
+            tc::mbar_arrive_expect_tx(&bar_load[q], 2u * kChunkPanel + dbytes);
+            tc::bulk_g2s(st, p0 + c * kChunkPanel, kChunkPanel, &bar_load[q]);
+            tc::bulk_g2s(st + kChunkPanel, p1 + c * kChunkPanel, kChunkPanel, &bar_load[q]);
+            tc::bulk_g2s(st + 2 * kChunkPanel, data + c * dbytes, dbytes, &bar_load[q]);
+            issued = u + 1;
+        }
+        if (!okp) {
+            raise_err(a.err, SHT_ETIMEOUT);
+            s_ok = 0;
+            for (int v = max(0, issued - S); v < issued; ++v)
+                (void)tc::mbar_wait_bounded(&bar_load[v % S], (uint32_t)((v / S) & 1), 100000000ull);
+        }
+    } else if (tid == 0) {
+        // ---------------- MMA issuer (warp 0 lane 0) ----------------
         const uint32_t idesc = tc::idesc_bf16_f32(kRows, NV);
-        const bool ok = produce<2>(a, smem, stage_bytes, bar_load, bar_mma, bar_done, a.panel + poff, a.dpanel + poff,
-                                   data, cstart, nlive, [&](unsigned char *st, unsigned char *dat, bool first) {
+        bool okm = true;
+        for (int u = 0; u < nlive; ++u) {
+            const int q = u % S;
+            if (!wait_or_abort(&bar_load[q], (uint32_t)((u / S) & 1), &s_abort)) { okm = false; break; }
+            tc::tc_fence_after();
+            unsigned char *st = smem + (size_t)q * stage_bytes;
+            unsigned char *dat = st + 2 * kChunkPanel;
+            const bool first = u == 0;
 #pragma unroll
             for (int cls = 0; cls < 2; ++cls) {
                 const int dp = SYNTH ? 1 - cls : cls;   // parity of n - m of the dP block
@@ -739,8 +717,13 @@ __global__ void __launch_bounds__(128, 1) k_tc_vec(TcArgs a)
                 tc::mma_bf16(d2, Adh, B2l, idesc, true);
                 tc::mma_bf16(d2, Adl, B2h, idesc, true);
             }
-        });
-        if (!ok) s_ok = 0;
+            tc::mma_commit(&bar_mma[q]);
+        }
+        if (!okm) {
+            raise_err(a.err, SHT_ETIMEOUT);
+            s_ok = 0;
+        }
+        tc::mma_commit(bar_done);   // arrives once every MMA issued above has completed
     }
     bool ok = tc::mbar_wait_bounded(bar_done, 0, 2 * kWaitNs);
     if (!ok) raise_err(a.err, SHT_ETIMEOUT);
