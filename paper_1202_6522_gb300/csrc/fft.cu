@@ -478,7 +478,7 @@ __device__ __forceinline__ void fft_synth_rows_tile(const PlanView<float> &pv, c
     const int mmax = pv.mmax, npairs = pv.npairs, nlat = pv.nlat;
     // 1. spectra of the CTA's rows: X_north = E + O, X_south = E - O, zero above
     //    mmax; the loads of a batch of U items are issued before their stores
-    constexpr int NT = 64 * kRowPairs, NQ = kRowPairs * H, U = 8;
+    constexpr int NT = 64 * kRowPairs, NQ = kRowPairs * H, U = 16;
     const float4 *eo4 = reinterpret_cast<const float4 *>(eo);
 #pragma unroll 1
     for (int q0 = threadIdx.x; q0 < NQ; q0 += U * NT) {
