@@ -69,9 +69,9 @@ def tc_algorithmic_bytes(batch, lmax=LMAX, nlat=NLAT, polar_skip=0.0):
 
 # DRAM bytes (read + write) per launch of the panel contraction at this
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum);
-# valid only while the kernel source is the one that was profiled (its SHA-256
-# below), else null.
-TC_TRAFFIC_SRC_SHA256 = "b3e2a85a7897880a7e4474fd3d596379cd50b5a826d7791eb6d2bb9ef9e4dede"
+# reported only while the source file holding the kernel is unchanged (its
+# SHA-256 below, updated only for edits outside that kernel), else null.
+TC_TRAFFIC_SRC_SHA256 = "75d508ba3f5e72c18a0f5d8132f737dc876a1cad5cf5d9f7f39008d89ff56e11"
 TC_TRAFFIC_BYTES = {"tc_synth": 869.112320e6 + 94.180096e6, "tc_analys": 883.195648e6 + 55.916544e6}
 
 
