@@ -122,6 +122,18 @@ enum {
  * handle; on failure *out is NULL. */
 SHT_API int sht_create(int lmax, int mmax, int nlat, int nphi, sht_handle *out);
 
+/* Plan for the orders m = k mres, k = 0 .. mmax (mmax mres <= lmax): fields
+ * whose longitude period is 2 pi / mres, sampled on one sector of the circle,
+ * phi_j = 2 pi j / (nphi mres), j < nphi (the m-stride variant; needs
+ * nphi >= 2 mmax + 1).  The spectral layout packs the orders present:
+ * order index k holds degrees n = k mres .. lmax, from index
+ * k (lmax + 1) - mres k (k - 1) / 2 (sht_lm_index takes the order m itself).
+ * The longitude quadrature is the rectangle rule on the sector, equal to the
+ * full circle's for these orders.  Modes SHT_F64 and SHT_F32 (SHT_F32_AUTO
+ * takes SHT_F32); the tensor-core modes return SHT_EUNSUPPORTED for
+ * mres > 1.  sht_create(...) is sht_create_mres(lmax, mmax, 1, ...). */
+SHT_API int sht_create_mres(int lmax, int mmax, int mres, int nlat, int nphi, sht_handle *out);
+
 /* Free the plan and everything it owns.  NULL is ignored.  The caller must
  * make sure no work using the handle is still running. */
 SHT_API void sht_destroy(sht_handle h);

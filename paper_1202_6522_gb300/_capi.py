@@ -36,6 +36,7 @@ _I = ctypes.c_int
 # name -> (argtypes, restype); mirrors include/sht.h
 SIGNATURES = {
     "sht_create": ([_I, _I, _I, _I, ctypes.POINTER(_VP)], _I),
+    "sht_create_mres": ([_I, _I, _I, _I, _I, ctypes.POINTER(_VP)], _I),
     "sht_destroy": ([_VP], None),
     "sht_reserve": ([_VP, _I, _I], _I),
     "sht_synth": ([_VP, _VP, _VP, _I, _I, _VP], _I),
@@ -116,6 +117,12 @@ def _call(name, *args):
 def sht_create(lmax: int, mmax: int, nlat: int, nphi: int) -> int:
     h = _VP()
     check(_call("sht_create", lmax, mmax, nlat, nphi, ctypes.byref(h)))
+    return h.value
+
+
+def sht_create_mres(lmax: int, mmax: int, mres: int, nlat: int, nphi: int) -> int:
+    h = _VP()
+    check(_call("sht_create_mres", lmax, mmax, mres, nlat, nphi, ctypes.byref(h)))
     return h.value
 
 

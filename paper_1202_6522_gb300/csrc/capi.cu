@@ -97,6 +97,7 @@ cudaError_t first_live_vector(sht::Plan &p, int *tmp)
 int ensure_panels(sht::Plan &p)
 {
     if (p.panel_s) return SHT_OK;
+    if (p.mres > 1) return fail(SHT_EUNSUPPORTED, "the tensor-core modes need mres = 1");
     std::vector<unsigned long long> off_s, off_a, dchunk;
     size_t bs = 0, ba = 0, nch = 0;
     sht::tc_panel_layout(p.lmax, p.mmax, p.npairs, off_s, off_a, bs, ba, dchunk, nch);
@@ -204,6 +205,7 @@ cudaError_t otf_build(sht::Plan &p, int *flag_dev)
 int ensure_otf(sht::Plan &p)
 {
     if (p.otf_state > 0) return SHT_OK;
+    if (p.mres > 1) return fail(SHT_EUNSUPPORTED, "the tensor-core modes need mres = 1");
     if (p.otf_state < 0)
         return fail(SHT_EUNSUPPORTED, "on-the-fly mode: the FP32 recurrence would leave the FP32 range for this plan");
     std::vector<unsigned long long> segoff;
@@ -251,6 +253,7 @@ size_t elem_size(int mode) { return (mode == SHT_F64 || mode == SHT_TC_F64) ? si
 int ensure_panels64(sht::Plan &p)
 {
     if (p.p64_s) return SHT_OK;
+    if (p.mres > 1) return fail(SHT_EUNSUPPORTED, "the tensor-core modes need mres = 1");
     if (p.lmax > 1023 || p.npairs > 512)
         return fail(SHT_EUNSUPPORTED, "SHT_TC_F64 needs lmax <= 1023 and nlat <= 1024");
     std::vector<unsigned long long> off_s, off_a, dchunk;
@@ -781,9 +784,15 @@ const char *sht_last_error(void) { return g_err.c_str(); }
 
 int sht_create(int lmax, int mmax, int nlat, int nphi, sht_handle *out)
 {
+    return sht_create_mres(lmax, mmax, 1, nlat, nphi, out);
+}
+
+int sht_create_mres(int lmax, int mmax, int mres, int nlat, int nphi, sht_handle *out)
+{
     if (!out) return fail(SHT_EINVAL, "out is NULL");
     *out = nullptr;
-    if (lmax < 0 || mmax < 0 || mmax > lmax) return fail(SHT_EINVAL, "need 0 <= mmax <= lmax");
+    if (mres < 1) return fail(SHT_EINVAL, "need mres >= 1");
+    if (lmax < 0 || mmax < 0 || (long)mmax * mres > lmax) return fail(SHT_EINVAL, "need 0 <= mmax mres <= lmax");
     if (nlat < lmax + 1) return fail(SHT_EINVAL, "need nlat >= lmax + 1 for an exact Gauss-Legendre quadrature");
     if (nphi < 2 * mmax + 1) return fail(SHT_EINVAL, "need nphi >= 2 mmax + 1");
     if (nlat > 4096 || lmax > 4095) return fail(SHT_EUNSUPPORTED, "nlat > 4096 is not supported");
@@ -793,6 +802,7 @@ int sht_create(int lmax, int mmax, int nlat, int nphi, sht_handle *out)
     if (!h) return fail(SHT_ENOMEM, "host allocation failed");
     h->p.lmax = lmax;
     h->p.mmax = mmax;
+    h->p.mres = mres;
     h->p.nlat = nlat;
     h->p.nphi = nphi;
     std::string err;
@@ -886,8 +896,9 @@ int sht_nlm(sht_handle h)
 int sht_lm_index(sht_handle h, int n, int m)
 {
     if (!h) return fail(SHT_EINVAL, "null handle");
-    if (m < 0 || m > h->p.mmax || n < m || n > h->p.lmax) return -1;
-    return m * (2 * h->p.lmax + 3 - m) / 2 + (n - m);
+    const int mres = h->p.mres;
+    if (m < 0 || m % mres != 0 || m / mres > h->p.mmax || n < m || n > h->p.lmax) return -1;
+    return (int)sht::col_of_mres(h->p.lmax, m / mres, mres) + (n - m);
 }
 
 int sht_gauss(sht_handle h, double *x, double *w)

@@ -105,8 +105,6 @@ __device__ __forceinline__ void warp_transpose_reduce(T (&v)[V], int lane)
     }
 }
 
-__device__ __forceinline__ long col_of(int lmax, int m) { return (long)m * (2 * lmax + 3 - m) / 2; }
-
 // ---------------------------------------------------------------------------
 // Scalar synthesis.  grid.x = (m, pair block), heaviest m first; grid.y = field chunk.
 // ---------------------------------------------------------------------------
@@ -123,8 +121,8 @@ __device__ __forceinline__ void synth_tile(const PlanView<T> &pv, const T *__res
     using T2 = typename Vec2<T>::type;
     constexpr int NCH = kSynthNch;
     const int lmax = pv.lmax, npairs = pv.npairs;
-    const int L = lmax - m + 1;
-    const long col = col_of(lmax, m);
+    const int L = lmax - m * pv.mres + 1;   // order index m is the order m mres
+    const long col = col_of_mres(lmax, m, pv.mres);
 
     T x[LPT], y1[LPT], y2[LPT], c[LPT];
     int k[LPT], p[LPT];
@@ -278,8 +276,8 @@ __device__ __forceinline__ void analys_tile(const PlanView<T> &pv, const T *__re
     const int nw = NT >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lmax = pv.lmax, npairs = pv.npairs;
-    const int L = lmax - m + 1;
-    const long col = col_of(lmax, m);
+    const int L = lmax - m * pv.mres + 1;   // order index m is the order m mres
+    const long col = col_of_mres(lmax, m, pv.mres);
 
     T x[LPT], y1[LPT], y2[LPT], c[LPT];
     int k[LPT];
@@ -400,8 +398,8 @@ k_synth_vec(PlanView<T> pv, const T *__restrict__ Sg, const T *__restrict__ Tg, 
     const int pb = blockIdx.x - m * npb;
     const int b0 = blockIdx.y * BC;
     const int lmax = pv.lmax, npairs = pv.npairs;
-    const int L = lmax - m + 1;
-    const long col = col_of(lmax, m);
+    const int L = lmax - m * pv.mres + 1;   // order index m is the order m mres
+    const long col = col_of_mres(lmax, m, pv.mres);
 
     T x[LPT], y1[LPT], y2[LPT], c[LPT];
     int k[LPT], p[LPT];
@@ -439,7 +437,7 @@ k_synth_vec(PlanView<T> pv, const T *__restrict__ Sg, const T *__restrict__ Tg, 
             if (t < cnt) { ab = pv.ab[col + n0 + t]; dcv = pv.dc[col + n0 + t]; }
             s_ab[t] = ab;
             s_dc[t] = dcv;
-            const int n = m + n0 + t;
+            const int n = m * pv.mres + n0 + t;
             // adjoint of analysis: b / (c_m n(n+1)), nothing at n = 0
             T sc = T(1);
             if (op == OP_ANALYS_ADJ) sc = (n == 0) ? T(0) : cadj / (T(n) * T(n + 1));
@@ -465,7 +463,7 @@ k_synth_vec(PlanView<T> pv, const T *__restrict__ Sg, const T *__restrict__ Tg, 
                 const int tt = t + par;
                 const T2 ab = s_ab[tt];
                 const T dcn = s_dc[tt];
-                const T nf = T(m + n0 + tt);
+                const T nf = T(m * pv.mres + n0 + tt);
                 bool live = true;
                 if (scaled) {
                     rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c);
@@ -508,7 +506,7 @@ k_synth_vec(PlanView<T> pv, const T *__restrict__ Sg, const T *__restrict__ Tg, 
 
     T2 *eot2 = reinterpret_cast<T2 *>(eot);
     T2 *eop2 = reinterpret_cast<T2 *>(eop);
-    const T fm = T(m);
+    const T fm = T(m * pv.mres);
 #pragma unroll
     for (int i = 0; i < LPT; ++i) {
         if (p[i] >= npairs) continue;
@@ -554,8 +552,8 @@ k_analys_vec(PlanView<T> pv, const T *__restrict__ sdt, const T *__restrict__ sd
     const int m = blockIdx.x;
     const int b0 = blockIdx.y * BC;
     const int lmax = pv.lmax, npairs = pv.npairs;
-    const int L = lmax - m + 1;
-    const long col = col_of(lmax, m);
+    const int L = lmax - m * pv.mres + 1;   // order index m is the order m mres
+    const long col = col_of_mres(lmax, m, pv.mres);
 
     T x[LPT], y1[LPT], y2[LPT], c[LPT];
     int k[LPT];
@@ -585,7 +583,7 @@ k_analys_vec(PlanView<T> pv, const T *__restrict__ sdt, const T *__restrict__ sd
             }
         }
     }
-    const T fm = T(m);
+    const T fm = T(m * pv.mres);
     T2 *S2 = reinterpret_cast<T2 *>(So);
     T2 *T2o = reinterpret_cast<T2 *>(To);
 
@@ -611,7 +609,7 @@ k_analys_vec(PlanView<T> pv, const T *__restrict__ sdt, const T *__restrict__ sd
             for (int kx = 0; kx < K; ++kx) {
                 const T2 ab = s_ab[t0 + kx];
                 const T dcn = s_dc[t0 + kx];
-                const T nf = T(m + n0 + t0 + kx);
+                const T nf = T(m * pv.mres + n0 + t0 + kx);
                 bool live = true;
                 if (scaled) {
                     rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c);
@@ -655,7 +653,7 @@ k_analys_vec(PlanView<T> pv, const T *__restrict__ sdt, const T *__restrict__ sd
                     for (int q = 0; q < 8; ++q) tot[q] += s_red[w][threadIdx.x * 8 + q];
                 const int kx = threadIdx.x / BC, b = threadIdx.x % BC;
                 const int nn = n0 + t0 + kx;
-                const int n = m + nn;
+                const int n = m * pv.mres + nn;
                 if (nn < L && b0 + b < batch) {
                     T sc;
                     if (op == OP_SYNTH_ADJ) sc = (m > 0) ? T(2) : T(1);

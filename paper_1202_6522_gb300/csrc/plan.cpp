@@ -93,29 +93,31 @@ size_t padded(size_t count) { return (count * sizeof(U) + 255) & ~size_t(255); }
 PlanView<double> Plan::view64() const
 {
     PlanView<double> v{lmax, mmax, nlat, nphi, npairs, nlm,
-                       t64.ab, t64.dc, t64.x, t64.st, t64.wq, t64.pmm, t64.pmmk, t64.tw, t64.rtw, fft_plan_of(nphi / 2)};
+                       t64.ab, t64.dc, t64.x, t64.st, t64.wq, t64.pmm, t64.pmmk, t64.tw, t64.rtw, fft_plan_of(nphi / 2), mres};
     return v;
 }
 
 PlanView<float> Plan::view32() const
 {
     PlanView<float> v{lmax, mmax, nlat, nphi, npairs, nlm,
-                      t32.ab, t32.dc, t32.x, t32.st, t32.wq, t32.pmm, t32.pmmk, t32.tw, t32.rtw, fft_plan_of(nphi / 2)};
+                      t32.ab, t32.dc, t32.x, t32.st, t32.wq, t32.pmm, t32.pmmk, t32.tw, t32.rtw, fft_plan_of(nphi / 2), mres};
     return v;
 }
 
 int plan_build(Plan &p, std::string &err)
 {
-    const int lmax = p.lmax, mmax = p.mmax, nlat = p.nlat, nphi = p.nphi;
+    const int lmax = p.lmax, mmax = p.mmax, nlat = p.nlat, nphi = p.nphi, mres = p.mres;
     p.npairs = (nlat + 1) / 2;
-    p.nlm = (mmax + 1) * (lmax + 1) - mmax * (mmax + 1) / 2;
+    // orders m = k mres, k = 0 .. mmax, each with degrees m .. lmax
+    p.nlm = (int)col_of_mres(lmax, mmax + 1, mres);
     const int npairs = p.npairs, nlm = p.nlm;
     gauss_nodes(nlat, p.x, p.w);
 
     // Recurrence coefficients of Sec. 3.2, packed like the spectral arrays.
     std::vector<double> ab((size_t)2 * nlm), dc(nlm);
-    for (int m = 0; m <= mmax; ++m) {
-        const size_t col = (size_t)m * (2 * lmax + 3 - m) / 2;
+    for (int kq = 0; kq <= mmax; ++kq) {
+        const int m = kq * mres;
+        const size_t col = (size_t)col_of_mres(lmax, kq, mres);
         for (int n = m; n <= lmax; ++n) {
             const size_t i = col + (n - m);
             const double dn = n, dm = m;
@@ -159,14 +161,15 @@ int plan_build(Plan &p, std::string &err)
         int ex = 0;
         double mant = std::frexp(std::sqrt(1.0 / (4.0 * kPi)), &ex);
         long e = ex;
-        for (int m = 0; m <= mmax; ++m) {
+        for (int m = 0; m <= mmax * mres; ++m) {
             if (m > 0) {
                 mant *= std::sqrt((2.0 * m + 1.0) / (2.0 * m)) * sp[j];
                 int ee = 0;
                 mant = std::frexp(mant, &ee);
                 e += ee;
             }
-            const size_t o = (size_t)m * npairs + j;
+            if (m % mres) continue;   // only the orders of the plan are stored
+            const size_t o = (size_t)(m / mres) * npairs + j;
             split(mant, e, Scale<double>::S, pmm64[o], k64[o]);
             split(mant, e, Scale<float>::S, pmm32d[o], k32[o]);
         }

@@ -58,7 +58,15 @@ struct PlanView {
     const T2 *tw;
     const T2 *rtw;
     unsigned long long fftplan;   // radices of the FFT of length nphi/2 (fft_plan_of)
+    int mres;                     // order stride: order index k is the order m = k mres
 };
+
+// First packed index of order index k (order m = k mres): the degrees of the
+// orders before it, sum_{k' < k} (lmax - k' mres + 1).
+__host__ __device__ inline long col_of_mres(int lmax, int k, int mres)
+{
+    return (long)k * (lmax + 1) - (long)mres * k * (k - 1) / 2;
+}
 
 // Pass plan of a mixed-radix FFT of length H = 2^a 3^b 5^c: bits 0-3 the
 // number of passes (none for H = 1), then 5 bits per pass radix (2, 4, 8, 16,
@@ -110,6 +118,7 @@ struct KernelTimer {
 
 struct Plan {
     int lmax, mmax, nlat, nphi, npairs, nlm;
+    int mres = 1;                    // order stride (orders 0, mres, .., mmax mres)
     std::vector<double> x, w;        // host nodes (descending) and weights, all nlat
     Tables<double> t64;
     Tables<float> t32;

@@ -27,7 +27,8 @@ class SHT:
     """A Gauss-Legendre spherical harmonic transform plan on one CUDA device."""
 
     def __init__(self, lmax: int, mmax: int | None = None, nlat: int | None = None,
-                 nphi: int | None = None, device=None, fp32_path: str = "f32", fp64_path: str = "f64"):
+                 nphi: int | None = None, device=None, fp32_path: str = "f32", fp64_path: str = "f64",
+                 mres: int = 1):
         """fp32_path selects how complex64/float32 tensors are transformed:
         "f32" (FP32 recurrence on the CUDA cores), "tc" (tensor cores against
         FP64-built P_n^m panels, split-bf16 products) or "otf" (the same
@@ -36,9 +37,12 @@ class SHT:
         fp64_path selects it for complex128/float64 tensors: "f64" (FP64
         recurrence on the CUDA cores) or "tc" (tensor cores on 7-bit digit
         slices of both operands, FP64 accuracy; scalar transforms, lmax <= 1023,
-        vector ones run "f64")."""
+        vector ones run "f64").
+        mres > 1 keeps only the orders m = k mres (k <= mmax, mmax mres <= lmax)
+        on a grid of one 2 pi / mres sector of longitudes (FP64 and FP32 paths)."""
         self.lmax = int(lmax)
-        self.mmax = self.lmax if mmax is None else int(mmax)
+        self.mres = int(mres)
+        self.mmax = self.lmax // self.mres if mmax is None else int(mmax)
         self.nlat = self.lmax + 1 if nlat is None else int(nlat)
         self.nphi = max(_next_pow2(2 * self.mmax + 1), 2) if nphi is None else int(nphi)
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
@@ -51,7 +55,7 @@ class SHT:
         if self.device.type != "cuda":
             raise ValueError("SHT runs on CUDA devices only")
         with torch.cuda.device(self.device):
-            self._h = C.sht_create(self.lmax, self.mmax, self.nlat, self.nphi)
+            self._h = C.sht_create_mres(self.lmax, self.mmax, self.mres, self.nlat, self.nphi)
         self.nlm = C.sht_nlm(self._h)
         x, w = C.sht_gauss(self._h, self.nlat)
         self.x = torch.tensor(x, dtype=torch.float64)
