@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc64(Tc64Args a)
                         tc::tmem_ld16(lane_base + (uint32_t)(t * kLevelCols + 16 * h), v);
 #pragma unroll
                         for (int k = 0; k < 16; ++k) {
-                            const long long L = __float2ll_rn(v[k]);
+                            const long long L = __float2int_rn(v[k]);   // an integer below 2^24
                             if (t < kL / 2) Zh[k] += L << (7 * (kL / 2 - 1 - t));
                             else Zl[k] += L << (7 * (kL - 1 - t));
                         }
