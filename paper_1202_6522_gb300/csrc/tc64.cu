@@ -287,65 +287,63 @@ __global__ void k_fill_int(int *__restrict__ a, int v, size_t n)
 // row = 32 slice + 2 field + (re|im).  Synthesis chunk (m, c) = degrees
 // n - m in [2 kKc c, 2 kKc (c + 1)), class = parity of n - m, numbered from
 // dchunk[m]; analysis chunk (m, kc) = pairs [kKc kc, kKc (kc + 1)), class
-// 0 = s fold, 1 = d fold, numbered m kch + kc.  One thread per (field,
-// degree or pair) of a chunk.
+// 0 = s fold, 1 = d fold, numbered m kch + kc.  One thread per (chunk, class,
+// field, re|im, half of the K positions): it splits 8 values and writes each
+// slice's 8 digits as one 16-byte core-matrix row.
 __global__ void k_prep64(int synth, int lmax, int mmax, int npairs, int nlm, int batch, int op,
                          const double *__restrict__ in, const int *__restrict__ f,
                          const unsigned long long *__restrict__ dchunk, unsigned char *__restrict__ data)
 {
     const int m = blockIdx.y;
     const int L = lmax - m + 1, Le = (L + 1) / 2;
-    const int per = synth ? 2 * kKc : kKc;                    // degrees or pairs per chunk
     const int nchunks = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
     const long item = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (item >= (long)nchunks * batch * per) return;
-    const int c = (int)(item / (batch * per));
-    const int r = (int)(item - (long)c * batch * per);
-    const int b = r / per, j = r - b * per;
+    const int per = 8 * batch;                                // items per chunk
+    if (item >= (long)nchunks * per) return;
+    const int c = (int)(item / per);
+    int r = (int)(item - (long)c * per);
+    const int kh = r & 1, q = (r >> 1) & 1;                   // K half, re|im
+    r >>= 2;
+    const int b = r % batch, cls = r / batch;
     const int e = f[b];
-    int dv[2][kSB];
-    unsigned char *chunk;
+    double v[8];
     if (synth) {
         const long col = col_of(lmax, m);
-        const int nn = 2 * kKc * c + j;
-        double re = 0.0, im = 0.0;
-        if (nn < L) {
-            const double2 v = reinterpret_cast<const double2 *>(in)[(size_t)b * nlm + col + nn];
-            re = v.x;
-            im = m == 0 ? 0.0 : v.y;
-            if (op == OP_ANALYS_ADJ && m > 0) {   // adjoint factor 1/2
-                re *= 0.5;
-                im *= 0.5;
-            }
+        const double sc = (op == OP_ANALYS_ADJ && m > 0) ? 0.5 : 1.0;   // adjoint factor 1/2
+        const double2 *spec = reinterpret_cast<const double2 *>(in) + (size_t)b * nlm + col;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int nn = 2 * kKc * c + 2 * (8 * kh + i) + cls;
+            double x = 0.0;
+            if (nn < L && !(q == 1 && m == 0)) x = q ? spec[nn].y : spec[nn].x;
+            v[i] = sc == 1.0 ? x : x * sc;
         }
-        digits_int(re, e, dv[0]);
-        digits_int(im, e, dv[1]);
-        chunk = data + (size_t)(dchunk[m] + c) * kDChunk + (size_t)(j & 1) * kDBlk;
-        const int k = j >> 1;
-#pragma unroll
-        for (int s = 0; s < kSB; ++s)
-#pragma unroll
-            for (int q = 0; q < 2; ++q)
-                *reinterpret_cast<__nv_bfloat16 *>(chunk + blk_off(kNC * s + 2 * b + q, k)) = __int2bfloat16_rn(dv[q][s]);
     } else {
-        const int p = kKc * c + j;
-        double4 v = make_double4(0.0, 0.0, 0.0, 0.0);
-        if (p < npairs) v = reinterpret_cast<const double4 *>(in)[((size_t)b * (mmax + 1) + m) * npairs + p];
-        const double vv[4] = {v.x, v.y, v.z, v.w};   // s.re s.im d.re d.im
-        unsigned char *base = data + ((size_t)m * nchunks + c) * kDChunk;
+        const double *folds = in + (((size_t)b * (mmax + 1) + m) * npairs) * 4 + 2 * cls + q;
 #pragma unroll
-        for (int cls = 0; cls < 2; ++cls) {
-            digits_int(vv[2 * cls], e, dv[0]);
-            digits_int(vv[2 * cls + 1], e, dv[1]);
-            chunk = base + (size_t)cls * kDBlk;
-#pragma unroll
-            for (int s = 0; s < kSB; ++s)
-#pragma unroll
-                for (int q = 0; q < 2; ++q)
-                    *reinterpret_cast<__nv_bfloat16 *>(chunk + blk_off(kNC * s + 2 * b + q, j)) =
-                        __int2bfloat16_rn(dv[q][s]);
+        for (int i = 0; i < 8; ++i) {
+            const int p = kKc * c + 8 * kh + i;
+            v[i] = p < npairs ? folds[(size_t)p * 4] : 0.0;
         }
     }
+    uint32_t w[kSB][4];
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) {
+        int d0[kSB], d1[kSB];
+        digits_int(v[i], e, d0);
+        digits_int(v[i + 1], e, d1);
+#pragma unroll
+        for (int s = 0; s < kSB; ++s)
+            w[s][i / 2] = (uint32_t)__bfloat16_as_ushort(__int2bfloat16_rn(d0[s])) |
+                          ((uint32_t)__bfloat16_as_ushort(__int2bfloat16_rn(d1[s])) << 16);
+    }
+    unsigned char *chunk = data +
+                           (synth ? (size_t)(dchunk[m] + c) : (size_t)m * nchunks + c) * kDChunk +
+                           (size_t)cls * kDBlk;
+#pragma unroll
+    for (int s = 0; s < kSB; ++s)
+        *reinterpret_cast<uint4 *>(chunk + blk_off(kNC * s + 2 * b + q, 8 * kh)) =
+            make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
 }
 
 struct Tc64Args {
@@ -605,7 +603,7 @@ cudaError_t launch_tc64(bool synth, int lmax, int mmax, int npairs, int nlm, con
     // data digits
     const int Le0 = (lmax + 2) / 2;
     const int maxch = synth ? (Le0 + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
-    const long items = (long)maxch * batch * (synth ? 2 * kKc : kKc);
+    const long items = (long)maxch * batch * 8;
     k_prep64<<<dim3((unsigned)((items + 127) / 128), (unsigned)(mmax + 1)), 128, 0, st>>>(
         synth ? 1 : 0, lmax, mmax, npairs, nlm, batch, (int)op, in, fcol, dchunk, data);
     Tc64Args a{};
