@@ -660,12 +660,12 @@ int run_tc64(sht::Plan &p, bool synth, const void *in_, void *out_, int batch, s
             });
             if (rc) return rc;
             rc = timed(p, SHT_K_FFT_SYNTH, s, "fft synthesis launch",
-                       [&] { return sht::launch_fft_synth<double>(p.view64(), inter, out, nb, op, s); });
+                       [&] { return sht::launch_fft_synth_df(p.view64(), inter, out, nb, op, s); });
         } else {
             const double *in = static_cast<const double *>(in_) + (size_t)b0 * grid_n;
             double *out = static_cast<double *>(out_) + (size_t)b0 * spec_n;
             rc = timed(p, SHT_K_FFT_ANALYS, s, "fft analysis launch",
-                       [&] { return sht::launch_fft_analys<double>(p.view64(), in, inter, nb, op, false, s); });
+                       [&] { return sht::launch_fft_analys_df(p.view64(), in, inter, nb, op, false, s); });
             if (rc) return rc;
             rc = timed(p, SHT_K_TC_ANALYS, s, "FP64 tensor-core analysis launch", [&] {
                 return sht::launch_tc64(false, p.lmax, p.mmax, p.npairs, p.nlm, p.p64_a, p.d_off64_a, p.d_c064_a,

@@ -37,6 +37,46 @@ template <typename T2> __device__ __forceinline__ T2 mul_i(T2 a) { return mk<T2>
 
 __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
 
+// Double-float numbers (used by the FFTs of the FP64-accurate tensor-core
+// mode, further down): the unevaluated sum hi + lo of two FP32 numbers with
+// |lo| <= ulp(hi) / 2, after Dekker's double-length arithmetic (1971).
+struct __align__(8) dfl {
+    float hi, lo;
+    dfl() = default;
+    __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ explicit constexpr dfl(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+};
+struct __align__(16) dfl2 { dfl x, y; };
+
+// s + e = a + b exactly, for |a| >= |b| or a = 0 (Dekker)
+__device__ __forceinline__ dfl fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return dfl(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dfl operator+(dfl x, dfl y)
+{
+    // Knuth's error-free sum of the high parts, then the low parts
+    const float s = __fadd_rn(x.hi, y.hi);
+    const float bb = __fsub_rn(s, x.hi);
+    const float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));
+    return fast_two_sum(s, __fadd_rn(e, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ dfl operator-(dfl x) { return dfl(-x.hi, -x.lo); }
+__device__ __forceinline__ dfl operator-(dfl x, dfl y) { return x + (-y); }
+__device__ __forceinline__ dfl operator*(dfl x, dfl y)
+{
+    // exact error of hi * hi by an FMA; the lo * lo term is below the result's precision
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return fast_two_sum(p, e);
+}
+// x s for a power of two s (exact unless the low part leaves FP32's range)
+__device__ __forceinline__ dfl scale2(dfl x, float s) { return dfl(x.hi * s, x.lo * s); }
+
+
 // cos(pi j / 32), j = 0..16
 __host__ __device__ constexpr double cospi32(int j)
 {
@@ -51,6 +91,28 @@ __host__ __device__ constexpr double cospi32(int j)
 __host__ __device__ constexpr double cos64_half(int k) { return k > 16 ? -cospi32(32 - k) : cospi32(k); }
 __host__ __device__ constexpr double cos64(int k) { return cos64_half((k & 63) > 32 ? 64 - (k & 63) : (k & 63)); }
 __host__ __device__ constexpr double sin64(int k) { return cos64(k - 16); }
+
+// z e^{SIGN 2 pi i q / 64} for q < 32 (a constant once the DFT loops are
+// unrolled).  In double-float the multiplications by +-i and by
+// (+-1 + i) sqrt(1/2) are done as such (a general product costs four
+// double-float products and two sums); other types keep the general form.
+template <typename T2, int SIGN>
+struct Tw64 {
+    using T = decltype(T2::x);
+    __device__ __forceinline__ static T2 mul(int q, T2 z) { return cmul(mk<T2>(T(cos64(q)), T(SIGN * sin64(q))), z); }
+};
+template <int SIGN>
+struct Tw64<dfl2, SIGN> {
+    __device__ __forceinline__ static dfl2 mul(int q, dfl2 z)
+    {
+        const dfl szr = SIGN > 0 ? z.x : -z.x, szi = SIGN > 0 ? z.y : -z.y;   // SIGN z
+        if (q == 16) return mk<dfl2>(-szi, szr);
+        const dfl c(0.70710678118654752440);
+        if (q == 8) return mk<dfl2>(c * (z.x - szi), c * (szr + z.y));
+        if (q == 24) return mk<dfl2>(c * (-z.x - szi), c * (szr - z.y));
+        return cmul(mk<dfl2>(dfl(cos64(q)), dfl(SIGN * sin64(q))), z);
+    }
+};
 
 // In-register DFT of size RD <= 64 (natural order in and out), split into
 // even and odd halves recursively.  SIGN = +1: e^{+2 pi i ...} (inverse),
@@ -67,9 +129,7 @@ struct RegDft {
         RegDft<T2, RD / 2, SIGN>::run(o);
 #pragma unroll
         for (int k = 0; k < RD / 2; ++k) {
-            const int q = k * (64 / RD);
-            const T2 w = mk<T2>(T(cos64(q)), T(SIGN * sin64(q)));
-            const T2 t = (k == 0) ? o[k] : cmul(w, o[k]);
+            const T2 t = (k == 0) ? o[k] : Tw64<T2, SIGN>::mul(k * (64 / RD), o[k]);
             v[k] = cadd(e[k], t);
             v[k + RD / 2] = csub(e[k], t);
         }
@@ -229,6 +289,34 @@ __device__ __forceinline__ void fill_wtab(T2 *wtab, const T2 *__restrict__ tw, i
     }
 }
 
+// Writes the last Stockham pass's outputs y[j + r H/RD] of a thread's items.
+template <int RD, int NR, typename T2, typename F>
+__device__ __forceinline__ void last_pass_out(const T2 (&v)[NR], int t, int TPR, int H, const F &put)
+{
+    constexpr int IT = (16 + RD - 1) / RD;
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int jj = t + it * TPR;
+        if (jj >= H / RD) break;
+#pragma unroll
+        for (int rr = 0; rr < RD; ++rr) put(jj + rr * (H / RD), v[it * RD + rr]);
+    }
+}
+template <bool MIXED, typename T2, typename F>
+__device__ __forceinline__ void last_pass_out(int rd, const T2 (&v)[PassRegs<MIXED>::n], int t, int TPR, int H,
+                                              const F &put)
+{
+    constexpr int NR = PassRegs<MIXED>::n;
+    if (MIXED && rd == 3) { last_pass_out<3, NR>(v, t, TPR, H, put); return; }
+    if (MIXED && rd == 5) { last_pass_out<5, NR>(v, t, TPR, H, put); return; }
+    switch (rd) {
+    case 2: last_pass_out<2, NR>(v, t, TPR, H, put); break;
+    case 4: last_pass_out<4, NR>(v, t, TPR, H, put); break;
+    case 8: last_pass_out<8, NR>(v, t, TPR, H, put); break;
+    default: last_pass_out<16, NR>(v, t, TPR, H, put); break;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Synthesis: EO [batch][mmax+1][npairs][2] -> grid [batch][nlat][nphi]
 // blockDim = R * TPR with TPR = max(1, H/16) threads per row, R = 2G rows.
@@ -307,18 +395,11 @@ __device__ __forceinline__ void fft_synth_tile(const PlanView<T> &pv, const T *_
         __syncthreads();
         if (last) {
             // last pass: y[j + r' H/RD] for item j -- contiguous over threads
-            if (live_row) {
-                const int IT = (16 + rd - 1) / rd;
-                for (int it = 0; it < IT; ++it) {
-                    const int jj = t + it * TPR;
-                    if (jj >= H / rd) break;
-                    for (int rr = 0; rr < rd; ++rr) {
-                        T2 z = v[it * rd + rr];
-                        z.x *= scale; z.y *= scale;
-                        out[jj + rr * (H / rd)] = z;
-                    }
-                }
-            }
+            if (live_row)
+                last_pass_out<MIXED>(rd, v, t, TPR, H, [&](int idx, T2 z) {
+                    z.x *= scale; z.y *= scale;
+                    out[idx] = z;
+                });
             break;
         }
         if (r < R) pass_store<T2, MIXED>(rd, row, t, TPR, H, Ns, v);
@@ -430,6 +511,359 @@ k_fft_analys(PlanView<T> pv, const T *__restrict__ grid, T *__restrict__ sd, int
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     fft_analys_tile<T, MIXED>(pv, grid, sd, blockIdx.y, blockIdx.x * G, G, op, vector, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// Double-float FFTs for the FP64 data of the FP64-accurate tensor-core mode.
+// A value is the unevaluated sum hi + lo of two FP32 numbers with
+// |lo| <= ulp(hi) / 2 (Dekker's double-length arithmetic, 1971): 48
+// significand bits from FP32 instructions only, which this GPU issues some
+// seventy times faster than FP64 ones.  The sum is the short form (error-free
+// sum of the high parts, the low parts added once, renormalised); its error is
+// a small multiple of 2^-48 (|x| + |y|), which is the form of per-operation
+// bound the normwise error analysis of an FFT rests on, so a transform keeps an
+// error of order 2^-48 log2(H) of the row norm.  FP32's exponent range is kept
+// out of the way by scaling each latitude pair by the power of two that brings
+// its largest value into [1, 2) (found from the FP64 exponent bits, exact) and
+// scaling back on the way out.  Conversions between FP64 and double-float work
+// on the bits with integer operations, so no FP64 instruction runs per element.
+// ---------------------------------------------------------------------------
+// Biased FP64 exponent field of the larger part of v (0 for zeros and subnormals).
+__device__ __forceinline__ int dexp2(double2 v)
+{
+    const int a = (int)((unsigned long long)__double_as_longlong(v.x) >> 52) & 0x7ff;
+    const int b = (int)((unsigned long long)__double_as_longlong(v.y) >> 52) & 0x7ff;
+    return a > b ? a : b;
+}
+
+// v 2^-u as a double-float, from the bits of v: hi takes the leading 24
+// significand bits, lo the remaining 29 (rounded to 24 by the integer-to-float
+// conversion), then the pair is renormalised.  Scaled values below 2^-126 are
+// flushed to zero (the scale puts the pair's largest value in [1, 2)), as are
+// FP64 subnormals.
+__device__ __forceinline__ dfl d2df(double v, int u)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const int E = (int)(bits >> 52) & 0x7ff;
+    const int fe = E - 1023 - u;
+    if (E == 0 || fe < -126) return dfl(0.f, 0.f);
+    const unsigned sgn = (unsigned)(bits >> 32) & 0x80000000u;
+    const float hi = __uint_as_float(sgn | ((unsigned)(fe + 127) << 23) | (unsigned)((bits >> 29) & 0x7fffffu));
+    float lo = 0.f;
+    if (fe >= -74) {
+        // the low 29 bits weigh 2^(fe - 52) each
+        lo = __fmul_rn(__uint2float_rn((unsigned)(bits & 0x1fffffffu)), __uint_as_float((unsigned)(fe + 75) << 23));
+        lo = __uint_as_float(__float_as_uint(lo) | sgn);
+    }
+    return fast_two_sum(hi, lo);
+}
+__device__ __forceinline__ dfl2 d2df2(double2 v, int u)
+{
+    dfl2 r;
+    r.x = d2df(v.x, u);
+    r.y = d2df(v.y, u);
+    return r;
+}
+
+// (z.hi + z.lo) 2^u as an FP64 number, from the bits: both significands are
+// aligned in a 64-bit integer (hi's leading bit at bit 53), summed, rounded to
+// 53 bits (half away from zero) and packed with the exponent.  Results below
+// 2^-1022 are flushed to zero.
+__device__ __forceinline__ double df2d(dfl z, int u)
+{
+    const unsigned bh = __float_as_uint(z.hi), bl = __float_as_uint(z.lo);
+    const int eh = (int)(bh >> 23) & 0xff, el = (int)(bl >> 23) & 0xff;
+    if (eh == 0) return 0.0;
+    // in units of 2^(eh - 180): hi = (1.f significand) << 30
+    long long S = (long long)((bh & 0x7fffffu) | 0x800000u) << 30;
+    if (bh >> 31) S = -S;
+    if (el != 0) {
+        long long ml = (long long)((bl & 0x7fffffu) | 0x800000u);
+        const int sh = el - eh + 30;            // <= 6 for a normalised pair
+        if (sh >= 0) ml <<= sh;
+        else ml = (sh > -40) ? (ml >> -sh) : 0;
+        S += (bl >> 31) ? -ml : ml;
+    }
+    const unsigned long long sgn = S < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long a = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
+    if (a == 0) return 0.0;
+    int rs = 11 - __clzll((long long)a);       // shift that puts the leading bit at bit 52
+    unsigned long long m = rs > 0 ? (a + (1ull << (rs - 1))) >> rs : a << -rs;
+    if (m >> 53) { m >>= 1; ++rs; }
+    const int E = rs + eh + u + 895;            // biased exponent of m 2^(rs + eh - 180 + u)
+    if (E <= 0) return 0.0;
+    if (E >= 2047) return __longlong_as_double((long long)(sgn | (0x7ffull << 52)));
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)E << 52) | (m & ((1ull << 52) - 1))));
+}
+
+__device__ __forceinline__ dfl2 ld_twdf(const float4 *__restrict__ tw, int k)
+{
+    const float4 t = tw[k];
+    dfl2 r;
+    r.x = dfl(t.x, t.y);
+    r.y = dfl(t.z, t.w);
+    return r;
+}
+
+// W_H^q = e^{2 pi i q / H}, q < H, from the plan's double-float e^{2 pi i k / nphi}.
+__device__ __forceinline__ void fill_wtab_df(dfl2 *wtab, const float4 *__restrict__ twdf, int H)
+{
+    for (int q = threadIdx.x; q < H; q += blockDim.x) {
+        dfl2 w;
+        if (2 * q < H) {
+            w = ld_twdf(twdf, 2 * q);
+        } else {
+            w = ld_twdf(twdf, 2 * q - H);
+            w.x = -w.x;
+            w.y = -w.y;
+        }
+        wtab[q] = w;
+    }
+}
+
+// Shared memory of a double-float tile beyond the FP64 tile's (same row
+// layout: a double-float complex is 16 bytes): per pair its exponent and a
+// double-float scale factor.
+__host__ __device__ constexpr size_t df_extra_smem(int G) { return (size_t)4 * (G + (G & 1)) + (size_t)8 * G; }
+
+// Synthesis tile in double-float (see fft_synth_tile for the steps).  The
+// Legendre output arrives as FP64 E, O; they are staged unconverted in the
+// rows while the pair's largest exponent is found, then converted in the
+// pre-twiddle.
+template <bool MIXED>
+__device__ __forceinline__ void fft_synth_tile_df(const PlanView<double> &pv, const double *__restrict__ eo,
+                                                  double *__restrict__ grid, int b, int p0, int G, int op,
+                                                  unsigned char *smem_raw)
+{
+    const int H = pv.nphi / 2, R = 2 * G;
+    const int TPR = row_tpr(H);
+    const int ld = padi(H) + 1;
+    dfl2 *wtab = reinterpret_cast<dfl2 *>(smem_raw);
+    dfl2 *buf = wtab + H;
+    int *s_e = reinterpret_cast<int *>(buf + R * ld);
+    dfl *s_w = reinterpret_cast<dfl *>(s_e + G + (G & 1));
+    const int mmax = pv.mmax, npairs = pv.npairs, nlat = pv.nlat;
+    const double2 *eo2 = reinterpret_cast<const double2 *>(eo);
+    double2 *raw = reinterpret_cast<double2 *>(buf);
+
+    fill_wtab_df(wtab, pv.twdf, H);
+    for (int i = threadIdx.x; i < G; i += blockDim.x) {
+        s_e[i] = 0;
+        const int p = p0 + i;
+        const double sc = (op == OP_ANALYS_ADJ && p < npairs) ? kTwoPiD / pv.nphi * pv.wq[p] : 1.0;
+        s_w[i] = dfl(sc);
+    }
+    __syncthreads();
+    // 1. E (row 2i) and O (row 2i+1) of the G pairs in natural order, zero
+    //    above mmax, and the largest exponent per pair
+    {
+        int cur = -1, emax = 0;
+        for (int q = threadIdx.x; q < G * H; q += blockDim.x) {
+            const int m = q / G, i = q - m * G;
+            const int p = p0 + i;
+            double2 E = make_double2(0.0, 0.0), O = E;
+            if (m <= mmax && p < npairs) {
+                const size_t o = (((size_t)b * (mmax + 1) + m) * npairs + p) * 2;
+                E = eo2[o];
+                O = eo2[o + 1];
+                if (m == 0) { E.y = 0.0; O.y = 0.0; }
+            }
+            raw[(2 * i) * ld + padi(m)] = E;
+            raw[(2 * i + 1) * ld + padi(m)] = O;
+            if (i != cur) {
+                if (cur >= 0) atomicMax(&s_e[cur], emax);
+                cur = i;
+                emax = 0;
+            }
+            emax = max(emax, max(dexp2(E), dexp2(O)));
+        }
+        if (cur >= 0) atomicMax(&s_e[cur], emax);
+    }
+    __syncthreads();
+    // 2. X_N = E + O, X_S = E - O and the pre-twiddle, in double-float; a thread
+    //    owns positions k and H - k of both rows of its pair (converted in place)
+    for (int q = threadIdx.x; q < G * (H / 2 + 1); q += blockDim.x) {
+        const int i = q / (H / 2 + 1), k = q - i * (H / 2 + 1);
+        const int u = s_e[i] - 1023;
+        const int k2 = k == 0 ? 0 : H - k;
+        const double2 *rE = raw + (2 * i) * ld, *rO = raw + (2 * i + 1) * ld;
+        const dfl2 Ea = d2df2(rE[padi(k)], u), Oa = d2df2(rO[padi(k)], u);
+        const dfl2 Eb = d2df2(rE[padi(k2)], u), Ob = d2df2(rO[padi(k2)], u);
+        dfl2 *dN = buf + (2 * i) * ld, *dS = buf + (2 * i + 1) * ld;
+        const dfl2 XNa = cadd(Ea, Oa), XSa = csub(Ea, Oa);
+        if (k == 0) {
+            dN[0] = cadd(XNa, mul_i(XNa));
+            dS[0] = cadd(XSa, mul_i(XSa));
+            continue;
+        }
+        const dfl2 XNb = cadd(Eb, Ob), XSb = csub(Eb, Ob);
+        const dfl2 wa = ld_twdf(pv.twdf, k);
+        dN[padi(k)] = cadd(cadd(XNa, conj_(XNb)), mul_i(cmul(wa, csub(XNa, conj_(XNb)))));
+        dS[padi(k)] = cadd(cadd(XSa, conj_(XSb)), mul_i(cmul(wa, csub(XSa, conj_(XSb)))));
+        if (k2 != k) {
+            const dfl2 wb = ld_twdf(pv.twdf, k2);
+            dN[padi(k2)] = cadd(cadd(XNb, conj_(XNa)), mul_i(cmul(wb, csub(XNb, conj_(XNa)))));
+            dS[padi(k2)] = cadd(cadd(XSb, conj_(XSa)), mul_i(cmul(wb, csub(XSb, conj_(XSa)))));
+        }
+    }
+    __syncthreads();
+    // 3. inverse complex FFT of length H; the last pass converts back to FP64 and writes the grid
+    const int r = threadIdx.x / TPR, t = threadIdx.x - r * TPR;
+    const int p = p0 + (r >> 1);
+    const int j = (r & 1) ? nlat - 1 - p : p;
+    const bool live_row = r < R && p < npairs && !((r & 1) && j == p);
+    dfl2 *row = buf + (r < R ? r : 0) * ld;
+    double2 *out = reinterpret_cast<double2 *>(grid) + ((size_t)b * nlat + (live_row ? j : 0)) * H;
+    const int u = r < R ? s_e[r >> 1] - 1023 : 0;
+    const bool scaled = op == OP_ANALYS_ADJ;
+    const dfl sc = r < R ? s_w[r >> 1] : dfl(1.f, 0.f);
+    const auto put = [&](int idx, dfl2 z) {
+        if (scaled) { z.x = z.x * sc; z.y = z.y * sc; }
+        out[idx] = make_double2(df2d(z.x, u), df2d(z.y, u));
+    };
+    if (H == 1) {
+        if (threadIdx.x < R && live_row) put(0, row[0]);
+        return;
+    }
+    int Ns = 1;
+    dfl2 v[PassRegs<MIXED>::n];
+    for (int ps = 0;; ++ps) {
+        const int rd = fft_plan_radix(pv.fftplan, ps);
+        if (r < R) pass_load<dfl2, 1, MIXED>(rd, row, false, t, TPR, H, Ns, wtab, v);
+        const bool last = Ns * rd == H;
+        __syncthreads();
+        if (last) {
+            if (live_row) last_pass_out<MIXED>(rd, v, t, TPR, H, put);
+            break;
+        }
+        if (r < R) pass_store<dfl2, MIXED>(rd, row, t, TPR, H, Ns, v);
+        __syncthreads();
+        Ns *= rd;
+    }
+}
+
+// Analysis tile in double-float (see fft_analys_tile).  Each thread reads its
+// share of its row into registers, the pair's largest exponent is found, and
+// the values go to shared memory converted; the fold converts back to FP64.
+template <bool MIXED>
+__device__ __forceinline__ void fft_analys_tile_df(const PlanView<double> &pv, const double *__restrict__ grid,
+                                                   double *__restrict__ sd, int b, int p0, int G, int op,
+                                                   int vector, unsigned char *smem_raw)
+{
+    const int H = pv.nphi / 2, R = 2 * G;
+    const int TPR = row_tpr(H);
+    const int ld = padi(H) + 1;
+    dfl2 *wtab = reinterpret_cast<dfl2 *>(smem_raw);
+    dfl2 *buf = wtab + H;
+    int *s_e = reinterpret_cast<int *>(buf + R * ld);
+    dfl *s_w = reinterpret_cast<dfl *>(s_e + G + (G & 1));
+    const int mmax = pv.mmax, npairs = pv.npairs, nlat = pv.nlat;
+
+    fill_wtab_df(wtab, pv.twdf, H);
+    for (int i = threadIdx.x; i < G; i += blockDim.x) {
+        s_e[i] = 0;
+        const int pp = p0 + i;
+        double wf = (op == OP_ANALYS) ? kTwoPiD / pv.nphi : 1.0;
+        if (pp < npairs) {
+            if (op == OP_ANALYS) wf *= pv.wq[pp];
+            if (vector) wf /= pv.st[pp];
+        }
+        s_w[i] = dfl(wf);
+    }
+    __syncthreads();
+    const int r = threadIdx.x / TPR, t = threadIdx.x - r * TPR;
+    const int p = p0 + (r >> 1);
+    const int j = (r & 1) ? nlat - 1 - p : p;
+    const bool live_row = r < R && p < npairs && !((r & 1) && j == p);
+    dfl2 *row = buf + (r < R ? r : 0) * ld;
+    const double2 *in = reinterpret_cast<const double2 *>(grid) + ((size_t)b * nlat + (live_row ? j : 0)) * H;
+    // H <= 16 TPR: at most 16 values per thread
+    double2 x[16];
+    {
+        int e = 0;
+#pragma unroll
+        for (int it = 0; it < 16; ++it) {
+            const int k = t + it * TPR;
+            x[it] = (live_row && k < H) ? in[k] : make_double2(0.0, 0.0);
+            e = max(e, dexp2(x[it]));
+        }
+        if (live_row) atomicMax(&s_e[r >> 1], e);
+    }
+    __syncthreads();
+    if (r < R) {
+        const int u = s_e[r >> 1] - 1023;
+#pragma unroll
+        for (int it = 0; it < 16; ++it) {
+            const int k = t + it * TPR;
+            if (k < H) row[padi(k)] = d2df2(x[it], u);
+        }
+    }
+    __syncthreads();
+    if (H > 1) {
+        // forward complex FFT of length H
+        int Ns = 1;
+        dfl2 v[PassRegs<MIXED>::n];
+        const int npass = fft_plan_npass(pv.fftplan);
+        for (int ps = 0; ps < npass; ++ps) {
+            const int rd = fft_plan_radix(pv.fftplan, ps);
+            if (r < R) pass_load<dfl2, -1, MIXED>(rd, row, false, t, TPR, H, Ns, wtab, v);
+            __syncthreads();
+            if (r < R) pass_store<dfl2, MIXED>(rd, row, t, TPR, H, Ns, v);
+            __syncthreads();
+            Ns *= rd;
+        }
+    }
+    // post-twiddle, fold north/south, weight, back to FP64
+    double2 *sd2 = reinterpret_cast<double2 *>(sd);
+    for (int q = threadIdx.x; q < G * (mmax + 1); q += blockDim.x) {
+        const int m = q / G, i = q - m * G;
+        const int pp = p0 + i;
+        if (pp >= npairs) continue;
+        const dfl2 wm = conj_(ld_twdf(pv.twdf, m));
+        dfl2 X[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const dfl2 *rw = buf + (2 * i + h) * ld;
+            const dfl2 Zk = rw[padi(m)];
+            const dfl2 Zc = conj_(rw[padi((H - m) % H)]);
+            dfl2 E = cadd(Zk, Zc), O = csub(Zk, Zc);
+            E.x = scale2(E.x, 0.5f);
+            E.y = scale2(E.y, 0.5f);
+            const dfl2 Od = mk<dfl2>(scale2(O.y, 0.5f), scale2(O.x, -0.5f));  // O / (2i)
+            X[h] = cadd(E, cmul(wm, Od));
+        }
+        const dfl wf = s_w[i];
+        const bool equator = (nlat & 1) && pp == npairs - 1;
+        dfl2 s, d;
+        if (equator) {
+            s = mk<dfl2>(wf * X[0].x, wf * X[0].y);
+            d = s;
+        } else {
+            s = mk<dfl2>(wf * (X[0].x + X[1].x), wf * (X[0].y + X[1].y));
+            d = mk<dfl2>(wf * (X[0].x - X[1].x), wf * (X[0].y - X[1].y));
+        }
+        const int u = s_e[i] - 1023;
+        const size_t o = (((size_t)b * (mmax + 1) + m) * npairs + pp) * 2;
+        sd2[o] = make_double2(df2d(s.x, u), df2d(s.y, u));
+        sd2[o + 1] = make_double2(df2d(d.x, u), df2d(d.y, u));
+    }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(512)
+k_fft_synth_df(PlanView<double> pv, const double *__restrict__ eo, double *__restrict__ grid, int G, int op)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fft_synth_tile_df<MIXED>(pv, eo, grid, blockIdx.y, blockIdx.x * G, G, op, smem_raw);
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(512)
+k_fft_analys_df(PlanView<double> pv, const double *__restrict__ grid, double *__restrict__ sd, int G, int op,
+                int vector)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fft_analys_tile_df<MIXED>(pv, grid, sd, blockIdx.y, blockIdx.x * G, G, op, vector, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -757,6 +1191,44 @@ cudaError_t launch_fft_analys(const PlanView<T> &pv, const T *grid, T *sd, int b
         k_fft_analys<T, true><<<gridd, threads, smem, s>>>(pv, grid, sd, G, (int)op, vector ? 1 : 0);
     else
         k_fft_analys<T, false><<<gridd, threads, smem, s>>>(pv, grid, sd, G, (int)op, vector ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft_synth_df(const PlanView<double> &pv, const double *eo, double *grid, int batch, Op op,
+                                cudaStream_t s)
+{
+    if (!pv.twdf) return cudaErrorInvalidValue;
+    int G, threads;
+    size_t smem;
+    fft_shape<double>(pv.nphi / 2, pv.npairs, G, threads, smem);
+    smem += df_extra_smem(G);
+    const bool mixed = !pow2(pv.nphi / 2);
+    cudaError_t e = mixed ? set_smem(k_fft_synth_df<true>, smem) : set_smem(k_fft_synth_df<false>, smem);
+    if (e != cudaSuccess) return e;
+    dim3 gridd((unsigned)((pv.npairs + G - 1) / G), (unsigned)batch);
+    if (mixed)
+        k_fft_synth_df<true><<<gridd, threads, smem, s>>>(pv, eo, grid, G, (int)op);
+    else
+        k_fft_synth_df<false><<<gridd, threads, smem, s>>>(pv, eo, grid, G, (int)op);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft_analys_df(const PlanView<double> &pv, const double *grid, double *sd, int batch, Op op,
+                                 bool vector, cudaStream_t s)
+{
+    if (!pv.twdf) return cudaErrorInvalidValue;
+    int G, threads;
+    size_t smem;
+    fft_shape<double>(pv.nphi / 2, pv.npairs, G, threads, smem);
+    smem += df_extra_smem(G);
+    const bool mixed = !pow2(pv.nphi / 2);
+    cudaError_t e = mixed ? set_smem(k_fft_analys_df<true>, smem) : set_smem(k_fft_analys_df<false>, smem);
+    if (e != cudaSuccess) return e;
+    dim3 gridd((unsigned)((pv.npairs + G - 1) / G), (unsigned)batch);
+    if (mixed)
+        k_fft_analys_df<true><<<gridd, threads, smem, s>>>(pv, grid, sd, G, (int)op, vector ? 1 : 0);
+    else
+        k_fft_analys_df<false><<<gridd, threads, smem, s>>>(pv, grid, sd, G, (int)op, vector ? 1 : 0);
     return cudaGetLastError();
 }
 

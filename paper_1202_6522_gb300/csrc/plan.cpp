@@ -93,14 +93,14 @@ size_t padded(size_t count) { return (count * sizeof(U) + 255) & ~size_t(255); }
 PlanView<double> Plan::view64() const
 {
     PlanView<double> v{lmax, mmax, nlat, nphi, npairs, nlm,
-                       t64.ab, t64.dc, t64.x, t64.st, t64.wq, t64.pmm, t64.pmmk, t64.tw, t64.rtw, fft_plan_of(nphi / 2), mres};
+                       t64.ab, t64.dc, t64.x, t64.st, t64.wq, t64.pmm, t64.pmmk, t64.tw, t64.rtw, fft_plan_of(nphi / 2), mres, twdf};
     return v;
 }
 
 PlanView<float> Plan::view32() const
 {
     PlanView<float> v{lmax, mmax, nlat, nphi, npairs, nlm,
-                      t32.ab, t32.dc, t32.x, t32.st, t32.wq, t32.pmm, t32.pmmk, t32.tw, t32.rtw, fft_plan_of(nphi / 2), mres};
+                      t32.ab, t32.dc, t32.x, t32.st, t32.wq, t32.pmm, t32.pmmk, t32.tw, t32.rtw, fft_plan_of(nphi / 2), mres, nullptr};
     return v;
 }
 
@@ -206,7 +206,7 @@ int plan_build(Plan &p, std::string &err)
     bytes += padded<float2>(nlm) + padded<float>(nlm) + 3 * padded<float>(npairs) +
              padded<float>((size_t)(mmax + 1) * npairs) + padded<int>((size_t)(mmax + 1) * npairs) +
              2 * padded<float2>(H1);
-    bytes += padded<int>(1);
+    bytes += padded<float4>(H1) + padded<int>(1);
     DevArena ar;
     cudaError_t ce = cudaGetDevice(&p.device);
     if (ce != cudaSuccess) { err = std::string("cudaGetDevice: ") + cudaGetErrorString(ce); return SHT_ECUDA; }
@@ -259,6 +259,15 @@ int plan_build(Plan &p, std::string &err)
     ok &= up(p.t32.tw, tw32.data(), sizeof(float) * 2 * H1);
     p.t32.rtw = ar.take<float2>(H1);
     ok &= up(p.t32.rtw, rtw32.data(), sizeof(float) * 2 * H1);
+    // the same twiddles as double-float pairs: hi = fl32(w), lo = fl32(w - hi)
+    std::vector<float> twdf(4 * H1, 0.f);
+    for (size_t k = 0; k < 2 * H1; ++k) {
+        const float hi = (float)tw[k];
+        twdf[2 * k] = hi;
+        twdf[2 * k + 1] = (float)(tw[k] - (double)hi);
+    }
+    p.twdf = ar.take<float4>(H1);
+    ok &= up(p.twdf, twdf.data(), sizeof(float) * 4 * H1);
     p.d_err = ar.take<int>(1);
     ok &= cudaMemset(p.d_err, 0, sizeof(int)) == cudaSuccess;
     if (!ok) {

@@ -59,6 +59,7 @@ struct PlanView {
     const T2 *rtw;
     unsigned long long fftplan;   // radices of the FFT of length nphi/2 (fft_plan_of)
     int mres;                     // order stride: order index k is the order m = k mres
+    const float4 *twdf;           // FP64 plans: tw as double-float pairs (re.hi, re.lo, im.hi, im.lo)
 };
 
 // First packed index of order index k (order m = k mres): the degrees of the
@@ -123,6 +124,7 @@ struct Plan {
     Tables<double> t64;
     Tables<float> t32;
     void *tables_base = nullptr;     // single device allocation holding t64 and t32
+    float4 *twdf = nullptr;          // [nphi/2] e^{2 pi i k / nphi} as double-float pairs
     int *d_err = nullptr;            // device error word written by bounded waits
     unsigned char *panel_s = nullptr, *panel_a = nullptr;   // tensor-core P panels
     unsigned long long *d_off_s = nullptr, *d_off_a = nullptr, *d_dchunk = nullptr;
@@ -187,6 +189,13 @@ cudaError_t launch_fft_synth(const PlanView<T> &pv, const T *eo, T *grid, int ba
 template <typename T>
 cudaError_t launch_fft_analys(const PlanView<T> &pv, const T *grid, T *sd, int batch, Op op,
                               bool vector, cudaStream_t s);
+// The same transforms of FP64 data in double-float arithmetic (pairs of FP32
+// numbers, ~2^-48 relative error per operation), for the FP64-accurate
+// tensor-core mode; needs the plan's double-float twiddles (pv.twdf).
+cudaError_t launch_fft_synth_df(const PlanView<double> &pv, const double *eo, double *grid, int batch, Op op,
+                                cudaStream_t s);
+cudaError_t launch_fft_analys_df(const PlanView<double> &pv, const double *grid, double *sd, int batch, Op op,
+                                 bool vector, cudaStream_t s);
 
 
 

@@ -5,7 +5,8 @@ slices (7 for P per row, 8 for the data per field) whose integer products the
 tensor core sums exactly; the bound is the FP64 path's, 1e-11 normwise.  Cases cover
 several 128-row tiles and ragged tails, mmax < lmax, odd nlat, batches of more
 than 16 fields (several launches), the adjoints, sampled rows/orders of the
-full N = 1023, batch 16 workload, and the size limit."""
+full N = 1023, batch 16 workload, exact power-of-two scaling and the size
+limit."""
 import numpy as np
 import pytest
 
@@ -142,3 +143,20 @@ def test_tc64_size_limit(SHT):
     a = torch.zeros(1, sht.nlm, dtype=torch.complex128, device=DEV)
     with pytest.raises(C.SHTError):
         sht.synth_(a)
+
+
+def test_tc64_power_of_two_scaling_is_exact(SHT):
+    """Inputs scaled by 2^-600 or 2^600 (far outside FP32's range) give outputs
+    scaled by the same power, bit for bit: the contraction scales each field and
+    the double-float FFT each latitude pair by a power of two taken from the
+    FP64 exponents, so only those exponents move."""
+    lmax, nlat, nphi = 63, 64, 128
+    sht = SHT(lmax, lmax, nlat, nphi, fp64_path="tc")
+    a = torch.from_numpy(synthetic.spectrum(lmax, batch=3, seed=8)).to(DEV)
+    g = sht.synth_(a)
+    x = torch.from_numpy(synthetic.grid(nlat, nphi, batch=3, seed=9)).to(DEV)
+    s = sht.analys_(x)
+    for k in (-600, 600):
+        assert torch.equal(sht.synth_(a * 2.0 ** k), g * 2.0 ** k), k
+        assert torch.equal(sht.analys_(x * 2.0 ** k), s * 2.0 ** k), k
+    assert normwise(_np(g), oracle.synth(lmax, lmax, nlat, nphi, _np(a))) < fp64_bound(lmax)
