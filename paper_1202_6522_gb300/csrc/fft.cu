@@ -73,6 +73,30 @@ __device__ __forceinline__ dfl operator*(dfl x, dfl y)
     e = __fmaf_rn(x.lo, y.hi, e);
     return fast_two_sum(p, e);
 }
+// Complex product in double-float with each component formed as one sum:
+// re = xr wr - xi wi from the two exact high products (FMA errors), one
+// error-free sum of them and the cross terms accumulated into the low part.
+__device__ __forceinline__ dfl dot2(dfl a, dfl b, dfl c, dfl d)   // a b + c d
+{
+    const float p1 = __fmul_rn(a.hi, b.hi), p2 = __fmul_rn(c.hi, d.hi);
+    const float e1 = __fmaf_rn(a.hi, b.hi, -p1), e2 = __fmaf_rn(c.hi, d.hi, -p2);
+    const float s = __fadd_rn(p1, p2);
+    const float bb = __fsub_rn(s, p1);
+    float t = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bb)), __fsub_rn(p2, bb));
+    t = __fadd_rn(t, __fadd_rn(e1, e2));
+    t = __fmaf_rn(a.hi, b.lo, t);
+    t = __fmaf_rn(a.lo, b.hi, t);
+    t = __fmaf_rn(c.hi, d.lo, t);
+    t = __fmaf_rn(c.lo, d.hi, t);
+    return fast_two_sum(s, t);
+}
+__device__ __forceinline__ dfl2 cmul(dfl2 a, dfl2 b)
+{
+    dfl2 r;
+    r.x = dot2(a.x, b.x, -a.y, b.y);
+    r.y = dot2(a.x, b.y, a.y, b.x);
+    return r;
+}
 // x s for a power of two s (exact unless the low part leaves FP32's range)
 __device__ __forceinline__ dfl scale2(dfl x, float s) { return dfl(x.hi * s, x.lo * s); }
 
