@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(kWsThreads, kWsCtasPerSm) k_tc_ws(TcArgs a, co
                 // never written out)
                 const uint32_t tx = (pgb - lo) + (uint32_t)(SYNTH && !a.fused ? dbytes : ws_raw_bytes(a.batch, SYNTH));
                 tc::mbar_arrive_expect_tx(&bar_load[q], tx);
-                if (pgb > lo) tc::bulk_g2s(st + lo, panel + (size_t)c * kChunkPanel + lo, pgb - lo, &bar_load[q]);
+                if (pgb > lo) tc::bulk_g2s_stream(st + lo, panel + (size_t)c * kChunkPanel + lo, pgb - lo, &bar_load[q]);
                 if (SYNTH && a.fused) {
                     // spectra of every field, degrees [2 kKc c, 2 kKc c + 2 kKc) of order
                     // m, from the 16-byte boundary at or below (one coefficient earlier
@@ -675,8 +675,8 @@ __global__ void __launch_bounds__(128, 1) k_tc_vec(TcArgs a)
             if (u >= S && !wait_or_abort(&bar_mma[q], (uint32_t)((u / S - 1) & 1), &s_abort)) { okp = false; break; }
             unsigned char *st = smem + (size_t)q * stage_bytes;
             tc::mbar_arrive_expect_tx(&bar_load[q], 2u * kChunkPanel + dbytes);
-            tc::bulk_g2s(st, p0 + c * kChunkPanel, kChunkPanel, &bar_load[q]);
-            tc::bulk_g2s(st + kChunkPanel, p1 + c * kChunkPanel, kChunkPanel, &bar_load[q]);
+            tc::bulk_g2s_stream(st, p0 + c * kChunkPanel, kChunkPanel, &bar_load[q]);
+            tc::bulk_g2s_stream(st + kChunkPanel, p1 + c * kChunkPanel, kChunkPanel, &bar_load[q]);
             tc::bulk_g2s(st + 2 * kChunkPanel, data + c * dbytes, dbytes, &bar_load[q]);
             issued = u + 1;
         }

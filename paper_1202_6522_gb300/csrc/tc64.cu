@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc64(Tc64Args a)
                 }
                 unsigned char *st = smem + (size_t)q * kStage;
                 tc::mbar_arrive_expect_tx(&bar_load[q], (uint32_t)kStage);
-                tc::bulk_g2s(st, panel + (size_t)c * kPChunk + (size_t)par * kPPar, (uint32_t)kPPar, &bar_load[q]);
+                tc::bulk_g2s_stream(st, panel + (size_t)c * kPChunk + (size_t)par * kPPar, (uint32_t)kPPar, &bar_load[q]);
                 tc::bulk_g2s(st + kPPar, data + (size_t)c * kDChunk + (size_t)par * kDBlk, (uint32_t)kDBlk,
                              &bar_load[q]);
                 issued = u + 1;
