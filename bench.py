@@ -263,8 +263,10 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 def uneven_batch(torch, dev, replays=200):
     """96 FP32 fields with N drawn from {63, 127, 255, 511} (nlat = N+1, nphi =
-    2(N+1)): round-trip latency of one graph launch per direction vs the same
-    persistent kernels launched directly vs one launch pair per field."""
+    2(N+1)): round-trip latency of one graph launch per direction (persistent
+    CUDA-core kernels, and the tensor-core mode with one contraction per shape
+    group) vs the persistent kernels launched directly vs one launch pair per
+    field, and the path the automatic mode picks."""
     from paper_1202_6522_gb300 import SHT, UnevenBatch, synthetic
     lmaxs = synthetic.uneven_truncations(96)
     hist = {str(n): lmaxs.count(n) for n in sorted(set(lmaxs))}
@@ -296,11 +298,16 @@ def uneven_batch(torch, dev, replays=200):
                 "round_trips_per_s": len(lmaxs) * replays / wall}
 
     out = {"fields": len(lmaxs), "truncations": hist, "replays": replays}
-    for name, graph in (("graph", True), ("persistent_no_graph", False)):
-        ub = UnevenBatch(lmaxs, device=dev, use_graph=graph)
+    for name, graph, path in (("graph", True, "f32"), ("persistent_no_graph", False, "f32"),
+                              ("tc_graph", True, "tc")):
+        ub = UnevenBatch(lmaxs, device=dev, use_graph=graph, path=path)
         grids = ub.synth_(specs)
         back = ub.analys_(grids)
         out[name] = measure(lambda: ub.analys_(ub.synth_(specs, out=grids), out=back))
+        del ub
+    auto = UnevenBatch(lmaxs, device=dev, path="auto")
+    out["auto"] = {"chosen": auto.path, "tuned_round_trip_ms": auto.tuned_ms}
+    del auto
     out["per_field_launches"] = measure(per_field)
     return out
 

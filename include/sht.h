@@ -245,6 +245,24 @@ SHT_API int sht_tune(sht_handle h, int batch, int mode, double *report, void *st
  * on this batch plan has started its pointer-table copy. */
 typedef struct sht_batch_plan *sht_batch;
 SHT_API int sht_batch_create(int nfields, const int *lmax, const int *nlat, const int *nphi, sht_batch *out);
+/* The same with a choice of path (Sec. 3.2's runtime choice, for batches):
+ * SHT_F32 the persistent CUDA-core kernels above; SHT_TC_BF16X3 the Legendre
+ * stage of each group of equal shape as one batched tensor-core contraction
+ * against that shape's P panels (built here, ~(N+1)^3 bytes per direction per
+ * shape), the group's spectra gathered into (synthesis) or scattered from
+ * (analysis) a contiguous buffer by one copy kernel, the FFTs one persistent
+ * kernel over all fields -- the graph then holds the copies, one contraction
+ * per group and the FFT; SHT_F32_AUTO times a round trip of both on zero
+ * fields here (a few launches, synchronising) and keeps the faster.  Errors as
+ * sht_batch_create, SHT_EINVAL for another mode, and the tensor-core
+ * preparation's (SHT_ENOMEM) for SHT_TC_BF16X3. */
+SHT_API int sht_batch_create_mode(int nfields, const int *lmax, const int *nlat, const int *nphi, int mode,
+                                  sht_batch *out);
+/* The path a batch plan runs (SHT_F32 or SHT_TC_BF16X3); for SHT_F32_AUTO
+ * plans also the round-trip times it measured (ms, 0 when not timed) of the
+ * CUDA-core and tensor-core paths, into *ms_f32 and *ms_tc (either may be
+ * NULL).  Negative SHT error for a NULL handle. */
+SHT_API int sht_batch_mode(sht_batch b, float *ms_f32, float *ms_tc);
 SHT_API void sht_batch_destroy(sht_batch b);
 SHT_API int sht_batch_synth(sht_batch b, void *const *spec, void *const *grid, int use_graph, void *stream);
 SHT_API int sht_batch_analys(sht_batch b, void *const *grid, void *const *spec, int use_graph, void *stream);

@@ -53,6 +53,9 @@ SIGNATURES = {
     "sht_sync_status": ([_VP, _VP], _I),
     "sht_synth_static": ([_VP, _VP, _VP, _I, _I, _VP], _I),
     "sht_batch_create": ([_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_VP)], _I),
+    "sht_batch_create_mode": ([_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), _I,
+                               ctypes.POINTER(_VP)], _I),
+    "sht_batch_mode": ([_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)], _I),
     "sht_batch_destroy": ([_VP], None),
     "sht_batch_synth": ([_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP], _I),
     "sht_batch_analys": ([_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP], _I),
@@ -208,6 +211,21 @@ def sht_batch_create(lmax, nlat, nphi) -> int:
     n = len(lmax)
     check(_call("sht_batch_create", n, _ints(lmax), _ints(nlat), _ints(nphi), ctypes.byref(h)))
     return h.value
+
+
+def sht_batch_create_mode(lmax, nlat, nphi, mode) -> int:
+    """Uneven batch plan with a path: SHT_F32, SHT_TC_BF16X3 or SHT_F32_AUTO."""
+    h = _VP()
+    n = len(lmax)
+    check(_call("sht_batch_create_mode", n, _ints(lmax), _ints(nlat), _ints(nphi), int(mode), ctypes.byref(h)))
+    return h.value
+
+
+def sht_batch_mode(b):
+    """(path in use, measured ms of the CUDA-core path, of the tensor-core path)."""
+    a, c = ctypes.c_float(0.0), ctypes.c_float(0.0)
+    mode = check(_call("sht_batch_mode", b, ctypes.byref(a), ctypes.byref(c)))
+    return mode, a.value, c.value
 
 
 def sht_batch_destroy(b) -> None:

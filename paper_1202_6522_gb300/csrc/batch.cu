@@ -11,6 +11,14 @@
 // (in the order of Sec. 2.2 / 2.3).  That sequence is captured once into a
 // CUDA graph and replayed on every call.  The persistent kernels take tiles
 // with atomicAdd on a counter and never wait on each other.
+//
+// Tensor-core mode: the fields of one shape form a group whose spectra (a
+// gather kernel copies them in, or the results out) and intermediates are
+// contiguous, so each group's Legendre stage is one batched tcgen05
+// contraction against that plan's P panels; the FFTs stay one persistent
+// launch over all fields.  The captured graph then holds the pointer-table
+// copy, the gather (or scatter), one contraction per group and the FFT.  The
+// automatic mode times both and keeps the faster.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,9 +31,27 @@
 
 #include "sht_internal.h"
 
+namespace {
+// One copy of the gather (synthesis) or scatter (analysis) of the tensor-core mode.
+struct BatchCopy {
+    const float2 *src;
+    float2 *dst;
+    long long n;   // complex values
+};
+}  // namespace
+
 struct sht_batch_plan {
     int nfields = 0;
     int device = 0;
+    int mode = SHT_F32;                    // SHT_F32 (persistent CUDA-core kernels) or SHT_TC_BF16X3
+    std::vector<std::vector<int>> group_fields;   // tensor cores: the fields of each plan, in order
+    float *d_gspec = nullptr;              // ... contiguous spectra of each group
+    std::vector<size_t> gspec_off;         // ... per group, floats
+    std::vector<size_t> field_gspec;       // ... per field: its slot in d_gspec, floats
+    std::vector<size_t> ginter_off;        // ... per group: its contiguous intermediate in d_inter, floats
+    std::vector<size_t> inter_tc;          // ... per field: its intermediate in that layout
+    BatchCopy *h_copies = nullptr, *d_copies = nullptr;
+    float tuned_ms[2] = {0.f, 0.f};        // automatic mode: round trip per path (CUDA cores, tensor cores)
     std::vector<std::unique_ptr<sht::Plan>> plans;   // one per distinct shape
     std::vector<int> field_plan;
     std::vector<int> lmax, nlat, nphi;
@@ -54,6 +80,9 @@ void free_batch(sht_batch_plan *b)
         if (g) cudaGraphExecDestroy(g);
     if (b->done) cudaEventDestroy(b->done);
     if (b->h_fields) cudaFreeHost(b->h_fields);
+    if (b->h_copies) cudaFreeHost(b->h_copies);
+    cudaFree(b->d_copies);
+    cudaFree(b->d_gspec);
     cudaFree(b->d_fields);
     cudaFree(b->d_tiles);
     cudaFree(b->d_counters);
@@ -63,16 +92,32 @@ void free_batch(sht_batch_plan *b)
     delete b;
 }
 
-// Fill the pointer table for one call.
-void fill_fields(sht_batch_plan *b, void *const *in, void *const *out)
+// Gather / scatter of the tensor-core mode: blockIdx.y = copy.
+__global__ void __launch_bounds__(256) k_batch_copy(const BatchCopy *__restrict__ copies)
 {
+    const BatchCopy c = copies[blockIdx.y];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < c.n; i += (long long)gridDim.x * blockDim.x)
+        c.dst[i] = c.src[i];
+}
+
+// Fill the pointer table (and the tensor-core mode's copy list) for one call.
+void fill_fields(sht_batch_plan *b, bool synth, void *const *in, void *const *out)
+{
+    const bool tc = b->mode == SHT_TC_BF16X3;
     for (int f = 0; f < b->nfields; ++f) {
         sht::BatchField &bf = b->h_fields[f];
         const sht::Plan &p = *b->plans[b->field_plan[f]];
         bf.pv = p.view32();
         bf.in = static_cast<const float *>(in[f]);
         bf.out = static_cast<float *>(out[f]);
-        bf.inter = b->d_inter + b->inter_off[f];
+        bf.inter = b->d_inter + (tc ? b->inter_tc[f] : b->inter_off[f]);
+        if (tc) {
+            BatchCopy &c = b->h_copies[f];
+            float2 *slot = reinterpret_cast<float2 *>(b->d_gspec + b->field_gspec[f]);
+            c.n = p.nlm;
+            c.src = synth ? static_cast<const float2 *>(in[f]) : slot;
+            c.dst = synth ? slot : static_cast<float2 *>(out[f]);
+        }
         // row FFT tiles for power-of-two lengths <= 2^10, else the mixed-radix kernel
         const int H = p.nphi / 2;
         int logH = 0;
@@ -82,7 +127,27 @@ void fill_fields(sht_batch_plan *b, void *const *in, void *const *out)
     }
 }
 
-// Enqueue the four steps of one direction on stream s.
+cudaError_t launch_copies(sht_batch_plan *b, cudaStream_t s)
+{
+    k_batch_copy<<<dim3(16, (unsigned)b->nfields), 256, 0, s>>>(b->d_copies);
+    return cudaGetLastError();
+}
+
+// Tensor-core mode: one contraction per group of equal shape.
+cudaError_t group_contractions(sht_batch_plan *b, bool synth, cudaStream_t s)
+{
+    for (size_t g = 0; g < b->group_fields.size(); ++g) {
+        sht::Plan &p = *b->plans[g];
+        float *spec = b->d_gspec + b->gspec_off[g], *inter = b->d_inter + b->ginter_off[g];
+        const int nb = (int)b->group_fields[g].size();
+        cudaError_t e = synth ? sht::tc_batch_legendre(p, true, spec, inter, nb, s)
+                              : sht::tc_batch_legendre(p, false, inter, spec, nb, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Enqueue the steps of one direction on stream s.
 cudaError_t enqueue(sht_batch_plan *b, bool synth, cudaStream_t s)
 {
     cudaError_t e = cudaMemcpyAsync(b->d_fields, b->h_fields, sizeof(sht::BatchField) * b->nfields,
@@ -90,6 +155,21 @@ cudaError_t enqueue(sht_batch_plan *b, bool synth, cudaStream_t s)
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(b->d_counters, 0, 4 * sizeof(int), s);
     if (e != cudaSuccess) return e;
+    if (b->mode == SHT_TC_BF16X3) {
+        e = cudaMemcpyAsync(b->d_copies, b->h_copies, sizeof(BatchCopy) * b->nfields, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+        if (synth) {
+            if ((e = launch_copies(b, s)) != cudaSuccess) return e;
+            if ((e = group_contractions(b, true, s)) != cudaSuccess) return e;
+            return sht::launch_batch_fft(true, b->d_fields, b->d_tiles + b->tile_off[1], b->ntile[1],
+                                         b->d_counters + 1, b->ctas_fft, b->fft_smem, s);
+        }
+        e = sht::launch_batch_fft(false, b->d_fields, b->d_tiles + b->tile_off[2], b->ntile[2], b->d_counters + 2,
+                                  b->ctas_fft, b->fft_smem, s);
+        if (e != cudaSuccess) return e;
+        if ((e = group_contractions(b, false, s)) != cudaSuccess) return e;
+        return launch_copies(b, s);
+    }
     if (synth) {
         e = sht::launch_batch_legendre(true, b->d_fields, b->d_tiles + b->tile_off[0], b->ntile[0], b->d_counters + 0,
                                        b->ctas_legendre_syn, s);
@@ -117,7 +197,7 @@ int run(sht_batch_plan *b, bool synth, void *const *in, void *const *out, int us
     // the previous launch copies h_fields when it runs: wait for it before overwriting
     cudaError_t e = cudaEventSynchronize(b->done);
     if (e != cudaSuccess) return bfail(SHT_ECUDA, std::string("waiting for the previous batch call: ") + cudaGetErrorString(e));
-    fill_fields(b, in, out);
+    fill_fields(b, synth, in, out);
     const int dir = synth ? 0 : 1;
     if (use_graph) {
         if (!b->graph[dir]) {
@@ -148,15 +228,82 @@ int run(sht_batch_plan *b, bool synth, void *const *in, void *const *out, int us
     return SHT_OK;
 }
 
+// Automatic mode: time a synthesis + analysis of zero fields on each path
+// (direct launches, after a warm-up) and keep the faster.
+int choose_mode(sht_batch_plan *b)
+{
+    const int nf = b->nfields;
+    std::vector<size_t> so(nf), go(nf);
+    size_t bytes = 0;
+    for (int f = 0; f < nf; ++f) {
+        const sht::Plan &p = *b->plans[b->field_plan[f]];
+        so[f] = bytes;
+        bytes = (bytes + (size_t)p.nlm * 8 + 255) & ~(size_t)255;
+        go[f] = bytes;
+        bytes = (bytes + (size_t)p.nlat * p.nphi * 4 + 255) & ~(size_t)255;
+    }
+    unsigned char *buf = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&buf, bytes);
+    if (e == cudaSuccess) e = cudaMemset(buf, 0, bytes);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    std::vector<void *> spec(nf), grid(nf);
+    for (int f = 0; f < nf && buf; ++f) {
+        spec[f] = buf + so[f];
+        grid[f] = buf + go[f];
+    }
+    int rc = SHT_OK;
+    float best = 0.f;
+    int best_mode = SHT_F32;
+    const int modes[2] = {SHT_F32, SHT_TC_BF16X3};
+    for (int k = 0; k < 2 && e == cudaSuccess && rc == SHT_OK; ++k) {
+        b->mode = modes[k];
+        for (int it = 0; it < 5 && rc == SHT_OK; ++it) {
+            if (it == 2) e = cudaEventRecord(e0, s);
+            rc = run(b, true, spec.data(), grid.data(), 0, s);
+            if (rc == SHT_OK) rc = run(b, false, grid.data(), spec.data(), 0, s);
+        }
+        if (rc != SHT_OK) break;
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        b->tuned_ms[k] = ms / 3.f;
+        if (e == cudaSuccess && (k == 0 || ms < best)) {
+            best = ms;
+            best_mode = modes[k];
+        }
+    }
+    if (s) cudaStreamSynchronize(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(buf);
+    b->mode = best_mode;
+    if (rc != SHT_OK) return rc;
+    if (e != cudaSuccess) return bfail(SHT_ECUDA, std::string("timing the batch paths: ") + cudaGetErrorString(e));
+    return SHT_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 int sht_batch_create(int nfields, const int *lmax, const int *nlat, const int *nphi, sht_batch *out)
 {
+    return sht_batch_create_mode(nfields, lmax, nlat, nphi, SHT_F32, out);
+}
+
+int sht_batch_create_mode(int nfields, const int *lmax, const int *nlat, const int *nphi, int mode, sht_batch *out)
+{
     if (!out) return bfail(SHT_EINVAL, "out is NULL");
     *out = nullptr;
     if (nfields < 1 || !lmax || !nlat || !nphi) return bfail(SHT_EINVAL, "need nfields >= 1 and size arrays");
+    if (mode != SHT_F32 && mode != SHT_TC_BF16X3 && mode != SHT_F32_AUTO)
+        return bfail(SHT_EINVAL, "batch mode must be SHT_F32, SHT_TC_BF16X3 or SHT_F32_AUTO");
     for (int f = 0; f < nfields; ++f) {
         if (lmax[f] < 0 || nlat[f] < lmax[f] + 1 || nphi[f] < 2 * lmax[f] + 1)
             return bfail(SHT_EINVAL, "field " + std::to_string(f) + ": need nlat >= lmax+1 and nphi >= 2 lmax + 1");
@@ -193,6 +340,8 @@ int sht_batch_create(int nfields, const int *lmax, const int *nlat, const int *n
         }
         b->field_plan.push_back(it->second);
     }
+    b->group_fields.assign(b->plans.size(), std::vector<int>());
+    for (int f = 0; f < nfields; ++f) b->group_fields[b->field_plan[f]].push_back(f);
     // intermediates, tile lists (longest first)
     size_t inter = 0;
     std::vector<std::pair<double, int4>> syn, ffts, ana;
@@ -217,6 +366,32 @@ int sht_batch_create(int nfields, const int *lmax, const int *nlat, const int *n
         for (int p0 = 0; p0 < p.npairs; p0 += G)
             ffts.push_back({(double)G * p.nphi * (logH + 2) + p.mmax, make_int4(f, p0, 0, 0)});
     }
+    // tensor-core layout: each group's intermediates and spectra contiguous
+    bool tc_ok = mode != SHT_F32;
+    size_t inter_tc = 0, gspec = 0;
+    b->inter_tc.assign(nfields, 0);
+    b->field_gspec.assign(nfields, 0);
+    for (size_t g = 0; g < b->plans.size() && tc_ok; ++g) {
+        const sht::Plan &p = *b->plans[g];
+        const size_t stride = (size_t)(p.mmax + 1) * p.npairs * 4;
+        b->ginter_off.push_back(inter_tc);
+        b->gspec_off.push_back(gspec);
+        for (size_t i = 0; i < b->group_fields[g].size(); ++i) {
+            b->inter_tc[b->group_fields[g][i]] = inter_tc + i * stride;
+            b->field_gspec[b->group_fields[g][i]] = gspec + i * (size_t)p.nlm * 2;
+        }
+        inter_tc = (inter_tc + b->group_fields[g].size() * stride + 63) & ~(size_t)63;
+        gspec = (gspec + b->group_fields[g].size() * (size_t)p.nlm * 2 + 63) & ~(size_t)63;
+        const int rc = sht::tc_batch_prepare(*b->plans[g], (int)b->group_fields[g].size());
+        if (rc) {
+            if (mode == SHT_TC_BF16X3) {
+                free_batch(b);
+                return rc;   // message set by the preparation
+            }
+            tc_ok = false;   // automatic mode: keep the CUDA-core path
+        }
+    }
+    if (tc_ok) inter = std::max(inter, inter_tc);
     auto by_cost = [](const std::pair<double, int4> &a, const std::pair<double, int4> &c) { return a.first > c.first; };
     std::stable_sort(syn.begin(), syn.end(), by_cost);
     std::stable_sort(ffts.begin(), ffts.end(), by_cost);
@@ -247,13 +422,32 @@ int sht_batch_create(int nfields, const int *lmax, const int *nlat, const int *n
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_inter, sizeof(float) * std::max<size_t>(inter, 64));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && tc_ok) e = cudaMallocHost(&b->h_copies, sizeof(BatchCopy) * nfields);
+    if (e == cudaSuccess && tc_ok) e = cudaMalloc(&b->d_copies, sizeof(BatchCopy) * nfields);
+    if (e == cudaSuccess && tc_ok) e = cudaMalloc(&b->d_gspec, sizeof(float) * std::max<size_t>(gspec, 64));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         free_batch(b);
         return bfail(SHT_ENOMEM, std::string("allocating the batch plan: ") + cudaGetErrorString(e));
     }
+    b->mode = mode == SHT_TC_BF16X3 ? SHT_TC_BF16X3 : SHT_F32;
+    if (mode == SHT_F32_AUTO && tc_ok) {
+        const int rc = choose_mode(b);
+        if (rc) {
+            sht_batch_destroy(b);
+            return rc;
+        }
+    }
     *out = b;
     return SHT_OK;
+}
+
+int sht_batch_mode(sht_batch b, float *ms_f32, float *ms_tc)
+{
+    if (!b) return bfail(SHT_EINVAL, "null batch handle");
+    if (ms_f32) *ms_f32 = b->tuned_ms[0];
+    if (ms_tc) *ms_tc = b->tuned_ms[1];
+    return b->mode;
 }
 
 void sht_batch_destroy(sht_batch b)

@@ -778,6 +778,38 @@ int run_analys_vec_tc(sht::Plan &p, const void *vt, const void *vp, void *S, voi
 
 int sht::set_error(int code, const std::string &msg) { return fail(code, msg); }
 
+// Uneven batches on the tensor cores (batch.cu): panels and the contraction's
+// operand scratch for `batch` fields of this plan, built outside any capture.
+int sht::tc_batch_prepare(sht::Plan &p, int batch)
+{
+    int rc = ensure_panels(p);
+    if (rc) return rc;
+    const int nb = batch > tc_chunk(false) ? tc_chunk(false) : batch;
+    return ensure_work(p, sht::tc_data_bytes(p.mmax, p.npairs, p.tc_nchunk_s, nb, false));
+}
+
+// The contraction alone, in chunks: synthesis spectra [batch][nlm] -> E/O
+// [batch][mmax+1][npairs][4]; analysis folds (same layout) -> spectra.
+cudaError_t sht::tc_batch_legendre(sht::Plan &p, bool synth, const float *in, float *out, int batch, cudaStream_t s)
+{
+    const int chunk = tc_chunk(false);
+    unsigned char *data = static_cast<unsigned char *>(p.work);
+    const size_t spec_n = (size_t)p.nlm * 2, inter_n = (size_t)(p.mmax + 1) * p.npairs * 4;
+    for (int b0 = 0; b0 < batch; b0 += chunk) {
+        const int nb = batch - b0 < chunk ? batch - b0 : chunk;
+        const float *i = in + (size_t)b0 * (synth ? spec_n : inter_n);
+        float *o = out + (size_t)b0 * (synth ? inter_n : spec_n);
+        cudaError_t e = synth ? sht::launch_tc_legendre(true, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_s, p.d_off_s,
+                                                        p.d_c0_s, p.d_gf_s, p.d_dchunk, data, i, o, nb,
+                                                        sht::OP_SYNTH, p.d_err, false, s)
+                              : sht::launch_tc_legendre(false, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_a, p.d_off_a,
+                                                        p.d_c0_a, p.d_gf_a, p.d_dchunk, data, i, o, nb,
+                                                        sht::OP_ANALYS, p.d_err, false, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 extern "C" {
 
 const char *sht_last_error(void) { return g_err.c_str(); }

@@ -219,6 +219,12 @@ cudaError_t launch_batch_fft(bool synth, const BatchField *fields, const int4 *t
 size_t batch_fft_smem(int H, int G);
 cudaError_t batch_fft_prepare(size_t smem);   // once, outside any stream capture
 
+// Uneven batches on the tensor cores (capi.cu): panels + operand scratch of a
+// plan for up to `batch` fields (SHT status), and the contraction alone over a
+// contiguous group of fields (E/O or folds in [batch][mmax+1][npairs][4]).
+int tc_batch_prepare(Plan &p, int batch);
+cudaError_t tc_batch_legendre(Plan &p, bool synth, const float *in, float *out, int batch, cudaStream_t s);
+
 // Records an error message for sht_last_error and returns `code`.
 int set_error(int code, const std::string &msg);
 int batch_fft_group(int H, int npairs);

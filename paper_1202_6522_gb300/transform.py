@@ -252,17 +252,27 @@ class _AnalysVec(torch.autograd.Function):
 
 class UnevenBatch:
     """Many FP32 scalar fields of different truncations transformed by one
-    graph launch (persistent kernels over a longest-first tile list)."""
+    graph launch.  path="f32": persistent CUDA-core kernels over a
+    longest-first tile list; "tc": one batched tensor-core contraction per
+    group of equal shape; "auto": both timed at construction, the faster kept
+    (``self.path`` tells which, ``self.tuned_ms`` the two times)."""
 
-    def __init__(self, lmax, nlat=None, nphi=None, device=None, use_graph=True):
+    _PATHS = {"f32": C.SHT_F32, "tc": C.SHT_TC_BF16X3, "auto": C.SHT_F32_AUTO}
+
+    def __init__(self, lmax, nlat=None, nphi=None, device=None, use_graph=True, path="f32"):
         self.lmax = [int(v) for v in lmax]
         self.nlat = [l + 1 for l in self.lmax] if nlat is None else [int(v) for v in nlat]
         self.nphi = ([max(_next_pow2(2 * l + 1), 2) for l in self.lmax] if nphi is None
                      else [int(v) for v in nphi])
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.use_graph = use_graph
+        if path not in self._PATHS:
+            raise ValueError("path must be 'f32', 'tc' or 'auto'")
         with torch.cuda.device(self.device):
-            self._h = C.sht_batch_create(self.lmax, self.nlat, self.nphi)
+            self._h = C.sht_batch_create_mode(self.lmax, self.nlat, self.nphi, self._PATHS[path])
+        mode, ms_f32, ms_tc = C.sht_batch_mode(self._h)
+        self.path = "tc" if mode == C.SHT_TC_BF16X3 else "f32"
+        self.tuned_ms = {"f32": ms_f32, "tc": ms_tc} if path == "auto" else None
         self.nlm = [(l + 1) * (l + 2) // 2 for l in self.lmax]
 
     def __del__(self):
