@@ -61,14 +61,14 @@ void free_panels(sht::Plan &p)
 cudaError_t first_live_scalar(sht::Plan &p)
 {
     int ts = 0, ta = 0;
-    cudaError_t e = sht::launch_panel_first_live(true, p.lmax, p.mmax, p.npairs, p.d_off_s, p.panel_s, p.polar_thr,
+    cudaError_t e = sht::launch_panel_first_live(true, p.lmax, p.mmax, p.mres, p.npairs, p.d_off_s, p.panel_s, p.polar_thr,
                                                  p.d_c0_s, ts, 0, p.d_gf_s);
     if (e == cudaSuccess)
-        e = sht::launch_panel_first_live(false, p.lmax, p.mmax, p.npairs, p.d_off_a, p.panel_a, p.polar_thr,
+        e = sht::launch_panel_first_live(false, p.lmax, p.mmax, p.mres, p.npairs, p.d_off_a, p.panel_a, p.polar_thr,
                                          p.d_c0_a, ta, 0, p.d_gf_a);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess)
-        e = sht::tc_polar_stats(p.lmax, p.mmax, p.npairs, p.d_c0_s, p.d_c0_a, p.polar_skip_s, p.polar_skip_a,
+        e = sht::tc_polar_stats(p.lmax, p.mmax, p.mres, p.npairs, p.d_c0_s, p.d_c0_a, p.polar_skip_s, p.polar_skip_a,
                                 p.d_gf_s, p.d_gf_a);
     return e;
 }
@@ -80,11 +80,11 @@ cudaError_t first_live_vector(sht::Plan &p, int *tmp)
     int T_s = 0, T_a = 0, nt = 0;
     sht::tc_tile_counts(p.lmax, p.npairs, T_s, T_a);
     const int ns = (p.mmax + 1) * T_s, na = (p.mmax + 1) * T_a;
-    cudaError_t e = sht::launch_panel_first_live(true, p.lmax, p.mmax, p.npairs, p.d_off_s, p.dpanel_s, p.polar_thr,
+    cudaError_t e = sht::launch_panel_first_live(true, p.lmax, p.mmax, p.mres, p.npairs, p.d_off_s, p.dpanel_s, p.polar_thr,
                                                  tmp, nt, 0);
     if (e == cudaSuccess) e = sht::launch_min_int(p.d_c0_s, tmp, p.d_c0v_s, ns, 0);
     if (e == cudaSuccess)
-        e = sht::launch_panel_first_live(false, p.lmax, p.mmax, p.npairs, p.d_off_a, p.dpanel_a, p.polar_thr, tmp,
+        e = sht::launch_panel_first_live(false, p.lmax, p.mmax, p.mres, p.npairs, p.d_off_a, p.dpanel_a, p.polar_thr, tmp,
                                          nt, 0);
     if (e == cudaSuccess) e = sht::launch_min_int(p.d_c0_a, tmp, p.d_c0v_a, na, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -97,10 +97,9 @@ cudaError_t first_live_vector(sht::Plan &p, int *tmp)
 int ensure_panels(sht::Plan &p)
 {
     if (p.panel_s) return SHT_OK;
-    if (p.mres > 1) return fail(SHT_EUNSUPPORTED, "the tensor-core modes need mres = 1");
     std::vector<unsigned long long> off_s, off_a, dchunk;
     size_t bs = 0, ba = 0, nch = 0;
-    sht::tc_panel_layout(p.lmax, p.mmax, p.npairs, off_s, off_a, bs, ba, dchunk, nch);
+    sht::tc_panel_layout(p.lmax, p.mmax, p.mres, p.npairs, off_s, off_a, bs, ba, dchunk, nch);
     const size_t ob = off_s.size() * sizeof(unsigned long long);
     int T_s = 0, T_a = 0;
     sht::tc_tile_counts(p.lmax, p.npairs, T_s, T_a);
@@ -150,7 +149,7 @@ int ensure_vec_panels(sht::Plan &p)
     if (p.dpanel_s) return SHT_OK;
     std::vector<unsigned long long> off_s, off_a, dchunk;
     size_t bs = 0, ba = 0, nch = 0;
-    sht::tc_panel_layout(p.lmax, p.mmax, p.npairs, off_s, off_a, bs, ba, dchunk, nch);
+    sht::tc_panel_layout(p.lmax, p.mmax, p.mres, p.npairs, off_s, off_a, bs, ba, dchunk, nch);
     int T_s = 0, T_a = 0;
     sht::tc_tile_counts(p.lmax, p.npairs, T_s, T_a);
     const size_t ns = (size_t)(p.mmax + 1) * T_s, na = (size_t)(p.mmax + 1) * T_a;
@@ -198,21 +197,21 @@ cudaError_t otf_build(sht::Plan &p, int *flag_dev)
                                     0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess)
-        e = sht::tc_polar_stats(p.lmax, p.mmax, p.npairs, p.d_c0o_s, p.d_c0o_a, p.otf_skip_s, p.otf_skip_a);
+        e = sht::tc_polar_stats(p.lmax, p.mmax, p.mres, p.npairs, p.d_c0o_s, p.d_c0o_a, p.otf_skip_s, p.otf_skip_a);
     return e;
 }
 
 int ensure_otf(sht::Plan &p)
 {
     if (p.otf_state > 0) return SHT_OK;
-    if (p.mres > 1) return fail(SHT_EUNSUPPORTED, "the tensor-core modes need mres = 1");
+    if (p.mres > 1) return fail(SHT_EUNSUPPORTED, "this tensor-core mode needs mres = 1");
     if (p.otf_state < 0)
         return fail(SHT_EUNSUPPORTED, "on-the-fly mode: the FP32 recurrence would leave the FP32 range for this plan");
     std::vector<unsigned long long> segoff;
     const size_t nseg = sht::otf_segment_offsets(p.lmax, p.mmax, segoff);
     std::vector<unsigned long long> off_s, off_a, dchunk;
     size_t bs = 0, ba = 0, nch = 0;
-    sht::tc_panel_layout(p.lmax, p.mmax, p.npairs, off_s, off_a, bs, ba, dchunk, nch);
+    sht::tc_panel_layout(p.lmax, p.mmax, p.mres, p.npairs, off_s, off_a, bs, ba, dchunk, nch);
     int T_s = 0, T_a = 0;
     sht::tc_tile_counts(p.lmax, p.npairs, T_s, T_a);
     int *flag = nullptr;
@@ -253,7 +252,7 @@ size_t elem_size(int mode) { return (mode == SHT_F64 || mode == SHT_TC_F64) ? si
 int ensure_panels64(sht::Plan &p)
 {
     if (p.p64_s) return SHT_OK;
-    if (p.mres > 1) return fail(SHT_EUNSUPPORTED, "the tensor-core modes need mres = 1");
+    if (p.mres > 1) return fail(SHT_EUNSUPPORTED, "this tensor-core mode needs mres = 1");
     if (p.lmax > 1023 || p.npairs > 512)
         return fail(SHT_EUNSUPPORTED, "SHT_TC_F64 needs lmax <= 1023 and nlat <= 1024");
     std::vector<unsigned long long> off_s, off_a, dchunk;
@@ -608,7 +607,7 @@ int run_synth_tc(sht::Plan &p, const void *spec, void *grid, int batch, sht::Op 
         const float *in = static_cast<const float *>(spec) + (size_t)b0 * p.nlm * 2;
         float *out = static_cast<float *>(grid) + (size_t)b0 * p.nlat * p.nphi;
         int rc = timed(p, SHT_K_TC_SYNTH, s, "tensor-core synthesis launch", [&] {
-            return sht::launch_tc_legendre(true, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_s, p.d_off_s, p.d_c0_s,
+            return sht::launch_tc_legendre(true, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.panel_s, p.d_off_s, p.d_c0_s,
                                            p.d_gf_s, p.d_dchunk, data, in, eo, nb, op, p.d_err, false, s);
         });
         if (rc) return rc;
@@ -632,7 +631,7 @@ int run_analys_tc(sht::Plan &p, const void *grid, void *spec, int batch, sht::Op
                        [&] { return sht::launch_fft_analys<float>(p.view32(), in, sd, nb, op, false, s); });
         if (rc) return rc;
         rc = timed(p, SHT_K_TC_ANALYS, s, "tensor-core analysis launch", [&] {
-            return sht::launch_tc_legendre(false, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_a, p.d_off_a, p.d_c0_a,
+            return sht::launch_tc_legendre(false, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.panel_a, p.d_off_a, p.d_c0_a,
                                            p.d_gf_a, p.d_dchunk, data, sd, out, nb, op, p.d_err, false, s);
         });
         if (rc) return rc;
@@ -727,7 +726,7 @@ int run_synth_vec_tc(sht::Plan &p, const void *S, const void *T, void *vt, void 
         const int nb = batch - b0 < chunk ? batch - b0 : chunk;
         const size_t so = (size_t)b0 * p.nlm * 2, go = (size_t)b0 * p.nlat * p.nphi;
         int rc = timed(p, SHT_K_TC_SYNTH_VEC, s, "tensor-core vector synthesis launch", [&] {
-            return sht::launch_tc_vec(true, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_s, p.dpanel_s, p.d_off_s,
+            return sht::launch_tc_vec(true, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.panel_s, p.dpanel_s, p.d_off_s,
                                       p.d_c0v_s, p.d_dchunk, data, static_cast<const float *>(S) + so,
                                       static_cast<const float *>(T) + so, eot, eop, p.t32.st, nb, op, p.d_err, false,
                                       s);
@@ -765,7 +764,7 @@ int run_analys_vec_tc(sht::Plan &p, const void *vt, const void *vp, void *S, voi
         });
         if (rc) return rc;
         rc = timed(p, SHT_K_TC_ANALYS_VEC, s, "tensor-core vector analysis launch", [&] {
-            return sht::launch_tc_vec(false, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_a, p.dpanel_a, p.d_off_a,
+            return sht::launch_tc_vec(false, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.panel_a, p.dpanel_a, p.d_off_a,
                                       p.d_c0v_a, p.d_dchunk, data, sdt, sdp, static_cast<float *>(S) + so,
                                       static_cast<float *>(T) + so, p.t32.st, nb, op, p.d_err, false, s);
         });
@@ -799,10 +798,10 @@ cudaError_t sht::tc_batch_legendre(sht::Plan &p, bool synth, const float *in, fl
         const int nb = batch - b0 < chunk ? batch - b0 : chunk;
         const float *i = in + (size_t)b0 * (synth ? spec_n : inter_n);
         float *o = out + (size_t)b0 * (synth ? inter_n : spec_n);
-        cudaError_t e = synth ? sht::launch_tc_legendre(true, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_s, p.d_off_s,
+        cudaError_t e = synth ? sht::launch_tc_legendre(true, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.panel_s, p.d_off_s,
                                                         p.d_c0_s, p.d_gf_s, p.d_dchunk, data, i, o, nb,
                                                         sht::OP_SYNTH, p.d_err, false, s)
-                              : sht::launch_tc_legendre(false, p.lmax, p.mmax, p.npairs, p.nlm, p.panel_a, p.d_off_a,
+                              : sht::launch_tc_legendre(false, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.panel_a, p.d_off_a,
                                                         p.d_c0_a, p.d_gf_a, p.d_dchunk, data, i, o, nb,
                                                         sht::OP_ANALYS, p.d_err, false, s);
         if (e != cudaSuccess) return e;

@@ -231,10 +231,11 @@ int batch_fft_group(int H, int npairs);
 constexpr int kBatchSynthPairs = 256;   // pairs per synthesis tile (128 threads x 2)
 constexpr int kBatchMaxPairs = 512;     // analysis CTA (256 threads x 2 pairs) limit
 
-// Tensor-core path (tc.cu).
+// Tensor-core path (tc.cu).  `mres` is the plan's order stride everywhere:
+// order index m (0 .. mmax) is the order m mres.
 // Panel byte offsets per order (synthesis and analysis layouts), their total
 // sizes, and the first synthesis data chunk of each order.
-void tc_panel_layout(int lmax, int mmax, int npairs, std::vector<unsigned long long> &off_s,
+void tc_panel_layout(int lmax, int mmax, int mres, int npairs, std::vector<unsigned long long> &off_s,
                      std::vector<unsigned long long> &off_a, size_t &bytes_s, size_t &bytes_a,
                      std::vector<unsigned long long> &dchunk, size_t &nchunk_s);
 // Bytes of the blocked data operand (either layout) for `batch` fields.
@@ -247,14 +248,14 @@ cudaError_t launch_build_panels(const PlanView<double> &pv, const unsigned long 
 // bf16 hi/lo in `data`; skipped when `prepped`, i.e. `data` already holds
 // this operand) then the tcgen05 kernel.  Synthesis: spectra -> E/O;
 // analysis: s/d folds -> spectra.
-cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
+cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const unsigned char *panel,
                                const unsigned long long *off, const int *c0, const unsigned short *gfirst,
                                const unsigned long long *dchunk,
                                unsigned char *data, const float *in, float *out, int batch, Op op, int *err,
                                bool prepped, cudaStream_t st);
 // Vector contraction of <= tc_vec_max_batch() fields.  Synthesis: (S, T) ->
 // (theta E/O, phi E/O); analysis: (theta, phi) folds -> (S, T).
-cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
+cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const unsigned char *panel,
                           const unsigned char *dpanel, const unsigned long long *off, const int *c0,
                           const unsigned long long *dchunk, unsigned char *data, const float *in0, const float *in1,
                           float *out0, float *out1, const float *st_pairs, int batch, Op op, int *err, bool prepped,
@@ -266,13 +267,13 @@ int tc_otf_max_batch();
 inline int tc_rows(int batch, bool vec) { return (vec ? 2 : 1) * (((2 * batch + 31) / 32) * 32); }
 // Static polar optimisation: per (m, tile) first chunk with a panel value >=
 // thr; with `gfirst`, also per 8-row group of the tile ([m][tile][16]).
-cudaError_t launch_panel_first_live(bool synth, int lmax, int mmax, int npairs, const unsigned long long *off,
+cudaError_t launch_panel_first_live(bool synth, int lmax, int mmax, int mres, int npairs, const unsigned long long *off,
                                     const unsigned char *panel, float thr, int *c0, int &ntiles, cudaStream_t st,
                                     unsigned short *gfirst = nullptr);
 void tc_tile_counts(int lmax, int npairs, int &ntiles_s, int &ntiles_a);
 // Fractions of panel bytes skipped: per 8-row group when the group tables are
 // given, else per whole chunk.
-cudaError_t tc_polar_stats(int lmax, int mmax, int npairs, const int *d_c0_s, const int *d_c0_a, double &frac_s,
+cudaError_t tc_polar_stats(int lmax, int mmax, int mres, int npairs, const int *d_c0_s, const int *d_c0_a, double &frac_s,
                            double &frac_a, const unsigned short *d_gf_s = nullptr,
                            const unsigned short *d_gf_a = nullptr);
 int tc_max_batch();

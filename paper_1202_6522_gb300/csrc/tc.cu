@@ -82,11 +82,12 @@ k_build_panels(PlanView<double> pv, const unsigned long long *__restrict__ off_s
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const int npairs = pv.npairs, lmax = pv.lmax;
     if (p >= npairs) return;
-    const int L = lmax - m + 1;
+    const int mo = m * pv.mres;                      // the order of order index m
+    const int L = lmax - mo + 1;
     const int Le = (L + 1) / 2;
     const int nch = (Le + kKc - 1) / kKc;            // synthesis chunks per tile
     const int kch = (npairs + kKc - 1) / kKc;        // analysis chunks (over pairs)
-    const long col = col_of(lmax, m);
+    const long col = col_of_mres(lmax, m, pv.mres);
     const double x = pv.x[p];
     double y2 = pv.pmm[(size_t)m * npairs + p], y1 = 0.0;
     int k = pv.pmmk[(size_t)m * npairs + p];
@@ -105,7 +106,7 @@ k_build_panels(PlanView<double> pv, const unsigned long long *__restrict__ off_s
             k -= 1;
         }
         if (k != 0) continue;
-        const double P = deriv ? fma((double)(m + nn) * x, y1, -pv.dc[col + nn] * y2) : y1;
+        const double P = deriv ? fma((double)(mo + nn) * x, y1, -pv.dc[col + nn] * y2) : y1;
         if (P == 0.0) continue;
         __nv_bfloat16 hi, lo;
         split_bf16_d(P, hi, lo);
@@ -167,12 +168,12 @@ __device__ __forceinline__ void put_row8(unsigned char *bh, unsigned char *bl, i
 // beyond the batch) are left as they are: they only feed output columns that
 // are never read.  grid = (ceil(max chunks * items / kPrepThreads), mmax + 1).
 __global__ void __launch_bounds__(kPrepThreads)
-k_tc_prep(int synth, int vec, int lmax, int mmax, int npairs, int nlm, int batch, int rows, int op,
+k_tc_prep(int synth, int vec, int lmax, int mmax, int mres, int npairs, int nlm, int batch, int rows, int op,
           const float *__restrict__ in0, const float *__restrict__ in1, const unsigned long long *__restrict__ dchunk,
           unsigned char *__restrict__ data)
 {
-    const int m = blockIdx.y;
-    const int L = lmax - m + 1, Le = (L + 1) / 2;
+    const int m = blockIdx.y;   // order index: the order is m mres
+    const int L = lmax - m * mres + 1, Le = (L + 1) / 2;
     const int nch = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
     const int nq = vec ? 2 : 1;
     // items per chunk: synthesis (quantity, field, parity, K half); analysis (quantity, field, K half)
@@ -191,7 +192,7 @@ k_tc_prep(int synth, int vec, int lmax, int mmax, int npairs, int nlm, int batch
         const int cls = it & 1;
         it >>= 1;
         const int b = it % batch, q = it / batch;
-        const long col = col_of(lmax, m);
+        const long col = col_of_mres(lmax, m, mres);
         const float2 *A = reinterpret_cast<const float2 *>(q ? in1 : in0) + (size_t)b * nlm + col;
         // adjoint of analysis: b / c_m (scalar) or b / (c_m n (n + 1)) (vector)
         const float cadj = (op == OP_ANALYS_ADJ && m > 0) ? 0.5f : 1.0f;
@@ -203,7 +204,7 @@ k_tc_prep(int synth, int vec, int lmax, int mmax, int npairs, int nlm, int batch
             if (nn < L) v = A[nn];
             float sc = cadj;
             if (vec && op == OP_ANALYS_ADJ) {
-                const int n = m + nn;
+                const int n = m * mres + nn;
                 sc = (n == 0) ? 0.f : cadj / ((float)n * (float)(n + 1));
             }
             re[i] = v.x * sc;
@@ -256,6 +257,7 @@ __host__ __device__ inline size_t smem_bytes_of(int npanels, int rows, int stage
 
 struct TcArgs {
     int lmax, mmax, npairs, nlm, batch, rows, ntiles, stages, op;
+    int mres;                              // order stride: order index m is the order m mres
     const float *in;                       // raw FP32 s/d folds (warp-specialised analysis)
     int fused;                             // synthesis: spectra converted in the kernel (tensor map)
     const unsigned char *panel, *dpanel;   // dpanel: vector transforms only
@@ -340,9 +342,9 @@ __global__ void __launch_bounds__(kWsThreads, kWsCtasPerSm) k_tc_ws(TcArgs a, co
     const int m = blockIdx.x / a.ntiles;
     const int tile = blockIdx.x - m * a.ntiles;
     const int lmax = a.lmax, npairs = a.npairs;
-    const int L = lmax - m + 1;
+    const int L = lmax - m * a.mres + 1;   // m is the order index
     const int Le = (L + 1) / 2;
-    const long col = col_of(lmax, m);
+    const long col = col_of_mres(lmax, m, a.mres);
     if (!SYNTH && tile * kRows >= Le) return;
     const int nchunks = SYNTH ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
     const unsigned char *panel = a.panel + a.off[m] + (size_t)tile * nchunks * kChunkPanel;
@@ -646,9 +648,9 @@ __global__ void __launch_bounds__(128, 1) k_tc_vec(TcArgs a)
     const int m = blockIdx.x / a.ntiles;
     const int tile = blockIdx.x - m * a.ntiles;
     const int lmax = a.lmax, npairs = a.npairs;
-    const int L = lmax - m + 1;
+    const int L = lmax - m * a.mres + 1;   // m is the order index
     const int Le = (L + 1) / 2;
-    const long col = col_of(lmax, m);
+    const long col = col_of_mres(lmax, m, a.mres);
     if (!SYNTH && tile * kRows >= Le) return;
     const int nchunks = SYNTH ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
     const size_t poff = a.off[m] + (size_t)tile * nchunks * kChunkPanel;
@@ -732,7 +734,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_vec(TcArgs a)
         tc::tc_fence_after();
         const int row = tile * kRows + warp * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-        const float fm = (float)m;
+        const float fm = (float)(m * a.mres);
         float isn = 1.f;
         if (SYNTH && row < npairs) isn = 1.f / a.st[row];
         for (int cls = 0; cls < 2; ++cls) {
@@ -766,7 +768,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_vec(TcArgs a)
                     } else {
                         const int nn = 2 * row + cls;
                         if (nn >= L) continue;
-                        const int n = m + nn;
+                        const int n = m * a.mres + nn;
                         float sc;
                         if (a.op == OP_SYNTH_ADJ) sc = (m > 0) ? 2.f : 1.f;
                         else sc = (n == 0) ? 0.f : 1.f / ((float)n * (float)(n + 1));
@@ -1261,12 +1263,12 @@ __global__ void __launch_bounds__(kOtfThreads, 2) k_tc_otf(OtfArgs a)
 // whose panel blocks hold a value >= thr.  One CTA per (m, tile).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128)
-k_panel_first_live(int synth, int lmax, int npairs, int ntiles, const unsigned long long *__restrict__ off,
+k_panel_first_live(int synth, int lmax, int mres, int npairs, int ntiles, const unsigned long long *__restrict__ off,
                    const unsigned char *__restrict__ panel, float thr, int *__restrict__ c0,
                    unsigned short *__restrict__ gfirst)
 {
-    const int m = blockIdx.y, tile = blockIdx.x;
-    const int L = lmax - m + 1, Le = (L + 1) / 2;
+    const int m = blockIdx.y, tile = blockIdx.x;   // m: order index
+    const int L = lmax - m * mres + 1, Le = (L + 1) / 2;
     const int nchunks = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
     const bool valid = synth || tile * kRows < Le;
     constexpr int NG = kRows / 8;
@@ -1353,16 +1355,16 @@ cudaError_t launch_contraction(K kernel, bool synth, int lmax, int mmax, int npa
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep(bool synth, bool vec, int lmax, int mmax, int npairs, int nlm, int batch, int rows, Op op,
-                        const float *in0, const float *in1, const unsigned long long *dchunk, unsigned char *data,
-                        cudaStream_t st)
+cudaError_t launch_prep(bool synth, bool vec, int lmax, int mmax, int mres, int npairs, int nlm, int batch, int rows,
+                        Op op, const float *in0, const float *in1, const unsigned long long *dchunk,
+                        unsigned char *data, cudaStream_t st)
 {
     const int Le0 = (lmax + 2) / 2;
     const int maxch = synth ? (Le0 + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
     const long items = (long)(synth ? 4 : 2) * batch * (vec ? 2 : 1);
     dim3 g((unsigned)((maxch * items + kPrepThreads - 1) / kPrepThreads), (unsigned)(mmax + 1));
-    k_tc_prep<<<g, kPrepThreads, 0, st>>>(synth ? 1 : 0, vec ? 1 : 0, lmax, mmax, npairs, nlm, batch, rows, (int)op, in0, in1,
-                                 dchunk, data);
+    k_tc_prep<<<g, kPrepThreads, 0, st>>>(synth ? 1 : 0, vec ? 1 : 0, lmax, mmax, mres, npairs, nlm, batch, rows,
+                                          (int)op, in0, in1, dchunk, data);
     return cudaGetLastError();
 }
 
@@ -1428,7 +1430,7 @@ int tc_max_batch() { return 64; }
 int tc_otf_max_batch() { return 32; }
 int tc_vec_max_batch() { return 32; }
 
-void tc_panel_layout(int lmax, int mmax, int npairs, std::vector<unsigned long long> &off_s,
+void tc_panel_layout(int lmax, int mmax, int mres, int npairs, std::vector<unsigned long long> &off_s,
                      std::vector<unsigned long long> &off_a, size_t &bytes_s, size_t &bytes_a,
                      std::vector<unsigned long long> &dchunk, size_t &nchunk_s)
 {
@@ -1438,8 +1440,8 @@ void tc_panel_layout(int lmax, int mmax, int npairs, std::vector<unsigned long l
     const int T = (npairs + kRows - 1) / kRows;
     const int kch = (npairs + kKc - 1) / kKc;
     unsigned long long s = 0, q = 0, ch = 0;
-    for (int m = 0; m <= mmax; ++m) {
-        const int L = lmax - m + 1, Le = (L + 1) / 2;
+    for (int m = 0; m <= mmax; ++m) {   // order index m, order m mres
+        const int L = lmax - m * mres + 1, Le = (L + 1) / 2;
         const int nch = (Le + kKc - 1) / kKc;
         const int Mt = (Le + kRows - 1) / kRows;
         off_s[m] = s;
@@ -1489,7 +1491,7 @@ void tc_tile_counts(int lmax, int npairs, int &ntiles_s, int &ntiles_a)
     ntiles_a = (((lmax + 2) / 2) + kRows - 1) / kRows;
 }
 
-cudaError_t tc_polar_stats(int lmax, int mmax, int npairs, const int *d_c0_s, const int *d_c0_a, double &frac_s,
+cudaError_t tc_polar_stats(int lmax, int mmax, int mres, int npairs, const int *d_c0_s, const int *d_c0_a, double &frac_s,
                            double &frac_a, const unsigned short *d_gf_s, const unsigned short *d_gf_a)
 {
     int T_s, T_a;
@@ -1504,7 +1506,7 @@ cudaError_t tc_polar_stats(int lmax, int mmax, int npairs, const int *d_c0_s, co
         if (e == cudaSuccess) e = cudaMemcpy(ga.data(), d_gf_a, sizeof(unsigned short) * ga.size(), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return e;
         for (int m = 0; m <= mmax; ++m) {
-            const int Le = (lmax - m + 2) / 2, nch = (Le + kKc - 1) / kKc;
+            const int Le = (lmax - m * mres + 2) / 2, nch = (Le + kKc - 1) / kKc;
             for (int t = 0; t < T_s; ++t) {
                 const int ng = (std::min(kRows, npairs - kRows * t) + 7) / 8;
                 for (int g = 0; g < ng; ++g) {
@@ -1528,7 +1530,7 @@ cudaError_t tc_polar_stats(int lmax, int mmax, int npairs, const int *d_c0_s, co
         if (e == cudaSuccess) e = cudaMemcpy(c0a.data(), d_c0_a, sizeof(int) * c0a.size(), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return e;
         for (int m = 0; m <= mmax; ++m) {
-            const int Le = (lmax - m + 2) / 2, nch = (Le + kKc - 1) / kKc;
+            const int Le = (lmax - m * mres + 2) / 2, nch = (Le + kKc - 1) / kKc;
             for (int t = 0; t < T_s; ++t) { sk_s += c0s[(size_t)m * T_s + t]; tot_s += nch; }
             for (int t = 0; t < T_a; ++t)
                 if (t * kRows < Le) { sk_a += c0a[(size_t)m * T_a + t]; tot_a += kch; }
@@ -1539,7 +1541,7 @@ cudaError_t tc_polar_stats(int lmax, int mmax, int npairs, const int *d_c0_s, co
     return cudaSuccess;
 }
 
-cudaError_t launch_panel_first_live(bool synth, int lmax, int mmax, int npairs, const unsigned long long *off,
+cudaError_t launch_panel_first_live(bool synth, int lmax, int mmax, int mres, int npairs, const unsigned long long *off,
                                     const unsigned char *panel, float thr, int *c0, int &ntiles, cudaStream_t st,
                                     unsigned short *gfirst)
 {
@@ -1547,11 +1549,11 @@ cudaError_t launch_panel_first_live(bool synth, int lmax, int mmax, int npairs, 
     tc_tile_counts(lmax, npairs, ts, ta);
     ntiles = synth ? ts : ta;
     dim3 g((unsigned)ntiles, (unsigned)(mmax + 1));
-    k_panel_first_live<<<g, 128, 0, st>>>(synth ? 1 : 0, lmax, npairs, ntiles, off, panel, thr, c0, gfirst);
+    k_panel_first_live<<<g, 128, 0, st>>>(synth ? 1 : 0, lmax, mres, npairs, ntiles, off, panel, thr, c0, gfirst);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
+cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const unsigned char *panel,
                                const unsigned long long *off, const int *c0, const unsigned short *gfirst,
                                const unsigned long long *dchunk,
                                unsigned char *data, const float *in, float *out, int batch, Op op, int *err,
@@ -1565,12 +1567,13 @@ cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int n
     const bool fuse_synth = synth && (nlm % 2 == 0);
     if (synth && !fuse_synth && !prepped) {
         cudaError_t e =
-            launch_prep(synth, false, lmax, mmax, npairs, nlm, batch, rows, op, in, nullptr, dchunk, data, st);
+            launch_prep(synth, false, lmax, mmax, mres, npairs, nlm, batch, rows, op, in, nullptr, dchunk, data, st);
         if (e != cudaSuccess) return e;
     }
     TcArgs a{};
     a.lmax = lmax;
     a.mmax = mmax;
+    a.mres = mres;
     a.npairs = npairs;
     a.nlm = nlm;
     a.batch = batch;
@@ -1623,7 +1626,7 @@ cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int npairs, int n
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
+cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const unsigned char *panel,
                           const unsigned char *dpanel, const unsigned long long *off, const int *c0,
                           const unsigned long long *dchunk, unsigned char *data, const float *in0, const float *in1,
                           float *out0, float *out1, const float *st_pairs, int batch, Op op, int *err, bool prepped,
@@ -1633,12 +1636,13 @@ cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int npairs, int nlm, c
     const int rows = 2 * cols_of(batch);   // 4 accumulators x rows columns <= 512
     if (!prepped) {
         cudaError_t e =
-            launch_prep(synth, true, lmax, mmax, npairs, nlm, batch, rows, op, in0, in1, dchunk, data, st);
+            launch_prep(synth, true, lmax, mmax, mres, npairs, nlm, batch, rows, op, in0, in1, dchunk, data, st);
         if (e != cudaSuccess) return e;
     }
     TcArgs a{};
     a.lmax = lmax;
     a.mmax = mmax;
+    a.mres = mres;
     a.npairs = npairs;
     a.nlm = nlm;
     a.batch = batch;
@@ -1694,7 +1698,7 @@ cudaError_t launch_tc_otf(bool synth, int lmax, int mmax, int npairs, int nlm, c
     if (batch < 1 || batch > tc_otf_max_batch()) return cudaErrorInvalidValue;
     const int rows = cols_of(batch);
     // synthesis data chunks are numbered like the segments (one chunk = one segment)
-    cudaError_t e = launch_prep(synth, false, lmax, mmax, npairs, nlm, batch, rows, op, in, nullptr, segoff, data, st);
+    cudaError_t e = launch_prep(synth, false, lmax, mmax, 1, npairs, nlm, batch, rows, op, in, nullptr, segoff, data, st);
     if (e != cudaSuccess) return e;
     OtfArgs a{};
     a.lmax = lmax;

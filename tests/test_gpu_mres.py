@@ -1,4 +1,5 @@
-"""The m-stride variant (orders m = k mres only, one 2 pi / mres sector of longitudes).
+"""The m-stride variant (orders m = k mres only, one 2 pi / mres sector of longitudes),
+on the FP64, FP32 and tensor-core (panel) paths.
 
 Such a field is an ordinary field whose orders off the stride vanish, and its
 grid repeats every 2 pi / mres.  So the oracle is the plain one on the full
@@ -11,7 +12,7 @@ import pytest
 import oracle
 from paper_1202_6522_gb300 import synthetic
 
-from _util import fp32_bound, fp64_bound, normwise
+from _util import fp32_bound, fp64_bound, normwise, tc_bound
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -55,18 +56,18 @@ def _spread(a, lmax, mmax, mres):
     return full
 
 
-@pytest.mark.parametrize("path", ["f64", "f32"])
+@pytest.mark.parametrize("path", ["f64", "f32", "tc"])
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_mres_scalar(SHT, case, path):
     lmax, mmax, mres, nlat, nphi, batch = case
-    sht = SHT(lmax, mmax, nlat, nphi, mres=mres)
+    sht = SHT(lmax, mmax, nlat, nphi, mres=mres, fp32_path="tc" if path == "tc" else "f32")
     assert sht.nlm == len(_strided_index(lmax, mmax, mres))
     rng = np.random.default_rng(7)
     a = (rng.standard_normal((batch, sht.nlm)) + 1j * rng.standard_normal((batch, sht.nlm))) * 0.3
     a[:, : lmax + 1] = a[:, : lmax + 1].real          # order 0 is real
     g = synthetic.grid(nlat, nphi, batch=batch, seed=3)
     cdt, fdt = (np.complex128, np.float64) if path == "f64" else (np.complex64, np.float32)
-    bound = fp64_bound(lmax) if path == "f64" else fp32_bound(lmax)
+    bound = {"f64": fp64_bound, "f32": fp32_bound, "tc": tc_bound}[path](lmax)
     a = a.astype(cdt)
     g = g.astype(fdt)
     got = _np(sht.synth_(torch.from_numpy(a).to(DEV)))
@@ -77,17 +78,34 @@ def test_mres_scalar(SHT, case, path):
     assert normwise(got, ref[..., _strided_index(lmax, mmax, mres)]) < bound
 
 
-def test_mres_vector_and_adjoint(SHT):
+@pytest.mark.parametrize("path", ["f64", "tc"])
+def test_mres_vector_and_adjoint(SHT, path):
     lmax, mmax, mres, nlat, nphi, batch = CASES[1]
-    sht = SHT(lmax, mmax, nlat, nphi, mres=mres)
+    sht = SHT(lmax, mmax, nlat, nphi, mres=mres, fp32_path="tc")
     rng = np.random.default_rng(11)
     S = rng.standard_normal((batch, sht.nlm)) + 1j * rng.standard_normal((batch, sht.nlm))
     T = rng.standard_normal((batch, sht.nlm)) + 1j * rng.standard_normal((batch, sht.nlm))
     S[:, : lmax + 1] = S[:, : lmax + 1].real
     T[:, : lmax + 1] = T[:, : lmax + 1].real
-    vt, vp = sht.synth_vec_(torch.from_numpy(S).to(DEV), torch.from_numpy(T).to(DEV))
     rt, rp = oracle.synth_vec(lmax, mmax * mres, nlat, nphi * mres, _spread(S, lmax, mmax, mres),
                               _spread(T, lmax, mmax, mres))
+    if path == "tc":
+        # the tensor-core vector path (FP32 data); its analysis against the oracle's
+        vt, vp = sht.synth_vec_(torch.from_numpy(S.astype(np.complex64)).to(DEV),
+                                torch.from_numpy(T.astype(np.complex64)).to(DEV))
+        assert normwise(_np(vt), rt[..., :nphi]) < tc_bound(lmax)
+        assert normwise(_np(vp), rp[..., :nphi]) < tc_bound(lmax)
+        gt = synthetic.grid(nlat, nphi, batch=batch, seed=12)
+        gp = synthetic.grid(nlat, nphi, batch=batch, seed=13)
+        Sg, Tg = sht.analys_vec_(torch.from_numpy(gt.astype(np.float32)).to(DEV),
+                                 torch.from_numpy(gp.astype(np.float32)).to(DEV))
+        rS, rT = oracle.analys_vec(lmax, mmax * mres, nlat, nphi * mres, np.tile(gt, (1, 1, mres)),
+                                   np.tile(gp, (1, 1, mres)))
+        idx = _strided_index(lmax, mmax, mres)
+        assert normwise(_np(Sg), rS[..., idx]) < tc_bound(lmax)
+        assert normwise(_np(Tg), rT[..., idx]) < tc_bound(lmax)
+        return
+    vt, vp = sht.synth_vec_(torch.from_numpy(S).to(DEV), torch.from_numpy(T).to(DEV))
     assert normwise(_np(vt), rt[..., :nphi]) < fp64_bound(lmax)
     assert normwise(_np(vp), rp[..., :nphi]) < fp64_bound(lmax)
     # adjoint of synthesis: the sector grid's transposed synthesis, which on the
@@ -105,8 +123,12 @@ def test_mres_index_and_refusals(SHT):
     sht = SHT(31, 7, 32, 16, mres=4)
     assert sht.lm_index(4, 4) == 32                 # order index 1 starts after the 32 degrees of m = 0
     assert sht.lm_index(5, 2) == -1                 # m off the stride
-    tc = SHT(31, 7, 32, 16, fp32_path="tc", mres=4)
+    # the on-the-fly and FP64-accurate tensor-core modes keep mres = 1
+    otf = SHT(31, 7, 32, 16, fp32_path="otf", mres=4)
     with pytest.raises(C.SHTError):
-        tc.synth_(torch.zeros(1, tc.nlm, dtype=torch.complex64, device=DEV))
+        otf.synth_(torch.zeros(1, otf.nlm, dtype=torch.complex64, device=DEV))
+    tc64 = SHT(31, 7, 32, 16, fp64_path="tc", mres=4)
+    with pytest.raises(C.SHTError):
+        tc64.synth_(torch.zeros(1, tc64.nlm, dtype=torch.complex128, device=DEV))
     with pytest.raises(ValueError):
         SHT(31, 8, 32, 32, mres=4)                  # mmax mres > lmax (SHT_EINVAL)
