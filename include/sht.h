@@ -129,10 +129,9 @@ SHT_API int sht_create(int lmax, int mmax, int nlat, int nphi, sht_handle *out);
  * order index k holds degrees n = k mres .. lmax, from index
  * k (lmax + 1) - mres k (k - 1) / 2 (sht_lm_index takes the order m itself).
  * The longitude quadrature is the rectangle rule on the sector, equal to the
- * full circle's for these orders.  Modes SHT_F64, SHT_F32, SHT_TC_BF16X3
- * (scalar and vector; the P panels hold the strided orders only) and
- * SHT_F32_AUTO; SHT_TC_OTF and SHT_TC_F64 return SHT_EUNSUPPORTED for
- * mres > 1.  sht_create(...) is sht_create_mres(lmax, mmax, 1, ...). */
+ * full circle's for these orders.  Every mode takes such plans: the
+ * tensor-core panels, recurrence seeds and digit tables hold the strided
+ * orders only.  sht_create(...) is sht_create_mres(lmax, mmax, 1, ...). */
 SHT_API int sht_create_mres(int lmax, int mmax, int mres, int nlat, int nphi, sht_handle *out);
 
 /* Free the plan and everything it owns.  NULL is ignored.  The caller must

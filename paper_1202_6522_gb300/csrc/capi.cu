@@ -204,11 +204,10 @@ cudaError_t otf_build(sht::Plan &p, int *flag_dev)
 int ensure_otf(sht::Plan &p)
 {
     if (p.otf_state > 0) return SHT_OK;
-    if (p.mres > 1) return fail(SHT_EUNSUPPORTED, "this tensor-core mode needs mres = 1");
     if (p.otf_state < 0)
         return fail(SHT_EUNSUPPORTED, "on-the-fly mode: the FP32 recurrence would leave the FP32 range for this plan");
     std::vector<unsigned long long> segoff;
-    const size_t nseg = sht::otf_segment_offsets(p.lmax, p.mmax, segoff);
+    const size_t nseg = sht::otf_segment_offsets(p.lmax, p.mmax, p.mres, segoff);
     std::vector<unsigned long long> off_s, off_a, dchunk;
     size_t bs = 0, ba = 0, nch = 0;
     sht::tc_panel_layout(p.lmax, p.mmax, p.mres, p.npairs, off_s, off_a, bs, ba, dchunk, nch);
@@ -252,12 +251,11 @@ size_t elem_size(int mode) { return (mode == SHT_F64 || mode == SHT_TC_F64) ? si
 int ensure_panels64(sht::Plan &p)
 {
     if (p.p64_s) return SHT_OK;
-    if (p.mres > 1) return fail(SHT_EUNSUPPORTED, "this tensor-core mode needs mres = 1");
     if (p.lmax > 1023 || p.npairs > 512)
         return fail(SHT_EUNSUPPORTED, "SHT_TC_F64 needs lmax <= 1023 and nlat <= 1024");
     std::vector<unsigned long long> off_s, off_a, dchunk;
     size_t bs = 0, ba = 0, nch = 0;
-    sht::tc64_panel_layout(p.lmax, p.mmax, p.npairs, off_s, off_a, bs, ba, dchunk, nch);
+    sht::tc64_panel_layout(p.lmax, p.mmax, p.mres, p.npairs, off_s, off_a, bs, ba, dchunk, nch);
     const size_t ob = off_s.size() * sizeof(unsigned long long);
     int T_s = 0, T_a = 0;
     sht::tc_tile_counts(p.lmax, p.npairs, T_s, T_a);
@@ -654,7 +652,7 @@ int run_tc64(sht::Plan &p, bool synth, const void *in_, void *out_, int batch, s
             const double *in = static_cast<const double *>(in_) + (size_t)b0 * spec_n;
             double *out = static_cast<double *>(out_) + (size_t)b0 * grid_n;
             rc = timed(p, SHT_K_TC_SYNTH, s, "FP64 tensor-core synthesis launch", [&] {
-                return sht::launch_tc64(true, p.lmax, p.mmax, p.npairs, p.nlm, p.p64_s, p.d_off64_s, p.d_c064_s,
+                return sht::launch_tc64(true, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.p64_s, p.d_off64_s, p.d_c064_s,
                                         p.d_e64_s, p.d_dchunk64, p.d_fcol, data, in, inter, nb, op, p.d_err, s);
             });
             if (rc) return rc;
@@ -667,7 +665,7 @@ int run_tc64(sht::Plan &p, bool synth, const void *in_, void *out_, int batch, s
                        [&] { return sht::launch_fft_analys_df(p.view64(), in, inter, nb, op, false, s); });
             if (rc) return rc;
             rc = timed(p, SHT_K_TC_ANALYS, s, "FP64 tensor-core analysis launch", [&] {
-                return sht::launch_tc64(false, p.lmax, p.mmax, p.npairs, p.nlm, p.p64_a, p.d_off64_a, p.d_c064_a,
+                return sht::launch_tc64(false, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.p64_a, p.d_off64_a, p.d_c064_a,
                                         p.d_e64_a, p.d_dchunk64, p.d_fcol, data, inter, out, nb, op,
                                         p.d_err, s);
             });
@@ -692,7 +690,7 @@ int run_otf(sht::Plan &p, bool synth, const void *in_, void *out_, int batch, sh
             const float *in = static_cast<const float *>(in_) + so;
             float *out = static_cast<float *>(out_) + go;
             rc = timed(p, SHT_K_TC_SYNTH, s, "on-the-fly tensor-core synthesis launch", [&] {
-                return sht::launch_tc_otf(true, p.lmax, p.mmax, p.npairs, p.nlm, p.otf_seeds, p.d_segoff, p.d_c0o_s,
+                return sht::launch_tc_otf(true, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.otf_seeds, p.d_segoff, p.d_c0o_s,
                                           pv.ab, pv.x, data, in, inter, nb, op, p.d_err, s);
             });
             if (rc) return rc;
@@ -705,7 +703,7 @@ int run_otf(sht::Plan &p, bool synth, const void *in_, void *out_, int batch, sh
                        [&] { return sht::launch_fft_analys<float>(pv, in, inter, nb, op, false, s); });
             if (rc) return rc;
             rc = timed(p, SHT_K_TC_ANALYS, s, "on-the-fly tensor-core analysis launch", [&] {
-                return sht::launch_tc_otf(false, p.lmax, p.mmax, p.npairs, p.nlm, p.otf_seeds, p.d_segoff, p.d_c0o_a,
+                return sht::launch_tc_otf(false, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.otf_seeds, p.d_segoff, p.d_c0o_a,
                                           pv.ab, pv.x, data, inter, out, nb, op, p.d_err, s);
             });
         }

@@ -284,13 +284,13 @@ int tc_max_batch();
 int tc64_max_batch();
 // Byte offsets of each order's digit-slice panel chunks (synthesis, analysis),
 // total bytes, and the first synthesis data chunk of each order.
-void tc64_panel_layout(int lmax, int mmax, int npairs, std::vector<unsigned long long> &off_s,
+void tc64_panel_layout(int lmax, int mmax, int mres, int npairs, std::vector<unsigned long long> &off_s,
                        std::vector<unsigned long long> &off_a, size_t &bytes_s, size_t &bytes_a,
                        std::vector<unsigned long long> &dchunk, size_t &nchunk_s);
 size_t tc64_data_bytes(int mmax, int npairs, size_t nchunk_s);
 cudaError_t tc64_build(const PlanView<double> &pv, const unsigned long long *off_s, const unsigned long long *off_a,
                        unsigned char *ps, unsigned char *pa, int *es, int *ea, int *c0_s, int *c0_a, cudaStream_t st);
-cudaError_t launch_tc64(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
+cudaError_t launch_tc64(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const unsigned char *panel,
                         const unsigned long long *off, const int *c0, const int *erow,
                         const unsigned long long *dchunk, int *fcol, unsigned char *data, const double *in,
                         double *out, int batch, Op op, int *err, cudaStream_t st);
@@ -299,14 +299,14 @@ cudaError_t launch_selftest_timeout(int *err, unsigned long long max_ns, cudaStr
 // On-the-fly mode (tc.cu): FP32 recurrence reseeded every 32 degrees.
 // Segment offsets per order (= synthesis data chunk numbering); returns the
 // total number of segments.
-size_t otf_segment_offsets(int lmax, int mmax, std::vector<unsigned long long> &segoff);
+size_t otf_segment_offsets(int lmax, int mmax, int mres, std::vector<unsigned long long> &segoff);
 // Seeds [segments][npairs] float4 and the polar-skip tables (first live chunk
 // per (m, synthesis tile) and per (m, analysis tile)); *flag set if some
 // segment would exceed the FP32 range.
 cudaError_t launch_build_seeds(const PlanView<double> &pv, const unsigned long long *segoff, float4 *seeds,
                                float thr, int *c0s, int *c0a, int *flag, cudaStream_t st);
 // Scalar contraction (prep + on-the-fly kernel) of <= tc_max_batch() fields.
-cudaError_t launch_tc_otf(bool synth, int lmax, int mmax, int npairs, int nlm, const float4 *seeds,
+cudaError_t launch_tc_otf(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const float4 *seeds,
                           const unsigned long long *segoff, const int *c0, const float2 *ab32, const float *x32,
                           unsigned char *data, const float *in, float *out, int batch, Op op, int *err,
                           cudaStream_t st);

@@ -57,7 +57,6 @@ __host__ __device__ __forceinline__ uint32_t pan_off(int kb, int row, int k)
     return (uint32_t)((row >> 3) * kPSbo + kb * kSbo + (k >> 3) * kLbo + (row & 7) * 16 + (k & 7) * 2);
 }
 using tcc::kWaitNs;
-using tcc::col_of;
 using tcc::raise_err;
 using tcc::wait_or_abort;
 
@@ -825,9 +824,9 @@ k_build_seeds(PlanView<double> pv, const unsigned long long *__restrict__ segoff
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const int npairs = pv.npairs, lmax = pv.lmax;
     if (p >= npairs) return;
-    const int L = lmax - m + 1;
+    const int L = lmax - m * pv.mres + 1;   // m is the order index
     const int nseg = (L + kSeg - 1) / kSeg;
-    const long col = col_of(lmax, m);
+    const long col = col_of_mres(lmax, m, pv.mres);
     const double x = pv.x[p];
     double y2 = pv.pmm[(size_t)m * npairs + p], y1 = 0.0;
     int k = pv.pmmk[(size_t)m * npairs + p];
@@ -884,19 +883,20 @@ k_build_seeds(PlanView<double> pv, const unsigned long long *__restrict__ segoff
 }
 
 // c0 tables before k_build_seeds: the chunk counts (nothing live).
-__global__ void k_init_c0(int lmax, int mmax, int npairs, int ntiles_s, int ntiles_a, int *c0s, int *c0a)
+__global__ void k_init_c0(int lmax, int mmax, int mres, int npairs, int ntiles_s, int ntiles_a, int *c0s, int *c0a)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int m = i / (ntiles_s + ntiles_a);
     if (m > mmax) return;
     const int t = i - m * (ntiles_s + ntiles_a);
-    const int Le = (lmax - m + 2) / 2;
+    const int Le = (lmax - m * mres + 2) / 2;
     if (t < ntiles_s) c0s[m * ntiles_s + t] = (Le + kKc - 1) / kKc;
     else c0a[m * ntiles_a + (t - ntiles_s)] = (npairs + kKc - 1) / kKc;
 }
 
 struct OtfArgs {
     int lmax, mmax, npairs, nlm, batch, rows, ntiles, stages, op, nab;
+    int mres;                           // order stride: order index m is the order m mres
     const float4 *seeds;
     const unsigned long long *segoff;   // first segment (= synthesis data chunk) of each order
     const int *c0;                      // per (m, tile): first live chunk
@@ -1023,9 +1023,9 @@ __global__ void __launch_bounds__(kOtfThreads, 2) k_tc_otf(OtfArgs a)
     const int m = blockIdx.x / a.ntiles;
     const int tile = blockIdx.x - m * a.ntiles;
     const int lmax = a.lmax, npairs = a.npairs;
-    const int L = lmax - m + 1;
+    const int L = lmax - m * a.mres + 1;   // m is the order index
     const int Le = (L + 1) / 2;
-    const long col = col_of(lmax, m);
+    const long col = col_of_mres(lmax, m, a.mres);
     if (!SYNTH && tile * kRows >= Le) return;
     const int nseg = (L + kSeg - 1) / kSeg;
     const int kch = (npairs + kKc - 1) / kKc;
@@ -1665,13 +1665,13 @@ cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int mres, int npairs, 
 // ---------------------------------------------------------------------------
 // On-the-fly mode (host side)
 // ---------------------------------------------------------------------------
-size_t otf_segment_offsets(int lmax, int mmax, std::vector<unsigned long long> &segoff)
+size_t otf_segment_offsets(int lmax, int mmax, int mres, std::vector<unsigned long long> &segoff)
 {
     segoff.assign(mmax + 1, 0);
     unsigned long long s = 0;
     for (int m = 0; m <= mmax; ++m) {
         segoff[m] = s;
-        s += (unsigned long long)((lmax - m + 1 + kSeg - 1) / kSeg);
+        s += (unsigned long long)((lmax - m * mres + 1 + kSeg - 1) / kSeg);
     }
     return (size_t)s;
 }
@@ -1682,7 +1682,7 @@ cudaError_t launch_build_seeds(const PlanView<double> &pv, const unsigned long l
     int ts, ta;
     tc_tile_counts(pv.lmax, pv.npairs, ts, ta);
     const int n = (pv.mmax + 1) * (ts + ta);
-    k_init_c0<<<(n + 255) / 256, 256, 0, st>>>(pv.lmax, pv.mmax, pv.npairs, ts, ta, c0s, c0a);
+    k_init_c0<<<(n + 255) / 256, 256, 0, st>>>(pv.lmax, pv.mmax, pv.mres, pv.npairs, ts, ta, c0s, c0a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 g((unsigned)((pv.npairs + 127) / 128), (unsigned)(pv.mmax + 1));
@@ -1690,7 +1690,7 @@ cudaError_t launch_build_seeds(const PlanView<double> &pv, const unsigned long l
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_otf(bool synth, int lmax, int mmax, int npairs, int nlm, const float4 *seeds,
+cudaError_t launch_tc_otf(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const float4 *seeds,
                           const unsigned long long *segoff, const int *c0, const float2 *ab32, const float *x32,
                           unsigned char *data, const float *in, float *out, int batch, Op op, int *err,
                           cudaStream_t st)
@@ -1698,11 +1698,12 @@ cudaError_t launch_tc_otf(bool synth, int lmax, int mmax, int npairs, int nlm, c
     if (batch < 1 || batch > tc_otf_max_batch()) return cudaErrorInvalidValue;
     const int rows = cols_of(batch);
     // synthesis data chunks are numbered like the segments (one chunk = one segment)
-    cudaError_t e = launch_prep(synth, false, lmax, mmax, 1, npairs, nlm, batch, rows, op, in, nullptr, segoff, data, st);
+    cudaError_t e = launch_prep(synth, false, lmax, mmax, mres, npairs, nlm, batch, rows, op, in, nullptr, segoff, data, st);
     if (e != cudaSuccess) return e;
     OtfArgs a{};
     a.lmax = lmax;
     a.mmax = mmax;
+    a.mres = mres;
     a.npairs = npairs;
     a.nlm = nlm;
     a.batch = batch;

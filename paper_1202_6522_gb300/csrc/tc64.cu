@@ -46,7 +46,7 @@
 namespace sht {
 namespace {
 
-using tcc::col_of;
+using sht::col_of_mres;
 using tcc::raise_err;
 using tcc::wait_or_abort;
 
@@ -150,14 +150,15 @@ __device__ __forceinline__ void digits_int(double v, int e, int (&d)[kSB])
     d[kSB - 1] = (int)Y;
 }
 
-// The Sec. 3.2 recurrence for (m, pair p) as in the panel builder of tc.cu,
-// calling f(nn, P) for every degree n = m + nn with P != 0 (k = 0 region).
+// The Sec. 3.2 recurrence for (order index m, pair p) as in the panel builder
+// of tc.cu, calling f(nn, P) for every degree n = m mres + nn with P != 0
+// (k = 0 region).
 template <typename F>
 __device__ __forceinline__ void recur_pair(const PlanView<double> &pv, int m, int p, F &&f)
 {
     const int npairs = pv.npairs, lmax = pv.lmax;
-    const int L = lmax - m + 1;
-    const long col = col_of(lmax, m);
+    const int L = lmax - m * pv.mres + 1;
+    const long col = col_of_mres(lmax, m, pv.mres);
     const double x = pv.x[p];
     double y2 = pv.pmm[(size_t)m * npairs + p], y1 = 0.0;
     int k = pv.pmmk[(size_t)m * npairs + p];
@@ -182,7 +183,7 @@ __global__ void k_p64_scales(PlanView<double> pv, int *__restrict__ es, int *__r
 {
     const int m = blockIdx.y, p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= pv.npairs) return;
-    const long col = col_of(pv.lmax, m);
+    const long col = col_of_mres(pv.lmax, m, pv.mres);
     double mx = 0.0;
     recur_pair(pv, m, p, [&](int nn, double P) {
         mx = fmax(mx, fabs(P));
@@ -202,9 +203,9 @@ __global__ void k_p64_build(PlanView<double> pv, const int *__restrict__ es, con
     const int m = blockIdx.y, p = blockIdx.x * blockDim.x + threadIdx.x;
     const int npairs = pv.npairs;
     if (p >= npairs) return;
-    const int L = pv.lmax - m + 1, Le = (L + 1) / 2;
+    const int L = pv.lmax - m * pv.mres + 1, Le = (L + 1) / 2;
     const int nch = (Le + kKc - 1) / kKc, kch = (npairs + kKc - 1) / kKc;
-    const long col = col_of(pv.lmax, m);
+    const long col = col_of_mres(pv.lmax, m, pv.mres);
     const int t = p / kR, row = p % kR, kc = p / kKc, pc = p % kKc;
     const int e_row = es[(size_t)m * npairs + p];
     unsigned char *sbase = ps + off_s[m] + (size_t)t * nch * kPChunk;
@@ -231,11 +232,12 @@ __global__ void k_p64_build(PlanView<double> pv, const int *__restrict__ es, con
 // First chunk of each (m, tile) holding a nonzero digit (all-zero chunks,
 // high orders near the poles, add nothing: the polar optimisation of
 // Sec. 3.1 without a threshold).
-__global__ void k_p64_first_live(int synth, int lmax, int npairs, int ntiles, const unsigned long long *__restrict__ off,
-                                 const unsigned char *__restrict__ panel, int *__restrict__ c0)
+__global__ void k_p64_first_live(int synth, int lmax, int mres, int npairs, int ntiles,
+                                 const unsigned long long *__restrict__ off, const unsigned char *__restrict__ panel,
+                                 int *__restrict__ c0)
 {
-    const int m = blockIdx.y, tile = blockIdx.x;
-    const int L = lmax - m + 1, Le = (L + 1) / 2;
+    const int m = blockIdx.y, tile = blockIdx.x;   // order index m, order m mres
+    const int L = lmax - m * mres + 1, Le = (L + 1) / 2;
     const int nchunks = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
     const bool valid = synth || tile * kR < Le;
     __shared__ int s_live;
@@ -290,12 +292,12 @@ __global__ void k_fill_int(int *__restrict__ a, int v, size_t n)
 // 0 = s fold, 1 = d fold, numbered m kch + kc.  One thread per (chunk, class,
 // field, re|im, half of the K positions): it splits 8 values and writes each
 // slice's 8 digits as one 16-byte core-matrix row.
-__global__ void k_prep64(int synth, int lmax, int mmax, int npairs, int nlm, int batch, int op,
+__global__ void k_prep64(int synth, int lmax, int mmax, int mres, int npairs, int nlm, int batch, int op,
                          const double *__restrict__ in, const int *__restrict__ f,
                          const unsigned long long *__restrict__ dchunk, unsigned char *__restrict__ data)
 {
-    const int m = blockIdx.y;
-    const int L = lmax - m + 1, Le = (L + 1) / 2;
+    const int m = blockIdx.y;   // order index: the order is m mres
+    const int L = lmax - m * mres + 1, Le = (L + 1) / 2;
     const int nchunks = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
     const long item = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const int per = 8 * batch;                                // items per chunk
@@ -308,7 +310,7 @@ __global__ void k_prep64(int synth, int lmax, int mmax, int npairs, int nlm, int
     const int e = f[b];
     double v[8];
     if (synth) {
-        const long col = col_of(lmax, m);
+        const long col = col_of_mres(lmax, m, mres);
         const double sc = (op == OP_ANALYS_ADJ && m > 0) ? 0.5 : 1.0;   // adjoint factor 1/2
         const double2 *spec = reinterpret_cast<const double2 *>(in) + (size_t)b * nlm + col;
 #pragma unroll
@@ -348,6 +350,7 @@ __global__ void k_prep64(int synth, int lmax, int mmax, int npairs, int nlm, int
 
 struct Tc64Args {
     int lmax, mmax, npairs, nlm, batch, ntiles, op;
+    int mres;                              // order stride: order index m is the order m mres
     const unsigned char *panel;
     const unsigned long long *off;         // per-order panel byte offsets
     const int *c0;                         // per (m, tile): first chunk with a nonzero digit
@@ -375,8 +378,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc64(Tc64Args a)
     const int m = (blockIdx.x >> 1) / a.ntiles;
     const int tile = (blockIdx.x >> 1) - m * a.ntiles;
     const int lmax = a.lmax, npairs = a.npairs;
-    const int L = lmax - m + 1, Le = (L + 1) / 2;
-    const long col = col_of(lmax, m);
+    const int L = lmax - m * a.mres + 1, Le = (L + 1) / 2;   // m is the order index
+    const long col = col_of_mres(lmax, m, a.mres);
     if (!SYNTH && tile * kR >= Le) return;
     const int nchunks = SYNTH ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
     const unsigned char *panel = a.panel + a.off[m] + (size_t)tile * nchunks * kPChunk;
@@ -540,7 +543,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc64(Tc64Args a)
 
 int tc64_max_batch() { return kBatch64; }
 
-void tc64_panel_layout(int lmax, int mmax, int npairs, std::vector<unsigned long long> &off_s,
+void tc64_panel_layout(int lmax, int mmax, int mres, int npairs, std::vector<unsigned long long> &off_s,
                        std::vector<unsigned long long> &off_a, size_t &bytes_s, size_t &bytes_a,
                        std::vector<unsigned long long> &dchunk, size_t &nchunk_s)
 {
@@ -551,7 +554,7 @@ void tc64_panel_layout(int lmax, int mmax, int npairs, std::vector<unsigned long
     const int kch = (npairs + kKc - 1) / kKc;
     unsigned long long s = 0, q = 0, ch = 0;
     for (int m = 0; m <= mmax; ++m) {
-        const int L = lmax - m + 1, Le = (L + 1) / 2;
+        const int L = lmax - m * mres + 1, Le = (L + 1) / 2;
         const int nch = (Le + kKc - 1) / kKc;
         const int Mt = (Le + kR - 1) / kR;
         off_s[m] = s;
@@ -583,14 +586,14 @@ cudaError_t tc64_build(const PlanView<double> &pv, const unsigned long long *off
     k_p64_build<<<g, 128, 0, st>>>(pv, es, ea, off_s, off_a, ps, pa);
     int ts, ta;
     tc_tile_counts(pv.lmax, pv.npairs, ts, ta);
-    k_p64_first_live<<<dim3((unsigned)ts, (unsigned)(pv.mmax + 1)), 256, 0, st>>>(1, pv.lmax, pv.npairs, ts, off_s,
+    k_p64_first_live<<<dim3((unsigned)ts, (unsigned)(pv.mmax + 1)), 256, 0, st>>>(1, pv.lmax, pv.mres, pv.npairs, ts, off_s,
                                                                                  ps, c0_s);
-    k_p64_first_live<<<dim3((unsigned)ta, (unsigned)(pv.mmax + 1)), 256, 0, st>>>(0, pv.lmax, pv.npairs, ta, off_a,
+    k_p64_first_live<<<dim3((unsigned)ta, (unsigned)(pv.mmax + 1)), 256, 0, st>>>(0, pv.lmax, pv.mres, pv.npairs, ta, off_a,
                                                                                  pa, c0_a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc64(bool synth, int lmax, int mmax, int npairs, int nlm, const unsigned char *panel,
+cudaError_t launch_tc64(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const unsigned char *panel,
                         const unsigned long long *off, const int *c0, const int *erow,
                         const unsigned long long *dchunk, int *fcol, unsigned char *data, const double *in,
                         double *out, int batch, Op op, int *err, cudaStream_t st)
@@ -605,10 +608,11 @@ cudaError_t launch_tc64(bool synth, int lmax, int mmax, int npairs, int nlm, con
     const int maxch = synth ? (Le0 + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
     const long items = (long)maxch * batch * 8;
     k_prep64<<<dim3((unsigned)((items + 127) / 128), (unsigned)(mmax + 1)), 128, 0, st>>>(
-        synth ? 1 : 0, lmax, mmax, npairs, nlm, batch, (int)op, in, fcol, dchunk, data);
+        synth ? 1 : 0, lmax, mmax, mres, npairs, nlm, batch, (int)op, in, fcol, dchunk, data);
     Tc64Args a{};
     a.lmax = lmax;
     a.mmax = mmax;
+    a.mres = mres;
     a.npairs = npairs;
     a.nlm = nlm;
     a.batch = batch;

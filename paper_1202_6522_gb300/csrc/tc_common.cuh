@@ -13,9 +13,6 @@ namespace tcc {
 
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s
 
-// First packed index of order m: m (2 lmax + 3 - m) / 2.
-__host__ __device__ __forceinline__ long col_of(int lmax, int m) { return (long)m * (2 * lmax + 3 - m) / 2; }
-
 // Records the first error code of a launch (0 = none).
 __device__ __forceinline__ void raise_err(int *err, int code)
 {

@@ -39,8 +39,7 @@ class SHT:
         slices of both operands, FP64 accuracy; scalar transforms, lmax <= 1023,
         vector ones run "f64").
         mres > 1 keeps only the orders m = k mres (k <= mmax, mmax mres <= lmax)
-        on a grid of one 2 pi / mres sector of longitudes (FP64, FP32 and the
-        tensor cores against panels; not "otf" nor fp64_path="tc")."""
+        on a grid of one 2 pi / mres sector of longitudes (every path)."""
         self.lmax = int(lmax)
         self.mres = int(mres)
         self.mmax = self.lmax // self.mres if mmax is None else int(mmax)

@@ -1,5 +1,5 @@
 """The m-stride variant (orders m = k mres only, one 2 pi / mres sector of longitudes),
-on the FP64, FP32 and tensor-core (panel) paths.
+on the FP64, FP32 and every tensor-core path (panels, on-the-fly P, FP64-accurate).
 
 Such a field is an ordinary field whose orders off the stride vanish, and its
 grid repeats every 2 pi / mres.  So the oracle is the plain one on the full
@@ -56,18 +56,19 @@ def _spread(a, lmax, mmax, mres):
     return full
 
 
-@pytest.mark.parametrize("path", ["f64", "f32", "tc"])
+@pytest.mark.parametrize("path", ["f64", "f32", "tc", "otf", "tc64"])
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_mres_scalar(SHT, case, path):
     lmax, mmax, mres, nlat, nphi, batch = case
-    sht = SHT(lmax, mmax, nlat, nphi, mres=mres, fp32_path="tc" if path == "tc" else "f32")
+    sht = SHT(lmax, mmax, nlat, nphi, mres=mres, fp32_path=path if path in ("tc", "otf") else "f32",
+              fp64_path="tc" if path == "tc64" else "f64")
     assert sht.nlm == len(_strided_index(lmax, mmax, mres))
     rng = np.random.default_rng(7)
     a = (rng.standard_normal((batch, sht.nlm)) + 1j * rng.standard_normal((batch, sht.nlm))) * 0.3
     a[:, : lmax + 1] = a[:, : lmax + 1].real          # order 0 is real
     g = synthetic.grid(nlat, nphi, batch=batch, seed=3)
-    cdt, fdt = (np.complex128, np.float64) if path == "f64" else (np.complex64, np.float32)
-    bound = {"f64": fp64_bound, "f32": fp32_bound, "tc": tc_bound}[path](lmax)
+    cdt, fdt = (np.complex128, np.float64) if path in ("f64", "tc64") else (np.complex64, np.float32)
+    bound = {"f64": fp64_bound, "tc64": fp64_bound, "f32": fp32_bound, "tc": tc_bound, "otf": tc_bound}[path](lmax)
     a = a.astype(cdt)
     g = g.astype(fdt)
     got = _np(sht.synth_(torch.from_numpy(a).to(DEV)))
@@ -119,16 +120,8 @@ def test_mres_vector_and_adjoint(SHT, path):
 
 
 def test_mres_index_and_refusals(SHT):
-    from paper_1202_6522_gb300 import _capi as C
     sht = SHT(31, 7, 32, 16, mres=4)
     assert sht.lm_index(4, 4) == 32                 # order index 1 starts after the 32 degrees of m = 0
     assert sht.lm_index(5, 2) == -1                 # m off the stride
-    # the on-the-fly and FP64-accurate tensor-core modes keep mres = 1
-    otf = SHT(31, 7, 32, 16, fp32_path="otf", mres=4)
-    with pytest.raises(C.SHTError):
-        otf.synth_(torch.zeros(1, otf.nlm, dtype=torch.complex64, device=DEV))
-    tc64 = SHT(31, 7, 32, 16, fp64_path="tc", mres=4)
-    with pytest.raises(C.SHTError):
-        tc64.synth_(torch.zeros(1, tc64.nlm, dtype=torch.complex128, device=DEV))
     with pytest.raises(ValueError):
         SHT(31, 8, 32, 32, mres=4)                  # mmax mres > lmax (SHT_EINVAL)
