@@ -257,6 +257,8 @@ __host__ __device__ inline size_t smem_bytes_of(int npanels, int rows, int stage
 struct TcArgs {
     int lmax, mmax, npairs, nlm, batch, rows, ntiles, stages, op;
     int mres;                              // order stride: order index m is the order m mres
+    int halves;                            // vector: field halves of kVecHalf per launch (CTA pairs)
+    unsigned long long data_half;          // vector: bytes of one half's data operand
     const float *in;                       // raw FP32 s/d folds (warp-specialised analysis)
     int fused;                             // synthesis: spectra converted in the kernel (tensor map)
     const unsigned char *panel, *dpanel;   // dpanel: vector transforms only
@@ -629,6 +631,12 @@ __global__ void __launch_bounds__(kWsThreads, kWsCtasPerSm) k_tc_ws(TcArgs a, co
 //     S_n = scale (acc2[th] - i m acc1[ph]),  T_n = scale (i m acc1[th] + acc2[ph]).
 // Accumulators: [cls][acc][N columns], N = 2 NH (first | second quantity).
 // ---------------------------------------------------------------------------
+// Fields per CTA of the vector contraction (4 accumulators x 2 cols_of(32)
+// columns fill the 512 TMEM columns).  A launch of up to 64 fields runs its
+// field groups as adjacent CTAs of each (m, tile), so the later ones read the
+// panel chunks the first brought into L2.
+constexpr int kVecHalf = 32;
+
 template <bool SYNTH>
 __global__ void __launch_bounds__(128, 1) k_tc_vec(TcArgs a)
 {
@@ -644,8 +652,11 @@ __global__ void __launch_bounds__(128, 1) k_tc_vec(TcArgs a)
     __shared__ int s_ok;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    const int m = blockIdx.x / a.ntiles;
-    const int tile = blockIdx.x - m * a.ntiles;
+    const int half = blockIdx.x % a.halves;                 // fields [kVecHalf half, ...)
+    const int mt = blockIdx.x / a.halves;
+    const int m = mt / a.ntiles;
+    const int tile = mt - m * a.ntiles;
+    const int fb0 = half * kVecHalf, nbh = min(kVecHalf, a.batch - fb0);
     const int lmax = a.lmax, npairs = a.npairs;
     const int L = lmax - m * a.mres + 1;   // m is the order index
     const int Le = (L + 1) / 2;
@@ -653,8 +664,8 @@ __global__ void __launch_bounds__(128, 1) k_tc_vec(TcArgs a)
     if (!SYNTH && tile * kRows >= Le) return;
     const int nchunks = SYNTH ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
     const size_t poff = a.off[m] + (size_t)tile * nchunks * kChunkPanel;
-    const unsigned char *data =
-        a.data + (SYNTH ? a.dchunk[m] : (unsigned long long)m * nchunks) * data_chunk_bytes(NV);
+    const unsigned char *data = a.data + (size_t)half * a.data_half +
+                                (SYNTH ? a.dchunk[m] : (unsigned long long)m * nchunks) * data_chunk_bytes(NV);
     const uint32_t ncols = 4 * NV <= 256 ? 256 : 512;
     const int cstart = a.c0 ? a.c0[m * a.ntiles + tile] : 0;
     const int nlive = nchunks - cstart;
@@ -751,8 +762,9 @@ __global__ void __launch_bounds__(128, 1) k_tc_vec(TcArgs a)
                         }
                     }
                 for (int q = 0; q < 32; q += 2) {
-                    const int b = (cb + q) >> 1;
-                    if (b >= a.batch) break;
+                    const int bl = (cb + q) >> 1;   // field within the half
+                    if (bl >= nbh) break;
+                    const int b = fb0 + bl;
                     if (SYNTH) {
                         if (row >= npairs) continue;
                         const float psr = v[0][0][q], psi = v[0][0][q + 1];   // sum P S
@@ -1348,7 +1360,7 @@ cudaError_t launch_contraction(K kernel, bool synth, int lmax, int mmax, int npa
     int ts, ta;
     tc_tile_counts(lmax, npairs, ts, ta);
     a.ntiles = synth ? ts : ta;
-    const unsigned blocks = (unsigned)((mmax + 1) * a.ntiles);
+    const unsigned blocks = (unsigned)((mmax + 1) * a.ntiles * (a.halves > 0 ? a.halves : 1));
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kernel<<<blocks, 128, smem, st>>>(a);
@@ -1428,7 +1440,7 @@ int tc_max_batch() { return 64; }
 // the on-the-fly kernel keeps 4 x 2 batch accumulator columns (+ the synthesis
 // operand) in tensor memory: at most 32 fields per launch
 int tc_otf_max_batch() { return 32; }
-int tc_vec_max_batch() { return 32; }
+int tc_vec_max_batch() { return 64; }   // in launches of 64 / kVecHalf adjacent CTAs per (m, tile)
 
 void tc_panel_layout(int lmax, int mmax, int mres, int npairs, std::vector<unsigned long long> &off_s,
                      std::vector<unsigned long long> &off_a, size_t &bytes_s, size_t &bytes_a,
@@ -1458,7 +1470,9 @@ void tc_panel_layout(int lmax, int mmax, int mres, int npairs, std::vector<unsig
 
 size_t tc_data_bytes(int mmax, int npairs, size_t nchunk_s, int batch, bool vec)
 {
-    const int rows = vec ? 2 * cols_of(batch) : cols_of(batch);
+    // vector: one operand per half of kVecHalf fields, each of 2 cols_of(half) rows
+    const int halves = (batch + kVecHalf - 1) / kVecHalf;
+    const int rows = vec ? halves * 2 * cols_of(halves > 1 ? kVecHalf : batch) : cols_of(batch);
     const size_t kch = (size_t)(npairs + kKc - 1) / kKc;
     const size_t an = (size_t)(mmax + 1) * kch;
     return (nchunk_s > an ? nchunk_s : an) * data_chunk_bytes(rows);
@@ -1633,13 +1647,25 @@ cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int mres, int npairs, 
                           cudaStream_t st)
 {
     if (batch < 1 || batch > tc_vec_max_batch()) return cudaErrorInvalidValue;
-    const int rows = 2 * cols_of(batch);   // 4 accumulators x rows columns <= 512
+    const int halves = (batch + kVecHalf - 1) / kVecHalf;
+    const int rows = 2 * cols_of(halves > 1 ? kVecHalf : batch);   // 4 accumulators x rows columns <= 512
+    // one half's data operand: the larger of the two chunk numberings
+    size_t nch_s = 0;
+    for (int m = 0; m <= mmax; ++m) nch_s += (size_t)(((lmax - m * mres + 2) / 2 + kKc - 1) / kKc);
+    const size_t nch_a = (size_t)(mmax + 1) * ((npairs + kKc - 1) / kKc);
+    const size_t data_half = (nch_s > nch_a ? nch_s : nch_a) * data_chunk_bytes(rows);
     if (!prepped) {
-        cudaError_t e =
-            launch_prep(synth, true, lmax, mmax, mres, npairs, nlm, batch, rows, op, in0, in1, dchunk, data, st);
-        if (e != cudaSuccess) return e;
+        for (int h = 0; h < halves; ++h) {
+            const int hb = std::min(kVecHalf, batch - h * kVecHalf);
+            const size_t fo = (size_t)h * kVecHalf * (synth ? (size_t)nlm * 2 : (size_t)(mmax + 1) * npairs * 4);
+            cudaError_t e = launch_prep(synth, true, lmax, mmax, mres, npairs, nlm, hb, rows, op, in0 + fo, in1 + fo,
+                                        dchunk, data + (size_t)h * data_half, st);
+            if (e != cudaSuccess) return e;
+        }
     }
     TcArgs a{};
+    a.halves = halves;
+    a.data_half = data_half;
     a.lmax = lmax;
     a.mmax = mmax;
     a.mres = mres;

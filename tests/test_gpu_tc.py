@@ -123,7 +123,8 @@ VEC_CASES = [
     (31, 20, 40, 64, 2),
     (40, 40, 41, 128, 3),
     (255, 255, 256, 512, 16),
-    (100, 100, 101, 256, 40),   # two chunks of at most 32 fields; 64 + 64 data columns
+    (100, 100, 101, 256, 40),   # one launch: field halves of 32 + 8 as adjacent CTAs
+    (31, 31, 32, 64, 70),       # two launches: 64 (two full halves) + 6 fields
 ]
 VEC_IDS = [f"N{c[0]}m{c[1]}lat{c[2]}phi{c[3]}b{c[4]}" for c in VEC_CASES]
 
