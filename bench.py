@@ -54,6 +54,19 @@ def legendre_flops_per_launch(batch, lmax=LMAX, nlat=NLAT):
     return nlm_of(lmax) * npairs * (4.0 + 4.0 * batch)
 
 
+def tc64_algorithmic_bytes(batch, lmax=LMAX, nlat=NLAT, zero_skip=0.0):
+    """Bytes one FP64-accurate tensor-core Legendre stage must move: 7 bf16
+    digit slices (14 B) of every P_n^m(x_j) of one hemisphere, less the
+    all-zero chunks it skips, plus the FP64 spectra and the FP64 E/O (or s/d)
+    intermediate of the batch (the digit data the stage writes and reads
+    back, and the tile padding, are not counted)."""
+    npairs = (nlat + 1) // 2
+    panel = nlm_of(lmax) * npairs * 14 * (1.0 - zero_skip)
+    spec = batch * nlm_of(lmax) * 16
+    inter = batch * (lmax + 1) * npairs * 32
+    return panel + spec + inter
+
+
 def tc_algorithmic_bytes(batch, lmax=LMAX, nlat=NLAT, polar_skip=0.0):
     """Bytes one tensor-core Legendre launch must move: every P_n^m(x_j) of one
     hemisphere as a bf16 hi+lo pair (4 B; the library's tile padding is not
@@ -683,7 +696,9 @@ def run_ours(args):
         # the panels stream from HBM once per launch: bytes bound the kernel
         from paper_1202_6522_gb300 import _capi as C
         skip_s, skip_a = C.sht_tc_polar_skip(sht._h)
-        algo = tc_algorithmic_bytes(BATCH, polar_skip=max(0.0, skip_a if dom_name == "tc_analys" else skip_s))
+        skip = max(0.0, skip_a if dom_name == "tc_analys" else skip_s)
+        algo = (tc64_algorithmic_bytes(BATCH, zero_skip=skip) if path_used == "tc_f64"
+                else tc_algorithmic_bytes(BATCH, polar_skip=skip))
         peaks = read_peaks()
         peak = peaks.get("hbm_gbs", 6800.0) * 1e9
         achieved = algo / (dom_avg / 1e3)

@@ -294,7 +294,8 @@ SHT_API const char *sht_kernel_name(int kind);
  * whose values are all below 2^-40 (near the poles at high order) are neither
  * loaded nor multiplied (SHT_TC_OTF: neither generated nor multiplied).
  * Fractions of the synthesis and analysis chunks skipped -- of the panels if
- * built, else of the on-the-fly mode's tables -- or -1 if neither is built. */
+ * built, else of the on-the-fly mode's tables, else of the SHT_TC_F64 digit
+ * panels (chunks whose digits are all zero) -- or -1 if none is built. */
 SHT_API int sht_tc_polar_skip(sht_handle h, double *synth_frac, double *analys_frac);
 
 /* Threshold of that optimisation (the paper leaves its value open; default

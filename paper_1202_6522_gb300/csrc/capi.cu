@@ -288,6 +288,12 @@ int ensure_panels64(sht::Plan &p)
         return fail(SHT_ENOMEM, std::string("building the digit-slice panels: ") + cudaGetErrorString(e));
     }
     p.nchunk64_s = nch;
+    // fractions of the digit chunks skipped as all-zero (whole chunks per (m, tile))
+    if (sht::tc_polar_stats(p.lmax, p.mmax, p.mres, p.npairs, p.d_c064_s, p.d_c064_a, p.skip64_s, p.skip64_a) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        p.skip64_s = p.skip64_a = -1.0;
+    }
     return SHT_OK;
 }
 
@@ -945,10 +951,11 @@ int sht_tc_polar_skip(sht_handle h, double *synth_frac, double *analys_frac)
 {
     if (!h) return fail(SHT_EINVAL, "null handle");
     if (!synth_frac || !analys_frac) return fail(SHT_EINVAL, "null output pointer");
-    // the panels' tables if built, else those of the on-the-fly mode
+    // the panels' tables if built, else those of the on-the-fly mode, else the
+    // FP64-accurate mode's all-zero digit chunks
     const sht::Plan &p = h->p;
-    *synth_frac = p.panel_s ? p.polar_skip_s : (p.otf_state > 0 ? p.otf_skip_s : -1.0);
-    *analys_frac = p.panel_s ? p.polar_skip_a : (p.otf_state > 0 ? p.otf_skip_a : -1.0);
+    *synth_frac = p.panel_s ? p.polar_skip_s : (p.otf_state > 0 ? p.otf_skip_s : (p.p64_s ? p.skip64_s : -1.0));
+    *analys_frac = p.panel_s ? p.polar_skip_a : (p.otf_state > 0 ? p.otf_skip_a : (p.p64_s ? p.skip64_a : -1.0));
     return SHT_OK;
 }
 

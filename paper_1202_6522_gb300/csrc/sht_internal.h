@@ -141,6 +141,7 @@ struct Plan {
     int *d_e64_s = nullptr, *d_e64_a = nullptr;           // ... row exponents
     int *d_c064_s = nullptr, *d_c064_a = nullptr;         // ... first nonzero chunk per (m, tile)
     int *d_fcol = nullptr;                                // ... field exponents of a launch
+    double skip64_s = -1, skip64_a = -1;                  // ... fractions of all-zero digit chunks
     float4 *otf_seeds = nullptr;                // on-the-fly mode: recurrence seeds
     unsigned long long *d_segoff = nullptr;     // first segment of each order
     int *d_c0o_s = nullptr, *d_c0o_a = nullptr; // on-the-fly mode: first live chunk per (m, tile)

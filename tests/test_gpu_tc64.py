@@ -84,6 +84,10 @@ def test_tc64_full_size_n1023_b16_sampled(SHT):
         ref = oracle.analys(lmax, lmax, nlat, nphi, g[b], ms=ms)
         assert normwise(spec[b][idx], ref[idx]) < fp64_bound(lmax), b
     assert sht.sync_status() == 0
+    # all-zero digit chunks (high orders near the poles) are reported and skipped
+    from paper_1202_6522_gb300 import _capi as C
+    fs, fa = C.sht_tc_polar_skip(sht._h)
+    assert 0.0 < fs < 0.5 and 0.0 < fa < 0.5
 
 
 def test_tc64_n511_b16_sampled(SHT):
