@@ -755,7 +755,7 @@ def run_ours(args):
                             "f64": "plain FP64 on-the-fly",
                             "tc": "tcgen05 split-bf16 contraction vs FP64-built P panels",
                             "otf": "tcgen05 split-bf16 contraction, P generated on the fly (FP32, reseeded)",
-                            "tc_f64": "tcgen05 contraction on 7-bit digit slices (FP64 accuracy), FP64 FFTs",
+                            "tc_f64": "tcgen05 contraction on 7-bit digit slices (FP64 accuracy), double-float FFTs",
                             "auto": "runtime-tuned: FP32 on-the-fly, tcgen05 panels or tcgen05 on-the-fly P"}[args.mode],
                    "path_used": path_used, "l2": "inputs larger than L2 (spectra+grids > 129 MB)",
                    "parallelism": f"replicas x{world}"},

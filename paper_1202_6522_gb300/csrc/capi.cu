@@ -643,8 +643,9 @@ int run_analys_tc(sht::Plan &p, const void *grid, void *spec, int batch, sht::Op
     return SHT_OK;
 }
 
-// FP64-accurate tensor-core mode: synthesis = contraction then FP64 FFT;
-// analysis = FP64 FFT then contraction; groups of up to 16 fields.
+// FP64-accurate tensor-core mode: synthesis = contraction then the
+// double-float FFT; analysis = double-float FFT then contraction; groups of up
+// to 16 fields.
 int run_tc64(sht::Plan &p, bool synth, const void *in_, void *out_, int batch, sht::Op op, cudaStream_t s)
 {
     const int chunk = sht::tc64_max_batch();
