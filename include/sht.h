@@ -99,17 +99,20 @@ enum {
                         * recurrence would leave the FP32 range (large lmax). */
     SHT_TC_F64 = 5     /* FP64 data; the per-order Legendre contraction on the bf16
                         * tensor cores to FP64 accuracy: P_n^m (per row) and the data
-                        * (per field) are scaled by powers of two and split into six
-                        * signed 7-bit digit slices; the tensor core sums the integer
-                        * products of each level exactly in FP32, and the epilogue
-                        * combines the levels in 64-bit integers (relative truncation
-                        * about 2^-42 of the row and field maxima).  FFTs in FP64.
-                        * Scalar transforms and adjoints, up to 16 fields per launch
-                        * (larger batches run in groups of 16).  Requires
-                        * lmax <= 1023 and nlat <= 1024 (so that every level's sum
-                        * stays below 2^24), else SHT_EUNSUPPORTED.  The digit panels
-                        * take about 6 (lmax+1)^3 bytes (6.4 GB at lmax = 1023) and
-                        * are built by the first call in this mode or by sht_reserve. */
+                        * (per field) are scaled by powers of two and split into
+                        * signed 7-bit digit slices (7 for P: 49 bits of the row
+                        * maximum; 8 for the data: 56 bits of the field maximum); the
+                        * tensor core sums the integer products of each level exactly
+                        * in FP32, and the epilogue combines the 8 leading levels in
+                        * 128-bit integers.  FFTs in double-float arithmetic (pairs of
+                        * FP32 numbers, ~2^-48 per operation) with a power-of-two scale
+                        * per latitude pair.  Scalar transforms and adjoints, up to 16
+                        * fields per launch (larger batches run in groups of 16).
+                        * Requires lmax <= 1023 and nlat <= 1024 (so that every
+                        * level's sum stays below 2^24), else SHT_EUNSUPPORTED.  The
+                        * digit panels take about 8 (lmax+1)^3 bytes (8.6 GB at
+                        * lmax = 1023) and are built by the first call in this mode
+                        * or by sht_reserve. */
 };
 
 /* Build a plan (Sec. 2.3 nodes/weights, Sec. 3.2 recurrence tables, FFT
