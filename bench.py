@@ -734,12 +734,14 @@ def run_ours(args):
     # in-kernel (a separate operand-prep kernel runs first only for a synthesis
     # with an odd coefficient count); the on-the-fly contraction always has one
     def kernels_per(k):
+        if path_used == "tc_f64":
+            # synthesis: field exponents (fill + reduction), data digits, contraction;
+            # analysis: the FFT (after a fill) finds the exponents, then digits and contraction
+            return {"tc_synth": 4, "tc_analys": 2, "fft_analys": 2}.get(k, 1)
         if not k.startswith("tc_"):
             return 1
         if path_used == "tc_otf":
             return 2
-        if path_used == "tc_f64":
-            return 4   # field exponents (fill + reduction), data digits, contraction
         return 2 if (k == "tc_synth" and nlm_of(LMAX) % 2) else 1
     launches = sum(v[1] * kernels_per(k) for k, v in table.items())
     line = {

@@ -668,13 +668,16 @@ int run_tc64(sht::Plan &p, bool synth, const void *in_, void *out_, int batch, s
         } else {
             const double *in = static_cast<const double *>(in_) + (size_t)b0 * grid_n;
             double *out = static_cast<double *>(out_) + (size_t)b0 * spec_n;
-            rc = timed(p, SHT_K_FFT_ANALYS, s, "fft analysis launch",
-                       [&] { return sht::launch_fft_analys_df(p.view64(), in, inter, nb, op, false, s); });
+            // the FFT also finds the folds' field exponents for the digit pass
+            rc = timed(p, SHT_K_FFT_ANALYS, s, "fft analysis launch", [&] {
+                cudaError_t e = sht::tc64_reset_fcol(p.d_fcol, nb, s);
+                return e != cudaSuccess ? e : sht::launch_fft_analys_df(p.view64(), in, inter, nb, op, false, s, p.d_fcol);
+            });
             if (rc) return rc;
             rc = timed(p, SHT_K_TC_ANALYS, s, "FP64 tensor-core analysis launch", [&] {
                 return sht::launch_tc64(false, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.p64_a, p.d_off64_a, p.d_c064_a,
                                         p.d_e64_a, p.d_dchunk64, p.d_fcol, data, inter, out, nb, op,
-                                        p.d_err, s);
+                                        p.d_err, s, true);
             });
         }
         if (rc) return rc;

@@ -769,10 +769,12 @@ __device__ __forceinline__ void fft_synth_tile_df(const PlanView<double> &pv, co
 // Analysis tile in double-float (see fft_analys_tile).  Each thread reads its
 // share of its row into registers, the pair's largest exponent is found, and
 // the values go to shared memory converted; the fold converts back to FP64.
+// fmax (may be null): per field, the running maximum of frexp exponents of
+// the folds written (the field scale of the FP64-accurate contraction).
 template <bool MIXED>
 __device__ __forceinline__ void fft_analys_tile_df(const PlanView<double> &pv, const double *__restrict__ grid,
                                                    double *__restrict__ sd, int b, int p0, int G, int op,
-                                                   int vector, unsigned char *smem_raw)
+                                                   int vector, int *__restrict__ fmax, unsigned char *smem_raw)
 {
     const int H = pv.nphi / 2, R = 2 * G;
     const int TPR = row_tpr(H);
@@ -839,6 +841,7 @@ __device__ __forceinline__ void fft_analys_tile_df(const PlanView<double> &pv, c
     }
     // post-twiddle, fold north/south, weight, back to FP64
     double2 *sd2 = reinterpret_cast<double2 *>(sd);
+    unsigned ebits = 0;   // largest biased exponent field written by this thread
     for (int q = threadIdx.x; q < G * (mmax + 1); q += blockDim.x) {
         const int m = q / G, i = q - m * G;
         const int pp = p0 + i;
@@ -868,8 +871,16 @@ __device__ __forceinline__ void fft_analys_tile_df(const PlanView<double> &pv, c
         }
         const int u = s_e[i] - 1023;
         const size_t o = (((size_t)b * (mmax + 1) + m) * npairs + pp) * 2;
-        sd2[o] = make_double2(df2d(s.x, u), df2d(s.y, u));
-        sd2[o + 1] = make_double2(df2d(d.x, u), df2d(d.y, u));
+        const double2 so = make_double2(df2d(s.x, u), df2d(s.y, u)), dd = make_double2(df2d(d.x, u), df2d(d.y, u));
+        sd2[o] = so;
+        sd2[o + 1] = dd;
+        ebits = max(ebits, (unsigned)max(dexp2(so), dexp2(dd)));
+    }
+    if (fmax) {
+        // outputs are normal or zero (df2d flushes below 2^-1022): frexp's
+        // exponent of a normal double is its biased exponent field - 1022
+        ebits = __reduce_max_sync(0xffffffffu, ebits);
+        if ((threadIdx.x & 31) == 0 && ebits != 0) atomicMax(&fmax[b], (int)ebits - 1022);
     }
 }
 
@@ -884,10 +895,10 @@ k_fft_synth_df(PlanView<double> pv, const double *__restrict__ eo, double *__res
 template <bool MIXED>
 __global__ void __launch_bounds__(512)
 k_fft_analys_df(PlanView<double> pv, const double *__restrict__ grid, double *__restrict__ sd, int G, int op,
-                int vector)
+                int vector, int *__restrict__ fmax)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fft_analys_tile_df<MIXED>(pv, grid, sd, blockIdx.y, blockIdx.x * G, G, op, vector, smem_raw);
+    fft_analys_tile_df<MIXED>(pv, grid, sd, blockIdx.y, blockIdx.x * G, G, op, vector, fmax, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -1238,7 +1249,7 @@ cudaError_t launch_fft_synth_df(const PlanView<double> &pv, const double *eo, do
 }
 
 cudaError_t launch_fft_analys_df(const PlanView<double> &pv, const double *grid, double *sd, int batch, Op op,
-                                 bool vector, cudaStream_t s)
+                                 bool vector, cudaStream_t s, int *fmax)
 {
     if (!pv.twdf) return cudaErrorInvalidValue;
     int G, threads;
@@ -1250,9 +1261,9 @@ cudaError_t launch_fft_analys_df(const PlanView<double> &pv, const double *grid,
     if (e != cudaSuccess) return e;
     dim3 gridd((unsigned)((pv.npairs + G - 1) / G), (unsigned)batch);
     if (mixed)
-        k_fft_analys_df<true><<<gridd, threads, smem, s>>>(pv, grid, sd, G, (int)op, vector ? 1 : 0);
+        k_fft_analys_df<true><<<gridd, threads, smem, s>>>(pv, grid, sd, G, (int)op, vector ? 1 : 0, fmax);
     else
-        k_fft_analys_df<false><<<gridd, threads, smem, s>>>(pv, grid, sd, G, (int)op, vector ? 1 : 0);
+        k_fft_analys_df<false><<<gridd, threads, smem, s>>>(pv, grid, sd, G, (int)op, vector ? 1 : 0, fmax);
     return cudaGetLastError();
 }
 

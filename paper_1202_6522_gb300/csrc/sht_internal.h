@@ -192,11 +192,13 @@ cudaError_t launch_fft_analys(const PlanView<T> &pv, const T *grid, T *sd, int b
                               bool vector, cudaStream_t s);
 // The same transforms of FP64 data in double-float arithmetic (pairs of FP32
 // numbers, ~2^-48 relative error per operation), for the FP64-accurate
-// tensor-core mode; needs the plan's double-float twiddles (pv.twdf).
+// tensor-core mode; needs the plan's double-float twiddles (pv.twdf).  With
+// fmax, the analysis also raises fmax[b] to the frexp exponent of every fold
+// of field b it writes (fmax initialised by the caller).
 cudaError_t launch_fft_synth_df(const PlanView<double> &pv, const double *eo, double *grid, int batch, Op op,
                                 cudaStream_t s);
 cudaError_t launch_fft_analys_df(const PlanView<double> &pv, const double *grid, double *sd, int batch, Op op,
-                                 bool vector, cudaStream_t s);
+                                 bool vector, cudaStream_t s, int *fmax = nullptr);
 
 
 
@@ -291,10 +293,14 @@ void tc64_panel_layout(int lmax, int mmax, int mres, int npairs, std::vector<uns
 size_t tc64_data_bytes(int mmax, int npairs, size_t nchunk_s);
 cudaError_t tc64_build(const PlanView<double> &pv, const unsigned long long *off_s, const unsigned long long *off_a,
                        unsigned char *ps, unsigned char *pa, int *es, int *ea, int *c0_s, int *c0_a, cudaStream_t st);
+// fcol_ready: fcol already holds the field exponents of `in` (else this
+// computes them first).
 cudaError_t launch_tc64(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const unsigned char *panel,
                         const unsigned long long *off, const int *c0, const int *erow,
                         const unsigned long long *dchunk, int *fcol, unsigned char *data, const double *in,
-                        double *out, int batch, Op op, int *err, cudaStream_t st);
+                        double *out, int batch, Op op, int *err, cudaStream_t st, bool fcol_ready = false);
+// Sets fcol[0 .. batch) to "no value yet" before a producer raises it.
+cudaError_t tc64_reset_fcol(int *fcol, int batch, cudaStream_t st);
 cudaError_t launch_selftest_timeout(int *err, unsigned long long max_ns, cudaStream_t st);
 
 // On-the-fly mode (tc.cu): FP32 recurrence reseeded every 32 degrees.

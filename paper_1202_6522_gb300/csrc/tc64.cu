@@ -543,6 +543,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc64(Tc64Args a)
 
 int tc64_max_batch() { return kBatch64; }
 
+cudaError_t tc64_reset_fcol(int *fcol, int batch, cudaStream_t st)
+{
+    k_fill_int<<<1, 32, 0, st>>>(fcol, kExpNone, (size_t)batch);
+    return cudaGetLastError();
+}
+
 void tc64_panel_layout(int lmax, int mmax, int mres, int npairs, std::vector<unsigned long long> &off_s,
                        std::vector<unsigned long long> &off_a, size_t &bytes_s, size_t &bytes_a,
                        std::vector<unsigned long long> &dchunk, size_t &nchunk_s)
@@ -596,13 +602,15 @@ cudaError_t tc64_build(const PlanView<double> &pv, const unsigned long long *off
 cudaError_t launch_tc64(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const unsigned char *panel,
                         const unsigned long long *off, const int *c0, const int *erow,
                         const unsigned long long *dchunk, int *fcol, unsigned char *data, const double *in,
-                        double *out, int batch, Op op, int *err, cudaStream_t st)
+                        double *out, int batch, Op op, int *err, cudaStream_t st, bool fcol_ready)
 {
     if (batch < 1 || batch > kBatch64) return cudaErrorInvalidValue;
-    // field exponents of the data
-    k_fill_int<<<1, 32, 0, st>>>(fcol, kExpNone, (size_t)batch);
-    const size_t per_field = synth ? (size_t)2 * nlm : (size_t)(mmax + 1) * npairs * 4;
-    k_colscale<<<dim3(64, (unsigned)batch), 256, 0, st>>>(in, per_field, fcol);
+    if (!fcol_ready) {
+        // field exponents of the data
+        k_fill_int<<<1, 32, 0, st>>>(fcol, kExpNone, (size_t)batch);
+        const size_t per_field = synth ? (size_t)2 * nlm : (size_t)(mmax + 1) * npairs * 4;
+        k_colscale<<<dim3(64, (unsigned)batch), 256, 0, st>>>(in, per_field, fcol);
+    }
     // data digits
     const int Le0 = (lmax + 2) / 2;
     const int maxch = synth ? (Le0 + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
