@@ -270,10 +270,20 @@ __global__ void k_colscale(const double *__restrict__ x, size_t per_field, int *
     const int b = blockIdx.y;
     // the bit patterns of non-negative doubles order like the values: the
     // maximum |x| is an integer maximum, off the FP64 pipe
+    constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
     const unsigned long long *xb = reinterpret_cast<const unsigned long long *>(x) + (size_t)b * per_field;
+    const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
     unsigned long long mx = 0;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_field; i += (size_t)gridDim.x * blockDim.x)
-        mx = max(mx, xb[i] & 0x7FFFFFFFFFFFFFFFull);
+    if ((per_field & 1) == 0 && (reinterpret_cast<uintptr_t>(xb) & 15) == 0) {
+        // 16-byte loads when the field starts on a 16-byte boundary
+        const ulonglong2 *x2 = reinterpret_cast<const ulonglong2 *>(xb);
+        for (size_t i = i0; i < per_field / 2; i += stride) {
+            const ulonglong2 v = x2[i];
+            mx = max(mx, max(v.x & kAbs, v.y & kAbs));
+        }
+    } else {
+        for (size_t i = i0; i < per_field; i += stride) mx = max(mx, xb[i] & kAbs);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx != 0) atomicMax(&f[b], exp_above(__longlong_as_double((long long)mx)));
