@@ -73,3 +73,24 @@ def test_python_errors_map_to_exceptions(lib):
     from paper_1202_6522_gb300 import _capi
     with pytest.raises(ValueError):
         _capi.sht_create(10, 11, 16, 32)
+
+
+def _ints(v):
+    return (ctypes.c_int * len(v))(*v)
+
+
+@pytest.mark.parametrize("mode,nphi,code", [
+    (7, 16, -1),     # not a batch path (SHT_F32, SHT_TC_BF16X3 or SHT_F32_AUTO)
+    (0, 16, -1),     # SHT_F64 has no uneven-batch form
+    (2, 28, -5),     # a field whose FFT length 14 has the factor 7
+    (3, 8192, -5),   # nphi above the batch FFT limit
+])
+def test_batch_create_mode_rejects_on_host(lib, mode, nphi, code):
+    b = ctypes.c_void_p()
+    assert lib.sht_batch_create_mode(2, _ints([7, 7]), _ints([8, 8]), _ints([16, nphi]), mode, ctypes.byref(b)) == code
+    assert b.value is None
+    assert lib.sht_last_error()
+
+
+def test_batch_mode_null_handle(lib):
+    assert lib.sht_batch_mode(None, None, None) == -1
