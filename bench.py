@@ -84,7 +84,7 @@ def tc_algorithmic_bytes(batch, lmax=LMAX, nlat=NLAT, polar_skip=0.0):
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum);
 # reported only while the source file holding the kernel is unchanged (its
 # SHA-256 below, updated only for edits outside that kernel), else null.
-TC_TRAFFIC_SRC_SHA256 = "743d6d8792eaaf66298136145a81966c89eb03cd39c9534c999d2c66b77fc602"
+TC_TRAFFIC_SRC_SHA256 = "e6f6626ca470714a564579e4c4fb51e0f562544fd10f999c3e9d88e837ea5708"
 TC_TRAFFIC_BYTES = {"tc_synth": 866.161408e6 + 73.604096e6, "tc_analys": 883.199872e6 + 37.287936e6}
 
 

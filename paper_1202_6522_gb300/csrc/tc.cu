@@ -1346,12 +1346,14 @@ __global__ void k_selftest_timeout(int *err, unsigned long long max_ns)
 
 int cols_of(int batch) { return tc_rows(batch, false); }
 
+// Launch of the vector contraction (two panels per stage, one CTA per SM:
+// its accumulators take the SM's tensor memory): up to 4 stages within 200 KB,
+// a.halves field groups per (m, tile).
 template <typename K>
 cudaError_t launch_contraction(K kernel, bool synth, int lmax, int mmax, int npairs, int npanels, TcArgs &a,
                                cudaStream_t st)
 {
     int stages = 4;
-    // scalar kernel: <= 110 KB so that two CTAs share an SM
     const size_t cap = npanels == 1 ? 110 * 1024 : 200 * 1024;
     while (stages > 2 && smem_bytes_of(npanels, a.rows, stages) > cap) --stages;
     a.stages = stages;
