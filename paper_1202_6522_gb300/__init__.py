@@ -2,7 +2,8 @@
 
 The transforms of Schaeffer's SHTns paper (arXiv:1202.6522) as hand-written
 CUDA kernels behind a C ABI (include/sht.h, libsht.so).  ``SHT`` is the torch
-front end; ``_capi`` is the ctypes binding with the C names.
+front end; ``_capi`` is the ctypes binding with the C names; ``build.build()``
+compiles the library in-tree.
 """
 from __future__ import annotations
 
@@ -16,7 +17,4 @@ def __getattr__(name):
     if name == "UnevenBatch":
         from .transform import UnevenBatch
         return UnevenBatch
-    if name == "build":
-        from .build import build
-        return build
     raise AttributeError(name)
