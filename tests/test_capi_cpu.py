@@ -94,3 +94,17 @@ def test_batch_create_mode_rejects_on_host(lib, mode, nphi, code):
 
 def test_batch_mode_null_handle(lib):
     assert lib.sht_batch_mode(None, None, None) == -1
+
+
+@pytest.mark.parametrize("args,code", [
+    ((31, 7, 0, 32, 16), -1),       # mres < 1
+    ((31, 8, 4, 32, 32), -1),       # mmax mres = 32 > lmax
+    ((31, 7, 4, 31, 16), -1),       # nlat < lmax + 1
+    ((31, 7, 4, 32, 14), -1),       # nphi < 2 mmax + 1 (orders counted by index)
+    ((31, 7, 4, 32, 22), -5),       # nphi / 2 = 11
+    ((5000, 10, 4, 5001, 32), -5),  # lmax above 4095
+])
+def test_create_mres_rejects_on_host(lib, args, code):
+    h = ctypes.c_void_p()
+    assert lib.sht_create_mres(*args, ctypes.byref(h)) == code
+    assert h.value is None
