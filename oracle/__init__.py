@@ -59,6 +59,7 @@ def _load():
         lib.oracle_gauss.restype = c_int
         lib.oracle_plm.argtypes = [c_int, c_int, ctypes.c_double, D]
         lib.oracle_dplm.argtypes = [c_int, c_int, ctypes.c_double, D]
+        lib.oracle_plm_order.argtypes = [c_int, c_int, ctypes.c_double, D, D]
         lib.oracle_nlm.argtypes = [c_int, c_int]
         lib.oracle_nlm.restype = ctypes.c_long
         lib.oracle_threads.restype = c_int
@@ -113,6 +114,22 @@ def plm(lmax: int, mmax: int, x: float) -> np.ndarray:
     """P_n^m(x) (Sec. 3.2 recurrence, no Condon-Shortley phase), packed."""
     out = np.zeros(nlm(lmax, mmax))
     _load().oracle_plm(lmax, mmax, float(x), _dp(out))
+    return out
+
+
+def plm_order(lmax: int, m: int, x, deriv: bool = False) -> np.ndarray:
+    """P_n^m(x_j) (or dP_n^m/dtheta) of one order m, n = m..lmax, at the nodes
+    x (scalar or 1-D): array [len(x), lmax - m + 1] -- the same recurrence as
+    plm, one column of its packed layout."""
+    xs = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    L = lmax - m + 1
+    p = np.zeros(L)
+    d = np.zeros(L)
+    out = np.zeros((xs.size, L))
+    lib = _load()
+    for i, xv in enumerate(xs):
+        lib.oracle_plm_order(lmax, m, float(xv), _dp(p), _dp(d) if deriv else None)
+        out[i] = d if deriv else p
     return out
 
 

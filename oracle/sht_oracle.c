@@ -195,6 +195,15 @@ void oracle_plm(int lmax, int mmax, double x, double *out)
     free(col);
 }
 
+/* Public: P_n^m(x) and dP_n^m/dtheta at x of one order m, n = m..lmax, into
+ * p[n - m] and (if not NULL) dtheta[n - m] -- the columns oracle_plm and
+ * oracle_dplm pack, for callers that need one order at many nodes. */
+void oracle_plm_order(int lmax, int m, double x, double *p, double *dtheta)
+{
+    plm_order(lmax, m, x, p);
+    if (dtheta) dtheta_order(lmax, m, x, p, dtheta);
+}
+
 /* Public: dP_n^m/dtheta at x for all (n, m <= mmax), packed. */
 void oracle_dplm(int lmax, int mmax, double x, double *out)
 {

@@ -433,3 +433,17 @@ def test_dense_synthesis_matrix_transpose():
         b = oracle.synth_adj(lmax, lmax, nlat, nphi, g.reshape(nlat, nphi))
         MT[:, q] = [b[i].real if part == 1.0 else b[i].imag for i, part, _ in cols]
     np.testing.assert_allclose(MT, M.T, atol=1e-14)
+
+
+def test_plm_order_is_a_column_of_plm():
+    """The single-order entry point returns exactly the packed columns of plm
+    and dplm_dtheta (same recurrence, same rounding)."""
+    lmax = 40
+    x, _ = oracle.gauss(33)
+    for m in (0, 3, 40):
+        idx = [oracle.lm_index(lmax, n, m) for n in range(m, lmax + 1)]
+        tab = oracle.plm_order(lmax, m, x[:5])
+        dtab = oracle.plm_order(lmax, m, x[:5], deriv=True)
+        for j in range(5):
+            assert np.array_equal(tab[j], oracle.plm(lmax, lmax, x[j])[idx])
+            assert np.array_equal(dtab[j], oracle.dplm_dtheta(lmax, lmax, x[j])[idx])
