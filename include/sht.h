@@ -73,7 +73,13 @@ enum {
 
 enum {
     SHT_F64 = 0,       /* FP64 throughout: the plain path                              */
-    SHT_F32 = 1,       /* FP32 data and recurrence with an explicit exponent scale     */
+    SHT_F32 = 1,       /* FP32 data and recurrence with the explicit exponent scale of
+                        * Sec. 3.5, restarted every 32 degrees from states the FP64
+                        * recurrence computes once per plan (built by the first call
+                        * in this mode or by sht_reserve: 16 B per latitude pair and
+                        * 32 degrees, (lmax+1)^2 ceil(nlat/2) / 4 bytes, 138 MB at
+                        * lmax = 1023), so that FP32 rounding errors grow over at most
+                        * 32 steps instead of lmax. */
     SHT_TC_BF16X3 = 2, /* FP32 data; the per-order Legendre contraction on the tensor
                         * cores against P_n^m panels built once by the FP64 recurrence
                         * (the precomputed-P_n^m variant of Sec. 3.1), each operand split
@@ -201,17 +207,21 @@ SHT_API int sht_sync_status(sht_handle h, void *stream);
  * or a custom pool, and loops where the implicit device synchronisation of
  * cudaMalloc/cudaFree is not acceptable.  The handle itself must have been
  * created beforehand (sht_create allocates the plan tables).
- *   - Modes SHT_F64 and SHT_F32 (SHT_F32_AUTO runs SHT_F32 here);
- *     SHT_TC_BF16X3, SHT_TC_OTF and SHT_TC_F64 return SHT_EUNSUPPORTED, their
- *     panels or seeds being allocated.
+ *   - Modes SHT_F64 and SHT_F32 (SHT_F32_AUTO runs SHT_F32 here), any plan
+ *     including m-stride ones; SHT_TC_BF16X3, SHT_TC_OTF and SHT_TC_F64 return
+ *     SHT_EUNSUPPORTED, their panels or seeds being allocated.  SHT_F32 needs
+ *     the plan's FP32 recurrence restart states, which the first SHT_F32 call
+ *     or sht_reserve(h, batch, SHT_F32) builds; without them the call returns
+ *     SHT_EUNSUPPORTED and enqueues nothing.
  *   - The fixed array holds SHT_STATIC_SCRATCH_BYTES (16 MiB) on every GPU that
  *     loads this library, until the process exits.  A call needs
  *     batch * (mmax+1) * ceil(nlat/2) * 4 * sizeof(element) bytes (N = 1023 in
  *     FP64 fits one field, in FP32 two); larger calls return SHT_EINVAL and
  *     enqueue nothing.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture begins.
+ *   - The array's device address is looked up (cudaGetSymbolAddress) by
+ *     sht_create, with the plan's device current, and kept per device; this
+ *     call only reads it.  cudaDeviceReset invalidates every handle; a handle
+ *     created after a reset stores the address of the reloaded module.
  *   - All calls, from any handle, share the one array: calls whose work can
  *     overlap on the GPU (different streams without ordering) race on it.
  *     Nothing in it needs to start at zero: each call overwrites the part it

@@ -331,7 +331,9 @@ int sht_batch_create_mode(int nfields, const int *lmax, const int *nlat, const i
             p->nphi = nphi[f];
             std::string err;
             int rc = sht::plan_build(*p, err);
+            if (!rc) rc = sht::plan_seeds32(*p, err);   // the CUDA-core kernels restart from these
             if (rc) {
+                sht::plan_free(*p);
                 free_batch(b);
                 return bfail(rc, err);
             }

@@ -244,6 +244,15 @@ int ensure_otf(sht::Plan &p)
     return SHT_OK;
 }
 
+// FP32 CUDA-core path: the recurrence restart states (plan_seeds32), built on
+// the first call that needs them.
+int ensure_seeds32(sht::Plan &p)
+{
+    std::string err;
+    const int rc = sht::plan_seeds32(p, err);
+    return rc ? fail(rc, err) : SHT_OK;
+}
+
 size_t elem_size(int mode) { return (mode == SHT_F64 || mode == SHT_TC_F64) ? sizeof(double) : sizeof(float); }
 
 // FP64-accurate tensor-core mode: digit-slice panels (about 6 (lmax+1)^3
@@ -531,6 +540,7 @@ int scalar_s2g(sht_handle h, const void *spec, void *grid, int batch, int mode, 
         if ((rc = ensure_work(h->p, tc64_work_bytes(h->p, batch)))) return rc;
         return run_tc64(h->p, true, spec, grid, batch, op, s);
     }
+    if (mode == SHT_F32 && (rc = ensure_seeds32(h->p))) return rc;
     if ((rc = ensure_work(h->p, inter_bytes(h->p, batch, mode)))) return rc;
     if (mode == SHT_F64) return run_synth<double>(h->p, h->p.view64(), spec, grid, batch, op, s);
     return run_synth<float>(h->p, h->p.view32(), spec, grid, batch, op, s);
@@ -558,6 +568,7 @@ int scalar_g2s(sht_handle h, const void *grid, void *spec, int batch, int mode, 
         if ((rc = ensure_work(h->p, tc64_work_bytes(h->p, batch)))) return rc;
         return run_tc64(h->p, false, grid, spec, batch, op, s);
     }
+    if (mode == SHT_F32 && (rc = ensure_seeds32(h->p))) return rc;
     if ((rc = ensure_work(h->p, inter_bytes(h->p, batch, mode)))) return rc;
     if (mode == SHT_F64) return run_analys<double>(h->p, h->p.view64(), grid, spec, batch, op, s);
     return run_analys<float>(h->p, h->p.view32(), grid, spec, batch, op, s);
@@ -576,6 +587,7 @@ int vector_s2g(sht_handle h, const void *S, const void *T, void *vt, void *vp, i
         if ((rc = ensure_work(h->p, tc_work_bytes(h->p, batch, true)))) return rc;
         return run_synth_vec_tc(h->p, S, T, vt, vp, batch, op, s);
     }
+    if (mode == SHT_F32 && (rc = ensure_seeds32(h->p))) return rc;
     if ((rc = ensure_work(h->p, 2 * inter_bytes(h->p, batch, mode)))) return rc;
     if (mode == SHT_F64) return run_synth_vec<double>(h->p, h->p.view64(), S, T, vt, vp, batch, op, s);
     return run_synth_vec<float>(h->p, h->p.view32(), S, T, vt, vp, batch, op, s);
@@ -594,6 +606,7 @@ int vector_g2s(sht_handle h, const void *vt, const void *vp, void *S, void *T, i
         if ((rc = ensure_work(h->p, tc_work_bytes(h->p, batch, true)))) return rc;
         return run_analys_vec_tc(h->p, vt, vp, S, T, batch, op, s);
     }
+    if (mode == SHT_F32 && (rc = ensure_seeds32(h->p))) return rc;
     if ((rc = ensure_work(h->p, 2 * inter_bytes(h->p, batch, mode)))) return rc;
     if (mode == SHT_F64) return run_analys_vec<double>(h->p, h->p.view64(), vt, vp, S, T, batch, op, s);
     return run_analys_vec<float>(h->p, h->p.view32(), vt, vp, S, T, batch, op, s);
@@ -817,6 +830,10 @@ cudaError_t sht::tc_batch_legendre(sht::Plan &p, bool synth, const float *in, fl
     return cudaSuccess;
 }
 
+namespace {
+int static_scratch_refresh(int device);
+}  // namespace
+
 extern "C" {
 
 const char *sht_last_error(void) { return g_err.c_str(); }
@@ -851,6 +868,13 @@ int sht_create_mres(int lmax, int mmax, int mres, int nlat, int nphi, sht_handle
         delete h;
         return fail(rc, err);
     }
+    // device address of the fixed array of sht_synth_static, looked up here
+    // with the plan's device current (see static_scratch_refresh)
+    if ((rc = static_scratch_refresh(h->p.device))) {
+        sht::plan_free(h->p);
+        delete h;
+        return rc;
+    }
     *out = h;
     return SHT_OK;
 }
@@ -881,6 +905,7 @@ int sht_reserve(sht_handle h, int batch, int mode)
         if ((rc = ensure_panels64(h->p))) return rc;
         return ensure_work(h->p, tc64_work_bytes(h->p, batch));
     }
+    if ((mode == SHT_F32 || mode == SHT_F32_AUTO) && (rc = ensure_seeds32(h->p))) return rc;
     return ensure_work(h->p, 2 * inter_bytes(h->p, batch, mode));
 }
 
@@ -1094,6 +1119,7 @@ extern "C" int sht_tune(sht_handle h, int batch, int mode, double *report, void 
     sht::Plan &p = h->p;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int shape_mode = mode == SHT_F64 ? SHT_F64 : SHT_F32;
+    if (shape_mode == SHT_F32 && (rc = ensure_seeds32(p))) return rc;
     const size_t es = elem_size(shape_mode);
     void *spec = nullptr, *grid = nullptr;
     cudaError_t e = cudaMalloc(&spec, (size_t)batch * p.nlm * 2 * es);
@@ -1189,25 +1215,44 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_static_scratch[SHT_STATIC_SCRATCH_BYTES];
 
-// Device address of g_static_scratch, looked up once per device.  In host code
-// the symbol name is only a stand-in for the device object, so kernels must
-// be given the address returned by cudaGetSymbolAddress.
+// Device address of g_static_scratch on each device.  In host code the
+// symbol's name is only a stand-in for the device object, so kernels must be
+// given the address cudaGetSymbolAddress returns with that device current.
+// sht_create looks it up (static_scratch_refresh) for the device it builds the
+// plan on -- the current device, which every later call on the handle must
+// also have current (check_handle) -- and stores it under that ordinal; a plan
+// created after a device reset thus stores the address of the reloaded
+// module.  sht_synth_static only reads the stored address.
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 void *g_static_ptr[kMaxDevices] = {};
 
-int static_scratch(int device, void **out)
+int static_scratch_refresh(int device)
 {
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return fail(SHT_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (cur != device) return fail(SHT_EINVAL, "static scratch: the plan's device is not current");
     if (device < 0 || device >= kMaxDevices) return fail(SHT_EUNSUPPORTED, "device ordinal too large");
+    void *ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess || !ptr)
+        return fail(SHT_ECUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[device]) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-        if (e != cudaSuccess || !ptr)
-            return fail(SHT_ECUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
-        g_static_ptr[device] = ptr;
-    }
-    *out = g_static_ptr[device];
+    g_static_ptr[device] = ptr;
+    return SHT_OK;
+}
+
+// The stored address for the current device (the handle's, see check_handle).
+int static_scratch(void **out)
+{
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return fail(SHT_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (cur < 0 || cur >= kMaxDevices) return fail(SHT_EUNSUPPORTED, "device ordinal too large");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[cur]) return fail(SHT_EINVAL, "sht_synth_static: no plan was created on this device");
+    *out = g_static_ptr[cur];
     return SHT_OK;
 }
 
@@ -1221,13 +1266,16 @@ extern "C" int sht_synth_static(sht_handle h, const void *spec, void *grid, int 
     if (mode == SHT_TC_BF16X3 || mode == SHT_TC_OTF || mode == SHT_TC_F64)
         return fail(SHT_EUNSUPPORTED, "sht_synth_static: the tensor-core modes need tables allocated by the handle");
     if (mode == SHT_F32_AUTO) mode = SHT_F32;
+    if (mode == SHT_F32 && !h->p.seeds32)
+        return fail(SHT_EUNSUPPORTED, "sht_synth_static: SHT_F32 needs the plan's FP32 recurrence restart states; "
+                                      "build them first with sht_reserve(h, batch, SHT_F32) or any SHT_F32 call");
     const size_t need = inter_bytes(h->p, batch, mode);
     if (need > (size_t)SHT_STATIC_SCRATCH_BYTES)
         return fail(SHT_EINVAL, "sht_synth_static: this call needs " + std::to_string(need) +
                                     " bytes of intermediate storage, more than the fixed " +
                                     std::to_string((size_t)SHT_STATIC_SCRATCH_BYTES) + "-byte array");
     void *scratch = nullptr;
-    if ((rc = static_scratch(h->p.device, &scratch))) return rc;
+    if ((rc = static_scratch(&scratch))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (mode == SHT_F64) {
         const sht::PlanView<double> pv = h->p.view64();

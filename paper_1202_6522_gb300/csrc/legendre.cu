@@ -86,6 +86,35 @@ __device__ __forceinline__ int kmin_of(const int (&k)[LPT])
     return r;
 }
 
+// FP32 plans: restart the recurrence of the LPT pairs p[] at segment `seg`
+// (degrees n - m in [kSeedSeg seg, kSeedSeg (seg + 1))) of order index m from
+// the state the FP64 recurrence computed once per plan (y1 = P_{n0-1},
+// y2 = P_{n0-2} and the exponent counter k of Sec. 3.5).  No-op in FP64.
+template <typename T, int LPT>
+__device__ __forceinline__ void reseed(const PlanView<T> &pv, int m, int seg, const int (&p)[LPT], T (&y1)[LPT],
+                                       T (&y2)[LPT], int (&k)[LPT])
+{
+    if constexpr (sizeof(T) == sizeof(float)) {
+        const float4 *sd = pv.seeds + (size_t)(pv.segoff[m] + seg) * pv.npairs;
+#pragma unroll
+        for (int i = 0; i < LPT; ++i) {
+            if (p[i] < pv.npairs) {
+                const float4 v = __ldg(sd + p[i]);
+                y1[i] = v.x;
+                y2[i] = v.y;
+                k[i] = __float_as_int(v.z);
+            }
+        }
+    }
+}
+
+// The FP32 kernels need the restart states; a plan without them is refused
+// rather than run on the unrestarted recurrence.
+template <typename T> bool seeds_ok(const PlanView<T> &pv)
+{
+    return sizeof(T) != sizeof(float) || (pv.seeds != nullptr && pv.segoff != nullptr);
+}
+
 // Warp butterfly that sums V values (V a multiple of 32) over the 32 lanes and
 // leaves lane l holding the sums of values [l*V/32, (l+1)*V/32) in v[0..V/32).
 template <typename T, int V>
@@ -109,6 +138,7 @@ __device__ __forceinline__ void warp_transpose_reduce(T (&v)[V], int lane)
 // Scalar synthesis.  grid.x = (m, pair block), heaviest m first; grid.y = field chunk.
 // ---------------------------------------------------------------------------
 constexpr int kSynthNch = 128;  // degrees staged per chunk (scalar synthesis)
+static_assert(kSynthNch % kSeedSeg == 0, "restart segments must not straddle staged chunks");
 
 // One (order m, pair block pb, field chunk b0) tile of the scalar synthesis,
 // run by a whole CTA of NT threads; s_ab[kSynthNch], s_f[kSynthNch * BC] are
@@ -167,37 +197,14 @@ __device__ __forceinline__ void synth_tile(const PlanView<T> &pv, const T *__res
             }
         }
         __syncthreads();
-        const bool scaled = __any_sync(kFull, kmax_of<T, LPT>(k) > 0);
-        if (!scaled) {
-            for (int t = 0; t < cnt; t += 2) {
-                T2 ab = s_ab[t];
-                rec_step<T, LPT, false>(ab.x, ab.y, x, y1, y2, k, c);
-#pragma unroll
-                for (int b = 0; b < BC; ++b) {
-                    const T2 f = s_f[t * BC + b];
-#pragma unroll
-                    for (int i = 0; i < LPT; ++i) {
-                        er[i][b] = fma(f.x, c[i], er[i][b]);
-                        ei[i][b] = fma(f.y, c[i], ei[i][b]);
-                    }
-                }
-                ab = s_ab[t + 1];
-                rec_step<T, LPT, false>(ab.x, ab.y, x, y1, y2, k, c);
-#pragma unroll
-                for (int b = 0; b < BC; ++b) {
-                    const T2 f = s_f[(t + 1) * BC + b];
-#pragma unroll
-                    for (int i = 0; i < LPT; ++i) {
-                        orr[i][b] = fma(f.x, c[i], orr[i][b]);
-                        oi[i][b] = fma(f.y, c[i], oi[i][b]);
-                    }
-                }
-            }
-        } else {
-            for (int t = 0; t < cnt; t += 2) {
-                T2 ab = s_ab[t];
-                rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c);
-                if (__any_sync(kFull, kmin_of<T, LPT>(k) == 0)) {
+        for (int s0 = 0; s0 < cnt; s0 += kSeedSeg) {
+            reseed<T, LPT>(pv, m, (n0 + s0) / kSeedSeg, p, y1, y2, k);
+            const int s1 = min(cnt, s0 + kSeedSeg);
+            const bool scaled = __any_sync(kFull, kmax_of<T, LPT>(k) > 0);
+            if (!scaled) {
+                for (int t = s0; t < s1; t += 2) {
+                    T2 ab = s_ab[t];
+                    rec_step<T, LPT, false>(ab.x, ab.y, x, y1, y2, k, c);
 #pragma unroll
                     for (int b = 0; b < BC; ++b) {
                         const T2 f = s_f[t * BC + b];
@@ -207,10 +214,8 @@ __device__ __forceinline__ void synth_tile(const PlanView<T> &pv, const T *__res
                             ei[i][b] = fma(f.y, c[i], ei[i][b]);
                         }
                     }
-                }
-                ab = s_ab[t + 1];
-                rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c);
-                if (__any_sync(kFull, kmin_of<T, LPT>(k) == 0)) {
+                    ab = s_ab[t + 1];
+                    rec_step<T, LPT, false>(ab.x, ab.y, x, y1, y2, k, c);
 #pragma unroll
                     for (int b = 0; b < BC; ++b) {
                         const T2 f = s_f[(t + 1) * BC + b];
@@ -218,6 +223,35 @@ __device__ __forceinline__ void synth_tile(const PlanView<T> &pv, const T *__res
                         for (int i = 0; i < LPT; ++i) {
                             orr[i][b] = fma(f.x, c[i], orr[i][b]);
                             oi[i][b] = fma(f.y, c[i], oi[i][b]);
+                        }
+                    }
+                }
+            } else {
+                for (int t = s0; t < s1; t += 2) {
+                    T2 ab = s_ab[t];
+                    rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c);
+                    if (__any_sync(kFull, kmin_of<T, LPT>(k) == 0)) {
+#pragma unroll
+                        for (int b = 0; b < BC; ++b) {
+                            const T2 f = s_f[t * BC + b];
+#pragma unroll
+                            for (int i = 0; i < LPT; ++i) {
+                                er[i][b] = fma(f.x, c[i], er[i][b]);
+                                ei[i][b] = fma(f.y, c[i], ei[i][b]);
+                            }
+                        }
+                    }
+                    ab = s_ab[t + 1];
+                    rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c);
+                    if (__any_sync(kFull, kmin_of<T, LPT>(k) == 0)) {
+#pragma unroll
+                        for (int b = 0; b < BC; ++b) {
+                            const T2 f = s_f[(t + 1) * BC + b];
+#pragma unroll
+                            for (int i = 0; i < LPT; ++i) {
+                                orr[i][b] = fma(f.x, c[i], orr[i][b]);
+                                oi[i][b] = fma(f.y, c[i], oi[i][b]);
+                            }
                         }
                     }
                 }
@@ -259,6 +293,7 @@ k_synth(PlanView<T> pv, const T *__restrict__ spec, T *__restrict__ eo, int batc
 // covers all latitude pairs (NT * LPT >= npairs).
 // ---------------------------------------------------------------------------
 constexpr int kAnalysNch = 128;  // degrees staged per chunk (scalar analysis)
+static_assert(kAnalysNch % kSeedSeg == 0 && kSeedSeg % 16 == 0, "restart segments must align with the chunks");
 
 // One (order m, field chunk b0) tile of the scalar analysis, run by the whole
 // CTA (blockDim.x * LPT >= npairs, at most 8 warps); s_ab[kAnalysNch] and
@@ -280,15 +315,15 @@ __device__ __forceinline__ void analys_tile(const PlanView<T> &pv, const T *__re
     const long col = col_of_mres(lmax, m, pv.mres);
 
     T x[LPT], y1[LPT], y2[LPT], c[LPT];
-    int k[LPT];
+    int k[LPT], p[LPT];
     T2 sv[LPT][BC], dv[LPT][BC];
     const T2 *sd2 = reinterpret_cast<const T2 *>(sd);
 #pragma unroll
     for (int i = 0; i < LPT; ++i) {
-        const int p = i * NT + threadIdx.x;
-        const bool v = p < npairs;
-        const size_t o = (size_t)m * npairs + p;
-        x[i] = v ? pv.x[p] : T(0);
+        p[i] = i * NT + threadIdx.x;
+        const bool v = p[i] < npairs;
+        const size_t o = (size_t)m * npairs + p[i];
+        x[i] = v ? pv.x[p[i]] : T(0);
         y2[i] = v ? pv.pmm[o] : T(0);
         k[i] = v ? pv.pmmk[o] : 0;
         y1[i] = T(0);
@@ -299,7 +334,7 @@ __device__ __forceinline__ void analys_tile(const PlanView<T> &pv, const T *__re
             sv[i][b] = z;
             dv[i][b] = z;
             if (v && b0 + b < batch) {
-                const size_t q = (((size_t)(b0 + b) * (pv.mmax + 1) + m) * npairs + p) * 2;
+                const size_t q = (((size_t)(b0 + b) * (pv.mmax + 1) + m) * npairs + p[i]) * 2;
                 sv[i][b] = sd2[q];
                 dv[i][b] = sd2[q + 1];
             }
@@ -320,6 +355,7 @@ __device__ __forceinline__ void analys_tile(const PlanView<T> &pv, const T *__re
         }
         __syncthreads();
         for (int t0 = 0; t0 < cnt; t0 += K) {
+            if ((n0 + t0) % kSeedSeg == 0) reseed<T, LPT>(pv, m, (n0 + t0) / kSeedSeg, p, y1, y2, k);
             T acc[32];
 #pragma unroll
             for (int q = 0; q < 32; ++q) acc[q] = T(0);
@@ -456,8 +492,12 @@ k_synth_vec(PlanView<T> pv, const T *__restrict__ Sg, const T *__restrict__ Tg, 
             }
         }
         __syncthreads();
-        const bool scaled = __any_sync(kFull, kmax_of<T, LPT>(k) > 0);
+        bool scaled = false;
         for (int t = 0; t < cnt; t += 2) {
+            if (t % kSeedSeg == 0) {
+                reseed<T, LPT>(pv, m, (n0 + t) / kSeedSeg, p, y1, y2, k);
+                scaled = __any_sync(kFull, kmax_of<T, LPT>(k) > 0);
+            }
 #pragma unroll
             for (int par = 0; par < 2; ++par) {
                 const int tt = t + par;
@@ -556,16 +596,16 @@ k_analys_vec(PlanView<T> pv, const T *__restrict__ sdt, const T *__restrict__ sd
     const long col = col_of_mres(lmax, m, pv.mres);
 
     T x[LPT], y1[LPT], y2[LPT], c[LPT];
-    int k[LPT];
+    int k[LPT], p[LPT];
     T2 st_[LPT][BC], dt_[LPT][BC], sp_[LPT][BC], dp_[LPT][BC];
     const T2 *sdt2 = reinterpret_cast<const T2 *>(sdt);
     const T2 *sdp2 = reinterpret_cast<const T2 *>(sdp);
 #pragma unroll
     for (int i = 0; i < LPT; ++i) {
-        const int p = i * NT + threadIdx.x;
-        const bool v = p < npairs;
-        const size_t o = (size_t)m * npairs + p;
-        x[i] = v ? pv.x[p] : T(0);
+        p[i] = i * NT + threadIdx.x;
+        const bool v = p[i] < npairs;
+        const size_t o = (size_t)m * npairs + p[i];
+        x[i] = v ? pv.x[p[i]] : T(0);
         y2[i] = v ? pv.pmm[o] : T(0);
         k[i] = v ? pv.pmmk[o] : 0;
         y1[i] = T(0);
@@ -575,7 +615,7 @@ k_analys_vec(PlanView<T> pv, const T *__restrict__ sdt, const T *__restrict__ sd
             z.x = T(0); z.y = T(0);
             st_[i][b] = dt_[i][b] = sp_[i][b] = dp_[i][b] = z;
             if (v && b0 + b < batch) {
-                const size_t q = (((size_t)(b0 + b) * (pv.mmax + 1) + m) * npairs + p) * 2;
+                const size_t q = (((size_t)(b0 + b) * (pv.mmax + 1) + m) * npairs + p[i]) * 2;
                 st_[i][b] = sdt2[q];
                 dt_[i][b] = sdt2[q + 1];
                 sp_[i][b] = sdp2[q];
@@ -600,6 +640,7 @@ k_analys_vec(PlanView<T> pv, const T *__restrict__ sdt, const T *__restrict__ sd
         }
         __syncthreads();
         for (int t0 = 0; t0 < cnt; t0 += K) {
+            if ((n0 + t0) % kSeedSeg == 0) reseed<T, LPT>(pv, m, (n0 + t0) / kSeedSeg, p, y1, y2, k);
             // per (kx, b): SA(2) SB(2) TA(2) TB(2)
             T acc[32];
 #pragma unroll
@@ -733,6 +774,7 @@ template <typename T>
 cudaError_t launch_legendre_synth_cfg(const PlanView<T> &pv, const T *spec, T *eo, int batch, Op op, int lpt, int bc,
                                       cudaStream_t s)
 {
+    if (!seeds_ok(pv)) return cudaErrorInvalidValue;
     // default shape: 2 pairs per thread, up to 4 fields per CTA
     if (lpt <= 0) lpt = 2;
     if (bc <= 0) bc = pick_bc(batch);
@@ -754,6 +796,7 @@ template <typename T>
 cudaError_t launch_legendre_analys_cfg(const PlanView<T> &pv, const T *sd, T *spec, int batch, Op op, int lpt, int bc,
                                        cudaStream_t s)
 {
+    if (!seeds_ok(pv)) return cudaErrorInvalidValue;
     // default shape: LPT from the pair count (<= 8 warps), 2 fields per CTA when batched
     if (lpt <= 0) lpt = analys_lpt(pv.npairs);
     if (bc <= 0) bc = batch >= 2 ? 2 : 1;
@@ -774,6 +817,7 @@ template <typename T>
 cudaError_t launch_legendre_synth_vec(const PlanView<T> &pv, const T *S, const T *Tc, T *eot, T *eop, int batch,
                                       Op op, cudaStream_t s)
 {
+    if (!seeds_ok(pv)) return cudaErrorInvalidValue;
     if (batch >= 2) return synth_vec_go<T, 1, 2>(pv, S, Tc, eot, eop, batch, op, s);
     return synth_vec_go<T, 1, 1>(pv, S, Tc, eot, eop, batch, op, s);
 }
@@ -782,6 +826,7 @@ template <typename T>
 cudaError_t launch_legendre_analys_vec(const PlanView<T> &pv, const T *sdt, const T *sdp, T *S, T *Tc, int batch,
                                        Op op, cudaStream_t s)
 {
+    if (!seeds_ok(pv)) return cudaErrorInvalidValue;
     switch (analys_lpt(pv.npairs)) {
     case 2: return analys_vec_go<T, 2, 1>(pv, sdt, sdp, S, Tc, batch, op, s);
     case 4: return analys_vec_go<T, 4, 1>(pv, sdt, sdp, S, Tc, batch, op, s);
@@ -837,6 +882,72 @@ cudaError_t launch_batch_legendre(bool synth, const BatchField *fields, const in
 {
     if (synth) k_batch_synth<<<ctas, 128, 0, s>>>(fields, tiles, ntiles, counter);
     else k_batch_analys<<<ctas, 256, 0, s>>>(fields, tiles, ntiles, counter);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Restart states of the FP32 recurrence.  One thread per (order index m,
+// pair): the FP64 recurrence of Sec. 3.2 from P_m^m, carried as y 2^(-240 k)
+// (Sec. 3.5), and at the start of every kSeedSeg-degree segment the state
+// (y1, y2) = (P_{n0-1}, P_{n0-2}) rewritten in the FP32 form y' 2^(-64 k'):
+// k' = 0 when the larger of the two is at least 2^-63, else the k' that
+// brings it into [2^-65, 1) -- the form in which the FP32 kernels carry it.
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ float4 fp32_state(double y1, double y2, int k)
+{
+    const double mx = fmax(fabs(y1), fabs(y2));
+    if (mx == 0.0) return make_float4(0.f, 0.f, __int_as_float(0), 0.f);
+    int ex = 0;
+    frexp(mx, &ex);
+    const long E = (long)ex - (long)Scale<double>::S * k;   // the larger value < 2^E
+    constexpr int S32 = Scale<float>::S;
+    long k32 = 0;
+    if (E < 1 - S32) k32 = (-E) / S32;
+    const int sh = (int)(-(long)Scale<double>::S * k + (long)S32 * k32);
+    return make_float4((float)scalbn(y1, sh), (float)scalbn(y2, sh), __int_as_float((int)k32), 0.f);
+}
+
+__global__ void __launch_bounds__(128)
+k_build_seeds32(PlanView<double> pv, const unsigned long long *__restrict__ segoff, float4 *__restrict__ seeds)
+{
+    const int m = blockIdx.y;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int npairs = pv.npairs;
+    if (p >= npairs) return;
+    const int L = pv.lmax - m * pv.mres + 1;
+    const int nseg = (L + kSeedSeg - 1) / kSeedSeg;
+    const long col = col_of_mres(pv.lmax, m, pv.mres);
+    const double x = pv.x[p];
+    double y1 = 0.0, y2 = pv.pmm[(size_t)m * npairs + p];
+    int k = pv.pmmk[(size_t)m * npairs + p];
+    for (int s = 0; s < nseg; ++s) {
+        seeds[(segoff[m] + s) * npairs + p] = fp32_state(y1, y2, k);
+        for (int i = 0; i < kSeedSeg; ++i) {
+            const int nn = kSeedSeg * s + i;
+            if (nn >= L) break;
+            const double2 ab = pv.ab[col + nn];
+            const double yn = fma(ab.x * x, y1, ab.y * y2);
+            y2 = y1;
+            y1 = yn;
+            if (k > 0 && fabs(yn) >= 1.0) {
+                y1 *= down_scale<double>();
+                y2 *= down_scale<double>();
+                k -= 1;
+            }
+        }
+    }
+}
+
+
+}  // namespace
+
+cudaError_t launch_build_seeds32(const PlanView<double> &pv, const unsigned long long *segoff, float4 *seeds,
+                                 cudaStream_t st)
+{
+    dim3 grid((unsigned)((pv.npairs + 127) / 128), (unsigned)(pv.mmax + 1));
+    k_build_seeds32<<<grid, 128, 0, st>>>(pv, segoff, seeds);
     return cudaGetLastError();
 }
 

@@ -93,14 +93,16 @@ size_t padded(size_t count) { return (count * sizeof(U) + 255) & ~size_t(255); }
 PlanView<double> Plan::view64() const
 {
     PlanView<double> v{lmax, mmax, nlat, nphi, npairs, nlm,
-                       t64.ab, t64.dc, t64.x, t64.st, t64.wq, t64.pmm, t64.pmmk, t64.tw, t64.rtw, fft_plan_of(nphi / 2), mres, twdf};
+                       t64.ab, t64.dc, t64.x, t64.st, t64.wq, t64.pmm, t64.pmmk, t64.tw, t64.rtw, fft_plan_of(nphi / 2), mres, twdf,
+                       nullptr, nullptr};
     return v;
 }
 
 PlanView<float> Plan::view32() const
 {
     PlanView<float> v{lmax, mmax, nlat, nphi, npairs, nlm,
-                      t32.ab, t32.dc, t32.x, t32.st, t32.wq, t32.pmm, t32.pmmk, t32.tw, t32.rtw, fft_plan_of(nphi / 2), mres, nullptr};
+                      t32.ab, t32.dc, t32.x, t32.st, t32.wq, t32.pmm, t32.pmmk, t32.tw, t32.rtw, fft_plan_of(nphi / 2), mres, nullptr,
+                      seeds32, d_seg32};
     return v;
 }
 
@@ -279,8 +281,53 @@ int plan_build(Plan &p, std::string &err)
     return 0;
 }
 
+size_t seed_segment_offsets(int lmax, int mmax, int mres, std::vector<unsigned long long> &segoff)
+{
+    segoff.assign(mmax + 1, 0);
+    unsigned long long s = 0;
+    for (int m = 0; m <= mmax; ++m) {
+        segoff[m] = s;
+        s += (unsigned long long)((lmax - m * mres + 1 + kSeedSeg - 1) / kSeedSeg);
+    }
+    return (size_t)s;
+}
+
+int plan_seeds32(Plan &p, std::string &err)
+{
+    if (p.seeds32) return SHT_OK;
+    std::vector<unsigned long long> segoff;
+    const size_t nseg = seed_segment_offsets(p.lmax, p.mmax, p.mres, segoff);
+    cudaError_t e = cudaMalloc(&p.seeds32, sizeof(float4) * nseg * (size_t)p.npairs);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_seg32, sizeof(unsigned long long) * segoff.size());
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p.seeds32);
+        cudaFree(p.d_seg32);
+        p.seeds32 = nullptr;
+        p.d_seg32 = nullptr;
+        err = std::string("cudaMalloc(FP32 recurrence seeds): ") + cudaGetErrorString(e);
+        return SHT_ENOMEM;
+    }
+    e = cudaMemcpy(p.d_seg32, segoff.data(), sizeof(unsigned long long) * segoff.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_build_seeds32(p.view64(), p.d_seg32, p.seeds32, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) {
+        cudaFree(p.seeds32);
+        cudaFree(p.d_seg32);
+        p.seeds32 = nullptr;
+        p.d_seg32 = nullptr;
+        err = std::string("building FP32 recurrence seeds: ") + cudaGetErrorString(e);
+        return SHT_ECUDA;
+    }
+    return SHT_OK;
+}
+
 void plan_free(Plan &p)
 {
+    cudaFree(p.seeds32);
+    cudaFree(p.d_seg32);
+    p.seeds32 = nullptr;
+    p.d_seg32 = nullptr;
     for (cudaEvent_t e : p.timer.pool) cudaEventDestroy(e);
     p.timer.pool.clear();
     if (p.tables_base) cudaFree(p.tables_base);

@@ -60,7 +60,17 @@ struct PlanView {
     unsigned long long fftplan;   // radices of the FFT of length nphi/2 (fft_plan_of)
     int mres;                     // order stride: order index k is the order m = k mres
     const float4 *twdf;           // FP64 plans: tw as double-float pairs (re.hi, re.lo, im.hi, im.lo)
+    // FP32 plans: restart states of the recurrence (see kSeedSeg), [segment][npairs]
+    // float4 (y1, y2, k as int bits, 0), segments of order index m from segoff[m].
+    const float4 *seeds;
+    const unsigned long long *segoff;
 };
+
+// The FP32 Legendre kernels restart the recurrence of Sec. 3.2 every kSeedSeg
+// degrees from the state (P_{n0-1}, P_{n0-2}) computed by the FP64 recurrence,
+// carried in the exponent-scaled form of Sec. 3.5 (y * 2^(-64 k)), so that
+// FP32 rounding errors accumulate over at most kSeedSeg steps.
+constexpr int kSeedSeg = 32;
 
 // First packed index of order index k (order m = k mres): the degrees of the
 // orders before it, sum_{k' < k} (lmax - k' mres + 1).
@@ -146,6 +156,8 @@ struct Plan {
     unsigned long long *d_segoff = nullptr;     // first segment of each order
     int *d_c0o_s = nullptr, *d_c0o_a = nullptr; // on-the-fly mode: first live chunk per (m, tile)
     int otf_state = 0;                          // 0 not built, 1 built, -1 not supported for this plan
+    float4 *seeds32 = nullptr;                  // FP32 recurrence restart states (kSeedSeg), built on first use
+    unsigned long long *d_seg32 = nullptr;      // ... first segment of each order index
     double otf_skip_s = 0, otf_skip_a = 0;      // on-the-fly mode: fraction of chunks skipped
     void *work = nullptr;            // scratch (grown on demand)
     size_t work_bytes = 0;
@@ -160,6 +172,14 @@ struct Plan {
 // Host plan construction (plan.cpp).
 int plan_build(Plan &p, std::string &err);
 void plan_free(Plan &p);
+// Builds the FP32 recurrence restart states of a plan once (16 B per pair
+// and kSeedSeg degrees: (lmax+1)^2 npairs / 4 bytes, 138 MB at lmax = 1023);
+// SHT status, message in err.
+int plan_seeds32(Plan &p, std::string &err);
+// Segment offsets of kSeedSeg degrees per order index; returns the total.
+size_t seed_segment_offsets(int lmax, int mmax, int mres, std::vector<unsigned long long> &segoff);
+cudaError_t launch_build_seeds32(const PlanView<double> &pv, const unsigned long long *segoff, float4 *seeds,
+                                 cudaStream_t st);
 
 // Launchers (legendre.cu, fft.cu).  `eo` / `sd` are intermediate buffers of
 // [batch][mmax+1][npairs][2] complex values of precision T.

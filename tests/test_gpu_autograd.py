@@ -108,3 +108,45 @@ def test_dot_product_identities_on_gpu(SHT, prec):
     lhs = sdot(sht.analys_(g), a)
     rhs = float((g.double() * sht.analys_adj_(a).double()).sum())
     assert abs(lhs - rhs) <= tol * max(1.0, abs(lhs))
+
+
+def test_config5_loss_gradient_n1023_b16_tensor_cores(SHT):
+    """The differentiable workload at its own size and precision: loss =
+    ||synth(a) - target||^2 at N = 1023 (1024 x 2048 grid), batch 16, on the
+    split-bf16 tensor-core path.  The gradient from the adjoint kernels against
+    2 synth^T(synth(a) - target) of the oracle, on sampled orders of three
+    fields, within the bound derived from the split-bf16 arithmetic of both
+    the synthesis and its adjoint; and against a directional central
+    difference, which for this quadratic loss is exact for any step, so a
+    step of 1 keeps the FP32 rounding of the loss small against the signal."""
+    import _bounds as B
+    lmax, nlat, nphi, batch = 1023, 1024, 2048, 16
+    sht = SHT(lmax, lmax, nlat, nphi, fp32_path="tc")
+    a0 = synthetic.spectrum(lmax, batch=batch, seed=2).astype(np.complex64).astype(np.complex128)
+    tgt = synthetic.grid(nlat, nphi, batch=batch, seed=2).astype(np.float32).astype(np.float64)
+    a = torch.from_numpy(a0.astype(np.complex64)).to(DEV).requires_grad_(True)
+    t = torch.from_numpy(tgt.astype(np.float32)).to(DEV)
+    loss = ((sht.synth(a) - t) ** 2).sum()
+    loss.backward()
+    g = a.grad.detach().cpu().numpy().astype(np.complex128)
+    ms = [0, 1, 64, 500, 1023]
+    sig = B.product_sigma("tc", lmax)
+    ns_, ms_ = synthetic.packed_degrees_orders(lmax)
+    sel = np.isin(ms_, ms)
+    for b in (0, 7, 15):
+        resid = oracle.synth(lmax, lmax, nlat, nphi, a0[b]) - tgt[b]
+        ref = 2 * oracle.synth_adj(lmax, lmax, nlat, nphi, resid, ms=ms)
+        bnd = B.loss_grad_bounds(lmax, nlat, nphi, a0[b], resid, sig, ms, sigma_rep=B.data_sigma("tc"))
+        B.check(g[b][sel], ref[sel], bnd[sel], f"config-5 gradient field {b}")
+    d = synthetic.spectrum(lmax, batch=batch, seed=9).astype(np.complex64)
+
+    def L(x):
+        with torch.no_grad():
+            r = sht.synth(torch.from_numpy(x).to(DEV)).double() - t.double()
+            return float((r * r).sum())
+    fd = (L(a0.astype(np.complex64) + d) - L(a0.astype(np.complex64) - d)) / 2.0
+    an = float(np.sum(g.real * d.real + g.imag * d.imag))
+    # rounding noise of either side is ~1e-5 of the signal (split-bf16 errors
+    # of ~1e-5 relative summed with random signs); 1e-3 leaves a wide margin
+    # while a wrong factor, sign or missing term fails
+    assert abs(fd - an) < 1e-3 * abs(an), (fd, an)

@@ -9,7 +9,8 @@ import pytest
 import oracle
 from paper_1202_6522_gb300 import synthetic
 
-from _util import fp64_bound, normwise, tc_bound
+import _bounds as B
+from _util import fp64_bound, normwise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -50,17 +51,18 @@ def test_n2047_tensor_core_sampled(SHT):
     g = sht.synth_(torch.from_numpy(a).to(DEV)).cpu().numpy()
     rows = [0, 3, 1000, 2047]
     for b in range(2):
-        ref = oracle.synth(N, N, NLAT, NPHI, a[b].astype(np.complex128), rows=rows)
-        assert normwise(g[b][rows], ref[rows]) < tc_bound(N)
+        B.assert_synth(g[b], a[b].astype(np.complex128), N, N, NLAT, NPHI, "tc", rows=rows,
+                       what=f"tc synth N2047 field {b}")
 
 
 def test_n4095_fp64_and_fp32_sampled(SHT):
     """N = 4095 (nlat 4096, nphi 8192): P_m^m spans ~13000 decimal orders of
     magnitude near the poles.  FP64 rows against the oracle and the round-trip
     error (the paper's 1e-11 statement covers N < 2048 only; bounded here by
-    1e-10); the FP32 path (rescaling with S = 64) within the FP32 bound for the
-    round trip and for rows away from the poles."""
-    from _util import fp32_bound
+    1e-10).  The FP32 path (exponent scale S = 64, recurrence restarted every 32
+    degrees) on rows at the poles and the equator and on sampled orders of its
+    analysis, within the bounds derived from its arithmetic -- the restarts
+    keep the error from growing with N."""
     n, nlat, nphi = 4095, 4096, 8192
     sht = SHT(n, n, nlat, nphi)
     Q = synthetic.spectrum(n, seed=0, uniform=True)
@@ -73,15 +75,32 @@ def test_n4095_fp64_and_fp32_sampled(SHT):
     emax, erms = oracle.eps_max_rms(R, Q, n)
     assert emax < 1e-10 and erms < 1e-11, (emax, erms)
     del g
-    Q32 = Q.astype(np.complex64)
-    g32 = sht.synth_(torch.from_numpy(Q32).to(DEV))
-    R32 = sht.analys_(g32).cpu().numpy()
-    emax32, _ = oracle.eps_max_rms(R32, Q32.astype(np.complex128), n)
-    assert emax32 < fp32_bound(n), emax32
-    # rows away from the poles; at the polemost rows the FP32 recurrence's
-    # rounding errors are amplified ~linearly over the N steps (the recurrence
-    # has a nearly double root there) and reach ~2e-2 normwise at this N
-    g32 = g32.cpu().numpy()
-    mid = [1023, 2047, 3072]
-    ref32 = oracle.synth(n, n, nlat, nphi, Q32.astype(np.complex128), rows=mid)
-    assert normwise(g32[mid], ref32[mid]) < fp32_bound(n)
+    Q32 = Q.astype(np.complex64).astype(np.complex128)
+    g32 = sht.synth_(torch.from_numpy(Q32.astype(np.complex64)).to(DEV))
+    G32 = g32.cpu().numpy()
+    rows32 = [0, 1, 700, 2047, 4095]
+    B.assert_synth(G32, Q32, n, n, nlat, nphi, "f32", rows=rows32, what="f32 synth N4095")
+    grid32 = synthetic.grid(nlat, nphi, seed=5).astype(np.float32).astype(np.float64)
+    S32 = sht.analys_(torch.from_numpy(grid32.astype(np.float32)).to(DEV)).cpu().numpy()
+    B.assert_analys(S32, grid32, n, n, nlat, nphi, "f32", ms_sel=[0, 1, 2000, 4095], what="f32 analys N4095")
+
+
+def test_n4095_tensor_core_sampled(SHT):
+    """Tensor-core panels at N = 4095 (about 69 GB per direction): sampled rows
+    of the synthesis and sampled orders of the analysis within the bound of
+    the split-bf16 arithmetic (the panels come from the FP64 recurrence with
+    the rescaling of Sec. 3.5, so the bound does not grow with N)."""
+    n, nlat, nphi = 4095, 4096, 8192
+    sht = SHT(n, n, nlat, nphi, fp32_path="tc")
+    a = synthetic.spectrum(n, batch=2, seed=3).astype(np.complex64)
+    g = sht.synth_(torch.from_numpy(a).to(DEV)).cpu().numpy()
+    rows = [0, 1, 1500, 2047, 4095]
+    for b in range(2):
+        B.assert_synth(g[b], a[b].astype(np.complex128), n, n, nlat, nphi, "tc", rows=rows,
+                       what=f"tc synth N4095 field {b}")
+    grid = synthetic.grid(nlat, nphi, batch=2, seed=4).astype(np.float32)
+    S = sht.analys_(torch.from_numpy(grid).to(DEV)).cpu().numpy()
+    for b in range(2):
+        B.assert_analys(S[b], grid[b].astype(np.float64), n, n, nlat, nphi, "tc", ms_sel=[0, 2, 3000, 4095],
+                        what=f"tc analys N4095 field {b}")
+    assert sht.sync_status() == 0

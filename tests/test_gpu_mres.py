@@ -12,7 +12,8 @@ import pytest
 import oracle
 from paper_1202_6522_gb300 import synthetic
 
-from _util import fp32_bound, fp64_bound, normwise, tc_bound
+import _bounds as B
+from _util import fp64_bound, normwise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -68,15 +69,25 @@ def test_mres_scalar(SHT, case, path):
     a[:, : lmax + 1] = a[:, : lmax + 1].real          # order 0 is real
     g = synthetic.grid(nlat, nphi, batch=batch, seed=3)
     cdt, fdt = (np.complex128, np.float64) if path in ("f64", "tc64") else (np.complex64, np.float32)
-    bound = {"f64": fp64_bound, "tc64": fp64_bound, "f32": fp32_bound, "tc": tc_bound, "otf": tc_bound}[path](lmax)
     a = a.astype(cdt)
     g = g.astype(fdt)
+    full = _spread(a.astype(np.complex128), lmax, mmax, mres)
+    tiled = np.tile(g.astype(np.float64), (1, 1, mres))
+    idx = _strided_index(lmax, mmax, mres)
     got = _np(sht.synth_(torch.from_numpy(a).to(DEV)))
-    ref = oracle.synth(lmax, mmax * mres, nlat, nphi * mres, _spread(a.astype(np.complex128), lmax, mmax, mres))
-    assert normwise(got, ref[..., :nphi]) < bound
-    got = _np(sht.analys_(torch.from_numpy(g).to(DEV)))
-    ref = oracle.analys(lmax, mmax * mres, nlat, nphi * mres, np.tile(g.astype(np.float64), (1, 1, mres)))
-    assert normwise(got, ref[..., _strided_index(lmax, mmax, mres)]) < bound
+    ref = oracle.synth(lmax, mmax * mres, nlat, nphi * mres, full)
+    gota = _np(sht.analys_(torch.from_numpy(g).to(DEV)))
+    refa = oracle.analys(lmax, mmax * mres, nlat, nphi * mres, tiled)
+    if path in ("f64", "tc64"):
+        assert normwise(got, ref[..., :nphi]) < fp64_bound(lmax)
+        assert normwise(gota, refa[..., idx]) < fp64_bound(lmax)
+        return
+    # the bounds of the full-circle transform the oracle computes
+    sig = B.product_sigma(path, lmax)
+    bnd = B.synth_row_bounds(lmax, mmax * mres, nlat, nphi * mres, full, sig)
+    B.check(got, ref[..., :nphi], bnd[:, :, None], f"{path} mres{mres} synth")
+    bnd = B.analys_coeff_bounds(lmax, mmax * mres, nlat, nphi * mres, tiled, sig)
+    B.check(gota, refa[..., idx], bnd[:, idx], f"{path} mres{mres} analys")
 
 
 @pytest.mark.parametrize("path", ["f64", "tc"])
@@ -92,19 +103,27 @@ def test_mres_vector_and_adjoint(SHT, path):
                               _spread(T, lmax, mmax, mres))
     if path == "tc":
         # the tensor-core vector path (FP32 data); its analysis against the oracle's
-        vt, vp = sht.synth_vec_(torch.from_numpy(S.astype(np.complex64)).to(DEV),
-                                torch.from_numpy(T.astype(np.complex64)).to(DEV))
-        assert normwise(_np(vt), rt[..., :nphi]) < tc_bound(lmax)
-        assert normwise(_np(vp), rp[..., :nphi]) < tc_bound(lmax)
-        gt = synthetic.grid(nlat, nphi, batch=batch, seed=12)
-        gp = synthetic.grid(nlat, nphi, batch=batch, seed=13)
+        S32 = S.astype(np.complex64)
+        T32 = T.astype(np.complex64)
+        rt, rp = oracle.synth_vec(lmax, mmax * mres, nlat, nphi * mres, _spread(S32.astype(np.complex128), lmax, mmax, mres),
+                                  _spread(T32.astype(np.complex128), lmax, mmax, mres))
+        vt, vp = sht.synth_vec_(torch.from_numpy(S32).to(DEV), torch.from_numpy(T32).to(DEV))
+        sig = B.product_sigma("tc", lmax)
+        bt, bp = B.synth_vec_row_bounds(lmax, mmax * mres, nlat, nphi * mres,
+                                        _spread(S32.astype(np.complex128), lmax, mmax, mres),
+                                        _spread(T32.astype(np.complex128), lmax, mmax, mres), sig)
+        B.check(_np(vt), rt[..., :nphi], bt[:, :, None], "tc mres vector theta")
+        B.check(_np(vp), rp[..., :nphi], bp[:, :, None], "tc mres vector phi")
+        gt = synthetic.grid(nlat, nphi, batch=batch, seed=12).astype(np.float32).astype(np.float64)
+        gp = synthetic.grid(nlat, nphi, batch=batch, seed=13).astype(np.float32).astype(np.float64)
         Sg, Tg = sht.analys_vec_(torch.from_numpy(gt.astype(np.float32)).to(DEV),
                                  torch.from_numpy(gp.astype(np.float32)).to(DEV))
-        rS, rT = oracle.analys_vec(lmax, mmax * mres, nlat, nphi * mres, np.tile(gt, (1, 1, mres)),
-                                   np.tile(gp, (1, 1, mres)))
+        tt, tp = np.tile(gt, (1, 1, mres)), np.tile(gp, (1, 1, mres))
+        rS, rT = oracle.analys_vec(lmax, mmax * mres, nlat, nphi * mres, tt, tp)
         idx = _strided_index(lmax, mmax, mres)
-        assert normwise(_np(Sg), rS[..., idx]) < tc_bound(lmax)
-        assert normwise(_np(Tg), rT[..., idx]) < tc_bound(lmax)
+        bnd = B.analys_vec_coeff_bounds(lmax, mmax * mres, nlat, nphi * mres, tt, tp, sig)
+        B.check(_np(Sg), rS[..., idx], bnd[:, idx], "tc mres vector S")
+        B.check(_np(Tg), rT[..., idx], bnd[:, idx], "tc mres vector T")
         return
     vt, vp = sht.synth_vec_(torch.from_numpy(S).to(DEV), torch.from_numpy(T).to(DEV))
     assert normwise(_np(vt), rt[..., :nphi]) < fp64_bound(lmax)

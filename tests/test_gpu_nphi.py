@@ -11,7 +11,8 @@ import pytest
 import oracle
 from paper_1202_6522_gb300 import synthetic
 
-from _util import fp32_bound, fp64_bound, normwise, tc_bound
+import _bounds as B
+from _util import fp64_bound, normwise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -51,17 +52,17 @@ def test_fp64_mixed_radix(lib, case):
     assert normwise(got, oracle.analys(lmax, mmax, nlat, nphi, g)) < fp64_bound(lmax)
 
 
-@pytest.mark.parametrize("path,bound", [("f32", fp32_bound), ("tc", tc_bound), ("otf", tc_bound)])
+@pytest.mark.parametrize("path", ["f32", "tc", "otf"])
 @pytest.mark.parametrize("case", CASES[:4], ids=IDS[:4])
-def test_fp32_paths_mixed_radix(lib, case, path, bound):
+def test_fp32_paths_mixed_radix(lib, case, path):
     lmax, mmax, nlat, nphi, batch = case
     sht = lib.SHT(lmax, mmax, nlat, nphi, fp32_path=path)
     a = synthetic.spectrum(lmax, mmax, batch=batch, seed=2).astype(np.complex64)
     got = _np(sht.synth_(torch.from_numpy(a).to(DEV)))
-    assert normwise(got, oracle.synth(lmax, mmax, nlat, nphi, a.astype(np.complex128))) < bound(lmax)
+    B.assert_synth(got, a.astype(np.complex128), lmax, mmax, nlat, nphi, path, what=f"{path} synth nphi{nphi}")
     g = synthetic.grid(nlat, nphi, batch=batch, seed=3).astype(np.float32)
     got = _np(sht.analys_(torch.from_numpy(g).to(DEV)))
-    assert normwise(got, oracle.analys(lmax, mmax, nlat, nphi, g.astype(np.float64))) < bound(lmax)
+    B.assert_analys(got, g.astype(np.float64), lmax, mmax, nlat, nphi, path, what=f"{path} analys nphi{nphi}")
 
 
 def test_fp64_tensor_core_mixed_radix(lib):
@@ -101,8 +102,8 @@ def test_uneven_batch_mixed_radix_matches_per_field(lib):
         ref = lib.SHT(l, l, l + 1, n).synth_(s)
         torch.cuda.synchronize()
         assert torch.equal(g, ref)
-        refo = oracle.synth(l, l, l + 1, n, s.cpu().numpy().astype(np.complex128))
-        assert normwise(g.cpu().numpy(), refo) < fp32_bound(l)
+        B.assert_synth(g.cpu().numpy(), s.cpu().numpy().astype(np.complex128), l, l, l + 1, n, "f32",
+                       what=f"f32 batch synth nphi{n}")
 
 
 def test_unsupported_nphi_refused(lib):

@@ -1,17 +1,19 @@
-"""Parity of the tensor-core mode (SHT_TC_BF16X3) with the FP64 oracle.
+"""Parity of the tensor-core modes (SHT_TC_BF16X3, SHT_TC_OTF) with the FP64 oracle.
 
 The per-order Legendre contraction runs on tcgen05 against P_n^m panels
-built once by the FP64 recurrence; data are FP32.  Cases cover several
-128-row tiles and ragged tails, mmax < lmax, odd nlat, batches split into
-several chunks, the vector transforms, and sampled rows/orders of the full
-N = 1023, batch 16 scalar and N = 511, batch 64 vector workloads."""
+built once by the FP64 recurrence (or generated on the fly in FP32); data are
+FP32.  Every comparison is element by element against the bound derived from
+the split-bf16 arithmetic (tests/_bounds.py).  Cases cover several 128-row
+tiles and ragged tails, mmax < lmax, odd nlat, batches split into several
+chunks, the vector transforms, the adjoints, and sampled rows/orders of the
+full N = 1023, batch 16 scalar and N = 511, batch 64 vector workloads."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_1202_6522_gb300 import synthetic
 
-from _util import normwise, tc_bound
+import _bounds as B
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -60,10 +62,10 @@ def test_tc_synthesis_and_analysis(SHT, case, path):
     sht = SHT(lmax, mmax, nlat, nphi, fp32_path=path)
     a = _spec(lmax, mmax, batch, 0)
     got = _np(sht.synth_(_dev(a)))
-    assert normwise(got, oracle.synth(lmax, mmax, nlat, nphi, a)) < tc_bound(lmax)
+    B.assert_synth(got, a, lmax, mmax, nlat, nphi, path, what=f"{path} synth N{lmax}b{batch}")
     g = _grid(nlat, nphi, batch, 1)
     got = _np(sht.analys_(_dev(g)))
-    assert normwise(got, oracle.analys(lmax, mmax, nlat, nphi, g)) < tc_bound(lmax)
+    B.assert_analys(got, g, lmax, mmax, nlat, nphi, path, what=f"{path} analys N{lmax}b{batch}")
     assert sht.sync_status() == 0
 
 
@@ -74,8 +76,8 @@ def test_tc_adjoints(SHT, case, path):
     sht = SHT(lmax, mmax, nlat, nphi, fp32_path=path)
     g = _grid(nlat, nphi, batch, 2)
     a = _spec(lmax, mmax, batch, 3)
-    assert normwise(_np(sht.synth_adj_(_dev(g))), oracle.synth_adj(lmax, mmax, nlat, nphi, g)) < tc_bound(lmax)
-    assert normwise(_np(sht.analys_adj_(_dev(a))), oracle.analys_adj(lmax, mmax, nlat, nphi, a)) < tc_bound(lmax)
+    B.check_scalar_adjoints(_np(sht.synth_adj_(_dev(g))), _np(sht.analys_adj_(_dev(a))), g, a,
+                            lmax, mmax, nlat, nphi, path, path)
 
 
 @pytest.mark.parametrize("path", ["tc", "otf"])
@@ -86,27 +88,53 @@ def test_tc_full_size_n1023_b16_sampled(SHT, path):
     grid = _np(sht.synth_(_dev(a)))
     rows = [0, 1, 127, 128, 511, 512, 900, 1023]
     for b in (0, 9, 15):
-        ref = oracle.synth(lmax, lmax, nlat, nphi, a[b], rows=rows)
-        assert normwise(grid[b][rows], ref[rows]) < tc_bound(lmax), b
+        B.assert_synth(grid[b], a[b], lmax, lmax, nlat, nphi, path, rows=rows,
+                       what=f"{path} synth N1023 field {b}")
     g = _grid(nlat, nphi, batch, 1)
     spec = _np(sht.analys_(_dev(g)))
     ms = [0, 1, 127, 300, 1000, 1023]
-    idx = np.concatenate([[oracle.lm_index(lmax, n, m) for n in range(m, lmax + 1)] for m in ms])
     for b in (0, 15):
-        ref = oracle.analys(lmax, lmax, nlat, nphi, g[b], ms=ms)
-        assert normwise(spec[b][idx], ref[idx]) < tc_bound(lmax), b
+        B.assert_analys(spec[b], g[b], lmax, lmax, nlat, nphi, path, ms_sel=ms,
+                        what=f"{path} analys N1023 field {b}")
+    assert sht.sync_status() == 0
+
+
+@pytest.mark.parametrize("path", ["tc", "otf"])
+def test_tc_adjoints_full_size_n1023_b16_sampled(SHT, path):
+    """The adjoints at the full differentiable workload (N = 1023, batch 16):
+    synth^T on sampled orders, analys^T on sampled rows, of three fields."""
+    lmax, nlat, nphi, batch = 1023, 1024, 2048, 16
+    sht = SHT(lmax, lmax, nlat, nphi, fp32_path=path)
+    g = _grid(nlat, nphi, batch, 2)
+    a = _spec(lmax, lmax, batch, 3)
+    sa = _np(sht.synth_adj_(_dev(g)))
+    aa = _np(sht.analys_adj_(_dev(a)))
+    rows = [0, 2, 255, 511, 512, 1023]
+    ms = [0, 1, 200, 777, 1023]
+    for b in (0, 8, 15):
+        B.check_scalar_adjoints(sa[b], aa[b], g[b], a[b], lmax, lmax, nlat, nphi, path,
+                                f"{path} field {b}", rows=rows, ms_sel=ms)
     assert sht.sync_status() == 0
 
 
 @pytest.mark.parametrize("path", ["tc", "otf"])
 def test_tc_round_trip_error_n1023(SHT, path):
-    """Sec. 3.5 error measures for the tensor-core round trip (stated, bounded)."""
+    """Sec. 3.5 error measures of the tensor-core round trip of uniform spectra:
+    per coefficient on sampled orders within the bound derived from the
+    arithmetic of both directions; eps_max and eps_rms over all coefficients
+    stated."""
     lmax = 1023
     sht = SHT(lmax, lmax, 1024, 2048, fp32_path=path)
-    Q = synthetic.spectrum(lmax, seed=0, uniform=True).astype(np.complex64)
-    R = _np(sht.analys_(sht.synth_(torch.from_numpy(Q).to(DEV))))
-    emax, erms = oracle.eps_max_rms(R, Q.astype(np.complex128), lmax)
-    assert emax < 4 * tc_bound(lmax) and erms < tc_bound(lmax)
+    Q = synthetic.spectrum(lmax, seed=0, uniform=True).astype(np.complex64).astype(np.complex128)
+    R = _np(sht.analys_(sht.synth_(torch.from_numpy(Q.astype(np.complex64)).to(DEV))))
+    ms = [0, 1, 10, 100, 511, 1000, 1023]
+    ns_, ms_ = synthetic.packed_degrees_orders(lmax)
+    sel = np.isin(ms_, ms)
+    sig = B.product_sigma(path, lmax)
+    bnd = B.round_trip_bounds(lmax, 1024, 2048, Q, sig, sig, ms, sigma_rep=B.data_sigma(path))
+    B.check(R[sel], Q[sel], bnd[sel], f"{path} round trip N1023")
+    emax, erms = oracle.eps_max_rms(R, Q, lmax)
+    assert np.isfinite(emax) and erms <= emax
 
 
 @pytest.mark.parametrize("path", ["tc", "otf"])
@@ -138,14 +166,12 @@ def test_tc_vector_synthesis_and_analysis(SHT, case):
     T = synthetic.spectrum(lmax, mmax, batch=batch, seed=5, power=1.5).astype(np.complex64).astype(np.complex128)
     vt, vp = sht.synth_vec_(_dev(S), _dev(T))
     rt, rp = oracle.synth_vec(lmax, mmax, nlat, nphi, S, T)
-    assert normwise(_np(vt), rt) < tc_bound(lmax)
-    assert normwise(_np(vp), rp) < tc_bound(lmax)
     gt = _grid(nlat, nphi, batch, 6)
     gp = _grid(nlat, nphi, batch, 7)
     S2, T2 = sht.analys_vec_(_dev(gt), _dev(gp))
     rS, rT = oracle.analys_vec(lmax, mmax, nlat, nphi, gt, gp)
-    assert normwise(_np(S2), rS) < tc_bound(lmax)
-    assert normwise(_np(T2), rT) < tc_bound(lmax)
+    B.check_vector(_np(vt), _np(vp), rt, rp, S, T, _np(S2), _np(T2), rS, rT, gt, gp, lmax, mmax, nlat, nphi,
+                   "tc", f"tc N{lmax}b{batch}")
     assert sht.sync_status() == 0
 
 
@@ -157,14 +183,12 @@ def test_tc_vector_adjoints(SHT, case):
     gp = _grid(nlat, nphi, batch, 9)
     S, T = sht.synth_vec_adj_(_dev(gt), _dev(gp))
     rS, rT = oracle.synth_vec_adj(lmax, mmax, nlat, nphi, gt, gp)
-    assert normwise(_np(S), rS) < tc_bound(lmax)
-    assert normwise(_np(T), rT) < tc_bound(lmax)
     A = _spec(lmax, mmax, batch, 10)
-    B = _spec(lmax, mmax, batch, 11)
-    ht, hp = sht.analys_vec_adj_(_dev(A), _dev(B))
-    rt, rp = oracle.analys_vec_adj(lmax, mmax, nlat, nphi, A, B)
-    assert normwise(_np(ht), rt) < tc_bound(lmax)
-    assert normwise(_np(hp), rp) < tc_bound(lmax)
+    Bs = _spec(lmax, mmax, batch, 11)
+    ht, hp = sht.analys_vec_adj_(_dev(A), _dev(Bs))
+    rt, rp = oracle.analys_vec_adj(lmax, mmax, nlat, nphi, A, Bs)
+    B.check_vector_adjoints(_np(S), _np(T), rS, rT, gt, gp, _np(ht), _np(hp), rt, rp, A, Bs,
+                            lmax, mmax, nlat, nphi, "tc", f"tc N{lmax}")
 
 
 def test_tc_vector_full_size_n511_b64_sampled(SHT):
@@ -176,21 +200,17 @@ def test_tc_vector_full_size_n511_b64_sampled(SHT):
     T = synthetic.spectrum(lmax, batch=batch, seed=5, power=1.5).astype(np.complex64).astype(np.complex128)
     vt, vp = sht.synth_vec_(_dev(S), _dev(T))
     vt, vp = _np(vt), _np(vp)
-    rows = [0, 1, 127, 255, 256, 400, 511]
-    for b in (0, 33, 63):
-        rt, rp = oracle.synth_vec(lmax, lmax, nlat, nphi, S[b], T[b], rows=rows)
-        assert normwise(vt[b][rows], rt[rows]) < tc_bound(lmax), b
-        assert normwise(vp[b][rows], rp[rows]) < tc_bound(lmax), b
     gt = _grid(nlat, nphi, batch, 6)
     gp = _grid(nlat, nphi, batch, 7)
     S2, T2 = sht.analys_vec_(_dev(gt), _dev(gp))
     S2, T2 = _np(S2), _np(T2)
+    rows = [0, 1, 127, 255, 256, 400, 511]
     ms = [0, 1, 200, 510, 511]
-    idx = np.concatenate([[oracle.lm_index(lmax, n, m) for n in range(m, lmax + 1)] for m in ms])
-    for b in (0, 40):
+    for b in (0, 33, 63):
+        rt, rp = oracle.synth_vec(lmax, lmax, nlat, nphi, S[b], T[b], rows=rows)
         rS, rT = oracle.analys_vec(lmax, lmax, nlat, nphi, gt[b], gp[b], ms=ms)
-        assert normwise(S2[b][idx], rS[idx]) < tc_bound(lmax), b
-        assert normwise(T2[b][idx], rT[idx]) < tc_bound(lmax), b
+        B.check_vector(vt[b], vp[b], rt, rp, S[b], T[b], S2[b], T2[b], rS, rT, gt[b], gp[b],
+                       lmax, lmax, nlat, nphi, "tc", f"tc vector N511 field {b}", rows=rows, ms_sel=ms)
     assert sht.sync_status() == 0
 
 
@@ -200,7 +220,10 @@ def test_tc_static_polar_skip_fraction(SHT):
     from paper_1202_6522_gb300 import _capi as C
     sht = SHT(1023, 1023, 1024, 2048, fp32_path="tc")
     assert C.sht_tc_polar_skip(sht._h) == (-1.0, -1.0)
-    sht.synth_(_dev(_spec(1023, 1023, 1, 0)))
+    a = _spec(1023, 1023, 1, 0)
+    g = _np(sht.synth_(_dev(a)))
+    rows = [0, 5, 40, 300]
+    B.assert_synth(g, a, 1023, 1023, 1024, 2048, "tc", rows=rows, what="tc polar-skip synth N1023")
     fs, fa = C.sht_tc_polar_skip(sht._h)
     assert 0.02 < fs < 0.5 and 0.02 < fa < 0.5, (fs, fa)
 
@@ -213,17 +236,35 @@ def test_tc_polar_threshold_api(SHT):
     sht = SHT(lmax, lmax, nlat, nphi, fp32_path="tc")
     a = _spec(lmax, lmax, 2, 7)
     ref = oracle.synth(lmax, lmax, nlat, nphi, a)
-    assert normwise(_np(sht.synth_(_dev(a))), ref) < tc_bound(lmax)
+
+    def syn(what):
+        B.assert_synth(_np(sht.synth_(_dev(a))), a, lmax, lmax, nlat, nphi, "tc", ref=ref, what=what)
+    syn("tc polar default")
     fs0, fa0 = C.sht_tc_polar_skip(sht._h)
     C.sht_set_polar_threshold(sht._h, 0.0)
     assert C.sht_tc_polar_skip(sht._h) == (0.0, 0.0)
-    assert normwise(_np(sht.synth_(_dev(a))), ref) < tc_bound(lmax)
+    syn("tc polar 0")
+    # 2^-20 drops terms up to 2^-20 |P| -- above the split's rounding, so the
+    # derived bound is widened by the dropped terms (at most 2^-20 each)
     C.sht_set_polar_threshold(sht._h, 2.0 ** -20)
     fs1, fa1 = C.sht_tc_polar_skip(sht._h)
     assert fs1 >= fs0 and fa1 >= fa0 and fa1 > 0
-    assert normwise(_np(sht.synth_(_dev(a))), ref) < tc_bound(lmax)
+    got = _np(sht.synth_(_dev(a)))
+    ns, ms = synthetic.packed_degrees_orders(lmax)
+    cm = np.where(ms == 0, 1.0, 2.0)
+    # dropped terms: |P| < 2^-20 each, random signs through the coefficients
+    drop = B.LAMBDA * 2.0 ** -20 * np.sqrt(np.sum((cm * np.abs(a)) ** 2, axis=-1))
+    bnd = B.synth_row_bounds(lmax, lmax, nlat, nphi, a, B.product_sigma("tc", lmax))
+    B.check(got, ref, bnd[:, :, None] + drop[:, None, None], "tc polar 2^-20")
     g = _grid(nlat, nphi, 2, 8)
-    assert normwise(_np(sht.analys_(_dev(g))), oracle.analys(lmax, lmax, nlat, nphi, g)) < tc_bound(lmax)
+    got = _np(sht.analys_(_dev(g)))
+    ref_a = oracle.analys(lmax, lmax, nlat, nphi, g)
+    bnd = B.analys_coeff_bounds(lmax, lmax, nlat, nphi, g, B.product_sigma("tc", lmax))
+    _, w = oracle.gauss(nlat)
+    F = (2 * np.pi / nphi) * np.fft.rfft(g, axis=-1)[..., : lmax + 1]          # [b, nlat, m]
+    dm = B.LAMBDA * 2.0 ** -20 * np.sqrt(np.sum((w[None, :, None] * np.abs(F)) ** 2, axis=1))
+    dropa = dm[:, ms]
+    B.check(got, ref_a, bnd + dropa, "tc polar 2^-20 analysis")
     for bad in (-1.0, 2.0, float("nan")):
         with pytest.raises((C.SHTError, ValueError)):
             C.sht_set_polar_threshold(sht._h, bad)
@@ -242,15 +283,19 @@ def test_otf_polar_threshold_and_skip(SHT):
     lmax, nlat, nphi = 511, 512, 1024
     sht = SHT(lmax, lmax, nlat, nphi, fp32_path="otf")
     a = _spec(lmax, lmax, 2, 9)
-    ref = oracle.synth(lmax, lmax, nlat, nphi, a)
-    assert normwise(_np(sht.synth_(_dev(a))), ref) < tc_bound(lmax)
+    rows = [0, 3, 100, 255]
+    ref = oracle.synth(lmax, lmax, nlat, nphi, a, rows=rows)
+    B.assert_synth(_np(sht.synth_(_dev(a))), a, lmax, lmax, nlat, nphi, "otf", rows=rows, ref=ref,
+                   what="otf polar default")
     fs, fa = C.sht_tc_polar_skip(sht._h)
     assert 0.0 < fs < 0.5 and 0.0 < fa < 0.5, (fs, fa)
     C.sht_set_polar_threshold(sht._h, 0.0)
     assert C.sht_tc_polar_skip(sht._h) == (0.0, 0.0)
-    assert normwise(_np(sht.synth_(_dev(a))), ref) < tc_bound(lmax)
+    B.assert_synth(_np(sht.synth_(_dev(a))), a, lmax, lmax, nlat, nphi, "otf", rows=rows, ref=ref,
+                   what="otf polar 0")
     g = _grid(nlat, nphi, 2, 10)
-    assert normwise(_np(sht.analys_(_dev(g))), oracle.analys(lmax, lmax, nlat, nphi, g)) < tc_bound(lmax)
+    ms = [0, 7, 300, 511]
+    B.assert_analys(_np(sht.analys_(_dev(g))), g, lmax, lmax, nlat, nphi, "otf", ms_sel=ms, what="otf polar 0 analys")
 
 
 def test_otf_vector_runs_panels(SHT):
@@ -260,4 +305,6 @@ def test_otf_vector_runs_panels(SHT):
     S = synthetic.spectrum(lmax, 20, batch=2, seed=4, power=1.5).astype(np.complex64).astype(np.complex128)
     vt, vp = sht.synth_vec_(_dev(S), _dev(S))
     rt, rp = oracle.synth_vec(lmax, 20, nlat, nphi, S, S)
-    assert normwise(_np(vt), rt) < tc_bound(lmax) and normwise(_np(vp), rp) < tc_bound(lmax)
+    bt, bp = B.synth_vec_row_bounds(lmax, 20, nlat, nphi, S, S, B.product_sigma("tc", lmax))
+    B.check(_np(vt), rt, bt[:, :, None], "otf vector on panels theta")
+    B.check(_np(vp), rp, bp[:, :, None], "otf vector on panels phi")

@@ -7,7 +7,8 @@ import pytest
 import oracle
 from paper_1202_6522_gb300 import synthetic
 
-from _util import fp32_bound, fp64_bound, normwise, tc_bound
+import _bounds as B
+from _util import fp64_bound, normwise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -37,11 +38,15 @@ def test_tuned_shapes_keep_results(lib, prec):
         a = a.astype(np.complex64).astype(np.complex128)
     g = sht.synth_(torch.from_numpy(a).to(DEV, cdt))
     ref = oracle.synth(lmax, lmax, nlat, nphi, a)
-    tol = fp64_bound(lmax) if prec == "f64" else fp32_bound(lmax)
-    assert normwise(g.cpu().numpy(), ref) < tol
     r = sht.analys_(g)
-    refa = oracle.analys(lmax, lmax, nlat, nphi, g.cpu().numpy().astype(np.float64))
-    assert normwise(r.cpu().numpy(), refa) < tol
+    gn = g.cpu().numpy().astype(np.float64)
+    refa = oracle.analys(lmax, lmax, nlat, nphi, gn)
+    if prec == "f64":
+        assert normwise(g.cpu().numpy(), ref) < fp64_bound(lmax)
+        assert normwise(r.cpu().numpy(), refa) < fp64_bound(lmax)
+    else:
+        B.assert_synth(g.cpu().numpy(), a, lmax, lmax, nlat, nphi, "f32", ref=ref, what="tuned f32 synth")
+        B.assert_analys(r.cpu().numpy(), gn, lmax, lmax, nlat, nphi, "f32", ref=refa, what="tuned f32 analys")
 
 
 def test_auto_mode_chooses_a_path(lib):
@@ -53,5 +58,6 @@ def test_auto_mode_chooses_a_path(lib):
     sht.fp32_mode = C.SHT_F32_AUTO
     a = synthetic.spectrum(lmax, batch=batch, seed=4).astype(np.complex64)
     g = sht.synth_(torch.from_numpy(a).to(DEV))
-    ref = oracle.synth(lmax, lmax, nlat, nphi, a.astype(np.complex128))
-    assert normwise(g.cpu().numpy(), ref) < max(fp32_bound(lmax), tc_bound(lmax))
+    chosen = min((f32_ms, "f32"), (tc_ms, "tc"), (otf_ms, "otf"))[1]
+    B.assert_synth(g.cpu().numpy(), a.astype(np.complex128), lmax, lmax, nlat, nphi, chosen,
+                   what=f"auto ({chosen}) synth")
