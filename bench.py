@@ -7,21 +7,36 @@ N = 1023 (nlat = 1024, nphi = 2048), batch 16, inputs resident in HBM.  The
 metric is round trips per second (fields x steps / time), with nominal
 GFLOP/s; the plain FP64 path is timed on the same workload for the ratio.
 
+The headline path (default --mode tc_f64) is the batched tensor-core form at
+the paper's FP64 accuracy (digit-sliced contraction, double-float FFTs).  The
+same line carries, as first-class secondary results, the split-bf16
+tensor-core path (key "bf16x3"), the plain FP64 and FP32 paths, the other
+workloads of the study (N = 511, the vector transform, the uneven batch, the
+differentiable form, high N, the polar threshold sweep, accuracy versus N), and
+the FP64 CPU oracle on the host cores (cpu_baseline), which after its timing
+also measures the errors of sampled GPU outputs of each workload against the
+oracle ("eps_vs_oracle" of each entry).
+
 Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas
 (each rank transforms its own batch, no collective): weak scaling.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode auto|tc|f32|f64] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode tc_f64|tc|otf|f32|f64|auto]
+                  [--impl ours|reference] [--no-extras] [--no-cpu-baseline]
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
+import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -32,6 +47,14 @@ LMAX, NLAT, NPHI, BATCH = 1023, 1024, 2048, 16
 WORKLOAD = f"scalar SHT round trip N={LMAX} nlat={NLAT} nphi={NPHI} batch={BATCH}"
 METRIC = "SHT round-trips/s (N=1023, batch 16)"
 UNIT = "round-trips/s"
+E2E_MIN_SECONDS = 1.0
+
+
+def bench_config(world):
+    """The workload, identical for this implementation's arm and the reference arm."""
+    return {"workload": WORKLOAD, "lmax": LMAX, "nlat": NLAT, "nphi": NPHI, "batch": BATCH,
+            "l2": "inputs larger than L2 (spectra + grids > 129 MB), no flush needed",
+            "parallelism": f"replicas x{world}"}
 
 
 def nlm_of(lmax, mmax=None):
@@ -80,23 +103,11 @@ def tc_algorithmic_bytes(batch, lmax=LMAX, nlat=NLAT, polar_skip=0.0):
     return panel + spec + inter
 
 
-# DRAM bytes (read + write) per launch of the panel contraction at this
-# workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum);
-# reported only while the source file holding the kernel is unchanged (its
-# SHA-256 below, updated only for edits outside that kernel), else null.
-TC_TRAFFIC_SRC_SHA256 = "e6f6626ca470714a564579e4c4fb51e0f562544fd10f999c3e9d88e837ea5708"
-TC_TRAFFIC_BYTES = {"tc_synth": 866.161408e6 + 73.604096e6, "tc_analys": 883.199872e6 + 37.287936e6}
-
-
-def tc_traffic(kernel):
-    import hashlib
-    src = os.path.join(ROOT, "paper_1202_6522_gb300", "csrc", "tc.cu")
-    try:
-        with open(src, "rb") as fh:
-            same = hashlib.sha256(fh.read()).hexdigest() == TC_TRAFFIC_SRC_SHA256
-    except OSError:
-        same = False
-    return TC_TRAFFIC_BYTES.get(kernel) if same else None
+def fft_algorithmic_bytes(batch, lmax=LMAX, nlat=NLAT, nphi=NPHI, elem=4):
+    """Bytes one longitude-FFT launch must move: the grid and the E/O (or s/d)
+    intermediate of the batch, each read or written once."""
+    npairs = (nlat + 1) // 2
+    return batch * (nlat * nphi * elem + (lmax + 1) * npairs * 4 * elem)
 
 
 def fp32_alu_peak(sm_mhz):
@@ -105,6 +116,35 @@ def fp32_alu_peak(sm_mhz):
 
 
 FP64_PEAK_NOMINAL = 1.25e12  # GB300 FP64 rate (nominal table of the pool)
+
+
+# ---------------------------------------------------------------------------
+# DRAM traffic of a kernel, from a committed ncu summary under profiles/: the
+# summary names the kernel's source file and its SHA-256 at capture time; the
+# figure is reported only while the source file is unchanged, else null.
+def profiled_traffic(kernel):
+    prof = os.path.join(ROOT, "profiles")
+    try:
+        names = sorted(os.listdir(prof))
+    except OSError:
+        return None
+    for name in names:
+        if not name.endswith(".md"):
+            continue
+        with open(os.path.join(prof, name)) as fh:
+            text = fh.read()
+        for m in re.finditer(r"^traffic: kernel=(\S+) source=(\S+) sha256=([0-9a-f]{64}) bytes_per_launch=([0-9.e+]+)",
+                             text, re.M):
+            if m.group(1) != kernel:
+                continue
+            try:
+                with open(os.path.join(ROOT, m.group(2)), "rb") as sf:
+                    if hashlib.sha256(sf.read()).hexdigest() != m.group(3):
+                        return None
+            except OSError:
+                return None
+            return float(m.group(4))
+    return None
 
 
 # ---------------------------------------------------------------------------
@@ -118,39 +158,86 @@ def read_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """SM clock and clock-event reasons during a timed region.  A background
+    thread reads them through NVML (libnvidia-ml, part of the driver) every
+    2 ms; where NVML cannot be loaded, nvidia-smi samples every 100 ms."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+    SMI_FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, uuid=None):
+    def __init__(self, uuid=None, period=0.002):
         self.uuid = uuid
-        self.proc = None
-        self.path = None
+        self.period = period
+        self.samples = []
+        self.smax = None
+        self._stop = threading.Event()
+        self._thread = None
+        self._proc = None
+        self._path = None
+        self._nvml = None
+        self._dev = None
+
+    def _nvml_open(self):
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        dev = ctypes.c_void_p()
+        if not self.uuid or lib.nvmlDeviceGetHandleByUUID(self.uuid.encode(), ctypes.byref(dev)) != 0:
+            raise RuntimeError("no NVML handle for the device")
+        mx = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(dev, 1, ctypes.byref(mx)) == 0:
+            self.smax = float(mx.value)
+        self._nvml, self._dev = lib, dev
+
+    def _loop(self):
+        lib, dev = self._nvml, self._dev
+        reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(dev, 1, ctypes.byref(clk)) == 0 and reasons_fn(dev, ctypes.byref(rs)) == 0:
+                self.samples.append((float(clk.value), int(rs.value)))
+            time.sleep(self.period)
 
     def start(self):
         try:
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            self._nvml_open()
+            self._thread = threading.Thread(target=self._loop, daemon=True)
+            self._thread.start()
+            return
+        except Exception:
+            self._nvml = None
+        try:
+            fd, self._path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
-            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+            cmd = ["nvidia-smi", f"--query-gpu={self.SMI_FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
             if self.uuid:
                 cmd += ["-i", self.uuid]
-            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            self._proc = subprocess.Popen(cmd, stdout=open(self._path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
-            self.proc = None
+            self._proc = None
 
     def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join(timeout=5)
+            sm = [c for c, _ in self.samples]
+            reasons = sorted({name for _, r in self.samples for bit, name in self.REASONS.items() if r & bit})
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.smax,
+                    "samples": len(sm), "source": "NVML every 2 ms", "reasons": reasons}
+        if self._proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "samples": 0, "reasons": ["no clock source"]}
+        self._proc.terminate()
         try:
-            self.proc.wait(timeout=5)
+            self._proc.wait(timeout=5)
         except Exception:
-            self.proc.kill()
+            self._proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        with open(self.path) as fh:
+        with open(self._path) as fh:
             for line in fh:
                 parts = [p.strip() for p in line.split(",")]
                 if len(parts) < 8:
@@ -163,10 +250,9 @@ class ClockSampler:
                 for name, v in zip(names, parts[4:8]):
                     if v.lower() == "active":
                         reasons.add(name)
-        os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+        os.unlink(self._path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "source": "nvidia-smi every 100 ms", "reasons": sorted(reasons)}
 
 
 def job_throughput(ms_local, world, units_per_rank, device=None):
@@ -188,8 +274,19 @@ def dist_setup():
     return world, rank, local
 
 
+def eps_measures(got, ref):
+    """max |got - ref|, rms |got - ref| (Sec. 3.5 measures over the given
+    entries) and max |got - ref| / max |ref| (normwise)."""
+    import numpy as np
+    d = np.abs(np.asarray(got, dtype=np.complex128) - np.asarray(ref, dtype=np.complex128))
+    scale = float(np.abs(ref).max()) or 1.0
+    return {"eps_max": float(d.max()), "eps_rms": float(np.sqrt(np.mean(d * d))), "normwise": float(d.max()) / scale}
+
+
 # ---------------------------------------------------------------------------
-def cpu_baseline(seconds_hint=True):
+# CPU baseline and the oracle checks of sampled GPU outputs
+# ---------------------------------------------------------------------------
+def cpu_baseline():
     """The oracle as it stands, one field round trip at the bench size, on all host cores."""
     import numpy as np
 
@@ -204,6 +301,38 @@ def cpu_baseline(seconds_hint=True):
     assert np.isfinite(r).all()
     return {"value": 1.0 / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
             "sample": f"1 field round trip at N={LMAX} ({dt:.1f} s, direct Fourier sums)"}
+
+
+def oracle_checks(samples):
+    """Errors of sampled GPU outputs against the oracle (run in the CPU
+    baseline leg, after every GPU timing).  Each sample names the transform,
+    its sizes, the input and the GPU output on a subset of rows or orders."""
+    import numpy as np
+
+    import oracle
+    out = {}
+    for key, s in samples.items():
+        kind = s["kind"]
+        L, M, nl, nph = s["lmax"], s.get("mmax", s["lmax"]), s["nlat"], s["nphi"]
+        if kind == "synth":
+            ref = oracle.synth(L, M, nl, nph, s["input"], rows=s["rows"])[s["rows"]]
+        elif kind == "analys":
+            ref = oracle.analys(L, M, nl, nph, s["input"], ms=s["ms"])[s["idx"]]
+        elif kind == "synth_vec":
+            rt, rp = oracle.synth_vec(L, M, nl, nph, s["input"][0], s["input"][1], rows=s["rows"])
+            ref = np.concatenate([rt[s["rows"]].ravel(), rp[s["rows"]].ravel()])
+        elif kind == "analys_vec":
+            rS, rT = oracle.analys_vec(L, M, nl, nph, s["input"][0], s["input"][1], ms=s["ms"])
+            ref = np.concatenate([rS[s["idx"]], rT[s["idx"]]])
+        elif kind == "loss_grad":
+            resid = oracle.synth(L, M, nl, nph, s["input"][0]) - s["input"][1]
+            ref = 2.0 * oracle.synth_adj(L, M, nl, nph, resid, ms=s["ms"])[s["idx"]]
+        else:
+            continue
+        e = eps_measures(np.asarray(s["got"]).ravel(), np.asarray(ref).ravel())
+        e["sample"] = s["what"]
+        out[key] = e
+    return out
 
 
 def oracle_sample_step(oracle, a, stride):
@@ -263,8 +392,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded N(0,1)/(n+1) spectra)",
-        "config": {"workload": WORKLOAD, "lmax": LMAX, "nlat": NLAT, "nphi": NPHI, "batch": BATCH,
-                   "path": "FP64 CPU oracle (direct Legendre and Fourier sums, OpenMP)"},
+        "config": bench_config(world),
+        "path": "FP64 CPU oracle (direct Legendre and Fourier sums, OpenMP over orders)",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -274,16 +403,236 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
-def uneven_batch(torch, dev, replays=200):
+# timed paths
+# ---------------------------------------------------------------------------
+PATHS = {
+    # mode: (dtype label, SHT kwargs, description)
+    "tc_f64": ("f64", {"fp64_path": "tc"},
+               "tcgen05 contraction on 7-bit digit slices (FP64 accuracy), double-float FFTs"),
+    "tc": ("bf16x3 (f32 data, f32 accumulate)", {"fp32_path": "tc"},
+           "tcgen05 split-bf16 contraction vs FP64-built P panels"),
+    "otf": ("bf16x3 (f32 data, f32 accumulate)", {"fp32_path": "otf"},
+            "tcgen05 split-bf16 contraction, P generated on the fly (FP32, restarted every 32 degrees)"),
+    "f32": ("f32", {}, "FP32 on-the-fly recurrence (exponent scale, restarted every 32 degrees)"),
+    "f64": ("f64", {}, "plain FP64 on-the-fly recurrence"),
+    "auto": ("f32 / bf16x3 (tuned)", {}, "runtime-tuned: FP32 on-the-fly, tcgen05 panels or tcgen05 on-the-fly P"),
+}
+
+
+def is_fp64(mode):
+    return mode in ("f64", "tc_f64")
+
+
+def make_plan(mode, dev, lmax=LMAX, nlat=NLAT, nphi=NPHI):
+    from paper_1202_6522_gb300 import SHT
+    return SHT(lmax, lmax, nlat, nphi, device=dev, **PATHS[mode][1])
+
+
+def device_timed(sht, torch, a, steps, warmup, stream, barrier, clocks=False, uuid=None):
+    """W warm-up round trips, then exactly `steps` round trips between CUDA
+    events on the launching stream, bracketed by barrier + synchronize; the
+    per-kernel table from the library's own events; clocks sampled during the
+    timed region.  Returns (ms total, kernel table, clocks)."""
+    from paper_1202_6522_gb300 import _capi as C
+    for _ in range(warmup):
+        sht.analys_(sht.synth_(a))
+    barrier()
+    C.sht_profile(sht._h, True)
+    C.sht_profile_read(sht._h)
+    sampler = ClockSampler(uuid) if clocks else None
+    if sampler:
+        sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(steps):
+        sht.analys_(sht.synth_(a))
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = sampler.stop() if sampler else None
+    table = C.sht_profile_read(sht._h)
+    C.sht_profile(sht._h, False)
+    return ms, table, clk
+
+
+def e2e_timed(sht, torch, dev, a_np, cdt, stream, min_steps, barrier, nbuf=2):
+    """The same round trips end to end through the public API from pinned host
+    memory: every step uploads its own input and downloads its result.
+    Uploads, transforms and downloads run on three streams with nbuf device
+    buffers, so step k+1's upload and step k-1's download overlap step k's
+    transforms.  The pipeline is first filled (nbuf + 2 steps); the timed
+    region then runs at least `min_steps` steps and at least E2E_MIN_SECONDS.
+    Returns (seconds, steps, bytes in, bytes out per step)."""
+    host_in = [torch.from_numpy(a_np).to(cdt).pin_memory() for _ in range(nbuf)]
+    host_out = [torch.empty_like(host_in[0]).pin_memory() for _ in range(nbuf)]
+    d_in = [torch.empty_like(host_in[0], device=dev) for _ in range(nbuf)]
+    s_up, s_down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    up_done = [torch.cuda.Event() for _ in range(nbuf)]
+    comp_done = [torch.cuda.Event() for _ in range(nbuf)]
+    down_done = [torch.cuda.Event() for _ in range(nbuf)]
+
+    def run(n):
+        for k in range(n):
+            i = k % nbuf
+            with torch.cuda.stream(s_up):
+                s_up.wait_event(comp_done[i])          # buffer i no longer read by step k - nbuf
+                d_in[i].copy_(host_in[i], non_blocking=True)
+                up_done[i].record(s_up)
+            d_in[i].record_stream(stream)
+            stream.wait_event(up_done[i])
+            stream.wait_event(down_done[i])            # host_out[i] of step k - nbuf downloaded
+            r = sht.analys_(sht.synth_(d_in[i]))
+            comp_done[i].record(stream)
+            with torch.cuda.stream(s_down):
+                s_down.wait_event(comp_done[i])
+                host_out[i].copy_(r, non_blocking=True)
+                r.record_stream(s_down)                # keep r's memory until the download ran
+                down_done[i].record(s_down)
+
+    run(nbuf + 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run(nbuf + 2)
+    torch.cuda.synchronize()
+    per = (time.perf_counter() - t0) / (nbuf + 2)
+    n = max(min_steps, int(math.ceil(E2E_MIN_SECONDS / max(per, 1e-6))))
+    barrier()
+    t0 = time.perf_counter()
+    run(n)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    b = host_in[0].numel() * host_in[0].element_size()
+    return dt, n, b, b
+
+
+def roofline(mode, sht, table, peaks, alu_peaks, sm_max, batch=BATCH, lmax=LMAX, nlat=NLAT, nphi=NPHI):
+    """Roofline of the dominant kernel kind of a timed region."""
+    from paper_1202_6522_gb300 import _capi as C
+    dom_name, (dom_ms, dom_n) = max(table.items(), key=lambda kv: kv[1][0])
+    dom_avg = dom_ms / dom_n
+    hbm = peaks.get("hbm_gbs", 6800.0) * 1e9
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s"
+    if dom_name.startswith("tc_") and mode == "otf":
+        skip_s, skip_a = C.sht_tc_polar_skip(sht._h)
+        skip = max(0.0, skip_a if dom_name == "tc_analys" else skip_s)
+        flops = nlm_of(lmax) * ((nlat + 1) // 2) * 5.0 * (1.0 - skip)
+        peak = (alu_peaks[0] * 1e12) if alu_peaks else fp32_alu_peak(sm_max)
+        ach = flops / (dom_avg / 1e3)
+        return {"bound": "alu", "kernel": dom_name, "achieved": ach / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_source": "measured FP32 FMA throughput (sht_alu_peaks)" if alu_peaks else "FP32 nominal",
+                "algorithmic_flops": flops, "kernel_avg_ms": dom_avg, "launches": dom_n}
+    if dom_name.startswith("tc_"):
+        skip_s, skip_a = C.sht_tc_polar_skip(sht._h)
+        skip = max(0.0, skip_a if dom_name == "tc_analys" else skip_s)
+        if mode == "tc_f64":
+            algo = tc64_algorithmic_bytes(batch, lmax, nlat, zero_skip=skip)
+            kern = "k_tc64<0>" if dom_name == "tc_analys" else "k_tc64<1>"
+            note = ("digit-data pass + contraction, timed together; bytes: digit panels less the all-zero "
+                    "chunks + FP64 data in and out")
+        else:
+            algo = tc_algorithmic_bytes(batch, lmax, nlat, polar_skip=skip)
+            kern = "k_tc_ws<0>" if dom_name == "tc_analys" else "k_tc_ws<1>"
+            note = "bytes: bf16 hi+lo panels less the polar skip + FP32 data in and out"
+        ach = algo / (dom_avg / 1e3)
+        return {"bound": "hbm", "kernel": dom_name, "achieved": ach / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": profiled_traffic(kern) if (lmax, batch) == (LMAX, BATCH) else None,
+                "peak_source": hbm_src, "algorithmic_bytes": algo, "kernel_avg_ms": dom_avg, "launches": dom_n,
+                "skip": {"synth": skip_s, "analys": skip_a}, "note": note}
+    if dom_name.startswith("fft") and not is_fp64(mode):
+        algo = fft_algorithmic_bytes(batch, lmax, nlat, nphi, 4)
+        ach = algo / (dom_avg / 1e3)
+        return {"bound": "hbm", "kernel": dom_name, "achieved": ach / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": hbm_src, "algorithmic_bytes": algo,
+                "kernel_avg_ms": dom_avg, "launches": dom_n}
+    flops = legendre_flops_per_launch(batch, lmax, nlat) if dom_name.startswith("legendre") else \
+        batch * nlat * 2.5 * nphi * math.log2(nphi)
+    if is_fp64(mode) and mode != "tc_f64":
+        peak, src = ((alu_peaks[1] * 1e12, "measured FP64 FMA throughput (sht_alu_peaks)") if alu_peaks
+                     else (FP64_PEAK_NOMINAL, "FP64 nominal 1.25 TFLOP/s"))
+    else:
+        peak, src = ((alu_peaks[0] * 1e12, "measured FP32 FMA throughput (sht_alu_peaks)") if alu_peaks
+                     else (fp32_alu_peak(sm_max), "FP32 nominal"))
+    ach = flops / (dom_avg / 1e3)
+    return {"bound": "alu", "kernel": dom_name, "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": None, "peak_source": src, "algorithmic_flops": flops,
+            "kernel_avg_ms": dom_avg, "launches": dom_n}
+
+
+def kernels_per_launch(mode, kind):
+    """Kernels the library launches per profiled call of a kind (the timer
+    brackets each call): the panel contraction converts its operands in-kernel
+    (a separate operand-prep kernel runs first only for a synthesis with an odd
+    coefficient count); the on-the-fly contraction always has a prep kernel;
+    the FP64-accurate synthesis finds the field exponents (fill + reduction)
+    and writes the data digits before its contraction, its analysis FFT fills
+    the exponent words first and its contraction has a digit pass."""
+    if mode == "tc_f64":
+        return {"tc_synth": 4, "tc_analys": 2, "fft_analys": 2}.get(kind, 1)
+    if not kind.startswith("tc_"):
+        return 1
+    if mode == "otf":
+        return 2
+    return 2 if (kind == "tc_synth" and nlm_of(LMAX) % 2) else 1
+
+
+def round_trip_errors(sht, torch, dev, cdt, lmax=LMAX):
+    """Sec. 3.5 error measures of one round trip of uniform [-1, 1] spectra."""
+    import numpy as np
+    from paper_1202_6522_gb300 import synthetic
+    Q = synthetic.spectrum(lmax, seed=0, uniform=True)
+    Qd = torch.from_numpy(Q).to(dev, cdt)
+    R = sht.analys_(sht.synth_(Qd)).cpu().numpy().astype(np.complex128)
+    Qr = Qd.cpu().numpy().astype(np.complex128)
+    d = np.abs(R - Qr)
+    return {"eps_max": float(d.max()), "eps_rms": float(np.sqrt(2.0 / ((lmax + 1) * (lmax + 2)) * np.sum(d * d)))}
+
+
+def collect_samples(key, sht, torch, dev, cdt, samples, lmax=LMAX, nlat=NLAT, nphi=NPHI, seed=0):
+    """GPU outputs on sampled rows (synthesis) and orders (analysis) of one
+    field, stored for the oracle check of the CPU baseline leg."""
+    import numpy as np
+    from paper_1202_6522_gb300 import synthetic
+    a = synthetic.spectrum(lmax, seed=seed)
+    if cdt == torch.complex64:
+        a = a.astype(np.complex64).astype(np.complex128)
+    rows = [0, 1, nlat // 4, nlat // 2 - 1, nlat - 1]
+    g = sht.synth_(torch.from_numpy(a).to(dev, cdt)).cpu().numpy().astype(np.float64)
+    samples[key + "_synth"] = {"kind": "synth", "lmax": lmax, "nlat": nlat, "nphi": nphi, "input": a, "rows": rows,
+                               "got": g[rows], "what": f"synthesis, 1 field, rows {rows}"}
+    grid = synthetic.grid(nlat, nphi, seed=seed + 1)
+    if cdt == torch.complex64:
+        grid = grid.astype(np.float32).astype(np.float64)
+    rdt = torch.float64 if cdt == torch.complex128 else torch.float32
+    s = sht.analys_(torch.from_numpy(grid).to(dev, rdt)).cpu().numpy().astype(np.complex128)
+    ms = [0, 1, lmax // 3, lmax]
+    idx = packed_index(lmax, ms)
+    samples[key + "_analys"] = {"kind": "analys", "lmax": lmax, "nlat": nlat, "nphi": nphi, "input": grid, "ms": ms,
+                                "idx": idx, "got": s[idx], "what": f"analysis, 1 field, orders {ms}"}
+
+
+def packed_index(lmax, ms):
+    import numpy as np
+    return np.concatenate([[m * (2 * lmax + 3 - m) // 2 + (n - m) for n in range(m, lmax + 1)] for m in ms])
+
+
+# ---------------------------------------------------------------------------
+# the other workloads of the study
+# ---------------------------------------------------------------------------
+def uneven_batch(torch, dev, samples, replays=200):
     """96 FP32 fields with N drawn from {63, 127, 255, 511} (nlat = N+1, nphi =
     2(N+1)): round-trip latency of one graph launch per direction (persistent
     CUDA-core kernels, and the tensor-core mode with one contraction per shape
     group) vs the persistent kernels launched directly vs one launch pair per
     field, and the path the automatic mode picks."""
+    import numpy as np
     from paper_1202_6522_gb300 import SHT, UnevenBatch, synthetic
     lmaxs = synthetic.uneven_truncations(96)
     hist = {str(n): lmaxs.count(n) for n in sorted(set(lmaxs))}
-    specs = [torch.from_numpy(synthetic.spectrum(l, seed=i).astype("complex64")).to(dev) for i, l in enumerate(lmaxs)]
+    specs_np = [synthetic.spectrum(l, seed=i).astype(np.complex64) for i, l in enumerate(lmaxs)]
+    specs = [torch.from_numpy(s).to(dev) for s in specs_np]
     plans = {l: SHT(l, l, l + 1, 2 * (l + 1), device=dev) for l in set(lmaxs)}
     stream = torch.cuda.current_stream(dev)
 
@@ -317,6 +666,20 @@ def uneven_batch(torch, dev, replays=200):
         grids = ub.synth_(specs)
         back = ub.analys_(grids)
         out[name] = measure(lambda: ub.analys_(ub.synth_(specs, out=grids), out=back))
+        if graph:
+            # Sec. 3.5 round trip over all fields, and two fields per path for the oracle check
+            torch.cuda.synchronize()
+            d = np.concatenate([np.abs(b.cpu().numpy().astype(np.complex128) - s.astype(np.complex128))
+                                for b, s in zip(back, specs_np)])
+            out[name]["round_trip_error_sec35"] = {"eps_max": float(d.max()), "eps_rms": float(np.sqrt(np.mean(d * d)))}
+            for i in (0, 95):
+                l = lmaxs[i]
+                rows = [0, l // 2, l]
+                samples[f"uneven_{name}_field{i}"] = {
+                    "kind": "synth", "lmax": l, "nlat": l + 1, "nphi": 2 * (l + 1),
+                    "input": specs_np[i].astype(np.complex128), "rows": rows,
+                    "got": grids[i].cpu().numpy().astype(np.float64)[rows],
+                    "what": f"uneven batch ({name}) synthesis, field {i} (N={l}), rows {rows}"}
         del ub
     auto = UnevenBatch(lmaxs, device=dev, path="auto")
     out["auto"] = {"chosen": auto.path, "tuned_round_trip_ms": auto.tuned_ms}
@@ -325,17 +688,21 @@ def uneven_batch(torch, dev, replays=200):
     return out
 
 
-def vector_config(torch, dev, steps=5):
+def vector_config(torch, dev, samples, steps=5):
     """Spheroidal/toroidal round trip, N = 511 (nlat 512, nphi 1024), 64 shells,
     FP32 data: round trips (shells) per second on the CUDA-core path ("f32")
-    and on the tensor-core path ("tc")."""
+    and on the tensor-core path ("tc"), with the Sec. 3.5 round-trip error and
+    sampled outputs for the oracle check."""
+    import numpy as np
     from paper_1202_6522_gb300 import SHT, synthetic
-    n, shells = 511, 64
-    S = torch.from_numpy(synthetic.spectrum(n, batch=shells, seed=4, power=1.5).astype("complex64")).to(dev)
-    T = torch.from_numpy(synthetic.spectrum(n, batch=shells, seed=5, power=1.5).astype("complex64")).to(dev)
+    n, shells, nlat, nphi = 511, 64, 512, 1024
+    S_np = synthetic.spectrum(n, batch=shells, seed=4, power=1.5).astype(np.complex64)
+    T_np = synthetic.spectrum(n, batch=shells, seed=5, power=1.5).astype(np.complex64)
+    S = torch.from_numpy(S_np).to(dev)
+    T = torch.from_numpy(T_np).to(dev)
     out = {"workload": "vector round trip N=511 nlat=512 nphi=1024, 64 shells, FP32 data"}
     for path in ("f32", "tc"):
-        sht = SHT(n, n, 512, 1024, device=dev, fp32_path=path)
+        sht = SHT(n, n, nlat, nphi, device=dev, fp32_path=path)
         for _ in range(2):
             sht.analys_vec_(*sht.synth_vec_(S, T))
         torch.cuda.synchronize()
@@ -347,18 +714,49 @@ def vector_config(torch, dev, steps=5):
         e1.record()
         e1.synchronize()
         ms = e0.elapsed_time(e1) / steps
-        out[path] = {"ms_per_step": ms, "round_trips_per_s": shells / (ms / 1e3)}
+        # Sec. 3.5 measures of the round trip (n = 0 carries no vector information)
+        vt, vp = sht.synth_vec_(S, T)
+        S2, T2 = sht.analys_vec_(vt, vp)
+        ns, _ = synthetic.packed_degrees_orders(n)
+        keep = ns > 0
+        d = np.concatenate([np.abs(S2.cpu().numpy() - S_np)[:, keep].ravel(),
+                            np.abs(T2.cpu().numpy() - T_np)[:, keep].ravel()]).astype(np.float64)
+        out[path] = {"ms_per_step": ms, "round_trips_per_s": shells / (ms / 1e3),
+                     "round_trip_error_sec35": {"eps_max": float(d.max()), "eps_rms": float(np.sqrt(np.mean(d * d)))}}
+        rows = [0, 127, 255, 511]
+        b = 33
+        samples[f"vector_{path}_synth"] = {
+            "kind": "synth_vec", "lmax": n, "nlat": nlat, "nphi": nphi,
+            "input": (S_np[b].astype(np.complex128), T_np[b].astype(np.complex128)), "rows": rows,
+            "got": np.concatenate([vt[b].cpu().numpy()[rows].ravel(), vp[b].cpu().numpy()[rows].ravel()]),
+            "what": f"vector synthesis ({path}), shell {b}, rows {rows}, v_theta and v_phi"}
+        gt = synthetic.grid(nlat, nphi, seed=6).astype(np.float32)
+        gp = synthetic.grid(nlat, nphi, seed=7).astype(np.float32)
+        S3, T3 = sht.analys_vec_(torch.from_numpy(gt).to(dev)[None], torch.from_numpy(gp).to(dev)[None])
+        ms_ = [0, 1, 200, 511]
+        idx = packed_index(n, ms_)
+        samples[f"vector_{path}_analys"] = {
+            "kind": "analys_vec", "lmax": n, "nlat": nlat, "nphi": nphi,
+            "input": (gt.astype(np.float64), gp.astype(np.float64)), "ms": ms_, "idx": idx,
+            "got": np.concatenate([S3[0].cpu().numpy()[idx], T3[0].cpu().numpy()[idx]]),
+            "what": f"vector analysis ({path}), 1 field, orders {ms_}, S and T"}
         del sht
     return out
 
 
-def differentiable_config(sht, torch, dev, cdt, steps=10):
+def differentiable_config(torch, dev, samples, steps=10):
     """loss = ||synth(a) - target||^2 and its gradient (through the adjoint
-    kernel) at the bench size: forward + backward steps per second x batch."""
+    kernels) at the bench size on the split-bf16 tensor-core path: forward +
+    backward steps per second x batch; the gradient's directional central
+    difference (exact for a quadratic loss at any step) and sampled orders for
+    the oracle check."""
+    import numpy as np
     from paper_1202_6522_gb300 import synthetic
-    a = torch.from_numpy(synthetic.spectrum(LMAX, batch=BATCH, seed=2)).to(dev, cdt).requires_grad_(True)
-    rdt = torch.float64 if cdt == torch.complex128 else torch.float32
-    tgt = torch.from_numpy(synthetic.grid(NLAT, NPHI, batch=BATCH, seed=2)).to(dev, rdt)
+    sht = make_plan("tc", dev)
+    a_np = synthetic.spectrum(LMAX, batch=BATCH, seed=2).astype(np.complex64)
+    t_np = synthetic.grid(NLAT, NPHI, batch=BATCH, seed=2).astype(np.float32)
+    a = torch.from_numpy(a_np).to(dev).requires_grad_(True)
+    tgt = torch.from_numpy(t_np).to(dev)
 
     def step():
         a.grad = None
@@ -377,20 +775,25 @@ def differentiable_config(sht, torch, dev, cdt, steps=10):
     e1.record()
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    return {"workload": f"loss=||synth(a)-target||^2 + gradient, N={LMAX}, batch {BATCH}",
-            "ms_per_step": ms, "fields_per_s": BATCH / (ms / 1e3)}
+    g = a.grad.detach().cpu().numpy().astype(np.complex128)
+    d = synthetic.spectrum(LMAX, batch=BATCH, seed=9).astype(np.complex64)
 
-
-def round_trip_errors(sht, torch, dev, cdt):
-    """Sec. 3.5 error measures of one round trip of uniform [-1, 1] spectra."""
-    import numpy as np
-    from paper_1202_6522_gb300 import synthetic
-    Q = synthetic.spectrum(LMAX, seed=0, uniform=True)
-    Qd = torch.from_numpy(Q).to(dev, cdt)
-    R = sht.analys_(sht.synth_(Qd)).cpu().numpy().astype(np.complex128)
-    Qr = Qd.cpu().numpy().astype(np.complex128)
-    d = np.abs(R - Qr)
-    return {"eps_max": float(d.max()), "eps_rms": float(np.sqrt(2.0 / ((LMAX + 1) * (LMAX + 2)) * np.sum(d * d)))}
+    def L(x):
+        with torch.no_grad():
+            r = sht.synth(torch.from_numpy(x).to(dev)).double() - tgt.double()
+            return float((r * r).sum())
+    fd = (L(a_np + d) - L(a_np - d)) / 2.0
+    an = float(np.sum(g.real * d.real + g.imag * d.imag))
+    ms_ = [0, 1, 64, 500, 1023]
+    idx = packed_index(LMAX, ms_)
+    samples["differentiable_gradient"] = {
+        "kind": "loss_grad", "lmax": LMAX, "nlat": NLAT, "nphi": NPHI,
+        "input": (a_np[0].astype(np.complex128), t_np[0].astype(np.float64)), "ms": ms_, "idx": idx,
+        "got": g[0][idx], "what": f"loss gradient, field 0, orders {ms_}"}
+    del sht
+    return {"workload": f"loss=||synth(a)-target||^2 + gradient, N={LMAX}, batch {BATCH}, split-bf16 tensor cores",
+            "ms_per_step": ms, "fields_per_s": BATCH / (ms / 1e3),
+            "directional_fd": {"fd": fd, "analytic": an, "rel_diff": abs(fd - an) / abs(an)}}
 
 
 def accuracy_vs_n(torch, dev, sizes=(255, 511, 1023, 2047, 4095)):
@@ -399,26 +802,18 @@ def accuracy_vs_n(torch, dev, sizes=(255, 511, 1023, 2047, 4095)):
     recurrence, (N <= 2047) the tensor-core path and (N <= 1023) the
     FP64-accurate tensor-core path: the analogue of the paper's
     error-versus-N study (its 1e-11 target is for N < 2048)."""
-    import numpy as np
-    from paper_1202_6522_gb300 import SHT, synthetic
+    from paper_1202_6522_gb300 import SHT
     out = {}
     for n in sizes:
-        Q = synthetic.spectrum(n, seed=0, uniform=True)
         row = {}
-        for path, cdt, fp32_path in (("f64", torch.complex128, "f32"), ("f32", torch.complex64, "f32"),
-                                     ("tc", torch.complex64, "tc"), ("tc_f64", torch.complex128, "f32")):
+        for path in ("f64", "f32", "tc", "tc_f64"):
             if path == "tc" and n > 2047:
                 continue
             if path == "tc_f64" and n > 1023:
                 continue
-            sht = SHT(n, n, n + 1, 2 * (n + 1), device=dev, fp32_path=fp32_path,
-                      fp64_path="tc" if path == "tc_f64" else "f64")
-            Qd = torch.from_numpy(Q).to(dev, cdt)
-            R = sht.analys_(sht.synth_(Qd)).cpu().numpy().astype(np.complex128)
-            d = np.abs(R - Qd.cpu().numpy().astype(np.complex128))
-            row[path] = {"eps_max": float(d.max()),
-                         "eps_rms": float(np.sqrt(2.0 / ((n + 1) * (n + 2)) * np.sum(d * d)))}
-            del sht, Qd
+            sht = make_plan(path, dev, n, n + 1, 2 * (n + 1))
+            row[path] = round_trip_errors(sht, torch, dev, torch.complex128 if is_fp64(path) else torch.complex64, n)
+            del sht
             torch.cuda.empty_cache()
         out[str(n)] = row
     return out
@@ -426,14 +821,14 @@ def accuracy_vs_n(torch, dev, sizes=(255, 511, 1023, 2047, 4095)):
 
 def n511_config(torch, dev, steps=20):
     """Scalar round trips per second at N = 511 (nlat 512, nphi 1024), batch
-    16, on the three paths (the metric's second size)."""
-    from paper_1202_6522_gb300 import SHT, synthetic
+    16, on every path (the metric's second size)."""
+    import numpy as np
+    from paper_1202_6522_gb300 import synthetic
     out = {"workload": "scalar SHT round trip N=511 nlat=512 nphi=1024 batch=16"}
     a_np = synthetic.spectrum(511, batch=16, seed=0)
-    for path, cdt, fp32_path in (("f64", torch.complex128, "f32"), ("f32", torch.complex64, "f32"),
-                                 ("tc", torch.complex64, "tc")):
-        sht = SHT(511, 511, 512, 1024, device=dev, fp32_path=fp32_path)
-        a = torch.from_numpy(a_np).to(dev, cdt)
+    for path in ("f64", "f32", "tc", "tc_f64"):
+        sht = make_plan(path, dev, 511, 512, 1024)
+        a = torch.from_numpy(a_np).to(dev, torch.complex128 if is_fp64(path) else torch.complex64)
         n = max(3, steps // 5) if path == "f64" else steps
         for _ in range(3):
             sht.analys_(sht.synth_(a))
@@ -446,8 +841,52 @@ def n511_config(torch, dev, steps=20):
         e1.record()
         e1.synchronize()
         ms = e0.elapsed_time(e1) / n
-        out[path] = {"ms_per_step": ms, "round_trips_per_s": 16 / (ms / 1e3)}
+        out[path] = {"ms_per_step": ms, "round_trips_per_s": 16 / (ms / 1e3),
+                     "gflops_nominal": 16 / (ms / 1e3) * nominal_flops_per_rt(511, 512, 1024) / 1e9}
         del sht, a
+    return out
+
+
+def high_n_config(torch, dev, peaks, alu_peaks, sm_max):
+    """Round trips per second, nominal GFLOP/s and the dominant kernel's roofline
+    at N = 2047 (4096 longitudes) and N = 4095 (8192), batch 4, on the FP64,
+    FP32 and tensor-core (panel) paths: the high-degree regime of the paper's
+    Table 1, where the rescaling of Sec. 3.5 is needed."""
+    import numpy as np
+    from paper_1202_6522_gb300 import _capi as C
+    from paper_1202_6522_gb300 import synthetic
+    out = {}
+    batch = 4
+    for n in (2047, 4095):
+        nlat, nphi = n + 1, 2 * (n + 1)
+        a_np = synthetic.spectrum(n, batch=batch, seed=0)
+        row = {"workload": f"scalar SHT round trip N={n} nlat={nlat} nphi={nphi} batch={batch}"}
+        for path in ("f64", "f32", "tc"):
+            sht = make_plan(path, dev, n, nlat, nphi)
+            a = torch.from_numpy(a_np).to(dev, torch.complex128 if is_fp64(path) else torch.complex64)
+            steps = 2 if path == "f64" else 5
+            sht.analys_(sht.synth_(a))
+            torch.cuda.synchronize()
+            C.sht_profile(sht._h, True)
+            C.sht_profile_read(sht._h)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                sht.analys_(sht.synth_(a))
+            e1.record()
+            e1.synchronize()
+            table = C.sht_profile_read(sht._h)
+            C.sht_profile(sht._h, False)
+            ms = e0.elapsed_time(e1) / steps
+            rt = batch / (ms / 1e3)
+            row[path] = {"ms_per_step": ms, "round_trips_per_s": rt,
+                         "gflops_nominal": rt * nominal_flops_per_rt(n, nlat, nphi) / 1e9,
+                         "elements_per_s": rt * (n + 1) ** 3,
+                         "roofline": roofline(path, sht, table, peaks, alu_peaks, sm_max, batch, n, nlat, nphi)}
+            del sht, a
+            torch.cuda.empty_cache()
+        out[str(n)] = row
     return out
 
 
@@ -457,11 +896,10 @@ def polar_sweep(torch, dev, thresholds=(0.0, 2.0 ** -40, 2.0 ** -32, 2.0 ** -26,
     round-trip error (Sec. 3.5 measures, uniform spectra) per threshold, at
     the bench size."""
     import numpy as np
-    from paper_1202_6522_gb300 import SHT, synthetic, _capi as C
-    sht = SHT(LMAX, LMAX, NLAT, NPHI, device=dev, fp32_path="tc")
+    from paper_1202_6522_gb300 import _capi as C
+    from paper_1202_6522_gb300 import synthetic
+    sht = make_plan("tc", dev)
     a = torch.from_numpy(synthetic.spectrum(LMAX, batch=BATCH, seed=0).astype(np.complex64)).to(dev)
-    Q = synthetic.spectrum(LMAX, seed=0, uniform=True).astype(np.complex64)
-    Qd = torch.from_numpy(Q).to(dev)
     out = []
     for thr in thresholds:
         C.sht_set_polar_threshold(sht._h, thr)
@@ -475,45 +913,65 @@ def polar_sweep(torch, dev, thresholds=(0.0, 2.0 ** -40, 2.0 ** -32, 2.0 ** -26,
             sht.analys_(sht.synth_(a))
         e1.record()
         e1.synchronize()
-        R = sht.analys_(sht.synth_(Qd)).cpu().numpy().astype(np.complex128)
-        d = np.abs(R - Q.astype(np.complex128))
         fs, fa = C.sht_tc_polar_skip(sht._h)
-        out.append({"threshold": thr, "ms_per_step": e0.elapsed_time(e1) / steps,
-                    "skip_synth": fs, "skip_analys": fa, "eps_max": float(d.max()),
-                    "eps_rms": float(np.sqrt(2.0 / ((LMAX + 1) * (LMAX + 2)) * np.sum(d * d)))})
+        out.append({"threshold": thr, "ms_per_step": e0.elapsed_time(e1) / steps, "skip_synth": fs,
+                    "skip_analys": fa, **round_trip_errors(sht, torch, dev, torch.complex64)})
+    del sht
     return out
 
 
-def time_path(sht, torch, a, steps, warmup, stream, profile=False):
-    """Device-timed round trips on inputs resident in HBM.  Returns (ms per step, kernel table)."""
-    from paper_1202_6522_gb300 import _capi as C
-    for _ in range(warmup):
-        sht.analys_(sht.synth_(a))
-    torch.cuda.synchronize()
-    if profile:
-        C.sht_profile(sht._h, True)
-        C.sht_profile_read(sht._h)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        sht.analys_(sht.synth_(a))
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    table = None
-    if profile:
-        table = C.sht_profile_read(sht._h)
-        C.sht_profile(sht._h, False)
-    return ms, table
+# ---------------------------------------------------------------------------
+def timed_leg(mode, torch, dev, stream, a_np, steps, warmup, world, barrier, peaks, alu_peaks, uuid, samples,
+              clocks=True, e2e=True):
+    """One path on the bench workload: the device-timed region, its kernel
+    table and roofline, the end-to-end measurement, the Sec. 3.5 round-trip
+    error and sampled outputs for the oracle check."""
+    sht = make_plan(mode, dev)
+    cdt = torch.complex128 if is_fp64(mode) else torch.complex64
+    tune = None
+    if mode == "auto":
+        from paper_1202_6522_gb300 import _capi as C
+        f32_ms, tc_ms, otf_ms = C.sht_tune(sht._h, BATCH, C.SHT_F32_AUTO, stream.cuda_stream)
+        sht.fp32_mode = C.SHT_F32_AUTO
+        cands = {"f32": f32_ms, "tc": tc_ms, "otf": otf_ms}
+        tune = {"f32_round_trip_ms": f32_ms, "tc_round_trip_ms": tc_ms, "tc_otf_round_trip_ms": otf_ms,
+                "chosen": min((v, k) for k, v in cands.items() if v > 0)[1]}
+    a = torch.from_numpy(a_np).to(dev, cdt)
+    ms_total, table, clk = device_timed(sht, torch, a, steps, warmup, stream, barrier, clocks, uuid)
+    ms_total, value = job_throughput(ms_total, world, BATCH * steps, dev)
+    path_used = (tune or {}).get("chosen", mode)
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    res = {"value": value, "unit": UNIT, "ms_per_step": ms_total / steps, "steps": steps, "warmup": warmup,
+           "dtype": PATHS[mode][0], "path": PATHS[mode][2], "path_used": path_used,
+           "gflops_nominal": value * nominal_flops_per_rt() / 1e9, "elements_per_s": value * (LMAX + 1) ** 3,
+           "roofline": roofline(path_used, sht, table, peaks, alu_peaks, sm_max),
+           "kernels": {k: {"avg_ms": v[0] / v[1], "launches": v[1],
+                           "share": v[0] / sum(x[0] for x in table.values())} for k, v in table.items()},
+           "gpu_launches": sum(v[1] * kernels_per_launch(path_used, k) for k, v in table.items())}
+    if clk is not None:
+        res["clocks"] = clk
+    if tune:
+        res["tuning"] = tune
+    if e2e:
+        dt, n, bi, bo = e2e_timed(sht, torch, dev, a_np, cdt, stream, steps, barrier)
+        _, ev = job_throughput(1e3 * dt, world, BATCH * n, dev)
+        res["e2e"] = {"value": ev, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": n,
+                      "seconds": dt, "note": "pinned host buffers, upload/transform/download overlapped across "
+                                             "steps on 3 streams; pipeline filled first, >= 1 s timed"}
+    res["round_trip_error_sec35"] = round_trip_errors(sht, torch, dev, cdt)
+    if samples is not None:
+        collect_samples(mode, sht, torch, dev, cdt, samples)
+    del sht, a
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_ours(args):
-    import numpy as np
     import torch
 
-    from paper_1202_6522_gb300 import SHT, synthetic
+    from paper_1202_6522_gb300 import _capi as C
     from paper_1202_6522_gb300 import build as B
+    from paper_1202_6522_gb300 import synthetic
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -521,31 +979,19 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     B.build()
-    sht = SHT(LMAX, LMAX, NLAT, NPHI, device=dev)
     stream = torch.cuda.current_stream(dev)
-    if args.mode in ("tc", "otf"):
-        sht = SHT(LMAX, LMAX, NLAT, NPHI, device=dev, fp32_path=args.mode)
-    if args.mode == "tc_f64":
-        sht = SHT(LMAX, LMAX, NLAT, NPHI, device=dev, fp64_path="tc")
-    tune_report = None
-    if args.mode == "auto":
-        # runtime tuning before timing: kernel shapes and on-the-fly vs precomputed panels
-        from paper_1202_6522_gb300 import _capi as C
-        f32_ms, tc_ms, otf_ms = C.sht_tune(sht._h, BATCH, C.SHT_F32_AUTO, stream.cuda_stream)
-        sht.fp32_mode = C.SHT_F32_AUTO
-        cands = {"f32": f32_ms, "tc": tc_ms, "tc_otf": otf_ms}
-        tune_report = {"f32_round_trip_ms": f32_ms, "tc_round_trip_ms": tc_ms, "tc_otf_round_trip_ms": otf_ms,
-                       "chosen": min((v, k) for k, v in cands.items() if v > 0)[1]}
-    # measured FMA throughput: the ALU roofline denominators (FP32 and FP64)
-    alu_peaks = None
+    peaks = read_peaks()
     try:
-        from paper_1202_6522_gb300 import _capi as C
-        alu_peaks = C.sht_alu_peaks(stream.cuda_stream)
+        alu_peaks = C.sht_alu_peaks(stream.cuda_stream)   # ALU roofline denominators (FP32, FP64)
     except Exception:
         alu_peaks = None
-    cdt = torch.complex128 if args.mode in ("f64", "tc_f64") else torch.complex64
-    a_np = synthetic.spectrum(LMAX, batch=BATCH, seed=rank)
-    a = torch.from_numpy(a_np).to(dev, cdt)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    extras = rank == 0 and not args.no_extras
+    samples = {} if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
 
     def barrier():
         if world > 1:
@@ -553,238 +999,65 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # accuracy of this run's path against the FP64 oracle on one field
-    r = sht.analys_(sht.synth_(a))
-    torch.cuda.synchronize()
-    a_in = a[0].cpu().numpy().astype(np.complex128)
-    ref_err = float(np.abs(r[0].cpu().numpy().astype(np.complex128) - a_in).max())
+    a_np = synthetic.spectrum(LMAX, batch=BATCH, seed=rank)
+    head = timed_leg(args.mode, torch, dev, stream, a_np, args.steps, args.warmup, world, barrier, peaks,
+                     alu_peaks, uuid, samples)
 
-    # --- device-timed region (max over ranks) ---
-    for _ in range(args.warmup):
-        sht.analys_(sht.synth_(a))
-    barrier()
-    uuid = None
-    try:
-        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        pass
-    clocks = ClockSampler(uuid)
-    clocks.start()
-    from paper_1202_6522_gb300 import _capi as C
-    C.sht_profile(sht._h, True)
-    C.sht_profile_read(sht._h)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    e0.record(stream)
-    for _ in range(args.steps):
-        sht.analys_(sht.synth_(a))
-    e1.record(stream)
-    barrier()
-    ms_total = e0.elapsed_time(e1)
-    table = C.sht_profile_read(sht._h)
-    C.sht_profile(sht._h, False)
-    clk = clocks.stop()
-    ms_total, value = job_throughput(ms_total, world, BATCH * args.steps, dev)
-    ms_step = ms_total / args.steps
+    # --- the other paths on the same workload ---
+    others = {}
+    legs = [m for m in ("tc", "f32", "f64", "tc_f64") if m != args.mode] if extras else \
+        ([] if args.mode == "f64" else ["f64"])
+    for m in legs:
+        k_steps = max(2, args.steps // 4) if m == "f64" else args.steps
+        k_warm = 1 if m == "f64" else args.warmup
+        others[m] = timed_leg(m, torch, dev, stream, a_np, k_steps, k_warm, world, barrier, peaks, alu_peaks, uuid,
+                              samples if m in ("tc",) else None, clocks=m == "tc", e2e=m == "tc")
 
-    # --- end to end through the public API with pinned host buffers ---
-    # Every step uploads its own input from pinned host memory and downloads
-    # its result; uploads, transforms and downloads run on three streams with
-    # double-buffered device tensors, so step k+1's upload and step k-1's
-    # download overlap step k's transforms (as a streaming user would).
-    nbuf = 2
-    host_in = [torch.from_numpy(a_np).to(cdt).pin_memory() for _ in range(nbuf)]
-    host_out = [torch.empty_like(host_in[0]).pin_memory() for _ in range(nbuf)]
-    d_in = [torch.empty_like(host_in[0], device=dev) for _ in range(nbuf)]
-    s_up, s_down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    up_done = [torch.cuda.Event() for _ in range(nbuf)]
-    comp_done = [torch.cuda.Event() for _ in range(nbuf)]
-    down_done = [torch.cuda.Event() for _ in range(nbuf)]
-    d_out = [None] * nbuf
-
-    def e2e_steps(n):
-        for k in range(n):
-            i = k % nbuf
-            with torch.cuda.stream(s_up):
-                s_up.wait_event(comp_done[i])          # buffer i no longer read by step k - nbuf
-                d_in[i].copy_(host_in[i], non_blocking=True)
-                up_done[i].record(s_up)
-            d_in[i].record_stream(stream)
-            stream.wait_event(up_done[i])
-            stream.wait_event(down_done[i])            # d_out[i] of step k - nbuf downloaded
-            r = sht.analys_(sht.synth_(d_in[i]))
-            d_out[i] = r
-            comp_done[i].record(stream)
-            with torch.cuda.stream(s_down):
-                s_down.wait_event(comp_done[i])
-                host_out[i].copy_(r, non_blocking=True)
-                r.record_stream(s_down)                # keep r's memory until the download ran
-                down_done[i].record(s_down)
-
-    e2e_steps(2)
-    barrier()
-    t0 = time.perf_counter()
-    e2e_steps(args.steps)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    bytes_step = host_in[0].numel() * host_in[0].element_size()
-    _, e2e_value = job_throughput(1e3 * e2e_s, world, BATCH * args.steps, dev)
-    e2e = {"value": e2e_value, "unit": UNIT,
-           "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step,
-           "note": "pinned host buffers, upload/transform/download overlapped across steps on 3 streams"}
-
-    errors = round_trip_errors(sht, torch, dev, cdt)
-    ubatch = uneven_batch(torch, dev) if (rank == 0 and not args.no_uneven) else None
     extra = {}
-    if rank == 0 and not args.no_uneven:
-        extra["vector"] = vector_config(torch, dev)
-        extra["differentiable"] = differentiable_config(sht, torch, dev, cdt)
+    if extras:
+        extra["vector"] = vector_config(torch, dev, samples if samples is not None else {})
+        extra["uneven_batch"] = uneven_batch(torch, dev, samples if samples is not None else {})
+        extra["differentiable"] = differentiable_config(torch, dev, samples if samples is not None else {})
         extra["n511"] = n511_config(torch, dev)
+        extra["high_n"] = high_n_config(torch, dev, peaks, alu_peaks, (head.get("clocks") or {}).get("sm_max_mhz") or 2070.0)
         extra["polar_threshold_sweep"] = polar_sweep(torch, dev)
         extra["accuracy_vs_n"] = accuracy_vs_n(torch, dev)
 
-    # --- the plain FP64 path on the same workload (the metric's denominator) ---
-    fp64 = None
-    if args.mode != "f64":
-        a64 = torch.from_numpy(a_np).to(dev, torch.complex128)
-        sht_plain = SHT(LMAX, LMAX, NLAT, NPHI, device=dev) if args.mode == "tc_f64" else sht
-        ms64, tab64 = time_path(sht_plain, torch, a64, max(2, args.steps // 4), 1, stream, profile=True)
-        del a64
-        fp64 = {"round_trips_per_s": world * BATCH / (ms64 / 1e3), "ms_per_step": ms64,
-                "kernels_ms": {k: v[0] / v[1] for k, v in tab64.items()}}
-
-    # --- FP64-accurate tensor-core path (digit slices) on the same workload ---
-    fp64tc = None
-    if args.mode not in ("f64", "tc_f64") and not args.no_uneven:
-        from paper_1202_6522_gb300 import SHT as _SHT
-        sht64 = _SHT(LMAX, LMAX, NLAT, NPHI, fp64_path="tc")
-        a64 = torch.from_numpy(a_np).to(dev, torch.complex128)
-        ms_t, tab_t = time_path(sht64, torch, a64, max(3, args.steps // 10), 2, stream, profile=True)
-        del a64
-        fp64tc = {"workload": WORKLOAD + ", FP64 data", "round_trips_per_s": world * BATCH / (ms_t / 1e3),
-                  "ms_per_step": ms_t, "kernels_ms": {k: v[0] / v[1] for k, v in tab_t.items()},
-                  "round_trip_error_sec35": round_trip_errors(sht64, torch, dev, torch.complex128)}
-        if fp64:
-            fp64tc["speedup_vs_fp64_plain"] = fp64tc["round_trips_per_s"] / fp64["round_trips_per_s"]
-        del sht64
-
     if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
         return 0
-    # dominant kernel and its roofline
-    dom = max(table.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_n) = dom
-    dom_avg = dom_ms / dom_n
-    sm_max = clk.get("sm_max_mhz") or 2070.0
-    path_used = {"auto": (tune_report or {}).get("chosen", "f32"), "otf": "tc_otf"}.get(args.mode, args.mode)
-    fft_flops = BATCH * NLAT * 2.5 * NPHI * math.log2(NPHI)   # one FFT launch, nominal
-    if dom_name.startswith("tc_") and path_used == "tc_otf":
-        # P generated in FP32 on the CUDA cores: 5 flops per (n, m, latitude pair)
-        # (a x, b P_{n-2}, one fma, the seed scale), the tensor-core work aside
-        from paper_1202_6522_gb300 import _capi as C
-        skip_s, skip_a = C.sht_tc_polar_skip(sht._h)
-        skip = max(0.0, skip_a if dom_name == "tc_analys" else skip_s)
-        flops = nlm_of(LMAX) * ((NLAT + 1) // 2) * 5.0 * (1.0 - skip)
-        peak = (alu_peaks[0] * 1e12) if alu_peaks else fp32_alu_peak(sm_max)
-        achieved = flops / (dom_avg / 1e3)
-        roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved / 1e12, "peak": peak / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "measured FP32 FMA throughput (sht_alu_peaks)" if alu_peaks else "FP32 nominal",
-                "algorithmic_flops": flops, "kernel_avg_ms": dom_avg, "launches": dom_n,
-                "polar_skip": {"synth": skip_s, "analys": skip_a}}
-    elif dom_name.startswith("tc_"):
-        # the panels stream from HBM once per launch: bytes bound the kernel
-        from paper_1202_6522_gb300 import _capi as C
-        skip_s, skip_a = C.sht_tc_polar_skip(sht._h)
-        skip = max(0.0, skip_a if dom_name == "tc_analys" else skip_s)
-        algo = (tc64_algorithmic_bytes(BATCH, zero_skip=skip) if path_used == "tc_f64"
-                else tc_algorithmic_bytes(BATCH, polar_skip=skip))
-        peaks = read_peaks()
-        peak = peaks.get("hbm_gbs", 6800.0) * 1e9
-        achieved = algo / (dom_avg / 1e3)
-        roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved / 1e9, "peak": peak / 1e9,
-                "unit": "GB/s", "frac": achieved / peak,
-                "traffic": tc_traffic(dom_name) if path_used == "tc" else None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
-                "algorithmic_bytes": algo, "kernel_avg_ms": dom_avg, "launches": dom_n,
-                "polar_skip": {"synth": skip_s, "analys": skip_a}}
-    else:
-        flops = legendre_flops_per_launch(BATCH) if dom_name.startswith("legendre") else None
-        if dom_name.startswith("fft"):
-            flops = fft_flops
-        if args.mode == "f32":
-            if alu_peaks:
-                peak, peak_note = alu_peaks[0] * 1e12, "measured FP32 FMA throughput (sht_alu_peaks)"
-            else:
-                peak = fp32_alu_peak(sm_max)
-                peak_note = f"FP32 FMA: 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz"
-        else:
-            if alu_peaks:
-                peak, peak_note = alu_peaks[1] * 1e12, "measured FP64 FMA throughput (sht_alu_peaks)"
-            else:
-                peak, peak_note = FP64_PEAK_NOMINAL, "FP64 nominal 1.25 TFLOP/s"
-        achieved = flops / (dom_avg / 1e3) if flops else None
-        roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved / 1e12 if achieved else None,
-                "peak": peak / 1e12, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                "traffic": None, "peak_source": peak_note,
-                "kernel_avg_ms": dom_avg, "launches": dom_n}
-    kernels = {k: {"avg_ms": v[0] / v[1], "launches": v[1], "share": v[0] / sum(x[0] for x in table.values())}
-               for k, v in table.items()}
-    # kernels per profiled launch: the panel contraction converts its operands
-    # in-kernel (a separate operand-prep kernel runs first only for a synthesis
-    # with an odd coefficient count); the on-the-fly contraction always has one
-    def kernels_per(k):
-        if path_used == "tc_f64":
-            # synthesis: field exponents (fill + reduction), data digits, contraction;
-            # analysis: the FFT (after a fill) finds the exponents, then digits and contraction
-            return {"tc_synth": 4, "tc_analys": 2, "fft_analys": 2}.get(k, 1)
-        if not k.startswith("tc_"):
-            return 1
-        if path_used == "tc_otf":
-            return 2
-        return 2 if (k == "tc_synth" and nlm_of(LMAX) % 2) else 1
-    launches = sum(v[1] * kernels_per(k) for k, v in table.items())
+    plain = others.get("f64") if args.mode != "f64" else head
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "tc": "bf16x3 (f32 accumulate)",
-                                       "otf": "bf16x3 (f32 accumulate)",
-                                       "tc_f64": "f64 (bf16 digit slices, exact f32 level sums)",
-                                       "auto": "f32 / bf16x3 (tuned)"}[args.mode],
-        "data": "synthetic (seeded N(0,1)/(n+1) spectra)",
-        "config": {"workload": WORKLOAD, "lmax": LMAX, "nlat": NLAT, "nphi": NPHI, "batch": BATCH,
-                   "path": {"f32": "FP32 on-the-fly recurrence with exponent scale",
-                            "f64": "plain FP64 on-the-fly",
-                            "tc": "tcgen05 split-bf16 contraction vs FP64-built P panels",
-                            "otf": "tcgen05 split-bf16 contraction, P generated on the fly (FP32, reseeded)",
-                            "tc_f64": "tcgen05 contraction on 7-bit digit slices (FP64 accuracy), double-float FFTs",
-                            "auto": "runtime-tuned: FP32 on-the-fly, tcgen05 panels or tcgen05 on-the-fly P"}[args.mode],
-                   "path_used": path_used, "l2": "inputs larger than L2 (spectra+grids > 129 MB)",
-                   "parallelism": f"replicas x{world}"},
-        "gflops_nominal": value * nominal_flops_per_rt() / 1e9,
-        "elements_per_s": value * (LMAX + 1) ** 3,
-        "roofline": roof,
-        "kernels": kernels,
-        "gpu_launches": launches,
-        "clocks": clk,
-        "e2e": e2e,
-        "round_trip_max_err_vs_input": ref_err,
-        "round_trip_error_sec35": errors,
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": head["dtype"], "data": "synthetic (seeded N(0,1)/(n+1) spectra)",
+        "config": bench_config(world), "path": head["path"], "path_used": head["path_used"],
+        "gflops_nominal": head["gflops_nominal"], "elements_per_s": head["elements_per_s"],
+        "roofline": head["roofline"], "kernels": head["kernels"], "gpu_launches": head["gpu_launches"],
+        "clocks": head.get("clocks"), "e2e": head["e2e"], "round_trip_error_sec35": head["round_trip_error_sec35"],
     }
-    if tune_report:
-        line["tuning"] = tune_report
+    if "tuning" in head:
+        line["tuning"] = head["tuning"]
+    if plain is not None:
+        line["speedup_vs_fp64_plain"] = head["value"] / plain["value"]
+    if "tc" in others:
+        line["bf16x3"] = others["tc"]
+    for m, key in (("f64", "fp64_plain"), ("f32", "fp32"), ("tc_f64", "fp64_tensor_core")):
+        if m in others:
+            line[key] = others[m]
+    if plain is not None:
+        for key in ("bf16x3", "fp32", "fp64_tensor_core"):
+            if key in line:
+                line[key]["speedup_vs_fp64_plain"] = line[key]["value"] / plain["value"]
     if alu_peaks:
         line["alu_peaks_measured"] = {"fp32_tflops": alu_peaks[0], "fp64_tflops": alu_peaks[1]}
-    if ubatch:
-        line["uneven_batch"] = ubatch
     line.update(extra)
-    if fp64:
-        line["fp64_plain"] = fp64
-        line["speedup_vs_fp64_plain"] = value / fp64["round_trips_per_s"]
-    if fp64tc:
-        line["fp64_tensor_core"] = fp64tc
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        eps = oracle_checks(samples or {})
+        line["eps_vs_oracle"] = eps
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
@@ -795,12 +1068,13 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["auto", "tc", "otf", "f32", "f64", "tc_f64"], default="auto")
+    ap.add_argument("--mode", choices=list(PATHS), default="tc_f64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch measurement")
+    ap.add_argument("--no-extras", "--no-uneven", dest="no_extras", action="store_true",
+                    help="time the headline path and the plain FP64 path only")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
