@@ -438,3 +438,78 @@ def loss_grad_bounds(lmax, nlat, nphi, a, resid, sigma, ms_sel, sigma_rep=0.0):
             v = v + sigma_rep ** 2 * (M ** 2 @ np.abs(a[idx[cols]]) ** 2)
         prop[idx[cols]] = LAMBDA * cm * nphi * np.sqrt(v)
     return 2.0 * np.sqrt(own ** 2 + prop ** 2)
+
+
+# --------------------------------------------------------------------------
+# composite checks used by several test files
+# --------------------------------------------------------------------------
+def check_scalar_adjoints(got_sa, got_aa, g, a, lmax, mmax, nlat, nphi, path, what, rows=None, ms_sel=None):
+    """synth_adj(g) (orders ms_sel) and analys_adj(a) (grid rows `rows`) of a
+    path against the oracle under the per-element bounds: synth^T is an
+    unweighted analysis times c_m, analys^T the synthesis of a / c_m
+    (imaginary part of order 0 dropped) times (2 pi / nphi) w_j on row j."""
+    sig = product_sigma(path, lmax)
+    g = np.asarray(g, dtype=np.float64)
+    g = g[None] if g.ndim == 2 else g
+    nb = g.shape[0]
+    ns, ms = _orders(lmax, mmax)
+    sel = np.ones(len(ms), dtype=bool) if ms_sel is None else np.isin(ms, np.asarray(ms_sel))
+    ref = oracle.synth_adj(lmax, mmax, nlat, nphi, g, ms=ms_sel).reshape(nb, -1)
+    bnd = synth_adj_coeff_bounds(lmax, mmax, nlat, nphi, g, sig, ms_sel=ms_sel)
+    r1 = check(np.asarray(got_sa).reshape(nb, -1)[:, sel], ref[:, sel], bnd[:, sel], f"{what} synth_adj N{lmax}")
+    a2 = np.atleast_2d(a)
+    ap = np.where(ms == 0, a2.real, a2) / _cm(ms)
+    _, w = oracle.gauss(nlat)
+    rr = list(range(nlat)) if rows is None else list(rows)
+    ref = oracle.analys_adj(lmax, mmax, nlat, nphi, a2, rows=rows).reshape(nb, nlat, nphi)
+    bnd = synth_row_bounds(lmax, mmax, nlat, nphi, ap, sig, rows=rr, row_scale=2 * np.pi / nphi * w)
+    r2 = check(np.asarray(got_aa).reshape(nb, nlat, nphi)[:, rr], ref[:, rr], bnd[:, :, None],
+               f"{what} analys_adj N{lmax}")
+    return max(r1, r2)
+
+
+def check_vector(vt, vp, rt, rp, S, T, S2, T2, rS, rT, gt, gp, lmax, mmax, nlat, nphi, path, what, rows=None,
+                 ms_sel=None):
+    """Vector synthesis (rows) and analysis (orders ms_sel) of a path against
+    the oracle under the per-element bounds."""
+    sig = product_sigma(path, lmax)
+    S, T = np.atleast_2d(S), np.atleast_2d(T)
+    nb = S.shape[0]
+    rr = list(range(nlat)) if rows is None else list(rows)
+    bt, bp = synth_vec_row_bounds(lmax, mmax, nlat, nphi, S, T, sig, rows=rr)
+    shp = (nb, nlat, nphi)
+    check(np.asarray(vt).reshape(shp)[:, rr], np.asarray(rt).reshape(shp)[:, rr], bt[:, :, None],
+          f"{what} synth_vec theta N{lmax}")
+    check(np.asarray(vp).reshape(shp)[:, rr], np.asarray(rp).reshape(shp)[:, rr], bp[:, :, None],
+          f"{what} synth_vec phi N{lmax}")
+    bnd = analys_vec_coeff_bounds(lmax, mmax, nlat, nphi, gt, gp, sig, ms_sel=ms_sel)
+    ns, ms = _orders(lmax, mmax)
+    sel = np.ones(len(ms), dtype=bool) if ms_sel is None else np.isin(ms, ms_sel)
+    check(np.asarray(S2).reshape(nb, -1)[:, sel], np.asarray(rS).reshape(nb, -1)[:, sel], bnd[:, sel],
+          f"{what} analys_vec S N{lmax}")
+    check(np.asarray(T2).reshape(nb, -1)[:, sel], np.asarray(rT).reshape(nb, -1)[:, sel], bnd[:, sel],
+          f"{what} analys_vec T N{lmax}")
+
+
+def check_vector_adjoints(S, T, rS, rT, gt, gp, ht, hp, rt, rp, A, Bs, lmax, mmax, nlat, nphi, path, what):
+    """synth_vec_adj (a weight-free vector analysis times c_m) and
+    analys_vec_adj (the vector synthesis of A, B over c_m n(n+1), times
+    (2 pi / nphi) w_j on row j) under the per-element bounds."""
+    sig = product_sigma(path, lmax)
+    bnd = analys_vec_coeff_bounds(lmax, mmax, nlat, nphi, gt, gp, sig, adjoint=True)
+    nb = bnd.shape[0]
+    check(np.asarray(S).reshape(nb, -1), np.asarray(rS).reshape(nb, -1), bnd, f"{what} synth_vec_adj S N{lmax}")
+    check(np.asarray(T).reshape(nb, -1), np.asarray(rT).reshape(nb, -1), bnd, f"{what} synth_vec_adj T N{lmax}")
+    ns, ms = _orders(lmax, mmax)
+    cm = _cm(ms)
+    nn = ns.astype(np.float64)
+    f = np.where(ns > 0, 1.0 / (cm * np.maximum(nn * (nn + 1), 1.0)), 0.0)
+    A2 = np.where(ms == 0, np.atleast_2d(A).real, np.atleast_2d(A)) * f
+    B2 = np.where(ms == 0, np.atleast_2d(Bs).real, np.atleast_2d(Bs)) * f
+    _, w = oracle.gauss(nlat)
+    bt, bp = synth_vec_row_bounds(lmax, mmax, nlat, nphi, A2, B2, sig, row_scale=2 * np.pi / nphi * w)
+    shp = (nb, nlat, nphi)
+    check(np.asarray(ht).reshape(shp), np.asarray(rt).reshape(shp), bt[:, :, None],
+          f"{what} analys_vec_adj theta N{lmax}")
+    check(np.asarray(hp).reshape(shp), np.asarray(rp).reshape(shp), bp[:, :, None],
+          f"{what} analys_vec_adj phi N{lmax}")
