@@ -38,8 +38,9 @@ template <typename T2> __device__ __forceinline__ T2 mul_i(T2 a) { return mk<T2>
 __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
 
 // Double-float numbers (used by the FFTs of the FP64-accurate tensor-core
-// mode, further down): the unevaluated sum hi + lo of two FP32 numbers with
-// |lo| <= ulp(hi) / 2, after Dekker's double-length arithmetic (1971).
+// mode, further down): the unevaluated sum hi + lo of two FP32 numbers, after
+// Dekker's double-length arithmetic (1971); normalised (|lo| <= ulp(hi) / 2)
+// on the way in and out, possibly not in between (see operator+).
 struct __align__(8) dfl {
     float hi, lo;
     dfl() = default;
@@ -54,13 +55,29 @@ __device__ __forceinline__ dfl fast_two_sum(float a, float b)
     const float s = __fadd_rn(a, b);
     return dfl(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
+// s + e = a + b exactly for any a, b (Knuth)
+__device__ __forceinline__ dfl two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return dfl(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+// The pair as hi + lo with |lo| <= ulp(hi) / 2 (the FFT's operations below
+// leave their results unnormalised; the conversions back to FP64 need this).
+__device__ __forceinline__ dfl renorm(dfl x) { return two_sum(x.hi, x.lo); }
+// The operations leave the pair unnormalised: the error-free sum or product
+// of the high parts and the low-order terms added in FP32, without the final
+// renormalisation, so |lo| can grow to a few units in the last place of hi
+// (or exceed hi after a cancellation).  Each result still equals the exact
+// one up to FP32 rounding of the low-order terms, an error of a few 2^-48
+// times the magnitude of the operands -- the per-operation bound the
+// normwise error analysis of an FFT rests on -- and the operations take the
+// low part of their inputs at full weight, so they accept such pairs.
 __device__ __forceinline__ dfl operator+(dfl x, dfl y)
 {
     // Knuth's error-free sum of the high parts, then the low parts
-    const float s = __fadd_rn(x.hi, y.hi);
-    const float bb = __fsub_rn(s, x.hi);
-    const float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));
-    return fast_two_sum(s, __fadd_rn(e, __fadd_rn(x.lo, y.lo)));
+    const dfl s = two_sum(x.hi, y.hi);
+    return dfl(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
 }
 __device__ __forceinline__ dfl operator-(dfl x) { return dfl(-x.hi, -x.lo); }
 __device__ __forceinline__ dfl operator-(dfl x, dfl y) { return x + (-y); }
@@ -71,7 +88,7 @@ __device__ __forceinline__ dfl operator*(dfl x, dfl y)
     float e = __fmaf_rn(x.hi, y.hi, -p);
     e = __fmaf_rn(x.hi, y.lo, e);
     e = __fmaf_rn(x.lo, y.hi, e);
-    return fast_two_sum(p, e);
+    return dfl(p, e);
 }
 // Complex product in double-float with each component formed as one sum:
 // re = xr wr - xi wi from the two exact high products (FMA errors), one
@@ -80,15 +97,13 @@ __device__ __forceinline__ dfl dot2(dfl a, dfl b, dfl c, dfl d)   // a b + c d
 {
     const float p1 = __fmul_rn(a.hi, b.hi), p2 = __fmul_rn(c.hi, d.hi);
     const float e1 = __fmaf_rn(a.hi, b.hi, -p1), e2 = __fmaf_rn(c.hi, d.hi, -p2);
-    const float s = __fadd_rn(p1, p2);
-    const float bb = __fsub_rn(s, p1);
-    float t = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bb)), __fsub_rn(p2, bb));
-    t = __fadd_rn(t, __fadd_rn(e1, e2));
+    const dfl s = two_sum(p1, p2);
+    float t = __fadd_rn(s.lo, __fadd_rn(e1, e2));
     t = __fmaf_rn(a.hi, b.lo, t);
     t = __fmaf_rn(a.lo, b.hi, t);
     t = __fmaf_rn(c.hi, d.lo, t);
     t = __fmaf_rn(c.lo, d.hi, t);
-    return fast_two_sum(s, t);
+    return dfl(s.hi, t);
 }
 __device__ __forceinline__ dfl2 cmul(dfl2 a, dfl2 b)
 {
@@ -216,7 +231,13 @@ __host__ __device__ inline int row_tpr(int H) { return (H + 15) / 16; }
 // up to ceil(16 / RD) items j = t + it * TPR; item j reads x[j + r H/RD],
 // applies the twiddle W^(r (j mod Ns) H/(Ns RD)), runs the RD-point DFT and
 // writes y[(j / Ns) Ns RD + j mod Ns + r Ns].
-template <typename T2, int RD, int SIGN, int NR>
+// log2 of a power of two
+__device__ __forceinline__ int lg2(int v) { return __popc(v - 1); }
+
+// P2: every length involved is a power of two, so the index arithmetic is
+// masks and shifts (a division by a run-time value is a long instruction
+// sequence on the integer pipe, which the FFT kernels are short of).
+template <typename T2, int RD, int SIGN, int NR, bool P2>
 __device__ __forceinline__ void stockham_load(const T2 *src, bool global_src, int t, int TPR, int H, int Ns,
                                               const T2 *__restrict__ wtab, T2 (&v)[NR])
 {
@@ -232,10 +253,10 @@ __device__ __forceinline__ void stockham_load(const T2 *src, bool global_src, in
             a[r] = global_src ? src[idx] : src[padi(idx)];
         }
         if (Ns > 1) {
-            const int q0 = (j % Ns) * (H / (Ns * RD));
+            const int q0 = P2 ? (j & (Ns - 1)) << (lg2(H) - lg2(Ns) - lg2(RD)) : (j % Ns) * (H / (Ns * RD));
 #pragma unroll
             for (int r = 1; r < RD; ++r) {
-                T2 w = wtab[(r * q0) % H];
+                T2 w = wtab[P2 ? (r * q0) & (H - 1) : (r * q0) % H];
                 if (SIGN < 0) w = conj_(w);
                 a[r] = cmul(a[r], w);
             }
@@ -246,13 +267,14 @@ __device__ __forceinline__ void stockham_load(const T2 *src, bool global_src, in
     }
 }
 
-template <typename T2, int RD>
+template <typename T2, int RD, bool P2>
 __device__ __forceinline__ int stockham_out(int j, int r, int Ns)
 {
+    if (P2) return ((j & ~(Ns - 1)) * RD) + (j & (Ns - 1)) + r * Ns;
     return (j / Ns) * Ns * RD + (j % Ns) + r * Ns;
 }
 
-template <typename T2, int RD, int NR>
+template <typename T2, int RD, int NR, bool P2>
 __device__ __forceinline__ void stockham_store_smem(T2 *row, int t, int TPR, int H, int Ns, const T2 (&v)[NR])
 {
     constexpr int IT = (16 + RD - 1) / RD;
@@ -261,7 +283,7 @@ __device__ __forceinline__ void stockham_store_smem(T2 *row, int t, int TPR, int
         const int j = t + it * TPR;
         if (j >= H / RD) break;
 #pragma unroll
-        for (int r = 0; r < RD; ++r) row[padi(stockham_out<T2, RD>(j, r, Ns))] = v[it * RD + r];
+        for (int r = 0; r < RD; ++r) row[padi(stockham_out<T2, RD, P2>(j, r, Ns))] = v[it * RD + r];
     }
 }
 
@@ -271,13 +293,14 @@ __device__ __forceinline__ void pass_load(int rd, const T2 *src, bool g, int t, 
                                           const T2 *wtab, T2 (&v)[PassRegs<MIXED>::n])
 {
     constexpr int NR = PassRegs<MIXED>::n;
-    if (MIXED && rd == 3) { stockham_load<T2, 3, SIGN, NR>(src, g, t, TPR, H, Ns, wtab, v); return; }
-    if (MIXED && rd == 5) { stockham_load<T2, 5, SIGN, NR>(src, g, t, TPR, H, Ns, wtab, v); return; }
+    constexpr bool P2 = !MIXED;
+    if (MIXED && rd == 3) { stockham_load<T2, 3, SIGN, NR, P2>(src, g, t, TPR, H, Ns, wtab, v); return; }
+    if (MIXED && rd == 5) { stockham_load<T2, 5, SIGN, NR, P2>(src, g, t, TPR, H, Ns, wtab, v); return; }
     switch (rd) {
-    case 2: stockham_load<T2, 2, SIGN, NR>(src, g, t, TPR, H, Ns, wtab, v); break;
-    case 4: stockham_load<T2, 4, SIGN, NR>(src, g, t, TPR, H, Ns, wtab, v); break;
-    case 8: stockham_load<T2, 8, SIGN, NR>(src, g, t, TPR, H, Ns, wtab, v); break;
-    default: stockham_load<T2, 16, SIGN, NR>(src, g, t, TPR, H, Ns, wtab, v); break;
+    case 2: stockham_load<T2, 2, SIGN, NR, P2>(src, g, t, TPR, H, Ns, wtab, v); break;
+    case 4: stockham_load<T2, 4, SIGN, NR, P2>(src, g, t, TPR, H, Ns, wtab, v); break;
+    case 8: stockham_load<T2, 8, SIGN, NR, P2>(src, g, t, TPR, H, Ns, wtab, v); break;
+    default: stockham_load<T2, 16, SIGN, NR, P2>(src, g, t, TPR, H, Ns, wtab, v); break;
     }
 }
 
@@ -286,13 +309,14 @@ __device__ __forceinline__ void pass_store(int rd, T2 *row, int t, int TPR, int 
                                            const T2 (&v)[PassRegs<MIXED>::n])
 {
     constexpr int NR = PassRegs<MIXED>::n;
-    if (MIXED && rd == 3) { stockham_store_smem<T2, 3, NR>(row, t, TPR, H, Ns, v); return; }
-    if (MIXED && rd == 5) { stockham_store_smem<T2, 5, NR>(row, t, TPR, H, Ns, v); return; }
+    constexpr bool P2 = !MIXED;
+    if (MIXED && rd == 3) { stockham_store_smem<T2, 3, NR, P2>(row, t, TPR, H, Ns, v); return; }
+    if (MIXED && rd == 5) { stockham_store_smem<T2, 5, NR, P2>(row, t, TPR, H, Ns, v); return; }
     switch (rd) {
-    case 2: stockham_store_smem<T2, 2, NR>(row, t, TPR, H, Ns, v); break;
-    case 4: stockham_store_smem<T2, 4, NR>(row, t, TPR, H, Ns, v); break;
-    case 8: stockham_store_smem<T2, 8, NR>(row, t, TPR, H, Ns, v); break;
-    default: stockham_store_smem<T2, 16, NR>(row, t, TPR, H, Ns, v); break;
+    case 2: stockham_store_smem<T2, 2, NR, P2>(row, t, TPR, H, Ns, v); break;
+    case 4: stockham_store_smem<T2, 4, NR, P2>(row, t, TPR, H, Ns, v); break;
+    case 8: stockham_store_smem<T2, 8, NR, P2>(row, t, TPR, H, Ns, v); break;
+    default: stockham_store_smem<T2, 16, NR, P2>(row, t, TPR, H, Ns, v); break;
     }
 }
 
@@ -505,7 +529,7 @@ __device__ __forceinline__ void fft_analys_tile(const PlanView<T> &pv, const T *
         for (int h = 0; h < 2; ++h) {
             const T2 *rw = buf + (2 * i + h) * ld;
             const T2 Zk = rw[padi(m)];
-            const T2 Zc = conj_(rw[padi((H - m) % H)]);
+            const T2 Zc = conj_(rw[padi(MIXED ? (H - m) % H : (H - m) & (H - 1))]);
             T2 E = cadd(Zk, Zc), O = csub(Zk, Zc);
             E.x *= T(0.5); E.y *= T(0.5);
             const T2 Od = mk<T2>(O.y * T(0.5), -O.x * T(0.5));  // O / (2i)
@@ -595,6 +619,7 @@ __device__ __forceinline__ dfl2 d2df2(double2 v, int u)
 // 2^-1022 are flushed to zero.
 __device__ __forceinline__ double df2d(dfl z, int u)
 {
+    z = renorm(z);
     const unsigned bh = __float_as_uint(z.hi), bl = __float_as_uint(z.lo);
     const int eh = (int)(bh >> 23) & 0xff, el = (int)(bl >> 23) & 0xff;
     if (eh == 0) return 0.0;
@@ -852,7 +877,7 @@ __device__ __forceinline__ void fft_analys_tile_df(const PlanView<double> &pv, c
         for (int h = 0; h < 2; ++h) {
             const dfl2 *rw = buf + (2 * i + h) * ld;
             const dfl2 Zk = rw[padi(m)];
-            const dfl2 Zc = conj_(rw[padi((H - m) % H)]);
+            const dfl2 Zc = conj_(rw[padi(MIXED ? (H - m) % H : (H - m) & (H - 1))]);
             dfl2 E = cadd(Zk, Zc), O = csub(Zk, Zc);
             E.x = scale2(E.x, 0.5f);
             E.y = scale2(E.y, 0.5f);
