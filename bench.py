@@ -72,7 +72,8 @@ def nominal_flops_per_rt(lmax=LMAX, nlat=NLAT, nphi=NPHI):
 def legendre_flops_per_launch(batch, lmax=LMAX, nlat=NLAT):
     """Algorithmic flops of one Legendre launch on `batch` fields: per
     (mode, latitude pair) the recurrence (2 mul + 1 fma = 4 flops, shared by
-    the batch) plus one complex x real accumulate per field (4 flops)."""
+    the batch) plus one complex x real accumulate per field (4 flops), before
+    the polar optimisation's skip."""
     npairs = (nlat + 1) // 2
     return nlm_of(lmax) * npairs * (4.0 + 4.0 * batch)
 
@@ -547,8 +548,15 @@ def roofline(mode, sht, table, peaks, alu_peaks, sm_max, batch=BATCH, lmax=LMAX,
         return {"bound": "hbm", "kernel": dom_name, "achieved": ach / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
                 "frac": ach / hbm, "traffic": None, "peak_source": hbm_src, "algorithmic_bytes": algo,
                 "kernel_avg_ms": dom_avg, "launches": dom_n}
-    flops = legendre_flops_per_launch(batch, lmax, nlat) if dom_name.startswith("legendre") else \
-        batch * nlat * 2.5 * nphi * math.log2(nphi)
+    skip = None
+    if dom_name.startswith("legendre"):
+        # terms before their pair's first live segment (static polar
+        # optimisation) are not algorithmic work; warps skip only whole
+        # groups of 32 pairs, so this count is at most the work done
+        skip = C.sht_cc_polar_skip(sht._h, C.SHT_F64 if is_fp64(mode) else C.SHT_F32)
+        flops = legendre_flops_per_launch(batch, lmax, nlat) * (1.0 - max(0.0, skip))
+    else:
+        flops = batch * nlat * 2.5 * nphi * math.log2(nphi)
     if is_fp64(mode) and mode != "tc_f64":
         peak, src = ((alu_peaks[1] * 1e12, "measured FP64 FMA throughput (sht_alu_peaks)") if alu_peaks
                      else (FP64_PEAK_NOMINAL, "FP64 nominal 1.25 TFLOP/s"))
@@ -556,9 +564,12 @@ def roofline(mode, sht, table, peaks, alu_peaks, sm_max, batch=BATCH, lmax=LMAX,
         peak, src = ((alu_peaks[0] * 1e12, "measured FP32 FMA throughput (sht_alu_peaks)") if alu_peaks
                      else (fp32_alu_peak(sm_max), "FP32 nominal"))
     ach = flops / (dom_avg / 1e3)
-    return {"bound": "alu", "kernel": dom_name, "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-            "frac": ach / peak, "traffic": None, "peak_source": src, "algorithmic_flops": flops,
-            "kernel_avg_ms": dom_avg, "launches": dom_n}
+    res = {"bound": "alu", "kernel": dom_name, "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+           "frac": ach / peak, "traffic": None, "peak_source": src, "algorithmic_flops": flops,
+           "kernel_avg_ms": dom_avg, "launches": dom_n}
+    if skip is not None:
+        res["polar_terms_skipped"] = skip
+    return res
 
 
 def kernels_per_launch(mode, kind):
@@ -920,6 +931,34 @@ def polar_sweep(torch, dev, thresholds=(0.0, 2.0 ** -40, 2.0 ** -32, 2.0 ** -26,
     return out
 
 
+def polar_sweep_cc(torch, dev, thresholds=(0.0, 2.0 ** -64, 2.0 ** -40, 2.0 ** -26, 2.0 ** -20), steps=3):
+    """The same sweep on the paper's own on-the-fly design: the plain FP64
+    CUDA-core path, whose kernels skip the 32-degree segments before each
+    pair's first live one (the FP64 default threshold is 2^-64)."""
+    import numpy as np
+    from paper_1202_6522_gb300 import _capi as C
+    from paper_1202_6522_gb300 import synthetic
+    sht = make_plan("f64", dev)
+    a = torch.from_numpy(synthetic.spectrum(LMAX, batch=BATCH, seed=0)).to(dev)
+    out = []
+    for thr in thresholds:
+        C.sht_set_polar_threshold(sht._h, thr)
+        sht.analys_(sht.synth_(a))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            sht.analys_(sht.synth_(a))
+        e1.record()
+        e1.synchronize()
+        out.append({"threshold": thr, "ms_per_step": e0.elapsed_time(e1) / steps,
+                    "terms_below_first_live": C.sht_cc_polar_skip(sht._h, C.SHT_F64),
+                    **round_trip_errors(sht, torch, dev, torch.complex128)})
+    del sht
+    return out
+
+
 # ---------------------------------------------------------------------------
 def timed_leg(mode, torch, dev, stream, a_np, steps, warmup, world, barrier, peaks, alu_peaks, uuid, samples,
               clocks=True, e2e=True):
@@ -1021,6 +1060,7 @@ def run_ours(args):
         extra["n511"] = n511_config(torch, dev)
         extra["high_n"] = high_n_config(torch, dev, peaks, alu_peaks, (head.get("clocks") or {}).get("sm_max_mhz") or 2070.0)
         extra["polar_threshold_sweep"] = polar_sweep(torch, dev)
+        extra["polar_threshold_sweep_fp64_cuda_cores"] = polar_sweep_cc(torch, dev)
         extra["accuracy_vs_n"] = accuracy_vs_n(torch, dev)
 
     if rank != 0:

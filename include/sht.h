@@ -72,7 +72,12 @@ enum {
 };
 
 enum {
-    SHT_F64 = 0,       /* FP64 throughout: the plain path                              */
+    SHT_F64 = 0,       /* FP64 throughout: the plain path.  Scalar transforms restart
+                        * the recurrence at every 32-degree segment they run, from
+                        * states the FP64 recurrence computes once per plan together
+                        * with the table of the static polar optimisation (built by
+                        * the first scalar call in this mode or by sht_reserve: 20 B
+                        * per latitude pair and 32 degrees, 175 MB at lmax = 1023). */
     SHT_F32 = 1,       /* FP32 data and recurrence with the explicit exponent scale of
                         * Sec. 3.5, restarted every 32 degrees from states the FP64
                         * recurrence computes once per plan (built by the first call
@@ -209,9 +214,10 @@ SHT_API int sht_sync_status(sht_handle h, void *stream);
  * created beforehand (sht_create allocates the plan tables).
  *   - Modes SHT_F64 and SHT_F32 (SHT_F32_AUTO runs SHT_F32 here), any plan
  *     including m-stride ones; SHT_TC_BF16X3, SHT_TC_OTF and SHT_TC_F64 return
- *     SHT_EUNSUPPORTED, their panels or seeds being allocated.  SHT_F32 needs
- *     the plan's FP32 recurrence restart states, which the first SHT_F32 call
- *     or sht_reserve(h, batch, SHT_F32) builds; without them the call returns
+ *     SHT_EUNSUPPORTED, their panels or seeds being allocated.  Both modes
+ *     need the plan's recurrence restart states of their precision (and the
+ *     polar table), which the first scalar call in that mode or
+ *     sht_reserve(h, batch, mode) builds; without them the call returns
  *     SHT_EUNSUPPORTED and enqueues nothing.
  *   - The fixed array holds SHT_STATIC_SCRATCH_BYTES (16 MiB) on every GPU that
  *     loads this library, until the process exits.  A call needs
@@ -311,12 +317,24 @@ SHT_API const char *sht_kernel_name(int kind);
  * panels (chunks whose digits are all zero) -- or -1 if none is built. */
 SHT_API int sht_tc_polar_skip(sht_handle h, double *synth_frac, double *analys_frac);
 
-/* Threshold of that optimisation (the paper leaves its value open; default
- * 2^-40): a panel chunk is skipped while all its |P_n^m| (and, for the vector
- * transforms, |sin(theta) dP/dtheta|) are below it.  0 skips nothing.  Must
+/* Threshold of the static polar optimisation (Sec. 3.1; the paper leaves its
+ * value open).  Tensor-core modes: a panel chunk is skipped while all its
+ * |P_n^m| (and, for the vector transforms, |sin(theta) dP/dtheta|) are below
+ * it; default 2^-40.  CUDA-core scalar transforms (SHT_F64, SHT_F32): per
+ * order and latitude pair the 32-degree segments before the first one that
+ * holds a |P_n^m| at or above it run neither the recurrence nor the sums
+ * (whole warps skip them); defaults 2^-64 (SHT_F64) and 2^-40 (SHT_F32) until
+ * the threshold is set, then the set value for both.  0 skips nothing.  Must
  * be in [0, 1]; waits for the device to be idle, then recomputes the skip
  * tables that exist. */
 SHT_API int sht_set_polar_threshold(sht_handle h, double threshold);
+
+/* Share of the (order, latitude pair, degree) terms of the CUDA-core scalar
+ * transforms in `mode` (SHT_F64 or SHT_F32) that lie before their pair's
+ * first live 32-degree segment under the current threshold (the terms the
+ * static polar optimisation may skip; a warp skips a segment only when all
+ * its pairs do), or -1 if the table was not built yet. */
+SHT_API int sht_cc_polar_skip(sht_handle h, int mode, double *frac);
 
 /* Failure-detection self-test (no counterpart in the paper): enqueue a kernel
  * that waits, with a bound of timeout_us microseconds, on a barrier that

@@ -64,6 +64,7 @@ SIGNATURES = {
     "sht_set_polar_threshold": ([_VP, ctypes.c_double], _I),
     "sht_alu_peaks": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _VP], _I),
     "sht_tc_polar_skip": ([_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], _I),
+    "sht_cc_polar_skip": ([_VP, _I, ctypes.POINTER(ctypes.c_double)], _I),
     "sht_profile": ([_VP, _I], _I),
     "sht_profile_read": ([_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I), _I], _I),
     "sht_kernel_name": ([_I], ctypes.c_char_p),
@@ -255,6 +256,13 @@ def sht_tc_polar_skip(h):
 
 def sht_set_polar_threshold(h, threshold):
     return check(_call("sht_set_polar_threshold", h, float(threshold)))
+
+
+def sht_cc_polar_skip(h, mode):
+    """Share of the CUDA-core scalar terms before their first live segment (-1: no table)."""
+    f = ctypes.c_double()
+    check(_call("sht_cc_polar_skip", h, mode, ctypes.byref(f)))
+    return f.value
 
 
 def sht_selftest_timeout(h, timeout_us, stream):

@@ -253,6 +253,15 @@ int ensure_seeds32(sht::Plan &p)
     return rc ? fail(rc, err) : SHT_OK;
 }
 
+// FP64 CUDA-core scalar path: the restart states and first-live table of the
+// static polar optimisation (plan_seeds64), built on the first call that needs them.
+int ensure_seeds64(sht::Plan &p)
+{
+    std::string err;
+    const int rc = sht::plan_seeds64(p, err);
+    return rc ? fail(rc, err) : SHT_OK;
+}
+
 size_t elem_size(int mode) { return (mode == SHT_F64 || mode == SHT_TC_F64) ? sizeof(double) : sizeof(float); }
 
 // FP64-accurate tensor-core mode: digit-slice panels (about 6 (lmax+1)^3
@@ -541,6 +550,7 @@ int scalar_s2g(sht_handle h, const void *spec, void *grid, int batch, int mode, 
         return run_tc64(h->p, true, spec, grid, batch, op, s);
     }
     if (mode == SHT_F32 && (rc = ensure_seeds32(h->p))) return rc;
+    if (mode == SHT_F64 && (rc = ensure_seeds64(h->p))) return rc;
     if ((rc = ensure_work(h->p, inter_bytes(h->p, batch, mode)))) return rc;
     if (mode == SHT_F64) return run_synth<double>(h->p, h->p.view64(), spec, grid, batch, op, s);
     return run_synth<float>(h->p, h->p.view32(), spec, grid, batch, op, s);
@@ -569,6 +579,7 @@ int scalar_g2s(sht_handle h, const void *grid, void *spec, int batch, int mode, 
         return run_tc64(h->p, false, grid, spec, batch, op, s);
     }
     if (mode == SHT_F32 && (rc = ensure_seeds32(h->p))) return rc;
+    if (mode == SHT_F64 && (rc = ensure_seeds64(h->p))) return rc;
     if ((rc = ensure_work(h->p, inter_bytes(h->p, batch, mode)))) return rc;
     if (mode == SHT_F64) return run_analys<double>(h->p, h->p.view64(), grid, spec, batch, op, s);
     return run_analys<float>(h->p, h->p.view32(), grid, spec, batch, op, s);
@@ -906,6 +917,7 @@ int sht_reserve(sht_handle h, int batch, int mode)
         return ensure_work(h->p, tc64_work_bytes(h->p, batch));
     }
     if ((mode == SHT_F32 || mode == SHT_F32_AUTO) && (rc = ensure_seeds32(h->p))) return rc;
+    if (mode == SHT_F64 && (rc = ensure_seeds64(h->p))) return rc;
     return ensure_work(h->p, 2 * inter_bytes(h->p, batch, mode));
 }
 
@@ -988,6 +1000,34 @@ int sht_tc_polar_skip(sht_handle h, double *synth_frac, double *analys_frac)
     return SHT_OK;
 }
 
+int sht_cc_polar_skip(sht_handle h, int mode, double *frac)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!frac) return fail(SHT_EINVAL, "sht_cc_polar_skip: null output");
+    const sht::Plan &p = h->p;
+    const unsigned short *live = mode == SHT_F64 ? p.live64 : (mode == SHT_F32 ? p.live32 : nullptr);
+    if (mode != SHT_F64 && mode != SHT_F32) return fail(SHT_EINVAL, "sht_cc_polar_skip: mode SHT_F64 or SHT_F32");
+    if (!live) {
+        *frac = -1.0;
+        return SHT_OK;
+    }
+    std::vector<unsigned short> t((size_t)(p.mmax + 1) * p.npairs);
+    cudaError_t e = cudaMemcpy(t.data(), live, sizeof(unsigned short) * t.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(SHT_ECUDA, std::string("sht_cc_polar_skip: ") + cudaGetErrorString(e));
+    double skipped = 0.0, total = 0.0;
+    for (int m = 0; m <= p.mmax; ++m) {
+        const int L = p.lmax - m * p.mres + 1;
+        for (int q = 0; q < p.npairs; ++q) {
+            const long dead = (long)t[(size_t)m * p.npairs + q] * sht::kSeedSeg;
+            skipped += (double)(dead < L ? dead : L);
+            total += L;
+        }
+    }
+    *frac = total > 0 ? skipped / total : 0.0;
+    return SHT_OK;
+}
+
 int sht_set_polar_threshold(sht_handle h, double threshold)
 {
     int rc = check_handle(h);
@@ -995,7 +1035,12 @@ int sht_set_polar_threshold(sht_handle h, double threshold)
     if (!(threshold >= 0.0) || threshold > 1.0) return fail(SHT_EINVAL, "polar threshold must be in [0, 1]");
     sht::Plan &p = h->p;
     p.polar_thr = (float)threshold;
+    p.polar_thr_set = true;
     cudaError_t e = cudaDeviceSynchronize();   // no transform may be reading the tables
+    if (e == cudaSuccess) {
+        std::string err;
+        if ((rc = sht::plan_relive(p, err))) return fail(rc, "sht_set_polar_threshold: " + err);
+    }
     if (e == cudaSuccess && p.panel_s) e = first_live_scalar(p);
     if (e == cudaSuccess && p.dpanel_s) {
         int T_s = 0, T_a = 0;
@@ -1120,6 +1165,7 @@ extern "C" int sht_tune(sht_handle h, int batch, int mode, double *report, void 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int shape_mode = mode == SHT_F64 ? SHT_F64 : SHT_F32;
     if (shape_mode == SHT_F32 && (rc = ensure_seeds32(p))) return rc;
+    if (shape_mode == SHT_F64 && (rc = ensure_seeds64(p))) return rc;
     const size_t es = elem_size(shape_mode);
     void *spec = nullptr, *grid = nullptr;
     cudaError_t e = cudaMalloc(&spec, (size_t)batch * p.nlm * 2 * es);
@@ -1135,11 +1181,12 @@ extern "C" int sht_tune(sht_handle h, int batch, int mode, double *report, void 
     sht::TunedShape best;
     double best_syn = 1e30, best_ana = 1e30;
     const int reps = 3;
-    const int lpts_s[3] = {1, 2, 4}, bcs_s[3] = {1, 2, 4};
+    const int lpts_s[3] = {1, 2, 4}, bcs_s[4] = {1, 2, 4, 8};
     for (int li = 0; li < 3; ++li)
-        for (int bi = 0; bi < 3; ++bi) {
+        for (int bi = 0; bi < 4; ++bi) {
             const int lpt = lpts_s[li], bc = bcs_s[bi];
             if (bc > batch && bc > 1) continue;
+            if (bc == 8 && (shape_mode != SHT_F64 || lpt > 2)) continue;
             bool ok = false;
             double ms;
             if (shape_mode == SHT_F64)
@@ -1148,12 +1195,14 @@ extern "C" int sht_tune(sht_handle h, int batch, int mode, double *report, void 
                 ms = time_ms([&] { return sht::launch_legendre_synth_cfg<float>(p.view32(), (const float *)spec, (float *)p.work, batch, sht::OP_SYNTH, lpt, bc, s); }, s, reps, ok);
             if (ok && ms < best_syn) { best_syn = ms; best.synth_lpt = lpt; best.synth_bc = bc; }
         }
-    const int lpts_a[3] = {2, 4, 8}, bcs_a[2] = {1, 2};
-    for (int li = 0; li < 3; ++li)
-        for (int bi = 0; bi < 2; ++bi) {
+    const int lpts_a[4] = {2, 4, 8, sht::kAnalysSeg}, bcs_a[4] = {1, 2, 4, 8};
+    for (int li = 0; li < 4; ++li)
+        for (int bi = 0; bi < 4; ++bi) {
             const int lpt = lpts_a[li], bc = bcs_a[bi];
             if (bc > batch && bc > 1) continue;
-            if ((p.npairs + 32 * lpt - 1) / (32 * lpt) > 8) continue;
+            if (lpt == sht::kAnalysSeg ? (shape_mode != SHT_F64 || p.npairs > 512)
+                                       : (bc > 2 || (p.npairs + 32 * lpt - 1) / (32 * lpt) > 8))
+                continue;
             bool ok = false;
             double ms;
             if (shape_mode == SHT_F64)
@@ -1266,14 +1315,18 @@ extern "C" int sht_synth_static(sht_handle h, const void *spec, void *grid, int 
     if (mode == SHT_TC_BF16X3 || mode == SHT_TC_OTF || mode == SHT_TC_F64)
         return fail(SHT_EUNSUPPORTED, "sht_synth_static: the tensor-core modes need tables allocated by the handle");
     if (mode == SHT_F32_AUTO) mode = SHT_F32;
-    if (mode == SHT_F32 && !h->p.seeds32)
-        return fail(SHT_EUNSUPPORTED, "sht_synth_static: SHT_F32 needs the plan's FP32 recurrence restart states; "
-                                      "build them first with sht_reserve(h, batch, SHT_F32) or any SHT_F32 call");
     const size_t need = inter_bytes(h->p, batch, mode);
     if (need > (size_t)SHT_STATIC_SCRATCH_BYTES)
         return fail(SHT_EINVAL, "sht_synth_static: this call needs " + std::to_string(need) +
                                     " bytes of intermediate storage, more than the fixed " +
                                     std::to_string((size_t)SHT_STATIC_SCRATCH_BYTES) + "-byte array");
+    if (mode == SHT_F32 && !h->p.seeds32)
+        return fail(SHT_EUNSUPPORTED, "sht_synth_static: SHT_F32 needs the plan's FP32 recurrence restart states; "
+                                      "build them first with sht_reserve(h, batch, SHT_F32) or any SHT_F32 call");
+    if (mode == SHT_F64 && !h->p.seeds64)
+        return fail(SHT_EUNSUPPORTED, "sht_synth_static: SHT_F64 needs the plan's FP64 restart states and polar "
+                                      "table; build them first with sht_reserve(h, batch, SHT_F64) or any SHT_F64 "
+                                      "call");
     void *scratch = nullptr;
     if ((rc = static_scratch(&scratch))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

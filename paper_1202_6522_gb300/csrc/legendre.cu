@@ -45,13 +45,18 @@ template <> __device__ __forceinline__ float down_scale<float>() { return 0x1p-6
 
 // One step of P_n = a x P_{n-1} + b P_{n-2} for LPT pairs.  With CHECK the
 // rescaling of Sec. 3.5 is applied and c[] receives the value entering the
-// sums (0 while k > 0); without it c[] is the value itself.
+// sums (0 while k > 0); without it c[] is the value itself.  Pairs i whose
+// bit in `live` (warp-uniform) is clear are left as they are, with c[i] = 0.
 template <typename T, int LPT, bool CHECK>
 __device__ __forceinline__ void rec_step(T a, T b, const T (&x)[LPT], T (&y1)[LPT], T (&y2)[LPT],
-                                         int (&k)[LPT], T (&c)[LPT])
+                                         int (&k)[LPT], T (&c)[LPT], unsigned live = ~0u)
 {
 #pragma unroll
     for (int i = 0; i < LPT; ++i) {
+        if (!((live >> i) & 1)) {
+            c[i] = T(0);
+            continue;
+        }
         T yn = fma(a * x[i], y1[i], b * y2[i]);
         y2[i] = y1[i];
         y1[i] = yn;
@@ -86,33 +91,70 @@ __device__ __forceinline__ int kmin_of(const int (&k)[LPT])
     return r;
 }
 
-// FP32 plans: restart the recurrence of the LPT pairs p[] at segment `seg`
-// (degrees n - m in [kSeedSeg seg, kSeedSeg (seg + 1))) of order index m from
-// the state the FP64 recurrence computed once per plan (y1 = P_{n0-1},
-// y2 = P_{n0-2} and the exponent counter k of Sec. 3.5).  No-op in FP64.
+// Restart the recurrence of the LPT pairs p[] at segment `seg` (degrees
+// n - m in [kSeedSeg seg, kSeedSeg (seg + 1))) of order index m from the
+// state the FP64 recurrence computed once per plan: y1 = P_{n0-1},
+// y2 = P_{n0-2} and the exponent counter k of Sec. 3.5, in the precision's
+// own scaled form.  FP32 kernels restart every segment (the FP32 recurrence
+// alone loses accuracy with n); FP64 kernels restart where they skip dead
+// segments (the static polar optimisation).
 template <typename T, int LPT>
 __device__ __forceinline__ void reseed(const PlanView<T> &pv, int m, int seg, const int (&p)[LPT], T (&y1)[LPT],
                                        T (&y2)[LPT], int (&k)[LPT])
 {
-    if constexpr (sizeof(T) == sizeof(float)) {
-        const float4 *sd = pv.seeds + (size_t)(pv.segoff[m] + seg) * pv.npairs;
+    const size_t base = (size_t)(pv.segoff[m] + seg) * pv.npairs;
 #pragma unroll
-        for (int i = 0; i < LPT; ++i) {
-            if (p[i] < pv.npairs) {
-                const float4 v = __ldg(sd + p[i]);
+    for (int i = 0; i < LPT; ++i) {
+        if (p[i] < pv.npairs) {
+            if constexpr (sizeof(T) == sizeof(float)) {
+                const float4 v = __ldg(pv.seeds + base + p[i]);
                 y1[i] = v.x;
                 y2[i] = v.y;
                 k[i] = __float_as_int(v.z);
+            } else {
+                const double2 v = __ldg(pv.seeds64 + base + p[i]);
+                y1[i] = v.x;
+                y2[i] = v.y;
+                k[i] = __ldg(pv.seeds64k + base + p[i]);
             }
         }
     }
 }
 
-// The FP32 kernels need the restart states; a plan without them is refused
-// rather than run on the unrestarted recurrence.
-template <typename T> bool seeds_ok(const PlanView<T> &pv)
+// First live segment of each group i of 32 pairs (the warp's lanes' p[i];
+// no pair: past every segment), warp-uniform; returns the smallest.
+template <typename T, int LPT>
+__device__ __forceinline__ int group_first_live(const PlanView<T> &pv, int m, const int (&p)[LPT], int (&gf)[LPT])
 {
-    return sizeof(T) != sizeof(float) || (pv.seeds != nullptr && pv.segoff != nullptr);
+    int r = 0xffff;
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) {
+        const int f = p[i] < pv.npairs ? (int)__ldg(pv.live + (size_t)m * pv.npairs + p[i]) : 0xffff;
+        gf[i] = __reduce_min_sync(kFull, f);
+        r = min(r, gf[i]);
+    }
+    return r;
+}
+
+// Bit i set when group i has a live pair in segment seg.
+template <int LPT>
+__device__ __forceinline__ unsigned live_groups(const int (&gf)[LPT], int seg)
+{
+    unsigned r = 0;
+#pragma unroll
+    for (int i = 0; i < LPT; ++i)
+        if (seg >= gf[i]) r |= 1u << i;
+    return r;
+}
+
+// The scalar kernels need the restart states and the first-live table (both
+// precisions); the vector kernels need the restart states in FP32 only.  A
+// plan without them is refused rather than run on other arithmetic.
+template <typename T> bool seeds_ok(const PlanView<T> &pv, bool scalar)
+{
+    if (sizeof(T) == sizeof(float))
+        return pv.segoff != nullptr && pv.seeds != nullptr && (!scalar || pv.live != nullptr);
+    return !scalar || (pv.segoff != nullptr && pv.seeds64 != nullptr && pv.seeds64k != nullptr && pv.live != nullptr);
 }
 
 // Warp butterfly that sums V values (V a multiple of 32) over the 32 lanes and
@@ -142,11 +184,17 @@ static_assert(kSynthNch % kSeedSeg == 0, "restart segments must not straddle sta
 
 // One (order m, pair block pb, field chunk b0) tile of the scalar synthesis,
 // run by a whole CTA of NT threads; s_ab[kSynthNch], s_f[kSynthNch * BC] are
-// the CTA's staging buffers.
+// the CTA's staging buffers, *s_first a shared word.
+//
+// Static polar optimisation (Sec. 3.1): the CTA starts at the first segment
+// in which one of its pairs is live; within a warp, a group of 32 pairs (one
+// p[i] per lane) runs neither the recurrence nor the sums over a segment in
+// which none of its pairs is live.  Each segment a warp runs restarts the
+// recurrence from the stored state.
 template <typename T, int LPT, int BC, int NT>
 __device__ __forceinline__ void synth_tile(const PlanView<T> &pv, const T *__restrict__ spec, T *__restrict__ eo,
                                            int batch, int m, int pb, int b0, int op, typename Vec2<T>::type *s_ab,
-                                           typename Vec2<T>::type *s_f)
+                                           typename Vec2<T>::type *s_f, int *s_first)
 {
     using T2 = typename Vec2<T>::type;
     constexpr int NCH = kSynthNch;
@@ -176,7 +224,15 @@ __device__ __forceinline__ void synth_tile(const PlanView<T> &pv, const T *__res
     const T insc = (op == OP_ANALYS_ADJ && m > 0) ? T(0.5) : T(1);
     const T2 *spec2 = reinterpret_cast<const T2 *>(spec);
 
-    for (int n0 = 0; n0 < L; n0 += NCH) {
+    int gf[LPT];
+    const int wfirst = group_first_live<T, LPT>(pv, m, p, gf);
+    if (threadIdx.x == 0) *s_first = 0xffff;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMin(s_first, wfirst);
+    __syncthreads();
+    const int start = min(*s_first * kSeedSeg, L);
+
+    for (int n0 = start; n0 < L; n0 += NCH) {
         const int cnt = min(NCH, L - n0);
         __syncthreads();
         for (int t = threadIdx.x; t < NCH; t += NT) {
@@ -198,29 +254,33 @@ __device__ __forceinline__ void synth_tile(const PlanView<T> &pv, const T *__res
         }
         __syncthreads();
         for (int s0 = 0; s0 < cnt; s0 += kSeedSeg) {
+            const unsigned gl = live_groups<LPT>(gf, (n0 + s0) / kSeedSeg);
+            if (gl == 0) continue;   // no live pair in this warp yet
             reseed<T, LPT>(pv, m, (n0 + s0) / kSeedSeg, p, y1, y2, k);
             const int s1 = min(cnt, s0 + kSeedSeg);
             const bool scaled = __any_sync(kFull, kmax_of<T, LPT>(k) > 0);
             if (!scaled) {
                 for (int t = s0; t < s1; t += 2) {
                     T2 ab = s_ab[t];
-                    rec_step<T, LPT, false>(ab.x, ab.y, x, y1, y2, k, c);
+                    rec_step<T, LPT, false>(ab.x, ab.y, x, y1, y2, k, c, gl);
 #pragma unroll
                     for (int b = 0; b < BC; ++b) {
                         const T2 f = s_f[t * BC + b];
 #pragma unroll
                         for (int i = 0; i < LPT; ++i) {
+                            if (!((gl >> i) & 1)) continue;
                             er[i][b] = fma(f.x, c[i], er[i][b]);
                             ei[i][b] = fma(f.y, c[i], ei[i][b]);
                         }
                     }
                     ab = s_ab[t + 1];
-                    rec_step<T, LPT, false>(ab.x, ab.y, x, y1, y2, k, c);
+                    rec_step<T, LPT, false>(ab.x, ab.y, x, y1, y2, k, c, gl);
 #pragma unroll
                     for (int b = 0; b < BC; ++b) {
                         const T2 f = s_f[(t + 1) * BC + b];
 #pragma unroll
                         for (int i = 0; i < LPT; ++i) {
+                            if (!((gl >> i) & 1)) continue;
                             orr[i][b] = fma(f.x, c[i], orr[i][b]);
                             oi[i][b] = fma(f.y, c[i], oi[i][b]);
                         }
@@ -229,26 +289,28 @@ __device__ __forceinline__ void synth_tile(const PlanView<T> &pv, const T *__res
             } else {
                 for (int t = s0; t < s1; t += 2) {
                     T2 ab = s_ab[t];
-                    rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c);
+                    rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c, gl);
                     if (__any_sync(kFull, kmin_of<T, LPT>(k) == 0)) {
 #pragma unroll
                         for (int b = 0; b < BC; ++b) {
                             const T2 f = s_f[t * BC + b];
 #pragma unroll
                             for (int i = 0; i < LPT; ++i) {
+                                if (!((gl >> i) & 1)) continue;
                                 er[i][b] = fma(f.x, c[i], er[i][b]);
                                 ei[i][b] = fma(f.y, c[i], ei[i][b]);
                             }
                         }
                     }
                     ab = s_ab[t + 1];
-                    rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c);
+                    rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c, gl);
                     if (__any_sync(kFull, kmin_of<T, LPT>(k) == 0)) {
 #pragma unroll
                         for (int b = 0; b < BC; ++b) {
                             const T2 f = s_f[(t + 1) * BC + b];
 #pragma unroll
                             for (int i = 0; i < LPT; ++i) {
+                                if (!((gl >> i) & 1)) continue;
                                 orr[i][b] = fma(f.x, c[i], orr[i][b]);
                                 oi[i][b] = fma(f.y, c[i], oi[i][b]);
                             }
@@ -283,9 +345,10 @@ k_synth(PlanView<T> pv, const T *__restrict__ spec, T *__restrict__ eo, int batc
     using T2 = typename Vec2<T>::type;
     __shared__ T2 s_ab[kSynthNch];
     __shared__ T2 s_f[kSynthNch * BC];
+    __shared__ int s_first;
     const int m = blockIdx.x / npb;
     const int pb = blockIdx.x - m * npb;
-    synth_tile<T, LPT, BC, NT>(pv, spec, eo, batch, m, pb, blockIdx.y * BC, op, s_ab, s_f);
+    synth_tile<T, LPT, BC, NT>(pv, spec, eo, batch, m, pb, blockIdx.y * BC, op, s_ab, s_f, &s_first);
 }
 
 // ---------------------------------------------------------------------------
@@ -343,6 +406,8 @@ __device__ __forceinline__ void analys_tile(const PlanView<T> &pv, const T *__re
     // output scale: c_m for the adjoint of synthesis
     const T outsc = (op == OP_SYNTH_ADJ && m > 0) ? T(2) : T(1);
     T2 *spec2 = reinterpret_cast<T2 *>(spec);
+    int gf[LPT];
+    group_first_live<T, LPT>(pv, m, p, gf);
 
     for (int n0 = 0; n0 < L; n0 += NCH) {
         const int cnt = min(NCH, L - n0);
@@ -355,34 +420,42 @@ __device__ __forceinline__ void analys_tile(const PlanView<T> &pv, const T *__re
         }
         __syncthreads();
         for (int t0 = 0; t0 < cnt; t0 += K) {
-            if ((n0 + t0) % kSeedSeg == 0) reseed<T, LPT>(pv, m, (n0 + t0) / kSeedSeg, p, y1, y2, k);
+            // static polar optimisation: groups of 32 pairs with no live pair
+            // in this segment run neither the recurrence nor the sums; a warp
+            // with none contributes zeros
+            const unsigned gl = live_groups<LPT>(gf, (n0 + t0) / kSeedSeg);
+            const bool wlive = gl != 0;
+            if (wlive && (n0 + t0) % kSeedSeg == 0) reseed<T, LPT>(pv, m, (n0 + t0) / kSeedSeg, p, y1, y2, k);
             T acc[32];
 #pragma unroll
             for (int q = 0; q < 32; ++q) acc[q] = T(0);
             const bool scaled = __any_sync(kFull, kmax_of<T, LPT>(k) > 0);
+            if (wlive) {
 #pragma unroll
-            for (int kx = 0; kx < K; ++kx) {
-                const T2 ab = s_ab[t0 + kx];
-                bool live = true;
-                if (scaled) {
-                    rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c);
-                    live = __any_sync(kFull, kmin_of<T, LPT>(k) == 0);
-                } else {
-                    rec_step<T, LPT, false>(ab.x, ab.y, x, y1, y2, k, c);
-                }
-                if (live) {
+                for (int kx = 0; kx < K; ++kx) {
+                    const T2 ab = s_ab[t0 + kx];
+                    bool live = true;
+                    if (scaled) {
+                        rec_step<T, LPT, true>(ab.x, ab.y, x, y1, y2, k, c, gl);
+                        live = __any_sync(kFull, kmin_of<T, LPT>(k) == 0);
+                    } else {
+                        rec_step<T, LPT, false>(ab.x, ab.y, x, y1, y2, k, c, gl);
+                    }
+                    if (live) {
 #pragma unroll
-                    for (int b = 0; b < BC; ++b) {
+                        for (int b = 0; b < BC; ++b) {
 #pragma unroll
-                        for (int i = 0; i < LPT; ++i) {
-                            const T2 v = (kx & 1) ? dv[i][b] : sv[i][b];
-                            acc[(kx * BC + b) * 2] = fma(c[i], v.x, acc[(kx * BC + b) * 2]);
-                            acc[(kx * BC + b) * 2 + 1] = fma(c[i], v.y, acc[(kx * BC + b) * 2 + 1]);
+                            for (int i = 0; i < LPT; ++i) {
+                                if (!((gl >> i) & 1)) continue;
+                                const T2 v = (kx & 1) ? dv[i][b] : sv[i][b];
+                                acc[(kx * BC + b) * 2] = fma(c[i], v.x, acc[(kx * BC + b) * 2]);
+                                acc[(kx * BC + b) * 2 + 1] = fma(c[i], v.y, acc[(kx * BC + b) * 2 + 1]);
+                            }
                         }
                     }
                 }
+                warp_transpose_reduce<T, 32>(acc, lane);
             }
-            warp_transpose_reduce<T, 32>(acc, lane);
             s_red[warp][lane] = acc[0];
             __syncthreads();
             if (threadIdx.x < 2 * K * BC) {
@@ -411,6 +484,140 @@ k_analys(PlanView<T> pv, const T *__restrict__ sd, T *__restrict__ spec, int bat
     __shared__ T2 s_ab[kAnalysNch];
     __shared__ T s_red[8][32];
     analys_tile<T, LPT, BC>(pv, sd, spec, batch, blockIdx.x, blockIdx.y * BC, op, s_ab, s_red);
+}
+
+// ---------------------------------------------------------------------------
+// Scalar analysis, one warp per segment (FP64; npairs <= 32 PPL).
+// grid.x = m (heaviest first), grid.y = field group of BC.  The CTA stages
+// the folds s, d of its BC fields for all pairs in shared memory; each of its
+// kSegWarps warps then takes kSeedSeg-degree segments from a shared counter,
+// restarts the recurrence from the stored state and sums over every pair on
+// its own: PPL pairs per lane, then one warp butterfly per K = 16 / BC
+// degrees.  There is no CTA-wide barrier inside the sums, the recurrence is
+// shared by BC fields, and the cross-lane reduction costs 1/PPL of the sums;
+// the order of every sum is fixed, so results are bitwise reproducible.
+// Groups of 32 pairs with no live pair in a segment (static polar
+// optimisation, Sec. 3.1) run neither the recurrence nor the sums.
+// ---------------------------------------------------------------------------
+constexpr int kSegWarps = 8;
+
+template <typename T, int PPL, int BC>
+__global__ void __launch_bounds__(kSegWarps * 32, 1)
+k_analys_seg(PlanView<T> pv, const T *__restrict__ sd, T *__restrict__ spec, int batch, int op)
+{
+    using T2 = typename Vec2<T>::type;
+    constexpr int K = 16 / BC;        // degrees per butterfly: 2 K BC = 32 values
+    constexpr int R = 32 * PPL;       // staged row: the pairs, zero-padded
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2 *s_v = reinterpret_cast<T2 *>(smem_raw);   // [BC][parity][R]: s (n - m even), d (odd)
+    __shared__ int s_next;
+    __shared__ int s_gfirst[PPL];                 // first live segment of each group of 32 pairs
+
+    const int m = blockIdx.x, b0 = blockIdx.y * BC;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int npairs = pv.npairs;
+    const int L = pv.lmax - m * pv.mres + 1;   // order index m is the order m mres
+    const long col = col_of_mres(pv.lmax, m, pv.mres);
+    const int nseg = (L + kSeedSeg - 1) / kSeedSeg;
+
+    const T2 *sd2 = reinterpret_cast<const T2 *>(sd);
+    for (int idx = threadIdx.x; idx < BC * 2 * R; idx += blockDim.x) {
+        const int b = idx / (2 * R), r = idx - b * 2 * R;
+        T2 v;
+        v.x = T(0); v.y = T(0);
+        if (r < 2 * npairs && b0 + b < batch) v = sd2[((size_t)(b0 + b) * (pv.mmax + 1) + m) * npairs * 2 + r];
+        s_v[(b * 2 + (r & 1)) * R + (r >> 1)] = v;
+    }
+    for (int g = warp; g < PPL; g += kSegWarps) {
+        const int pp = g * 32 + lane;
+        const int f = pp < npairs ? (int)pv.live[(size_t)m * npairs + pp] : 0xffff;
+        const int gm = __reduce_min_sync(kFull, f);
+        if (lane == 0) s_gfirst[g] = gm;
+    }
+    if (threadIdx.x == 0) s_next = kSegWarps;
+    __syncthreads();
+
+    const T outsc = (op == OP_SYNTH_ADJ && m > 0) ? T(2) : T(1);   // c_m for the adjoint of synthesis
+    T2 *spec2 = reinterpret_cast<T2 *>(spec);
+    int p[PPL];
+    T x[PPL];
+#pragma unroll
+    for (int i = 0; i < PPL; ++i) {
+        p[i] = lane + 32 * i;
+        x[i] = p[i] < npairs ? pv.x[p[i]] : T(0);
+    }
+    // value `lane` of the butterfly: degree t0 + kx, field b, real/imaginary part
+    const int okx = lane / (2 * BC), ob = (lane >> 1) % BC, opart = lane & 1;
+
+    for (int seg = warp; seg < nseg;) {
+        const int nn0 = seg * kSeedSeg, cnt = min(kSeedSeg, L - nn0);
+        unsigned live = 0;
+#pragma unroll
+        for (int i = 0; i < PPL; ++i)
+            if (s_gfirst[i] <= seg) live |= 1u << i;
+        if (live == 0) {
+            for (int q = lane; q < cnt * 2 * BC; q += 32) {
+                const int kx = q / (2 * BC), b = (q >> 1) % BC;
+                if (b0 + b < batch)
+                    reinterpret_cast<T *>(&spec2[(size_t)(b0 + b) * pv.nlm + col + nn0 + kx])[q & 1] = T(0);
+            }
+        } else {
+            T y1[PPL], y2[PPL];
+            int k[PPL];
+#pragma unroll
+            for (int i = 0; i < PPL; ++i) {
+                y1[i] = y2[i] = T(0);
+                k[i] = 0;
+            }
+            reseed<T, PPL>(pv, m, seg, p, y1, y2, k);
+            unsigned scaled = 0;
+#pragma unroll
+            for (int i = 0; i < PPL; ++i)
+                if (__any_sync(kFull, k[i] > 0)) scaled |= 1u << i;
+            for (int t0 = 0; t0 < cnt; t0 += K) {
+                T acc[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) acc[q] = T(0);
+#pragma unroll
+                for (int kx = 0; kx < K; ++kx) {
+                    if (t0 + kx >= cnt) break;
+                    const T2 ab = __ldg(&pv.ab[col + nn0 + t0 + kx]);
+                    const T2 *vrow = s_v + ((t0 + kx) & 1) * R;   // nn0 is even
+#pragma unroll
+                    for (int i = 0; i < PPL; ++i) {
+                        if (!((live >> i) & 1)) continue;
+                        const T yn = fma(ab.x * x[i], y1[i], ab.y * y2[i]);
+                        y2[i] = y1[i];
+                        y1[i] = yn;
+                        T c = yn;
+                        if ((scaled >> i) & 1) {
+                            if (k[i] > 0 && abs_ge_one(yn)) {
+                                y1[i] *= down_scale<T>();
+                                y2[i] *= down_scale<T>();
+                                k[i] -= 1;
+                            }
+                            c = (k[i] == 0) ? y1[i] : T(0);
+                        }
+#pragma unroll
+                        for (int b = 0; b < BC; ++b) {
+                            const T2 v = vrow[b * 2 * R + p[i]];
+                            acc[(kx * BC + b) * 2] = fma(c, v.x, acc[(kx * BC + b) * 2]);
+                            acc[(kx * BC + b) * 2 + 1] = fma(c, v.y, acc[(kx * BC + b) * 2 + 1]);
+                        }
+                    }
+                }
+                warp_transpose_reduce<T, 32>(acc, lane);
+                if (t0 + okx < cnt && b0 + ob < batch) {
+                    T val = acc[0] * outsc;
+                    if (m == 0 && opart == 1) val = T(0);
+                    reinterpret_cast<T *>(&spec2[(size_t)(b0 + ob) * pv.nlm + col + nn0 + t0 + okx])[opart] = val;
+                }
+            }
+        }
+        int nx = 0;
+        if (lane == 0) nx = atomicAdd(&s_next, 1);
+        seg = __shfl_sync(kFull, nx, 0);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -495,7 +702,7 @@ k_synth_vec(PlanView<T> pv, const T *__restrict__ Sg, const T *__restrict__ Tg, 
         bool scaled = false;
         for (int t = 0; t < cnt; t += 2) {
             if (t % kSeedSeg == 0) {
-                reseed<T, LPT>(pv, m, (n0 + t) / kSeedSeg, p, y1, y2, k);
+                if constexpr (sizeof(T) == sizeof(float)) reseed<T, LPT>(pv, m, (n0 + t) / kSeedSeg, p, y1, y2, k);
                 scaled = __any_sync(kFull, kmax_of<T, LPT>(k) > 0);
             }
 #pragma unroll
@@ -640,7 +847,8 @@ k_analys_vec(PlanView<T> pv, const T *__restrict__ sdt, const T *__restrict__ sd
         }
         __syncthreads();
         for (int t0 = 0; t0 < cnt; t0 += K) {
-            if ((n0 + t0) % kSeedSeg == 0) reseed<T, LPT>(pv, m, (n0 + t0) / kSeedSeg, p, y1, y2, k);
+            if (sizeof(T) == sizeof(float) && (n0 + t0) % kSeedSeg == 0)
+                reseed<T, LPT>(pv, m, (n0 + t0) / kSeedSeg, p, y1, y2, k);
             // per (kx, b): SA(2) SB(2) TA(2) TB(2)
             T acc[32];
 #pragma unroll
@@ -741,6 +949,22 @@ cudaError_t analys_go(const PlanView<T> &pv, const T *sd, T *spec, int batch, Op
     return cudaGetLastError();
 }
 
+// Pairs per lane of the segment analysis kernel (0: too many pairs for it).
+inline int seg_ppl(int npairs) { return npairs <= 128 ? 4 : (npairs <= 256 ? 8 : (npairs <= 512 ? 16 : 0)); }
+
+template <typename T, int PPL, int BC>
+cudaError_t analys_seg_go(const PlanView<T> &pv, const T *sd, T *spec, int batch, Op op, cudaStream_t s)
+{
+    using T2 = typename Vec2<T>::type;
+    const size_t smem = sizeof(T2) * BC * 2 * 32 * PPL;
+    cudaError_t e = cudaFuncSetAttribute(k_analys_seg<T, PPL, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(pv.mmax + 1), (unsigned)((batch + BC - 1) / BC));
+    k_analys_seg<T, PPL, BC><<<grid, kSegWarps * 32, smem, s>>>(pv, sd, spec, batch, (int)op);
+    return cudaGetLastError();
+}
+
 template <typename T, int LPT, int BC>
 cudaError_t synth_vec_go(const PlanView<T> &pv, const T *S, const T *Tc, T *eot, T *eop, int batch, Op op,
                          cudaStream_t s)
@@ -774,15 +998,20 @@ template <typename T>
 cudaError_t launch_legendre_synth_cfg(const PlanView<T> &pv, const T *spec, T *eo, int batch, Op op, int lpt, int bc,
                                       cudaStream_t s)
 {
-    if (!seeds_ok(pv)) return cudaErrorInvalidValue;
-    // default shape: 2 pairs per thread, up to 4 fields per CTA
-    if (lpt <= 0) lpt = 2;
-    if (bc <= 0) bc = pick_bc(batch);
+    if (!seeds_ok(pv, true)) return cudaErrorInvalidValue;
+    // default shape: 2 pairs per thread, up to 4 fields per CTA (FP64: 1 pair
+    // per thread, 8 fields, sharing each recurrence step among more sums)
+    if (lpt <= 0) lpt = (sizeof(T) == sizeof(double) && batch >= 8) ? 1 : 2;
+    if (bc <= 0) bc = (sizeof(T) == sizeof(double) && batch >= 8) ? 8 : pick_bc(batch);
 #define SHT_SYN(L, B) if (lpt == L && bc == B) return synth_go<T, L, B>(pv, spec, eo, batch, op, s);
     SHT_SYN(1, 1) SHT_SYN(1, 2) SHT_SYN(1, 4)
     SHT_SYN(2, 1) SHT_SYN(2, 2) SHT_SYN(2, 4)
     SHT_SYN(4, 1) SHT_SYN(4, 2) SHT_SYN(4, 4)
 #undef SHT_SYN
+    if constexpr (sizeof(T) == sizeof(double)) {
+        if (lpt == 1 && bc == 8) return synth_go<T, 1, 8>(pv, spec, eo, batch, op, s);
+        if (lpt == 2 && bc == 8) return synth_go<T, 2, 8>(pv, spec, eo, batch, op, s);
+    }
     return cudaErrorInvalidValue;
 }
 
@@ -796,9 +1025,24 @@ template <typename T>
 cudaError_t launch_legendre_analys_cfg(const PlanView<T> &pv, const T *sd, T *spec, int batch, Op op, int lpt, int bc,
                                        cudaStream_t s)
 {
-    if (!seeds_ok(pv)) return cudaErrorInvalidValue;
-    // default shape: LPT from the pair count (<= 8 warps), 2 fields per CTA when batched
-    if (lpt <= 0) lpt = analys_lpt(pv.npairs);
+    if (!seeds_ok(pv, true)) return cudaErrorInvalidValue;
+    // default shape: FP64 up to 512 pairs, the segment kernel with up to 8
+    // fields per CTA; otherwise LPT from the pair count (<= 8 warps), 2 fields
+    // per CTA when batched
+    if (lpt <= 0) lpt = (sizeof(T) == sizeof(double) && seg_ppl(pv.npairs)) ? kAnalysSeg : analys_lpt(pv.npairs);
+    if (lpt == kAnalysSeg) {
+        if (sizeof(T) != sizeof(double)) return cudaErrorInvalidValue;
+        const int ppl = seg_ppl(pv.npairs);
+        if (bc <= 0) bc = batch >= 8 ? 8 : (batch >= 4 ? 4 : (batch >= 2 ? 2 : 1));
+        if constexpr (sizeof(T) == sizeof(double)) {
+#define SHT_SEG(P, B) if (ppl == P && bc == B) return analys_seg_go<T, P, B>(pv, sd, spec, batch, op, s);
+            SHT_SEG(4, 1) SHT_SEG(4, 2) SHT_SEG(4, 4) SHT_SEG(4, 8)
+            SHT_SEG(8, 1) SHT_SEG(8, 2) SHT_SEG(8, 4) SHT_SEG(8, 8)
+            SHT_SEG(16, 1) SHT_SEG(16, 2) SHT_SEG(16, 4) SHT_SEG(16, 8)
+#undef SHT_SEG
+        }
+        return cudaErrorInvalidValue;
+    }
     if (bc <= 0) bc = batch >= 2 ? 2 : 1;
     if (analys_warps(pv.npairs, lpt) > 8) return cudaErrorInvalidValue;
 #define SHT_ANA(L, B) if (lpt == L && bc == B) return analys_go<T, L, B>(pv, sd, spec, batch, op, s);
@@ -817,7 +1061,7 @@ template <typename T>
 cudaError_t launch_legendre_synth_vec(const PlanView<T> &pv, const T *S, const T *Tc, T *eot, T *eop, int batch,
                                       Op op, cudaStream_t s)
 {
-    if (!seeds_ok(pv)) return cudaErrorInvalidValue;
+    if (!seeds_ok(pv, false)) return cudaErrorInvalidValue;
     if (batch >= 2) return synth_vec_go<T, 1, 2>(pv, S, Tc, eot, eop, batch, op, s);
     return synth_vec_go<T, 1, 1>(pv, S, Tc, eot, eop, batch, op, s);
 }
@@ -826,7 +1070,7 @@ template <typename T>
 cudaError_t launch_legendre_analys_vec(const PlanView<T> &pv, const T *sdt, const T *sdp, T *S, T *Tc, int batch,
                                        Op op, cudaStream_t s)
 {
-    if (!seeds_ok(pv)) return cudaErrorInvalidValue;
+    if (!seeds_ok(pv, false)) return cudaErrorInvalidValue;
     switch (analys_lpt(pv.npairs)) {
     case 2: return analys_vec_go<T, 2, 1>(pv, sdt, sdp, S, Tc, batch, op, s);
     case 4: return analys_vec_go<T, 4, 1>(pv, sdt, sdp, S, Tc, batch, op, s);
@@ -844,7 +1088,7 @@ __global__ void __launch_bounds__(128) k_batch_synth(const BatchField *__restric
 {
     __shared__ float2 s_ab[kSynthNch];
     __shared__ float2 s_f[kSynthNch];
-    __shared__ int s_tile;
+    __shared__ int s_tile, s_first;
     for (;;) {
         __syncthreads();  // the previous tile is done with the shared buffers
         if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
@@ -853,7 +1097,7 @@ __global__ void __launch_bounds__(128) k_batch_synth(const BatchField *__restric
         if (t >= ntiles) break;
         const int4 tl = tiles[t];
         const BatchField f = fields[tl.x];
-        synth_tile<float, 2, 1, 128>(f.pv, f.in, f.inter, 1, tl.y, tl.z, 0, OP_SYNTH, s_ab, s_f);
+        synth_tile<float, 2, 1, 128>(f.pv, f.in, f.inter, 1, tl.y, tl.z, 0, OP_SYNTH, s_ab, s_f, &s_first);
     }
 }
 
@@ -886,12 +1130,16 @@ cudaError_t launch_batch_legendre(bool synth, const BatchField *fields, const in
 }
 
 // ---------------------------------------------------------------------------
-// Restart states of the FP32 recurrence.  One thread per (order index m,
-// pair): the FP64 recurrence of Sec. 3.2 from P_m^m, carried as y 2^(-240 k)
-// (Sec. 3.5), and at the start of every kSeedSeg-degree segment the state
-// (y1, y2) = (P_{n0-1}, P_{n0-2}) rewritten in the FP32 form y' 2^(-64 k'):
-// k' = 0 when the larger of the two is at least 2^-63, else the k' that
-// brings it into [2^-65, 1) -- the form in which the FP32 kernels carry it.
+// Restart states of the recurrence and the first-live table of the static
+// polar optimisation.  One thread per (order index m, pair): the FP64
+// recurrence of Sec. 3.2 from P_m^m, carried as y 2^(-240 k) (Sec. 3.5).  At
+// the start of every kSeedSeg-degree segment the state (y1, y2) =
+// (P_{n0-1}, P_{n0-2}) is stored, either as it is with k (FP64 plans) or
+// rewritten in the FP32 form y' 2^(-64 k'): k' = 0 when the larger of the two
+// is at least 2^-63, else the k' that brings it into [2^-65, 1) -- the form in
+// which the FP32 kernels carry it.  live[m][pair] is the first segment that
+// holds a degree with |P_n^m| >= thr (all segments live when thr <= 0; the
+// segment count when none is).
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -910,7 +1158,9 @@ __device__ float4 fp32_state(double y1, double y2, int k)
 }
 
 __global__ void __launch_bounds__(128)
-k_build_seeds32(PlanView<double> pv, const unsigned long long *__restrict__ segoff, float4 *__restrict__ seeds)
+k_build_restarts(PlanView<double> pv, const unsigned long long *__restrict__ segoff, float4 *__restrict__ seeds32,
+                 double2 *__restrict__ seeds64, int *__restrict__ seeds64k, unsigned short *__restrict__ live,
+                 double thr)
 {
     const int m = blockIdx.y;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -922,8 +1172,14 @@ k_build_seeds32(PlanView<double> pv, const unsigned long long *__restrict__ sego
     const double x = pv.x[p];
     double y1 = 0.0, y2 = pv.pmm[(size_t)m * npairs + p];
     int k = pv.pmmk[(size_t)m * npairs + p];
+    int first = thr > 0.0 ? nseg : 0;
     for (int s = 0; s < nseg; ++s) {
-        seeds[(segoff[m] + s) * npairs + p] = fp32_state(y1, y2, k);
+        const size_t o = (segoff[m] + s) * npairs + p;
+        if (seeds32) seeds32[o] = fp32_state(y1, y2, k);
+        if (seeds64) {
+            seeds64[o] = make_double2(y1, y2);
+            seeds64k[o] = k;
+        }
         for (int i = 0; i < kSeedSeg; ++i) {
             const int nn = kSeedSeg * s + i;
             if (nn >= L) break;
@@ -936,18 +1192,19 @@ k_build_seeds32(PlanView<double> pv, const unsigned long long *__restrict__ sego
                 y2 *= down_scale<double>();
                 k -= 1;
             }
+            if (k == 0 && fabs(y1) >= thr && s < first) first = s;
         }
     }
+    live[(size_t)m * npairs + p] = (unsigned short)first;
 }
-
 
 }  // namespace
 
-cudaError_t launch_build_seeds32(const PlanView<double> &pv, const unsigned long long *segoff, float4 *seeds,
-                                 cudaStream_t st)
+cudaError_t launch_build_restarts(const PlanView<double> &pv, const unsigned long long *segoff, float4 *seeds32,
+                                  double2 *seeds64, int *seeds64k, unsigned short *live, double thr, cudaStream_t st)
 {
     dim3 grid((unsigned)((pv.npairs + 127) / 128), (unsigned)(pv.mmax + 1));
-    k_build_seeds32<<<grid, 128, 0, st>>>(pv, segoff, seeds);
+    k_build_restarts<<<grid, 128, 0, st>>>(pv, segoff, seeds32, seeds64, seeds64k, live, thr);
     return cudaGetLastError();
 }
 

@@ -94,7 +94,7 @@ PlanView<double> Plan::view64() const
 {
     PlanView<double> v{lmax, mmax, nlat, nphi, npairs, nlm,
                        t64.ab, t64.dc, t64.x, t64.st, t64.wq, t64.pmm, t64.pmmk, t64.tw, t64.rtw, fft_plan_of(nphi / 2), mres, twdf,
-                       nullptr, nullptr};
+                       nullptr, d_seg32, seeds64, seeds64k, live64};
     return v;
 }
 
@@ -102,7 +102,7 @@ PlanView<float> Plan::view32() const
 {
     PlanView<float> v{lmax, mmax, nlat, nphi, npairs, nlm,
                       t32.ab, t32.dc, t32.x, t32.st, t32.wq, t32.pmm, t32.pmmk, t32.tw, t32.rtw, fft_plan_of(nphi / 2), mres, nullptr,
-                      seeds32, d_seg32};
+                      seeds32, d_seg32, nullptr, nullptr, live32};
     return v;
 }
 
@@ -292,31 +292,94 @@ size_t seed_segment_offsets(int lmax, int mmax, int mres, std::vector<unsigned l
     return (size_t)s;
 }
 
+namespace {
+
+// The segment offsets (shared by both precisions).
+int plan_segments(Plan &p, std::string &err)
+{
+    if (p.d_seg32) return SHT_OK;
+    std::vector<unsigned long long> segoff;
+    seed_segment_offsets(p.lmax, p.mmax, p.mres, segoff);
+    cudaError_t e = cudaMalloc(&p.d_seg32, sizeof(unsigned long long) * segoff.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p.d_seg32, segoff.data(), sizeof(unsigned long long) * segoff.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p.d_seg32);
+        p.d_seg32 = nullptr;
+        err = std::string("segment table: ") + cudaGetErrorString(e);
+        return SHT_ENOMEM;
+    }
+    return SHT_OK;
+}
+
+size_t plan_nseg(const Plan &p)
+{
+    std::vector<unsigned long long> segoff;
+    return seed_segment_offsets(p.lmax, p.mmax, p.mres, segoff);
+}
+
+}  // namespace
+
 int plan_seeds32(Plan &p, std::string &err)
 {
     if (p.seeds32) return SHT_OK;
-    std::vector<unsigned long long> segoff;
-    const size_t nseg = seed_segment_offsets(p.lmax, p.mmax, p.mres, segoff);
+    int rc = plan_segments(p, err);
+    if (rc) return rc;
+    const size_t nseg = plan_nseg(p);
     cudaError_t e = cudaMalloc(&p.seeds32, sizeof(float4) * nseg * (size_t)p.npairs);
-    if (e == cudaSuccess) e = cudaMalloc(&p.d_seg32, sizeof(unsigned long long) * segoff.size());
+    if (e == cudaSuccess) e = cudaMalloc(&p.live32, sizeof(unsigned short) * (size_t)(p.mmax + 1) * p.npairs);
+    if (e == cudaSuccess)
+        e = launch_build_restarts(p.view64(), p.d_seg32, p.seeds32, nullptr, nullptr, p.live32, p.thr_cc32(), 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         cudaFree(p.seeds32);
-        cudaFree(p.d_seg32);
+        cudaFree(p.live32);
         p.seeds32 = nullptr;
-        p.d_seg32 = nullptr;
-        err = std::string("cudaMalloc(FP32 recurrence seeds): ") + cudaGetErrorString(e);
+        p.live32 = nullptr;
+        err = std::string("building FP32 recurrence seeds: ") + cudaGetErrorString(e);
         return SHT_ENOMEM;
     }
-    e = cudaMemcpy(p.d_seg32, segoff.data(), sizeof(unsigned long long) * segoff.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = launch_build_seeds32(p.view64(), p.d_seg32, p.seeds32, 0);
+    return SHT_OK;
+}
+
+int plan_seeds64(Plan &p, std::string &err)
+{
+    if (p.seeds64) return SHT_OK;
+    int rc = plan_segments(p, err);
+    if (rc) return rc;
+    const size_t nseg = plan_nseg(p);
+    cudaError_t e = cudaMalloc(&p.seeds64, sizeof(double2) * nseg * (size_t)p.npairs);
+    if (e == cudaSuccess) e = cudaMalloc(&p.seeds64k, sizeof(int) * nseg * (size_t)p.npairs);
+    if (e == cudaSuccess) e = cudaMalloc(&p.live64, sizeof(unsigned short) * (size_t)(p.mmax + 1) * p.npairs);
+    if (e == cudaSuccess)
+        e = launch_build_restarts(p.view64(), p.d_seg32, nullptr, p.seeds64, p.seeds64k, p.live64, p.thr_cc64(), 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) {
-        cudaFree(p.seeds32);
-        cudaFree(p.d_seg32);
-        p.seeds32 = nullptr;
-        p.d_seg32 = nullptr;
-        err = std::string("building FP32 recurrence seeds: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        cudaFree(p.seeds64);
+        cudaFree(p.seeds64k);
+        cudaFree(p.live64);
+        p.seeds64 = nullptr;
+        p.seeds64k = nullptr;
+        p.live64 = nullptr;
+        err = std::string("building FP64 recurrence seeds: ") + cudaGetErrorString(e);
+        return SHT_ENOMEM;
+    }
+    return SHT_OK;
+}
+
+int plan_relive(Plan &p, std::string &err)
+{
+    cudaError_t e = cudaSuccess;
+    if (p.seeds32)
+        e = launch_build_restarts(p.view64(), p.d_seg32, p.seeds32, nullptr, nullptr, p.live32, p.thr_cc32(), 0);
+    if (e == cudaSuccess && p.seeds64)
+        e = launch_build_restarts(p.view64(), p.d_seg32, nullptr, p.seeds64, p.seeds64k, p.live64, p.thr_cc64(), 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) {
+        err = std::string("rebuilding the polar tables: ") + cudaGetErrorString(e);
         return SHT_ECUDA;
     }
     return SHT_OK;
@@ -326,8 +389,15 @@ void plan_free(Plan &p)
 {
     cudaFree(p.seeds32);
     cudaFree(p.d_seg32);
+    cudaFree(p.seeds64);
+    cudaFree(p.seeds64k);
+    cudaFree(p.live32);
+    cudaFree(p.live64);
     p.seeds32 = nullptr;
     p.d_seg32 = nullptr;
+    p.seeds64 = nullptr;
+    p.seeds64k = nullptr;
+    p.live32 = p.live64 = nullptr;
     for (cudaEvent_t e : p.timer.pool) cudaEventDestroy(e);
     p.timer.pool.clear();
     if (p.tables_base) cudaFree(p.tables_base);

@@ -64,6 +64,13 @@ struct PlanView {
     // float4 (y1, y2, k as int bits, 0), segments of order index m from segoff[m].
     const float4 *seeds;
     const unsigned long long *segoff;
+    // FP64 plans: the same states as (y1, y2) and k, [segment][npairs].
+    const double2 *seeds64;
+    const int *seeds64k;
+    // Static polar optimisation (Sec. 3.1): per (order index m, pair) the
+    // first kSeedSeg-degree segment holding a |P_n^m| at or above the
+    // threshold (the segment count when none does), [mmax+1][npairs].
+    const unsigned short *live;
 };
 
 // The FP32 Legendre kernels restart the recurrence of Sec. 3.2 every kSeedSeg
@@ -71,6 +78,8 @@ struct PlanView {
 // carried in the exponent-scaled form of Sec. 3.5 (y * 2^(-64 k)), so that
 // FP32 rounding errors accumulate over at most kSeedSeg steps.
 constexpr int kSeedSeg = 32;
+// Analysis shape code (TunedShape::analys_lpt) of the FP64 warp-per-segment kernel.
+constexpr int kAnalysSeg = 32;
 
 // First packed index of order index k (order m = k mres): the degrees of the
 // orders before it, sum_{k' < k} (lmax - k' mres + 1).
@@ -157,7 +166,15 @@ struct Plan {
     int *d_c0o_s = nullptr, *d_c0o_a = nullptr; // on-the-fly mode: first live chunk per (m, tile)
     int otf_state = 0;                          // 0 not built, 1 built, -1 not supported for this plan
     float4 *seeds32 = nullptr;                  // FP32 recurrence restart states (kSeedSeg), built on first use
-    unsigned long long *d_seg32 = nullptr;      // ... first segment of each order index
+    unsigned long long *d_seg32 = nullptr;      // first kSeedSeg segment of each order index (both precisions)
+    double2 *seeds64 = nullptr;                 // FP64 restart states (y1, y2) ...
+    int *seeds64k = nullptr;                    // ... and their exponent counters
+    unsigned short *live32 = nullptr, *live64 = nullptr;   // first live segment per (m, pair), per precision
+    bool polar_thr_set = false;                 // sht_set_polar_threshold was called
+    // thresholds of the static polar optimisation of the CUDA-core kernels:
+    // the set value, else 2^-40 (FP32) and 2^-64 (FP64, below the rounding of its sums)
+    float thr_cc32() const { return polar_thr_set ? polar_thr : 0x1p-40f; }
+    float thr_cc64() const { return polar_thr_set ? polar_thr : 0x1p-64f; }
     double otf_skip_s = 0, otf_skip_a = 0;      // on-the-fly mode: fraction of chunks skipped
     void *work = nullptr;            // scratch (grown on demand)
     size_t work_bytes = 0;
@@ -172,14 +189,20 @@ struct Plan {
 // Host plan construction (plan.cpp).
 int plan_build(Plan &p, std::string &err);
 void plan_free(Plan &p);
-// Builds the FP32 recurrence restart states of a plan once (16 B per pair
-// and kSeedSeg degrees: (lmax+1)^2 npairs / 4 bytes, 138 MB at lmax = 1023);
-// SHT status, message in err.
+// Builds the recurrence restart states of a plan once, with the first-live
+// table of the static polar optimisation: FP32 (16 B per pair and kSeedSeg
+// degrees, (lmax+1)^2 npairs / 4 bytes, 138 MB at lmax = 1023) or FP64
+// (20 B, 175 MB at lmax = 1023).  SHT status, message in err.
 int plan_seeds32(Plan &p, std::string &err);
+int plan_seeds64(Plan &p, std::string &err);
+// Recomputes the first-live tables that exist (threshold change).
+int plan_relive(Plan &p, std::string &err);
 // Segment offsets of kSeedSeg degrees per order index; returns the total.
 size_t seed_segment_offsets(int lmax, int mmax, int mres, std::vector<unsigned long long> &segoff);
-cudaError_t launch_build_seeds32(const PlanView<double> &pv, const unsigned long long *segoff, float4 *seeds,
-                                 cudaStream_t st);
+// One thread per (m, pair): FP32 states (seeds32) or FP64 states (seeds64,
+// seeds64k), and the first segment holding |P| >= thr (thr <= 0: segment 0).
+cudaError_t launch_build_restarts(const PlanView<double> &pv, const unsigned long long *segoff, float4 *seeds32,
+                                  double2 *seeds64, int *seeds64k, unsigned short *live, double thr, cudaStream_t st);
 
 // Launchers (legendre.cu, fft.cu).  `eo` / `sd` are intermediate buffers of
 // [batch][mmax+1][npairs][2] complex values of precision T.

@@ -275,9 +275,19 @@ __global__ void k_colscale(const double *__restrict__ x, size_t per_field, int *
     const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
     unsigned long long mx = 0;
     if ((per_field & 1) == 0 && (reinterpret_cast<uintptr_t>(xb) & 15) == 0) {
-        // 16-byte loads when the field starts on a 16-byte boundary
+        // 16-byte loads when the field starts on a 16-byte boundary, four in
+        // flight per thread
         const ulonglong2 *x2 = reinterpret_cast<const ulonglong2 *>(xb);
-        for (size_t i = i0; i < per_field / 2; i += stride) {
+        const size_t n2 = per_field / 2;
+        size_t i = i0;
+        for (; i + 3 * stride < n2; i += 4 * stride) {
+            ulonglong2 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = x2[i + u * stride];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) mx = max(mx, max(v[u].x & kAbs, v[u].y & kAbs));
+        }
+        for (; i < n2; i += stride) {
             const ulonglong2 v = x2[i];
             mx = max(mx, max(v.x & kAbs, v.y & kAbs));
         }

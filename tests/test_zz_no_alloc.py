@@ -13,8 +13,8 @@ library.  These tests call it through the C ABI and check that
 * on a handle that has never run another transform, the device's free memory
   is the same before and after two calls (after one warm-up call, which may
   load the kernels' code), and the results still equal sht_synth's;
-* calls too large for the array, and FP32 calls on a plan whose FP32
-  restart states were never built, are refused on the host.
+* calls too large for the array, and calls on a plan whose restart states
+  (and, in FP64, polar table) were never built, are refused on the host.
 
 The file is named so that pytest collects it last.
 """
@@ -70,10 +70,9 @@ def test_static_synthesis_on_a_fresh_handle_allocates_nothing(C, prec):
     try:
         a = [torch.from_numpy(synthetic.spectrum(lmax, batch=batch, seed=s)).to(DEV, cdt) for s in (5, 6)]
         got = [torch.full((batch, nlat, nphi), float("nan"), dtype=rdt, device=DEV) for _ in a]
-        if prec == "f32":
-            with pytest.raises(C.SHTError):                 # restart states not built yet
-                C.sht_synth_static(h, a[0].data_ptr(), got[0].data_ptr(), batch, mode, stream)
-            C.sht_reserve(h, 1, mode)                       # builds them (and a 1-field scratch)
+        with pytest.raises(C.SHTError):                     # restart states not built yet
+            C.sht_synth_static(h, a[0].data_ptr(), got[0].data_ptr(), batch, mode, stream)
+        C.sht_reserve(h, 1, mode)                           # builds them (and a 1-field scratch)
         # a first call may load the kernels' code (lazy module loading takes
         # device memory for it); the allocation-free property is about the calls
         C.sht_synth_static(h, a[1].data_ptr(), got[0].data_ptr(), batch, mode, stream)
