@@ -298,14 +298,34 @@ int ensure_panels64(sht::Plan &p)
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(p.p64_s); cudaFree(p.p64_a); cudaFree(p.d_off64_s); cudaFree(p.d_off64_a); cudaFree(p.d_dchunk64);
-        cudaFree(p.d_e64_s); cudaFree(p.d_e64_a); cudaFree(p.d_c064_s); cudaFree(p.d_c064_a); cudaFree(p.d_fcol);
-        p.p64_s = p.p64_a = nullptr;
-        p.d_off64_s = p.d_off64_a = p.d_dchunk64 = nullptr;
-        p.d_e64_s = p.d_e64_a = p.d_c064_s = p.d_c064_a = p.d_fcol = nullptr;
+        sht::plan_free_tc64(p);
         return fail(SHT_ENOMEM, std::string("building the digit-slice panels: ") + cudaGetErrorString(e));
     }
     p.nchunk64_s = nch;
+    {
+        // balanced work lists of the persistent contraction, two CTAs per SM
+        int dev = 0, sms = 0;
+        std::vector<int> c0s((size_t)(p.mmax + 1) * T_s), c0a((size_t)(p.mmax + 1) * T_a), ss, sa;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaMemcpy(c0s.data(), p.d_c064_s, sizeof(int) * c0s.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(c0a.data(), p.d_c064_a, sizeof(int) * c0a.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) {
+            sms *= sht::tc64_ctas_per_sm();
+            sht::tc64_schedule(p.lmax, p.mmax, p.mres, p.npairs, true, c0s, sms, ss);
+            sht::tc64_schedule(p.lmax, p.mmax, p.mres, p.npairs, false, c0a, sms, sa);
+            e = cudaMalloc(&p.d_sched64_s, sizeof(int) * ss.size());
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&p.d_sched64_a, sizeof(int) * sa.size());
+        if (e == cudaSuccess) e = cudaMemcpy(p.d_sched64_s, ss.data(), sizeof(int) * ss.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p.d_sched64_a, sa.data(), sizeof(int) * sa.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            sht::plan_free_tc64(p);
+            return fail(SHT_ENOMEM, std::string("scheduling the digit-slice contraction: ") + cudaGetErrorString(e));
+        }
+        p.sched64_ctas = sms;
+    }
     // fractions of the digit chunks skipped as all-zero (whole chunks per (m, tile))
     if (sht::tc_polar_stats(p.lmax, p.mmax, p.mres, p.npairs, p.d_c064_s, p.d_c064_a, p.skip64_s, p.skip64_a) !=
         cudaSuccess) {
@@ -684,7 +704,7 @@ int run_tc64(sht::Plan &p, bool synth, const void *in_, void *out_, int batch, s
             double *out = static_cast<double *>(out_) + (size_t)b0 * grid_n;
             rc = timed(p, SHT_K_TC_SYNTH, s, "FP64 tensor-core synthesis launch", [&] {
                 return sht::launch_tc64(true, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.p64_s, p.d_off64_s, p.d_c064_s,
-                                        p.d_e64_s, p.d_dchunk64, p.d_fcol, data, in, inter, nb, op, p.d_err, s);
+                                        p.d_sched64_s, p.sched64_ctas, p.d_e64_s, p.d_dchunk64, p.d_fcol, data, in, inter, nb, op, p.d_err, s);
             });
             if (rc) return rc;
             rc = timed(p, SHT_K_FFT_SYNTH, s, "fft synthesis launch",
@@ -700,7 +720,7 @@ int run_tc64(sht::Plan &p, bool synth, const void *in_, void *out_, int batch, s
             if (rc) return rc;
             rc = timed(p, SHT_K_TC_ANALYS, s, "FP64 tensor-core analysis launch", [&] {
                 return sht::launch_tc64(false, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.p64_a, p.d_off64_a, p.d_c064_a,
-                                        p.d_e64_a, p.d_dchunk64, p.d_fcol, data, inter, out, nb, op,
+                                        p.d_sched64_a, p.sched64_ctas, p.d_e64_a, p.d_dchunk64, p.d_fcol, data, inter, out, nb, op,
                                         p.d_err, s, true);
             });
         }

@@ -385,6 +385,18 @@ int plan_relive(Plan &p, std::string &err)
     return SHT_OK;
 }
 
+void plan_free_tc64(Plan &p)
+{
+    cudaFree(p.p64_s); cudaFree(p.p64_a); cudaFree(p.d_off64_s); cudaFree(p.d_off64_a); cudaFree(p.d_dchunk64);
+    cudaFree(p.d_e64_s); cudaFree(p.d_e64_a); cudaFree(p.d_c064_s); cudaFree(p.d_c064_a); cudaFree(p.d_fcol);
+    cudaFree(p.d_sched64_s); cudaFree(p.d_sched64_a);
+    p.p64_s = p.p64_a = nullptr;
+    p.d_off64_s = p.d_off64_a = p.d_dchunk64 = nullptr;
+    p.d_e64_s = p.d_e64_a = p.d_c064_s = p.d_c064_a = p.d_fcol = nullptr;
+    p.d_sched64_s = p.d_sched64_a = nullptr;
+    p.sched64_ctas = 0;
+}
+
 void plan_free(Plan &p)
 {
     cudaFree(p.seeds32);
@@ -409,12 +421,7 @@ void plan_free(Plan &p)
     if (p.d_dchunk) cudaFree(p.d_dchunk);
     if (p.d_c0_s) cudaFree(p.d_c0_s);
     if (p.d_c0_a) cudaFree(p.d_c0_a);
-    cudaFree(p.p64_s); cudaFree(p.p64_a); cudaFree(p.d_off64_s); cudaFree(p.d_off64_a); cudaFree(p.d_dchunk64);
-    p.d_dchunk64 = nullptr;
-    cudaFree(p.d_e64_s); cudaFree(p.d_e64_a); cudaFree(p.d_c064_s); cudaFree(p.d_c064_a); cudaFree(p.d_fcol);
-    p.p64_s = p.p64_a = nullptr;
-    p.d_off64_s = p.d_off64_a = nullptr;
-    p.d_e64_s = p.d_e64_a = p.d_c064_s = p.d_c064_a = p.d_fcol = nullptr;
+    plan_free_tc64(p);
     if (p.d_gf_s) cudaFree(p.d_gf_s);
     if (p.d_gf_a) cudaFree(p.d_gf_a);
     p.d_gf_s = p.d_gf_a = nullptr;

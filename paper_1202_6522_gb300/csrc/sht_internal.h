@@ -159,6 +159,8 @@ struct Plan {
     size_t nchunk64_s = 0;                                // ... synthesis data chunks over all orders
     int *d_e64_s = nullptr, *d_e64_a = nullptr;           // ... row exponents
     int *d_c064_s = nullptr, *d_c064_a = nullptr;         // ... first nonzero chunk per (m, tile)
+    int *d_sched64_s = nullptr, *d_sched64_a = nullptr;   // ... work lists of the persistent contraction
+    int sched64_ctas = 0;                                 // ... and their CTA count
     int *d_fcol = nullptr;                                // ... field exponents of a launch
     double skip64_s = -1, skip64_a = -1;                  // ... fractions of all-zero digit chunks
     float4 *otf_seeds = nullptr;                // on-the-fly mode: recurrence seeds
@@ -189,6 +191,8 @@ struct Plan {
 // Host plan construction (plan.cpp).
 int plan_build(Plan &p, std::string &err);
 void plan_free(Plan &p);
+// Frees the FP64-accurate tensor-core mode's tables (digit panels, exponents, work lists).
+void plan_free_tc64(Plan &p);
 // Builds the recurrence restart states of a plan once, with the first-live
 // table of the static polar optimisation: FP32 (16 B per pair and kSeedSeg
 // degrees, (lmax+1)^2 npairs / 4 bytes, 138 MB at lmax = 1023) or FP64
@@ -328,6 +332,7 @@ int tc_max_batch();
 // contraction.  Synthesis: FP64 spectra -> E/O (double4 [b][m][pair]);
 // analysis: FP64 s/d folds -> spectra.
 int tc64_max_batch();
+int tc64_ctas_per_sm();   // resident CTAs per SM of the persistent contraction
 // Byte offsets of each order's digit-slice panel chunks (synthesis, analysis),
 // total bytes, and the first synthesis data chunk of each order.
 void tc64_panel_layout(int lmax, int mmax, int mres, int npairs, std::vector<unsigned long long> &off_s,
@@ -338,8 +343,12 @@ cudaError_t tc64_build(const PlanView<double> &pv, const unsigned long long *off
                        unsigned char *ps, unsigned char *pa, int *es, int *ea, int *c0_s, int *c0_a, cudaStream_t st);
 // fcol_ready: fcol already holds the field exponents of `in` (else this
 // computes them first).
+// Work lists of the persistent FP64-accurate contraction for nctas CTAs
+// (tc64_ctas_per_sm per SM) from the first nonzero chunks c0 [mmax+1][tiles].
+void tc64_schedule(int lmax, int mmax, int mres, int npairs, bool synth, const std::vector<int> &c0, int nctas,
+                   std::vector<int> &sched);
 cudaError_t launch_tc64(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const unsigned char *panel,
-                        const unsigned long long *off, const int *c0, const int *erow,
+                        const unsigned long long *off, const int *c0, const int *sched, int nctas, const int *erow,
                         const unsigned long long *dchunk, int *fcol, unsigned char *data, const double *in,
                         double *out, int batch, Op op, int *err, cudaStream_t st, bool fcol_ready = false);
 // Sets fcol[0 .. batch) to "no value yet" before a producer raises it.

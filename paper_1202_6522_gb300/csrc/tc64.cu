@@ -26,15 +26,18 @@
 // That is kSA MMAs per parity and chunk (N = 32 (kL - i)), 14 per chunk.
 // The accumulators are zeroed once and every MMA accumulates.
 //
-// CTA: one (order m, 128-row tile, parity of n - m), 192 threads: warps 0-3
-// run the epilogue, warp 4 lane 0 issues the MMAs, warp 5 lane 0 streams the
-// parity's 28 KB of each panel chunk and its 8 KB of data by bulk copy into 3
-// stages.  Tensor memory: kL levels x 32 columns (16 fields x re/im) = 256, so
-// two CTAs share an SM.  Every wait is bounded.
+// Work item: one (order m, 128-row tile, parity of n - m).  Two persistent
+// CTAs per SM walk balanced lists of items with 192 threads: warps 0-3 run the
+// epilogue, warp 4 lane 0 issues the MMAs, warp 5 lane 0 streams the parity's
+// 28 KB of each panel chunk and its 8 KB of data by bulk copy into a ring of 3
+// stages that runs on across items.  Tensor memory: kL levels x 32 columns (16
+// fields x re/im) = 256 per CTA.  Every wait is bounded; a kernel whose wait
+// gave up records SHT_ETIMEOUT and skips the rest of its output.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <vector>
 
@@ -62,12 +65,15 @@ constexpr int kDRows = kSB * kNC;              // data rows per class: slices st
 constexpr int kDBlk = kDRows * kKc * 2;        // 6 KB
 constexpr int kDChunk = 2 * kDBlk;             // data chunk: [class] blocks = 12 KB
 constexpr int kStage = kPPar + kDBlk;          // one parity: 36 KB
-constexpr int kStages = 3;
+constexpr int kStages = 3;                     // two CTAs per SM: 2 x 108 KB of ring
+constexpr int kCtasPerSm = 2;                  // two MMA chains per SM (each MMA of a chunk accumulates
+                                               // onto the previous one's columns, so one chain waits out
+                                               // every MMA's latency)
 constexpr int kThreads = 192;
 constexpr int kL = kSB;                        // accumulated levels t = i + j < kL
 constexpr int kLevelCols = kNC;                // accumulator columns per level
 constexpr int kParCols = kL * kLevelCols;      // accumulator columns of a CTA: 256
-constexpr uint32_t kTmemCols = kParCols;
+constexpr uint32_t kTmemCols = kParCols;       // one accumulator per CTA: half of tensor memory
 constexpr int kExpNone = INT_MIN / 2;          // exponent of an all-zero row or column
 
 // Panel slice block of (slice i, parity par) in a chunk.
@@ -382,37 +388,61 @@ struct Tc64Args {
     int *err;
 };
 
+// Work item w of a launch (heaviest first): parity w & 1, then order index
+// and 128-row tile.  Every role of a CTA walks the same items.
+struct Item64 {
+    int m, tile, par, L, Le, nchunks, cstart, nlive;
+    long col;
+    bool valid;
+};
+
 template <bool SYNTH>
-__global__ void __launch_bounds__(kThreads, 2) k_tc64(Tc64Args a)
+__device__ __forceinline__ Item64 item64(const Tc64Args &a, int w)
+{
+    Item64 it;
+    it.par = w & 1;
+    it.m = (w >> 1) / a.ntiles;
+    it.tile = (w >> 1) - it.m * a.ntiles;
+    it.L = a.lmax - it.m * a.mres + 1;   // m is the order index
+    it.Le = (it.L + 1) / 2;
+    it.col = col_of_mres(a.lmax, it.m, a.mres);
+    it.valid = SYNTH || it.tile * kR < it.Le;
+    it.nchunks = SYNTH ? (it.Le + kKc - 1) / kKc : (a.npairs + kKc - 1) / kKc;
+    it.cstart = it.valid ? a.c0[it.m * a.ntiles + it.tile] : 0;
+    it.nlive = it.valid ? it.nchunks - it.cstart : 0;
+    return it;
+}
+
+// Persistent contraction: kCtasPerSm CTAs per SM, each walking its list of
+// work items, the entries sched[gridDim.x + 1 + k] for k in
+// [sched[blockIdx.x], sched[blockIdx.x + 1]) (tc64_schedule).  The producer's
+// ring of kStages stages runs on across items, so the next item's first
+// chunks load while the epilogue reads the accumulator; the MMAs of item j + 1
+// start once it has.  Barriers: bar_load / bar_mma per stage (full / free),
+// bar_full / bar_free for the accumulator, bar_done for the drain.
+template <bool SYNTH>
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_tc64(Tc64Args a, const int *__restrict__ sched)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     uint64_t *bar_load = reinterpret_cast<uint64_t *>(smem + (size_t)kStages * kStage);
     uint64_t *bar_mma = bar_load + kStages;
-    uint64_t *bar_done = bar_mma + kStages;
+    uint64_t *bar_full = bar_mma + kStages;
+    uint64_t *bar_free = bar_full + 1;
+    uint64_t *bar_done = bar_free + 1;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_done + 1);
     __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    const int par = blockIdx.x & 1;
-    const int m = (blockIdx.x >> 1) / a.ntiles;
-    const int tile = (blockIdx.x >> 1) - m * a.ntiles;
-    const int lmax = a.lmax, npairs = a.npairs;
-    const int L = lmax - m * a.mres + 1, Le = (L + 1) / 2;   // m is the order index
-    const long col = col_of_mres(lmax, m, a.mres);
-    if (!SYNTH && tile * kR >= Le) return;
-    const int nchunks = SYNTH ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
-    const unsigned char *panel = a.panel + a.off[m] + (size_t)tile * nchunks * kPChunk;
-    const unsigned char *data =
-        a.data + (SYNTH ? a.dchunk[m] : (unsigned long long)m * nchunks) * (unsigned long long)kDChunk;
-    const int cstart = a.c0[m * a.ntiles + tile];
-    const int nlive = nchunks - cstart;
+    const int k0 = sched[blockIdx.x], k1 = sched[blockIdx.x + 1];
+    const int *items = sched + gridDim.x + 1;
 
     if (tid == 0) {
         for (int q = 0; q < kStages; ++q) {
             tc::mbar_init(&bar_load[q], 1);
             tc::mbar_init(&bar_mma[q], 1);
         }
+        tc::mbar_init(bar_full, 1);
+        tc::mbar_init(bar_free, 4);   // one arrival per epilogue warp
         tc::mbar_init(bar_done, 1);
         tc::mbar_fence_init();
         s_abort = 0;
@@ -422,16 +452,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc64(Tc64Args a)
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
-    if (warp < 4) {
-        // zero this warp's lanes of every accumulator column; the MMAs all accumulate
-        const uint32_t zero8[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-        for (int c = 0; c < kParCols; c += 8)
-            tc::tmem_st8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, zero8);
-        tc::tmem_wait_st();
-    }
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::tc_fence_after();
 
     if (warp == 4) {
         if (lane == 0) {
@@ -446,77 +466,96 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc64(Tc64Args a)
             db = tc::smem_desc(smem + kPPar, kLbo, kSbo);
             const uint64_t sstep = (uint64_t)kStage >> 4;
             bool ok = true;
-            for (int u = 0; u < nlive; ++u) {
-                const int q = u % kStages;
-                if (!wait_or_abort(&bar_load[q], (uint32_t)((u / kStages) & 1), &s_abort)) { ok = false; break; }
+            unsigned u = 0, j = 0;
+            for (int kk = k0; ok && kk < k1; ++kk) {
+                const Item64 it = item64<SYNTH>(a, items[kk]);
+                if (!it.valid) continue;
+                if (j >= 1 && !wait_or_abort(bar_free, (j - 1) & 1, &s_abort)) { ok = false; break; }
                 tc::tc_fence_after();
-                const uint64_t so = sstep * (uint64_t)q;
+                const uint32_t acc = tmem;
+                for (int c = 0; c < it.nlive; ++c, ++u) {
+                    const unsigned q = u % kStages;
+                    if (!wait_or_abort(&bar_load[q], (u / kStages) & 1, &s_abort)) { ok = false; break; }
+                    tc::tc_fence_after();
+                    const uint64_t so = sstep * (uint64_t)q;
+                    // slice 0 spans every level: its first MMA of the item overwrites them
 #pragma unroll
-                for (int i = 0; i < kSA; ++i)
-                    tc::mma_bf16(tmem + (uint32_t)(i * kLevelCols), da[i] + so, db + so, idesc[i], true);
-                tc::mma_commit(&bar_mma[q]);
+                    for (int i = 0; i < kSA; ++i)
+                        tc::mma_bf16(acc + (uint32_t)(i * kLevelCols), da[i] + so, db + so, idesc[i], c > 0 || i > 0);
+                    tc::mma_commit(&bar_mma[q]);
+                }
+                if (!ok) break;
+                tc::mma_commit(bar_full);
+                ++j;
             }
             if (!ok) raise_err(a.err, SHT_ETIMEOUT);
+            // drain: no MMA may still write tensor memory when it is freed
             tc::mma_commit(bar_done);
+            (void)tc::mbar_wait_bounded(bar_done, 0, 100000000ull);
         }
     } else if (warp == 5) {
         if (lane == 0) {
             // ---------------- producer ----------------
             bool ok = true;
-            int issued = 0;
-            for (int u = 0; u < nlive; ++u) {
-                const int q = u % kStages;
-                const int c = cstart + u;
-                if (u >= kStages && !wait_or_abort(&bar_mma[q], (uint32_t)((u / kStages - 1) & 1), &s_abort)) {
-                    ok = false;
-                    break;
+            unsigned u = 0;
+            for (int kk = k0; ok && kk < k1; ++kk) {
+                const Item64 it = item64<SYNTH>(a, items[kk]);
+                if (!it.valid) continue;
+                const unsigned char *panel =
+                    a.panel + a.off[it.m] + (size_t)it.tile * it.nchunks * kPChunk + (size_t)it.par * kPPar;
+                const unsigned char *data =
+                    a.data + (SYNTH ? a.dchunk[it.m] : (unsigned long long)it.m * it.nchunks) *
+                                 (unsigned long long)kDChunk + (size_t)it.par * kDBlk;
+                for (int c = it.cstart; c < it.nchunks; ++c, ++u) {
+                    const unsigned q = u % kStages;
+                    if (u >= kStages && !wait_or_abort(&bar_mma[q], (u / kStages - 1) & 1, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *st = smem + (size_t)q * kStage;
+                    tc::mbar_arrive_expect_tx(&bar_load[q], (uint32_t)kStage);
+                    tc::bulk_g2s_stream(st, panel + (size_t)c * kPChunk, (uint32_t)kPPar, &bar_load[q]);
+                    tc::bulk_g2s(st + kPPar, data + (size_t)c * kDChunk, (uint32_t)kDBlk, &bar_load[q]);
                 }
-                unsigned char *st = smem + (size_t)q * kStage;
-                tc::mbar_arrive_expect_tx(&bar_load[q], (uint32_t)kStage);
-                tc::bulk_g2s_stream(st, panel + (size_t)c * kPChunk + (size_t)par * kPPar, (uint32_t)kPPar, &bar_load[q]);
-                tc::bulk_g2s(st + kPPar, data + (size_t)c * kDChunk + (size_t)par * kDBlk, (uint32_t)kDBlk,
-                             &bar_load[q]);
-                issued = u + 1;
             }
             if (!ok) {
                 raise_err(a.err, SHT_ETIMEOUT);
-                for (int v = issued > kStages ? issued - kStages : 0; v < issued; ++v)
-                    (void)tc::mbar_wait_bounded(&bar_load[v % kStages], (uint32_t)((v / kStages) & 1), 100000000ull);
+                // wait (bounded) for the copies still in flight
+                for (unsigned v = u > kStages ? u - kStages : 0; v < u; ++v)
+                    (void)tc::mbar_wait_bounded(&bar_load[v % kStages], (v / kStages) & 1, 100000000ull);
             }
         }
-    }
-    bool ok = true;
-    if (warp < 4) {
-        ok = wait_or_abort(bar_done, 0, &s_abort);
-        if (!ok) {
-            (void)tc::mbar_wait_bounded(bar_done, 0, 100000000ull);
-            raise_err(a.err, SHT_ETIMEOUT);
-        }
-    }
-    ok = __syncthreads_and(ok && !*(volatile int *)&s_abort);
-    if (ok && warp < 4) {
-        // ---------------- epilogue ----------------
-        tc::tc_fence_after();
-        const int row = tile * kR + warp * 32 + lane;
+    } else {
+        // ---------------- epilogue (warps 0-3: TMEM lanes 32 warp ..) ----------------
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-        const int sc_log2 = (!SYNTH && a.op == OP_SYNTH_ADJ && m > 0) ? 1 : 0;   // adjoint factor 2
-        {
+        unsigned j = 0;
+        for (int kk = k0; kk < k1; ++kk) {
+            const Item64 it = item64<SYNTH>(a, items[kk]);
+            if (!it.valid) continue;
+            if (!wait_or_abort(bar_full, j & 1, &s_abort)) {
+                raise_err(a.err, SHT_ETIMEOUT);
+                break;
+            }
+            tc::tc_fence_after();
+            ++j;
+            const int row = it.tile * kR + warp * 32 + lane;
+            const int sc_log2 = (!SYNTH && a.op == OP_SYNTH_ADJ && it.m > 0) ? 1 : 0;   // adjoint factor 2
             // row exponent: synthesis per (m, pair), analysis per (m, n)
-            const int nn = 2 * row + par;
+            const int nn = 2 * row + it.par;
             int e_row = kExpNone;
             if (SYNTH) {
-                if (row < npairs) e_row = a.erow[(size_t)m * npairs + row];
+                if (row < a.npairs) e_row = a.erow[(size_t)it.m * a.npairs + row];
             } else {
-                if (nn < L) e_row = a.erow[col + nn];
+                if (nn < it.L) e_row = a.erow[it.col + nn];
             }
 #pragma unroll 1
             for (int h = 0; h < kNC / 16; ++h) {
-                // Z = sum_t L_t 2^(7 (kL - 1 - t)) = Zh 2^28 + Zl, levels split so that
-                // both parts stay exact in 64-bit integers and in doubles (< 2^48)
+                // Z = sum_t L_t 2^(7 (kL - 1 - t)) = Zh 2^28 + Zl per column, levels
+                // split so that both parts stay exact in 64-bit integers (< 2^48)
                 long long Zh[16], Zl[16];
 #pragma unroll
                 for (int k = 0; k < 16; ++k) Zh[k] = Zl[k] = 0;
-                if (nlive > 0) {
+                if (it.nlive > 0) {
 #pragma unroll
                     for (int t = 0; t < kL; ++t) {
                         float v[16];
@@ -528,6 +567,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc64(Tc64Args a)
                             else Zl[k] += L << (7 * (kL - 1 - t));
                         }
                     }
+                }
+                if (h == kNC / 16 - 1) {
+                    // the accumulator is read: the next item's MMAs may overwrite it
+                    tc::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(bar_free);
                 }
 #pragma unroll
                 for (int k = 0; k < 16; k += 2) {
@@ -542,13 +587,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc64(Tc64Args a)
                     const double re = zero ? 0.0 : i128_ldexp(zr, sh);
                     double im = zero ? 0.0 : i128_ldexp(zi, sh);
                     if (SYNTH) {
-                        if (row < npairs) {
+                        if (row < a.npairs) {
                             double2 *eo = reinterpret_cast<double2 *>(a.out);
-                            eo[(((size_t)b * (a.mmax + 1) + m) * npairs + row) * 2 + par] = make_double2(re, im);
+                            eo[(((size_t)b * (a.mmax + 1) + it.m) * a.npairs + row) * 2 + it.par] =
+                                make_double2(re, im);
                         }
                     } else {
-                        if (m == 0) im = 0.0;
-                        if (nn < L) reinterpret_cast<double2 *>(a.out)[(size_t)b * a.nlm + col + nn] = make_double2(re, im);
+                        if (it.m == 0) im = 0.0;
+                        if (nn < it.L)
+                            reinterpret_cast<double2 *>(a.out)[(size_t)b * a.nlm + it.col + nn] = make_double2(re, im);
                     }
                 }
             }
@@ -562,6 +609,42 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc64(Tc64Args a)
 }  // namespace
 
 int tc64_max_batch() { return kBatch64; }
+int tc64_ctas_per_sm() { return kCtasPerSm; }
+
+// Work lists of the persistent contraction: the items (order index, tile,
+// parity) that hold rows, costed as their nonzero chunks plus two for the
+// epilogue, heaviest first, each given to the CTA with the least work so far
+// (longest-processing-time first).  sched = [nctas + 1 offsets | items].
+void tc64_schedule(int lmax, int mmax, int mres, int npairs, bool synth, const std::vector<int> &c0, int nctas,
+                   std::vector<int> &sched)
+{
+    int ts, ta;
+    tc_tile_counts(lmax, npairs, ts, ta);
+    const int ntiles = synth ? ts : ta;
+    std::vector<std::pair<int, int>> cost;   // (cost, item)
+    for (int w = 0; w < 2 * (mmax + 1) * ntiles; ++w) {
+        const int m = (w >> 1) / ntiles, tile = (w >> 1) - m * ntiles;
+        const int L = lmax - m * mres + 1, Le = (L + 1) / 2;
+        if (!synth && tile * kR >= Le) continue;
+        const int nchunks = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
+        cost.push_back({nchunks - c0[(size_t)m * ntiles + tile] + 2, w});
+    }
+    std::stable_sort(cost.begin(), cost.end(), [](const std::pair<int, int> &x, const std::pair<int, int> &y) {
+        return x.first > y.first;
+    });
+    std::vector<long long> load(nctas, 0);
+    std::vector<std::vector<int>> lists(nctas);
+    for (const auto &c : cost) {
+        int best = 0;
+        for (int i = 1; i < nctas; ++i)
+            if (load[i] < load[best]) best = i;
+        load[best] += c.first;
+        lists[best].push_back(c.second);
+    }
+    sched.assign(nctas + 1, 0);
+    for (int i = 0; i < nctas; ++i) sched[i + 1] = sched[i] + (int)lists[i].size();
+    for (int i = 0; i < nctas; ++i) sched.insert(sched.end(), lists[i].begin(), lists[i].end());
+}
 
 cudaError_t tc64_reset_fcol(int *fcol, int batch, cudaStream_t st)
 {
@@ -620,7 +703,7 @@ cudaError_t tc64_build(const PlanView<double> &pv, const unsigned long long *off
 }
 
 cudaError_t launch_tc64(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const unsigned char *panel,
-                        const unsigned long long *off, const int *c0, const int *erow,
+                        const unsigned long long *off, const int *c0, const int *sched, int nctas, const int *erow,
                         const unsigned long long *dchunk, int *fcol, unsigned char *data, const double *in,
                         double *out, int batch, Op op, int *err, cudaStream_t st, bool fcol_ready)
 {
@@ -657,17 +740,18 @@ cudaError_t launch_tc64(bool synth, int lmax, int mmax, int mres, int npairs, in
     int ts, ta;
     tc_tile_counts(lmax, npairs, ts, ta);
     a.ntiles = synth ? ts : ta;
-    const size_t smem = 128 + (size_t)kStages * kStage + 8 * (2 * kStages + 1) + 16;
-    const unsigned blocks = (unsigned)(2 * (mmax + 1) * a.ntiles);   // x parity
+    // ring, barriers (2 per stage, 2 for the accumulator, the drain) and the TMEM slot
+    const size_t smem = 128 + (size_t)kStages * kStage + 8 * (2 * kStages + 3) + 16;
+    if (!sched || nctas < 1) return cudaErrorInvalidValue;
     cudaError_t e;
     if (synth) {
         e = cudaFuncSetAttribute(k_tc64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_tc64<true><<<blocks, kThreads, smem, st>>>(a);
+        k_tc64<true><<<(unsigned)nctas, kThreads, smem, st>>>(a, sched);
     } else {
         e = cudaFuncSetAttribute(k_tc64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_tc64<false><<<blocks, kThreads, smem, st>>>(a);
+        k_tc64<false><<<(unsigned)nctas, kThreads, smem, st>>>(a, sched);
     }
     return cudaGetLastError();
 }
