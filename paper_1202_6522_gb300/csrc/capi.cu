@@ -138,6 +138,38 @@ void free_vec_panels(sht::Plan &p)
     cudaFree(p.dpanel_s); cudaFree(p.dpanel_a); cudaFree(p.d_c0v_s); cudaFree(p.d_c0v_a);
     p.dpanel_s = p.dpanel_a = nullptr;
     p.d_c0v_s = p.d_c0v_a = nullptr;
+    for (int h = 0; h < 2; ++h) {
+        cudaFree(p.d_schedv_s[h]);
+        cudaFree(p.d_schedv_a[h]);
+        p.d_schedv_s[h] = p.d_schedv_a[h] = nullptr;
+    }
+    p.schedv_ctas = 0;
+}
+
+// Work lists of the persistent vector contraction (one CTA per SM) for one
+// and two field halves, from the current first-live chunks; rebuilt when
+// the polar threshold changes (the lists only balance the work).
+cudaError_t vec_schedules(sht::Plan &p)
+{
+    int T_s = 0, T_a = 0, dev = 0, sms = 0;
+    sht::tc_tile_counts(p.lmax, p.npairs, T_s, T_a);
+    std::vector<int> c0s((size_t)(p.mmax + 1) * T_s), c0a((size_t)(p.mmax + 1) * T_a), cost, sc;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaMemcpy(c0s.data(), p.d_c0v_s, sizeof(int) * c0s.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(c0a.data(), p.d_c0v_a, sizeof(int) * c0a.size(), cudaMemcpyDeviceToHost);
+    for (int dir = 0; dir < 2 && e == cudaSuccess; ++dir)
+        for (int h = 0; h < 2 && e == cudaSuccess; ++h) {
+            sht::tc_vec_costs(p.lmax, p.mmax, p.mres, p.npairs, dir == 0, h + 1, dir == 0 ? c0s : c0a, cost);
+            sht::schedule_lpt(cost, sms, sc);
+            int *&d = dir == 0 ? p.d_schedv_s[h] : p.d_schedv_a[h];
+            cudaFree(d);
+            d = nullptr;
+            e = cudaMalloc(&d, sizeof(int) * sc.size());
+            if (e == cudaSuccess) e = cudaMemcpy(d, sc.data(), sizeof(int) * sc.size(), cudaMemcpyHostToDevice);
+        }
+    if (e == cudaSuccess) p.schedv_ctas = sms;
+    return e;
 }
 
 // The sin(theta) dP/dtheta panels of the vector transforms (same layouts and
@@ -171,6 +203,7 @@ int ensure_vec_panels(sht::Plan &p)
         e = sht::launch_build_panels(p.view64(), p.d_off_s, p.d_off_a, p.dpanel_s, p.dpanel_a, true, 0);
     if (e == cudaSuccess) e = first_live_vector(p, tmp);
     cudaFree(tmp);
+    if (e == cudaSuccess) e = vec_schedules(p);
     if (e != cudaSuccess) {
         free_vec_panels(p);
         return fail(SHT_ECUDA, std::string("building vector tensor-core panels: ") + cudaGetErrorString(e));
@@ -312,8 +345,11 @@ int ensure_panels64(sht::Plan &p)
         if (e == cudaSuccess) e = cudaMemcpy(c0a.data(), p.d_c064_a, sizeof(int) * c0a.size(), cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) {
             sms *= sht::tc64_ctas_per_sm();
-            sht::tc64_schedule(p.lmax, p.mmax, p.mres, p.npairs, true, c0s, sms, ss);
-            sht::tc64_schedule(p.lmax, p.mmax, p.mres, p.npairs, false, c0a, sms, sa);
+            std::vector<int> cost;
+            sht::tc64_costs(p.lmax, p.mmax, p.mres, p.npairs, true, c0s, cost);
+            sht::schedule_lpt(cost, sms, ss);
+            sht::tc64_costs(p.lmax, p.mmax, p.mres, p.npairs, false, c0a, cost);
+            sht::schedule_lpt(cost, sms, sa);
             e = cudaMalloc(&p.d_sched64_s, sizeof(int) * ss.size());
         }
         if (e == cudaSuccess) e = cudaMalloc(&p.d_sched64_a, sizeof(int) * sa.size());
@@ -779,7 +815,7 @@ int run_synth_vec_tc(sht::Plan &p, const void *S, const void *T, void *vt, void 
         const size_t so = (size_t)b0 * p.nlm * 2, go = (size_t)b0 * p.nlat * p.nphi;
         int rc = timed(p, SHT_K_TC_SYNTH_VEC, s, "tensor-core vector synthesis launch", [&] {
             return sht::launch_tc_vec(true, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.panel_s, p.dpanel_s, p.d_off_s,
-                                      p.d_c0v_s, p.d_dchunk, data, static_cast<const float *>(S) + so,
+                                      p.d_c0v_s, p.d_schedv_s, p.schedv_ctas, p.d_dchunk, data, static_cast<const float *>(S) + so,
                                       static_cast<const float *>(T) + so, eot, eop, p.t32.st, nb, op, p.d_err, false,
                                       s);
         });
@@ -817,7 +853,7 @@ int run_analys_vec_tc(sht::Plan &p, const void *vt, const void *vp, void *S, voi
         if (rc) return rc;
         rc = timed(p, SHT_K_TC_ANALYS_VEC, s, "tensor-core vector analysis launch", [&] {
             return sht::launch_tc_vec(false, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.panel_a, p.dpanel_a, p.d_off_a,
-                                      p.d_c0v_a, p.d_dchunk, data, sdt, sdp, static_cast<float *>(S) + so,
+                                      p.d_c0v_a, p.d_schedv_a, p.schedv_ctas, p.d_dchunk, data, sdt, sdp, static_cast<float *>(S) + so,
                                       static_cast<float *>(T) + so, p.t32.st, nb, op, p.d_err, false, s);
         });
         if (rc) return rc;
@@ -1069,6 +1105,7 @@ int sht_set_polar_threshold(sht_handle h, double threshold)
         e = cudaMalloc(&tmp, sizeof(int) * (size_t)(p.mmax + 1) * (T_s > T_a ? T_s : T_a));
         if (e == cudaSuccess) e = first_live_vector(p, tmp);
         cudaFree(tmp);
+        if (e == cudaSuccess) e = vec_schedules(p);
     }
     if (e == cudaSuccess && p.otf_state > 0) {
         int *flag = nullptr;

@@ -6,6 +6,7 @@
 // rounded from the FP64 values.
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 
 #include "sht_internal.h"
@@ -385,6 +386,27 @@ int plan_relive(Plan &p, std::string &err)
     return SHT_OK;
 }
 
+void schedule_lpt(const std::vector<int> &cost, int nctas, std::vector<int> &sched)
+{
+    std::vector<std::pair<int, int>> order;   // (cost, item)
+    for (int w = 0; w < (int)cost.size(); ++w)
+        if (cost[w] >= 0) order.push_back({cost[w], w});
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<int, int> &x, const std::pair<int, int> &y) { return x.first > y.first; });
+    std::vector<long long> load(nctas, 0);
+    std::vector<std::vector<int>> lists(nctas);
+    for (const auto &c : order) {
+        int best = 0;
+        for (int i = 1; i < nctas; ++i)
+            if (load[i] < load[best]) best = i;
+        load[best] += c.first;
+        lists[best].push_back(c.second);
+    }
+    sched.assign(nctas + 1, 0);
+    for (int i = 0; i < nctas; ++i) sched[i + 1] = sched[i] + (int)lists[i].size();
+    for (int i = 0; i < nctas; ++i) sched.insert(sched.end(), lists[i].begin(), lists[i].end());
+}
+
 void plan_free_tc64(Plan &p)
 {
     cudaFree(p.p64_s); cudaFree(p.p64_a); cudaFree(p.d_off64_s); cudaFree(p.d_off64_a); cudaFree(p.d_dchunk64);
@@ -425,6 +447,11 @@ void plan_free(Plan &p)
     if (p.d_gf_s) cudaFree(p.d_gf_s);
     if (p.d_gf_a) cudaFree(p.d_gf_a);
     p.d_gf_s = p.d_gf_a = nullptr;
+    for (int h = 0; h < 2; ++h) {
+        cudaFree(p.d_schedv_s[h]);
+        cudaFree(p.d_schedv_a[h]);
+        p.d_schedv_s[h] = p.d_schedv_a[h] = nullptr;
+    }
     if (p.dpanel_s) cudaFree(p.dpanel_s);
     if (p.dpanel_a) cudaFree(p.dpanel_a);
     if (p.d_c0v_s) cudaFree(p.d_c0v_s);

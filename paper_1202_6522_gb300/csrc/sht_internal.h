@@ -161,6 +161,9 @@ struct Plan {
     int *d_c064_s = nullptr, *d_c064_a = nullptr;         // ... first nonzero chunk per (m, tile)
     int *d_sched64_s = nullptr, *d_sched64_a = nullptr;   // ... work lists of the persistent contraction
     int sched64_ctas = 0;                                 // ... and their CTA count
+    int *d_schedv_s[2] = {nullptr, nullptr};              // vector contraction work lists (1 | 2 field halves)
+    int *d_schedv_a[2] = {nullptr, nullptr};
+    int schedv_ctas = 0;
     int *d_fcol = nullptr;                                // ... field exponents of a launch
     double skip64_s = -1, skip64_a = -1;                  // ... fractions of all-zero digit chunks
     float4 *otf_seeds = nullptr;                // on-the-fly mode: recurrence seeds
@@ -307,6 +310,7 @@ cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int mres, int npa
 // (theta E/O, phi E/O); analysis: (theta, phi) folds -> (S, T).
 cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const unsigned char *panel,
                           const unsigned char *dpanel, const unsigned long long *off, const int *c0,
+                          const int *const sched[2], int nctas,
                           const unsigned long long *dchunk, unsigned char *data, const float *in0, const float *in1,
                           float *out0, float *out1, const float *st_pairs, int batch, Op op, int *err, bool prepped,
                           cudaStream_t st);
@@ -343,10 +347,18 @@ cudaError_t tc64_build(const PlanView<double> &pv, const unsigned long long *off
                        unsigned char *ps, unsigned char *pa, int *es, int *ea, int *c0_s, int *c0_a, cudaStream_t st);
 // fcol_ready: fcol already holds the field exponents of `in` (else this
 // computes them first).
-// Work lists of the persistent FP64-accurate contraction for nctas CTAs
-// (tc64_ctas_per_sm per SM) from the first nonzero chunks c0 [mmax+1][tiles].
-void tc64_schedule(int lmax, int mmax, int mres, int npairs, bool synth, const std::vector<int> &c0, int nctas,
-                   std::vector<int> &sched);
+// Work lists of persistent CTAs, longest processing time first: the items
+// with cost >= 0, heaviest first, each to the CTA with the least work so far;
+// sched = [nctas + 1 offsets | items].
+void schedule_lpt(const std::vector<int> &cost, int nctas, std::vector<int> &sched);
+// Item costs of the persistent FP64-accurate contraction (item = 2 (m tiles + tile) + parity)
+// from the first nonzero chunks c0 [mmax+1][tiles].
+void tc64_costs(int lmax, int mmax, int mres, int npairs, bool synth, const std::vector<int> &c0,
+                std::vector<int> &cost);
+// Item costs of the persistent vector contraction (item = (m tiles + tile) halves + half)
+// from its first live chunks c0 [mmax+1][tiles].
+void tc_vec_costs(int lmax, int mmax, int mres, int npairs, bool synth, int halves, const std::vector<int> &c0,
+                  std::vector<int> &cost);
 cudaError_t launch_tc64(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const unsigned char *panel,
                         const unsigned long long *off, const int *c0, const int *sched, int nctas, const int *erow,
                         const unsigned long long *dchunk, int *fcol, unsigned char *data, const double *in,

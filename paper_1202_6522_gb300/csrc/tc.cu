@@ -269,6 +269,7 @@ struct TcArgs {
     const unsigned long long *dchunk;      // synthesis: first data chunk of each order
     float *out0, *out1;                    // outputs (vector: second quantity in out1)
     const float *st;                       // sin(theta) per pair (vector synthesis)
+    const int *sched;                      // vector: work lists of the persistent CTAs (schedule_lpt)
     int *err;
 };
 
@@ -637,8 +638,15 @@ __global__ void __launch_bounds__(kWsThreads, kWsCtasPerSm) k_tc_ws(TcArgs a, co
 // panel chunks the first brought into L2.
 constexpr int kVecHalf = 32;
 
+// Persistent: one CTA per SM walks its list of work items (order, tile,
+// field half), the entries sched[gridDim.x + 1 + k] for k in
+// [sched[blockIdx.x], sched[blockIdx.x + 1]) (schedule_lpt), with 192
+// threads: warps 0-3 run the epilogue, warp 4 lane 0 issues the MMAs, warp 5
+// lane 0 streams the P, dP and data chunks.  The ring of stages runs on across
+// items, so the next item's chunks load while the epilogue drains the
+// accumulators; the next item's MMAs start once the epilogue has read them.
 template <bool SYNTH>
-__global__ void __launch_bounds__(128, 1) k_tc_vec(TcArgs a)
+__global__ void __launch_bounds__(192, 1) k_tc_vec(TcArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -647,151 +655,211 @@ __global__ void __launch_bounds__(128, 1) k_tc_vec(TcArgs a)
     const size_t blk = (size_t)NV * kKc * 2;
     uint64_t *bar_load = reinterpret_cast<uint64_t *>(smem + (size_t)S * stage_bytes);
     uint64_t *bar_mma = bar_load + S;
-    uint64_t *bar_done = bar_mma + S;
+    uint64_t *bar_full = bar_mma + S;
+    uint64_t *bar_free = bar_full + 1;
+    uint64_t *bar_done = bar_free + 1;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_done + 1);
-    __shared__ int s_ok;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    const int half = blockIdx.x % a.halves;                 // fields [kVecHalf half, ...)
-    const int mt = blockIdx.x / a.halves;
-    const int m = mt / a.ntiles;
-    const int tile = mt - m * a.ntiles;
-    const int fb0 = half * kVecHalf, nbh = min(kVecHalf, a.batch - fb0);
-    const int lmax = a.lmax, npairs = a.npairs;
-    const int L = lmax - m * a.mres + 1;   // m is the order index
-    const int Le = (L + 1) / 2;
-    const long col = col_of_mres(lmax, m, a.mres);
-    if (!SYNTH && tile * kRows >= Le) return;
-    const int nchunks = SYNTH ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
-    const size_t poff = a.off[m] + (size_t)tile * nchunks * kChunkPanel;
-    const unsigned char *data = a.data + (size_t)half * a.data_half +
-                                (SYNTH ? a.dchunk[m] : (unsigned long long)m * nchunks) * data_chunk_bytes(NV);
-    const uint32_t ncols = 4 * NV <= 256 ? 256 : 512;
-    const int cstart = a.c0 ? a.c0[m * a.ntiles + tile] : 0;
-    const int nlive = nchunks - cstart;
-
-    const uint32_t tmem = setup_ctas(S, bar_load, bar_mma, bar_done, tslot, ncols, &s_ok);
     __shared__ int s_abort;
-    if (tid == 0) s_abort = 0;
-    __syncthreads();
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int k0 = a.sched[blockIdx.x], k1 = a.sched[blockIdx.x + 1];
+    const int *items = a.sched + gridDim.x + 1;
+    const uint32_t ncols = 4 * NV <= 256 ? 256 : 512;
+    const int lmax = a.lmax, npairs = a.npairs;
 
-    if (tid == 32) {
-        // ---------------- producer (warp 1 lane 0): P, dP and data chunks, S - 1 ahead ----------------
-        const unsigned char *p0 = a.panel + poff, *p1 = a.dpanel + poff;
-        const uint32_t dbytes = (uint32_t)data_chunk_bytes(NV);
-        bool okp = true;
-        int issued = 0;
-        for (int u = 0; u < nlive; ++u) {
-            const int q = u % S;
-            const size_t c = (size_t)(cstart + u);
-            if (u >= S && !wait_or_abort(&bar_mma[q], (uint32_t)((u / S - 1) & 1), &s_abort)) { okp = false; break; }
-            unsigned char *st = smem + (size_t)q * stage_bytes;
-            tc::mbar_arrive_expect_tx(&bar_load[q], 2u * kChunkPanel + dbytes);
-            tc::bulk_g2s_stream(st, p0 + c * kChunkPanel, kChunkPanel, &bar_load[q]);
-            tc::bulk_g2s_stream(st + kChunkPanel, p1 + c * kChunkPanel, kChunkPanel, &bar_load[q]);
-            tc::bulk_g2s(st + 2 * kChunkPanel, data + c * dbytes, dbytes, &bar_load[q]);
-            issued = u + 1;
+    // item w: field half w % halves, then (order index, tile)
+    struct Item {
+        int m, tile, half, L, Le, nchunks, cstart, nlive;
+        bool valid;
+    };
+    const auto item_of = [&](int w) {
+        Item it;
+        it.half = w % a.halves;
+        const int mt = w / a.halves;
+        it.m = mt / a.ntiles;
+        it.tile = mt - it.m * a.ntiles;
+        it.L = lmax - it.m * a.mres + 1;
+        it.Le = (it.L + 1) / 2;
+        it.valid = SYNTH || it.tile * kRows < it.Le;
+        it.nchunks = SYNTH ? (it.Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
+        it.cstart = it.valid && a.c0 ? a.c0[it.m * a.ntiles + it.tile] : 0;
+        it.nlive = it.valid ? it.nchunks - it.cstart : 0;
+        return it;
+    };
+
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) {
+            tc::mbar_init(&bar_load[q], 1);
+            tc::mbar_init(&bar_mma[q], 1);
         }
-        if (!okp) {
-            raise_err(a.err, SHT_ETIMEOUT);
-            s_ok = 0;
-            for (int v = max(0, issued - S); v < issued; ++v)
-                (void)tc::mbar_wait_bounded(&bar_load[v % S], (uint32_t)((v / S) & 1), 100000000ull);
-        }
-    } else if (tid == 0) {
-        // ---------------- MMA issuer (warp 0 lane 0) ----------------
-        const uint32_t idesc = tc::idesc_bf16_f32(kRows, NV);
-        bool okm = true;
-        for (int u = 0; u < nlive; ++u) {
-            const int q = u % S;
-            if (!wait_or_abort(&bar_load[q], (uint32_t)((u / S) & 1), &s_abort)) { okm = false; break; }
-            tc::tc_fence_after();
-            unsigned char *st = smem + (size_t)q * stage_bytes;
-            unsigned char *dat = st + 2 * kChunkPanel;
-            const bool first = u == 0;
-#pragma unroll
-            for (int cls = 0; cls < 2; ++cls) {
-                const int dp = SYNTH ? 1 - cls : cls;   // parity of n - m of the dP block
-                const unsigned char *aph = st + (size_t)(cls * 2) * kSbo, *apl = aph + kSbo;
-                const unsigned char *adh = st + kChunkPanel + (size_t)(dp * 2) * kSbo, *adl = adh + kSbo;
-                const unsigned char *b1h = dat + (size_t)(cls * 2) * blk, *b1l = b1h + blk;
-                const unsigned char *b2h = dat + (size_t)((1 - cls) * 2) * blk, *b2l = b2h + blk;
-                const uint32_t d1 = tmem + (uint32_t)((cls * 2 + 0) * NV);
-                const uint32_t d2 = tmem + (uint32_t)((cls * 2 + 1) * NV);
-                const uint64_t Aph = tc::smem_desc(aph, kLbo, kPSbo), Apl = tc::smem_desc(apl, kLbo, kPSbo);
-                const uint64_t Adh = tc::smem_desc(adh, kLbo, kPSbo), Adl = tc::smem_desc(adl, kLbo, kPSbo);
-                const uint64_t B1h = tc::smem_desc(b1h, kLbo, kSbo), B1l = tc::smem_desc(b1l, kLbo, kSbo);
-                const uint64_t B2h = tc::smem_desc(b2h, kLbo, kSbo), B2l = tc::smem_desc(b2l, kLbo, kSbo);
-                tc::mma_bf16(d1, Aph, B1h, idesc, !first);
-                tc::mma_bf16(d1, Aph, B1l, idesc, true);
-                tc::mma_bf16(d1, Apl, B1h, idesc, true);
-                tc::mma_bf16(d2, Adh, B2h, idesc, !first);
-                tc::mma_bf16(d2, Adh, B2l, idesc, true);
-                tc::mma_bf16(d2, Adl, B2h, idesc, true);
-            }
-            tc::mma_commit(&bar_mma[q]);
-        }
-        if (!okm) {
-            raise_err(a.err, SHT_ETIMEOUT);
-            s_ok = 0;
-        }
-        tc::mma_commit(bar_done);   // arrives once every MMA issued above has completed
+        tc::mbar_init(bar_full, 1);
+        tc::mbar_init(bar_free, 4);   // one arrival per epilogue warp
+        tc::mbar_init(bar_done, 1);
+        tc::mbar_fence_init();
+        s_abort = 0;
     }
-    bool ok = tc::mbar_wait_bounded(bar_done, 0, 2 * kWaitNs);
-    if (!ok) raise_err(a.err, SHT_ETIMEOUT);
-    ok = __syncthreads_and(ok && s_ok);
-    if (ok) {
-        tc::tc_fence_after();
-        const int row = tile * kRows + warp * 32 + lane;
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-        const float fm = (float)(m * a.mres);
-        float isn = 1.f;
-        if (SYNTH && row < npairs) isn = 1.f / a.st[row];
-        for (int cls = 0; cls < 2; ++cls) {
-            for (int cb = 0; cb < NH; cb += 32) {
-                float v[2][2][32];  // [acc][first|second quantity][col]
-#pragma unroll
-                for (int ac = 0; ac < 2; ++ac)
-#pragma unroll
-                    for (int hf = 0; hf < 2; ++hf) {
-                        if (nlive > 0) {
-                            tc::tmem_ld32(lane_base + (uint32_t)((cls * 2 + ac) * NV + hf * NH + cb), v[ac][hf]);
-                        } else {
-#pragma unroll
-                            for (int i = 0; i < 32; ++i) v[ac][hf][i] = 0.f;
-                        }
+    if (warp == 0) tc::tmem_alloc(tslot, ncols);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 5) {
+        if (lane == 0) {
+            // ---------------- producer: P, dP and data chunks ----------------
+            const uint32_t dbytes = (uint32_t)data_chunk_bytes(NV);
+            bool ok = true;
+            unsigned u = 0;
+            for (int kk = k0; ok && kk < k1; ++kk) {
+                const Item it = item_of(items[kk]);
+                if (!it.valid) continue;
+                const size_t poff = a.off[it.m] + (size_t)it.tile * it.nchunks * kChunkPanel;
+                const unsigned char *p0 = a.panel + poff, *p1 = a.dpanel + poff;
+                const unsigned char *data =
+                    a.data + (size_t)it.half * a.data_half +
+                    (SYNTH ? a.dchunk[it.m] : (unsigned long long)it.m * it.nchunks) * data_chunk_bytes(NV);
+                for (int c = it.cstart; c < it.nchunks; ++c, ++u) {
+                    const unsigned q = u % S;
+                    if (u >= (unsigned)S && !wait_or_abort(&bar_mma[q], (u / S - 1) & 1, &s_abort)) {
+                        ok = false;
+                        break;
                     }
-                for (int q = 0; q < 32; q += 2) {
-                    const int bl = (cb + q) >> 1;   // field within the half
-                    if (bl >= nbh) break;
-                    const int b = fb0 + bl;
-                    if (SYNTH) {
-                        if (row >= npairs) continue;
-                        const float psr = v[0][0][q], psi = v[0][0][q + 1];   // sum P S
-                        const float ptr = v[0][1][q], pti = v[0][1][q + 1];   // sum P T
-                        const float dsr = v[1][0][q], dsi = v[1][0][q + 1];   // sum dP S
-                        const float dtr = v[1][1][q], dti = v[1][1][q + 1];   // sum dP T
-                        const size_t oi = (((size_t)b * (a.mmax + 1) + m) * npairs + row) * 2 + cls;
-                        reinterpret_cast<float2 *>(a.out0)[oi] =
-                            make_float2((dsr + fm * pti) * isn, (dsi - fm * ptr) * isn);
-                        reinterpret_cast<float2 *>(a.out1)[oi] =
-                            make_float2((dtr - fm * psi) * isn, (dti + fm * psr) * isn);
-                    } else {
-                        const int nn = 2 * row + cls;
-                        if (nn >= L) continue;
-                        const int n = m * a.mres + nn;
-                        float sc;
-                        if (a.op == OP_SYNTH_ADJ) sc = (m > 0) ? 2.f : 1.f;
-                        else sc = (n == 0) ? 0.f : 1.f / ((float)n * (float)(n + 1));
-                        const float pthr = v[0][0][q], pthi = v[0][0][q + 1];   // P^T theta folds
-                        const float pphr = v[0][1][q], pphi = v[0][1][q + 1];   // P^T phi folds
-                        const float dthr = v[1][0][q], dthi = v[1][0][q + 1];   // dP^T theta folds
-                        const float dphr = v[1][1][q], dphi = v[1][1][q + 1];   // dP^T phi folds
-                        float2 sv = make_float2(sc * (dthr + fm * pphi), sc * (dthi - fm * pphr));
-                        float2 tv = make_float2(sc * (dphr - fm * pthi), sc * (dphi + fm * pthr));
-                        if (m == 0) { sv.y = 0.f; tv.y = 0.f; }
-                        reinterpret_cast<float2 *>(a.out0)[(size_t)b * a.nlm + col + nn] = sv;
-                        reinterpret_cast<float2 *>(a.out1)[(size_t)b * a.nlm + col + nn] = tv;
+                    unsigned char *st = smem + (size_t)q * stage_bytes;
+                    tc::mbar_arrive_expect_tx(&bar_load[q], 2u * kChunkPanel + dbytes);
+                    tc::bulk_g2s_stream(st, p0 + (size_t)c * kChunkPanel, kChunkPanel, &bar_load[q]);
+                    tc::bulk_g2s_stream(st + kChunkPanel, p1 + (size_t)c * kChunkPanel, kChunkPanel, &bar_load[q]);
+                    tc::bulk_g2s(st + 2 * kChunkPanel, data + (size_t)c * dbytes, dbytes, &bar_load[q]);
+                }
+            }
+            if (!ok) {
+                raise_err(a.err, SHT_ETIMEOUT);
+                for (unsigned v = u > (unsigned)S ? u - S : 0; v < u; ++v)
+                    (void)tc::mbar_wait_bounded(&bar_load[v % S], (v / S) & 1, 100000000ull);
+            }
+        }
+    } else if (warp == 4) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            const uint32_t idesc = tc::idesc_bf16_f32(kRows, NV);
+            bool ok = true;
+            unsigned u = 0, j = 0;
+            for (int kk = k0; ok && kk < k1; ++kk) {
+                const Item it = item_of(items[kk]);
+                if (!it.valid) continue;
+                if (j >= 1 && !wait_or_abort(bar_free, (j - 1) & 1, &s_abort)) { ok = false; break; }
+                tc::tc_fence_after();
+                for (int c = 0; c < it.nlive; ++c, ++u) {
+                    const unsigned q = u % S;
+                    if (!wait_or_abort(&bar_load[q], (u / S) & 1, &s_abort)) { ok = false; break; }
+                    tc::tc_fence_after();
+                    unsigned char *st = smem + (size_t)q * stage_bytes;
+                    unsigned char *dat = st + 2 * kChunkPanel;
+                    const bool first = c == 0;   // the item's first chunk overwrites the accumulators
+#pragma unroll
+                    for (int cls = 0; cls < 2; ++cls) {
+                        const int dp = SYNTH ? 1 - cls : cls;   // parity of n - m of the dP block
+                        const unsigned char *aph = st + (size_t)(cls * 2) * kSbo, *apl = aph + kSbo;
+                        const unsigned char *adh = st + kChunkPanel + (size_t)(dp * 2) * kSbo, *adl = adh + kSbo;
+                        const unsigned char *b1h = dat + (size_t)(cls * 2) * blk, *b1l = b1h + blk;
+                        const unsigned char *b2h = dat + (size_t)((1 - cls) * 2) * blk, *b2l = b2h + blk;
+                        const uint32_t d1 = tmem + (uint32_t)((cls * 2 + 0) * NV);
+                        const uint32_t d2 = tmem + (uint32_t)((cls * 2 + 1) * NV);
+                        const uint64_t Aph = tc::smem_desc(aph, kLbo, kPSbo), Apl = tc::smem_desc(apl, kLbo, kPSbo);
+                        const uint64_t Adh = tc::smem_desc(adh, kLbo, kPSbo), Adl = tc::smem_desc(adl, kLbo, kPSbo);
+                        const uint64_t B1h = tc::smem_desc(b1h, kLbo, kSbo), B1l = tc::smem_desc(b1l, kLbo, kSbo);
+                        const uint64_t B2h = tc::smem_desc(b2h, kLbo, kSbo), B2l = tc::smem_desc(b2l, kLbo, kSbo);
+                        tc::mma_bf16(d1, Aph, B1h, idesc, !first);
+                        tc::mma_bf16(d1, Aph, B1l, idesc, true);
+                        tc::mma_bf16(d1, Apl, B1h, idesc, true);
+                        tc::mma_bf16(d2, Adh, B2h, idesc, !first);
+                        tc::mma_bf16(d2, Adh, B2l, idesc, true);
+                        tc::mma_bf16(d2, Adl, B2h, idesc, true);
+                    }
+                    tc::mma_commit(&bar_mma[q]);
+                }
+                if (!ok) break;
+                tc::mma_commit(bar_full);
+                ++j;
+            }
+            if (!ok) raise_err(a.err, SHT_ETIMEOUT);
+            // drain: no MMA may still write tensor memory when it is freed
+            tc::mma_commit(bar_done);
+            (void)tc::mbar_wait_bounded(bar_done, 0, 100000000ull);
+        }
+    } else {
+        // ---------------- epilogue (warps 0-3: TMEM lanes 32 warp ..) ----------------
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        unsigned j = 0;
+        for (int kk = k0; kk < k1; ++kk) {
+            const Item it = item_of(items[kk]);
+            if (!it.valid) continue;
+            if (!wait_or_abort(bar_full, j & 1, &s_abort)) {
+                raise_err(a.err, SHT_ETIMEOUT);
+                break;
+            }
+            tc::tc_fence_after();
+            ++j;
+            const int m = it.m, L = it.L;
+            const long col = col_of_mres(lmax, m, a.mres);
+            const int fb0 = it.half * kVecHalf, nbh = min(kVecHalf, a.batch - fb0);
+            const int row = it.tile * kRows + warp * 32 + lane;
+            const float fm = (float)(m * a.mres);
+            float isn = 1.f;
+            if (SYNTH && row < npairs) isn = 1.f / a.st[row];
+            for (int cls = 0; cls < 2; ++cls) {
+                for (int cb = 0; cb < NH; cb += 32) {
+                    float v[2][2][32];  // [acc][first|second quantity][col]
+#pragma unroll
+                    for (int ac = 0; ac < 2; ++ac)
+#pragma unroll
+                        for (int hf = 0; hf < 2; ++hf) {
+                            if (it.nlive > 0) {
+                                tc::tmem_ld32(lane_base + (uint32_t)((cls * 2 + ac) * NV + hf * NH + cb), v[ac][hf]);
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 32; ++i) v[ac][hf][i] = 0.f;
+                            }
+                        }
+                    if (cls == 1 && cb + 32 >= NH) {
+                        // the accumulators are read: the next item's MMAs may overwrite them
+                        tc::tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(bar_free);
+                    }
+                    for (int q = 0; q < 32; q += 2) {
+                        const int bl = (cb + q) >> 1;   // field within the half
+                        if (bl >= nbh) break;
+                        const int b = fb0 + bl;
+                        if (SYNTH) {
+                            if (row >= npairs) continue;
+                            const float psr = v[0][0][q], psi = v[0][0][q + 1];   // sum P S
+                            const float ptr = v[0][1][q], pti = v[0][1][q + 1];   // sum P T
+                            const float dsr = v[1][0][q], dsi = v[1][0][q + 1];   // sum dP S
+                            const float dtr = v[1][1][q], dti = v[1][1][q + 1];   // sum dP T
+                            const size_t oi = (((size_t)b * (a.mmax + 1) + m) * npairs + row) * 2 + cls;
+                            reinterpret_cast<float2 *>(a.out0)[oi] =
+                                make_float2((dsr + fm * pti) * isn, (dsi - fm * ptr) * isn);
+                            reinterpret_cast<float2 *>(a.out1)[oi] =
+                                make_float2((dtr - fm * psi) * isn, (dti + fm * psr) * isn);
+                        } else {
+                            const int nn = 2 * row + cls;
+                            if (nn >= L) continue;
+                            const int n = m * a.mres + nn;
+                            float sc;
+                            if (a.op == OP_SYNTH_ADJ) sc = (m > 0) ? 2.f : 1.f;
+                            else sc = (n == 0) ? 0.f : 1.f / ((float)n * (float)(n + 1));
+                            const float pthr = v[0][0][q], pthi = v[0][0][q + 1];   // P^T theta folds
+                            const float pphr = v[0][1][q], pphi = v[0][1][q + 1];   // P^T phi folds
+                            const float dthr = v[1][0][q], dthi = v[1][0][q + 1];   // dP^T theta folds
+                            const float dphr = v[1][1][q], dphi = v[1][1][q + 1];   // dP^T phi folds
+                            float2 sv = make_float2(sc * (dthr + fm * pphi), sc * (dthi - fm * pphr));
+                            float2 tv = make_float2(sc * (dphr - fm * pthi), sc * (dphi + fm * pthr));
+                            if (m == 0) {
+                                sv.y = 0.f;
+                                tv.y = 0.f;
+                            }
+                            reinterpret_cast<float2 *>(a.out0)[(size_t)b * a.nlm + col + nn] = sv;
+                            reinterpret_cast<float2 *>(a.out1)[(size_t)b * a.nlm + col + nn] = tv;
+                        }
                     }
                 }
             }
@@ -1349,26 +1417,6 @@ int cols_of(int batch) { return tc_rows(batch, false); }
 // Launch of the vector contraction (two panels per stage, one CTA per SM:
 // its accumulators take the SM's tensor memory): up to 4 stages within 200 KB,
 // a.halves field groups per (m, tile).
-template <typename K>
-cudaError_t launch_contraction(K kernel, bool synth, int lmax, int mmax, int npairs, int npanels, TcArgs &a,
-                               cudaStream_t st)
-{
-    int stages = 4;
-    const size_t cap = npanels == 1 ? 110 * 1024 : 200 * 1024;
-    while (stages > 2 && smem_bytes_of(npanels, a.rows, stages) > cap) --stages;
-    a.stages = stages;
-    const size_t smem = smem_bytes_of(npanels, a.rows, stages);
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    int ts, ta;
-    tc_tile_counts(lmax, npairs, ts, ta);
-    a.ntiles = synth ? ts : ta;
-    const unsigned blocks = (unsigned)((mmax + 1) * a.ntiles * (a.halves > 0 ? a.halves : 1));
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kernel<<<blocks, 128, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_prep(bool synth, bool vec, int lmax, int mmax, int mres, int npairs, int nlm, int batch, int rows,
                         Op op, const float *in0, const float *in1, const unsigned long long *dchunk,
                         unsigned char *data, cudaStream_t st)
@@ -1644,6 +1692,7 @@ cudaError_t launch_tc_legendre(bool synth, int lmax, int mmax, int mres, int npa
 
 cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const unsigned char *panel,
                           const unsigned char *dpanel, const unsigned long long *off, const int *c0,
+                          const int *const sched[2], int nctas,
                           const unsigned long long *dchunk, unsigned char *data, const float *in0, const float *in1,
                           float *out0, float *out1, const float *st_pairs, int batch, Op op, int *err, bool prepped,
                           cudaStream_t st)
@@ -1686,8 +1735,44 @@ cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int mres, int npairs, 
     a.out1 = out1;
     a.st = st_pairs;
     a.err = err;
-    return synth ? launch_contraction(k_tc_vec<true>, true, lmax, mmax, npairs, 2, a, st)
-                 : launch_contraction(k_tc_vec<false>, false, lmax, mmax, npairs, 2, a, st);
+    a.sched = sched[halves - 1];
+    if (!a.sched || nctas < 1) return cudaErrorInvalidValue;
+    int stages = 4;
+    while (stages > 2 && smem_bytes_of(2, rows, stages) + 16 > 200 * 1024) --stages;
+    a.stages = stages;
+    const size_t smem = smem_bytes_of(2, rows, stages) + 16;   // + the accumulator barriers
+    int ts, ta;
+    tc_tile_counts(lmax, npairs, ts, ta);
+    a.ntiles = synth ? ts : ta;
+    cudaError_t e;
+    if (synth) {
+        e = cudaFuncSetAttribute(k_tc_vec<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_tc_vec<true><<<(unsigned)nctas, 192, smem, st>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(k_tc_vec<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_tc_vec<false><<<(unsigned)nctas, 192, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+// Work items of the vector contraction, (order index, tile) x field half,
+// costed as their live chunks plus two for the epilogue (-1: no rows).
+void tc_vec_costs(int lmax, int mmax, int mres, int npairs, bool synth, int halves, const std::vector<int> &c0,
+                  std::vector<int> &cost)
+{
+    int ts, ta;
+    tc_tile_counts(lmax, npairs, ts, ta);
+    const int ntiles = synth ? ts : ta;
+    cost.assign((size_t)(mmax + 1) * ntiles * halves, -1);
+    for (int m = 0; m <= mmax; ++m)
+        for (int t = 0; t < ntiles; ++t) {
+            const int L = lmax - m * mres + 1, Le = (L + 1) / 2;
+            if (!synth && t * kRows >= Le) continue;
+            const int nchunks = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
+            for (int h = 0; h < halves; ++h) cost[((size_t)m * ntiles + t) * halves + h] = nchunks - c0[(size_t)m * ntiles + t] + 2;
+        }
 }
 
 // ---------------------------------------------------------------------------

@@ -37,7 +37,6 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
-#include <algorithm>
 #include <climits>
 #include <vector>
 
@@ -415,7 +414,7 @@ __device__ __forceinline__ Item64 item64(const Tc64Args &a, int w)
 
 // Persistent contraction: kCtasPerSm CTAs per SM, each walking its list of
 // work items, the entries sched[gridDim.x + 1 + k] for k in
-// [sched[blockIdx.x], sched[blockIdx.x + 1]) (tc64_schedule).  The producer's
+// [sched[blockIdx.x], sched[blockIdx.x + 1]) (schedule_lpt).  The producer's
 // ring of kStages stages runs on across items, so the next item's first
 // chunks load while the epilogue reads the accumulator; the MMAs of item j + 1
 // start once it has.  Barriers: bar_load / bar_mma per stage (full / free),
@@ -611,39 +610,22 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_tc64(Tc64Args a, const
 int tc64_max_batch() { return kBatch64; }
 int tc64_ctas_per_sm() { return kCtasPerSm; }
 
-// Work lists of the persistent contraction: the items (order index, tile,
-// parity) that hold rows, costed as their nonzero chunks plus two for the
-// epilogue, heaviest first, each given to the CTA with the least work so far
-// (longest-processing-time first).  sched = [nctas + 1 offsets | items].
-void tc64_schedule(int lmax, int mmax, int mres, int npairs, bool synth, const std::vector<int> &c0, int nctas,
-                   std::vector<int> &sched)
+// Work items of the persistent contraction, (order index, tile) x parity,
+// costed as their nonzero chunks plus two for the epilogue (-1: no rows).
+void tc64_costs(int lmax, int mmax, int mres, int npairs, bool synth, const std::vector<int> &c0,
+                std::vector<int> &cost)
 {
     int ts, ta;
     tc_tile_counts(lmax, npairs, ts, ta);
     const int ntiles = synth ? ts : ta;
-    std::vector<std::pair<int, int>> cost;   // (cost, item)
+    cost.assign((size_t)2 * (mmax + 1) * ntiles, -1);
     for (int w = 0; w < 2 * (mmax + 1) * ntiles; ++w) {
         const int m = (w >> 1) / ntiles, tile = (w >> 1) - m * ntiles;
         const int L = lmax - m * mres + 1, Le = (L + 1) / 2;
         if (!synth && tile * kR >= Le) continue;
         const int nchunks = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
-        cost.push_back({nchunks - c0[(size_t)m * ntiles + tile] + 2, w});
+        cost[w] = nchunks - c0[(size_t)m * ntiles + tile] + 2;
     }
-    std::stable_sort(cost.begin(), cost.end(), [](const std::pair<int, int> &x, const std::pair<int, int> &y) {
-        return x.first > y.first;
-    });
-    std::vector<long long> load(nctas, 0);
-    std::vector<std::vector<int>> lists(nctas);
-    for (const auto &c : cost) {
-        int best = 0;
-        for (int i = 1; i < nctas; ++i)
-            if (load[i] < load[best]) best = i;
-        load[best] += c.first;
-        lists[best].push_back(c.second);
-    }
-    sched.assign(nctas + 1, 0);
-    for (int i = 0; i < nctas; ++i) sched[i + 1] = sched[i] + (int)lists[i].size();
-    for (int i = 0; i < nctas; ++i) sched.insert(sched.end(), lists[i].begin(), lists[i].end());
 }
 
 cudaError_t tc64_reset_fcol(int *fcol, int batch, cudaStream_t st)
