@@ -153,15 +153,15 @@ cudaError_t vec_schedules(sht::Plan &p)
 {
     int T_s = 0, T_a = 0, dev = 0, sms = 0;
     sht::tc_tile_counts(p.lmax, p.npairs, T_s, T_a);
-    std::vector<int> c0s((size_t)(p.mmax + 1) * T_s), c0a((size_t)(p.mmax + 1) * T_a), cost, sc;
+    std::vector<int> c0s((size_t)(p.mmax + 1) * T_s), c0a((size_t)(p.mmax + 1) * T_a), cost, group, sc;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaMemcpy(c0s.data(), p.d_c0v_s, sizeof(int) * c0s.size(), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(c0a.data(), p.d_c0v_a, sizeof(int) * c0a.size(), cudaMemcpyDeviceToHost);
     for (int dir = 0; dir < 2 && e == cudaSuccess; ++dir)
         for (int h = 0; h < 2 && e == cudaSuccess; ++h) {
-            sht::tc_vec_costs(p.lmax, p.mmax, p.mres, p.npairs, dir == 0, h + 1, dir == 0 ? c0s : c0a, cost);
-            sht::schedule_lpt(cost, sms, sc);
+            sht::tc_vec_costs(p.lmax, p.mmax, p.mres, p.npairs, dir == 0, h + 1, dir == 0 ? c0s : c0a, cost, group);
+            sht::schedule_lpt(cost, group, sms, sc);
             int *&d = dir == 0 ? p.d_schedv_s[h] : p.d_schedv_a[h];
             cudaFree(d);
             d = nullptr;
@@ -345,11 +345,11 @@ int ensure_panels64(sht::Plan &p)
         if (e == cudaSuccess) e = cudaMemcpy(c0a.data(), p.d_c064_a, sizeof(int) * c0a.size(), cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) {
             sms *= sht::tc64_ctas_per_sm();
-            std::vector<int> cost;
-            sht::tc64_costs(p.lmax, p.mmax, p.mres, p.npairs, true, c0s, cost);
-            sht::schedule_lpt(cost, sms, ss);
-            sht::tc64_costs(p.lmax, p.mmax, p.mres, p.npairs, false, c0a, cost);
-            sht::schedule_lpt(cost, sms, sa);
+            std::vector<int> cost, group;
+            sht::tc64_costs(p.lmax, p.mmax, p.mres, p.npairs, true, c0s, cost, group);
+            sht::schedule_lpt(cost, group, sms, ss);
+            sht::tc64_costs(p.lmax, p.mmax, p.mres, p.npairs, false, c0a, cost, group);
+            sht::schedule_lpt(cost, group, sms, sa);
             e = cudaMalloc(&p.d_sched64_s, sizeof(int) * ss.size());
         }
         if (e == cudaSuccess) e = cudaMalloc(&p.d_sched64_a, sizeof(int) * sa.size());

@@ -386,21 +386,36 @@ int plan_relive(Plan &p, std::string &err)
     return SHT_OK;
 }
 
-void schedule_lpt(const std::vector<int> &cost, int nctas, std::vector<int> &sched)
+void schedule_lpt(const std::vector<int> &cost, const std::vector<int> &group, int nctas, std::vector<int> &sched)
 {
-    std::vector<std::pair<int, int>> order;   // (cost, item)
-    for (int w = 0; w < (int)cost.size(); ++w)
-        if (cost[w] >= 0) order.push_back({cost[w], w});
-    std::stable_sort(order.begin(), order.end(),
-                     [](const std::pair<int, int> &x, const std::pair<int, int> &y) { return x.first > y.first; });
+    // groups in order of first appearance, their items in ascending order
+    std::vector<int> gid(cost.size(), -1);
+    std::vector<std::vector<int>> members;
+    std::vector<long long> gcost;
+    std::vector<int> slot;   // group id -> index in members
+    for (int w = 0; w < (int)cost.size(); ++w) {
+        if (cost[w] < 0) continue;
+        const int g = group[w];
+        if (g >= (int)slot.size()) slot.resize(g + 1, -1);
+        if (slot[g] < 0) {
+            slot[g] = (int)members.size();
+            members.emplace_back();
+            gcost.push_back(0);
+        }
+        members[slot[g]].push_back(w);
+        gcost[slot[g]] += cost[w];
+    }
+    std::vector<int> order(members.size());
+    for (int i = 0; i < (int)order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return gcost[x] > gcost[y]; });
     std::vector<long long> load(nctas, 0);
     std::vector<std::vector<int>> lists(nctas);
-    for (const auto &c : order) {
+    for (const int g : order) {
         int best = 0;
         for (int i = 1; i < nctas; ++i)
             if (load[i] < load[best]) best = i;
-        load[best] += c.first;
-        lists[best].push_back(c.second);
+        load[best] += gcost[g];
+        lists[best].insert(lists[best].end(), members[g].begin(), members[g].end());
     }
     sched.assign(nctas + 1, 0);
     for (int i = 0; i < nctas; ++i) sched[i + 1] = sched[i] + (int)lists[i].size();

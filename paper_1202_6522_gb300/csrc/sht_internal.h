@@ -348,17 +348,21 @@ cudaError_t tc64_build(const PlanView<double> &pv, const unsigned long long *off
 // fcol_ready: fcol already holds the field exponents of `in` (else this
 // computes them first).
 // Work lists of persistent CTAs, longest processing time first: the items
-// with cost >= 0, heaviest first, each to the CTA with the least work so far;
+// with cost >= 0 form groups (items of one group id go to one CTA, in
+// ascending order, so that the data they share is still in L2); groups are
+// taken heaviest first, each to the CTA with the least work so far.
 // sched = [nctas + 1 offsets | items].
-void schedule_lpt(const std::vector<int> &cost, int nctas, std::vector<int> &sched);
-// Item costs of the persistent FP64-accurate contraction (item = 2 (m tiles + tile) + parity)
-// from the first nonzero chunks c0 [mmax+1][tiles].
+void schedule_lpt(const std::vector<int> &cost, const std::vector<int> &group, int nctas, std::vector<int> &sched);
+// Item costs and groups of the persistent FP64-accurate contraction (item =
+// 2 (m tiles + tile) + parity; group = (m, parity), whose tiles read the same
+// data digits) from the first nonzero chunks c0 [mmax+1][tiles].
 void tc64_costs(int lmax, int mmax, int mres, int npairs, bool synth, const std::vector<int> &c0,
-                std::vector<int> &cost);
-// Item costs of the persistent vector contraction (item = (m tiles + tile) halves + half)
-// from its first live chunks c0 [mmax+1][tiles].
+                std::vector<int> &cost, std::vector<int> &group);
+// Item costs and groups of the persistent vector contraction (item =
+// (m tiles + tile) halves + half; group = m: the halves of a tile share its
+// panel chunks, the tiles share the data) from its first live chunks c0.
 void tc_vec_costs(int lmax, int mmax, int mres, int npairs, bool synth, int halves, const std::vector<int> &c0,
-                  std::vector<int> &cost);
+                  std::vector<int> &cost, std::vector<int> &group);
 cudaError_t launch_tc64(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const unsigned char *panel,
                         const unsigned long long *off, const int *c0, const int *sched, int nctas, const int *erow,
                         const unsigned long long *dchunk, int *fcol, unsigned char *data, const double *in,

@@ -1758,14 +1758,17 @@ cudaError_t launch_tc_vec(bool synth, int lmax, int mmax, int mres, int npairs, 
 }
 
 // Work items of the vector contraction, (order index, tile) x field half,
-// costed as their live chunks plus two for the epilogue (-1: no rows).
+// costed as their live chunks plus two for the epilogue (-1: no rows),
+// grouped by order index.
 void tc_vec_costs(int lmax, int mmax, int mres, int npairs, bool synth, int halves, const std::vector<int> &c0,
-                  std::vector<int> &cost)
+                  std::vector<int> &cost, std::vector<int> &group)
 {
     int ts, ta;
     tc_tile_counts(lmax, npairs, ts, ta);
     const int ntiles = synth ? ts : ta;
     cost.assign((size_t)(mmax + 1) * ntiles * halves, -1);
+    group.assign(cost.size(), 0);
+    for (size_t w = 0; w < group.size(); ++w) group[w] = (int)(w / ((size_t)ntiles * halves));
     for (int m = 0; m <= mmax; ++m)
         for (int t = 0; t < ntiles; ++t) {
             const int L = lmax - m * mres + 1, Le = (L + 1) / 2;

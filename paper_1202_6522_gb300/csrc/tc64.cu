@@ -505,6 +505,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_tc64(Tc64Args a, const
                 const unsigned char *data =
                     a.data + (SYNTH ? a.dchunk[it.m] : (unsigned long long)it.m * it.nchunks) *
                                  (unsigned long long)kDChunk + (size_t)it.par * kDBlk;
+                // rows of the tile that hold a pair (synthesis) or a degree (analysis):
+                // only their 8-row groups are copied; the rest of the stage keeps
+                // whatever it held, which reaches only accumulator rows the
+                // epilogue does not write
+                const int live_rows = min(kR, (SYNTH ? a.npairs : it.Le) - it.tile * kR);
+                const uint32_t slice_bytes = (uint32_t)((live_rows + 7) / 8) * kSbo;
+                const bool full = slice_bytes == (uint32_t)kPBlk;
                 for (int c = it.cstart; c < it.nchunks; ++c, ++u) {
                     const unsigned q = u % kStages;
                     if (u >= kStages && !wait_or_abort(&bar_mma[q], (u / kStages - 1) & 1, &s_abort)) {
@@ -512,8 +519,15 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_tc64(Tc64Args a, const
                         break;
                     }
                     unsigned char *st = smem + (size_t)q * kStage;
-                    tc::mbar_arrive_expect_tx(&bar_load[q], (uint32_t)kStage);
-                    tc::bulk_g2s_stream(st, panel + (size_t)c * kPChunk, (uint32_t)kPPar, &bar_load[q]);
+                    const unsigned char *src = panel + (size_t)c * kPChunk;
+                    tc::mbar_arrive_expect_tx(&bar_load[q], (uint32_t)kSA * slice_bytes + (uint32_t)kDBlk);
+                    if (full) {
+                        tc::bulk_g2s_stream(st, src, (uint32_t)kPPar, &bar_load[q]);
+                    } else {
+#pragma unroll 1
+                        for (int i = 0; i < kSA; ++i)
+                            tc::bulk_g2s_stream(st + pblk(i, 0), src + pblk(i, 0), slice_bytes, &bar_load[q]);
+                    }
                     tc::bulk_g2s(st + kPPar, data + (size_t)c * kDChunk, (uint32_t)kDBlk, &bar_load[q]);
                 }
             }
@@ -611,16 +625,19 @@ int tc64_max_batch() { return kBatch64; }
 int tc64_ctas_per_sm() { return kCtasPerSm; }
 
 // Work items of the persistent contraction, (order index, tile) x parity,
-// costed as their nonzero chunks plus two for the epilogue (-1: no rows).
+// costed as their nonzero chunks plus two for the epilogue (-1: no rows),
+// grouped by (order index, parity).
 void tc64_costs(int lmax, int mmax, int mres, int npairs, bool synth, const std::vector<int> &c0,
-                std::vector<int> &cost)
+                std::vector<int> &cost, std::vector<int> &group)
 {
     int ts, ta;
     tc_tile_counts(lmax, npairs, ts, ta);
     const int ntiles = synth ? ts : ta;
     cost.assign((size_t)2 * (mmax + 1) * ntiles, -1);
+    group.assign(cost.size(), 0);
     for (int w = 0; w < 2 * (mmax + 1) * ntiles; ++w) {
         const int m = (w >> 1) / ntiles, tile = (w >> 1) - m * ntiles;
+        group[w] = 2 * m + (w & 1);
         const int L = lmax - m * mres + 1, Le = (L + 1) / 2;
         if (!synth && tile * kR >= Le) continue;
         const int nchunks = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
