@@ -717,6 +717,11 @@ __global__ void __launch_bounds__(192, 1) k_tc_vec(TcArgs a)
                 const unsigned char *data =
                     a.data + (size_t)it.half * a.data_half +
                     (SYNTH ? a.dchunk[it.m] : (unsigned long long)it.m * it.nchunks) * data_chunk_bytes(NV);
+                // panel bytes up to the last 8-row group holding a pair (synthesis) or
+                // a degree (analysis); the MMA rows above read stale data and are never
+                // written out
+                const int rows_valid = min(kRows, (SYNTH ? npairs : it.Le) - kRows * it.tile);
+                const uint32_t pgb = (uint32_t)((rows_valid + 7) / 8) * kPSbo;
                 for (int c = it.cstart; c < it.nchunks; ++c, ++u) {
                     const unsigned q = u % S;
                     if (u >= (unsigned)S && !wait_or_abort(&bar_mma[q], (u / S - 1) & 1, &s_abort)) {
@@ -724,9 +729,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_vec(TcArgs a)
                         break;
                     }
                     unsigned char *st = smem + (size_t)q * stage_bytes;
-                    tc::mbar_arrive_expect_tx(&bar_load[q], 2u * kChunkPanel + dbytes);
-                    tc::bulk_g2s_stream(st, p0 + (size_t)c * kChunkPanel, kChunkPanel, &bar_load[q]);
-                    tc::bulk_g2s_stream(st + kChunkPanel, p1 + (size_t)c * kChunkPanel, kChunkPanel, &bar_load[q]);
+                    tc::mbar_arrive_expect_tx(&bar_load[q], 2u * pgb + dbytes);
+                    tc::bulk_g2s_stream(st, p0 + (size_t)c * kChunkPanel, pgb, &bar_load[q]);
+                    tc::bulk_g2s_stream(st + kChunkPanel, p1 + (size_t)c * kChunkPanel, pgb, &bar_load[q]);
                     tc::bulk_g2s(st + 2 * kChunkPanel, data + (size_t)c * dbytes, dbytes, &bar_load[q]);
                 }
             }
