@@ -796,12 +796,16 @@ __device__ __forceinline__ void fft_synth_tile_df(const PlanView<double> &pv, co
 // the values go to shared memory converted; the fold converts back to FP64.
 // fmax (may be null): per field, the running maximum of frexp exponents of
 // the folds written (the field scale of the FP64-accurate contraction).
-template <bool MIXED>
+// LOGH > 0: the row length is 2^LOGH, known at compile time, and the passes are
+// spelled out (radix 4, 16, 16 for LOGH = 10, the plan's order), so the index
+// arithmetic folds and no code of other radices sits in the kernel.  (The same
+// for synthesis measured slower, 0.525 against 0.509 ms at nphi = 2048.)
+template <bool MIXED, int LOGH = 0>
 __device__ __forceinline__ void fft_analys_tile_df(const PlanView<double> &pv, const double *__restrict__ grid,
                                                    double *__restrict__ sd, int b, int p0, int G, int op,
                                                    int vector, int *__restrict__ fmax, unsigned char *smem_raw)
 {
-    const int H = pv.nphi / 2, R = 2 * G;
+    const int H = LOGH ? (1 << LOGH) : pv.nphi / 2, R = 2 * G;
     const int TPR = row_tpr(H);
     const int ld = padi(H) + 1;
     dfl2 *wtab = reinterpret_cast<dfl2 *>(smem_raw);
@@ -850,7 +854,23 @@ __device__ __forceinline__ void fft_analys_tile_df(const PlanView<double> &pv, c
         }
     }
     __syncthreads();
-    if (H > 1) {
+    if constexpr (LOGH == 10) {
+        // forward complex FFT of length 1024: radix 4, 16, 16
+        constexpr int NR = PassRegs<false>::n;
+        dfl2 v[NR];
+        if (r < R) stockham_load<dfl2, 4, -1, NR, true>(row, false, t, TPR, H, 1, wtab, v);
+        __syncthreads();
+        if (r < R) stockham_store_smem<dfl2, 4, NR, true>(row, t, TPR, H, 1, v);
+        __syncthreads();
+        if (r < R) stockham_load<dfl2, 16, -1, NR, true>(row, false, t, TPR, H, 4, wtab, v);
+        __syncthreads();
+        if (r < R) stockham_store_smem<dfl2, 16, NR, true>(row, t, TPR, H, 4, v);
+        __syncthreads();
+        if (r < R) stockham_load<dfl2, 16, -1, NR, true>(row, false, t, TPR, H, 64, wtab, v);
+        __syncthreads();
+        if (r < R) stockham_store_smem<dfl2, 16, NR, true>(row, t, TPR, H, 64, v);
+        __syncthreads();
+    } else if (H > 1) {
         // forward complex FFT of length H
         int Ns = 1;
         dfl2 v[PassRegs<MIXED>::n];
@@ -917,13 +937,13 @@ k_fft_synth_df(PlanView<double> pv, const double *__restrict__ eo, double *__res
     fft_synth_tile_df<MIXED>(pv, eo, grid, blockIdx.y, blockIdx.x * G, G, op, smem_raw);
 }
 
-template <bool MIXED>
+template <bool MIXED, int LOGH = 0>
 __global__ void __launch_bounds__(512)
 k_fft_analys_df(PlanView<double> pv, const double *__restrict__ grid, double *__restrict__ sd, int G, int op,
                 int vector, int *__restrict__ fmax)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fft_analys_tile_df<MIXED>(pv, grid, sd, blockIdx.y, blockIdx.x * G, G, op, vector, fmax, smem_raw);
+    fft_analys_tile_df<MIXED, LOGH>(pv, grid, sd, blockIdx.y, blockIdx.x * G, G, op, vector, fmax, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -1281,12 +1301,15 @@ cudaError_t launch_fft_analys_df(const PlanView<double> &pv, const double *grid,
     size_t smem;
     fft_shape<double>(pv.nphi / 2, pv.npairs, G, threads, smem);
     smem += df_extra_smem(G);
-    const bool mixed = !pow2(pv.nphi / 2);
-    cudaError_t e = mixed ? set_smem(k_fft_analys_df<true>, smem) : set_smem(k_fft_analys_df<false>, smem);
+    const bool mixed = !pow2(pv.nphi / 2), h1024 = pv.nphi == 2048;
+    cudaError_t e = mixed ? set_smem(k_fft_analys_df<true>, smem)
+                          : (h1024 ? set_smem(k_fft_analys_df<false, 10>, smem) : set_smem(k_fft_analys_df<false>, smem));
     if (e != cudaSuccess) return e;
     dim3 gridd((unsigned)((pv.npairs + G - 1) / G), (unsigned)batch);
     if (mixed)
         k_fft_analys_df<true><<<gridd, threads, smem, s>>>(pv, grid, sd, G, (int)op, vector ? 1 : 0, fmax);
+    else if (h1024)
+        k_fft_analys_df<false, 10><<<gridd, threads, smem, s>>>(pv, grid, sd, G, (int)op, vector ? 1 : 0, fmax);
     else
         k_fft_analys_df<false><<<gridd, threads, smem, s>>>(pv, grid, sd, G, (int)op, vector ? 1 : 0, fmax);
     return cudaGetLastError();
