@@ -746,13 +746,16 @@ __device__ __forceinline__ void fft_synth_tile_df(const PlanView<double> &pv, co
             continue;
         }
         const dfl2 XNb = cadd(Eb, Ob), XSb = csub(Eb, Ob);
+        // with A = X_k + conj X_{H-k} and P = W^k (X_k - conj X_{H-k}), W = e^{2 pi i / (2H)}:
+        // Z_k = A + i P and, since W^{H-k} = -conj W^k, Z_{H-k} = conj A + i conj P
         const dfl2 wa = ld_twdf(pv.twdf, k);
-        dN[padi(k)] = cadd(cadd(XNa, conj_(XNb)), mul_i(cmul(wa, csub(XNa, conj_(XNb)))));
-        dS[padi(k)] = cadd(cadd(XSa, conj_(XSb)), mul_i(cmul(wa, csub(XSa, conj_(XSb)))));
+        const dfl2 AN = cadd(XNa, conj_(XNb)), PN = cmul(wa, csub(XNa, conj_(XNb)));
+        const dfl2 AS = cadd(XSa, conj_(XSb)), PS = cmul(wa, csub(XSa, conj_(XSb)));
+        dN[padi(k)] = cadd(AN, mul_i(PN));
+        dS[padi(k)] = cadd(AS, mul_i(PS));
         if (k2 != k) {
-            const dfl2 wb = ld_twdf(pv.twdf, k2);
-            dN[padi(k2)] = cadd(cadd(XNb, conj_(XNa)), mul_i(cmul(wb, csub(XNb, conj_(XNa)))));
-            dS[padi(k2)] = cadd(cadd(XSb, conj_(XSa)), mul_i(cmul(wb, csub(XSb, conj_(XSa)))));
+            dN[padi(k2)] = cadd(conj_(AN), mul_i(conj_(PN)));
+            dS[padi(k2)] = cadd(conj_(AS), mul_i(conj_(PS)));
         }
     }
     __syncthreads();
