@@ -887,26 +887,13 @@ __device__ __forceinline__ void fft_analys_tile_df(const PlanView<double> &pv, c
             Ns *= rd;
         }
     }
-    // post-twiddle, fold north/south, weight, back to FP64
+    // post-twiddle, fold north/south, weight, back to FP64.  Positions m and
+    // H - m share their terms: with E = (Z_m + conj Z_{H-m}) / 2,
+    // Od = (Z_m - conj Z_{H-m}) / (2i) and P = W^{-m} Od (W = e^{2 pi i / (2H)}),
+    // X_m = E + P and X_{H-m} = conj(E - P), one product for both.
     double2 *sd2 = reinterpret_cast<double2 *>(sd);
     unsigned ebits = 0;   // largest biased exponent field written by this thread
-    for (int q = threadIdx.x; q < G * (mmax + 1); q += blockDim.x) {
-        const int m = q / G, i = q - m * G;
-        const int pp = p0 + i;
-        if (pp >= npairs) continue;
-        const dfl2 wm = conj_(ld_twdf(pv.twdf, m));
-        dfl2 X[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const dfl2 *rw = buf + (2 * i + h) * ld;
-            const dfl2 Zk = rw[padi(m)];
-            const dfl2 Zc = conj_(rw[padi(MIXED ? (H - m) % H : (H - m) & (H - 1))]);
-            dfl2 E = cadd(Zk, Zc), O = csub(Zk, Zc);
-            E.x = scale2(E.x, 0.5f);
-            E.y = scale2(E.y, 0.5f);
-            const dfl2 Od = mk<dfl2>(scale2(O.y, 0.5f), scale2(O.x, -0.5f));  // O / (2i)
-            X[h] = cadd(E, cmul(wm, Od));
-        }
+    const auto emit = [&](int m, int i, int pp, const dfl2 (&X)[2]) {
         const dfl wf = s_w[i];
         const bool equator = (nlat & 1) && pp == npairs - 1;
         dfl2 s, d;
@@ -923,6 +910,31 @@ __device__ __forceinline__ void fft_analys_tile_df(const PlanView<double> &pv, c
         sd2[o] = so;
         sd2[o + 1] = dd;
         ebits = max(ebits, (unsigned)max(dexp2(so), dexp2(dd)));
+    };
+    const int mhalf = min(H / 2, mmax);
+    for (int q = threadIdx.x; q < G * (mhalf + 1); q += blockDim.x) {
+        const int m = q / G, i = q - m * G;
+        const int pp = p0 + i;
+        if (pp >= npairs) continue;
+        const int m2 = H - m;   // its partner, when it is another position and an order of the plan
+        const bool two = m2 != m && m2 < H && m2 <= mmax;
+        const dfl2 wm = conj_(ld_twdf(pv.twdf, m));
+        dfl2 X[2], X2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const dfl2 *rw = buf + (2 * i + h) * ld;
+            const dfl2 Zk = rw[padi(m)];
+            const dfl2 Zc = conj_(rw[padi(MIXED ? (H - m) % H : (H - m) & (H - 1))]);
+            dfl2 E = cadd(Zk, Zc), O = csub(Zk, Zc);
+            E.x = scale2(E.x, 0.5f);
+            E.y = scale2(E.y, 0.5f);
+            const dfl2 Od = mk<dfl2>(scale2(O.y, 0.5f), scale2(O.x, -0.5f));  // O / (2i)
+            const dfl2 P = cmul(wm, Od);
+            X[h] = cadd(E, P);
+            X2[h] = conj_(csub(E, P));
+        }
+        emit(m, i, pp, X);
+        if (two) emit(m2, i, pp, X2);
     }
     if (fmax) {
         // outputs are normal or zero (df2d flushes below 2^-1022): frexp's
