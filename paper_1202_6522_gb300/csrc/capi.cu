@@ -1257,8 +1257,10 @@ extern "C" int sht_tune(sht_handle h, int batch, int mode, double *report, void 
         for (int bi = 0; bi < 4; ++bi) {
             const int lpt = lpts_a[li], bc = bcs_a[bi];
             if (bc > batch && bc > 1) continue;
-            if (lpt == sht::kAnalysSeg ? (shape_mode != SHT_F64 || p.npairs > 512)
-                                       : (bc > 2 || (p.npairs + 32 * lpt - 1) / (32 * lpt) > 8))
+            if (lpt == sht::kAnalysSeg
+                    ? (shape_mode != SHT_F64 || p.npairs > 2048 || (p.npairs > 1024 && bc > 2) ||
+                       (p.npairs > 512 && bc > 4))
+                    : (bc > 2 || (p.npairs + 32 * lpt - 1) / (32 * lpt) > 8))
                 continue;
             bool ok = false;
             double ms;

@@ -620,6 +620,143 @@ k_analys_seg(PlanView<T> pv, const T *__restrict__ sd, T *__restrict__ spec, int
     }
 }
 
+// More pairs than a warp holds (npairs <= 32 PPL TEAM): a team of TEAM warps
+// takes each segment, every warp summing its own 32 PPL pairs; per butterfly
+// the warps' partial sums meet in shared memory (double-buffered by
+// butterfly, one named barrier per team each time) and the team's first warp
+// adds them in a fixed order and writes the coefficients.  Teams take the
+// segments t, t + teams, ... of the order.
+template <typename T, int PPL, int BC, int TEAM>
+__global__ void __launch_bounds__(kSegWarps * 32, 1)
+k_analys_seg_team(PlanView<T> pv, const T *__restrict__ sd, T *__restrict__ spec, int batch, int op)
+{
+    using T2 = typename Vec2<T>::type;
+    constexpr int K = 16 / BC;           // degrees per butterfly: 2 K BC = 32 values
+    constexpr int R = 32 * PPL * TEAM;   // staged row: the pairs, zero-padded
+    constexpr int NTEAM = kSegWarps / TEAM, NG = PPL * TEAM;
+    static_assert(kSegWarps % TEAM == 0, "whole teams");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2 *s_v = reinterpret_cast<T2 *>(smem_raw);   // [BC][parity][R]: s (n - m even), d (odd)
+    __shared__ int s_gfirst[NG];                  // first live segment of each group of 32 pairs
+    __shared__ T s_part[NTEAM][2][TEAM][32];      // the warps' partial sums
+
+    const int m = blockIdx.x, b0 = blockIdx.y * BC;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int team = warp / TEAM, wt = warp - team * TEAM;
+    const int npairs = pv.npairs;
+    const int L = pv.lmax - m * pv.mres + 1;   // order index m is the order m mres
+    const long col = col_of_mres(pv.lmax, m, pv.mres);
+    const int nseg = (L + kSeedSeg - 1) / kSeedSeg;
+
+    const T2 *sd2 = reinterpret_cast<const T2 *>(sd);
+    for (int idx = threadIdx.x; idx < BC * 2 * R; idx += blockDim.x) {
+        const int b = idx / (2 * R), r = idx - b * 2 * R;
+        T2 v;
+        v.x = T(0); v.y = T(0);
+        if (r < 2 * npairs && b0 + b < batch) v = sd2[((size_t)(b0 + b) * (pv.mmax + 1) + m) * npairs * 2 + r];
+        s_v[(b * 2 + (r & 1)) * R + (r >> 1)] = v;
+    }
+    for (int g = warp; g < NG; g += kSegWarps) {
+        const int pp = g * 32 + lane;
+        const int f = pp < npairs ? (int)pv.live[(size_t)m * npairs + pp] : 0xffff;
+        const int gm = __reduce_min_sync(kFull, f);
+        if (lane == 0) s_gfirst[g] = gm;
+    }
+    __syncthreads();
+
+    const T outsc = (op == OP_SYNTH_ADJ && m > 0) ? T(2) : T(1);   // c_m for the adjoint of synthesis
+    T2 *spec2 = reinterpret_cast<T2 *>(spec);
+    const int pbase = wt * 32 * PPL;
+    int p[PPL];
+    T x[PPL];
+#pragma unroll
+    for (int i = 0; i < PPL; ++i) {
+        p[i] = pbase + lane + 32 * i;
+        x[i] = p[i] < npairs ? pv.x[p[i]] : T(0);
+    }
+    const int okx = lane / (2 * BC), ob = (lane >> 1) % BC, opart = lane & 1;
+    unsigned kb = 0;   // butterflies done by this team (selects the partial buffer)
+
+    for (int seg = team; seg < nseg; seg += NTEAM) {
+        const int nn0 = seg * kSeedSeg, cnt = min(kSeedSeg, L - nn0);
+        unsigned live = 0;      // this warp's groups
+        bool team_live = false;
+#pragma unroll
+        for (int i = 0; i < PPL; ++i)
+            if (s_gfirst[wt * PPL + i] <= seg) live |= 1u << i;
+        for (int g = 0; g < NG; ++g) team_live |= s_gfirst[g] <= seg;
+        if (!team_live) {
+            if (wt == 0) {
+                for (int q = lane; q < cnt * 2 * BC; q += 32) {
+                    const int kx = q / (2 * BC), b = (q >> 1) % BC;
+                    if (b0 + b < batch)
+                        reinterpret_cast<T *>(&spec2[(size_t)(b0 + b) * pv.nlm + col + nn0 + kx])[q & 1] = T(0);
+                }
+            }
+            continue;
+        }
+        T y1[PPL], y2[PPL];
+        int k[PPL];
+#pragma unroll
+        for (int i = 0; i < PPL; ++i) {
+            y1[i] = y2[i] = T(0);
+            k[i] = 0;
+        }
+        if (live) reseed<T, PPL>(pv, m, seg, p, y1, y2, k);
+        unsigned scaled = 0;
+#pragma unroll
+        for (int i = 0; i < PPL; ++i)
+            if (__any_sync(kFull, k[i] > 0)) scaled |= 1u << i;
+        for (int t0 = 0; t0 < cnt; t0 += K, ++kb) {
+            T acc[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) acc[q] = T(0);
+            if (live) {
+#pragma unroll
+                for (int kx = 0; kx < K; ++kx) {
+                    if (t0 + kx >= cnt) break;
+                    const T2 ab = __ldg(&pv.ab[col + nn0 + t0 + kx]);
+                    const T2 *vrow = s_v + ((t0 + kx) & 1) * R;   // nn0 is even
+#pragma unroll
+                    for (int i = 0; i < PPL; ++i) {
+                        if (!((live >> i) & 1)) continue;
+                        const T yn = fma(ab.x * x[i], y1[i], ab.y * y2[i]);
+                        y2[i] = y1[i];
+                        y1[i] = yn;
+                        T c = yn;
+                        if ((scaled >> i) & 1) {
+                            if (k[i] > 0 && abs_ge_one(yn)) {
+                                y1[i] *= down_scale<T>();
+                                y2[i] *= down_scale<T>();
+                                k[i] -= 1;
+                            }
+                            c = (k[i] == 0) ? y1[i] : T(0);
+                        }
+#pragma unroll
+                        for (int b = 0; b < BC; ++b) {
+                            const T2 v = vrow[b * 2 * R + p[i]];
+                            acc[(kx * BC + b) * 2] = fma(c, v.x, acc[(kx * BC + b) * 2]);
+                            acc[(kx * BC + b) * 2 + 1] = fma(c, v.y, acc[(kx * BC + b) * 2 + 1]);
+                        }
+                    }
+                }
+                warp_transpose_reduce<T, 32>(acc, lane);
+            }
+            s_part[team][kb & 1][wt][lane] = acc[0];
+            // the team's warps: named barrier 1 + team over 32 TEAM threads
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + team), "r"(32 * TEAM) : "memory");
+            if (wt == 0 && t0 + okx < cnt && b0 + ob < batch) {
+                T tot = s_part[team][kb & 1][0][lane];
+#pragma unroll
+                for (int w = 1; w < TEAM; ++w) tot += s_part[team][kb & 1][w][lane];
+                T val = tot * outsc;
+                if (m == 0 && opart == 1) val = T(0);
+                reinterpret_cast<T *>(&spec2[(size_t)(b0 + ob) * pv.nlm + col + nn0 + t0 + okx])[opart] = val;
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Vector synthesis.  With dP = sin(theta) dP/dtheta = n x P_n - dc_n P_{n-1}:
 //   sin * V_theta,m = sum [S dP - i m T P],   sin * V_phi,m = sum [i m S P + T dP].
@@ -949,8 +1086,22 @@ cudaError_t analys_go(const PlanView<T> &pv, const T *sd, T *spec, int batch, Op
     return cudaGetLastError();
 }
 
-// Pairs per lane of the segment analysis kernel (0: too many pairs for it).
+// Pairs per lane of the segment analysis kernel (0: too many pairs for one warp).
 inline int seg_ppl(int npairs) { return npairs <= 128 ? 4 : (npairs <= 256 ? 8 : (npairs <= 512 ? 16 : 0)); }
+
+// FP64 analysis with 512 < npairs <= 2048: teams of 2 or 4 warps of 16 pairs per lane.
+template <int TEAM, int BC>
+cudaError_t analys_team_go(const PlanView<double> &pv, const double *sd, double *spec, int batch, Op op,
+                           cudaStream_t s)
+{
+    const size_t smem = sizeof(double2) * BC * 2 * 32 * 16 * TEAM;
+    cudaError_t e = cudaFuncSetAttribute(k_analys_seg_team<double, 16, BC, TEAM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(pv.mmax + 1), (unsigned)((batch + BC - 1) / BC));
+    k_analys_seg_team<double, 16, BC, TEAM><<<grid, kSegWarps * 32, smem, s>>>(pv, sd, spec, batch, (int)op);
+    return cudaGetLastError();
+}
 
 template <typename T, int PPL, int BC>
 cudaError_t analys_seg_go(const PlanView<T> &pv, const T *sd, T *spec, int batch, Op op, cudaStream_t s)
@@ -1029,10 +1180,28 @@ cudaError_t launch_legendre_analys_cfg(const PlanView<T> &pv, const T *sd, T *sp
     // default shape: FP64 up to 512 pairs, the segment kernel with up to 8
     // fields per CTA; otherwise LPT from the pair count (<= 8 warps), 2 fields
     // per CTA when batched
-    if (lpt <= 0) lpt = (sizeof(T) == sizeof(double) && seg_ppl(pv.npairs)) ? kAnalysSeg : analys_lpt(pv.npairs);
+    if (lpt <= 0)
+        lpt = (sizeof(T) == sizeof(double) && pv.npairs <= 2048) ? kAnalysSeg : analys_lpt(pv.npairs);
     if (lpt == kAnalysSeg) {
         if (sizeof(T) != sizeof(double)) return cudaErrorInvalidValue;
         const int ppl = seg_ppl(pv.npairs);
+        if constexpr (sizeof(T) == sizeof(double)) {
+            if (ppl == 0) {
+                // teams: 2 warps and up to 4 fields per CTA, or 4 warps and 2 fields
+                // (128 KB of staged folds either way)
+                if (pv.npairs <= 1024) {
+                    if (bc <= 0) bc = batch >= 4 ? 4 : (batch >= 2 ? 2 : 1);
+                    if (bc == 4) return analys_team_go<2, 4>(pv, sd, spec, batch, op, s);
+                    if (bc == 2) return analys_team_go<2, 2>(pv, sd, spec, batch, op, s);
+                    if (bc == 1) return analys_team_go<2, 1>(pv, sd, spec, batch, op, s);
+                } else if (pv.npairs <= 2048) {
+                    if (bc <= 0) bc = batch >= 2 ? 2 : 1;
+                    if (bc == 2) return analys_team_go<4, 2>(pv, sd, spec, batch, op, s);
+                    if (bc == 1) return analys_team_go<4, 1>(pv, sd, spec, batch, op, s);
+                }
+                return cudaErrorInvalidValue;
+            }
+        }
         if (bc <= 0) bc = batch >= 8 ? 8 : (batch >= 4 ? 4 : (batch >= 2 ? 2 : 1));
         if constexpr (sizeof(T) == sizeof(double)) {
 #define SHT_SEG(P, B) if (ppl == P && bc == B) return analys_seg_go<T, P, B>(pv, sd, spec, batch, op, s);
