@@ -131,3 +131,23 @@ def test_fp64_segment_analysis_field_groups(SHT, data):
         B.check(got, ref_a[:nb], fp64_bound(LMAX) * np.abs(ref_a[:nb]).max(), f"f64 segment analysis b{nb}")
     C.sht_tune(sht._h, 8, C.SHT_F64, torch.cuda.current_stream().cuda_stream)
     B.check(_np(sht.analys_(_dev(g, "f64"))), ref_a, fp64_bound(LMAX) * np.abs(ref_a).max(), "f64 tuned analysis")
+
+
+def test_fp64_team_analysis_beyond_512_pairs(SHT):
+    """More latitude pairs than one warp holds (551 here): each segment is
+    summed by a team of warps whose partial sums meet in shared memory.
+    Sampled orders against the oracle at every field-group width (1, 2 and 4
+    fields per CTA, ragged batches), bitwise the same across repeated calls."""
+    lmax, nlat, nphi = 1100, 1101, 2304
+    ms = [0, 1, 257, 550, 1100]
+    g = synthetic.grid(nlat, nphi, batch=5, seed=41)
+    ref = oracle.analys(lmax, lmax, nlat, nphi, g, ms=ms)
+    ns, mm = synthetic.packed_degrees_orders(lmax)
+    sel = np.isin(mm, ms)
+    sht = SHT(lmax, lmax, nlat, nphi, device=DEV)
+    for nb in (1, 3, 5):
+        x = _dev(g[:nb], "f64")
+        got = _np(sht.analys_(x))
+        assert np.array_equal(got, _np(sht.analys_(x)))
+        r = ref.reshape(5, -1)[:nb][:, sel]
+        B.check(got[:, sel], r, fp64_bound(lmax) * np.abs(r).max(), f"f64 team analysis b{nb}")
