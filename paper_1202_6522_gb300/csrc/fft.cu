@@ -706,25 +706,41 @@ __device__ __forceinline__ void fft_synth_tile_df(const PlanView<double> &pv, co
     // 1. E (row 2i) and O (row 2i+1) of the G pairs in natural order, zero
     //    above mmax, and the largest exponent per pair
     {
+        // the loads of U items are issued before their stores (latency, not bandwidth, is the limit here)
+        constexpr int U = 8;
         int cur = -1, emax = 0;
-        for (int q = threadIdx.x; q < G * H; q += blockDim.x) {
-            const int m = q / G, i = q - m * G;
-            const int p = p0 + i;
-            double2 E = make_double2(0.0, 0.0), O = E;
-            if (m <= mmax && p < npairs) {
-                const size_t o = (((size_t)b * (mmax + 1) + m) * npairs + p) * 2;
-                E = eo2[o];
-                O = eo2[o + 1];
-                if (m == 0) { E.y = 0.0; O.y = 0.0; }
+        for (int q0 = threadIdx.x; q0 < G * H; q0 += U * blockDim.x) {
+            double2 E[U], O[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + u * blockDim.x;
+                E[u] = make_double2(0.0, 0.0);
+                O[u] = E[u];
+                if (q < G * H) {
+                    const int m = q / G, i = q - m * G;
+                    const int p = p0 + i;
+                    if (m <= mmax && p < npairs) {
+                        const size_t o = (((size_t)b * (mmax + 1) + m) * npairs + p) * 2;
+                        E[u] = eo2[o];
+                        O[u] = eo2[o + 1];
+                    }
+                }
             }
-            raw[(2 * i) * ld + padi(m)] = E;
-            raw[(2 * i + 1) * ld + padi(m)] = O;
-            if (i != cur) {
-                if (cur >= 0) atomicMax(&s_e[cur], emax);
-                cur = i;
-                emax = 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + u * blockDim.x;
+                if (q >= G * H) break;
+                const int m = q / G, i = q - m * G;
+                if (m == 0) { E[u].y = 0.0; O[u].y = 0.0; }
+                raw[(2 * i) * ld + padi(m)] = E[u];
+                raw[(2 * i + 1) * ld + padi(m)] = O[u];
+                if (i != cur) {
+                    if (cur >= 0) atomicMax(&s_e[cur], emax);
+                    cur = i;
+                    emax = 0;
+                }
+                emax = max(emax, max(dexp2(E[u]), dexp2(O[u])));
             }
-            emax = max(emax, max(dexp2(E), dexp2(O)));
         }
         if (cur >= 0) atomicMax(&s_e[cur], emax);
     }
