@@ -530,7 +530,7 @@ def roofline(mode, sht, table, peaks, alu_peaks, sm_max, batch=BATCH, lmax=LMAX,
         skip = max(0.0, skip_a if dom_name == "tc_analys" else skip_s)
         if mode == "tc_f64":
             algo = tc64_algorithmic_bytes(batch, lmax, nlat, zero_skip=skip)
-            kern = "k_tc64<0>" if dom_name == "tc_analys" else "k_tc64<1>"
+            kern = dom_name      # the stage's kernels, timed together
             note = ("digit-data pass + contraction, timed together; bytes: digit panels less the all-zero "
                     "chunks + FP64 data in and out")
         else:

@@ -62,9 +62,6 @@ __device__ __forceinline__ dfl two_sum(float a, float b)
     const float bb = __fsub_rn(s, a);
     return dfl(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
 }
-// The pair as hi + lo with |lo| <= ulp(hi) / 2 (the FFT's operations below
-// leave their results unnormalised; the conversions back to FP64 need this).
-__device__ __forceinline__ dfl renorm(dfl x) { return two_sum(x.hi, x.lo); }
 // The operations leave the pair unnormalised: the error-free sum or product
 // of the high parts and the low-order terms added in FP32, without the final
 // renormalisation, so |lo| can grow to a few units in the last place of hi
@@ -613,37 +610,26 @@ __device__ __forceinline__ dfl2 d2df2(double2 v, int u)
     return r;
 }
 
-// (z.hi + z.lo) 2^u as an FP64 number, from the bits: both significands are
-// aligned in a 64-bit integer (hi's leading bit at bit 53), summed, rounded to
-// 53 bits (half away from zero) and packed with the exponent.  Results below
-// 2^-1022 are flushed to zero.
-__device__ __forceinline__ double df2d(dfl z, int u)
+// f 2^u as an FP64 number, exactly: the float's sign and significand bits
+// placed in a double whose exponent field is the float's raised by u
+// (1023 - 127 = 896 re-biases it).  FP32 subnormals and zeros give 0, as do
+// results below 2^-1022; results beyond the FP64 range give infinity.
+__device__ __forceinline__ double f2d_pow2(float f, int u)
 {
-    z = renorm(z);
-    const unsigned bh = __float_as_uint(z.hi), bl = __float_as_uint(z.lo);
-    const int eh = (int)(bh >> 23) & 0xff, el = (int)(bl >> 23) & 0xff;
-    if (eh == 0) return 0.0;
-    // in units of 2^(eh - 180): hi = (1.f significand) << 30
-    long long S = (long long)((bh & 0x7fffffu) | 0x800000u) << 30;
-    if (bh >> 31) S = -S;
-    if (el != 0) {
-        long long ml = (long long)((bl & 0x7fffffu) | 0x800000u);
-        const int sh = el - eh + 30;            // <= 6 for a normalised pair
-        if (sh >= 0) ml <<= sh;
-        else ml = (sh > -40) ? (ml >> -sh) : 0;
-        S += (bl >> 31) ? -ml : ml;
-    }
-    const unsigned long long sgn = S < 0 ? (1ull << 63) : 0ull;
-    const unsigned long long a = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
-    if (a == 0) return 0.0;
-    int rs = 11 - __clzll((long long)a);       // shift that puts the leading bit at bit 52
-    unsigned long long m = rs > 0 ? (a + (1ull << (rs - 1))) >> rs : a << -rs;
-    if (m >> 53) { m >>= 1; ++rs; }
-    const int E = rs + eh + u + 895;            // biased exponent of m 2^(rs + eh - 180 + u)
-    if (E <= 0) return 0.0;
-    if (E >= 2047) return __longlong_as_double((long long)(sgn | (0x7ffull << 52)));
-    return __longlong_as_double((long long)(sgn | ((unsigned long long)E << 52) | (m & ((1ull << 52) - 1))));
+    const unsigned b = __float_as_uint(f);
+    const int e = (int)((b >> 23) & 0xffu), E = e + 896 + u;
+    const unsigned s = b & 0x80000000u;
+    if (e == 0 || E <= 0) return __hiloint2double((int)s, 0);
+    if (E >= 2047) return __hiloint2double((int)(s | 0x7ff00000u), 0);
+    return __hiloint2double((int)(s | ((unsigned)E << 20) | ((b >> 3) & 0xfffffu)), (int)(b << 29));
 }
+
+// (z.hi + z.lo) 2^u as an FP64 number: both parts are exact in FP64, so one
+// FP64 addition rounds their exact sum (to nearest, ties to even); the pair
+// need not be normalised.  (A bit-level sum of the two significands in a
+// 64-bit integer took about 60 integer instructions per value, a third of
+// the synthesis FFT's instructions; this takes about 20 and one FP64 add.)
+__device__ __forceinline__ double df2d(dfl z, int u) { return f2d_pow2(z.hi, u) + f2d_pow2(z.lo, u); }
 
 __device__ __forceinline__ dfl2 ld_twdf(const float4 *__restrict__ tw, int k)
 {
@@ -704,7 +690,10 @@ __device__ __forceinline__ void fft_synth_tile_df(const PlanView<double> &pv, co
     }
     __syncthreads();
     // 1. E (row 2i) and O (row 2i+1) of the G pairs in natural order, zero
-    //    above mmax, and the largest exponent per pair
+    //    above mmax, and the largest exponent per pair (G is a power of two
+    //    unless the plan has fewer pairs: shifts, not divisions, split q)
+    const bool gp2 = (G & (G - 1)) == 0;
+    const int lgG = __popc(G - 1);
     {
         // the loads of U items are issued before their stores (latency, not bandwidth, is the limit here)
         constexpr int U = 8;
@@ -717,7 +706,7 @@ __device__ __forceinline__ void fft_synth_tile_df(const PlanView<double> &pv, co
                 E[u] = make_double2(0.0, 0.0);
                 O[u] = E[u];
                 if (q < G * H) {
-                    const int m = q / G, i = q - m * G;
+                    const int m = gp2 ? q >> lgG : q / G, i = q - m * G;
                     const int p = p0 + i;
                     if (m <= mmax && p < npairs) {
                         const size_t o = (((size_t)b * (mmax + 1) + m) * npairs + p) * 2;
@@ -730,7 +719,7 @@ __device__ __forceinline__ void fft_synth_tile_df(const PlanView<double> &pv, co
             for (int u = 0; u < U; ++u) {
                 const int q = q0 + u * blockDim.x;
                 if (q >= G * H) break;
-                const int m = q / G, i = q - m * G;
+                const int m = gp2 ? q >> lgG : q / G, i = q - m * G;
                 if (m == 0) { E[u].y = 0.0; O[u].y = 0.0; }
                 raw[(2 * i) * ld + padi(m)] = E[u];
                 raw[(2 * i + 1) * ld + padi(m)] = O[u];
@@ -928,8 +917,10 @@ __device__ __forceinline__ void fft_analys_tile_df(const PlanView<double> &pv, c
         ebits = max(ebits, (unsigned)max(dexp2(so), dexp2(dd)));
     };
     const int mhalf = min(H / 2, mmax);
+    const bool gp2 = (G & (G - 1)) == 0;
+    const int lgG = __popc(G - 1);
     for (int q = threadIdx.x; q < G * (mhalf + 1); q += blockDim.x) {
-        const int m = q / G, i = q - m * G;
+        const int m = gp2 ? q >> lgG : q / G, i = q - m * G;
         const int pp = p0 + i;
         if (pp >= npairs) continue;
         const int m2 = H - m;   // its partner, when it is another position and an order of the plan
