@@ -665,12 +665,12 @@ __host__ __device__ constexpr size_t df_extra_smem(int G) { return (size_t)4 * (
 // Legendre output arrives as FP64 E, O; they are staged unconverted in the
 // rows while the pair's largest exponent is found, then converted in the
 // pre-twiddle.
-template <bool MIXED>
+template <bool MIXED, int LOGH = 0>
 __device__ __forceinline__ void fft_synth_tile_df(const PlanView<double> &pv, const double *__restrict__ eo,
                                                   double *__restrict__ grid, int b, int p0, int G, int op,
                                                   unsigned char *smem_raw)
 {
-    const int H = pv.nphi / 2, R = 2 * G;
+    const int H = LOGH ? (1 << LOGH) : pv.nphi / 2, R = 2 * G;
     const int TPR = row_tpr(H);
     const int ld = padi(H) + 1;
     dfl2 *wtab = reinterpret_cast<dfl2 *>(smem_raw);
@@ -778,6 +778,22 @@ __device__ __forceinline__ void fft_synth_tile_df(const PlanView<double> &pv, co
         if (scaled) { z.x = z.x * sc; z.y = z.y * sc; }
         out[idx] = make_double2(df2d(z.x, u), df2d(z.y, u));
     };
+    if constexpr (LOGH == 10) {
+        // inverse complex FFT of length 1024: radix 4, 16, 16, the last from registers to the grid
+        constexpr int NR = PassRegs<false>::n;
+        dfl2 v[NR];
+        if (r < R) stockham_load<dfl2, 4, 1, NR, true>(row, false, t, TPR, H, 1, wtab, v);
+        __syncthreads();
+        if (r < R) stockham_store_smem<dfl2, 4, NR, true>(row, t, TPR, H, 1, v);
+        __syncthreads();
+        if (r < R) stockham_load<dfl2, 16, 1, NR, true>(row, false, t, TPR, H, 4, wtab, v);
+        __syncthreads();
+        if (r < R) stockham_store_smem<dfl2, 16, NR, true>(row, t, TPR, H, 4, v);
+        __syncthreads();
+        if (r < R) stockham_load<dfl2, 16, 1, NR, true>(row, false, t, TPR, H, 64, wtab, v);
+        if (live_row) last_pass_out<16, NR>(v, t, TPR, H, put);
+        return;
+    }
     if (H == 1) {
         if (threadIdx.x < R && live_row) put(0, row[0]);
         return;
@@ -806,8 +822,8 @@ __device__ __forceinline__ void fft_synth_tile_df(const PlanView<double> &pv, co
 // the folds written (the field scale of the FP64-accurate contraction).
 // LOGH > 0: the row length is 2^LOGH, known at compile time, and the passes are
 // spelled out (radix 4, 16, 16 for LOGH = 10, the plan's order), so the index
-// arithmetic folds and no code of other radices sits in the kernel.  (The same
-// for synthesis measured slower, 0.525 against 0.509 ms at nphi = 2048.)
+// arithmetic folds and no code of other radices sits in the kernel (the
+// synthesis tile has the same form).
 template <bool MIXED, int LOGH = 0>
 __device__ __forceinline__ void fft_analys_tile_df(const PlanView<double> &pv, const double *__restrict__ grid,
                                                    double *__restrict__ sd, int b, int p0, int G, int op,
@@ -951,12 +967,12 @@ __device__ __forceinline__ void fft_analys_tile_df(const PlanView<double> &pv, c
     }
 }
 
-template <bool MIXED>
+template <bool MIXED, int LOGH = 0>
 __global__ void __launch_bounds__(512)
 k_fft_synth_df(PlanView<double> pv, const double *__restrict__ eo, double *__restrict__ grid, int G, int op)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fft_synth_tile_df<MIXED>(pv, eo, grid, blockIdx.y, blockIdx.x * G, G, op, smem_raw);
+    fft_synth_tile_df<MIXED, LOGH>(pv, eo, grid, blockIdx.y, blockIdx.x * G, G, op, smem_raw);
 }
 
 template <bool MIXED, int LOGH = 0>
@@ -1304,12 +1320,15 @@ cudaError_t launch_fft_synth_df(const PlanView<double> &pv, const double *eo, do
     size_t smem;
     fft_shape<double>(pv.nphi / 2, pv.npairs, G, threads, smem);
     smem += df_extra_smem(G);
-    const bool mixed = !pow2(pv.nphi / 2);
-    cudaError_t e = mixed ? set_smem(k_fft_synth_df<true>, smem) : set_smem(k_fft_synth_df<false>, smem);
+    const bool mixed = !pow2(pv.nphi / 2), h1024 = pv.nphi == 2048;
+    cudaError_t e = mixed ? set_smem(k_fft_synth_df<true>, smem)
+                          : (h1024 ? set_smem(k_fft_synth_df<false, 10>, smem) : set_smem(k_fft_synth_df<false>, smem));
     if (e != cudaSuccess) return e;
     dim3 gridd((unsigned)((pv.npairs + G - 1) / G), (unsigned)batch);
     if (mixed)
         k_fft_synth_df<true><<<gridd, threads, smem, s>>>(pv, eo, grid, G, (int)op);
+    else if (h1024)
+        k_fft_synth_df<false, 10><<<gridd, threads, smem, s>>>(pv, eo, grid, G, (int)op);
     else
         k_fft_synth_df<false><<<gridd, threads, smem, s>>>(pv, eo, grid, G, (int)op);
     return cudaGetLastError();
