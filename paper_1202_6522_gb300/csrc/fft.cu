@@ -786,11 +786,18 @@ __device__ __forceinline__ void fft_synth_tile_df(const PlanView<double> &pv, co
         __syncthreads();
         if (r < R) stockham_store_smem<dfl2, 4, NR, true>(row, t, TPR, H, 1, v);
         __syncthreads();
-        if (r < R) stockham_load<dfl2, 16, 1, NR, true>(row, false, t, TPR, H, 4, wtab, v);
-        __syncthreads();
-        if (r < R) stockham_store_smem<dfl2, 16, NR, true>(row, t, TPR, H, 4, v);
-        __syncthreads();
-        if (r < R) stockham_load<dfl2, 16, 1, NR, true>(row, false, t, TPR, H, 64, wtab, v);
+        // the two radix-16 passes run one copy of their code (a smaller
+        // instruction footprint for the two CTAs of an SM)
+        int Ns = 4;
+#pragma unroll 1
+        for (;;) {
+            if (r < R) stockham_load<dfl2, 16, 1, NR, true>(row, false, t, TPR, H, Ns, wtab, v);
+            if (Ns == 64) break;
+            __syncthreads();
+            if (r < R) stockham_store_smem<dfl2, 16, NR, true>(row, t, TPR, H, Ns, v);
+            __syncthreads();
+            Ns = 64;
+        }
         if (live_row) last_pass_out<16, NR>(v, t, TPR, H, put);
         return;
     }
@@ -886,14 +893,13 @@ __device__ __forceinline__ void fft_analys_tile_df(const PlanView<double> &pv, c
         __syncthreads();
         if (r < R) stockham_store_smem<dfl2, 4, NR, true>(row, t, TPR, H, 1, v);
         __syncthreads();
-        if (r < R) stockham_load<dfl2, 16, -1, NR, true>(row, false, t, TPR, H, 4, wtab, v);
-        __syncthreads();
-        if (r < R) stockham_store_smem<dfl2, 16, NR, true>(row, t, TPR, H, 4, v);
-        __syncthreads();
-        if (r < R) stockham_load<dfl2, 16, -1, NR, true>(row, false, t, TPR, H, 64, wtab, v);
-        __syncthreads();
-        if (r < R) stockham_store_smem<dfl2, 16, NR, true>(row, t, TPR, H, 64, v);
-        __syncthreads();
+#pragma unroll 1
+        for (int Ns = 4; Ns <= 64; Ns *= 16) {   // one copy of the radix-16 code
+            if (r < R) stockham_load<dfl2, 16, -1, NR, true>(row, false, t, TPR, H, Ns, wtab, v);
+            __syncthreads();
+            if (r < R) stockham_store_smem<dfl2, 16, NR, true>(row, t, TPR, H, Ns, v);
+            __syncthreads();
+        }
     } else if (H > 1) {
         // forward complex FFT of length H
         int Ns = 1;
