@@ -49,12 +49,6 @@ struct __align__(8) dfl {
 };
 struct __align__(16) dfl2 { dfl x, y; };
 
-// s + e = a + b exactly, for |a| >= |b| or a = 0 (Dekker)
-__device__ __forceinline__ dfl fast_two_sum(float a, float b)
-{
-    const float s = __fadd_rn(a, b);
-    return dfl(s, __fsub_rn(b, __fsub_rn(s, a)));
-}
 // s + e = a + b exactly for any a, b (Knuth)
 __device__ __forceinline__ dfl two_sum(float a, float b)
 {
@@ -582,25 +576,23 @@ __device__ __forceinline__ int dexp2(double2 v)
 }
 
 // v 2^-u as a double-float, from the bits of v: hi takes the leading 24
-// significand bits, lo the remaining 29 (rounded to 24 by the integer-to-float
-// conversion), then the pair is renormalised.  Scaled values below 2^-126 are
-// flushed to zero (the scale puts the pair's largest value in [1, 2)), as are
-// FP64 subnormals.
+// significand bits (truncated), lo the remaining 29 (rounded to 24 by the
+// integer-to-float conversion), so 0 <= |lo| < ulp(hi), same sign: an
+// unnormalised pair, which the operations above accept.  Scaled values below
+// 2^-126 are flushed to zero (the scale puts the pair's largest value in
+// [1, 2), so fe <= 0), as are FP64 subnormals.  Selects, not branches.
 __device__ __forceinline__ dfl d2df(double v, int u)
 {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-    const int E = (int)(bits >> 52) & 0x7ff;
-    const int fe = E - 1023 - u;
-    if (E == 0 || fe < -126) return dfl(0.f, 0.f);
-    const unsigned sgn = (unsigned)(bits >> 32) & 0x80000000u;
-    const float hi = __uint_as_float(sgn | ((unsigned)(fe + 127) << 23) | (unsigned)((bits >> 29) & 0x7fffffu));
-    float lo = 0.f;
-    if (fe >= -74) {
-        // the low 29 bits weigh 2^(fe - 52) each
-        lo = __fmul_rn(__uint2float_rn((unsigned)(bits & 0x1fffffffu)), __uint_as_float((unsigned)(fe + 75) << 23));
-        lo = __uint_as_float(__float_as_uint(lo) | sgn);
-    }
-    return fast_two_sum(hi, lo);
+    const unsigned hw = (unsigned)__double2hiint(v), lw = (unsigned)__double2loint(v);
+    const int E = (int)((hw >> 20) & 0x7ffu), fe = E - 1023 - u;
+    const unsigned sgn = hw & 0x80000000u;
+    const unsigned top = __funnelshift_r(lw, hw, 29) & 0x7fffffu;           // significand bits 51..29
+    const float hi = __uint_as_float(sgn | ((unsigned)(fe + 127) << 23) | top);
+    // the low 29 bits weigh 2^(fe - 52) each; a scale below FP32's normal range gives 0
+    float lo = __fmul_rn(__uint2float_rn(lw & 0x1fffffffu), __uint_as_float((unsigned)max(fe + 75, 0) << 23));
+    lo = __uint_as_float(__float_as_uint(lo) | sgn);
+    const bool zero = E == 0 || fe < -126;
+    return dfl(zero ? 0.f : hi, zero ? 0.f : lo);
 }
 __device__ __forceinline__ dfl2 d2df2(double2 v, int u)
 {
@@ -616,12 +608,13 @@ __device__ __forceinline__ dfl2 d2df2(double2 v, int u)
 // results below 2^-1022; results beyond the FP64 range give infinity.
 __device__ __forceinline__ double f2d_pow2(float f, int u)
 {
-    const unsigned b = __float_as_uint(f);
+    const unsigned b = __float_as_uint(f), s = b & 0x80000000u;
     const int e = (int)((b >> 23) & 0xffu), E = e + 896 + u;
-    const unsigned s = b & 0x80000000u;
-    if (e == 0 || E <= 0) return __hiloint2double((int)s, 0);
-    if (E >= 2047) return __hiloint2double((int)(s | 0x7ff00000u), 0);
-    return __hiloint2double((int)(s | ((unsigned)E << 20) | ((b >> 3) & 0xfffffu)), (int)(b << 29));
+    unsigned hw = s | ((unsigned)E << 20) | ((b >> 3) & 0xfffffu), lw = b << 29;
+    const bool zero = e == 0 || E <= 0, inf = E >= 2047;
+    hw = zero ? s : (inf ? (s | 0x7ff00000u) : hw);
+    lw = zero || inf ? 0u : lw;
+    return __hiloint2double((int)hw, (int)lw);
 }
 
 // (z.hi + z.lo) 2^u as an FP64 number: both parts are exact in FP64, so one
