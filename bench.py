@@ -81,7 +81,7 @@ def legendre_flops_per_launch(batch, lmax=LMAX, nlat=NLAT):
 def tc64_algorithmic_bytes(batch, lmax=LMAX, nlat=NLAT, zero_skip=0.0):
     """Bytes one FP64-accurate tensor-core Legendre stage must move: 7 bf16
     digit slices (14 B) of every P_n^m(x_j) of one hemisphere, less the
-    all-zero chunks it skips, plus the FP64 spectra and the FP64 E/O (or s/d)
+    all-zero 8-row groups it skips, plus the FP64 spectra and the FP64 E/O (or s/d)
     intermediate of the batch (the digit data the stage writes and reads
     back, and the tile padding, are not counted)."""
     npairs = (nlat + 1) // 2
@@ -532,7 +532,7 @@ def roofline(mode, sht, table, peaks, alu_peaks, sm_max, batch=BATCH, lmax=LMAX,
             algo = tc64_algorithmic_bytes(batch, lmax, nlat, zero_skip=skip)
             kern = dom_name      # the stage's kernels, timed together
             note = ("digit-data pass + contraction, timed together; bytes: digit panels less the all-zero "
-                    "chunks + FP64 data in and out")
+                    "8-row groups + FP64 data in and out")
         else:
             algo = tc_algorithmic_bytes(batch, lmax, nlat, polar_skip=skip)
             kern = "k_tc_ws<0>" if dom_name == "tc_analys" else "k_tc_ws<1>"

@@ -314,7 +314,8 @@ SHT_API const char *sht_kernel_name(int kind);
  * loaded nor multiplied (SHT_TC_OTF: neither generated nor multiplied).
  * Fractions of the synthesis and analysis chunks skipped -- of the panels if
  * built, else of the on-the-fly mode's tables, else of the SHT_TC_F64 digit
- * panels (chunks whose digits are all zero) -- or -1 if none is built. */
+ * panels (per chunk, the 8-row groups below its first group with a nonzero
+ * digit, which the contraction does not read) -- or -1 if none is built. */
 SHT_API int sht_tc_polar_skip(sht_handle h, double *synth_frac, double *analys_frac);
 
 /* Threshold of the static polar optimisation (Sec. 3.1; the paper leaves its

@@ -319,6 +319,11 @@ int ensure_panels64(sht::Plan &p)
     if (e == cudaSuccess) e = cudaMalloc(&p.d_e64_a, sizeof(int) * (size_t)p.nlm);
     if (e == cudaSuccess) e = cudaMalloc(&p.d_c064_s, sizeof(int) * (size_t)(p.mmax + 1) * T_s);
     if (e == cudaSuccess) e = cudaMalloc(&p.d_c064_a, sizeof(int) * (size_t)(p.mmax + 1) * T_a);
+    const size_t ngs = (size_t)(p.mmax + 1) * T_s * 32, nga = (size_t)(p.mmax + 1) * T_a * 32;   // 2 parities x 16 groups
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_gf64_s, sizeof(unsigned short) * ngs);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_gf64_a, sizeof(unsigned short) * nga);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_zero64, sht::tc64_zero_bytes());
+    if (e == cudaSuccess) e = cudaMemset(p.d_zero64, 0, sht::tc64_zero_bytes());
     if (e == cudaSuccess) e = cudaMalloc(&p.d_fcol, sizeof(int) * (size_t)sht::tc64_max_batch());
     if (e == cudaSuccess) e = cudaMemcpy(p.d_off64_s, off_s.data(), ob, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p.d_off64_a, off_a.data(), ob, cudaMemcpyHostToDevice);
@@ -327,7 +332,7 @@ int ensure_panels64(sht::Plan &p)
     if (e == cudaSuccess) e = cudaMemset(p.p64_a, 0, ba);
     if (e == cudaSuccess)
         e = sht::tc64_build(p.view64(), p.d_off64_s, p.d_off64_a, p.p64_s, p.p64_a, p.d_e64_s, p.d_e64_a, p.d_c064_s,
-                            p.d_c064_a, 0);
+                            p.d_c064_a, p.d_gf64_s, p.d_gf64_a, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -339,17 +344,22 @@ int ensure_panels64(sht::Plan &p)
         // balanced work lists of the persistent contraction, two CTAs per SM
         int dev = 0, sms = 0;
         std::vector<int> c0s((size_t)(p.mmax + 1) * T_s), c0a((size_t)(p.mmax + 1) * T_a), ss, sa;
+        std::vector<unsigned short> gfs(ngs), gfa(nga);
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = cudaMemcpy(c0s.data(), p.d_c064_s, sizeof(int) * c0s.size(), cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) e = cudaMemcpy(c0a.data(), p.d_c064_a, sizeof(int) * c0a.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(gfs.data(), p.d_gf64_s, sizeof(unsigned short) * ngs, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(gfa.data(), p.d_gf64_a, sizeof(unsigned short) * nga, cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) {
             sms *= sht::tc64_ctas_per_sm();
             std::vector<int> cost, group;
-            sht::tc64_costs(p.lmax, p.mmax, p.mres, p.npairs, true, c0s, cost, group);
+            sht::tc64_costs(p.lmax, p.mmax, p.mres, p.npairs, true, c0s, gfs, cost, group);
             sht::schedule_lpt(cost, group, sms, ss);
-            sht::tc64_costs(p.lmax, p.mmax, p.mres, p.npairs, false, c0a, cost, group);
+            sht::tc64_costs(p.lmax, p.mmax, p.mres, p.npairs, false, c0a, gfa, cost, group);
             sht::schedule_lpt(cost, group, sms, sa);
+            // fractions of the panel bytes the contraction does not read
+            sht::tc64_skip_stats(p.lmax, p.mmax, p.mres, p.npairs, c0s, c0a, gfs, gfa, p.skip64_s, p.skip64_a);
             e = cudaMalloc(&p.d_sched64_s, sizeof(int) * ss.size());
         }
         if (e == cudaSuccess) e = cudaMalloc(&p.d_sched64_a, sizeof(int) * sa.size());
@@ -361,12 +371,6 @@ int ensure_panels64(sht::Plan &p)
             return fail(SHT_ENOMEM, std::string("scheduling the digit-slice contraction: ") + cudaGetErrorString(e));
         }
         p.sched64_ctas = sms;
-    }
-    // fractions of the digit chunks skipped as all-zero (whole chunks per (m, tile))
-    if (sht::tc_polar_stats(p.lmax, p.mmax, p.mres, p.npairs, p.d_c064_s, p.d_c064_a, p.skip64_s, p.skip64_a) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        p.skip64_s = p.skip64_a = -1.0;
     }
     return SHT_OK;
 }
@@ -740,7 +744,7 @@ int run_tc64(sht::Plan &p, bool synth, const void *in_, void *out_, int batch, s
             double *out = static_cast<double *>(out_) + (size_t)b0 * grid_n;
             rc = timed(p, SHT_K_TC_SYNTH, s, "FP64 tensor-core synthesis launch", [&] {
                 return sht::launch_tc64(true, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.p64_s, p.d_off64_s, p.d_c064_s,
-                                        p.d_sched64_s, p.sched64_ctas, p.d_e64_s, p.d_dchunk64, p.d_fcol, data, in, inter, nb, op, p.d_err, s);
+                                        p.d_gf64_s, p.d_zero64, p.d_sched64_s, p.sched64_ctas, p.d_e64_s, p.d_dchunk64, p.d_fcol, data, in, inter, nb, op, p.d_err, s);
             });
             if (rc) return rc;
             rc = timed(p, SHT_K_FFT_SYNTH, s, "fft synthesis launch",
@@ -756,7 +760,7 @@ int run_tc64(sht::Plan &p, bool synth, const void *in_, void *out_, int batch, s
             if (rc) return rc;
             rc = timed(p, SHT_K_TC_ANALYS, s, "FP64 tensor-core analysis launch", [&] {
                 return sht::launch_tc64(false, p.lmax, p.mmax, p.mres, p.npairs, p.nlm, p.p64_a, p.d_off64_a, p.d_c064_a,
-                                        p.d_sched64_a, p.sched64_ctas, p.d_e64_a, p.d_dchunk64, p.d_fcol, data, inter, out, nb, op,
+                                        p.d_gf64_a, p.d_zero64, p.d_sched64_a, p.sched64_ctas, p.d_e64_a, p.d_dchunk64, p.d_fcol, data, inter, out, nb, op,
                                         p.d_err, s, true);
             });
         }
@@ -1049,7 +1053,7 @@ int sht_tc_polar_skip(sht_handle h, double *synth_frac, double *analys_frac)
     if (!h) return fail(SHT_EINVAL, "null handle");
     if (!synth_frac || !analys_frac) return fail(SHT_EINVAL, "null output pointer");
     // the panels' tables if built, else those of the on-the-fly mode, else the
-    // FP64-accurate mode's all-zero digit chunks
+    // FP64-accurate mode's digit groups it does not read (all-zero 8-row groups)
     const sht::Plan &p = h->p;
     *synth_frac = p.panel_s ? p.polar_skip_s : (p.otf_state > 0 ? p.otf_skip_s : (p.p64_s ? p.skip64_s : -1.0));
     *analys_frac = p.panel_s ? p.polar_skip_a : (p.otf_state > 0 ? p.otf_skip_a : (p.p64_s ? p.skip64_a : -1.0));

@@ -427,6 +427,9 @@ void plan_free_tc64(Plan &p)
     cudaFree(p.p64_s); cudaFree(p.p64_a); cudaFree(p.d_off64_s); cudaFree(p.d_off64_a); cudaFree(p.d_dchunk64);
     cudaFree(p.d_e64_s); cudaFree(p.d_e64_a); cudaFree(p.d_c064_s); cudaFree(p.d_c064_a); cudaFree(p.d_fcol);
     cudaFree(p.d_sched64_s); cudaFree(p.d_sched64_a);
+    cudaFree(p.d_gf64_s); cudaFree(p.d_gf64_a); cudaFree(p.d_zero64);
+    p.d_gf64_s = p.d_gf64_a = nullptr;
+    p.d_zero64 = nullptr;
     p.p64_s = p.p64_a = nullptr;
     p.d_off64_s = p.d_off64_a = p.d_dchunk64 = nullptr;
     p.d_e64_s = p.d_e64_a = p.d_c064_s = p.d_c064_a = p.d_fcol = nullptr;

@@ -159,13 +159,15 @@ struct Plan {
     size_t nchunk64_s = 0;                                // ... synthesis data chunks over all orders
     int *d_e64_s = nullptr, *d_e64_a = nullptr;           // ... row exponents
     int *d_c064_s = nullptr, *d_c064_a = nullptr;         // ... first nonzero chunk per (m, tile)
+    unsigned short *d_gf64_s = nullptr, *d_gf64_a = nullptr;  // ... and per (m, tile, parity, 8-row group)
+    unsigned char *d_zero64 = nullptr;                    // ... zeros for the stage rows it does not read
     int *d_sched64_s = nullptr, *d_sched64_a = nullptr;   // ... work lists of the persistent contraction
     int sched64_ctas = 0;                                 // ... and their CTA count
     int *d_schedv_s[2] = {nullptr, nullptr};              // vector contraction work lists (1 | 2 field halves)
     int *d_schedv_a[2] = {nullptr, nullptr};
     int schedv_ctas = 0;
     int *d_fcol = nullptr;                                // ... field exponents of a launch
-    double skip64_s = -1, skip64_a = -1;                  // ... fractions of all-zero digit chunks
+    double skip64_s = -1, skip64_a = -1;                  // ... fractions of the panel bytes not read
     float4 *otf_seeds = nullptr;                // on-the-fly mode: recurrence seeds
     unsigned long long *d_segoff = nullptr;     // first segment of each order
     int *d_c0o_s = nullptr, *d_c0o_a = nullptr; // on-the-fly mode: first live chunk per (m, tile)
@@ -344,7 +346,13 @@ void tc64_panel_layout(int lmax, int mmax, int mres, int npairs, std::vector<uns
                        std::vector<unsigned long long> &dchunk, size_t &nchunk_s);
 size_t tc64_data_bytes(int mmax, int npairs, size_t nchunk_s);
 cudaError_t tc64_build(const PlanView<double> &pv, const unsigned long long *off_s, const unsigned long long *off_a,
-                       unsigned char *ps, unsigned char *pa, int *es, int *ea, int *c0_s, int *c0_a, cudaStream_t st);
+                       unsigned char *ps, unsigned char *pa, int *es, int *ea, int *c0_s, int *c0_a,
+                       unsigned short *gf_s, unsigned short *gf_a, cudaStream_t st);
+// Bytes of the zero buffer the FP64-accurate contraction copies from.
+size_t tc64_zero_bytes();
+void tc64_skip_stats(int lmax, int mmax, int mres, int npairs, const std::vector<int> &c0s,
+                     const std::vector<int> &c0a, const std::vector<unsigned short> &gfs,
+                     const std::vector<unsigned short> &gfa, double &frac_s, double &frac_a);
 // fcol_ready: fcol already holds the field exponents of `in` (else this
 // computes them first).
 // Work lists of persistent CTAs, longest processing time first: the items
@@ -355,16 +363,18 @@ cudaError_t tc64_build(const PlanView<double> &pv, const unsigned long long *off
 void schedule_lpt(const std::vector<int> &cost, const std::vector<int> &group, int nctas, std::vector<int> &sched);
 // Item costs and groups of the persistent FP64-accurate contraction (item =
 // 2 (m tiles + tile) + parity; group = (m, parity), whose tiles read the same
-// data digits) from the first nonzero chunks c0 [mmax+1][tiles].
+// data digits) from the first nonzero chunks c0 [mmax+1][tiles] and gf
+// [mmax+1][tiles][parity][16 groups]: the panel groups each item reads.
 void tc64_costs(int lmax, int mmax, int mres, int npairs, bool synth, const std::vector<int> &c0,
-                std::vector<int> &cost, std::vector<int> &group);
+                const std::vector<unsigned short> &gf, std::vector<int> &cost, std::vector<int> &group);
 // Item costs and groups of the persistent vector contraction (item =
 // (m tiles + tile) halves + half; group = m: the halves of a tile share its
 // panel chunks, the tiles share the data) from its first live chunks c0.
 void tc_vec_costs(int lmax, int mmax, int mres, int npairs, bool synth, int halves, const std::vector<int> &c0,
                   std::vector<int> &cost, std::vector<int> &group);
 cudaError_t launch_tc64(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const unsigned char *panel,
-                        const unsigned long long *off, const int *c0, const int *sched, int nctas, const int *erow,
+                        const unsigned long long *off, const int *c0, const unsigned short *gf,
+                        const unsigned char *zero, const int *sched, int nctas, const int *erow,
                         const unsigned long long *dchunk, int *fcol, unsigned char *data, const double *in,
                         double *out, int batch, Op op, int *err, cudaStream_t st, bool fcol_ready = false);
 // Sets fcol[0 .. batch) to "no value yet" before a producer raises it.

@@ -29,14 +29,17 @@
 // Work item: one (order m, 128-row tile, parity of n - m).  Two persistent
 // CTAs per SM walk balanced lists of items with 192 threads: warps 0-3 run the
 // epilogue, warp 4 lane 0 issues the MMAs, warp 5 lane 0 streams the parity's
-// 28 KB of each panel chunk and its 8 KB of data by bulk copy into a ring of 3
-// stages that runs on across items.  Tensor memory: kL levels x 32 columns (16
+// share of each panel chunk (up to 28 KB: from the chunk's first 8-row group
+// with a nonzero digit on, the polar optimisation of Sec. 3.1 at the digits'
+// own precision) and its 6 KB of data by bulk copy into a ring of 3 stages that
+// runs on across items.  Tensor memory: kL levels x 32 columns (16
 // fields x re/im) = 256 per CTA.  Every wait is bounded; a kernel whose wait
 // gave up records SHT_ETIMEOUT and skips the rest of its output.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <vector>
 
@@ -75,8 +78,17 @@ constexpr int kParCols = kL * kLevelCols;      // accumulator columns of a CTA: 
 constexpr uint32_t kTmemCols = kParCols;       // one accumulator per CTA: half of tensor memory
 constexpr int kExpNone = INT_MIN / 2;          // exponent of an all-zero row or column
 
-// Panel slice block of (slice i, parity par) in a chunk.
-__host__ __device__ __forceinline__ uint32_t pblk(int i, int par) { return (uint32_t)(par * kPPar + i * kPBlk); }
+// Panel chunk layout: per parity (kPPar bytes), 8-row group g of slice i at
+// g kGS + i kSbo, a [8 x kKc] bf16 pair of core matrices -- the seven slices of
+// a group side by side, so that groups [g0, g1) of every slice are one
+// contiguous range (one bulk copy).  The MMA operand of slice i starts at
+// i kSbo with 8-row group stride kGS.
+constexpr uint32_t kGS = (uint32_t)kSA * kSbo;
+__host__ __device__ __forceinline__ uint32_t pofs(int i, int par, int row, int k)
+{
+    return (uint32_t)(par * kPPar) + (uint32_t)(row >> 3) * kGS + (uint32_t)i * kSbo + (uint32_t)(k >> 3) * kLbo +
+           (uint32_t)((row & 7) * 16 + (k & 7) * 2);
+}
 
 // Z 2^k as a double, for a 128-bit integer Z, with integer operations only
 // (the FP64 pipe is the scarce one): normalise, round the 53-bit mantissa to
@@ -220,17 +232,15 @@ __global__ void k_p64_build(PlanView<double> pv, const int *__restrict__ es, con
         int d[kSA];
         digits_fp64(P, e_row, d);
         unsigned char *b = sbase + (size_t)(kk / kKc) * kPChunk;
-        const uint32_t o = blk_off(row, kk % kKc);
 #pragma unroll
         for (int i = 0; i < kSA; ++i)
-            *reinterpret_cast<__nv_bfloat16 *>(b + pblk(i, par) + o) = __int2bfloat16_rn(d[i]);
+            *reinterpret_cast<__nv_bfloat16 *>(b + pofs(i, par, row, kk % kKc)) = __int2bfloat16_rn(d[i]);
         digits_fp64(P, ea[col + nn], d);
         const int mt = kk / kR, r = kk % kR;
         unsigned char *ba = abase + ((size_t)mt * kch + kc) * kPChunk;
-        const uint32_t oa = blk_off(r, pc);
 #pragma unroll
         for (int i = 0; i < kSA; ++i)
-            *reinterpret_cast<__nv_bfloat16 *>(ba + pblk(i, par) + oa) = __int2bfloat16_rn(d[i]);
+            *reinterpret_cast<__nv_bfloat16 *>(ba + pofs(i, par, r, pc)) = __int2bfloat16_rn(d[i]);
     });
 }
 
@@ -266,6 +276,53 @@ __global__ void k_p64_first_live(int synth, int lmax, int mres, int npairs, int 
         }
     }
     if (threadIdx.x == 0) c0[m * ntiles + tile] = first;
+}
+
+// First chunk with a nonzero digit of each (parity, 8-row group) of a tile,
+// nchunks if none: gfirst[((m ntiles + tile) 2 + par) 16 + g].  The rows of a
+// group below its first live chunk hold only zero digits (their P lies 2^-48
+// or more below the row's largest), so the contraction need not read them.
+// Thread t: (parity, group) t / 8, one eighth of the group's kGS bytes.
+__global__ void k_p64_group_first(int synth, int lmax, int mres, int npairs, int ntiles,
+                                  const unsigned long long *__restrict__ off,
+                                  const unsigned char *__restrict__ panel, unsigned short *__restrict__ gfirst)
+{
+    const int m = blockIdx.y, tile = blockIdx.x;   // order index m, order m mres
+    const int L = lmax - m * mres + 1, Le = (L + 1) / 2;
+    const int nchunks = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
+    const bool valid = synth || tile * kR < Le;
+    const int pg = threadIdx.x >> 3, part = threadIdx.x & 7, par = pg >> 4, g = pg & 15;
+    constexpr int kV = (int)(kGS / 16);              // 16-byte words of one 8-row group (all slices)
+    const unsigned gmask = 0xffu << (threadIdx.x & 24);
+    int first = nchunks;
+    if (valid) {
+        const unsigned char *base = panel + off[m] + (size_t)tile * nchunks * kPChunk;
+        for (int c = 0; c < nchunks; ++c) {
+            bool nz = false;
+            if (first == nchunks) {
+                for (int v = part; v < kV; v += 8) {
+                    const uint4 x = *reinterpret_cast<const uint4 *>(base + (size_t)c * kPChunk + (size_t)par * kPPar +
+                                                                     (size_t)g * kGS + (size_t)v * 16);
+                    nz |= (x.x | x.y | x.z | x.w) != 0u;
+                }
+            }
+            nz = __any_sync(gmask, nz);   // the 8 threads of (parity, group)
+            if (nz && first == nchunks) first = c;
+            if (__syncthreads_and(first != nchunks)) break;
+        }
+    }
+    if (part == 0) gfirst[(((size_t)m * ntiles + tile) * 2 + par) * 16 + g] = (unsigned short)min(first, 65535);
+}
+
+// First live 8-row group of a chunk: the smallest g < hi whose first live
+// chunk is at or before c (hi if none).  Rows of the tile below it are all-zero
+// digits in chunk c; from it on they are copied (any dead group among them
+// holds zeros in the panel too).
+__host__ __device__ __forceinline__ int first_live_group(const unsigned short *f, int c, int hi)
+{
+    for (int g = 0; g < hi; ++g)
+        if ((int)f[g] <= c) return g;
+    return hi;
 }
 
 // Column exponents: f[b] with |x| < 2^f[b] for every value of field b
@@ -379,6 +436,8 @@ struct Tc64Args {
     const unsigned char *panel;
     const unsigned long long *off;         // per-order panel byte offsets
     const int *c0;                         // per (m, tile): first chunk with a nonzero digit
+    const unsigned short *gf;              // per (m, tile, parity, 8-row group): first chunk with a nonzero digit
+    const unsigned char *zero;             // kPPar zero bytes, copied into the stage rows not read
     const int *erow;                       // row exponents (synthesis [m][pair], analysis packed [nlm])
     const int *fcol;                       // field exponents
     const unsigned char *data;             // blocked data digits
@@ -460,7 +519,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_tc64(Tc64Args a, const
 #pragma unroll
             for (int i = 0; i < kSA; ++i) {
                 idesc[i] = tc::idesc_bf16_f32(kR, (kL - i) * kNC);
-                da[i] = tc::smem_desc(smem + pblk(i, 0), kLbo, kSbo);
+                da[i] = tc::smem_desc(smem + (size_t)i * kSbo, kLbo, kGS);
             }
             db = tc::smem_desc(smem + kPPar, kLbo, kSbo);
             const uint64_t sstep = (uint64_t)kStage >> 4;
@@ -497,6 +556,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_tc64(Tc64Args a, const
             // ---------------- producer ----------------
             bool ok = true;
             unsigned u = 0;
+            int zl[kStages];   // leading 8-row groups of each stage known to hold zeros
+#pragma unroll
+            for (int q = 0; q < kStages; ++q) zl[q] = 0;
             for (int kk = k0; ok && kk < k1; ++kk) {
                 const Item64 it = item64<SYNTH>(a, items[kk]);
                 if (!it.valid) continue;
@@ -506,12 +568,24 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_tc64(Tc64Args a, const
                     a.data + (SYNTH ? a.dchunk[it.m] : (unsigned long long)it.m * it.nchunks) *
                                  (unsigned long long)kDChunk + (size_t)it.par * kDBlk;
                 // rows of the tile that hold a pair (synthesis) or a degree (analysis):
-                // only their 8-row groups are copied; the rest of the stage keeps
-                // whatever it held, which reaches only accumulator rows the
-                // epilogue does not write
+                // 8-row groups [0, hi).  Of those, the groups below the chunk's
+                // first live one, g0, are all-zero digits: they are not read, and
+                // the stage must hold zeros there for the MMAs.  zl[q] counts the
+                // leading groups of stage q known to be zero; groups [zl, g0) are
+                // zeroed from a zero buffer (in L2) when g0 is above it, which
+                // happens at an item's first chunks only, since g0 never grows
+                // with c.  Groups from hi on keep whatever the stage held: they
+                // reach only accumulator rows the epilogue does not write.
                 const int live_rows = min(kR, (SYNTH ? a.npairs : it.Le) - it.tile * kR);
-                const uint32_t slice_bytes = (uint32_t)((live_rows + 7) / 8) * kSbo;
-                const bool full = slice_bytes == (uint32_t)kPBlk;
+                const int hi = (live_rows + 7) / 8;
+                uint4 fv[2];   // the item's 16 first live chunks, one per 8-row group
+                {
+                    const uint4 *fp = reinterpret_cast<const uint4 *>(
+                        a.gf + (((size_t)it.m * a.ntiles + it.tile) * 2 + it.par) * 16);
+                    fv[0] = fp[0];
+                    fv[1] = fp[1];
+                }
+                const unsigned short *f = reinterpret_cast<const unsigned short *>(fv);
                 for (int c = it.cstart; c < it.nchunks; ++c, ++u) {
                     const unsigned q = u % kStages;
                     if (u >= kStages && !wait_or_abort(&bar_mma[q], (u / kStages - 1) & 1, &s_abort)) {
@@ -520,14 +594,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_tc64(Tc64Args a, const
                     }
                     unsigned char *st = smem + (size_t)q * kStage;
                     const unsigned char *src = panel + (size_t)c * kPChunk;
-                    tc::mbar_arrive_expect_tx(&bar_load[q], (uint32_t)kSA * slice_bytes + (uint32_t)kDBlk);
-                    if (full) {
-                        tc::bulk_g2s_stream(st, src, (uint32_t)kPPar, &bar_load[q]);
-                    } else {
-#pragma unroll 1
-                        for (int i = 0; i < kSA; ++i)
-                            tc::bulk_g2s_stream(st + pblk(i, 0), src + pblk(i, 0), slice_bytes, &bar_load[q]);
-                    }
+                    const int g0 = first_live_group(f, c, hi), z0 = zl[q];
+                    const int nzero = g0 > z0 ? g0 - z0 : 0;
+                    tc::mbar_arrive_expect_tx(&bar_load[q], (uint32_t)(hi - g0 + nzero) * kGS + (uint32_t)kDBlk);
+                    if (g0 < hi)
+                        tc::bulk_g2s_stream(st + (size_t)g0 * kGS, src + (size_t)g0 * kGS, (uint32_t)(hi - g0) * kGS,
+                                            &bar_load[q]);
+                    if (nzero > 0) tc::bulk_g2s(st + (size_t)z0 * kGS, a.zero, (uint32_t)nzero * kGS, &bar_load[q]);
+                    zl[q] = g0;
                     tc::bulk_g2s(st + kPPar, data + (size_t)c * kDChunk, (uint32_t)kDBlk, &bar_load[q]);
                 }
             }
@@ -628,7 +702,7 @@ int tc64_ctas_per_sm() { return kCtasPerSm; }
 // costed as their nonzero chunks plus two for the epilogue (-1: no rows),
 // grouped by (order index, parity).
 void tc64_costs(int lmax, int mmax, int mres, int npairs, bool synth, const std::vector<int> &c0,
-                std::vector<int> &cost, std::vector<int> &group)
+                const std::vector<unsigned short> &gf, std::vector<int> &cost, std::vector<int> &group)
 {
     int ts, ta;
     tc_tile_counts(lmax, npairs, ts, ta);
@@ -641,9 +715,51 @@ void tc64_costs(int lmax, int mmax, int mres, int npairs, bool synth, const std:
         const int L = lmax - m * mres + 1, Le = (L + 1) / 2;
         if (!synth && tile * kR >= Le) continue;
         const int nchunks = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
-        cost[w] = nchunks - c0[(size_t)m * ntiles + tile] + 2;
+        const int hi = (std::min(kR, (synth ? npairs : Le) - tile * kR) + 7) / 8;
+        const unsigned short *f = gf.data() + ((size_t)(w >> 1) * 2 + (w & 1)) * 16;
+        // in 8-row groups of panel (kGS bytes each): the groups read, 8 per
+        // chunk for the data copy and the MMAs, 32 for the epilogue
+        int units = 32;
+        for (int c = c0[(size_t)m * ntiles + tile]; c < nchunks; ++c)
+            units += hi - first_live_group(f, c, hi) + 8;
+        cost[w] = units;
     }
 }
+
+// Fractions of the digit panels' bytes the contraction does not read: the
+// chunks before the tile's first live chunk and the 8-row groups of each
+// (m, tile, parity) and chunk below the chunk's first live group.
+void tc64_skip_stats(int lmax, int mmax, int mres, int npairs, const std::vector<int> &c0s,
+                     const std::vector<int> &c0a, const std::vector<unsigned short> &gfs,
+                     const std::vector<unsigned short> &gfa, double &frac_s, double &frac_a)
+{
+    int ts, ta;
+    tc_tile_counts(lmax, npairs, ts, ta);
+    for (int dir = 0; dir < 2; ++dir) {
+        const bool synth = dir == 0;
+        const int ntiles = synth ? ts : ta;
+        const std::vector<int> &c0 = synth ? c0s : c0a;
+        const std::vector<unsigned short> &gf = synth ? gfs : gfa;
+        double read = 0, tot = 0;
+        for (int m = 0; m <= mmax; ++m) {
+            const int Le = (lmax - m * mres + 2) / 2;
+            const int nchunks = synth ? (Le + kKc - 1) / kKc : (npairs + kKc - 1) / kKc;
+            for (int t = 0; t < ntiles; ++t) {
+                if (!synth && t * kR >= Le) continue;
+                const int hi = (std::min(kR, (synth ? npairs : Le) - t * kR) + 7) / 8;
+                for (int par = 0; par < 2; ++par) {
+                    const unsigned short *f = gf.data() + (((size_t)m * ntiles + t) * 2 + par) * 16;
+                    tot += (double)nchunks * hi;
+                    for (int c = c0[(size_t)m * ntiles + t]; c < nchunks; ++c)
+                        read += hi - first_live_group(f, c, hi);
+                }
+            }
+        }
+        (synth ? frac_s : frac_a) = tot > 0 ? 1.0 - read / tot : 0.0;
+    }
+}
+
+size_t tc64_zero_bytes() { return (size_t)kPPar; }
 
 cudaError_t tc64_reset_fcol(int *fcol, int batch, cudaStream_t st)
 {
@@ -685,7 +801,8 @@ size_t tc64_data_bytes(int mmax, int npairs, size_t nchunk_s)
 }
 
 cudaError_t tc64_build(const PlanView<double> &pv, const unsigned long long *off_s, const unsigned long long *off_a,
-                       unsigned char *ps, unsigned char *pa, int *es, int *ea, int *c0_s, int *c0_a, cudaStream_t st)
+                       unsigned char *ps, unsigned char *pa, int *es, int *ea, int *c0_s, int *c0_a,
+                       unsigned short *gf_s, unsigned short *gf_a, cudaStream_t st)
 {
     const int nlm = pv.nlm;
     k_fill_int<<<(unsigned)((nlm + 255) / 256), 256, 0, st>>>(ea, kExpNone, (size_t)nlm);
@@ -698,11 +815,16 @@ cudaError_t tc64_build(const PlanView<double> &pv, const unsigned long long *off
                                                                                  ps, c0_s);
     k_p64_first_live<<<dim3((unsigned)ta, (unsigned)(pv.mmax + 1)), 256, 0, st>>>(0, pv.lmax, pv.mres, pv.npairs, ta, off_a,
                                                                                  pa, c0_a);
+    k_p64_group_first<<<dim3((unsigned)ts, (unsigned)(pv.mmax + 1)), 256, 0, st>>>(1, pv.lmax, pv.mres, pv.npairs, ts,
+                                                                                  off_s, ps, gf_s);
+    k_p64_group_first<<<dim3((unsigned)ta, (unsigned)(pv.mmax + 1)), 256, 0, st>>>(0, pv.lmax, pv.mres, pv.npairs, ta,
+                                                                                  off_a, pa, gf_a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc64(bool synth, int lmax, int mmax, int mres, int npairs, int nlm, const unsigned char *panel,
-                        const unsigned long long *off, const int *c0, const int *sched, int nctas, const int *erow,
+                        const unsigned long long *off, const int *c0, const unsigned short *gf,
+                        const unsigned char *zero, const int *sched, int nctas, const int *erow,
                         const unsigned long long *dchunk, int *fcol, unsigned char *data, const double *in,
                         double *out, int batch, Op op, int *err, cudaStream_t st, bool fcol_ready)
 {
@@ -730,6 +852,8 @@ cudaError_t launch_tc64(bool synth, int lmax, int mmax, int mres, int npairs, in
     a.panel = panel;
     a.off = off;
     a.c0 = c0;
+    a.gf = gf;
+    a.zero = zero;
     a.erow = erow;
     a.fcol = fcol;
     a.data = data;
@@ -741,7 +865,7 @@ cudaError_t launch_tc64(bool synth, int lmax, int mmax, int mres, int npairs, in
     a.ntiles = synth ? ts : ta;
     // ring, barriers (2 per stage, 2 for the accumulator, the drain) and the TMEM slot
     const size_t smem = 128 + (size_t)kStages * kStage + 8 * (2 * kStages + 3) + 16;
-    if (!sched || nctas < 1) return cudaErrorInvalidValue;
+    if (!sched || nctas < 1 || !gf || !zero) return cudaErrorInvalidValue;
     cudaError_t e;
     if (synth) {
         e = cudaFuncSetAttribute(k_tc64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
