@@ -129,7 +129,13 @@ __host__ __device__ constexpr double sin64(int k) { return cos64(k - 16); }
 template <typename T2, int SIGN>
 struct Tw64 {
     using T = decltype(T2::x);
-    __device__ __forceinline__ static T2 mul(int q, T2 z) { return cmul(mk<T2>(T(cos64(q)), T(SIGN * sin64(q))), z); }
+    __device__ __forceinline__ static T2 mul(int q, T2 z)
+    {
+        // z (SIGN i): a swap and a sign (a general product by (0, +-1) keeps
+        // its multiplications by zero, which IEEE arithmetic cannot drop)
+        if (q == 16) return SIGN > 0 ? mk<T2>(-z.y, z.x) : mk<T2>(z.y, -z.x);
+        return cmul(mk<T2>(T(cos64(q)), T(SIGN * sin64(q))), z);
+    }
 };
 template <int SIGN>
 struct Tw64<dfl2, SIGN> {
