@@ -1012,7 +1012,15 @@ struct RowShape {
     static constexpr int LD = LDN > N2 * LDT ? LDN : N2 * LDT;
 };
 
-__host__ __device__ constexpr size_t row_fft_smem(int ld) { return (size_t)2 * kRowPairs * ld * sizeof(float2); }
+// Pairs per row-FFT tile (one CTA of 8 warps).  H = 512 = 32 x 16: one warp
+// per latitude pair (8 pairs), each half-warp one of the pair's rows in the
+// first DFT (lane 16 h + n2 holds z[n2 + 16 n1] of row h) and every lane both
+// rows' columns in the second (lane k1 holds Z[k1 + 32 k2], k2 < 16, of both):
+// no lane idles, where one warp per row leaves half the lanes idle in the
+// first DFT.  Other lengths: one warp per row (4 pairs).
+template <int LOGH> struct RowPairs { static constexpr int n = LOGH == 9 ? 8 : kRowPairs; };
+__host__ __device__ inline int row_pairs(int logH) { return logH == 9 ? 8 : kRowPairs; }
+__host__ __device__ constexpr size_t row_fft_smem(int ld, int rp) { return (size_t)2 * rp * ld * sizeof(float2); }
 
 // Runtime row length of RowShape<logH>.
 __host__ __device__ inline int row_ld(int logH)
@@ -1022,8 +1030,8 @@ __host__ __device__ inline int row_ld(int logH)
     return ldn > N2 * (N1 + 1) ? ldn : N2 * (N1 + 1);
 }
 
-// One synthesis tile (field b, pairs p0 .. p0 + kRowPairs - 1), run by a CTA of
-// 64 kRowPairs threads; smem_raw holds row_fft_smem(LD) bytes.
+// One synthesis tile (field b, pairs p0 .. p0 + RowPairs - 1), run by a CTA of
+// 64 kRowPairs threads; smem_raw holds row_fft_smem(LD, RowPairs) bytes.
 template <int LOGH>
 __device__ __forceinline__ void fft_synth_rows_tile(const PlanView<float> &pv, const float *__restrict__ eo,
                                                     float *__restrict__ grid, int b, int p0, int op,
@@ -1031,11 +1039,12 @@ __device__ __forceinline__ void fft_synth_rows_tile(const PlanView<float> &pv, c
 {
     using S = RowShape<LOGH>;
     constexpr int H = S::H, N1 = S::N1, N2 = S::N2, LD = S::LD, LDT = S::LDT;
+    constexpr int RP = RowPairs<LOGH>::n;
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
     const int mmax = pv.mmax, npairs = pv.npairs, nlat = pv.nlat;
     // 1. spectra of the CTA's rows: X_north = E + O, X_south = E - O, zero above
     //    mmax; the loads of a batch of U items are issued before their stores
-    constexpr int NT = 64 * kRowPairs, NQ = kRowPairs * H, U = 16;
+    constexpr int NT = 64 * kRowPairs, NQ = RP * H, U = 16;
     const float4 *eo4 = reinterpret_cast<const float4 *>(eo);
 #pragma unroll 1
     for (int q0 = threadIdx.x; q0 < NQ; q0 += U * NT) {
@@ -1043,7 +1052,7 @@ __device__ __forceinline__ void fft_synth_rows_tile(const PlanView<float> &pv, c
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int q = q0 + u * NT;
-            const int m = q / kRowPairs, p = p0 + (q - m * kRowPairs);
+            const int m = q / RP, p = p0 + (q - m * RP);
             v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (q < NQ && m <= mmax && p < npairs) v[u] = eo4[((size_t)b * (mmax + 1) + m) * npairs + p];
         }
@@ -1051,7 +1060,7 @@ __device__ __forceinline__ void fft_synth_rows_tile(const PlanView<float> &pv, c
         for (int u = 0; u < U; ++u) {
             const int q = q0 + u * NT;
             if (q >= NQ) break;
-            const int m = q / kRowPairs, i = q - m * kRowPairs;
+            const int m = q / RP, i = q - m * RP;
             const float2 XN = make_float2(v[u].x + v[u].z, m == 0 ? 0.f : v[u].y + v[u].w);
             const float2 XS = make_float2(v[u].x - v[u].z, m == 0 ? 0.f : v[u].y - v[u].w);
             buf[(2 * i) * LD + padi(m)] = XN;
@@ -1060,6 +1069,52 @@ __device__ __forceinline__ void fft_synth_rows_tile(const PlanView<float> &pv, c
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr (RP != kRowPairs) {
+        // a warp per pair (see RowPairs): half-warp h, row h of pair p, in the first DFT
+        static_assert(N1 == 32 && N2 == 16, "a half-warp per row in the first DFT");
+        const int p = p0 + warp;
+        if (p >= npairs) return;   // no barrier follows in this tile
+        const int h = lane >> 4, n2 = lane & 15;
+        const bool equator = (nlat & 1) && p == npairs - 1;   // one row only
+        float2 *row = buf + (2 * warp + h) * LD;
+        float2 v[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) {
+            const int k = n2 + N2 * n1;
+            const float2 Xa = row[padi(k)];
+            if (k == 0) {
+                v[n1] = cadd(Xa, mul_i(Xa));
+            } else {
+                const float2 Xb = row[padi(H - k)];
+                v[n1] = cadd(cadd(Xa, conj_(Xb)), mul_i(cmul(pv.tw[k], csub(Xa, conj_(Xb)))));
+            }
+        }
+        RegDft<float2, N1, 1>::run(v);
+        __syncwarp();
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) row[n2 * LDT + k1] = k1 == 0 ? v[k1] : cmul(v[k1], pv.rtw[k1 * N2 + n2]);
+        __syncwarp();
+        const float2 *r0 = buf + (2 * warp) * LD, *r1 = r0 + LD;
+        float2 u0[N2], u1[N2];
+#pragma unroll
+        for (int m2 = 0; m2 < N2; ++m2) {
+            u0[m2] = r0[m2 * LDT + lane];
+            u1[m2] = r1[m2 * LDT + lane];
+        }
+        RegDft<float2, N2, 1>::run(u0);
+        RegDft<float2, N2, 1>::run(u1);
+        float scale = 1.f;
+        if (op == OP_ANALYS_ADJ) scale = float(kTwoPiD) / float(pv.nphi) * pv.wq[p];
+        float2 *outN = reinterpret_cast<float2 *>(grid) + ((size_t)b * nlat + p) * H;
+        float2 *outS = reinterpret_cast<float2 *>(grid) + ((size_t)b * nlat + (nlat - 1 - p)) * H;
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) outN[lane + N1 * k2] = make_float2(u0[k2].x * scale, u0[k2].y * scale);
+        if (!equator) {
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) outS[lane + N1 * k2] = make_float2(u1[k2].x * scale, u1[k2].y * scale);
+        }
+        return;
+    }
     const int p = p0 + (warp >> 1);
     const int j = (warp & 1) ? nlat - 1 - p : p;
     if (p >= npairs || ((warp & 1) && j == p)) return;   // no barrier follows in this tile
@@ -1114,9 +1169,44 @@ __device__ __forceinline__ void fft_analys_rows_tile(const PlanView<float> &pv, 
 {
     using S = RowShape<LOGH>;
     constexpr int H = S::H, N1 = S::N1, N2 = S::N2, LD = S::LD, LDT = S::LDT;
+    constexpr int RP = RowPairs<LOGH>::n;
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
     const int mmax = pv.mmax, npairs = pv.npairs, nlat = pv.nlat;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr (RP != kRowPairs) {
+        // a warp per pair (see RowPairs); the south row of an equator pair is
+        // the north one again, transformed and never folded in
+        static_assert(N1 == 32 && N2 == 16, "a half-warp per row in the first DFT");
+        const int p = p0 + warp;
+        if (p < npairs) {
+            const int h = lane >> 4, n2 = lane & 15;
+            float2 *row = buf + (2 * warp + h) * LD;
+            const float2 *in = reinterpret_cast<const float2 *>(grid) + ((size_t)b * nlat + (h ? nlat - 1 - p : p)) * H;
+            float2 v[N1];
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) v[n1] = in[n2 + N2 * n1];
+            RegDft<float2, N1, -1>::run(v);
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1)
+                row[n2 * LDT + k1] = k1 == 0 ? v[k1] : cmul(v[k1], conj_(pv.rtw[k1 * N2 + n2]));
+            __syncwarp();
+            float2 *r0 = buf + (2 * warp) * LD, *r1 = r0 + LD;
+            float2 u0[N2], u1[N2];
+#pragma unroll
+            for (int m2 = 0; m2 < N2; ++m2) {
+                u0[m2] = r0[m2 * LDT + lane];
+                u1[m2] = r1[m2 * LDT + lane];
+            }
+            RegDft<float2, N2, -1>::run(u0);
+            RegDft<float2, N2, -1>::run(u1);
+            __syncwarp();
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                r0[padi(lane + N1 * k2)] = u0[k2];
+                r1[padi(lane + N1 * k2)] = u1[k2];
+            }
+        }
+    } else {
     const int p = p0 + (warp >> 1);
     const int j = (warp & 1) ? nlat - 1 - p : p;
     const bool live = p < npairs && !((warp & 1) && j == p);
@@ -1146,12 +1236,13 @@ __device__ __forceinline__ void fft_analys_rows_tile(const PlanView<float> &pv, 
             for (int k2 = 0; k2 < N2; ++k2) row[padi(lane + N1 * k2)] = u[k2];
         }
     }
+    }
     __syncthreads();
     // 2. post-twiddle, scale, fold north/south, weight
     float4 *sd4 = reinterpret_cast<float4 *>(sd);
     const float fscale = (op == OP_ANALYS) ? float(kTwoPiD) / float(pv.nphi) : 1.f;
-    for (int q = threadIdx.x; q < kRowPairs * (mmax + 1); q += blockDim.x) {
-        const int m = q / kRowPairs, i = q - m * kRowPairs;
+    for (int q = threadIdx.x; q < RP * (mmax + 1); q += blockDim.x) {
+        const int m = q / RP, i = q - m * RP;
         const int pp = p0 + i;
         if (pp >= npairs) continue;
         const bool equator = (nlat & 1) && pp == npairs - 1;
@@ -1187,7 +1278,7 @@ __global__ void __launch_bounds__(64 * kRowPairs, 2)
 k_fft_synth_rows(PlanView<float> pv, const float *__restrict__ eo, float *__restrict__ grid, int op)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fft_synth_rows_tile<LOGH>(pv, eo, grid, blockIdx.y, blockIdx.x * kRowPairs, op, smem_raw);
+    fft_synth_rows_tile<LOGH>(pv, eo, grid, blockIdx.y, blockIdx.x * RowPairs<LOGH>::n, op, smem_raw);
 }
 
 template <int LOGH>
@@ -1195,15 +1286,16 @@ __global__ void __launch_bounds__(64 * kRowPairs, 2)
 k_fft_analys_rows(PlanView<float> pv, const float *__restrict__ grid, float *__restrict__ sd, int op, int vector)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fft_analys_rows_tile<LOGH>(pv, grid, sd, blockIdx.y, blockIdx.x * kRowPairs, op, vector, smem_raw);
+    fft_analys_rows_tile<LOGH>(pv, grid, sd, blockIdx.y, blockIdx.x * RowPairs<LOGH>::n, op, vector, smem_raw);
 }
 
 template <int LOGH>
 cudaError_t launch_rows(bool synth, const PlanView<float> &pv, const float *in, float *out, int batch, Op op,
                         bool vector, cudaStream_t s)
 {
-    const size_t smem = row_fft_smem(RowShape<LOGH>::LD);
-    dim3 g((unsigned)((pv.npairs + kRowPairs - 1) / kRowPairs), (unsigned)batch);
+    constexpr int RP = RowPairs<LOGH>::n;
+    const size_t smem = row_fft_smem(RowShape<LOGH>::LD, RP);
+    dim3 g((unsigned)((pv.npairs + RP - 1) / RP), (unsigned)batch);
     cudaError_t e;
     if (synth) {
         if (smem > 48 * 1024) {
@@ -1406,7 +1498,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_fft(int synth, const BatchFiel
 // (logH <= 10), else 2G rows of max(1, H/16) threads.
 int batch_fft_group(int H, int npairs)
 {
-    if (pow2(H) && ilog2(H) <= kRowLogMax) return kRowPairs;
+    if (pow2(H) && ilog2(H) <= kRowLogMax) return row_pairs(ilog2(H));
     const int TPR = row_tpr(H);
     int G = 256 / (2 * TPR);
     if (G < 1) G = 1;
@@ -1416,7 +1508,7 @@ int batch_fft_group(int H, int npairs)
 
 size_t batch_fft_smem(int H, int G)
 {
-    if (pow2(H) && ilog2(H) <= kRowLogMax) return row_fft_smem(row_ld(ilog2(H)));
+    if (pow2(H) && ilog2(H) <= kRowLogMax) return row_fft_smem(row_ld(ilog2(H)), row_pairs(ilog2(H)));
     const size_t row_bytes = (size_t)((H + (H >> 4)) + 1) * sizeof(float2);
     return (size_t)H * sizeof(float2) + (size_t)2 * G * row_bytes;
 }
