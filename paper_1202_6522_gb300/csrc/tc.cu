@@ -730,8 +730,15 @@ __global__ void __launch_bounds__(192, 1) k_tc_vec(TcArgs a)
                     }
                     unsigned char *st = smem + (size_t)q * stage_bytes;
                     tc::mbar_arrive_expect_tx(&bar_load[q], 2u * pgb + dbytes);
-                    tc::bulk_g2s_stream(st, p0 + (size_t)c * kChunkPanel, pgb, &bar_load[q]);
-                    tc::bulk_g2s_stream(st + kChunkPanel, p1 + (size_t)c * kChunkPanel, pgb, &bar_load[q]);
+                    if (it.half == a.halves - 1) {
+                        // the tile's last use of these panel chunks: evict them first
+                        tc::bulk_g2s_stream(st, p0 + (size_t)c * kChunkPanel, pgb, &bar_load[q]);
+                        tc::bulk_g2s_stream(st + kChunkPanel, p1 + (size_t)c * kChunkPanel, pgb, &bar_load[q]);
+                    } else {
+                        // the next field half of the tile reads them again, from L2
+                        tc::bulk_g2s(st, p0 + (size_t)c * kChunkPanel, pgb, &bar_load[q]);
+                        tc::bulk_g2s(st + kChunkPanel, p1 + (size_t)c * kChunkPanel, pgb, &bar_load[q]);
+                    }
                     tc::bulk_g2s(st + 2 * kChunkPanel, data + (size_t)c * dbytes, dbytes, &bar_load[q]);
                 }
             }
